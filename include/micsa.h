@@ -1,0 +1,145 @@
+/*
+ * micsa.h -- C ABI of the GB300 (sm_103a) microcanonical simulated annealing
+ * library for the 3D Edwards-Anderson +-J spin glass.
+ *
+ * The method (Bernaschi et al., "Microcanonical simulated annealing: massively
+ * parallel Monte Carlo simulations with sporadic random-number generation"):
+ *   - H_EA = -sum_<x,y> J_xy s_x s_y on a periodic L^3 lattice, J = +-1 with
+ *     probability 1/2 (Sec. 2.1, Eq. Hamiltonian);
+ *   - one daemon per spin holding n = 4m, m in {0,1,2,3} (Sec. 2.4, 2.5);
+ *   - elementary move: flip s_x and set n -> n - dH iff 0 <= n - dH <= 12
+ *     (Eq. Creutz, Eq. flip-OK), even sublattice then odd sublattice (Sec. 2.8);
+ *   - the only random numbers: daemons redrawn from Eq. (prob-daemons-walkers)
+ *     at the annealing temperature at refresh times (Sec. 2.7).
+ *
+ * Conventions for every entry point:
+ *   - Return MICSA_OK (0) on success or a negative MICSA_E_* code; nothing
+ *     aborts. micsa_last_error() gives a message for the last failure of a
+ *     handle.
+ *   - Host pointers are owned by the caller and only read or written during
+ *     the call; every call that returns data to the host is synchronous with
+ *     respect to that data. Device memory is owned by the handle.
+ *   - A handle is used by one host thread at a time.
+ *   - Natural layout: site = (z*L + y)*L + x. Couplings are the three forward
+ *     bonds of each site, J[(sample*N + site)*3 + d] = +-1 for the bond between
+ *     site and site + e_d (d = 0: x, 1: y, 2: z), N = L^3. Spins are int8 +-1,
+ *     indexed [(sample*R + replica)*N + site]; daemons the same, uint8 m in
+ *     {0,1,2,3} (energy 4m).
+ *   - L must be even (the checkerboard of Sec. 2.1 needs it), 2 <= L <= 1600.
+ *
+ * Random numbers (the paper names no generator; this is the library's
+ * contract): Philox4x32-10 with key (seed mod 2^32, seed >> 32) and counters
+ *   couplings: (site, 0, sample << 2 | 0, 0), word d >= 2^31 <=> J_{+d} = -1
+ *   spins:     (site, 0, gid << 2 | 1, 0),    word 0 >= 2^31 <=> s = -1
+ *   daemons:   (quad, t mod 2^32, gid << 2 | 2, t >> 32), u = word[lane]
+ *   Metropolis:(quad, t mod 2^32, gid << 2 | 3, t >> 32), u = word[lane]
+ * with gid = sample*R + replica, t the global sweep index, h = x >> 1,
+ * Q = ceil(L/2 / 4), quad = ((p*L + z)*L + y)*Q + (h >> 2), lane = h & 3,
+ * p = (x + y + z) & 1. A refreshed daemon is m = [u >= c0] + [u >= c1] +
+ * [u >= c2] with the cut points of micsa_daemon_thresholds().
+ */
+#ifndef MICSA_H
+#define MICSA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MICSA_OK 0
+#define MICSA_E_INVALID_ARG (-1) /* bad size, odd L, T <= 0 or not finite, interval < 1 */
+#define MICSA_E_OOM (-2)         /* device or host allocation failed */
+#define MICSA_E_CUDA (-3)        /* a CUDA runtime call failed; see micsa_last_error */
+#define MICSA_E_TIMEOUT (-4)     /* a bounded device-side wait gave up */
+#define MICSA_E_BUSY (-5)        /* pool: no free slot or memory for the job now */
+#define MICSA_E_NOT_FOUND (-6)   /* pool: unknown job id */
+
+typedef struct micsa_ctx *micsa_t;
+
+/* Allocate the state of n_samples disorder samples x n_replicas replicas of an
+ * L^3 lattice on the current CUDA device; draw the couplings (Sec. 2.1) and a
+ * fully disordered start (Sec. 3) from `seed`; daemons are zero until the
+ * first refresh; t = 0. *out receives the handle. 1 <= n_replicas <= 32. */
+int micsa_create(int L, int n_samples, int n_replicas, uint64_t seed, micsa_t *out);
+
+/* Start over on the resident memory: redraw couplings and spins from `seed`
+ * exactly as micsa_create does, zero the daemons, set t = 0. Asynchronous on
+ * the handle's stream; no host data moves. */
+int micsa_reinit(micsa_t h, uint64_t seed);
+
+/* Replace the couplings with host J[S][N][3] of +-1 (natural layout). Spins,
+ * daemons and t are kept. */
+int micsa_set_couplings(micsa_t h, const int8_t *J);
+
+/* Copy the couplings back to host J[S][N][3]. */
+int micsa_get_couplings(micsa_t h, int8_t *J);
+
+/* Run n_sweeps MicSA sweeps (Sec. 2.8, gamma = 1 daemon per spin). Sweep k
+ * (k < n_sweeps) has global index t = t0 + k; if t % refresh_interval == 0 all
+ * daemons are redrawn at T = schedule[k] before it (Sec. 2.7, fixed-interval
+ * refresh). Each sweep updates the even sublattice, then the odd one (Eq.
+ * Creutz with Eq. flip-OK). schedule is a host array of n_sweeps finite
+ * temperatures > 0. t advances by n_sweeps and persists across calls, so
+ * run(a) then run(b) equals run(a + b). Asynchronous on the handle's stream. */
+int micsa_run(micsa_t h, const double *schedule, int64_t n_sweeps, int32_t refresh_interval);
+
+/* As micsa_run with the refresh times of the procedure in Sec. 2.8 taken
+ * literally: daemons are redrawn before global sweeps t = 2^s - 1. */
+int micsa_run_logrefresh(micsa_t h, const double *schedule, int64_t n_sweeps);
+
+/* Checkerboard Metropolis at T = schedule[k] (the random-number-greedy
+ * comparison of Sec. 2.3 and App. B): a flip with dH <= 0 is accepted, one
+ * with dH > 0 iff u < c(dH), c from micsa_metro_thresholds. Daemons untouched. */
+int micsa_run_metropolis(micsa_t h, const double *schedule, int64_t n_sweeps);
+
+/* Observables of the current state (Sec. 3, App. C), exact integers:
+ *   energy[S*R]          H_EA per (sample, replica)
+ *   aux[S*R]             H_aux = sum of daemon energies 4m
+ *   overlap[S*R(R-1)/2]  sum_x s^a_x s^b_x for replica pairs a < b of each
+ *                        sample, pairs in lexicographic order.
+ * Host arrays; any may be NULL. Synchronous. */
+int micsa_measure(micsa_t h, int64_t *energy, int64_t *aux, int64_t *overlap);
+
+/* Copy the state to / from host arrays in natural layout: spins[S*R*N] int8
+ * +-1, daemons[S*R*N] uint8 in {0..3}, and the global sweep index t. Any
+ * pointer may be NULL (that part is skipped). set_state validates values. */
+int micsa_get_state(micsa_t h, int8_t *spins, uint8_t *daemons, int64_t *t);
+int micsa_set_state(micsa_t h, const int8_t *spins, const uint8_t *daemons, int64_t t);
+
+/* Use `stream` (a cudaStream_t, e.g. torch.cuda.current_stream().cuda_stream)
+ * for all later work of the handle; NULL selects the handle's own stream. */
+int micsa_set_stream(micsa_t h, void *stream);
+
+/* Block until the handle's queued work is done. */
+int micsa_sync(micsa_t h);
+
+/* Device bytes held by the handle. */
+int micsa_device_bytes(micsa_t h, size_t *bytes);
+
+/* Number of CUDA kernels the handle has launched since it was created. */
+int micsa_launch_count(micsa_t h, int64_t *count);
+
+/* Free the handle and its device memory. NULL is allowed. */
+void micsa_destroy(micsa_t h);
+
+/* Message of the last failed call on `h` ("" if none; a static message if h is
+ * NULL). Valid until the next call on h. */
+const char *micsa_last_error(micsa_t h);
+
+/* Cut points of the daemon refresh at temperature T, Eq. (prob-daemons-walkers):
+ * with beta = 1/T, x = exp(-4 beta), p0 = (1 - x)/(1 - x^4) (x^4 as
+ * (x*x)*(x*x); p0 = 1/4 when x == 1), p1 = p0 x, p2 = p1 x, c0 = p0,
+ * c1 = c0 + p1, c2 = c1 + p2 in IEEE double, theta_k = min(floor(c_k 2^32), 2^32).
+ * Host-only; needs no GPU. */
+int micsa_daemon_thresholds(double T, uint64_t theta[3]);
+
+/* Metropolis cut points theta_k = floor(exp(-beta*4(k+1)) 2^32), k = 0, 1, 2
+ * (dH = 4, 8, 12). Host-only. */
+int micsa_metro_thresholds(double T, uint64_t theta[3]);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -20,12 +20,12 @@ def lib_path(mutant=0):
 
 def build(mutant=0, force=False):
     out = lib_path(mutant)
-    newest_src = max(os.path.getmtime(SRC), os.path.getmtime(HDR))
+    newest_src = max(os.path.getmtime(SRC), os.path.getmtime(HDR), os.path.getmtime(__file__))
     if not force and os.path.exists(out) and os.path.getmtime(out) >= newest_src:
         return out
     os.makedirs(OUT_DIR, exist_ok=True)
     tmp = f"{out}.{os.getpid()}.tmp"
-    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-Wall", "-Wextra",
+    cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-Wall", "-Wextra", "-ffp-contract=off",
            f"-DORC_MUTANT={int(mutant)}", "-o", tmp, SRC, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, out)  # atomic, so concurrent builders never load a partial file

@@ -1,0 +1,201 @@
+"""Python binding of ``libmicsa.so`` (include/micsa.h): argument marshalling only.
+
+Every step of the simulation runs in the library's CUDA kernels; this module
+converts numpy arrays / Python numbers to the C ABI and raises on error codes.
+There is no CPU fallback: if the compiled library is missing the import of
+:func:`lib` fails loudly.
+
+Natural layout (as in the C ABI): ``site = (z*L + y)*L + x``; couplings
+``J[S, N, 3]`` (+-1 for the +x, +y, +z bonds of each site), spins
+``s[S, R, N]`` int8 +-1, daemons ``m[S, R, N]`` uint8 (energy 4m).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "libmicsa.so")
+
+MICSA_OK = 0
+MICSA_E_INVALID_ARG = -1
+MICSA_E_OOM = -2
+MICSA_E_CUDA = -3
+MICSA_E_TIMEOUT = -4
+MICSA_E_BUSY = -5
+MICSA_E_NOT_FOUND = -6
+
+_ERRNAMES = {-1: "MICSA_E_INVALID_ARG", -2: "MICSA_E_OOM", -3: "MICSA_E_CUDA",
+             -4: "MICSA_E_TIMEOUT", -5: "MICSA_E_BUSY", -6: "MICSA_E_NOT_FOUND"}
+
+
+class MicsaError(RuntimeError):
+    def __init__(self, code, msg=""):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+_c = ctypes
+_P = ctypes.c_void_p
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+
+# name -> (restype, argtypes); every symbol of include/micsa.h
+SIGNATURES = {
+    "micsa_create": (_c.c_int, [_c.c_int, _c.c_int, _c.c_int, _c.c_uint64, ctypes.POINTER(_P)]),
+    "micsa_reinit": (_c.c_int, [_P, _c.c_uint64]),
+    "micsa_set_couplings": (_c.c_int, [_P, _P]),
+    "micsa_get_couplings": (_c.c_int, [_P, _P]),
+    "micsa_run": (_c.c_int, [_P, _P, _c.c_int64, _c.c_int32]),
+    "micsa_run_logrefresh": (_c.c_int, [_P, _P, _c.c_int64]),
+    "micsa_run_metropolis": (_c.c_int, [_P, _P, _c.c_int64]),
+    "micsa_measure": (_c.c_int, [_P, _P, _P, _P]),
+    "micsa_get_state": (_c.c_int, [_P, _P, _P, _i64p]),
+    "micsa_set_state": (_c.c_int, [_P, _P, _P, _c.c_int64]),
+    "micsa_set_stream": (_c.c_int, [_P, _P]),
+    "micsa_sync": (_c.c_int, [_P]),
+    "micsa_device_bytes": (_c.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "micsa_launch_count": (_c.c_int, [_P, _i64p]),
+    "micsa_destroy": (None, [_P]),
+    "micsa_last_error": (_c.c_char_p, [_P]),
+    "micsa_daemon_thresholds": (_c.c_int, [_c.c_double, _u64p]),
+    "micsa_metro_thresholds": (_c.c_int, [_c.c_double, _u64p]),
+}
+
+
+def lib():
+    """Load the compiled library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(
+                f"{LIB_PATH} is missing: build it with `python -c \"import __graft_entry__ as g; g.build()\"` "
+                "(there is no CPU fallback)")
+        handle = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+
+
+def _check(rc, h=None):
+    if rc != MICSA_OK:
+        msg = lib().micsa_last_error(h).decode() if h is not None else ""
+        raise MicsaError(rc, msg)
+
+
+def daemon_thresholds(T):
+    th = (ctypes.c_uint64 * 3)()
+    _check(lib().micsa_daemon_thresholds(float(T), th))
+    return np.array(list(th), np.uint64)
+
+
+def metro_thresholds(T):
+    th = (ctypes.c_uint64 * 3)()
+    _check(lib().micsa_metro_thresholds(float(T), th))
+    return np.array(list(th), np.uint64)
+
+
+class Micsa:
+    """One handle of the C ABI: S disorder samples x R replicas of an L^3 lattice."""
+
+    def __init__(self, L, n_samples=1, n_replicas=2, seed=0, stream=None):
+        self.L, self.S, self.R, self.seed = int(L), int(n_samples), int(n_replicas), int(seed)
+        self.N = self.L ** 3
+        h = ctypes.c_void_p()
+        rc = lib().micsa_create(self.L, self.S, self.R, ctypes.c_uint64(self.seed), ctypes.byref(h))
+        if rc != MICSA_OK:
+            raise MicsaError(rc, f"micsa_create(L={L}, S={n_samples}, R={n_replicas})")
+        self.h = h
+        if stream is not None:
+            self.set_stream(stream)
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().micsa_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def set_stream(self, stream):
+        """stream: a torch.cuda.Stream, an integer cudaStream_t, or None."""
+        raw = getattr(stream, "cuda_stream", stream)
+        _check(lib().micsa_set_stream(self.h, ctypes.c_void_p(raw) if raw else None), self.h)
+
+    def reinit(self, seed):
+        """Redraw couplings and spins from `seed` on the device; t = 0."""
+        self.seed = int(seed)
+        _check(lib().micsa_reinit(self.h, ctypes.c_uint64(self.seed)), self.h)
+
+    def set_couplings(self, J):
+        J = np.ascontiguousarray(J, np.int8)
+        assert J.size == self.S * self.N * 3
+        _check(lib().micsa_set_couplings(self.h, _ptr(J)), self.h)
+
+    def get_couplings(self):
+        J = np.zeros((self.S, self.N, 3), np.int8)
+        _check(lib().micsa_get_couplings(self.h, _ptr(J)), self.h)
+        return J
+
+    def run(self, schedule, refresh_interval):
+        sched = np.ascontiguousarray(schedule, np.float64)
+        _check(lib().micsa_run(self.h, _ptr(sched), len(sched), int(refresh_interval)), self.h)
+
+    def run_logrefresh(self, schedule):
+        sched = np.ascontiguousarray(schedule, np.float64)
+        _check(lib().micsa_run_logrefresh(self.h, _ptr(sched), len(sched)), self.h)
+
+    def run_metropolis(self, schedule):
+        sched = np.ascontiguousarray(schedule, np.float64)
+        _check(lib().micsa_run_metropolis(self.h, _ptr(sched), len(sched)), self.h)
+
+    def measure(self):
+        """(energy[S*R], aux[S*R], overlap[S*R(R-1)/2]) as int64 arrays."""
+        e = np.zeros(self.S * self.R, np.int64)
+        a = np.zeros(self.S * self.R, np.int64)
+        q = np.zeros(self.S * self.R * (self.R - 1) // 2, np.int64)
+        _check(lib().micsa_measure(self.h, _ptr(e), _ptr(a), _ptr(q) if q.size else None), self.h)
+        return e, a, q
+
+    def get_state(self):
+        s = np.zeros((self.S, self.R, self.N), np.int8)
+        m = np.zeros((self.S, self.R, self.N), np.uint8)
+        t = ctypes.c_int64()
+        _check(lib().micsa_get_state(self.h, _ptr(s), _ptr(m), ctypes.byref(t)), self.h)
+        return s, m, t.value
+
+    def set_state(self, spins=None, daemons=None, t=0):
+        s = None if spins is None else np.ascontiguousarray(spins, np.int8)
+        m = None if daemons is None else np.ascontiguousarray(daemons, np.uint8)
+        _check(lib().micsa_set_state(self.h, _ptr(s), _ptr(m), int(t)), self.h)
+
+    def sync(self):
+        _check(lib().micsa_sync(self.h), self.h)
+
+    def launch_count(self):
+        n = ctypes.c_int64()
+        _check(lib().micsa_launch_count(self.h, ctypes.byref(n)), self.h)
+        return n.value
+
+    def device_bytes(self):
+        n = ctypes.c_size_t()
+        _check(lib().micsa_device_bytes(self.h, ctypes.byref(n)), self.h)
+        return n.value

@@ -1,0 +1,424 @@
+// micsa_api.cu -- host side of the C ABI declared in include/micsa.h: argument
+// checking, device memory of a handle, the refresh cut points (host FP64) and
+// the launch sequence of a run (Sec. 2.8 procedure with gamma = 1).
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "micsa_internal.h"
+#include "../../include/micsa.h"
+
+using namespace micsa;
+
+struct micsa_ctx {
+    int L = 0, S = 0, R = 0;
+    uint64_t seed = 0;
+    int64_t t = 0;
+    Geometry geo{};
+    int device = 0;
+    int8_t *d_spins = nullptr;
+    uint8_t *d_daemons = nullptr;
+    uint8_t *d_bonds = nullptr;
+    unsigned long long *d_meas = nullptr;
+    uint8_t *d_stage = nullptr;  // natural-layout staging for state / coupling copies
+    size_t stage_bytes = 0;
+    size_t device_bytes = 0;
+    int64_t launches = 0;  // kernels launched by this handle
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    std::string err;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+int fail(micsa_t h, int code, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+int fail(micsa_t h, int code, const char *fmt, ...) {
+    if (h) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        h->err = buf;
+    }
+    return code;
+}
+
+int cuda_fail(micsa_t h, cudaError_t e, const char *what) {
+    return fail(h, e == cudaErrorMemoryAllocation ? MICSA_E_OOM : MICSA_E_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define CK(h, expr, what)                                    \
+    do {                                                     \
+        cudaError_t e_ = (expr);                             \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, what); \
+    } while (0)
+
+int64_t sites(const micsa_ctx *h) { return (int64_t)h->L * h->L * h->L; }
+
+uint64_t cut_point(double c) {
+    const double v = std::floor(c * 4294967296.0);
+    if (v >= 4294967296.0) return 4294967296ull;
+    if (v <= 0.0) return 0;
+    return (uint64_t)v;
+}
+
+bool temperature_ok(double T) { return T > 0.0 && std::isfinite(T); }
+
+int ensure_stage(micsa_t h, size_t bytes) {
+    if (h->stage_bytes >= bytes) return MICSA_OK;
+    if (h->d_stage) {
+        CK(h, cudaStreamSynchronize(h->stream), "synchronize before staging realloc");
+        cudaFree(h->d_stage);
+        h->device_bytes -= h->stage_bytes;
+        h->d_stage = nullptr;
+        h->stage_bytes = 0;
+    }
+    CK(h, cudaMalloc(&h->d_stage, bytes), "cudaMalloc staging");
+    h->stage_bytes = bytes;
+    h->device_bytes += bytes;
+    return MICSA_OK;
+}
+
+SweepArgs sweep_args(const micsa_ctx *h) {
+    SweepArgs a{};
+    a.spins = h->d_spins;
+    a.daemons = h->d_daemons;
+    a.bonds = h->d_bonds;
+    a.geo = h->geo;
+    a.S = h->S;
+    a.R = h->R;
+    a.key0 = (uint32_t)(h->seed & 0xFFFFFFFFu);
+    a.key1 = (uint32_t)(h->seed >> 32);
+    return a;
+}
+
+// One sweep: even half, then odd half (Sec. 2.8 steps (i), (ii)).
+int launch_sweep(micsa_t h, SweepArgs a, int mode, const uint64_t th[3]) {
+    a.th0 = th[0];
+    a.th1 = th[1];
+    a.th2 = th[2];
+    for (int p = 0; p < 2; ++p) {
+        a.parity = p;
+        CK(h, launch_half_sweep(a, mode, h->stream), "half-sweep launch");
+        ++h->launches;
+    }
+    return MICSA_OK;
+}
+
+// Couplings and spins from the seed (Sec. 2.1 and the disordered start of
+// Sec. 3), daemons zero, t = 0.
+int init_from_seed(micsa_t h, uint64_t seed) {
+    const size_t state = (size_t)h->S * h->R * 2 * h->geo.half;
+    const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFu), k1 = (uint32_t)(seed >> 32);
+    h->seed = seed;
+    CK(h, cudaMemsetAsync(h->d_daemons, 0, state, h->stream), "memset daemons");
+    CK(h, launch_init_couplings(h->d_bonds, h->geo, h->S, k0, k1, h->stream), "init couplings");
+    CK(h, launch_init_spins(h->d_spins, h->geo, h->S, h->R, k0, k1, h->stream), "init spins");
+    h->launches += 2;
+    h->t = 0;
+    return MICSA_OK;
+}
+
+template <class IsRefresh>
+int run_micsa(micsa_t h, const double *schedule, int64_t n_sweeps, IsRefresh is_refresh) {
+    if (!h) return MICSA_E_INVALID_ARG;
+    if (n_sweeps < 0 || (n_sweeps > 0 && !schedule))
+        return fail(h, MICSA_E_INVALID_ARG, "n_sweeps must be >= 0 and schedule non-NULL");
+    for (int64_t k = 0; k < n_sweeps; ++k)
+        if (!temperature_ok(schedule[k]))
+            return fail(h, MICSA_E_INVALID_ARG, "schedule[%lld] = %g is not a finite T > 0",
+                        (long long)k, schedule[k]);
+    DeviceGuard dg(h->device);
+    SweepArgs a = sweep_args(h);
+    const uint64_t none[3] = {0, 0, 0};
+    for (int64_t k = 0; k < n_sweeps; ++k) {
+        a.t = h->t + k;
+        if (is_refresh(a.t)) {
+            uint64_t th[3];
+            micsa_daemon_thresholds(schedule[k], th);
+            if (int rc = launch_sweep(h, a, kModeRefresh, th)) return rc;
+        } else {
+            if (int rc = launch_sweep(h, a, kModeMicsa, none)) return rc;
+        }
+    }
+    h->t += n_sweeps;
+    return MICSA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int micsa_daemon_thresholds(double T, uint64_t theta[3]) {
+    if (!theta || !temperature_ok(T)) return MICSA_E_INVALID_ARG;
+    const double beta = 1.0 / T;
+    const double x = std::exp(-4.0 * beta);
+    double p0;
+    if (x == 1.0) {
+        p0 = 0.25;
+    } else {
+        const double x2 = x * x;
+        const double x4 = x2 * x2;
+        p0 = (1.0 - x) / (1.0 - x4);
+    }
+    const double p1 = p0 * x;
+    const double p2 = p1 * x;
+    const double c0 = p0;
+    const double c1 = c0 + p1;
+    const double c2 = c1 + p2;
+    theta[0] = cut_point(c0);
+    theta[1] = cut_point(c1);
+    theta[2] = cut_point(c2);
+    return MICSA_OK;
+}
+
+int micsa_metro_thresholds(double T, uint64_t theta[3]) {
+    if (!theta || !temperature_ok(T)) return MICSA_E_INVALID_ARG;
+    const double beta = 1.0 / T;
+    for (int k = 0; k < 3; ++k) theta[k] = cut_point(std::exp(-beta * 4.0 * (k + 1)));
+    return MICSA_OK;
+}
+
+const char *micsa_last_error(micsa_t h) {
+    if (!h) return "invalid handle (NULL)";
+    return h->err.c_str();
+}
+
+void micsa_destroy(micsa_t h) {
+    if (!h) return;
+    DeviceGuard dg(h->device);
+    if (h->stream) cudaStreamSynchronize(h->stream);
+    cudaFree(h->d_spins);
+    cudaFree(h->d_daemons);
+    cudaFree(h->d_bonds);
+    cudaFree(h->d_meas);
+    cudaFree(h->d_stage);
+    if (h->own_stream) cudaStreamDestroy(h->own_stream);
+    delete h;
+}
+
+int micsa_create(int L, int n_samples, int n_replicas, uint64_t seed, micsa_t *out) {
+    if (!out) return MICSA_E_INVALID_ARG;
+    *out = nullptr;
+    if (L < 2 || L > 1600 || (L & 1) || n_samples < 1 || n_replicas < 1 || n_replicas > 32 ||
+        (int64_t)n_samples * n_replicas >= (1ll << 30))
+        return MICSA_E_INVALID_ARG;
+    micsa_ctx *h = new (std::nothrow) micsa_ctx;
+    if (!h) return MICSA_E_OOM;
+    h->L = L;
+    h->S = n_samples;
+    h->R = n_replicas;
+    h->seed = seed;
+    h->geo = make_geometry(L);
+    int rc = MICSA_OK;
+    do {
+        if (cudaGetDevice(&h->device) != cudaSuccess) { rc = cuda_fail(h, cudaGetLastError(), "cudaGetDevice"); break; }
+        cudaError_t e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) { rc = cuda_fail(h, e, "cudaStreamCreate"); break; }
+        h->stream = h->own_stream;
+        const size_t state = (size_t)h->S * h->R * 2 * h->geo.half;
+        const size_t bonds = (size_t)h->S * 2 * h->geo.half;
+        const size_t meas = sizeof(unsigned long long) * ((size_t)2 * h->S * h->R + (size_t)h->S * h->R * (h->R - 1) / 2);
+        if ((e = cudaMalloc(&h->d_spins, state)) != cudaSuccess) { rc = cuda_fail(h, e, "cudaMalloc spins"); break; }
+        if ((e = cudaMalloc(&h->d_daemons, state)) != cudaSuccess) { rc = cuda_fail(h, e, "cudaMalloc daemons"); break; }
+        if ((e = cudaMalloc(&h->d_bonds, bonds)) != cudaSuccess) { rc = cuda_fail(h, e, "cudaMalloc bonds"); break; }
+        if ((e = cudaMalloc(&h->d_meas, meas)) != cudaSuccess) { rc = cuda_fail(h, e, "cudaMalloc measure"); break; }
+        h->device_bytes = 2 * state + bonds + meas;
+        if ((e = cudaMemsetAsync(h->d_spins, 0, state, h->stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(h->d_daemons, 0, state, h->stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(h->d_bonds, 0, bonds, h->stream)) != cudaSuccess) { rc = cuda_fail(h, e, "cudaMemset"); break; }
+        if ((rc = init_from_seed(h, seed)) != MICSA_OK) break;
+        if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) { rc = cuda_fail(h, e, "create synchronize"); break; }
+    } while (0);
+    if (rc != MICSA_OK) {
+        micsa_destroy(h);
+        return rc;
+    }
+    *out = h;
+    return MICSA_OK;
+}
+
+int micsa_reinit(micsa_t h, uint64_t seed) {
+    if (!h) return MICSA_E_INVALID_ARG;
+    DeviceGuard dg(h->device);
+    return init_from_seed(h, seed);
+}
+
+int micsa_set_couplings(micsa_t h, const int8_t *J) {
+    if (!h) return MICSA_E_INVALID_ARG;
+    if (!J) return fail(h, MICSA_E_INVALID_ARG, "J is NULL");
+    const int64_t n = sites(h) * 3 * h->S;
+    for (int64_t i = 0; i < n; ++i)
+        if (J[i] != 1 && J[i] != -1) return fail(h, MICSA_E_INVALID_ARG, "J[%lld] = %d is not +-1", (long long)i, J[i]);
+    DeviceGuard dg(h->device);
+    if (int rc = ensure_stage(h, (size_t)n)) return rc;
+    CK(h, cudaMemcpyAsync(h->d_stage, J, (size_t)n, cudaMemcpyHostToDevice, h->stream), "copy J");
+    CK(h, launch_pack_couplings(h->d_bonds, reinterpret_cast<const int8_t *>(h->d_stage), h->geo, h->S, h->stream), "pack couplings");
+    ++h->launches;
+    CK(h, cudaStreamSynchronize(h->stream), "set_couplings synchronize");
+    return MICSA_OK;
+}
+
+int micsa_get_couplings(micsa_t h, int8_t *J) {
+    if (!h) return MICSA_E_INVALID_ARG;
+    if (!J) return fail(h, MICSA_E_INVALID_ARG, "J is NULL");
+    const int64_t n = sites(h) * 3 * h->S;
+    DeviceGuard dg(h->device);
+    if (int rc = ensure_stage(h, (size_t)n)) return rc;
+    CK(h, launch_unpack_couplings(reinterpret_cast<int8_t *>(h->d_stage), h->d_bonds, h->geo, h->S, h->stream), "unpack couplings");
+    ++h->launches;
+    CK(h, cudaMemcpyAsync(J, h->d_stage, (size_t)n, cudaMemcpyDeviceToHost, h->stream), "copy J");
+    CK(h, cudaStreamSynchronize(h->stream), "get_couplings synchronize");
+    return MICSA_OK;
+}
+
+int micsa_run(micsa_t h, const double *schedule, int64_t n_sweeps, int32_t refresh_interval) {
+    if (!h) return MICSA_E_INVALID_ARG;
+    if (refresh_interval < 1) return fail(h, MICSA_E_INVALID_ARG, "refresh_interval must be >= 1");
+    return run_micsa(h, schedule, n_sweeps, [=](int64_t t) { return t % refresh_interval == 0; });
+}
+
+int micsa_run_logrefresh(micsa_t h, const double *schedule, int64_t n_sweeps) {
+    return run_micsa(h, schedule, n_sweeps, [](int64_t t) {
+        const uint64_t v = (uint64_t)t + 1;
+        return (v & (v - 1)) == 0;
+    });
+}
+
+int micsa_run_metropolis(micsa_t h, const double *schedule, int64_t n_sweeps) {
+    if (!h) return MICSA_E_INVALID_ARG;
+    if (n_sweeps < 0 || (n_sweeps > 0 && !schedule))
+        return fail(h, MICSA_E_INVALID_ARG, "n_sweeps must be >= 0 and schedule non-NULL");
+    for (int64_t k = 0; k < n_sweeps; ++k)
+        if (!temperature_ok(schedule[k]))
+            return fail(h, MICSA_E_INVALID_ARG, "schedule[%lld] = %g is not a finite T > 0", (long long)k, schedule[k]);
+    DeviceGuard dg(h->device);
+    SweepArgs a = sweep_args(h);
+    for (int64_t k = 0; k < n_sweeps; ++k) {
+        uint64_t th[3];
+        micsa_metro_thresholds(schedule[k], th);
+        a.t = h->t + k;
+        if (int rc = launch_sweep(h, a, kModeMetro, th)) return rc;
+    }
+    h->t += n_sweeps;
+    return MICSA_OK;
+}
+
+int micsa_measure(micsa_t h, int64_t *energy, int64_t *aux, int64_t *overlap) {
+    if (!h) return MICSA_E_INVALID_ARG;
+    DeviceGuard dg(h->device);
+    const size_t SR = (size_t)h->S * h->R;
+    const size_t npair = (size_t)h->S * h->R * (h->R - 1) / 2;
+    const size_t n = 2 * SR + npair;
+    CK(h, cudaMemsetAsync(h->d_meas, 0, n * sizeof(unsigned long long), h->stream), "memset measure");
+    CK(h, launch_measure(h->d_spins, h->d_daemons, h->d_bonds, h->geo, h->S, h->R, h->d_meas, h->stream), "measure launch");
+    ++h->launches;
+    std::vector<long long> host(n);
+    CK(h, cudaMemcpyAsync(host.data(), h->d_meas, n * sizeof(long long), cudaMemcpyDeviceToHost, h->stream), "copy measure");
+    CK(h, cudaStreamSynchronize(h->stream), "measure synchronize");
+    if (energy) std::memcpy(energy, host.data(), SR * sizeof(int64_t));
+    if (aux) std::memcpy(aux, host.data() + SR, SR * sizeof(int64_t));
+    if (overlap && npair) std::memcpy(overlap, host.data() + 2 * SR, npair * sizeof(int64_t));
+    return MICSA_OK;
+}
+
+int micsa_get_state(micsa_t h, int8_t *spins, uint8_t *daemons, int64_t *t) {
+    if (!h) return MICSA_E_INVALID_ARG;
+    DeviceGuard dg(h->device);
+    const int64_t n = (int64_t)h->S * h->R;
+    const size_t bytes = (size_t)(n * sites(h));
+    if (spins || daemons) {
+        if (int rc = ensure_stage(h, bytes)) return rc;
+    }
+    if (spins) {
+        CK(h, launch_convert_sites(reinterpret_cast<uint8_t *>(h->d_spins), h->d_stage, h->geo, n, false, h->stream), "gather spins");
+        ++h->launches;
+        CK(h, cudaMemcpyAsync(spins, h->d_stage, bytes, cudaMemcpyDeviceToHost, h->stream), "copy spins");
+        CK(h, cudaStreamSynchronize(h->stream), "get_state synchronize");
+    }
+    if (daemons) {
+        CK(h, launch_convert_sites(h->d_daemons, h->d_stage, h->geo, n, false, h->stream), "gather daemons");
+        ++h->launches;
+        CK(h, cudaMemcpyAsync(daemons, h->d_stage, bytes, cudaMemcpyDeviceToHost, h->stream), "copy daemons");
+        CK(h, cudaStreamSynchronize(h->stream), "get_state synchronize");
+    }
+    if (t) *t = h->t;
+    return MICSA_OK;
+}
+
+int micsa_set_state(micsa_t h, const int8_t *spins, const uint8_t *daemons, int64_t t) {
+    if (!h) return MICSA_E_INVALID_ARG;
+    if (t < 0) return fail(h, MICSA_E_INVALID_ARG, "t must be >= 0");
+    const int64_t n = (int64_t)h->S * h->R;
+    const size_t bytes = (size_t)(n * sites(h));
+    if (spins)
+        for (size_t i = 0; i < bytes; ++i)
+            if (spins[i] != 1 && spins[i] != -1) return fail(h, MICSA_E_INVALID_ARG, "spins[%zu] = %d is not +-1", i, spins[i]);
+    if (daemons)
+        for (size_t i = 0; i < bytes; ++i)
+            if (daemons[i] > 3) return fail(h, MICSA_E_INVALID_ARG, "daemons[%zu] = %u exceeds 3", i, daemons[i]);
+    DeviceGuard dg(h->device);
+    if (spins || daemons) {
+        if (int rc = ensure_stage(h, bytes)) return rc;
+    }
+    if (spins) {
+        CK(h, cudaMemcpyAsync(h->d_stage, spins, bytes, cudaMemcpyHostToDevice, h->stream), "copy spins");
+        CK(h, launch_convert_sites(reinterpret_cast<uint8_t *>(h->d_spins), h->d_stage, h->geo, n, true, h->stream), "scatter spins");
+        ++h->launches;
+        CK(h, cudaStreamSynchronize(h->stream), "set_state synchronize");
+    }
+    if (daemons) {
+        CK(h, cudaMemcpyAsync(h->d_stage, daemons, bytes, cudaMemcpyHostToDevice, h->stream), "copy daemons");
+        CK(h, launch_convert_sites(h->d_daemons, h->d_stage, h->geo, n, true, h->stream), "scatter daemons");
+        ++h->launches;
+        CK(h, cudaStreamSynchronize(h->stream), "set_state synchronize");
+    }
+    h->t = t;
+    return MICSA_OK;
+}
+
+int micsa_set_stream(micsa_t h, void *stream) {
+    if (!h) return MICSA_E_INVALID_ARG;
+    DeviceGuard dg(h->device);
+    CK(h, cudaStreamSynchronize(h->stream), "synchronize old stream");
+    h->stream = stream ? reinterpret_cast<cudaStream_t>(stream) : h->own_stream;
+    return MICSA_OK;
+}
+
+int micsa_sync(micsa_t h) {
+    if (!h) return MICSA_E_INVALID_ARG;
+    DeviceGuard dg(h->device);
+    CK(h, cudaStreamSynchronize(h->stream), "synchronize");
+    return MICSA_OK;
+}
+
+int micsa_launch_count(micsa_t h, int64_t *count) {
+    if (!h || !count) return MICSA_E_INVALID_ARG;
+    *count = h->launches;
+    return MICSA_OK;
+}
+
+int micsa_device_bytes(micsa_t h, size_t *bytes) {
+    if (!h || !bytes) return MICSA_E_INVALID_ARG;
+    *bytes = h->device_bytes;
+    return MICSA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,154 @@
+// micsa_device.cuh -- device-side building blocks shared by the sweep,
+// initialisation and measurement kernels.
+//
+// Device layout (sublattice split, Sec. 2.1): each (sample, replica) holds two
+// parity halves; a half is L planes (z) x L rows (y) x P bytes, where row
+// (z, y) of parity p stores the L/2 sites x = 2i + ((p + y + z) & 1),
+// i = 0..L/2-1, at bytes 0..L/2-1 and zero padding up to the pitch
+// P = 4 * ceil(L/2 / 4). Spins are int8 +-1 (0x01 / 0xFF), daemons uint8 m in
+// {0..3}; a bond byte per site holds the six incident couplings, bit k set <=>
+// J = -1 for k = 0: +x, 1: +y, 2: +z, 3: -x, 4: -y, 5: -z. Bonds are shared by
+// the replicas of a sample.
+//
+// Four sites of a row travel together in one 32-bit word (byte lane i & 3).
+// Bit 5 of a spin byte is its sign bit (0x01 -> 0, 0xFF -> 1), so the
+// per-lane arithmetic below runs on all four lanes of a word at once.
+#pragma once
+
+#include <cstdint>
+
+namespace micsa {
+
+constexpr uint32_t kTagCoupling = 0, kTagSpin = 1, kTagDaemon = 2, kTagMetro = 3;
+
+// ----------------------------------------------------------------- Philox --
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of the
+// two-multiplier S-box with the Weyl key schedule.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+    constexpr uint32_t kM0 = 0xD2511F53u, kM1 = 0xCD9E8D57u;
+    constexpr uint32_t kW0 = 0x9E3779B9u, kW1 = 0xBB67AE85u;
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(kM0, c.x), lo0 = kM0 * c.x;
+        const uint32_t hi1 = __umulhi(kM1, c.z), lo1 = kM1 * c.z;
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += kW0;
+        k1 += kW1;
+    }
+    return c;
+}
+
+__device__ __forceinline__ uint32_t lane_of(uint4 w, int lane) {
+    return lane == 0 ? w.x : lane == 1 ? w.y : lane == 2 ? w.z : w.w;
+}
+
+// ------------------------------------------------------------- geometry --
+struct Geometry {
+    int L;        // linear size (even)
+    int Lh;       // L / 2 sites per row of one parity
+    int P;        // row pitch in bytes (multiple of 4)
+    int W;        // 32-bit words per row, P / 4
+    int64_t half; // bytes of one parity half, L * L * P
+};
+
+// ------------------------------------------------- neighbour word assembly --
+// O[0..NW-1]: words of the opposite-parity row that sits at the same (y, z),
+// covering bytes [b0, b0 + 4 NW) of the row. Builds the +x and -x neighbour
+// words of the own-parity sites in the same byte range. `o` is the own row's
+// x offset ((p + y + z) & 1): for o = 0 site i sits at x = 2i, its +x
+// neighbour is O[i] and its -x neighbour O[i-1]; for o = 1 (x = 2i + 1) they
+// are O[i+1] and O[i]. `edge` is the byte just before the range (o = 0) or
+// just after it (o = 1), `first` and `last` the row's bytes 0 and Lh - 1 for
+// the periodic wrap.
+template <int NW>
+__device__ __forceinline__ void x_neighbours(const uint32_t (&O)[NW], int o, int b0, int Lh,
+                                             uint32_t edge, uint32_t first, uint32_t last,
+                                             uint32_t (&xp)[NW], uint32_t (&xm)[NW]) {
+    if (o == 0) {
+        const uint32_t prev = (b0 == 0) ? last : edge;
+#pragma unroll
+        for (int j = 0; j < NW; ++j) {
+            xp[j] = O[j];
+            xm[j] = (O[j] << 8) | (j == 0 ? prev : (O[j - 1] >> 24));
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < NW; ++j) {
+            xm[j] = O[j];
+            xp[j] = (O[j] >> 8) | ((j + 1 < NW ? (O[j + 1] & 0xFFu) : edge) << 24);
+        }
+        const int e = Lh - 1 - b0;  // position of the row's last site in this range
+        if (e >= 0 && e < 4 * NW) {
+#pragma unroll
+            for (int j = 0; j < NW; ++j)
+                if ((e >> 2) == j) {
+                    const int sh = 8 * (e & 3);
+                    xp[j] = (xp[j] & ~(0xFFu << sh)) | (first << sh);
+                }
+        }
+    }
+}
+
+// Mask of the byte lanes of word j (bytes b0 + 4j ..) that hold real sites.
+__device__ __forceinline__ uint32_t valid_mask(int b0, int j, int Lh) {
+    const int n = Lh - (b0 + 4 * j);
+    if (n >= 4) return 0xFFFFFFFFu;
+    if (n <= 0) return 0u;
+    return 0xFFFFFFFFu >> (8 * (4 - n));
+}
+
+// 0xFF in every byte lane whose most significant bit is set, 0x00 elsewhere.
+// (__byte_perm selects bytes with the low three selector bits only and does not
+// replicate signs, so the expansion is done arithmetically.)
+__device__ __forceinline__ uint32_t lanes_from_msb(uint32_t x) {
+    return ((x >> 7) & 0x01010101u) * 0xFFu;
+}
+
+// Bond word shifted so that the bit of direction k lands on bit 5 of each lane.
+struct BondPlanes {
+    uint32_t xp, yp, zp, xm, ym, zm;
+};
+
+__device__ __forceinline__ BondPlanes bond_planes(uint32_t B) {
+    return {B << 5, B << 4, B << 3, B << 2, B << 1, B};
+}
+
+// 32 * (number of frustrated-or-not bonds whose J s_nb is negative) per lane:
+// bit 5 of (neighbour ^ shifted bond) is set iff J s_nb = -1.
+__device__ __forceinline__ uint32_t negative_terms(const BondPlanes &b, uint32_t xp, uint32_t xm,
+                                                   uint32_t yp, uint32_t ym, uint32_t zp,
+                                                   uint32_t zm) {
+    constexpr uint32_t M = 0x20202020u;
+    return ((xp ^ b.xp) & M) + ((xm ^ b.xm) & M) + ((yp ^ b.yp) & M) + ((ym ^ b.ym) & M) +
+           ((zp ^ b.zp) & M) + ((zm ^ b.zm) & M);
+}
+
+// Per lane: 32 * u, u = number of unsatisfied bonds of the site (J s s_nb = -1),
+// from the negative-term count and the site's own spin word S.
+__device__ __forceinline__ uint32_t unsatisfied32(uint32_t neg, uint32_t S) {
+    const uint32_t smask = lanes_from_msb(S);  // 0xFF where s = -1 (0xFF), 0 where s = +1
+    const uint32_t pos = 0xC0C0C0C0u - neg;             // 32 * (6 - count)
+    return neg ^ ((neg ^ pos) & smask);
+}
+
+// The elementary move on four lanes. With u unsatisfied bonds dH = 12 - 4u, so
+// Eq. (flip-OK), 0 <= 4m - dH <= 12, reads 3 <= u + m <= 6 and Eq. (Creutz)
+// gives m' = u + m - 3. Returns the byte mask of accepted lanes and updates
+// D (daemons) in place.
+__device__ __forceinline__ uint32_t creutz4(uint32_t u32, uint32_t &D, uint32_t valid) {
+    const uint32_t t = (u32 >> 5) + D;         // u + m in 0..9 per lane
+    const uint32_t v = t + 0x7D7D7D7Du;         // 0x80..0x83 <=> accepted
+    const uint32_t ok = v & ~(v << 5) & 0x80808080u;
+    const uint32_t am = lanes_from_msb(ok) & valid;
+    D = (D & ~am) | (v & 0x03030303u & am);
+    return am;
+}
+
+// Daemon value from a uniform word and the three refresh cut points.
+__device__ __forceinline__ uint32_t daemon_from_uniform(uint32_t u, uint64_t c0, uint64_t c1,
+                                                        uint64_t c2) {
+    const uint64_t v = u;
+    return (uint32_t)(v >= c0) + (uint32_t)(v >= c1) + (uint32_t)(v >= c2);
+}
+
+}  // namespace micsa

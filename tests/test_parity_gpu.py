@@ -1,0 +1,177 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, bit-exact
+on spins, daemons and integer observables (the integer update of Eq. Creutz /
+Eq. flip-OK leaves no room for rounding), and within 1e-9 relative on the
+derived doubles e = H/N and q^2.
+
+Sizes span several 16-byte chunks and ragged rows: L/2 not a multiple of 4
+(L = 2, 6, 10, 18, 34) uses the 4-byte path with padding lanes, L = 30 and 62
+the 16-byte path with a ragged last word, L = 32, 64, 160 the aligned 16-byte
+path.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2506_16240_gb300 as micsa
+
+pytestmark = pytest.mark.gpu
+
+O = oracle.Oracle()
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _library():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    micsa.lib()
+
+
+def assert_same_state(g, st, what=""):
+    s, m, t = g.get_state()
+    assert t == st["t"], what
+    np.testing.assert_array_equal(s, st["s"], err_msg=f"spins {what}")
+    np.testing.assert_array_equal(m, st["m"], err_msg=f"daemons {what}")
+    e, a, q = g.measure()
+    eo, ao, qo = O.measure(st)
+    np.testing.assert_array_equal(e, eo, err_msg=f"energy {what}")
+    np.testing.assert_array_equal(a, ao, err_msg=f"aux {what}")
+    np.testing.assert_array_equal(q, qo, err_msg=f"overlap {what}")
+
+
+@pytest.mark.parametrize("L", [2, 4, 6, 8, 10, 16, 18, 24, 30, 32, 34, 62, 64])
+def test_initial_state_matches_oracle(L):
+    S, R, seed = 2, 3, 1000 + L
+    with micsa.Micsa(L, S, R, seed) as g:
+        st = O.create(L, S, R, seed)
+        np.testing.assert_array_equal(g.get_couplings(), st["J"])
+        assert_same_state(g, st, f"L={L} initial")
+
+
+@pytest.mark.parametrize("L,S,R,n,interval", [
+    (2, 3, 2, 40, 3), (4, 2, 3, 33, 5), (6, 2, 2, 41, 4), (8, 1, 1, 60, 10), (10, 1, 4, 25, 7),
+    (16, 2, 2, 30, 10), (18, 1, 3, 21, 5), (24, 2, 1, 23, 10), (30, 1, 2, 20, 6),
+    (32, 2, 2, 24, 10), (34, 1, 2, 13, 1), (62, 1, 2, 9, 3), (64, 1, 2, 11, 10),
+])
+def test_micsa_run_bit_exact(L, S, R, n, interval):
+    seed = 7 * L + R
+    sched = np.linspace(2.8, 0.4, n)
+    with micsa.Micsa(L, S, R, seed) as g:
+        st = O.create(L, S, R, seed)
+        g.run(sched, interval)
+        O.run(st, sched, interval)
+        assert_same_state(g, st, f"L={L} after {n} sweeps")
+
+
+def test_config_l8_anneal_full():
+    """L = 8, 1 x 1, linear anneal 3.0 -> 0.5 over 1000 sweeps, refresh every 10,
+    checked at every 100 sweeps."""
+    sched = np.linspace(3.0, 0.5, 1000)
+    with micsa.Micsa(8, 1, 1, 1) as g:
+        st = O.create(8, 1, 1, 1)
+        for k in range(0, 1000, 100):
+            g.run(sched[k:k + 100], 10)
+            O.run(st, sched[k:k + 100], 10)
+            assert_same_state(g, st, f"t={st['t']}")
+
+
+def test_config_l32_quench_observables():
+    """L = 32, 16 samples x 2 replicas (a subset of the 64-sample workload), quench
+    to T = 0.7, refresh every 10; e(t) and q^2(t) on a log time grid."""
+    L, S, R = 32, 16, 2
+    N = L ** 3
+    grid = sorted(set([0] + [int(10 ** (k / 8)) for k in range(0, 17)]))
+    with micsa.Micsa(L, S, R, 2) as g:
+        st = O.create(L, S, R, 2)
+        t = 0
+        for tm in grid:
+            if tm > t:
+                g.run(np.full(tm - t, 0.7), 10)
+                O.run(st, np.full(tm - t, 0.7), 10)
+                t = tm
+            e, a, q = g.measure()
+            eo, ao, qo = O.measure(st)
+            np.testing.assert_array_equal(e, eo)
+            np.testing.assert_array_equal(q, qo)
+            e_gpu = e.astype(np.float64) / N
+            q2_gpu = (q.astype(np.float64) / N) ** 2
+            np.testing.assert_allclose(e_gpu, eo / N, rtol=1e-9)
+            np.testing.assert_allclose(q2_gpu, (qo / N) ** 2, rtol=1e-9)
+        assert_same_state(g, st, "final")
+
+
+def test_metropolis_bit_exact():
+    for L, S, R, n in [(4, 2, 3, 20), (10, 1, 2, 15), (32, 1, 2, 8), (30, 2, 1, 7)]:
+        seed = 31 * L
+        sched = np.linspace(2.0, 0.6, n)
+        with micsa.Micsa(L, S, R, seed) as g:
+            st = O.create(L, S, R, seed)
+            g.run_metropolis(sched)
+            O.run_metropolis(st, sched)
+            assert_same_state(g, st, f"metropolis L={L}")
+
+
+def test_log_refresh_bit_exact():
+    for L in (6, 16, 32):
+        sched = np.full(70, 1.1)
+        with micsa.Micsa(L, 1, 2, 9) as g:
+            st = O.create(L, 1, 2, 9)
+            g.run_logrefresh(sched[:30])
+            g.run_logrefresh(sched[30:])
+            O.run_logrefresh(st, sched)
+            assert_same_state(g, st, f"log refresh L={L}")
+
+
+def test_chunked_runs_and_state_roundtrip():
+    L, S, R = 16, 2, 2
+    sched = np.linspace(2.5, 0.5, 90)
+    with micsa.Micsa(L, S, R, 5) as a, micsa.Micsa(L, S, R, 5) as b:
+        a.run(sched, 9)
+        b.run(sched[:31], 9)
+        b.run(sched[31:32], 9)
+        b.run(sched[32:], 9)
+        sa, ma, ta = a.get_state()
+        sb, mb, tb = b.get_state()
+        assert ta == tb == 90
+        np.testing.assert_array_equal(sa, sb)
+        np.testing.assert_array_equal(ma, mb)
+        # checkpoint / resume: save, load into a fresh handle, continue both
+        with micsa.Micsa(L, S, R, 5) as c:
+            c.set_state(sa, ma, ta)
+            a.run(np.full(20, 0.6), 9)
+            c.run(np.full(20, 0.6), 9)
+            s1, m1, _ = a.get_state()
+            s2, m2, _ = c.get_state()
+            np.testing.assert_array_equal(s1, s2)
+            np.testing.assert_array_equal(m1, m2)
+
+
+def test_user_couplings_and_state():
+    L, S, R = 10, 2, 2
+    rng = np.random.default_rng(3)
+    J = rng.choice(np.array([-1, 1], np.int8), (S, L ** 3, 3))
+    s0 = rng.choice(np.array([-1, 1], np.int8), (S, R, L ** 3))
+    m0 = rng.integers(0, 4, (S, R, L ** 3)).astype(np.uint8)
+    with micsa.Micsa(L, S, R, 77) as g:
+        g.set_couplings(J)
+        g.set_state(s0, m0, 3)  # t = 3: the next refresh comes at t = 5 (interval 5)
+        st = {"L": L, "S": S, "R": R, "seed": 77, "J": J.copy(), "s": s0.copy(), "m": m0.copy(), "t": 3}
+        assert_same_state(g, st, "after set_state")
+        g.run(np.full(12, 0.9), 5)
+        O.run(st, np.full(12, 0.9), 5)
+        assert_same_state(g, st, "after run")
+
+
+def test_invalid_arguments_fail_cleanly():
+    with pytest.raises(micsa.MicsaError):
+        micsa.Micsa(7, 1, 1, 0)  # odd L
+    with pytest.raises(micsa.MicsaError):
+        micsa.Micsa(8, 1, 33, 0)
+    with micsa.Micsa(8, 1, 1, 0) as g:
+        with pytest.raises(micsa.MicsaError):
+            g.run([1.0, 0.0], 10)
+        with pytest.raises(micsa.MicsaError):
+            g.run([1.0], 0)
+        with pytest.raises(micsa.MicsaError):
+            g.set_state(np.zeros((1, 1, 512), np.int8))  # 0 is not a spin
+        _, _, t = g.get_state()
+        assert t == 0  # rejected calls change nothing
