@@ -208,7 +208,10 @@ def main():
         return float(t.item())
 
     w = WORKLOAD
-    stream = torch.cuda.current_stream()
+    # a dedicated (non-default) stream: the library launches on it and the CUDA
+    # events below are recorded on it
+    stream = torch.cuda.Stream(device=dev)
+    torch.cuda.set_stream(stream)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     sched = np.full(args.sweeps, w["T"])
     base_seed = 3 + 1000 * rank  # independent lattice per rank

@@ -118,6 +118,22 @@ int micsa_sync(micsa_t h);
 /* Device bytes held by the handle. */
 int micsa_device_bytes(micsa_t h, size_t *bytes);
 
+/* Launch shape of the sweep kernels (the autotuner's knobs; results are
+ * bit-identical for every choice): words_per_thread 1, 2 or 4 (32-bit words of
+ * sites per thread, reduced to what the row pitch allows), block 32..256 in
+ * steps of 32, blocks_per_sm -1 (grid-stride loop over the resident capacity),
+ * 0 (one thread per chunk) or a positive cap, pdl != 0 chains consecutive
+ * half-sweeps with programmatic dependent launch, graph_sweeps > 0 replays a
+ * captured CUDA graph of that many sweeps (0: direct launches). Synchronizes
+ * the handle's stream. */
+int micsa_set_launch_config(micsa_t h, int words_per_thread, int block, int blocks_per_sm, int pdl,
+                            int graph_sweeps);
+
+/* The launch shape in effect (blocks_per_sm reports the grid cap / SM count).
+ * Any pointer may be NULL. */
+int micsa_get_launch_config(micsa_t h, int *words_per_thread, int *block, int *blocks_per_sm,
+                            int *pdl, int *graph_sweeps);
+
 /* Number of CUDA kernels the handle has launched since it was created. */
 int micsa_launch_count(micsa_t h, int64_t *count);
 

@@ -41,6 +41,7 @@ _c = ctypes
 _P = ctypes.c_void_p
 _i64p = ctypes.POINTER(ctypes.c_int64)
 _u64p = ctypes.POINTER(ctypes.c_uint64)
+_ip = ctypes.POINTER(ctypes.c_int)
 
 # name -> (restype, argtypes); every symbol of include/micsa.h
 SIGNATURES = {
@@ -58,6 +59,8 @@ SIGNATURES = {
     "micsa_sync": (_c.c_int, [_P]),
     "micsa_device_bytes": (_c.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
     "micsa_launch_count": (_c.c_int, [_P, _i64p]),
+    "micsa_set_launch_config": (_c.c_int, [_P, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int]),
+    "micsa_get_launch_config": (_c.c_int, [_P, _ip, _ip, _ip, _ip, _ip]),
     "micsa_destroy": (None, [_P]),
     "micsa_last_error": (_c.c_char_p, [_P]),
     "micsa_daemon_thresholds": (_c.c_int, [_c.c_double, _u64p]),
@@ -189,6 +192,18 @@ class Micsa:
 
     def sync(self):
         _check(lib().micsa_sync(self.h), self.h)
+
+    def set_launch_config(self, words_per_thread=4, block=256, blocks_per_sm=-1, pdl=True,
+                          graph_sweeps=64):
+        _check(lib().micsa_set_launch_config(self.h, int(words_per_thread), int(block),
+                                             int(blocks_per_sm), int(bool(pdl)), int(graph_sweeps)),
+               self.h)
+
+    def launch_config(self):
+        v = [ctypes.c_int() for _ in range(5)]
+        _check(lib().micsa_get_launch_config(self.h, *[ctypes.byref(x) for x in v]), self.h)
+        keys = ("words_per_thread", "block", "blocks_per_sm", "pdl", "graph_sweeps")
+        return {k: x.value for k, x in zip(keys, v)}
 
     def launch_count(self):
         n = ctypes.c_int64()

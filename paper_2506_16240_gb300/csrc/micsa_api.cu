@@ -29,6 +29,18 @@ struct micsa_ctx {
     int64_t launches = 0;  // kernels launched by this handle
     cudaStream_t own_stream = nullptr;
     cudaStream_t stream = nullptr;
+    cudaStream_t capture_stream = nullptr;  // graphs are captured here (never the legacy stream)
+    int sm_count = 0;
+    LaunchConfig lc;                // requested launch shape
+    int blocks_per_sm = 0;          // -1: resident capacity (grid-stride), 0: no cap
+    // per-run sweep parameter table: pinned host copy, device copy
+    SweepParam *h_params = nullptr;
+    SweepParam *d_params = nullptr;
+    int64_t params_cap = 0;
+    cudaEvent_t params_free = nullptr;  // the last upload of h_params has been consumed
+    int64_t *d_cursor = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // [metro]: G sweeps + cursor advance
+    int graph_g[2] = {0, 0};
     std::string err;
 };
 
@@ -109,17 +121,132 @@ SweepArgs sweep_args(const micsa_ctx *h) {
     return a;
 }
 
-// One sweep: even half, then odd half (Sec. 2.8 steps (i), (ii)).
-int launch_sweep(micsa_t h, SweepArgs a, int mode, const uint64_t th[3]) {
-    a.th0 = th[0];
-    a.th1 = th[1];
-    a.th2 = th[2];
-    for (int p = 0; p < 2; ++p) {
-        a.parity = p;
-        CK(h, launch_half_sweep(a, mode, h->stream), "half-sweep launch");
-        ++h->launches;
+void drop_graphs(micsa_t h) {
+    for (int i = 0; i < 2; ++i) {
+        if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
+        h->graph[i] = nullptr;
+        h->graph_g[i] = 0;
     }
+}
+
+// Effective launch shape for this handle: vector width the pitch allows and the
+// grid cap of the grid-stride loop.
+LaunchConfig effective_config(micsa_t h, bool metro) {
+    LaunchConfig lc = h->lc;
+    lc.nw = vector_words(h->geo, lc.nw);
+    if (h->blocks_per_sm < 0) {
+        const dim3 b = block_shape(h->R, lc.block);
+        const int per_sm = max_resident_blocks(metro, lc.nw, (int)(b.x * b.y));
+        lc.max_blocks = per_sm > 0 ? per_sm * h->sm_count : 0;
+    } else {
+        lc.max_blocks = h->blocks_per_sm * h->sm_count;
+    }
+    return lc;
+}
+
+int ensure_params(micsa_t h, int64_t n) {
+    if (h->params_cap >= n) {
+        CK(h, cudaEventSynchronize(h->params_free), "wait for the previous parameter upload");
+        return MICSA_OK;
+    }
+    CK(h, cudaStreamSynchronize(h->stream), "synchronize before parameter realloc");
+    cudaFreeHost(h->h_params);
+    cudaFree(h->d_params);
+    h->h_params = nullptr;
+    h->d_params = nullptr;
+    h->device_bytes -= sizeof(SweepParam) * (size_t)h->params_cap;
+    h->params_cap = 0;
+    drop_graphs(h);  // captured graphs point at the old table
+    int64_t cap = 1024;
+    while (cap < n) cap *= 2;
+    CK(h, cudaMallocHost(&h->h_params, sizeof(SweepParam) * (size_t)cap), "cudaMallocHost parameters");
+    CK(h, cudaMalloc(&h->d_params, sizeof(SweepParam) * (size_t)cap), "cudaMalloc parameters");
+    h->params_cap = cap;
+    h->device_bytes += sizeof(SweepParam) * (size_t)cap;
     return MICSA_OK;
+}
+
+// Capture G sweeps (2G half-sweeps reading params[*cursor + k]) and the cursor
+// advance into an executable graph.
+int capture_graph(micsa_t h, bool metro, int G, const LaunchConfig &lc) {
+    const int gi = metro ? 1 : 0;
+    if (h->graph[gi] && h->graph_g[gi] == G) return MICSA_OK;
+    if (h->graph[gi]) cudaGraphExecDestroy(h->graph[gi]);
+    h->graph[gi] = nullptr;
+    SweepArgs a = sweep_args(h);
+    a.params = h->d_params;
+    a.cursor = h->d_cursor;
+    CK(h, cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < G && e == cudaSuccess; ++k)
+        for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
+            a.k = k;
+            a.parity = p;
+            e = launch_half_sweep(a, metro, lc, h->capture_stream);
+        }
+    if (e == cudaSuccess) e = launch_advance_cursor(h->d_cursor, G, lc.pdl, h->capture_stream);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(h->capture_stream, &graph);
+    if (e != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return cuda_fail(h, e, "launch during capture");
+    }
+    if (e2 != cudaSuccess) return cuda_fail(h, e2, "end capture");
+    e = cudaGraphInstantiate(&h->graph[gi], graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        h->graph[gi] = nullptr;
+        return cuda_fail(h, e, "graph instantiate");
+    }
+    h->graph_g[gi] = G;
+    return MICSA_OK;
+}
+
+// Upload the table of n sweeps and run them: whole blocks of G sweeps by graph
+// replay, the rest by direct launches. Every sweep is the even half-sweep
+// followed by the odd one (Sec. 2.8 steps (i), (ii)).
+int run_table(micsa_t h, bool metro, int64_t n) {
+    if (n == 0) return MICSA_OK;
+    const LaunchConfig lc = effective_config(h, metro);
+    CK(h, cudaMemcpyAsync(h->d_params, h->h_params, sizeof(SweepParam) * (size_t)n,
+                          cudaMemcpyHostToDevice, h->stream), "upload sweep parameters");
+    CK(h, cudaEventRecord(h->params_free, h->stream), "record parameter event");
+    const int G = lc.graph_sweeps;
+    int64_t done = 0;
+    if (G > 0 && n >= 2 * (int64_t)G) {
+        if (int rc = capture_graph(h, metro, G, lc)) return rc;
+        CK(h, cudaMemsetAsync(h->d_cursor, 0, sizeof(int64_t), h->stream), "reset cursor");
+        const int64_t reps = n / G;
+        for (int64_t r = 0; r < reps; ++r)
+            CK(h, cudaGraphLaunch(h->graph[metro ? 1 : 0], h->stream), "graph launch");
+        h->launches += reps * (2 * (int64_t)G + 1);
+        done = reps * G;
+    }
+    SweepArgs a = sweep_args(h);
+    a.params = h->d_params;
+    a.cursor = nullptr;
+    for (int64_t k = done; k < n; ++k)
+        for (int p = 0; p < 2; ++p) {
+            a.k = k;
+            a.parity = p;
+            CK(h, launch_half_sweep(a, metro, lc, h->stream), "half-sweep launch");
+            ++h->launches;
+        }
+    return MICSA_OK;
+}
+
+bool schedule_ok(micsa_t h, const double *schedule, int64_t n_sweeps) {
+    if (n_sweeps < 0 || (n_sweeps > 0 && !schedule)) {
+        fail(h, MICSA_E_INVALID_ARG, "n_sweeps must be >= 0 and schedule non-NULL");
+        return false;
+    }
+    for (int64_t k = 0; k < n_sweeps; ++k)
+        if (!temperature_ok(schedule[k])) {
+            fail(h, MICSA_E_INVALID_ARG, "schedule[%lld] = %g is not a finite T > 0", (long long)k,
+                 schedule[k]);
+            return false;
+        }
+    return true;
 }
 
 // Couplings and spins from the seed (Sec. 2.1 and the disordered start of
@@ -136,28 +263,30 @@ int init_from_seed(micsa_t h, uint64_t seed) {
     return MICSA_OK;
 }
 
+// MicSA run with refresh before sweep t iff is_refresh(t) (Sec. 2.7, 2.8).
 template <class IsRefresh>
 int run_micsa(micsa_t h, const double *schedule, int64_t n_sweeps, IsRefresh is_refresh) {
     if (!h) return MICSA_E_INVALID_ARG;
-    if (n_sweeps < 0 || (n_sweeps > 0 && !schedule))
-        return fail(h, MICSA_E_INVALID_ARG, "n_sweeps must be >= 0 and schedule non-NULL");
-    for (int64_t k = 0; k < n_sweeps; ++k)
-        if (!temperature_ok(schedule[k]))
-            return fail(h, MICSA_E_INVALID_ARG, "schedule[%lld] = %g is not a finite T > 0",
-                        (long long)k, schedule[k]);
+    if (!schedule_ok(h, schedule, n_sweeps)) return MICSA_E_INVALID_ARG;
+    if (n_sweeps == 0) return MICSA_OK;
     DeviceGuard dg(h->device);
-    SweepArgs a = sweep_args(h);
-    const uint64_t none[3] = {0, 0, 0};
+    if (int rc = ensure_params(h, n_sweeps)) return rc;
+    double last_T = -1.0;
+    uint64_t th[3] = {0, 0, 0};
     for (int64_t k = 0; k < n_sweeps; ++k) {
-        a.t = h->t + k;
-        if (is_refresh(a.t)) {
-            uint64_t th[3];
+        SweepParam &q = h->h_params[k];
+        q.t = h->t + k;
+        q.mode = is_refresh(q.t) ? kModeRefresh : kModeMicsa;
+        if (q.mode == kModeRefresh && schedule[k] != last_T) {
             micsa_daemon_thresholds(schedule[k], th);
-            if (int rc = launch_sweep(h, a, kModeRefresh, th)) return rc;
-        } else {
-            if (int rc = launch_sweep(h, a, kModeMicsa, none)) return rc;
+            last_T = schedule[k];
         }
+        q.th0 = th[0];
+        q.th1 = th[1];
+        q.th2 = th[2];
+        q.pad = 0;
     }
+    if (int rc = run_table(h, false, n_sweeps)) return rc;
     h->t += n_sweeps;
     return MICSA_OK;
 }
@@ -210,6 +339,12 @@ void micsa_destroy(micsa_t h) {
     cudaFree(h->d_bonds);
     cudaFree(h->d_meas);
     cudaFree(h->d_stage);
+    cudaFree(h->d_cursor);
+    cudaFree(h->d_params);
+    cudaFreeHost(h->h_params);
+    drop_graphs(h);
+    if (h->params_free) cudaEventDestroy(h->params_free);
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     if (h->own_stream) cudaStreamDestroy(h->own_stream);
     delete h;
 }
@@ -233,6 +368,10 @@ int micsa_create(int L, int n_samples, int n_replicas, uint64_t seed, micsa_t *o
         cudaError_t e = cudaStreamCreateWithFlags(&h->own_stream, cudaStreamNonBlocking);
         if (e != cudaSuccess) { rc = cuda_fail(h, e, "cudaStreamCreate"); break; }
         h->stream = h->own_stream;
+        if ((e = cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking)) != cudaSuccess) { rc = cuda_fail(h, e, "cudaStreamCreate"); break; }
+        if ((e = cudaEventCreateWithFlags(&h->params_free, cudaEventDisableTiming)) != cudaSuccess) { rc = cuda_fail(h, e, "cudaEventCreate"); break; }
+        if ((e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device)) != cudaSuccess) { rc = cuda_fail(h, e, "SM count"); break; }
+        if ((e = cudaMalloc(&h->d_cursor, sizeof(int64_t))) != cudaSuccess) { rc = cuda_fail(h, e, "cudaMalloc cursor"); break; }
         const size_t state = (size_t)h->S * h->R * 2 * h->geo.half;
         const size_t bonds = (size_t)h->S * 2 * h->geo.half;
         const size_t meas = sizeof(unsigned long long) * ((size_t)2 * h->S * h->R + (size_t)h->S * h->R * (h->R - 1) / 2);
@@ -304,20 +443,57 @@ int micsa_run_logrefresh(micsa_t h, const double *schedule, int64_t n_sweeps) {
 
 int micsa_run_metropolis(micsa_t h, const double *schedule, int64_t n_sweeps) {
     if (!h) return MICSA_E_INVALID_ARG;
-    if (n_sweeps < 0 || (n_sweeps > 0 && !schedule))
-        return fail(h, MICSA_E_INVALID_ARG, "n_sweeps must be >= 0 and schedule non-NULL");
-    for (int64_t k = 0; k < n_sweeps; ++k)
-        if (!temperature_ok(schedule[k]))
-            return fail(h, MICSA_E_INVALID_ARG, "schedule[%lld] = %g is not a finite T > 0", (long long)k, schedule[k]);
+    if (!schedule_ok(h, schedule, n_sweeps)) return MICSA_E_INVALID_ARG;
+    if (n_sweeps == 0) return MICSA_OK;
     DeviceGuard dg(h->device);
-    SweepArgs a = sweep_args(h);
+    if (int rc = ensure_params(h, n_sweeps)) return rc;
+    double last_T = -1.0;
+    uint64_t th[3] = {0, 0, 0};
     for (int64_t k = 0; k < n_sweeps; ++k) {
-        uint64_t th[3];
-        micsa_metro_thresholds(schedule[k], th);
-        a.t = h->t + k;
-        if (int rc = launch_sweep(h, a, kModeMetro, th)) return rc;
+        SweepParam &q = h->h_params[k];
+        q.t = h->t + k;
+        q.mode = kModeMetro;
+        if (schedule[k] != last_T) {
+            micsa_metro_thresholds(schedule[k], th);
+            last_T = schedule[k];
+        }
+        q.th0 = th[0];
+        q.th1 = th[1];
+        q.th2 = th[2];
+        q.pad = 0;
     }
+    if (int rc = run_table(h, true, n_sweeps)) return rc;
     h->t += n_sweeps;
+    return MICSA_OK;
+}
+
+int micsa_set_launch_config(micsa_t h, int words_per_thread, int block, int blocks_per_sm, int pdl,
+                            int graph_sweeps) {
+    if (!h) return MICSA_E_INVALID_ARG;
+    if ((words_per_thread != 1 && words_per_thread != 2 && words_per_thread != 4) ||
+        block < 32 || block > 256 || block % 32 || blocks_per_sm < -1 || blocks_per_sm > 64 ||
+        graph_sweeps < 0 || graph_sweeps > 4096)
+        return fail(h, MICSA_E_INVALID_ARG, "bad launch configuration");
+    DeviceGuard dg(h->device);
+    CK(h, cudaStreamSynchronize(h->stream), "synchronize before reconfiguring");
+    drop_graphs(h);
+    h->lc.nw = words_per_thread;
+    h->lc.block = block;
+    h->lc.pdl = pdl != 0;
+    h->lc.graph_sweeps = graph_sweeps;
+    h->blocks_per_sm = blocks_per_sm;
+    return MICSA_OK;
+}
+
+int micsa_get_launch_config(micsa_t h, int *words_per_thread, int *block, int *blocks_per_sm,
+                            int *pdl, int *graph_sweeps) {
+    if (!h) return MICSA_E_INVALID_ARG;
+    const LaunchConfig lc = effective_config(h, false);
+    if (words_per_thread) *words_per_thread = lc.nw;
+    if (block) *block = lc.block;
+    if (blocks_per_sm) *blocks_per_sm = h->sm_count ? lc.max_blocks / h->sm_count : 0;
+    if (pdl) *pdl = lc.pdl;
+    if (graph_sweeps) *graph_sweeps = lc.graph_sweeps;
     return MICSA_OK;
 }
 

@@ -77,14 +77,16 @@ __device__ __forceinline__ void x_neighbours(const uint32_t (&O)[NW], int o, int
             xm[j] = O[j];
             xp[j] = (O[j] >> 8) | ((j + 1 < NW ? (O[j + 1] & 0xFFu) : edge) << 24);
         }
+        // the row's last site takes the row's first byte as its +x neighbour;
+        // written branch-free per word so that xp stays in registers
         const int e = Lh - 1 - b0;  // position of the row's last site in this range
-        if (e >= 0 && e < 4 * NW) {
 #pragma unroll
-            for (int j = 0; j < NW; ++j)
-                if ((e >> 2) == j) {
-                    const int sh = 8 * (e & 3);
-                    xp[j] = (xp[j] & ~(0xFFu << sh)) | (first << sh);
-                }
+        for (int j = 0; j < NW; ++j) {
+            const int pos = e - 4 * j;
+            const bool here = pos >= 0 && pos < 4;
+            const uint32_t sh = here ? 8u * (uint32_t)pos : 0u;
+            const uint32_t m = here ? (0xFFu << sh) : 0u;
+            xp[j] = (xp[j] & ~m) | ((first << sh) & m);
         }
     }
 }

@@ -175,3 +175,34 @@ def test_invalid_arguments_fail_cleanly():
             g.set_state(np.zeros((1, 1, 512), np.int8))  # 0 is not a spin
         _, _, t = g.get_state()
         assert t == 0  # rejected calls change nothing
+
+
+@pytest.mark.parametrize("L", [16, 18, 32, 160])
+def test_launch_configs_agree(L):
+    """Every launch shape (vector width, block, grid-stride cap, PDL, graph
+    replay) produces the same bits; checked against the oracle for small L."""
+    R, n, interval = 2, 140, 10
+    sched = np.linspace(2.0, 0.6, n)
+    ref = None
+    configs = [(4, 256, -1, 1, 64), (2, 128, 0, 0, 0), (1, 256, -1, 1, 16), (4, 64, 3, 0, 7),
+               (2, 256, -1, 1, 64)]
+    for cfg in configs:
+        with micsa.Micsa(L, 1, R, 42) as g:
+            g.set_launch_config(*cfg)
+            g.run(sched[:70], interval)
+            g.run_metropolis(sched[70:90])
+            g.run(sched[90:], interval)
+            s, m, t = g.get_state()
+        if ref is None:
+            ref = (s, m, t)
+            if L <= 32:
+                st = O.create(L, 1, R, 42)
+                O.run(st, sched[:70], interval)
+                O.run_metropolis(st, sched[70:90])
+                O.run(st, sched[90:], interval)
+                np.testing.assert_array_equal(s, st["s"])
+                np.testing.assert_array_equal(m, st["m"])
+        else:
+            np.testing.assert_array_equal(s, ref[0], err_msg=str(cfg))
+            np.testing.assert_array_equal(m, ref[1], err_msg=str(cfg))
+            assert t == ref[2]
