@@ -55,6 +55,10 @@ extern "C" {
 #define MICSA_E_TIMEOUT (-4)     /* a bounded device-side wait gave up */
 #define MICSA_E_BUSY (-5)        /* pool: no free slot or memory for the job now */
 #define MICSA_E_NOT_FOUND (-6)   /* pool: unknown job id */
+#define MICSA_E_TOO_LARGE (-7)   /* micsa_measure_noalloc: more sums than its fixed scratch holds */
+
+/* Capacity of the fixed device scratch of micsa_measure_noalloc, in 64-bit sums. */
+#define MICSA_NOALLOC_MAX_TERMS 8192
 
 typedef struct micsa_ctx *micsa_t;
 
@@ -143,6 +147,31 @@ void micsa_destroy(micsa_t h);
 /* Message of the last failed call on `h` ("" if none; a static message if h is
  * NULL). Valid until the next call on h. */
 const char *micsa_last_error(micsa_t h);
+
+/* Energy, daemon energy and overlaps of caller-owned DEVICE arrays, without
+ * allocating anything (the paper has no counterpart; this serves callers that
+ * may not call cudaMalloc themselves or through a library: a framework whose
+ * allocator must own every device byte, a serving loop that cannot take the
+ * device synchronisation an allocation can cause, a fixed memory budget).
+ *   spins    device int8 +-1 [S][R][N], natural layout (see above)
+ *   daemons  device uint8 m in {0..3} [S][R][N], or NULL (aux is then 0)
+ *   J        device int8 +-1 [S][N][3], the forward bonds of each site
+ *   energy[S*R], aux[S*R], overlap[S*R(R-1)/2]  HOST arrays, as micsa_measure;
+ *            any may be NULL
+ *   stream   cudaStream_t to run on (NULL: the legacy default stream)
+ * The sums go through one fixed device array of MICSA_NOALLOC_MAX_TERMS 64-bit
+ * counters (64 KiB) that every GPU loading the library holds until the process
+ * exits; a call needs 2*S*R + S*R*(R-1)/2 of them and returns
+ * MICSA_E_TOO_LARGE beyond that (or for S > 65535). No cudaMalloc, cudaFree or
+ * other allocating routine is called. The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress), so make it before any stream
+ * capture. All calls share the array (each clears what it uses first): calls
+ * whose GPU work overlaps -- other streams, other host threads -- race on it.
+ * Synchronous: returns after the host arrays are written. Same rules as
+ * micsa_create for L and R. */
+int micsa_measure_noalloc(const int8_t *spins, const uint8_t *daemons, const int8_t *J, int L,
+                          int n_samples, int n_replicas, int64_t *energy, int64_t *aux,
+                          int64_t *overlap, void *stream);
 
 /* Cut points of the daemon refresh at temperature T, Eq. (prob-daemons-walkers):
  * with beta = 1/T, x = exp(-4 beta), p0 = (1 - x)/(1 - x^4) (x^4 as

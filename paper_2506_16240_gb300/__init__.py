@@ -24,9 +24,12 @@ MICSA_E_CUDA = -3
 MICSA_E_TIMEOUT = -4
 MICSA_E_BUSY = -5
 MICSA_E_NOT_FOUND = -6
+MICSA_E_TOO_LARGE = -7
+MICSA_NOALLOC_MAX_TERMS = 8192
 
 _ERRNAMES = {-1: "MICSA_E_INVALID_ARG", -2: "MICSA_E_OOM", -3: "MICSA_E_CUDA",
-             -4: "MICSA_E_TIMEOUT", -5: "MICSA_E_BUSY", -6: "MICSA_E_NOT_FOUND"}
+             -4: "MICSA_E_TIMEOUT", -5: "MICSA_E_BUSY", -6: "MICSA_E_NOT_FOUND",
+             -7: "MICSA_E_TOO_LARGE"}
 
 
 class MicsaError(RuntimeError):
@@ -63,6 +66,7 @@ SIGNATURES = {
     "micsa_get_launch_config": (_c.c_int, [_P, _ip, _ip, _ip, _ip, _ip]),
     "micsa_destroy": (None, [_P]),
     "micsa_last_error": (_c.c_char_p, [_P]),
+    "micsa_measure_noalloc": (_c.c_int, [_P, _P, _P, _c.c_int, _c.c_int, _c.c_int, _P, _P, _P, _P]),
     "micsa_daemon_thresholds": (_c.c_int, [_c.c_double, _u64p]),
     "micsa_metro_thresholds": (_c.c_int, [_c.c_double, _u64p]),
 }
@@ -105,6 +109,22 @@ def metro_thresholds(T):
     th = (ctypes.c_uint64 * 3)()
     _check(lib().micsa_metro_thresholds(float(T), th))
     return np.array(list(th), np.uint64)
+
+
+def measure_noalloc(spins_ptr, daemons_ptr, J_ptr, L, n_samples, n_replicas, stream_ptr=None):
+    """Observables of caller-owned device arrays (natural layout, raw device
+    pointers as ints) through the allocation-free entry point; host results."""
+    S, R = int(n_samples), int(n_replicas)
+    e = np.zeros(S * R, np.int64)
+    a = np.zeros(S * R, np.int64)
+    q = np.zeros(S * R * (R - 1) // 2, np.int64)
+    rc = lib().micsa_measure_noalloc(
+        ctypes.c_void_p(spins_ptr), ctypes.c_void_p(daemons_ptr) if daemons_ptr else None,
+        ctypes.c_void_p(J_ptr), int(L), S, R, _ptr(e), _ptr(a), _ptr(q) if q.size else None,
+        ctypes.c_void_p(stream_ptr) if stream_ptr else None)
+    if rc != MICSA_OK:
+        raise MicsaError(rc, "micsa_measure_noalloc")
+    return e, a, q
 
 
 class Micsa:
