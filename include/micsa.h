@@ -173,6 +173,89 @@ int micsa_measure_noalloc(const int8_t *spins, const uint8_t *daemons, const int
                           int n_samples, int n_replicas, int64_t *energy, int64_t *aux,
                           int64_t *overlap, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batched engine / serving pool: independent annealing jobs of mixed L,
+ * replica count, length and refresh interval, resident in one device arena
+ * and advanced together (one persistent launch per half-sweep over all jobs,
+ * a tick of K sweeps replayed as one CUDA graph). Jobs are admitted and
+ * retired between ticks (continuous batching), limited by free slots and by
+ * free arena bytes. A job computes exactly what micsa_create(L, 1, R, seed)
+ * followed by micsa_run(schedule, n_sweeps, refresh_interval) computes, with
+ * the linear schedule T(k) = T_start + (T_end - T_start) * (k / (n_sweeps - 1))
+ * in IEEE double (T(0) = T_start when n_sweeps == 1), so its result does not
+ * depend on its slot or on the other jobs. After every tick (every K sweeps of
+ * the job's own clock, and after its last sweep) the exact energy of each
+ * replica is measured; the lowest one seen (ties: the earliest) and that
+ * configuration are kept ("best configuration").
+ * ------------------------------------------------------------------------ */
+#define MICSA_POOL_MAX_REPLICAS 8
+
+typedef struct micsa_pool *micsa_pool_t;
+
+typedef struct {
+    int L;                    /* even, 2..1024 */
+    int n_replicas;           /* 1..MICSA_POOL_MAX_REPLICAS */
+    uint64_t seed;            /* couplings, spins and daemons of this job */
+    int64_t n_sweeps;         /* >= 1 */
+    int32_t refresh_interval; /* >= 1 */
+    double T_start, T_end;    /* finite, > 0 */
+} micsa_job_desc;
+
+typedef struct {
+    int64_t job_id;
+    int64_t sweeps_done;
+    int32_t n_replicas;
+    int64_t energy[MICSA_POOL_MAX_REPLICAS];      /* final H_EA per replica */
+    int64_t aux[MICSA_POOL_MAX_REPLICAS];         /* final H_aux per replica */
+    int64_t best_energy[MICSA_POOL_MAX_REPLICAS]; /* lowest H_EA at the measurement points */
+    int64_t best_t[MICSA_POOL_MAX_REPLICAS];      /* sweep count where it was first seen */
+} micsa_job_result;
+
+/* Reserve an arena of arena_bytes (>= 1 MiB) on the current device and room for
+ * max_jobs (1..65535) resident jobs; a tick advances every job by tick_sweeps
+ * (1..4096) sweeps. */
+int micsa_pool_create(size_t arena_bytes, int max_jobs, int tick_sweeps, micsa_pool_t *out);
+
+/* Arena bytes a job needs (host-only). */
+int micsa_pool_job_bytes(const micsa_job_desc *job, size_t *bytes);
+
+/* Admit a job: returns its id in *job_id, MICSA_E_BUSY if no slot or not enough
+ * contiguous arena memory is free now (retry after a completed job has been
+ * polled), MICSA_E_INVALID_ARG for a bad description. Its initial state is
+ * drawn on the device; nothing waits for queued ticks. */
+int micsa_pool_submit(micsa_pool_t p, const micsa_job_desc *job, int64_t *job_id);
+
+/* Queue one tick: every admitted job that is not finished advances by
+ * min(tick_sweeps, sweeps left) sweeps. Asynchronous. */
+int micsa_pool_tick(micsa_pool_t p);
+
+/* Block until every queued tick has run. */
+int micsa_pool_wait(micsa_pool_t p);
+
+/* Block until at most max_pending queued ticks have not run yet (bounds how far
+ * the host runs ahead of the device, so that new admissions start soon). */
+int micsa_pool_wait_ticks(micsa_pool_t p, int max_pending);
+
+/* If job `job_id` has finished and its last tick has run: fill *res, copy its
+ * best configurations to best_spins[R][N] (host, natural layout, int8 +-1;
+ * may be NULL), free its slot and memory, return MICSA_OK. MICSA_E_BUSY if it
+ * is still running, MICSA_E_NOT_FOUND for an unknown (or already polled) id. */
+int micsa_pool_poll(micsa_pool_t p, int64_t job_id, micsa_job_result *res, int8_t *best_spins);
+
+/* Jobs resident, free arena bytes, kernels launched so far. Any pointer may be NULL. */
+int micsa_pool_stats(micsa_pool_t p, int *live_jobs, size_t *free_bytes, int64_t *launches);
+
+/* Grid of the batched kernels (blocks per SM, 1..64), programmatic dependent
+ * launch on/off, CUDA graph replay of ticks on/off (the autotuner's knobs;
+ * results are identical for every choice). Synchronizes. */
+int micsa_pool_set_launch_config(micsa_pool_t p, int blocks_per_sm, int pdl, int use_graph);
+
+/* Message of the last failure on p. */
+const char *micsa_pool_last_error(micsa_pool_t p);
+
+/* Free the pool and its arena (NULL allowed). */
+void micsa_pool_destroy(micsa_pool_t p);
+
 /* Cut points of the daemon refresh at temperature T, Eq. (prob-daemons-walkers):
  * with beta = 1/T, x = exp(-4 beta), p0 = (1 - x)/(1 - x^4) (x^4 as
  * (x*x)*(x*x); p0 = 1/4 when x == 1), p1 = p0 x, p2 = p1 x, c0 = p0,

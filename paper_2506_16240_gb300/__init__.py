@@ -234,3 +234,136 @@ class Micsa:
         n = ctypes.c_size_t()
         _check(lib().micsa_device_bytes(self.h, ctypes.byref(n)), self.h)
         return n.value
+
+
+# ----------------------------------------------------------- batched pool --
+MICSA_POOL_MAX_REPLICAS = 8
+
+
+class JobDesc(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int), ("n_replicas", ctypes.c_int), ("seed", ctypes.c_uint64),
+                ("n_sweeps", ctypes.c_int64), ("refresh_interval", ctypes.c_int32),
+                ("T_start", ctypes.c_double), ("T_end", ctypes.c_double)]
+
+
+class JobResult(ctypes.Structure):
+    _fields_ = [("job_id", ctypes.c_int64), ("sweeps_done", ctypes.c_int64),
+                ("n_replicas", ctypes.c_int32),
+                ("energy", ctypes.c_int64 * MICSA_POOL_MAX_REPLICAS),
+                ("aux", ctypes.c_int64 * MICSA_POOL_MAX_REPLICAS),
+                ("best_energy", ctypes.c_int64 * MICSA_POOL_MAX_REPLICAS),
+                ("best_t", ctypes.c_int64 * MICSA_POOL_MAX_REPLICAS)]
+
+
+SIGNATURES.update({
+    "micsa_pool_create": (_c.c_int, [_c.c_size_t, _c.c_int, _c.c_int, ctypes.POINTER(_P)]),
+    "micsa_pool_job_bytes": (_c.c_int, [ctypes.POINTER(JobDesc), ctypes.POINTER(ctypes.c_size_t)]),
+    "micsa_pool_submit": (_c.c_int, [_P, ctypes.POINTER(JobDesc), _i64p]),
+    "micsa_pool_tick": (_c.c_int, [_P]),
+    "micsa_pool_wait": (_c.c_int, [_P]),
+    "micsa_pool_wait_ticks": (_c.c_int, [_P, _c.c_int]),
+    "micsa_pool_poll": (_c.c_int, [_P, _c.c_int64, ctypes.POINTER(JobResult), _P]),
+    "micsa_pool_stats": (_c.c_int, [_P, ctypes.POINTER(_c.c_int), ctypes.POINTER(ctypes.c_size_t), _i64p]),
+    "micsa_pool_set_launch_config": (_c.c_int, [_P, _c.c_int, _c.c_int, _c.c_int]),
+    "micsa_pool_last_error": (_c.c_char_p, [_P]),
+    "micsa_pool_destroy": (None, [_P]),
+})
+
+
+def linear_schedule(T_start, T_end, n_sweeps):
+    """T(k) exactly as the pool computes it: T0 + (T1 - T0) * (k / (n - 1))."""
+    k = np.arange(n_sweeps, dtype=np.float64)
+    if n_sweeps <= 1:
+        return np.full(n_sweeps, float(T_start))
+    return float(T_start) + (float(T_end) - float(T_start)) * (k / float(n_sweeps - 1))
+
+
+class Pool:
+    """Resident pool of annealing jobs advanced together (continuous batching)."""
+
+    def __init__(self, arena_bytes=1 << 30, max_jobs=1024, tick_sweeps=64):
+        h = ctypes.c_void_p()
+        rc = lib().micsa_pool_create(int(arena_bytes), int(max_jobs), int(tick_sweeps), ctypes.byref(h))
+        if rc != MICSA_OK:
+            raise MicsaError(rc, "micsa_pool_create")
+        self.h = h
+        self.tick_sweeps = int(tick_sweeps)
+        self.jobs = {}  # id -> (L, R)
+
+    def _check(self, rc):
+        if rc != MICSA_OK:
+            raise MicsaError(rc, lib().micsa_pool_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().micsa_pool_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @staticmethod
+    def job_bytes(L, n_replicas, n_sweeps, refresh_interval):
+        d = JobDesc(int(L), int(n_replicas), 0, int(n_sweeps), int(refresh_interval), 1.0, 1.0)
+        n = ctypes.c_size_t()
+        _check(lib().micsa_pool_job_bytes(ctypes.byref(d), ctypes.byref(n)))
+        return n.value
+
+    def submit(self, L, n_replicas, seed, n_sweeps, refresh_interval, T_start, T_end):
+        """Job id, or None when the pool has no slot or memory for it now."""
+        d = JobDesc(int(L), int(n_replicas), ctypes.c_uint64(int(seed)).value, int(n_sweeps),
+                    int(refresh_interval), float(T_start), float(T_end))
+        jid = ctypes.c_int64()
+        rc = lib().micsa_pool_submit(self.h, ctypes.byref(d), ctypes.byref(jid))
+        if rc == MICSA_E_BUSY:
+            return None
+        self._check(rc)
+        self.jobs[jid.value] = (int(L), int(n_replicas))
+        return jid.value
+
+    def tick(self):
+        self._check(lib().micsa_pool_tick(self.h))
+
+    def wait(self):
+        self._check(lib().micsa_pool_wait(self.h))
+
+    def wait_ticks(self, max_pending):
+        self._check(lib().micsa_pool_wait_ticks(self.h, int(max_pending)))
+
+    def poll(self, job_id, best_spins=True):
+        """Result dict of a finished job (and frees it), or None while it runs."""
+        L, R = self.jobs[job_id]
+        res = JobResult()
+        spins = np.zeros((R, L ** 3), np.int8) if best_spins else None
+        rc = lib().micsa_pool_poll(self.h, int(job_id), ctypes.byref(res), _ptr(spins))
+        if rc == MICSA_E_BUSY:
+            return None
+        self._check(rc)
+        del self.jobs[job_id]
+        out = {"job_id": res.job_id, "sweeps_done": res.sweeps_done,
+               "energy": np.array(res.energy[:R], np.int64), "aux": np.array(res.aux[:R], np.int64),
+               "best_energy": np.array(res.best_energy[:R], np.int64),
+               "best_t": np.array(res.best_t[:R], np.int64)}
+        if best_spins:
+            out["best_spins"] = spins
+        return out
+
+    def stats(self):
+        n = ctypes.c_int()
+        free = ctypes.c_size_t()
+        launches = ctypes.c_int64()
+        self._check(lib().micsa_pool_stats(self.h, ctypes.byref(n), ctypes.byref(free), ctypes.byref(launches)))
+        return {"live_jobs": n.value, "free_bytes": free.value, "launches": launches.value}
+
+    def set_launch_config(self, blocks_per_sm, pdl=True, use_graph=True):
+        self._check(lib().micsa_pool_set_launch_config(self.h, int(blocks_per_sm), int(bool(pdl)),
+                                                       int(bool(use_graph))))

@@ -1,0 +1,704 @@
+// pool.cu -- the batched engine: many independent annealing jobs of mixed L,
+// replicas, sweep counts and refresh intervals resident in one device arena,
+// advanced together by one persistent grid-stride launch per half-sweep, a tick
+// of K sweeps replayed as one CUDA graph. Jobs are admitted and retired between
+// ticks (continuous batching): admission is limited by free slots and by free
+// arena memory.
+//
+// A job is micsa_create(L, 1, R, seed) + micsa_run with the linear schedule
+// T(k) = T_start + (T_end - T_start) * (k / (n_sweeps - 1)) and its refresh
+// interval: the same Philox counters (sample 0, gid = replica), so its result
+// does not depend on which slot it occupies or on which jobs run beside it.
+// After every tick each job's exact energy is measured and the lowest energy
+// seen so far (ties: the earliest) is kept together with that configuration.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "sweep_body.cuh"
+#include "../../include/micsa.h"
+
+namespace micsa {
+
+constexpr int kPoolMaxR = MICSA_POOL_MAX_REPLICAS;
+constexpr int kVBlock = 128;  // chunk items per virtual block
+
+struct JobDesc {
+    int8_t *spins;         // [R][2][half]
+    uint8_t *daemons;      // [R][2][half]
+    const uint8_t *bonds;  // [2][half]
+    int8_t *best;          // [R][N] natural layout
+    const uint64_t *thr;   // refresh cut points [n_refresh][3]
+    Geometry geo;
+    int R, nw;
+    uint32_t key0, key1;
+    int64_t t;             // sweeps done
+    int64_t n_sweeps;
+    int32_t interval;
+    int32_t live;
+};
+
+struct VBlock {
+    int32_t slot;
+    int32_t chunk0;
+};
+
+struct PoolTables {
+    JobDesc *jobs;          // [max_jobs]
+    const VBlock *vblocks;  // [max_vblocks]
+    const int32_t *n_vblocks;
+    long long *energy;      // [max_jobs][kPoolMaxR]
+    long long *aux;
+    long long *best_energy;
+    long long *best_t;
+};
+
+__device__ __forceinline__ void pool_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pool_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <int NW>
+__device__ __forceinline__ void pool_item(const JobDesc &J, int64_t item, int p, int64_t t) {
+    const int chunks = J.geo.W / NW;
+    const int64_t per_rep = (int64_t)J.geo.L * J.geo.L * chunks;
+    const int r = (int)(item / per_rep);
+    const int64_t rem = item - (int64_t)r * per_rep;
+    const int row = (int)(rem / chunks);
+    const int c = (int)(rem - (int64_t)row * chunks);
+    const bool refresh = (t % J.interval) == 0;
+    uint64_t th0 = 0, th1 = 0, th2 = 0;
+    if (refresh) {
+        const uint64_t *q = J.thr + 3 * (t / J.interval);
+        th0 = q[0];
+        th1 = q[1];
+        th2 = q[2];
+    }
+    update_chunk<NW, false>(J.geo, J.spins + (int64_t)r * 2 * J.geo.half,
+                            J.daemons + (int64_t)r * 2 * J.geo.half, J.bonds, p, row, c, (uint32_t)r,
+                            J.key0, J.key1, t, refresh, th0, th1, th2);
+}
+
+// One half-sweep (parity p) of sweep k of the tick for every live job.
+__global__ void __launch_bounds__(kVBlock) pool_half_sweep_kernel(PoolTables T, int k, int p) {
+    pool_wait();
+    pool_release();
+    const int nvb = *T.n_vblocks;
+    for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+        const VBlock b = T.vblocks[vb];
+        const JobDesc &J = T.jobs[b.slot];
+        const int64_t t = J.t + k;
+        if (!J.live || t >= J.n_sweeps) continue;
+        const int64_t items = (int64_t)J.R * J.geo.L * J.geo.L * (J.geo.W / J.nw);
+        const int64_t item = (int64_t)b.chunk0 + threadIdx.x;
+        if (item >= items) continue;
+        if (J.nw == 4) pool_item<4>(J, item, p, t);
+        else pool_item<1>(J, item, p, t);
+    }
+}
+
+// Exact energy and daemon energy of every (live, advancing) job replica after
+// the tick; keeps the lowest energy and its configuration. One block per
+// (slot, replica).
+__global__ void __launch_bounds__(256) pool_measure_kernel(PoolTables T, int K) {
+    pool_wait();
+    pool_release();
+    const int slot = blockIdx.x, r = blockIdx.y;
+    const JobDesc &J = T.jobs[slot];
+    if (!J.live || r >= J.R || J.t >= J.n_sweeps) return;
+    const Geometry g = J.geo;
+    const int8_t *even = J.spins + (int64_t)r * 2 * g.half;
+    const int8_t *odd = even + g.half;
+    const uint8_t *d0 = J.daemons + (int64_t)r * 2 * g.half;
+    const int64_t words = (int64_t)g.L * g.L * g.W;
+    long long e_sum = 0, a_sum = 0;
+    for (int64_t w = threadIdx.x; w < words; w += blockDim.x) {
+        const int row = (int)(w / g.W);
+        const int b0 = (int)(w - (int64_t)row * g.W) * 4;
+        const int y = row % g.L, z = row / g.L;
+        const int o = (y + z) & 1;
+        const int yp = (y + 1 == g.L) ? 0 : y + 1, ym = (y == 0) ? g.L - 1 : y - 1;
+        const int zp = (z + 1 == g.L) ? 0 : z + 1, zm = (z == 0) ? g.L - 1 : z - 1;
+        const int64_t row0 = (int64_t)row * g.P, off = row0 + b0;
+        const uint32_t valid = valid_mask(b0, 0, g.Lh);
+        uint32_t O[1] = {*reinterpret_cast<const uint32_t *>(odd + off)};
+        uint32_t edge = 0, first = 0, last = 0;
+        if (o == 0) {
+            if (b0 == 0) last = (uint8_t)odd[row0 + g.Lh - 1];
+            else edge = (uint8_t)odd[off - 1];
+        } else {
+            if (b0 + 4 <= g.Lh - 1) edge = (uint8_t)odd[off + 4];
+            else first = (b0 == 0) ? (O[0] & 0xFFu) : (uint8_t)odd[row0];
+        }
+        uint32_t xp[1], xm[1];
+        x_neighbours<1>(O, o, b0, g.Lh, edge, first, last, xp, xm);
+        const BondPlanes bp = bond_planes(*reinterpret_cast<const uint32_t *>(J.bonds + off));
+        const uint32_t neg = negative_terms(
+            bp, xp[0], xm[0], *reinterpret_cast<const uint32_t *>(odd + ((int64_t)z * g.L + yp) * g.P + b0),
+            *reinterpret_cast<const uint32_t *>(odd + ((int64_t)z * g.L + ym) * g.P + b0),
+            *reinterpret_cast<const uint32_t *>(odd + ((int64_t)zp * g.L + y) * g.P + b0),
+            *reinterpret_cast<const uint32_t *>(odd + ((int64_t)zm * g.L + y) * g.P + b0));
+        const uint32_t u32 = unsatisfied32(neg, *reinterpret_cast<const uint32_t *>(even + off)) & valid;
+        e_sum += 2 * (int)((((u32 >> 5) * 0x01010101u) >> 24)) - 6 * (__popc(valid) / 8);
+        const uint32_t D0 = *reinterpret_cast<const uint32_t *>(d0 + off) & valid;
+        const uint32_t D1 = *reinterpret_cast<const uint32_t *>(d0 + g.half + off) & valid;
+        a_sum += 4 * (long long)(((D0 * 0x01010101u) >> 24) + ((D1 * 0x01010101u) >> 24));
+    }
+    __shared__ long long red[2][8];
+    __shared__ int improved;
+    e_sum = __reduce_add_sync(0xFFFFFFFFu, (int)e_sum);
+    a_sum = __reduce_add_sync(0xFFFFFFFFu, (int)a_sum);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) {
+        red[0][warp] = e_sum;
+        red[1][warp] = a_sum;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long e = 0, a = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            e += red[0][i];
+            a += red[1][i];
+        }
+        const int64_t t_after = J.t + K < J.n_sweeps ? J.t + K : J.n_sweeps;
+        T.energy[slot * kPoolMaxR + r] = e;
+        T.aux[slot * kPoolMaxR + r] = a;
+        improved = e < T.best_energy[slot * kPoolMaxR + r];
+        if (improved) {
+            T.best_energy[slot * kPoolMaxR + r] = e;
+            T.best_t[slot * kPoolMaxR + r] = t_after;
+        }
+    }
+    __syncthreads();
+    if (!improved) return;
+    // copy the configuration to the natural-layout best buffer
+    const int64_t N = (int64_t)g.L * g.L * g.L;
+    int8_t *best = J.best + (int64_t)r * N;
+    for (int64_t site = threadIdx.x; site < N; site += blockDim.x) {
+        const int x = (int)(site % g.L), y = (int)((site / g.L) % g.L), z = (int)(site / ((int64_t)g.L * g.L));
+        const int par = (x + y + z) & 1;
+        best[site] = even[(int64_t)par * g.half + ((int64_t)z * g.L + y) * g.P + (x >> 1)];
+    }
+}
+
+// t <- min(t + K, n_sweeps) for every live job (the last node of a tick).
+__global__ void pool_advance_kernel(JobDesc *jobs, int max_jobs, int K) {
+    pool_wait();
+    pool_release();
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max_jobs; i += gridDim.x * blockDim.x) {
+        JobDesc &J = jobs[i];
+        if (!J.live) continue;
+        J.t = J.t + K < J.n_sweeps ? J.t + K : J.n_sweeps;
+    }
+}
+
+static cudaError_t launch_pdl(const void *fn, dim3 grid, dim3 block, cudaStream_t st, void **args, bool pdl) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, fn, args);
+}
+
+}  // namespace micsa
+
+using namespace micsa;
+
+// ------------------------------------------------------------------ host --
+struct PoolJob {
+    int64_t id = -1;
+    micsa_job_desc desc{};
+    size_t off_bonds = 0, off_spins = 0, off_daemons = 0, off_best = 0, off_thr = 0, bytes = 0;
+    int64_t t = 0;           // host mirror of sweeps done after the queued ticks
+    int64_t done_tick = -1;  // tick index whose completion finishes the job
+    bool live = false;
+};
+
+struct micsa_pool {
+    int device = 0, sm_count = 0;
+    int max_jobs = 0, K = 64;
+    size_t arena_bytes = 0;
+    uint8_t *arena = nullptr;
+    std::map<size_t, size_t> free_list;  // offset -> size
+    JobDesc *d_jobs = nullptr;           // device table
+    std::vector<JobDesc> h_jobs;         // host mirror (t follows every queued tick)
+    JobDesc *h_jobs_stage = nullptr;     // pinned copy being uploaded
+    VBlock *d_vblocks = nullptr, *h_vblocks = nullptr;  // h_vblocks: pinned upload source
+    int32_t *d_nvb = nullptr, *h_nvb = nullptr;
+    int max_vblocks = 0;
+    long long *d_results = nullptr;  // energy | aux | best_energy | best_t, [max_jobs][kPoolMaxR] each
+    std::vector<PoolJob> slots;
+    int64_t next_id = 1;
+    int64_t ticks_queued = 0;
+    std::vector<cudaEvent_t> tick_events;  // ring of events, one per queued tick
+    int64_t launches = 0;
+    cudaStream_t stream = nullptr;
+    cudaStream_t capture_stream = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    bool tables_dirty = true;
+    cudaEvent_t tables_free = nullptr;  // the last table upload has been consumed
+    // per slot: pinned staging of the job's initial data (cut points + result
+    // reset values) and the event after which it may be overwritten
+    std::vector<uint64_t *> stage;
+    std::vector<size_t> stage_cap;
+    std::vector<cudaEvent_t> stage_free;
+    int grid_blocks = 0;
+    bool pdl = true;
+    int use_graph = 1;
+    std::string err;
+};
+
+namespace {
+
+int pfail(micsa_pool_t p, int code, const char *fmt, ...) __attribute__((format(printf, 3, 4)));
+int pfail(micsa_pool_t p, int code, const char *fmt, ...) {
+    if (p) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        p->err = buf;
+    }
+    return code;
+}
+
+#define PCK(p, expr, what)                                                                   \
+    do {                                                                                     \
+        cudaError_t e_ = (expr);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return pfail(p, e_ == cudaErrorMemoryAllocation ? MICSA_E_OOM : MICSA_E_CUDA, "%s: %s", \
+                         what, cudaGetErrorString(e_));                                      \
+    } while (0)
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+bool arena_alloc(micsa_pool_t p, size_t bytes, size_t *off) {
+    bytes = align_up(bytes);
+    for (auto it = p->free_list.begin(); it != p->free_list.end(); ++it) {
+        if (it->second >= bytes) {
+            *off = it->first;
+            const size_t rest = it->second - bytes;
+            const size_t new_off = it->first + bytes;
+            p->free_list.erase(it);
+            if (rest) p->free_list[new_off] = rest;
+            return true;
+        }
+    }
+    return false;
+}
+
+void arena_free(micsa_pool_t p, size_t off, size_t bytes) {
+    bytes = align_up(bytes);
+    auto it = p->free_list.emplace(off, bytes).first;
+    auto next = std::next(it);
+    if (next != p->free_list.end() && it->first + it->second == next->first) {
+        it->second += next->second;
+        p->free_list.erase(next);
+    }
+    if (it != p->free_list.begin()) {
+        auto prev = std::prev(it);
+        if (prev->first + prev->second == it->first) {
+            prev->second += it->second;
+            p->free_list.erase(it);
+        }
+    }
+}
+
+size_t arena_free_bytes(const micsa_pool_t p) {
+    size_t s = 0;
+    for (auto &kv : p->free_list) s += kv.second;
+    return s;
+}
+
+double schedule_T(const micsa_job_desc &d, int64_t k) {
+    if (d.n_sweeps <= 1) return d.T_start;
+    return d.T_start + (d.T_end - d.T_start) * ((double)k / (double)(d.n_sweeps - 1));
+}
+
+struct JobSizes {
+    Geometry g;
+    int nw;
+    size_t bonds, state, best, thr;
+    int64_t n_refresh;
+};
+
+JobSizes job_sizes(const micsa_job_desc &d) {
+    JobSizes s;
+    s.g = make_geometry(d.L);
+    s.nw = s.g.W % 4 == 0 ? 4 : 1;
+    s.bonds = (size_t)2 * s.g.half;
+    s.state = (size_t)d.n_replicas * 2 * s.g.half;
+    s.best = (size_t)d.n_replicas * d.L * d.L * d.L;
+    s.n_refresh = (d.n_sweeps + d.refresh_interval - 1) / d.refresh_interval;
+    if (s.n_refresh < 1) s.n_refresh = 1;
+    s.thr = sizeof(uint64_t) * 3 * (size_t)s.n_refresh;
+    return s;
+}
+
+// Rebuild the virtual-block table and upload both tables (descriptor rows and
+// vblocks) after the previous upload has been consumed.
+int upload_tables(micsa_pool_t p) {
+    if (!p->tables_dirty) return MICSA_OK;
+    PCK(p, cudaEventSynchronize(p->tables_free), "wait for table upload");
+    int nvb = 0;
+    // big jobs first, so that the grid-stride loop starts on the long work items
+    std::vector<int> order;
+    for (int i = 0; i < p->max_jobs; ++i)
+        if (p->slots[i].live) order.push_back(i);
+    std::sort(order.begin(), order.end(), [&](int a, int b) {
+        return p->slots[a].desc.L * p->slots[a].desc.n_replicas > p->slots[b].desc.L * p->slots[b].desc.n_replicas;
+    });
+    for (int i : order) {
+        const JobDesc &J = p->h_jobs[i];
+        const int64_t items = (int64_t)J.R * J.geo.L * J.geo.L * (J.geo.W / J.nw);
+        for (int64_t c = 0; c < items; c += kVBlock) {
+            if (nvb >= p->max_vblocks) return pfail(p, MICSA_E_BUSY, "virtual block table full");
+            p->h_vblocks[nvb++] = VBlock{i, (int32_t)c};
+        }
+    }
+    *p->h_nvb = nvb;
+    std::memcpy(p->h_jobs_stage, p->h_jobs.data(), sizeof(JobDesc) * p->max_jobs);
+    PCK(p, cudaMemcpyAsync(p->d_jobs, p->h_jobs_stage, sizeof(JobDesc) * p->max_jobs, cudaMemcpyHostToDevice, p->stream), "upload jobs");
+    PCK(p, cudaMemcpyAsync(p->d_vblocks, p->h_vblocks, sizeof(VBlock) * (size_t)(nvb ? nvb : 1), cudaMemcpyHostToDevice, p->stream), "upload vblocks");
+    PCK(p, cudaMemcpyAsync(p->d_nvb, p->h_nvb, sizeof(int32_t), cudaMemcpyHostToDevice, p->stream), "upload vblock count");
+    PCK(p, cudaEventRecord(p->tables_free, p->stream), "record table event");
+    p->tables_dirty = false;
+    return MICSA_OK;
+}
+
+int enqueue_tick(micsa_pool_t p, cudaStream_t st) {
+    PoolTables T{p->d_jobs, p->d_vblocks, p->d_nvb, p->d_results, p->d_results + (size_t)p->max_jobs * kPoolMaxR,
+                 p->d_results + 2 * (size_t)p->max_jobs * kPoolMaxR, p->d_results + 3 * (size_t)p->max_jobs * kPoolMaxR};
+    for (int k = 0; k < p->K; ++k)
+        for (int par = 0; par < 2; ++par) {
+            void *args[] = {&T, &k, &par};
+            PCK(p, launch_pdl((const void *)pool_half_sweep_kernel, dim3(p->grid_blocks), dim3(kVBlock), st, args, p->pdl), "pool half-sweep launch");
+        }
+    int K = p->K;
+    void *margs[] = {&T, &K};
+    PCK(p, launch_pdl((const void *)pool_measure_kernel, dim3(p->max_jobs, kPoolMaxR), dim3(256), st, margs, p->pdl), "pool measure launch");
+    int mj = p->max_jobs;
+    void *aargs[] = {&p->d_jobs, &mj, &K};
+    PCK(p, launch_pdl((const void *)pool_advance_kernel, dim3((p->max_jobs + 255) / 256), dim3(256), st, aargs, p->pdl), "pool advance launch");
+    return MICSA_OK;
+}
+
+int ensure_graph(micsa_pool_t p) {
+    if (p->graph || !p->use_graph) return MICSA_OK;
+    PCK(p, cudaStreamBeginCapture(p->capture_stream, cudaStreamCaptureModeThreadLocal), "pool begin capture");
+    const int rc = enqueue_tick(p, p->capture_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(p->capture_stream, &g);
+    if (rc != MICSA_OK) {
+        if (g) cudaGraphDestroy(g);
+        return rc;
+    }
+    PCK(p, e, "pool end capture");
+    const cudaError_t e2 = cudaGraphInstantiate(&p->graph, g, 0);
+    cudaGraphDestroy(g);
+    PCK(p, e2, "pool graph instantiate");
+    return MICSA_OK;
+}
+
+void release_slot(micsa_pool_t p, int i) {
+    PoolJob &j = p->slots[i];
+    arena_free(p, j.off_bonds, j.bytes);
+    j = PoolJob{};
+    p->h_jobs[i] = JobDesc{};
+    p->tables_dirty = true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int micsa_pool_create(size_t arena_bytes, int max_jobs, int tick_sweeps, micsa_pool_t *out) {
+    if (!out || max_jobs < 1 || max_jobs > 65535 || tick_sweeps < 1 || tick_sweeps > 4096 || arena_bytes < (1u << 20))
+        return MICSA_E_INVALID_ARG;
+    *out = nullptr;
+    micsa_pool *p = new (std::nothrow) micsa_pool;
+    if (!p) return MICSA_E_OOM;
+    p->max_jobs = max_jobs;
+    p->K = tick_sweeps;
+    p->arena_bytes = align_up(arena_bytes);
+    p->slots.resize(max_jobs);
+    p->h_jobs.assign(max_jobs, JobDesc{});
+    p->stage.assign(max_jobs, nullptr);
+    p->stage_cap.assign(max_jobs, 0);
+    p->stage_free.assign(max_jobs, nullptr);
+    int rc = MICSA_OK;
+    auto bail = [&](int code) { rc = code; };
+    cudaError_t e = cudaSuccess;
+    do {
+        if ((e = cudaGetDevice(&p->device)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+        if ((e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+        if ((e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+        if ((e = cudaStreamCreateWithFlags(&p->capture_stream, cudaStreamNonBlocking)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+        if ((e = cudaEventCreateWithFlags(&p->tables_free, cudaEventDisableTiming)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+        if ((e = cudaMalloc(&p->arena, p->arena_bytes)) != cudaSuccess) { bail(MICSA_E_OOM); break; }
+        p->free_list[0] = p->arena_bytes;
+        p->max_vblocks = 1 << 22;
+        if ((e = cudaMalloc(&p->d_jobs, sizeof(JobDesc) * max_jobs)) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_vblocks, sizeof(VBlock) * (size_t)p->max_vblocks)) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_nvb, sizeof(int32_t))) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_results, sizeof(long long) * 4 * (size_t)max_jobs * kPoolMaxR)) != cudaSuccess) { bail(MICSA_E_OOM); break; }
+        if ((e = cudaMallocHost(&p->h_jobs_stage, sizeof(JobDesc) * max_jobs)) != cudaSuccess ||
+            (e = cudaMallocHost(&p->h_vblocks, sizeof(VBlock) * (size_t)p->max_vblocks)) != cudaSuccess ||
+            (e = cudaMallocHost(&p->h_nvb, sizeof(int32_t))) != cudaSuccess) { bail(MICSA_E_OOM); break; }
+        *p->h_nvb = 0;
+        for (auto &ev : p->stage_free)
+            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+        if (rc) break;
+        if ((e = cudaMemsetAsync(p->d_jobs, 0, sizeof(JobDesc) * max_jobs, p->stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(p->d_nvb, 0, sizeof(int32_t), p->stream)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+        int per_sm = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pool_half_sweep_kernel, kVBlock, 0);
+        p->grid_blocks = (per_sm > 0 ? per_sm : 4) * p->sm_count;
+        p->tick_events.resize(64);
+        for (auto &ev : p->tick_events)
+            if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+        if (rc) break;
+        if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+    } while (0);
+    if (rc != MICSA_OK) p->err = std::string("pool creation failed: ") + cudaGetErrorString(e);
+    if (rc != MICSA_OK) {
+        micsa_pool_destroy(p);
+        return rc;
+    }
+    *out = p;
+    return MICSA_OK;
+}
+
+void micsa_pool_destroy(micsa_pool_t p) {
+    if (!p) return;
+    if (p->stream) cudaStreamSynchronize(p->stream);
+    if (p->graph) cudaGraphExecDestroy(p->graph);
+    for (auto ev : p->tick_events)
+        if (ev) cudaEventDestroy(ev);
+    for (auto *b : p->stage) cudaFreeHost(b);
+    for (auto ev : p->stage_free)
+        if (ev) cudaEventDestroy(ev);
+    if (p->tables_free) cudaEventDestroy(p->tables_free);
+    cudaFree(p->arena);
+    cudaFree(p->d_jobs);
+    cudaFree(p->d_vblocks);
+    cudaFree(p->d_nvb);
+    cudaFree(p->d_results);
+    cudaFreeHost(p->h_jobs_stage);
+    cudaFreeHost(p->h_vblocks);
+    cudaFreeHost(p->h_nvb);
+    if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
+    if (p->stream) cudaStreamDestroy(p->stream);
+    delete p;
+}
+
+const char *micsa_pool_last_error(micsa_pool_t p) { return p ? p->err.c_str() : "invalid pool (NULL)"; }
+
+int micsa_pool_job_bytes(const micsa_job_desc *job, size_t *bytes) {
+    if (!job || !bytes) return MICSA_E_INVALID_ARG;
+    const JobSizes s = job_sizes(*job);
+    *bytes = align_up(s.bonds) + 2 * align_up(s.state) + align_up(s.best) + align_up(s.thr);
+    return MICSA_OK;
+}
+
+int micsa_pool_submit(micsa_pool_t p, const micsa_job_desc *job, int64_t *job_id) {
+    if (!p || !job || !job_id) return MICSA_E_INVALID_ARG;
+    const micsa_job_desc d = *job;
+    if (d.L < 2 || d.L > 1024 || (d.L & 1) || d.n_replicas < 1 || d.n_replicas > kPoolMaxR || d.n_sweeps < 1 ||
+        d.refresh_interval < 1 || !(d.T_start > 0.0) || !(d.T_end > 0.0) || !std::isfinite(d.T_start) ||
+        !std::isfinite(d.T_end))
+        return pfail(p, MICSA_E_INVALID_ARG, "bad job description");
+    int slot = -1;
+    for (int i = 0; i < p->max_jobs; ++i)
+        if (p->slots[i].id < 0) { slot = i; break; }
+    if (slot < 0) return pfail(p, MICSA_E_BUSY, "no free slot");
+    const JobSizes s = job_sizes(d);
+    size_t total = 0;
+    micsa_pool_job_bytes(&d, &total);
+    size_t off = 0;
+    if (!arena_alloc(p, total, &off)) return pfail(p, MICSA_E_BUSY, "arena has no %zu free bytes", total);
+    PoolJob &J = p->slots[slot];
+    J.id = p->next_id++;
+    J.desc = d;
+    J.bytes = total;
+    J.off_bonds = off;
+    J.off_spins = J.off_bonds + align_up(s.bonds);
+    J.off_daemons = J.off_spins + align_up(s.state);
+    J.off_best = J.off_daemons + align_up(s.state);
+    J.off_thr = J.off_best + align_up(s.best);
+    J.t = 0;
+    J.live = true;
+    J.done_tick = -1;
+    // refresh cut points for every refresh of the job (ordinal j at sweep
+    // j * interval) and the reset values of its result rows, staged in pinned
+    // memory so that nothing here waits for the queued ticks
+    const size_t need = s.thr + sizeof(long long) * 4 * kPoolMaxR;
+    if (p->stage_cap[slot] < need) {
+        PCK(p, cudaEventSynchronize(p->stage_free[slot]), "staging reuse");
+        cudaFreeHost(p->stage[slot]);
+        p->stage[slot] = nullptr;
+        p->stage_cap[slot] = 0;
+        PCK(p, cudaMallocHost(&p->stage[slot], need), "pinned job staging");
+        p->stage_cap[slot] = need;
+    } else {
+        PCK(p, cudaEventSynchronize(p->stage_free[slot]), "staging reuse");
+    }
+    uint64_t *thr = p->stage[slot];
+    for (int64_t j = 0; j < s.n_refresh; ++j)
+        micsa_daemon_thresholds(schedule_T(d, j * (int64_t)d.refresh_interval), thr + 3 * j);
+    long long *init = reinterpret_cast<long long *>(reinterpret_cast<uint8_t *>(thr) + s.thr);
+    for (int q = 0; q < 4; ++q)
+        for (int r = 0; r < kPoolMaxR; ++r) init[q * kPoolMaxR + r] = (q == 2) ? (1ll << 62) : 0;
+    uint8_t *base = p->arena;
+    PCK(p, cudaMemcpyAsync(base + J.off_thr, thr, s.thr, cudaMemcpyHostToDevice, p->stream), "upload thresholds");
+    for (int q = 0; q < 4; ++q)
+        PCK(p, cudaMemcpyAsync(p->d_results + (size_t)q * p->max_jobs * kPoolMaxR + (size_t)slot * kPoolMaxR,
+                               init + q * kPoolMaxR, sizeof(long long) * kPoolMaxR, cudaMemcpyHostToDevice, p->stream),
+            "reset results");
+    PCK(p, cudaEventRecord(p->stage_free[slot], p->stream), "record staging event");
+    PCK(p, cudaMemsetAsync(base + J.off_bonds, 0, s.bonds, p->stream), "clear bonds");
+    PCK(p, cudaMemsetAsync(base + J.off_spins, 0, s.state, p->stream), "clear spins");
+    PCK(p, cudaMemsetAsync(base + J.off_daemons, 0, s.state, p->stream), "clear daemons");
+    const uint32_t k0 = (uint32_t)(d.seed & 0xFFFFFFFFu), k1 = (uint32_t)(d.seed >> 32);
+    PCK(p, launch_init_couplings(base + J.off_bonds, s.g, 1, k0, k1, p->stream), "job couplings");
+    PCK(p, launch_init_spins(reinterpret_cast<int8_t *>(base + J.off_spins), s.g, 1, d.n_replicas, k0, k1, p->stream), "job spins");
+    p->launches += 2;
+    JobDesc &D = p->h_jobs[slot];
+    D.spins = reinterpret_cast<int8_t *>(base + J.off_spins);
+    D.daemons = base + J.off_daemons;
+    D.bonds = base + J.off_bonds;
+    D.best = reinterpret_cast<int8_t *>(base + J.off_best);
+    D.thr = reinterpret_cast<const uint64_t *>(base + J.off_thr);
+    D.geo = s.g;
+    D.R = d.n_replicas;
+    D.nw = s.nw;
+    D.key0 = k0;
+    D.key1 = k1;
+    D.t = 0;
+    D.n_sweeps = d.n_sweeps;
+    D.interval = d.refresh_interval;
+    D.live = 1;
+    p->tables_dirty = true;
+    *job_id = J.id;
+    return MICSA_OK;
+}
+
+int micsa_pool_tick(micsa_pool_t p) {
+    if (!p) return MICSA_E_INVALID_ARG;
+    if (int rc = upload_tables(p)) return rc;
+    if (int rc = ensure_graph(p)) return rc;
+    if (p->graph) {
+        PCK(p, cudaGraphLaunch(p->graph, p->stream), "pool graph launch");
+    } else {
+        if (int rc = enqueue_tick(p, p->stream)) return rc;
+    }
+    p->launches += 2 * (int64_t)p->K + 2;
+    const int64_t tick = p->ticks_queued++;
+    cudaEvent_t ev = p->tick_events[tick % p->tick_events.size()];
+    if (tick >= (int64_t)p->tick_events.size())
+        PCK(p, cudaEventSynchronize(ev), "tick event reuse");  // bounds the ticks in flight
+    PCK(p, cudaEventRecord(ev, p->stream), "record tick event");
+    for (int i = 0; i < p->max_jobs; ++i) {
+        PoolJob &J = p->slots[i];
+        if (!J.live || J.done_tick >= 0) continue;
+        J.t = std::min<int64_t>(J.t + p->K, J.desc.n_sweeps);
+        p->h_jobs[i].t = J.t;  // what the tick's advance kernel will leave on the device
+        if (J.t >= J.desc.n_sweeps) J.done_tick = tick;
+    }
+    return MICSA_OK;
+}
+
+int micsa_pool_wait(micsa_pool_t p) {
+    if (!p) return MICSA_E_INVALID_ARG;
+    PCK(p, cudaStreamSynchronize(p->stream), "pool synchronize");
+    return MICSA_OK;
+}
+
+int micsa_pool_wait_ticks(micsa_pool_t p, int max_pending) {
+    if (!p || max_pending < 0) return MICSA_E_INVALID_ARG;
+    const int64_t ring = (int64_t)p->tick_events.size();
+    for (int64_t tick = p->ticks_queued - 1 - max_pending; tick >= 0 && tick > p->ticks_queued - 1 - ring; --tick) {
+        // ticks complete in order: waiting for the newest one that must be done suffices
+        PCK(p, cudaEventSynchronize(p->tick_events[tick % ring]), "tick event");
+        break;
+    }
+    return MICSA_OK;
+}
+
+int micsa_pool_poll(micsa_pool_t p, int64_t job_id, micsa_job_result *res, int8_t *best_spins) {
+    if (!p) return MICSA_E_INVALID_ARG;
+    int slot = -1;
+    for (int i = 0; i < p->max_jobs; ++i)
+        if (p->slots[i].id == job_id) { slot = i; break; }
+    if (slot < 0) return pfail(p, MICSA_E_NOT_FOUND, "unknown job %lld", (long long)job_id);
+    PoolJob &J = p->slots[slot];
+    if (J.done_tick < 0) return MICSA_E_BUSY;
+    cudaEvent_t ev = p->tick_events[J.done_tick % p->tick_events.size()];
+    if (J.done_tick + (int64_t)p->tick_events.size() > p->ticks_queued - 1) {
+        const cudaError_t q = cudaEventQuery(ev);
+        if (q == cudaErrorNotReady) return MICSA_E_BUSY;
+        PCK(p, q, "tick event query");
+    } else {
+        PCK(p, cudaEventSynchronize(ev), "tick event");  // event slot reused: wait on it via the stream order
+    }
+    const int R = J.desc.n_replicas;
+    long long vals[4][kPoolMaxR];
+    for (int q = 0; q < 4; ++q)
+        PCK(p, cudaMemcpy(vals[q], p->d_results + (size_t)q * p->max_jobs * kPoolMaxR + (size_t)slot * kPoolMaxR,
+                          sizeof(long long) * kPoolMaxR, cudaMemcpyDeviceToHost), "copy results");
+    if (best_spins) {
+        const size_t n = (size_t)R * J.desc.L * J.desc.L * J.desc.L;
+        PCK(p, cudaMemcpy(best_spins, p->arena + J.off_best, n, cudaMemcpyDeviceToHost), "copy best spins");
+    }
+    if (res) {
+        std::memset(res, 0, sizeof(*res));
+        res->job_id = J.id;
+        res->sweeps_done = J.desc.n_sweeps;
+        res->n_replicas = R;
+        for (int r = 0; r < R; ++r) {
+            res->energy[r] = vals[0][r];
+            res->aux[r] = vals[1][r];
+            res->best_energy[r] = vals[2][r];
+            res->best_t[r] = vals[3][r];
+        }
+    }
+    // the slot's device memory may be reused only after its last tick has run
+    release_slot(p, slot);
+    return MICSA_OK;
+}
+
+int micsa_pool_stats(micsa_pool_t p, int *live_jobs, size_t *free_bytes, int64_t *launches) {
+    if (!p) return MICSA_E_INVALID_ARG;
+    if (live_jobs) {
+        int n = 0;
+        for (auto &j : p->slots) n += j.id >= 0;
+        *live_jobs = n;
+    }
+    if (free_bytes) *free_bytes = arena_free_bytes(p);
+    if (launches) *launches = p->launches;
+    return MICSA_OK;
+}
+
+int micsa_pool_set_launch_config(micsa_pool_t p, int blocks_per_sm, int pdl, int use_graph) {
+    if (!p || blocks_per_sm < 1 || blocks_per_sm > 64) return MICSA_E_INVALID_ARG;
+    PCK(p, cudaStreamSynchronize(p->stream), "synchronize before reconfiguring");
+    if (p->graph) cudaGraphExecDestroy(p->graph);
+    p->graph = nullptr;
+    p->grid_blocks = blocks_per_sm * p->sm_count;
+    p->pdl = pdl != 0;
+    p->use_graph = use_graph != 0;
+    return MICSA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,97 @@
+// sweep_body.cuh -- the update of one thread's chunk of a row: the body shared
+// by the single-handle half-sweep kernel and the batched (pool) kernel.
+#pragma once
+
+#include "micsa_internal.h"
+
+namespace micsa {
+
+// Update NW words (4 NW sites) of row `row` (= z L + y) of parity p of one
+// replica: spins/daemons point at that replica's [2][half] block, bonds at the
+// sample's [2][half] block. gid is the replica's global id in the Philox
+// counter, t the global sweep index. refresh: draw the daemon words instead of
+// reading them (Sec. 2.7); METRO: Metropolis acceptance with the cut points th*.
+template <int NW, bool METRO>
+__device__ __forceinline__ void update_chunk(const Geometry &g, int8_t *spins, uint8_t *daemons,
+                                             const uint8_t *bonds, int p, int row, int c,
+                                             uint32_t gid, uint32_t key0, uint32_t key1, int64_t t,
+                                             bool refresh, uint64_t th0, uint64_t th1,
+                                             uint64_t th2) {
+    const int y = row % g.L, z = row / g.L;
+    const int o = (p + y + z) & 1;
+    const int b0 = c * 4 * NW;  // first byte of this thread's range within the row
+    const int yp = (y + 1 == g.L) ? 0 : y + 1, ym = (y == 0) ? g.L - 1 : y - 1;
+    const int zp = (z + 1 == g.L) ? 0 : z + 1, zm = (z == 0) ? g.L - 1 : z - 1;
+    const int64_t row0 = (int64_t)row * g.P;
+    const int64_t off_c = row0 + b0;
+    const int8_t *__restrict__ opp = spins + (int64_t)(1 - p) * g.half;
+    int8_t *__restrict__ own_s = spins + (int64_t)p * g.half;
+    uint8_t *__restrict__ own_d = daemons + (int64_t)p * g.half;
+
+    uint32_t Bw[NW], O[NW], Oyp[NW], Oym[NW], Ozp[NW], Ozm[NW], S[NW], D[NW];
+    load_words_ro<NW>(bonds + (int64_t)p * g.half + off_c, Bw);
+    load_words_ro<NW>(opp + off_c, O);
+    load_words_ro<NW>(opp + ((int64_t)z * g.L + yp) * g.P + b0, Oyp);
+    load_words_ro<NW>(opp + ((int64_t)z * g.L + ym) * g.P + b0, Oym);
+    load_words_ro<NW>(opp + ((int64_t)zp * g.L + y) * g.P + b0, Ozp);
+    load_words_ro<NW>(opp + ((int64_t)zm * g.L + y) * g.P + b0, Ozm);
+    load_words<NW>(own_s + off_c, S);
+    if (!METRO && !refresh) load_words<NW>(own_d + off_c, D);
+
+    // edge bytes for the x shift and the periodic wrap of the row
+    uint32_t edge = 0, first = 0, last = 0;
+    if (o == 0) {
+        if (b0 == 0) last = (uint8_t)__ldg(opp + row0 + g.Lh - 1);
+        else edge = (uint8_t)__ldg(opp + off_c - 1);
+    } else {
+        if (b0 + 4 * NW <= g.Lh - 1) edge = (uint8_t)__ldg(opp + off_c + 4 * NW);
+        else first = (b0 == 0) ? (O[0] & 0xFFu) : (uint8_t)__ldg(opp + row0);
+    }
+    uint32_t xp[NW], xm[NW];
+    x_neighbours<NW>(O, o, b0, g.Lh, edge, first, last, xp, xm);
+    const uint32_t quad0 = (uint32_t)((((int64_t)p * g.L + z) * g.L + y) * g.W + c * NW);
+
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+        const BondPlanes bp = bond_planes(Bw[j]);
+        const uint32_t neg = negative_terms(bp, xp[j], xm[j], Oyp[j], Oym[j], Ozp[j], Ozm[j]);
+        const uint32_t u32 = unsatisfied32(neg, S[j]);
+        const uint32_t valid = valid_mask(b0, j, g.Lh);
+        if (METRO) {
+            // dH = 12 - 4u > 0 <=> u < 3; accept iff a fresh uniform is below
+            // the Metropolis cut point of dH (index 2 - u).
+            const uint4 w = philox4x32_10(
+                make_uint4(quad0 + j, (uint32_t)t, (gid << 2) | kTagMetro, (uint32_t)((uint64_t)t >> 32)),
+                key0, key1);
+            uint32_t am = 0;
+#pragma unroll
+            for (int l = 0; l < 4; ++l) {
+                const uint32_t u = (u32 >> (8 * l + 5)) & 7u;
+                bool acc = u >= 3;
+                if (!acc) {
+                    const uint64_t cut = (u == 2) ? th0 : (u == 1) ? th1 : th2;
+                    acc = (uint64_t)lane_of(w, l) < cut;
+                }
+                if (acc) am |= 0xFFu << (8 * l);
+            }
+            am &= valid;
+            S[j] ^= am & 0xFEFEFEFEu;
+        } else {
+            if (refresh) {
+                const uint4 w = philox4x32_10(
+                    make_uint4(quad0 + j, (uint32_t)t, (gid << 2) | kTagDaemon, (uint32_t)((uint64_t)t >> 32)),
+                    key0, key1);
+                D[j] = (daemon_from_uniform(w.x, th0, th1, th2) |
+                        (daemon_from_uniform(w.y, th0, th1, th2) << 8) |
+                        (daemon_from_uniform(w.z, th0, th1, th2) << 16) |
+                        (daemon_from_uniform(w.w, th0, th1, th2) << 24)) & valid;
+            }
+            const uint32_t am = creutz4(u32, D[j], valid);
+            S[j] ^= am & 0xFEFEFEFEu;
+        }
+    }
+    store_words<NW>(own_s + off_c, S);
+    if (!METRO) store_words<NW>(own_d + off_c, D);
+}
+
+}  // namespace micsa

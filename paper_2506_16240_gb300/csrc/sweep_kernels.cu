@@ -15,7 +15,7 @@
 // whole run; consecutive half-sweeps are chained with programmatic dependent
 // launch (griddepcontrol) so that a grid is scheduled while its predecessor
 // drains.
-#include "micsa_internal.h"
+#include "sweep_body.cuh"
 
 namespace micsa {
 
@@ -37,97 +37,21 @@ __global__ void __launch_bounds__(256) half_sweep_kernel(SweepArgs a) {
     const int64_t kidx = a.k + (a.cursor ? *a.cursor : 0);
     const SweepParam prm = a.params[kidx];
     const bool refresh = !METRO && prm.mode == kModeRefresh;
-    const int p = a.parity;
 
     // thread row y of the block takes replicas y, y + blockDim.y, ...
     for (int r = threadIdx.y; r < a.R; r += blockDim.y)
-    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
-         q += (int64_t)gridDim.x * blockDim.x) {
-        const int sample = (int)(q / per_sample);
-        const int64_t rem = q - (int64_t)sample * per_sample;
-        const int row = (int)(rem / chunks);
-        const int c = (int)(rem - (int64_t)row * chunks);
-        const int y = row % g.L, z = row / g.L;
-        const int o = (p + y + z) & 1;
-        const int b0 = c * 4 * NW;  // first byte of this thread's range within the row
-
-        const int yp = (y + 1 == g.L) ? 0 : y + 1, ym = (y == 0) ? g.L - 1 : y - 1;
-        const int zp = (z + 1 == g.L) ? 0 : z + 1, zm = (z == 0) ? g.L - 1 : z - 1;
-        const int64_t row0 = (int64_t)row * g.P;
-        const int64_t off_c = row0 + b0;
-        const int64_t gid = (int64_t)sample * a.R + r;
-        const int8_t *__restrict__ opp = a.spins + (gid * 2 + (1 - p)) * g.half;
-        int8_t *__restrict__ own_s = a.spins + (gid * 2 + p) * g.half;
-        uint8_t *__restrict__ own_d = a.daemons + (gid * 2 + p) * g.half;
-
-        uint32_t Bw[NW], O[NW], Oyp[NW], Oym[NW], Ozp[NW], Ozm[NW], S[NW], D[NW];
-        load_words_ro<NW>(a.bonds + (int64_t)(sample * 2 + p) * g.half + off_c, Bw);
-        load_words_ro<NW>(opp + off_c, O);
-        load_words_ro<NW>(opp + ((int64_t)z * g.L + yp) * g.P + b0, Oyp);
-        load_words_ro<NW>(opp + ((int64_t)z * g.L + ym) * g.P + b0, Oym);
-        load_words_ro<NW>(opp + ((int64_t)zp * g.L + y) * g.P + b0, Ozp);
-        load_words_ro<NW>(opp + ((int64_t)zm * g.L + y) * g.P + b0, Ozm);
-        load_words<NW>(own_s + off_c, S);
-        if (!METRO && !refresh) load_words<NW>(own_d + off_c, D);
-
-        // edge bytes for the x shift and the periodic wrap of the row
-        uint32_t edge = 0, first = 0, last = 0;
-        if (o == 0) {
-            if (b0 == 0) last = (uint8_t)__ldg(opp + row0 + g.Lh - 1);
-            else edge = (uint8_t)__ldg(opp + off_c - 1);
-        } else {
-            if (b0 + 4 * NW <= g.Lh - 1) edge = (uint8_t)__ldg(opp + off_c + 4 * NW);
-            else first = (b0 == 0) ? (O[0] & 0xFFu) : (uint8_t)__ldg(opp + row0);
+        for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
+             q += (int64_t)gridDim.x * blockDim.x) {
+            const int sample = (int)(q / per_sample);
+            const int64_t rem = q - (int64_t)sample * per_sample;
+            const int row = (int)(rem / chunks);
+            const int c = (int)(rem - (int64_t)row * chunks);
+            const int64_t gid = (int64_t)sample * a.R + r;
+            update_chunk<NW, METRO>(g, a.spins + gid * 2 * g.half, a.daemons + gid * 2 * g.half,
+                                    a.bonds + (int64_t)sample * 2 * g.half, a.parity, row, c,
+                                    (uint32_t)gid, a.key0, a.key1, prm.t, refresh, prm.th0, prm.th1,
+                                    prm.th2);
         }
-        uint32_t xp[NW], xm[NW];
-        x_neighbours<NW>(O, o, b0, g.Lh, edge, first, last, xp, xm);
-        const uint32_t quad0 = (uint32_t)((((int64_t)p * g.L + z) * g.L + y) * g.W + c * NW);
-
-#pragma unroll
-        for (int j = 0; j < NW; ++j) {
-            const BondPlanes bp = bond_planes(Bw[j]);
-            const uint32_t neg = negative_terms(bp, xp[j], xm[j], Oyp[j], Oym[j], Ozp[j], Ozm[j]);
-            const uint32_t u32 = unsatisfied32(neg, S[j]);
-            const uint32_t valid = valid_mask(b0, j, g.Lh);
-            if (METRO) {
-                // dH = 12 - 4u > 0 <=> u < 3; accept iff a fresh uniform is below
-                // the Metropolis cut point of dH (index 2 - u).
-                const uint4 w = philox4x32_10(
-                    make_uint4(quad0 + j, (uint32_t)prm.t, (uint32_t)(gid << 2) | kTagMetro,
-                               (uint32_t)((uint64_t)prm.t >> 32)),
-                    a.key0, a.key1);
-                uint32_t am = 0;
-#pragma unroll
-                for (int l = 0; l < 4; ++l) {
-                    const uint32_t u = (u32 >> (8 * l + 5)) & 7u;
-                    bool acc = u >= 3;
-                    if (!acc) {
-                        const uint64_t cut = (u == 2) ? prm.th0 : (u == 1) ? prm.th1 : prm.th2;
-                        acc = (uint64_t)lane_of(w, l) < cut;
-                    }
-                    if (acc) am |= 0xFFu << (8 * l);
-                }
-                am &= valid;
-                S[j] ^= am & 0xFEFEFEFEu;
-            } else {
-                if (refresh) {
-                    const uint4 w = philox4x32_10(
-                        make_uint4(quad0 + j, (uint32_t)prm.t, (uint32_t)(gid << 2) | kTagDaemon,
-                                   (uint32_t)((uint64_t)prm.t >> 32)),
-                        a.key0, a.key1);
-                    D[j] = daemon_from_uniform(w.x, prm.th0, prm.th1, prm.th2) |
-                           (daemon_from_uniform(w.y, prm.th0, prm.th1, prm.th2) << 8) |
-                           (daemon_from_uniform(w.z, prm.th0, prm.th1, prm.th2) << 16) |
-                           (daemon_from_uniform(w.w, prm.th0, prm.th1, prm.th2) << 24);
-                    D[j] &= valid;
-                }
-                const uint32_t am = creutz4(u32, D[j], valid);
-                S[j] ^= am & 0xFEFEFEFEu;
-            }
-        }
-        store_words<NW>(own_s + off_c, S);
-        if (!METRO) store_words<NW>(own_d + off_c, D);
-    }
 }
 
 // Advance the graph replay cursor by `step` sweeps (the last node of a graph).

@@ -1,0 +1,141 @@
+"""GPU tests of the batched pool and the serving loop.
+
+A pool job must compute exactly what a single handle computes for the same
+(L, R, seed, schedule, refresh interval), whatever slot it gets and whatever
+runs beside it; its best configuration must be the oracle's lowest-energy
+state at the tick boundaries. Admission must respect the arena size.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2506_16240_gb300 as micsa
+from paper_2506_16240_gb300 import serve
+
+pytestmark = pytest.mark.gpu
+
+O = oracle.Oracle()
+
+
+def single_handle(L, R, seed, n, interval, T0, T1):
+    sched = micsa.linear_schedule(T0, T1, n)
+    with micsa.Micsa(L, 1, R, seed) as g:
+        g.run(sched, interval)
+        e, a, _ = g.measure()
+        s, _, _ = g.get_state()
+    return e, a, s
+
+
+def run_pool(jobs, K=16, arena=1 << 28, max_jobs=64, order=None):
+    with micsa.Pool(arena, max_jobs, K) as p:
+        ids = {}
+        for idx in (order or range(len(jobs))):
+            jid = p.submit(*jobs[idx])
+            assert jid is not None
+            ids[idx] = jid
+        results = {}
+        while len(results) < len(jobs):
+            p.tick()
+            for idx, jid in ids.items():
+                if idx not in results:
+                    r = p.poll(jid)
+                    if r is not None:
+                        results[idx] = r
+        return results
+
+
+JOBS = [  # (L, R, seed, n_sweeps, interval, T_start, T_end)
+    (8, 1, 11, 100, 10, 3.0, 0.5), (16, 2, 12, 77, 5, 2.5, 0.5), (10, 3, 13, 40, 7, 2.0, 1.0),
+    (32, 2, 14, 50, 20, 2.5, 0.5), (6, 4, 15, 33, 1, 3.0, 0.3), (18, 1, 16, 64, 9, 2.5, 0.4),
+    (24, 2, 17, 16, 16, 1.5, 1.5), (30, 1, 18, 5, 3, 2.0, 0.7),
+]
+
+
+def test_pool_jobs_equal_single_handle_runs():
+    res = run_pool(JOBS)
+    for idx, (L, R, seed, n, interval, T0, T1) in enumerate(JOBS):
+        e, a, _ = single_handle(L, R, seed, n, interval, T0, T1)
+        np.testing.assert_array_equal(res[idx]["energy"], e, err_msg=str(JOBS[idx]))
+        np.testing.assert_array_equal(res[idx]["aux"], a, err_msg=str(JOBS[idx]))
+        assert res[idx]["sweeps_done"] == n
+
+
+def test_pool_result_independent_of_slot_and_neighbours():
+    alone = run_pool([JOBS[1]])[0]
+    mixed = run_pool(JOBS, order=list(reversed(range(len(JOBS)))))[1]
+    for k in ("energy", "aux", "best_energy", "best_t"):
+        np.testing.assert_array_equal(alone[k], mixed[k], err_msg=k)
+    np.testing.assert_array_equal(alone["best_spins"], mixed["best_spins"])
+
+
+@pytest.mark.parametrize("job", [JOBS[0], JOBS[2], JOBS[5]])
+def test_pool_best_configuration_matches_oracle(job):
+    L, R, seed, n, interval, T0, T1 = job
+    K = 16
+    r = run_pool([job], K=K)[0]
+    st = O.create(L, 1, R, seed)
+    sched = micsa.linear_schedule(T0, T1, n)
+    best = np.full(R, 1 << 62, np.int64)
+    best_t = np.zeros(R, np.int64)
+    best_s = np.zeros((R, L ** 3), np.int8)
+    for k0 in range(0, n, K):
+        O.run(st, sched[k0:k0 + K], interval)
+        e, a, _ = O.measure(st)
+        for rr in range(R):
+            if e[rr] < best[rr]:
+                best[rr], best_t[rr] = e[rr], st["t"]
+                best_s[rr] = st["s"][0, rr]
+    np.testing.assert_array_equal(r["best_energy"], best)
+    np.testing.assert_array_equal(r["best_t"], best_t)
+    np.testing.assert_array_equal(r["best_spins"], best_s)
+    np.testing.assert_array_equal(r["energy"], e)
+    np.testing.assert_array_equal(r["aux"], a)
+
+
+def test_admission_is_limited_by_arena_memory():
+    job = (64, 2, 21, 40, 10, 2.0, 0.5)
+    need = micsa.Pool.job_bytes(64, 2, 40, 10)
+    assert 2.5 * need > (1 << 20)
+    with micsa.Pool(arena_bytes=int(2.5 * need), max_jobs=8, tick_sweeps=16) as p:
+        a = p.submit(*job)
+        b = p.submit(*job[:2], 22, *job[3:])
+        assert a is not None and b is not None
+        assert p.submit(*job[:2], 23, *job[3:]) is None  # no room for a third
+        free_before = p.stats()["free_bytes"]
+        while p.poll(a) is None:
+            p.tick()
+        assert p.stats()["free_bytes"] > free_before
+        c = p.submit(*job[:2], 23, *job[3:])
+        assert c is not None
+        for jid in (b, c):
+            while p.poll(jid) is None:
+                p.tick()
+        assert p.stats()["live_jobs"] == 0
+
+
+def test_pool_rejects_bad_jobs():
+    with micsa.Pool(1 << 24, 4, 8) as p:
+        with pytest.raises(micsa.MicsaError):
+            p.submit(7, 1, 1, 10, 10, 1.0, 1.0)  # odd L
+        with pytest.raises(micsa.MicsaError):
+            p.submit(8, 9, 1, 10, 10, 1.0, 1.0)  # too many replicas
+        with pytest.raises(micsa.MicsaError):
+            p.submit(8, 1, 1, 10, 0, 1.0, 1.0)  # interval 0
+
+
+def test_serving_stream_results_match_alone():
+    """Requests arriving while others run are admitted into the running batch;
+    each result equals the job run alone."""
+    reqs = serve.poisson_stream(24, rate_hz=400.0, seed=5, L_range=(8, 24), sweeps_range=(20, 300),
+                                replicas_range=(1, 3))
+    with micsa.Pool(1 << 26, 6, 16) as p:  # 6 slots: later requests queue and join mid-stream
+        done = serve.Server(p).serve(reqs, realtime=True)
+    assert len(done) == len(reqs)
+    overlapped = sum(1 for r in done if any(o.admitted < r.admitted < o.done for o in done if o is not r))
+    assert overlapped > 0
+    for r in done:
+        e, a, _ = single_handle(r.L, r.n_replicas, r.seed, r.n_sweeps, r.refresh_interval, r.T_start, r.T_end)
+        np.testing.assert_array_equal(r.result["energy"], e)
+        np.testing.assert_array_equal(r.result["aux"], a)
+    s = serve.summarize(done, 1.0)
+    assert s["p99_latency_s"] >= s["p50_latency_s"] > 0
