@@ -133,6 +133,26 @@ int micsa_device_bytes(micsa_t h, size_t *bytes);
 int micsa_set_launch_config(micsa_t h, int words_per_thread, int block, int blocks_per_sm, int pdl,
                             int graph_sweeps);
 
+/* Which kernel runs MicSA sweeps (results are bit-identical for every choice):
+ *   MICSA_ENGINE_AUTO      MULTISPIN for L <= 32, RESIDENT for L <= 40,
+ *                          STREAM above
+ *   MICSA_ENGINE_STREAM    one launch per half-sweep over the lattice in HBM/L2
+ *   MICSA_ENGINE_RESIDENT  each CTA keeps one replica in shared memory (bytes,
+ *                          6 * L*L*P <= 200 KiB with P the row pitch, i.e.
+ *                          L <= 40) for resident_sweeps sweeps per launch
+ *   MICSA_ENGINE_MULTISPIN as RESIDENT with the replica held as bit planes
+ *                          (32 sites per word, Boolean update; L <= 32)
+ * An engine whose size limit the lattice exceeds is rejected.
+ * Metropolis runs always use the streaming kernel. Synchronizes. */
+#define MICSA_ENGINE_AUTO 0
+#define MICSA_ENGINE_STREAM 1
+#define MICSA_ENGINE_RESIDENT 2
+#define MICSA_ENGINE_MULTISPIN 3
+int micsa_set_engine(micsa_t h, int engine, int resident_sweeps);
+
+/* The engine that the next micsa_run will use (STREAM, RESIDENT or MULTISPIN). */
+int micsa_get_engine(micsa_t h, int *engine);
+
 /* The launch shape in effect (blocks_per_sm reports the grid cap / SM count).
  * Any pointer may be NULL. */
 int micsa_get_launch_config(micsa_t h, int *words_per_thread, int *block, int *blocks_per_sm,

@@ -25,6 +25,7 @@ MICSA_E_TIMEOUT = -4
 MICSA_E_BUSY = -5
 MICSA_E_NOT_FOUND = -6
 MICSA_E_TOO_LARGE = -7
+MICSA_ENGINE_AUTO, MICSA_ENGINE_STREAM, MICSA_ENGINE_RESIDENT, MICSA_ENGINE_MULTISPIN = 0, 1, 2, 3
 MICSA_NOALLOC_MAX_TERMS = 8192
 
 _ERRNAMES = {-1: "MICSA_E_INVALID_ARG", -2: "MICSA_E_OOM", -3: "MICSA_E_CUDA",
@@ -64,6 +65,8 @@ SIGNATURES = {
     "micsa_launch_count": (_c.c_int, [_P, _i64p]),
     "micsa_set_launch_config": (_c.c_int, [_P, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int]),
     "micsa_get_launch_config": (_c.c_int, [_P, _ip, _ip, _ip, _ip, _ip]),
+    "micsa_set_engine": (_c.c_int, [_P, _c.c_int, _c.c_int]),
+    "micsa_get_engine": (_c.c_int, [_P, _ip]),
     "micsa_destroy": (None, [_P]),
     "micsa_last_error": (_c.c_char_p, [_P]),
     "micsa_measure_noalloc": (_c.c_int, [_P, _P, _P, _c.c_int, _c.c_int, _c.c_int, _P, _P, _P, _P]),
@@ -224,6 +227,17 @@ class Micsa:
         _check(lib().micsa_get_launch_config(self.h, *[ctypes.byref(x) for x in v]), self.h)
         keys = ("words_per_thread", "block", "blocks_per_sm", "pdl", "graph_sweeps")
         return {k: x.value for k, x in zip(keys, v)}
+
+    def set_engine(self, engine="auto", resident_sweeps=64):
+        code = {"auto": MICSA_ENGINE_AUTO, "stream": MICSA_ENGINE_STREAM,
+                "resident": MICSA_ENGINE_RESIDENT, "multispin": MICSA_ENGINE_MULTISPIN}[engine]
+        _check(lib().micsa_set_engine(self.h, code, int(resident_sweeps)), self.h)
+
+    def engine(self):
+        v = ctypes.c_int()
+        _check(lib().micsa_get_engine(self.h, ctypes.byref(v)), self.h)
+        return {MICSA_ENGINE_STREAM: "stream", MICSA_ENGINE_RESIDENT: "resident",
+                MICSA_ENGINE_MULTISPIN: "multispin"}[v.value]
 
     def launch_count(self):
         n = ctypes.c_int64()

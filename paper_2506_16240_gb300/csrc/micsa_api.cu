@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -40,6 +41,9 @@ struct micsa_ctx {
     cudaEvent_t params_free = nullptr;  // the last upload of h_params has been consumed
     int64_t *d_cursor = nullptr;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};  // [metro]: G sweeps + cursor advance
+    int engine = MICSA_ENGINE_AUTO;  // which kernel runs MicSA sweeps
+    int resident_sweeps = 256;       // sweeps per resident launch
+    ResidentUnit *d_units = nullptr; // one unit per (sample, replica)
     int graph_g[2] = {0, 0};
     std::string err;
 };
@@ -202,6 +206,44 @@ int capture_graph(micsa_t h, bool metro, int G, const LaunchConfig &lc) {
     return MICSA_OK;
 }
 
+// The engine a MicSA run uses now.
+int active_engine(micsa_t h) {
+    if (!h->d_units || h->engine == MICSA_ENGINE_STREAM) return MICSA_ENGINE_STREAM;
+    if (h->engine == MICSA_ENGINE_RESIDENT) return MICSA_ENGINE_RESIDENT;
+    if (multispin_smem_bytes(h->geo) > 0) return MICSA_ENGINE_MULTISPIN;
+    return h->engine == MICSA_ENGINE_MULTISPIN ? MICSA_ENGINE_STREAM : MICSA_ENGINE_RESIDENT;
+}
+
+bool use_resident(micsa_t h) { return active_engine(h) != MICSA_ENGINE_STREAM; }
+
+// MicSA sweeps [0, n) of the uploaded table with the shared-memory resident
+// kernel, resident_sweeps per launch; every (sample, replica) is one unit.
+int run_resident(micsa_t h, int64_t n, const LaunchConfig &lc) {
+    const bool ms = active_engine(h) == MICSA_ENGINE_MULTISPIN;
+    const size_t smem = ms ? multispin_smem_bytes(h->geo) : resident_smem_bytes(h->geo);
+    const int per_sm = ms ? multispin_blocks_per_sm(false, smem) : resident_blocks_per_sm(false, smem);
+    const int n_units = h->S * h->R;
+    int grid = (per_sm > 0 ? per_sm : 1) * h->sm_count;
+    if (grid > n_units) grid = n_units;
+    ResidentArgs ra{};
+    ra.units = h->d_units;
+    ra.n_units = n_units;
+    ra.geo = h->geo;
+    ra.key0 = (uint32_t)(h->seed & 0xFFFFFFFFu);
+    ra.key1 = (uint32_t)(h->seed >> 32);
+    ra.params = h->d_params;
+    for (int64_t k0 = 0; k0 < n; k0 += h->resident_sweeps) {
+        ra.k0 = k0;
+        ra.K = (int)std::min<int64_t>(h->resident_sweeps, n - k0);
+        if (ms)
+            CK(h, launch_multispin(ra, false, smem, grid, lc.pdl, h->stream), "multispin launch");
+        else
+            CK(h, launch_resident(ra, false, smem, grid, lc.pdl, h->stream), "resident launch");
+        ++h->launches;
+    }
+    return MICSA_OK;
+}
+
 // Upload the table of n sweeps and run them: whole blocks of G sweeps by graph
 // replay, the rest by direct launches. Every sweep is the even half-sweep
 // followed by the odd one (Sec. 2.8 steps (i), (ii)).
@@ -211,6 +253,7 @@ int run_table(micsa_t h, bool metro, int64_t n) {
     CK(h, cudaMemcpyAsync(h->d_params, h->h_params, sizeof(SweepParam) * (size_t)n,
                           cudaMemcpyHostToDevice, h->stream), "upload sweep parameters");
     CK(h, cudaEventRecord(h->params_free, h->stream), "record parameter event");
+    if (!metro && use_resident(h)) return run_resident(h, n, lc);
     const int G = lc.graph_sweeps;
     int64_t done = 0;
     if (G > 0 && n >= 2 * (int64_t)G) {
@@ -340,6 +383,7 @@ void micsa_destroy(micsa_t h) {
     cudaFree(h->d_meas);
     cudaFree(h->d_stage);
     cudaFree(h->d_cursor);
+    cudaFree(h->d_units);
     cudaFree(h->d_params);
     cudaFreeHost(h->h_params);
     drop_graphs(h);
@@ -379,6 +423,17 @@ int micsa_create(int L, int n_samples, int n_replicas, uint64_t seed, micsa_t *o
         if ((e = cudaMalloc(&h->d_daemons, state)) != cudaSuccess) { rc = cuda_fail(h, e, "cudaMalloc daemons"); break; }
         if ((e = cudaMalloc(&h->d_bonds, bonds)) != cudaSuccess) { rc = cuda_fail(h, e, "cudaMalloc bonds"); break; }
         if ((e = cudaMalloc(&h->d_meas, meas)) != cudaSuccess) { rc = cuda_fail(h, e, "cudaMalloc measure"); break; }
+        if (resident_smem_bytes(h->geo) > 0) {
+            std::vector<ResidentUnit> units((size_t)h->S * h->R);
+            for (int a = 0; a < h->S; ++a)
+                for (int r = 0; r < h->R; ++r) {
+                    const int64_t gid = (int64_t)a * h->R + r;
+                    units[gid] = ResidentUnit{h->d_spins + gid * 2 * h->geo.half, h->d_daemons + gid * 2 * h->geo.half,
+                                              h->d_bonds + (int64_t)a * 2 * h->geo.half, (int32_t)gid, -1};
+                }
+            if ((e = cudaMalloc(&h->d_units, sizeof(ResidentUnit) * units.size())) != cudaSuccess) { rc = cuda_fail(h, e, "cudaMalloc units"); break; }
+            if ((e = cudaMemcpy(h->d_units, units.data(), sizeof(ResidentUnit) * units.size(), cudaMemcpyHostToDevice)) != cudaSuccess) { rc = cuda_fail(h, e, "upload units"); break; }
+        }
         h->device_bytes = 2 * state + bonds + meas;
         if ((e = cudaMemsetAsync(h->d_spins, 0, state, h->stream)) != cudaSuccess ||
             (e = cudaMemsetAsync(h->d_daemons, 0, state, h->stream)) != cudaSuccess ||
@@ -482,6 +537,27 @@ int micsa_set_launch_config(micsa_t h, int words_per_thread, int block, int bloc
     h->lc.pdl = pdl != 0;
     h->lc.graph_sweeps = graph_sweeps;
     h->blocks_per_sm = blocks_per_sm;
+    return MICSA_OK;
+}
+
+int micsa_set_engine(micsa_t h, int engine, int resident_sweeps) {
+    if (!h) return MICSA_E_INVALID_ARG;
+    if (engine < MICSA_ENGINE_AUTO || engine > MICSA_ENGINE_MULTISPIN || resident_sweeps < 1 || resident_sweeps > 1 << 20)
+        return fail(h, MICSA_E_INVALID_ARG, "bad engine selection");
+    if (engine == MICSA_ENGINE_RESIDENT && resident_smem_bytes(h->geo) == 0)
+        return fail(h, MICSA_E_INVALID_ARG, "an L=%d replica does not fit in shared memory", h->L);
+    if (engine == MICSA_ENGINE_MULTISPIN && multispin_smem_bytes(h->geo) == 0)
+        return fail(h, MICSA_E_INVALID_ARG, "the multispin engine needs L <= 32 (L=%d)", h->L);
+    DeviceGuard dg(h->device);
+    CK(h, cudaStreamSynchronize(h->stream), "synchronize before reconfiguring");
+    h->engine = engine;
+    h->resident_sweeps = resident_sweeps;
+    return MICSA_OK;
+}
+
+int micsa_get_engine(micsa_t h, int *engine) {
+    if (!h || !engine) return MICSA_E_INVALID_ARG;
+    *engine = active_engine(h);
     return MICSA_OK;
 }
 

@@ -43,6 +43,48 @@ struct LaunchConfig {
     int graph_sweeps = 64;  // sweeps per captured CUDA graph (0: no graphs)
 };
 
+// One job of the batched pool (device-resident descriptor).
+struct JobDesc {
+    int32_t resident;      // advanced by the shared-memory resident kernel
+    int8_t *spins;         // [R][2][half]
+    uint8_t *daemons;      // [R][2][half]
+    const uint8_t *bonds;  // [2][half]
+    int8_t *best;          // [R][N] natural layout
+    const uint64_t *thr;   // refresh cut points [n_refresh][3]
+    Geometry geo;
+    int R, nw;
+    uint32_t key0, key1;
+    int64_t t;             // sweeps done
+    int64_t n_sweeps;
+    int32_t interval;
+    int32_t live;
+};
+
+// One lattice (a replica of a sample or of a pool job) that a CTA keeps in
+// shared memory while it runs a block of sweeps.
+struct ResidentUnit {
+    int8_t *spins;         // [2][half] of this replica
+    uint8_t *daemons;      // [2][half]
+    const uint8_t *bonds;  // [2][half] of its sample
+    int32_t gid;           // replica id in the Philox counter
+    int32_t slot;          // pool: job slot (clock, schedule, results); handle: -1
+};
+
+struct ResidentArgs {
+    const ResidentUnit *units;
+    int n_units;
+    const int *n_units_dev;       // pool mode: unit count read on the device (graph replays)
+    Geometry geo;                 // handle mode: the common geometry
+    uint32_t key0, key1;          // handle mode: the common key
+    const SweepParam *params;     // handle mode: sweep table
+    int64_t k0;                   // handle mode: first sweep of this launch in the table
+    int K;                        // sweeps per launch
+    int *counter;                 // pool mode: work counter (reset by the tick's last node)
+    const JobDesc *jobs;          // pool mode: job table
+    long long *results;           // pool mode: energy | aux | best_energy | best_t rows
+    int max_jobs;                 // pool mode: row length of each results array / kPoolMaxR
+};
+
 // word loads/stores of NW consecutive 32-bit words as one 4-, 8- or 16-byte
 // access (the caller guarantees the matching alignment)
 template <int NW>
@@ -88,6 +130,16 @@ __device__ __forceinline__ void store_words(void *p, const uint32_t (&w)[NW]) {
 Geometry make_geometry(int L);
 
 cudaError_t launch_half_sweep(const SweepArgs &a, bool metro, const LaunchConfig &lc, cudaStream_t st);
+
+// shared-memory resident kernel (resident.cu)
+size_t resident_smem_bytes(const Geometry &g);  // 0 when the lattice does not fit
+cudaError_t launch_resident(const ResidentArgs &a, bool pool, size_t smem, int grid, bool pdl, cudaStream_t st);
+int resident_blocks_per_sm(bool pool, size_t smem);
+
+// multispin (bit-plane) resident kernel for L <= 32 (multispin.cu)
+size_t multispin_smem_bytes(const Geometry &g);  // 0 when L > 32
+cudaError_t launch_multispin(const ResidentArgs &a, bool pool, size_t smem, int grid, bool pdl, cudaStream_t st);
+int multispin_blocks_per_sm(bool pool, size_t smem);
 cudaError_t launch_advance_cursor(int64_t *cursor, int64_t step, bool pdl, cudaStream_t st);
 int vector_words(const Geometry &g, int want);
 int max_resident_blocks(bool metro, int nw, int block);

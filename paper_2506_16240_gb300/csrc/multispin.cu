@@ -1,0 +1,450 @@
+// multispin.cu -- shared-memory resident MicSA with multispin coding (the
+// Boolean-only update the paper describes for its CUDA code, App. B and
+// Sec. 2.5), for lattices with L <= 32.
+//
+// A CTA converts one replica from the global byte layout into bit planes in
+// shared memory, runs a block of sweeps there, and converts back. Bit plane
+// words: for parity p, row y and half-row index i, bit z of word (p, y, i)
+// belongs to the site x = 2i + ((p + y + z) & 1), y, z of parity p (the same
+// site the byte layout keeps at row (z, y), byte i). Planes: spin sign (1 = -1),
+// daemon bits m0 and m1, and six bond planes (bit set <=> J = -1) for +x, +y,
+// +z, -x, -y, -z.
+//
+// Neighbours of the 32 sites of word (p, y, i) in the opposite parity:
+//   +-y: word (1-p, y+-1, i)                    (same x offset)
+//   +-z: word (1-p, y, i) rotated by one bit    (same x, periodic in L bits)
+//   +x:  bits with x offset 0 take word (1-p, y, i), offset 1 take (1-p, y, i+1)
+//   -x:  offset 0 take (1-p, y, i-1), offset 1 take (1-p, y, i)
+// The number u of unsatisfied bonds (J s s_nb = -1) is summed bit-sliced; the
+// move of Eq. (Creutz) with Eq. (flip-OK) is accept <=> 3 <= u + m <= 6,
+// m' = u + m - 3 (dH = 12 - 4u), evaluated with Boolean operations only. The
+// daemon refresh draws the same Philox words as every other kernel, so the
+// results are bit-identical to them.
+#include "sweep_body.cuh"
+#include "../../include/micsa.h"
+
+namespace micsa {
+
+constexpr int kMsThreads = 512;  // >= L * L / 2 words of one parity for L <= 32
+constexpr int kMsPoolMaxR = MICSA_POOL_MAX_REPLICAS;
+
+// bit-plane words per parity and plane
+__host__ __device__ __forceinline__ int ms_words(int L) { return L * (L / 2); }
+
+size_t multispin_smem_bytes(const Geometry &g) {
+    if (g.L > 32) return 0;
+    return sizeof(uint32_t) * 9 * 2 * (size_t)ms_words(g.L);
+}
+
+struct MsPlanes {
+    uint32_t *s, *m0, *m1, *b;  // each [2][L][Lh]; b: [6][2][L][Lh]
+    int L, Lh, n;               // n = words per parity
+    __device__ __forceinline__ int idx(int p, int y, int i) const { return (p * L + y) * Lh + i; }
+    __device__ __forceinline__ uint32_t &bond(int k, int p, int y, int i) const { return b[k * 2 * n + idx(p, y, i)]; }
+};
+
+__device__ __forceinline__ uint32_t rot_up(uint32_t v, int L, uint32_t mask) {  // bit z <- bit z-1
+    return L == 32 ? __funnelshift_l(v, v, 1) : (((v << 1) | (v >> (L - 1))) & mask);
+}
+__device__ __forceinline__ uint32_t rot_down(uint32_t v, int L, uint32_t mask) {  // bit z <- bit z+1
+    return L == 32 ? __funnelshift_r(v, v, 1) : (((v >> 1) | (v << (L - 1))) & mask);
+}
+
+// Byte layout (global) -> bit planes. One warp per (parity, y, word q of the
+// row) -- the four sites i = 4q .. 4q+3 -- and one lane per z: a lane loads
+// the byte words of row (z, y) and the warp votes each bit plane together.
+__device__ void ms_pack(const MsPlanes &P, const Geometry &g, const int8_t *spins, const uint8_t *daemons,
+                        const uint8_t *bonds) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int items = 2 * g.L * g.W;
+    for (int it = warp; it < items; it += nwarps) {
+        const int q = it % g.W;
+        const int y = (it / g.W) % g.L;
+        const int p = it / (g.W * g.L);
+        uint32_t S = 0, D = 0, B = 0;
+        if (lane < g.L) {
+            const int64_t off = (int64_t)p * g.half + ((int64_t)lane * g.L + y) * g.P + 4 * q;
+            S = *reinterpret_cast<const uint32_t *>(spins + off);
+            D = *reinterpret_cast<const uint32_t *>(daemons + off);
+            B = *reinterpret_cast<const uint32_t *>(bonds + off);
+        }
+        // lane 9 l + j (j < 9) stores plane j of word i = 4q + l: spin, m0, m1, bonds 0..5
+        uint32_t mine = 0;
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            const uint32_t v[9] = {__ballot_sync(0xFFFFFFFFu, (S >> (8 * l + 7)) & 1u),
+                                   __ballot_sync(0xFFFFFFFFu, (D >> (8 * l)) & 1u),
+                                   __ballot_sync(0xFFFFFFFFu, (D >> (8 * l + 1)) & 1u),
+                                   __ballot_sync(0xFFFFFFFFu, (B >> (8 * l)) & 1u),
+                                   __ballot_sync(0xFFFFFFFFu, (B >> (8 * l + 1)) & 1u),
+                                   __ballot_sync(0xFFFFFFFFu, (B >> (8 * l + 2)) & 1u),
+                                   __ballot_sync(0xFFFFFFFFu, (B >> (8 * l + 3)) & 1u),
+                                   __ballot_sync(0xFFFFFFFFu, (B >> (8 * l + 4)) & 1u),
+                                   __ballot_sync(0xFFFFFFFFu, (B >> (8 * l + 5)) & 1u)};
+#pragma unroll
+            for (int j = 0; j < 9; ++j)
+                if (lane == 9 * l + j || (l == 3 && lane + 32 == 9 * l + j)) mine = v[j];
+            if (l == 2) {  // lanes 0..26 hold words 0..2; store them, then reuse lanes for word 3
+                const int j = lane % 9, li = lane / 9, i = 4 * q + li;
+                if (lane < 27 && i < g.Lh) {
+                    const int w = P.idx(p, y, i);
+                    uint32_t *dst = j == 0 ? &P.s[w] : j == 1 ? &P.m0[w] : j == 2 ? &P.m1[w] : &P.bond(j - 3, p, y, i);
+                    *dst = mine;
+                }
+                mine = 0;
+            }
+        }
+        {
+            // word 3: planes 0..4 went to lanes 27..31, planes 5..8 to lanes 0..3
+            const int j = lane >= 27 ? lane - 27 : lane + 5, i = 4 * q + 3;
+            if ((lane >= 27 || lane < 4) && i < g.Lh) {
+                const int w = P.idx(p, y, i);
+                uint32_t *dst = j == 0 ? &P.s[w] : j == 1 ? &P.m0[w] : j == 2 ? &P.m1[w] : &P.bond(j - 3, p, y, i);
+                *dst = mine;
+            }
+        }
+    }
+}
+
+// Bit planes -> byte layout (spins and daemons; bonds never change). Same
+// warp/lane mapping as ms_pack.
+__device__ void ms_unpack(const MsPlanes &P, const Geometry &g, int8_t *spins, uint8_t *daemons) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int items = 2 * g.L * g.W;
+    for (int it = warp; it < items; it += nwarps) {
+        const int q = it % g.W;
+        const int y = (it / g.W) % g.L;
+        const int p = it / (g.W * g.L);
+        if (lane >= g.L) continue;
+        uint32_t S = 0, D = 0;
+#pragma unroll
+        for (int l = 0; l < 4; ++l) {
+            const int i = 4 * q + l;
+            if (i >= g.Lh) break;
+            const int w = P.idx(p, y, i);
+            S |= (((P.s[w] >> lane) & 1u) ? 0xFFu : 0x01u) << (8 * l);
+            D |= (((P.m0[w] >> lane) & 1u) | (((P.m1[w] >> lane) & 1u) << 1)) << (8 * l);
+        }
+        const uint32_t valid = valid_mask(4 * q, 0, g.Lh);
+        const int64_t off = (int64_t)p * g.half + ((int64_t)lane * g.L + y) * g.P + 4 * q;
+        *reinterpret_cast<uint32_t *>(spins + off) = S & valid;
+        *reinterpret_cast<uint32_t *>(daemons + off) = D & valid;
+    }
+}
+
+// Philox4x32-10 with the ten round keys precomputed (same function as
+// philox4x32_10: round r uses key + r * Weyl increment).
+struct RoundKeys {
+    uint32_t k0[10], k1[10];
+};
+
+__device__ __forceinline__ RoundKeys round_keys(uint32_t key0, uint32_t key1) {
+    RoundKeys r;
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        r.k0[i] = key0 + (uint32_t)i * 0x9E3779B9u;
+        r.k1[i] = key1 + (uint32_t)i * 0xBB67AE85u;
+    }
+    return r;
+}
+
+__device__ __forceinline__ uint4 philox_rk(uint4 c, const RoundKeys &rk) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        c = make_uint4(hi1 ^ c.y ^ rk.k0[r], lo1, hi0 ^ c.w ^ rk.k1[r], lo0);
+    }
+    return c;
+}
+
+// Cut points as 32-bit compares: [u >= c] with c <= 2^32; c == 2^32 never holds.
+struct Cuts {
+    uint32_t c[3];
+    bool ok[3];
+};
+
+__device__ __forceinline__ Cuts make_cuts(uint64_t th0, uint64_t th1, uint64_t th2) {
+    Cuts k;
+    const uint64_t t[3] = {th0, th1, th2};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        k.ok[i] = t[i] <= 0xFFFFFFFFull;
+        k.c[i] = (uint32_t)t[i];
+    }
+    return k;
+}
+
+__device__ __forceinline__ uint32_t daemon_cut(uint32_t u, const Cuts &k) {
+    return (uint32_t)(k.ok[0] & (u >= k.c[0])) + (uint32_t)(k.ok[1] & (u >= k.c[1])) +
+           (uint32_t)(k.ok[2] & (u >= k.c[2]));
+}
+
+// Daemon bit planes of words (p, y, i), i = 4q .. 4q+3, for the refresh at
+// sweep t. Lane z draws the Philox block of site z -- quad = ((p L + z) L + y) W
+// + q, lane i & 3 of the block for word i (the library's counter contract) --
+// and the warp votes the two daemon bit planes of the four words.
+__device__ __forceinline__ void ms_refresh_warp(const MsPlanes &P, const Geometry &g, int p, int y, int q,
+                                                uint32_t gid, const RoundKeys &rk, int64_t t, const Cuts &cut) {
+    const int lane = threadIdx.x & 31;
+    uint32_t m[4] = {0, 0, 0, 0};
+    if (lane < g.L) {
+        const uint32_t quad = (uint32_t)((((int64_t)p * g.L + lane) * g.L + y) * g.W + q);
+        const uint4 w = philox_rk(
+            make_uint4(quad, (uint32_t)t, (gid << 2) | kTagDaemon, (uint32_t)((uint64_t)t >> 32)), rk);
+        m[0] = daemon_cut(w.x, cut);
+        m[1] = daemon_cut(w.y, cut);
+        m[2] = daemon_cut(w.z, cut);
+        m[3] = daemon_cut(w.w, cut);
+    }
+    // planes (m0, m1) of the four words; lane j < 8 stores plane j & 1 of word j >> 1
+    uint32_t mine = 0;
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+        const uint32_t a = __ballot_sync(0xFFFFFFFFu, m[l] & 1u);
+        const uint32_t c = __ballot_sync(0xFFFFFFFFu, m[l] >> 1);
+        if (lane == 2 * l) mine = a;
+        if (lane == 2 * l + 1) mine = c;
+    }
+    const int i = 4 * q + (lane >> 1);
+    if (lane < 8 && i < g.Lh) {
+        const int wi = P.idx(p, y, i);
+        ((lane & 1) ? P.m1 : P.m0)[wi] = mine;
+    }
+}
+
+// Word indices of one thread's site word (y, i) for parity p and its
+// opposite-parity neighbours, computed once per unit (L <= 32 gives at most
+// L * L / 2 <= 512 words per parity, one per thread).
+struct MsItem {
+    int own, oc, oip, oim, oyp, oym;
+    uint32_t M;  // bits whose site has x offset 1
+};
+
+__device__ __forceinline__ MsItem ms_item(const MsPlanes &P, int p, int y, int i, uint32_t mask) {
+    const int L = P.L, Lh = P.Lh, o = 1 - p;
+    const int yp = (y + 1 == L) ? 0 : y + 1, ym = (y == 0) ? L - 1 : y - 1;
+    const int ip = (i + 1 == Lh) ? 0 : i + 1, im = (i == 0) ? Lh - 1 : i - 1;
+    MsItem it;
+    it.own = P.idx(p, y, i);
+    it.oc = P.idx(o, y, i);
+    it.oip = P.idx(o, y, ip);
+    it.oim = P.idx(o, y, im);
+    it.oyp = P.idx(o, yp, i);
+    it.oym = P.idx(o, ym, i);
+    it.M = (((p + y) & 1) ? 0x55555555u : 0xAAAAAAAAu) & mask;
+    return it;
+}
+
+// The elementary move on the 32 sites of one word (Eq. Creutz, Eq. flip-OK).
+__device__ __forceinline__ void ms_update(const MsPlanes &P, const MsItem &it, int L, uint32_t mask) {
+    const uint32_t *bp = P.b + it.own;  // bond plane k of this word at bp[k * 2n]
+    const int stride = 2 * P.n;
+    const uint32_t Oc = P.s[it.oc];
+    const uint32_t nxp = (Oc & ~it.M) | (P.s[it.oip] & it.M);
+    const uint32_t nxm = (P.s[it.oim] & ~it.M) | (Oc & it.M);
+    const uint32_t nzp = rot_down(Oc, L, mask);
+    const uint32_t nzm = rot_up(Oc, L, mask);
+    const uint32_t sg = P.s[it.own];
+    // unsatisfied bond indicators: j ^ s ^ s_nb
+    const uint32_t q0 = sg ^ nxp ^ bp[0];
+    const uint32_t q1 = sg ^ P.s[it.oyp] ^ bp[stride];
+    const uint32_t q2 = sg ^ nzp ^ bp[2 * stride];
+    const uint32_t q3 = sg ^ nxm ^ bp[3 * stride];
+    const uint32_t q4 = sg ^ P.s[it.oym] ^ bp[4 * stride];
+    const uint32_t q5 = sg ^ nzm ^ bp[5 * stride];
+    // u = q0 + ... + q5 (bit-sliced, three planes)
+    const uint32_t s1 = q0 ^ q1 ^ q2, c1 = (q0 & q1) | (q2 & (q0 ^ q1));
+    const uint32_t s2 = q3 ^ q4 ^ q5, c2 = (q3 & q4) | (q5 & (q3 ^ q4));
+    const uint32_t u0 = s1 ^ s2, k = s1 & s2;
+    const uint32_t u1 = c1 ^ c2 ^ k, u2 = (c1 & c2) | (k & (c1 ^ c2));
+    // v = u + m (four planes)
+    const uint32_t m0 = P.m0[it.own], m1 = P.m1[it.own];
+    const uint32_t v0 = u0 ^ m0, k0 = u0 & m0;
+    const uint32_t v1 = u1 ^ m1 ^ k0, k1 = (u1 & m1) | (k0 & (u1 ^ m1));
+    const uint32_t v2 = u2 ^ k1, v3 = u2 & k1;
+    // 3 <= v <= 6  <=>  v3 == 0 and v2 != (v1 & v0); then m' = v - 3
+    const uint32_t acc = (v2 ^ (v1 & v0)) & ~v3 & mask;
+    P.m0[it.own] = (m0 & ~acc) | (~v0 & acc);
+    P.m1[it.own] = (m1 & ~acc) | (v2 & (v1 | v0) & acc);
+    P.s[it.own] = sg ^ acc;
+}
+
+__device__ __forceinline__ void ms_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void ms_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <bool POOL>
+__global__ void __launch_bounds__(kMsThreads, 2) multispin_kernel(ResidentArgs A) {
+    ms_wait();
+    ms_release();
+    extern __shared__ __align__(16) uint32_t msm[];
+    __shared__ int s_unit;
+    __shared__ long long s_red[2][kMsThreads / 32];
+    __shared__ int s_improved;
+
+    const int n_units = A.n_units_dev ? *A.n_units_dev : A.n_units;
+    for (int n_done = 0;; ++n_done) {
+        int u;
+        if (POOL) {
+            if (threadIdx.x == 0) s_unit = atomicAdd(A.counter, 1);
+            __syncthreads();
+            u = s_unit;
+        } else {
+            u = blockIdx.x + n_done * gridDim.x;
+        }
+        if (u >= n_units) break;
+        const ResidentUnit U = A.units[u];
+        Geometry g = A.geo;
+        uint32_t key0 = A.key0, key1 = A.key1;
+        int64_t t0 = 0, n_sweeps = 0;
+        int32_t interval = 1;
+        const uint64_t *thr = nullptr;
+        if (POOL) {
+            const JobDesc &J = A.jobs[U.slot];
+            g = J.geo;
+            key0 = J.key0;
+            key1 = J.key1;
+            t0 = J.t;
+            n_sweeps = J.n_sweeps;
+            interval = J.interval;
+            thr = J.thr;
+            if (t0 >= n_sweeps) {
+                __syncthreads();
+                continue;
+            }
+        }
+        const int n = ms_words(g.L);
+        MsPlanes P{msm, msm + 2 * n, msm + 4 * n, msm + 6 * n, g.L, g.Lh, n};
+        const uint32_t mask = g.L == 32 ? 0xFFFFFFFFu : ((1u << g.L) - 1u);
+        ms_pack(P, g, U.spins, U.daemons, U.bonds);
+        const bool has_item = threadIdx.x < n;  // n <= blockDim for L <= 32
+        const int iy = has_item ? (int)threadIdx.x / g.Lh : 0, ix = has_item ? (int)threadIdx.x - iy * g.Lh : 0;
+        const MsItem item[2] = {ms_item(P, 0, iy, ix, mask), ms_item(P, 1, iy, ix, mask)};
+        const RoundKeys rk = round_keys(key0, key1);
+        __syncthreads();
+
+        int64_t t_end = 0;
+        for (int k = 0; k < A.K; ++k) {
+            int64_t t;
+            bool refresh;
+            uint64_t th0 = 0, th1 = 0, th2 = 0;
+            if (POOL) {
+                t = t0 + k;
+                if (t >= n_sweeps) break;
+                refresh = (t % interval) == 0;
+                if (refresh) {
+                    const uint64_t *q = thr + 3 * (t / interval);
+                    th0 = q[0];
+                    th1 = q[1];
+                    th2 = q[2];
+                }
+            } else {
+                const SweepParam prm = A.params[A.k0 + k];
+                t = prm.t;
+                refresh = prm.mode == kModeRefresh;
+                th0 = prm.th0;
+                th1 = prm.th1;
+                th2 = prm.th2;
+            }
+            for (int p = 0; p < 2; ++p) {
+                if (refresh) {  // fresh daemons of parity p before its half-sweep (Sec. 2.7)
+                    const Cuts cut = make_cuts(th0, th1, th2);
+                    const int items = g.L * g.W;
+                    for (int it = threadIdx.x >> 5; it < items; it += blockDim.x >> 5)
+                        ms_refresh_warp(P, g, p, it / g.W, it % g.W, (uint32_t)U.gid, rk, t, cut);
+                    __syncthreads();
+                }
+                if (has_item) ms_update(P, item[p], g.L, mask);
+                __syncthreads();
+            }
+            t_end = t + 1;
+        }
+        ms_unpack(P, g, U.spins, U.daemons);
+
+        if (POOL) {
+            // exact energy (even sites: 2u - 6 each) and daemon energy from the planes
+            long long e = 0, a = 0;
+            for (int it = threadIdx.x; it < n; it += blockDim.x) {
+                const int y = it / g.Lh, i = it - y * g.Lh;
+                const int yp = (y + 1 == g.L) ? 0 : y + 1, ym = (y == 0) ? g.L - 1 : y - 1;
+                const int ip = (i + 1 == g.Lh) ? 0 : i + 1, im = (i == 0) ? g.Lh - 1 : i - 1;
+                const uint32_t Oc = P.s[P.idx(1, y, i)];
+                const uint32_t M = ((y & 1) ? 0x55555555u : 0xAAAAAAAAu) & mask;
+                const uint32_t nb[6] = {(Oc & ~M) | (P.s[P.idx(1, y, ip)] & M), P.s[P.idx(1, yp, i)],
+                                        rot_down(Oc, g.L, mask), (P.s[P.idx(1, y, im)] & ~M) | (Oc & M),
+                                        P.s[P.idx(1, ym, i)], rot_up(Oc, g.L, mask)};
+                const uint32_t sg = P.s[P.idx(0, y, i)];
+                int usum = 0;
+#pragma unroll
+                for (int kk = 0; kk < 6; ++kk) usum += __popc((sg ^ nb[kk] ^ P.bond(kk, 0, y, i)) & mask);
+                e += 2 * usum - 6 * g.L;
+                a += 4 * (__popc(P.m0[P.idx(0, y, i)]) + 2 * __popc(P.m1[P.idx(0, y, i)]) +
+                          __popc(P.m0[P.idx(1, y, i)]) + 2 * __popc(P.m1[P.idx(1, y, i)]));
+            }
+            e = __reduce_add_sync(0xFFFFFFFFu, (int)e);
+            a = __reduce_add_sync(0xFFFFFFFFu, (int)a);
+            if ((threadIdx.x & 31) == 0) {
+                s_red[0][threadIdx.x >> 5] = e;
+                s_red[1][threadIdx.x >> 5] = a;
+            }
+            __syncthreads();
+            const int cell = U.slot * kMsPoolMaxR + U.gid;
+            const int64_t rows = (int64_t)A.max_jobs * kMsPoolMaxR;
+            if (threadIdx.x == 0) {
+                long long es = 0, as = 0;
+                for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+                    es += s_red[0][i];
+                    as += s_red[1][i];
+                }
+                A.results[cell] = es;
+                A.results[rows + cell] = as;
+                s_improved = es < A.results[2 * rows + cell];
+                if (s_improved) {
+                    A.results[2 * rows + cell] = es;
+                    A.results[3 * rows + cell] = t_end;
+                }
+            }
+            __syncthreads();
+            if (s_improved) {
+                const JobDesc &J = A.jobs[U.slot];
+                const int64_t N = (int64_t)g.L * g.L * g.L;
+                int8_t *best = J.best + (int64_t)U.gid * N;
+                for (int64_t site = threadIdx.x; site < N; site += blockDim.x) {
+                    const int x = (int)(site % g.L), y = (int)((site / g.L) % g.L), z = (int)(site / ((int64_t)g.L * g.L));
+                    const int par = (x + y + z) & 1;
+                    best[site] = ((P.s[P.idx(par, y, x >> 1)] >> z) & 1u) ? (int8_t)-1 : (int8_t)1;
+                }
+            }
+        }
+        __syncthreads();  // the planes are reused by the next unit
+    }
+}
+
+cudaError_t launch_multispin(const ResidentArgs &a, bool pool, size_t smem, int grid, bool pdl, cudaStream_t st) {
+    const void *fn = pool ? (const void *)multispin_kernel<true> : (const void *)multispin_kernel<false>;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3(kMsThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    ResidentArgs args = a;
+    void *kargs[] = {&args};
+    return cudaLaunchKernelExC(&cfg, fn, kargs);
+}
+
+int multispin_blocks_per_sm(bool pool, size_t smem) {
+    const void *fn = pool ? (const void *)multispin_kernel<true> : (const void *)multispin_kernel<false>;
+    if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kMsThreads, smem) != cudaSuccess) return 0;
+    return n;
+}
+
+}  // namespace micsa

@@ -29,20 +29,7 @@ namespace micsa {
 constexpr int kPoolMaxR = MICSA_POOL_MAX_REPLICAS;
 constexpr int kVBlock = 128;  // chunk items per virtual block
 
-struct JobDesc {
-    int8_t *spins;         // [R][2][half]
-    uint8_t *daemons;      // [R][2][half]
-    const uint8_t *bonds;  // [2][half]
-    int8_t *best;          // [R][N] natural layout
-    const uint64_t *thr;   // refresh cut points [n_refresh][3]
-    Geometry geo;
-    int R, nw;
-    uint32_t key0, key1;
-    int64_t t;             // sweeps done
-    int64_t n_sweeps;
-    int32_t interval;
-    int32_t live;
-};
+
 
 struct VBlock {
     int32_t slot;
@@ -109,7 +96,7 @@ __global__ void __launch_bounds__(256) pool_measure_kernel(PoolTables T, int K) 
     pool_release();
     const int slot = blockIdx.x, r = blockIdx.y;
     const JobDesc &J = T.jobs[slot];
-    if (!J.live || r >= J.R || J.t >= J.n_sweeps) return;
+    if (!J.live || J.resident || r >= J.R || J.t >= J.n_sweeps) return;
     const Geometry g = J.geo;
     const int8_t *even = J.spins + (int64_t)r * 2 * g.half;
     const int8_t *odd = even + g.half;
@@ -186,9 +173,10 @@ __global__ void __launch_bounds__(256) pool_measure_kernel(PoolTables T, int K) 
 }
 
 // t <- min(t + K, n_sweeps) for every live job (the last node of a tick).
-__global__ void pool_advance_kernel(JobDesc *jobs, int max_jobs, int K) {
+__global__ void pool_advance_kernel(JobDesc *jobs, int max_jobs, int K, int *counter) {
     pool_wait();
     pool_release();
+    if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;  // work counter of the next tick's resident launch
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max_jobs; i += gridDim.x * blockDim.x) {
         JobDesc &J = jobs[i];
         if (!J.live) continue;
@@ -243,7 +231,6 @@ struct micsa_pool {
     int64_t launches = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t capture_stream = nullptr;
-    cudaGraphExec_t graph = nullptr;
     bool tables_dirty = true;
     cudaEvent_t tables_free = nullptr;  // the last table upload has been consumed
     // per slot: pinned staging of the job's initial data (cut points + result
@@ -254,6 +241,15 @@ struct micsa_pool {
     int grid_blocks = 0;
     bool pdl = true;
     int use_graph = 1;
+    // resident (shared-memory) part: jobs whose replica fits kResidentBudget
+    size_t resident_smem = 0;  // 0: resident kernel disabled
+    int resident_grid = 0;
+    ResidentUnit *d_units = nullptr, *h_units = nullptr;  // h_units: pinned upload source
+    int32_t *d_nunits = nullptr, *h_nunits = nullptr;
+    int *d_counter = nullptr;
+    int max_units = 0;
+    bool has_stream_jobs = false, has_resident_jobs = false;
+    cudaGraphExec_t graphs[4] = {nullptr, nullptr, nullptr, nullptr};  // by part mask
     std::string err;
 };
 
@@ -351,8 +347,8 @@ JobSizes job_sizes(const micsa_job_desc &d) {
 int upload_tables(micsa_pool_t p) {
     if (!p->tables_dirty) return MICSA_OK;
     PCK(p, cudaEventSynchronize(p->tables_free), "wait for table upload");
-    int nvb = 0;
-    // big jobs first, so that the grid-stride loop starts on the long work items
+    int nvb = 0, nunits = 0;
+    // big jobs first, so that the grid-stride loop and the work counter start on the long items
     std::vector<int> order;
     for (int i = 0; i < p->max_jobs; ++i)
         if (p->slots[i].live) order.push_back(i);
@@ -361,6 +357,14 @@ int upload_tables(micsa_pool_t p) {
     });
     for (int i : order) {
         const JobDesc &J = p->h_jobs[i];
+        if (J.resident) {
+            for (int r = 0; r < J.R; ++r) {
+                if (nunits >= p->max_units) return pfail(p, MICSA_E_BUSY, "resident unit table full");
+                p->h_units[nunits++] = ResidentUnit{J.spins + (int64_t)r * 2 * J.geo.half,
+                                                    J.daemons + (int64_t)r * 2 * J.geo.half, J.bonds, r, i};
+            }
+            continue;
+        }
         const int64_t items = (int64_t)J.R * J.geo.L * J.geo.L * (J.geo.W / J.nw);
         for (int64_t c = 0; c < items; c += kVBlock) {
             if (nvb >= p->max_vblocks) return pfail(p, MICSA_E_BUSY, "virtual block table full");
@@ -368,36 +372,65 @@ int upload_tables(micsa_pool_t p) {
         }
     }
     *p->h_nvb = nvb;
+    *p->h_nunits = nunits;
+    p->has_stream_jobs = nvb > 0;
+    p->has_resident_jobs = nunits > 0;
     std::memcpy(p->h_jobs_stage, p->h_jobs.data(), sizeof(JobDesc) * p->max_jobs);
     PCK(p, cudaMemcpyAsync(p->d_jobs, p->h_jobs_stage, sizeof(JobDesc) * p->max_jobs, cudaMemcpyHostToDevice, p->stream), "upload jobs");
     PCK(p, cudaMemcpyAsync(p->d_vblocks, p->h_vblocks, sizeof(VBlock) * (size_t)(nvb ? nvb : 1), cudaMemcpyHostToDevice, p->stream), "upload vblocks");
     PCK(p, cudaMemcpyAsync(p->d_nvb, p->h_nvb, sizeof(int32_t), cudaMemcpyHostToDevice, p->stream), "upload vblock count");
+    if (p->max_units) {
+        PCK(p, cudaMemcpyAsync(p->d_units, p->h_units, sizeof(ResidentUnit) * (size_t)(nunits ? nunits : 1), cudaMemcpyHostToDevice, p->stream), "upload units");
+        PCK(p, cudaMemcpyAsync(p->d_nunits, p->h_nunits, sizeof(int32_t), cudaMemcpyHostToDevice, p->stream), "upload unit count");
+    }
     PCK(p, cudaEventRecord(p->tables_free, p->stream), "record table event");
     p->tables_dirty = false;
     return MICSA_OK;
 }
 
-int enqueue_tick(micsa_pool_t p, cudaStream_t st) {
-    PoolTables T{p->d_jobs, p->d_vblocks, p->d_nvb, p->d_results, p->d_results + (size_t)p->max_jobs * kPoolMaxR,
-                 p->d_results + 2 * (size_t)p->max_jobs * kPoolMaxR, p->d_results + 3 * (size_t)p->max_jobs * kPoolMaxR};
-    for (int k = 0; k < p->K; ++k)
-        for (int par = 0; par < 2; ++par) {
-            void *args[] = {&T, &k, &par};
-            PCK(p, launch_pdl((const void *)pool_half_sweep_kernel, dim3(p->grid_blocks), dim3(kVBlock), st, args, p->pdl), "pool half-sweep launch");
-        }
-    int K = p->K;
-    void *margs[] = {&T, &K};
-    PCK(p, launch_pdl((const void *)pool_measure_kernel, dim3(p->max_jobs, kPoolMaxR), dim3(256), st, margs, p->pdl), "pool measure launch");
-    int mj = p->max_jobs;
-    void *aargs[] = {&p->d_jobs, &mj, &K};
+// One tick: the resident kernel (mask bit 0) runs K sweeps of every job that
+// lives in shared memory and measures it; the streaming half-sweeps (bit 1)
+// run K sweeps of the other jobs, which the measure kernel then measures; the
+// advance kernel moves every job's clock.
+int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
+    long long *R0 = p->d_results;
+    const size_t rows = (size_t)p->max_jobs * kPoolMaxR;
+    PoolTables T{p->d_jobs, p->d_vblocks, p->d_nvb, R0, R0 + rows, R0 + 2 * rows, R0 + 3 * rows};
+    if ((mask & 1) && p->resident_smem) {
+        ResidentArgs ra{};
+        ra.units = p->d_units;
+        ra.n_units_dev = p->d_nunits;
+        ra.K = p->K;
+        ra.counter = p->d_counter;
+        ra.jobs = p->d_jobs;
+        ra.results = p->d_results;
+        ra.max_jobs = p->max_jobs;
+        PCK(p, launch_multispin(ra, true, p->resident_smem, p->resident_grid, p->pdl, st), "pool multispin launch");
+    }
+    if (mask & 2) {
+        for (int k = 0; k < p->K; ++k)
+            for (int par = 0; par < 2; ++par) {
+                void *args[] = {&T, &k, &par};
+                PCK(p, launch_pdl((const void *)pool_half_sweep_kernel, dim3(p->grid_blocks), dim3(kVBlock), st, args, p->pdl), "pool half-sweep launch");
+            }
+        int K = p->K;
+        void *margs[] = {&T, &K};
+        PCK(p, launch_pdl((const void *)pool_measure_kernel, dim3(p->max_jobs, kPoolMaxR), dim3(256), st, margs, p->pdl), "pool measure launch");
+    }
+    int K = p->K, mj = p->max_jobs;
+    void *aargs[] = {&p->d_jobs, &mj, &K, &p->d_counter};
     PCK(p, launch_pdl((const void *)pool_advance_kernel, dim3((p->max_jobs + 255) / 256), dim3(256), st, aargs, p->pdl), "pool advance launch");
     return MICSA_OK;
 }
 
-int ensure_graph(micsa_pool_t p) {
-    if (p->graph || !p->use_graph) return MICSA_OK;
+int tick_launches(micsa_pool_t p, int mask) {
+    return ((mask & 1) && p->resident_smem ? 1 : 0) + ((mask & 2) ? 2 * p->K + 1 : 0) + 1;
+}
+
+int ensure_graph(micsa_pool_t p, int mask) {
+    if (p->graphs[mask] || !p->use_graph) return MICSA_OK;
     PCK(p, cudaStreamBeginCapture(p->capture_stream, cudaStreamCaptureModeThreadLocal), "pool begin capture");
-    const int rc = enqueue_tick(p, p->capture_stream);
+    const int rc = enqueue_tick(p, p->capture_stream, mask);
     cudaGraph_t g = nullptr;
     const cudaError_t e = cudaStreamEndCapture(p->capture_stream, &g);
     if (rc != MICSA_OK) {
@@ -405,10 +438,17 @@ int ensure_graph(micsa_pool_t p) {
         return rc;
     }
     PCK(p, e, "pool end capture");
-    const cudaError_t e2 = cudaGraphInstantiate(&p->graph, g, 0);
+    const cudaError_t e2 = cudaGraphInstantiate(&p->graphs[mask], g, 0);
     cudaGraphDestroy(g);
     PCK(p, e2, "pool graph instantiate");
     return MICSA_OK;
+}
+
+void drop_pool_graphs(micsa_pool_t p) {
+    for (auto &g : p->graphs) {
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
+    }
 }
 
 void release_slot(micsa_pool_t p, int i) {
@@ -462,6 +502,20 @@ int micsa_pool_create(size_t arena_bytes, int max_jobs, int tick_sweeps, micsa_p
         if (rc) break;
         if ((e = cudaMemsetAsync(p->d_jobs, 0, sizeof(JobDesc) * max_jobs, p->stream)) != cudaSuccess ||
             (e = cudaMemsetAsync(p->d_nvb, 0, sizeof(int32_t), p->stream)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+        // jobs of L <= 32 live in shared memory as bit planes (multispin kernel)
+        p->resident_smem = multispin_smem_bytes(make_geometry(32));
+        const int res_per_sm = multispin_blocks_per_sm(true, p->resident_smem);
+        if (res_per_sm <= 0) p->resident_smem = 0;
+        p->resident_grid = (res_per_sm > 0 ? res_per_sm : 1) * p->sm_count;
+        p->max_units = max_jobs * kPoolMaxR;
+        if ((e = cudaMalloc(&p->d_units, sizeof(ResidentUnit) * (size_t)p->max_units)) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_nunits, sizeof(int32_t))) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_counter, sizeof(int))) != cudaSuccess ||
+            (e = cudaMallocHost(&p->h_units, sizeof(ResidentUnit) * (size_t)p->max_units)) != cudaSuccess ||
+            (e = cudaMallocHost(&p->h_nunits, sizeof(int32_t))) != cudaSuccess) { bail(MICSA_E_OOM); break; }
+        *p->h_nunits = 0;
+        if ((e = cudaMemsetAsync(p->d_nunits, 0, sizeof(int32_t), p->stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(p->d_counter, 0, sizeof(int), p->stream)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pool_half_sweep_kernel, kVBlock, 0);
         p->grid_blocks = (per_sm > 0 ? per_sm : 4) * p->sm_count;
@@ -483,7 +537,7 @@ int micsa_pool_create(size_t arena_bytes, int max_jobs, int tick_sweeps, micsa_p
 void micsa_pool_destroy(micsa_pool_t p) {
     if (!p) return;
     if (p->stream) cudaStreamSynchronize(p->stream);
-    if (p->graph) cudaGraphExecDestroy(p->graph);
+    drop_pool_graphs(p);
     for (auto ev : p->tick_events)
         if (ev) cudaEventDestroy(ev);
     for (auto *b : p->stage) cudaFreeHost(b);
@@ -496,6 +550,11 @@ void micsa_pool_destroy(micsa_pool_t p) {
     cudaFree(p->d_nvb);
     cudaFree(p->d_results);
     cudaFreeHost(p->h_jobs_stage);
+    cudaFree(p->d_units);
+    cudaFree(p->d_nunits);
+    cudaFree(p->d_counter);
+    cudaFreeHost(p->h_units);
+    cudaFreeHost(p->h_nunits);
     cudaFreeHost(p->h_vblocks);
     cudaFreeHost(p->h_nvb);
     if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
@@ -589,6 +648,7 @@ int micsa_pool_submit(micsa_pool_t p, const micsa_job_desc *job, int64_t *job_id
     D.n_sweeps = d.n_sweeps;
     D.interval = d.refresh_interval;
     D.live = 1;
+    D.resident = (p->resident_smem && multispin_smem_bytes(s.g) && multispin_smem_bytes(s.g) <= p->resident_smem) ? 1 : 0;
     p->tables_dirty = true;
     *job_id = J.id;
     return MICSA_OK;
@@ -597,13 +657,14 @@ int micsa_pool_submit(micsa_pool_t p, const micsa_job_desc *job, int64_t *job_id
 int micsa_pool_tick(micsa_pool_t p) {
     if (!p) return MICSA_E_INVALID_ARG;
     if (int rc = upload_tables(p)) return rc;
-    if (int rc = ensure_graph(p)) return rc;
-    if (p->graph) {
-        PCK(p, cudaGraphLaunch(p->graph, p->stream), "pool graph launch");
+    const int mask = (p->has_resident_jobs ? 1 : 0) | (p->has_stream_jobs ? 2 : 0);
+    if (int rc = ensure_graph(p, mask)) return rc;
+    if (p->graphs[mask]) {
+        PCK(p, cudaGraphLaunch(p->graphs[mask], p->stream), "pool graph launch");
     } else {
-        if (int rc = enqueue_tick(p, p->stream)) return rc;
+        if (int rc = enqueue_tick(p, p->stream, mask)) return rc;
     }
-    p->launches += 2 * (int64_t)p->K + 2;
+    p->launches += tick_launches(p, mask);
     const int64_t tick = p->ticks_queued++;
     cudaEvent_t ev = p->tick_events[tick % p->tick_events.size()];
     if (tick >= (int64_t)p->tick_events.size())
@@ -693,8 +754,7 @@ int micsa_pool_stats(micsa_pool_t p, int *live_jobs, size_t *free_bytes, int64_t
 int micsa_pool_set_launch_config(micsa_pool_t p, int blocks_per_sm, int pdl, int use_graph) {
     if (!p || blocks_per_sm < 1 || blocks_per_sm > 64) return MICSA_E_INVALID_ARG;
     PCK(p, cudaStreamSynchronize(p->stream), "synchronize before reconfiguring");
-    if (p->graph) cudaGraphExecDestroy(p->graph);
-    p->graph = nullptr;
+    drop_pool_graphs(p);
     p->grid_blocks = blocks_per_sm * p->sm_count;
     p->pdl = pdl != 0;
     p->use_graph = use_graph != 0;

@@ -11,7 +11,20 @@ namespace micsa {
 // sample's [2][half] block. gid is the replica's global id in the Philox
 // counter, t the global sweep index. refresh: draw the daemon words instead of
 // reading them (Sec. 2.7); METRO: Metropolis acceptance with the cut points th*.
-template <int NW, bool METRO>
+// Read-only word loads from global (through the read-only path) or shared memory.
+template <int NW, bool SMEM>
+__device__ __forceinline__ void load_ro(const void *p, uint32_t (&w)[NW]) {
+    if constexpr (SMEM) load_words<NW>(p, w);
+    else load_words_ro<NW>(p, w);
+}
+
+template <bool SMEM>
+__device__ __forceinline__ uint32_t load_byte(const int8_t *p) {
+    if constexpr (SMEM) return (uint8_t)*p;
+    else return (uint8_t)__ldg(p);
+}
+
+template <int NW, bool METRO, bool SMEM = false>
 __device__ __forceinline__ void update_chunk(const Geometry &g, int8_t *spins, uint8_t *daemons,
                                              const uint8_t *bonds, int p, int row, int c,
                                              uint32_t gid, uint32_t key0, uint32_t key1, int64_t t,
@@ -29,23 +42,23 @@ __device__ __forceinline__ void update_chunk(const Geometry &g, int8_t *spins, u
     uint8_t *__restrict__ own_d = daemons + (int64_t)p * g.half;
 
     uint32_t Bw[NW], O[NW], Oyp[NW], Oym[NW], Ozp[NW], Ozm[NW], S[NW], D[NW];
-    load_words_ro<NW>(bonds + (int64_t)p * g.half + off_c, Bw);
-    load_words_ro<NW>(opp + off_c, O);
-    load_words_ro<NW>(opp + ((int64_t)z * g.L + yp) * g.P + b0, Oyp);
-    load_words_ro<NW>(opp + ((int64_t)z * g.L + ym) * g.P + b0, Oym);
-    load_words_ro<NW>(opp + ((int64_t)zp * g.L + y) * g.P + b0, Ozp);
-    load_words_ro<NW>(opp + ((int64_t)zm * g.L + y) * g.P + b0, Ozm);
+    load_ro<NW, SMEM>(bonds + (int64_t)p * g.half + off_c, Bw);
+    load_ro<NW, SMEM>(opp + off_c, O);
+    load_ro<NW, SMEM>(opp + ((int64_t)z * g.L + yp) * g.P + b0, Oyp);
+    load_ro<NW, SMEM>(opp + ((int64_t)z * g.L + ym) * g.P + b0, Oym);
+    load_ro<NW, SMEM>(opp + ((int64_t)zp * g.L + y) * g.P + b0, Ozp);
+    load_ro<NW, SMEM>(opp + ((int64_t)zm * g.L + y) * g.P + b0, Ozm);
     load_words<NW>(own_s + off_c, S);
     if (!METRO && !refresh) load_words<NW>(own_d + off_c, D);
 
     // edge bytes for the x shift and the periodic wrap of the row
     uint32_t edge = 0, first = 0, last = 0;
     if (o == 0) {
-        if (b0 == 0) last = (uint8_t)__ldg(opp + row0 + g.Lh - 1);
-        else edge = (uint8_t)__ldg(opp + off_c - 1);
+        if (b0 == 0) last = load_byte<SMEM>(opp + row0 + g.Lh - 1);
+        else edge = load_byte<SMEM>(opp + off_c - 1);
     } else {
-        if (b0 + 4 * NW <= g.Lh - 1) edge = (uint8_t)__ldg(opp + off_c + 4 * NW);
-        else first = (b0 == 0) ? (O[0] & 0xFFu) : (uint8_t)__ldg(opp + row0);
+        if (b0 + 4 * NW <= g.Lh - 1) edge = load_byte<SMEM>(opp + off_c + 4 * NW);
+        else first = (b0 == 0) ? (O[0] & 0xFFu) : load_byte<SMEM>(opp + row0);
     }
     uint32_t xp[NW], xm[NW];
     x_neighbours<NW>(O, o, b0, g.Lh, edge, first, last, xp, xm);
@@ -92,6 +105,44 @@ __device__ __forceinline__ void update_chunk(const Geometry &g, int8_t *spins, u
     }
     store_words<NW>(own_s + off_c, S);
     if (!METRO) store_words<NW>(own_d + off_c, D);
+}
+
+// Sum over the valid lanes of word w of an even row of (2u - 6): the energy of
+// the bonds of those even sites (each bond has exactly one even end for even
+// L, so the sum over all even words is H_EA). `even`/`odd` point at the two
+// parity halves of one replica, `bonds` at the even bond half.
+template <bool SMEM>
+__device__ __forceinline__ int even_word_energy(const Geometry &g, const int8_t *even, const int8_t *odd,
+                                                const uint8_t *bonds, int64_t w) {
+    const int row = (int)(w / g.W);
+    const int b0 = (int)(w - (int64_t)row * g.W) * 4;
+    const int y = row % g.L, z = row / g.L;
+    const int o = (y + z) & 1;
+    const int yp = (y + 1 == g.L) ? 0 : y + 1, ym = (y == 0) ? g.L - 1 : y - 1;
+    const int zp = (z + 1 == g.L) ? 0 : z + 1, zm = (z == 0) ? g.L - 1 : z - 1;
+    const int64_t row0 = (int64_t)row * g.P, off = row0 + b0;
+    const uint32_t valid = valid_mask(b0, 0, g.Lh);
+    uint32_t O[1], Oyp[1], Oym[1], Ozp[1], Ozm[1], B[1], S[1];
+    load_ro<1, SMEM>(odd + off, O);
+    load_ro<1, SMEM>(odd + ((int64_t)z * g.L + yp) * g.P + b0, Oyp);
+    load_ro<1, SMEM>(odd + ((int64_t)z * g.L + ym) * g.P + b0, Oym);
+    load_ro<1, SMEM>(odd + ((int64_t)zp * g.L + y) * g.P + b0, Ozp);
+    load_ro<1, SMEM>(odd + ((int64_t)zm * g.L + y) * g.P + b0, Ozm);
+    load_ro<1, SMEM>(bonds + off, B);
+    load_ro<1, SMEM>(even + off, S);
+    uint32_t edge = 0, first = 0, last = 0;
+    if (o == 0) {
+        if (b0 == 0) last = load_byte<SMEM>(odd + row0 + g.Lh - 1);
+        else edge = load_byte<SMEM>(odd + off - 1);
+    } else {
+        if (b0 + 4 <= g.Lh - 1) edge = load_byte<SMEM>(odd + off + 4);
+        else first = (b0 == 0) ? (O[0] & 0xFFu) : load_byte<SMEM>(odd + row0);
+    }
+    uint32_t xp[1], xm[1];
+    x_neighbours<1>(O, o, b0, g.Lh, edge, first, last, xp, xm);
+    const uint32_t u32 =
+        unsatisfied32(negative_terms(bond_planes(B[0]), xp[0], xm[0], Oyp[0], Oym[0], Ozp[0], Ozm[0]), S[0]) & valid;
+    return 2 * (int)(((u32 >> 5) * 0x01010101u) >> 24) - 6 * (__popc(valid) / 8);
 }
 
 }  // namespace micsa

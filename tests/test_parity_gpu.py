@@ -177,6 +177,35 @@ def test_invalid_arguments_fail_cleanly():
         assert t == 0  # rejected calls change nothing
 
 
+@pytest.mark.parametrize("L,S,R", [(2, 2, 2), (4, 1, 3), (8, 3, 1), (18, 2, 3), (24, 1, 2), (30, 1, 2),
+                                   (32, 4, 2), (40, 1, 1)])
+def test_resident_engine_matches_streaming_and_oracle(L, S, R):
+    """The shared-memory resident kernel and the streaming kernel give the same
+    bits; blocks of resident sweeps of any length compose."""
+    sched = np.linspace(2.6, 0.5, 90)
+    out = []
+    engines = [("stream", 64), ("resident", 64), ("resident", 7), ("resident", 1)]
+    if L <= 32:
+        engines += [("multispin", 64), ("multispin", 5), ("multispin", 1)]
+    for engine, blk in engines:
+        with micsa.Micsa(L, S, R, 99 + L) as g:
+            g.set_engine(engine, blk)
+            assert g.engine() == engine
+            g.run(sched[:40], 6)
+            g.run_logrefresh(sched[40:70])
+            g.run(sched[70:], 3)
+            out.append(g.get_state())
+    for s, m, t in out[1:]:
+        np.testing.assert_array_equal(s, out[0][0])
+        np.testing.assert_array_equal(m, out[0][1])
+    st = O.create(L, S, R, 99 + L)
+    O.run(st, sched[:40], 6)
+    O.run_logrefresh(st, sched[40:70])
+    O.run(st, sched[70:], 3)
+    np.testing.assert_array_equal(out[0][0], st["s"])
+    np.testing.assert_array_equal(out[0][1], st["m"])
+
+
 @pytest.mark.parametrize("L", [16, 18, 32, 160])
 def test_launch_configs_agree(L):
     """Every launch shape (vector width, block, grid-stride cap, PDL, graph

@@ -48,6 +48,7 @@ JOBS = [  # (L, R, seed, n_sweeps, interval, T_start, T_end)
     (8, 1, 11, 100, 10, 3.0, 0.5), (16, 2, 12, 77, 5, 2.5, 0.5), (10, 3, 13, 40, 7, 2.0, 1.0),
     (32, 2, 14, 50, 20, 2.5, 0.5), (6, 4, 15, 33, 1, 3.0, 0.3), (18, 1, 16, 64, 9, 2.5, 0.4),
     (24, 2, 17, 16, 16, 1.5, 1.5), (30, 1, 18, 5, 3, 2.0, 0.7),
+    (34, 2, 19, 30, 6, 2.0, 0.6), (40, 1, 20, 21, 4, 2.0, 1.0),  # too big for the resident kernel
 ]
 
 
@@ -68,7 +69,7 @@ def test_pool_result_independent_of_slot_and_neighbours():
     np.testing.assert_array_equal(alone["best_spins"], mixed["best_spins"])
 
 
-@pytest.mark.parametrize("job", [JOBS[0], JOBS[2], JOBS[5]])
+@pytest.mark.parametrize("job", [JOBS[0], JOBS[2], JOBS[5], JOBS[8]])
 def test_pool_best_configuration_matches_oracle(job):
     L, R, seed, n, interval, T0, T1 = job
     K = 16
