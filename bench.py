@@ -1,23 +1,33 @@
 #!/usr/bin/env python
 """Benchmark of the MicSA hot path on GB300 (one JSON line on rank 0).
 
-Workload (one "step"): the single-lattice quench -- a 3D EA +-J lattice with
-L = 160 (4,096,000 spins), 1 disorder sample x 2 replicas, couplings and a
-random start drawn on the device from the step's seed, quenched to T = 0.7 for
-10^5 MicSA sweeps with a daemon refresh every 10 sweeps, then the exact energy
-and overlap are measured. Metric: spin-flip attempts per ns
-(N x replicas x samples x sweeps / device time of the step).
+Headline workload (one "step"): the single-lattice quench -- a 3D EA +-J
+lattice with L = 160 (4,096,000 spins), 1 disorder sample x 2 replicas,
+couplings and a random start drawn on the device from the step's seed,
+quenched to T = 0.7 for 10^5 MicSA sweeps with a daemon refresh every 10
+sweeps. Metric: spin-flip attempts per ns (N x replicas x samples x sweeps /
+device time). The exact energy and overlap are measured after every step.
 
-Legs reported on the same JSON line:
-  value       device time of the step (CUDA events on the launching stream),
-              state resident in HBM, L2 flushed between steps
-  e2e         the same job through the C ABI from pinned host buffers:
-              couplings and initial spins copied in, final spins, daemons and
-              observables copied out, all inside the timed region
-  roofline    the plain half-sweep kernel: algorithmic bytes per launch over
-              its average duration in a timed run of plain sweeps
-  metropolis  the random-number-per-update Metropolis kernel on the same
-              lattice (same layout), spin-flips/ns
+Legs on the same JSON line:
+  value        device time of the step (CUDA events on the launching stream),
+               state resident in HBM, L2 flushed (512 MB write) between steps
+  e2e          the same job through the C ABI from pinned host buffers:
+               couplings and initial spins copied in, final spins, daemons and
+               observables copied out, all inside the timed region
+  roofline     the plain streaming half-sweep kernel at L = 160: algorithmic
+               bytes per launch over its mean duration in a timed run of
+               sweeps without refresh (CUDA events, launching stream)
+  dram_point   the same kernel at L = 320 (164 MB of state, larger than L2)
+  metropolis   the random-number-per-update Metropolis kernel, same lattice
+  quench_l32   L = 32, 64 samples x 2 replicas, T = 0.7, 10^4 sweeps, refresh
+               every 10, e and q^2 measured on a log time grid (multispin
+               shared-memory engine)
+  batched      256 lattices, L in {16,24,32,48,64}, 2 replicas, anneal 2.5 -> 0.5
+               over 2x10^4 sweeps, refresh 5..20: one pool (all jobs in each
+               launch) against the per-lattice launch loop
+  serving      Poisson stream of annealing jobs (L 16..96, 10^3..10^5 sweeps,
+               1..4 replicas, anneal 3.0 -> 0.3) through the continuous-batching
+               pool: p50/p99 latency and aggregate spin-flips/ns
   cpu_baseline the CPU oracle (single thread) on a bounded sample of sweeps
 
 --impl reference times the oracle itself (the deliberately slow reference).
@@ -26,7 +36,6 @@ data-path collective); the barrier and the max over ranks only time the job.
 """
 import argparse
 import json
-import math
 import os
 import subprocess
 import sys
@@ -46,7 +55,7 @@ METRIC = "spin-flips/ns"
 L2_FLUSH_BYTES = 512 << 20
 
 
-def parse():
+def parse(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=3)
@@ -55,19 +64,41 @@ def parse():
     ap.add_argument("--sweeps", type=int, default=WORKLOAD["sweeps"],
                     help="sweeps per step (profiling runs only; reported numbers use the default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    return ap.parse_args()
+    ap.add_argument("--no-extras", action="store_true", help="headline leg only")
+    ap.add_argument("--serving-jobs", type=int, default=300,
+                    help="jobs in the serving stream (the full stream is 2000)")
+    return ap.parse_args(argv)
 
 
 def dist_env():
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return rank, world, local
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def updates_per_step(sweeps):
-    w = WORKLOAD
-    return w["L"] ** 3 * w["samples"] * w["replicas"] * sweeps
+def updates(L, S, R, sweeps):
+    return L ** 3 * S * R * sweeps
+
+
+def rank_seed(rank):
+    """Seed of the lattice a rank runs (weak scaling: independent lattices)."""
+    return 3 + 1000 * rank
+
+
+def gather_ms(torch, x, rank, world, device):
+    """Every rank's timing on every rank (a timing exchange only; no data-path
+    collective exists: ranks run independent lattices)."""
+    if world == 1:
+        return [x]
+    t = torch.zeros(world, dtype=torch.float64, device=device)
+    t[rank] = x
+    torch.distributed.all_reduce(t)
+    return t.tolist()
+
+
+def aggregate(world, per_rank_ms, updates_per_rank):
+    """Whole-job value: all ranks' updates over the slowest rank's time."""
+    total_ms = max(per_rank_ms)
+    return world * updates_per_rank / (total_ms * 1e6), total_ms
 
 
 # ------------------------------------------------------------ clocks --
@@ -78,9 +109,7 @@ class ClockSampler:
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
     def __init__(self, gpu_index):
-        self.gpu = gpu_index
-        self.proc = None
-        self.lines = []
+        self.gpu, self.proc, self.lines = gpu_index, None, []
 
     def start(self):
         try:
@@ -90,7 +119,7 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
-        except (OSError, FileNotFoundError):
+        except OSError:
             self.proc = None
 
     def _read(self):
@@ -106,81 +135,219 @@ class ClockSampler:
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self.thread.join(timeout=2)
-        sm, smax, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
-            parts = [p.strip() for p in ln.split(",")]
-            if len(parts) < 9:
-                continue
-            try:
-                sm.append(float(parts[1]))
-                smax.append(float(parts[2]))
-            except ValueError:
-                continue
-            for nm, v in zip(names, parts[5:9]):
-                if v.lower() == "active":
-                    reasons.add(nm)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm)}
+        return parse_clock_lines(self.lines)
+
+
+def parse_clock_lines(lines):
+    sm, smax, reasons = [], [], set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for ln in lines:
+        parts = [p.strip() for p in ln.split(",")]
+        if len(parts) < 9:
+            continue
+        try:
+            sm.append(float(parts[1]))
+            smax.append(float(parts[2]))
+        except ValueError:
+            continue
+        for nm, v in zip(names, parts[5:9]):
+            if v.lower() == "active":
+                reasons.add(nm)
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+    return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+            "samples": len(sm)}
 
 
 # -------------------------------------------------------- CPU oracle --
 def oracle_sample(sweeps, seed=3):
-    """The oracle on the bench lattice for `sweeps` sweeps; returns (updates, seconds)."""
+    """The oracle on the headline lattice for `sweeps` sweeps: (updates, seconds)."""
     import oracle
     w = WORKLOAD
     O = oracle.Oracle()
     st = O.create(w["L"], w["samples"], w["replicas"], seed)
     t0 = time.perf_counter()
     O.run(st, np.full(sweeps, w["T"]), w["refresh_interval"])
-    dt = time.perf_counter() - t0
-    return updates_per_step(sweeps), dt
+    return updates(w["L"], w["samples"], w["replicas"], sweeps), time.perf_counter() - t0
 
 
 def cpu_baseline(target_s=12.0):
-    upd1, dt1 = oracle_sample(2)
-    n = max(2, int(target_s / max(dt1 / 2, 1e-3)))
-    n = min(n, 200)
+    _, dt2 = oracle_sample(2)
+    n = min(200, max(2, int(target_s / max(dt2 / 2, 1e-3))))
     upd, dt = oracle_sample(n)
     return {"value": upd / (dt * 1e9), "unit": METRIC, "cores": 1, "kind": "oracle",
             "sample": f"{n} sweeps of the L=160 1x2 lattice at T=0.7 (refresh every 10), "
-                      f"single-threaded C oracle, {dt:.1f} s"}
+                      f"single-threaded C oracle, {dt:.1f} s, host {os.uname().machine} "
+                      f"with {os.cpu_count()} cores"}
 
 
 def run_reference(args):
-    rank, world, _ = dist_env()
+    rank, _, _ = dist_env()
     if rank != 0:
         return 0
     w = WORKLOAD
-    sweeps_per_step = 10
+    per_step = 10
     for _ in range(args.warmup):
-        oracle_sample(2)
-    times = []
-    for k in range(args.steps):
-        upd, dt = oracle_sample(sweeps_per_step, seed=100 + k)
-        times.append(dt)
-    total_upd = updates_per_step(sweeps_per_step) * args.steps
-    value = total_upd / (sum(times) * 1e9)
-    out = {
+        oracle_sample(1)
+    times = [oracle_sample(per_step, seed=100 + k)[1] for k in range(args.steps)]
+    value = updates(w["L"], w["samples"], w["replicas"], per_step) * args.steps / (sum(times) * 1e9)
+    print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
-        "data": "synthetic", "config": {"workload": w["name"], "L": w["L"], "samples": w["samples"],
-                                        "replicas": w["replicas"],
-                                        "sample_per_step": f"{sweeps_per_step} sweeps"},
+        "data": "synthetic",
+        "config": {"workload": w["name"], "L": w["L"], "samples": w["samples"], "replicas": w["replicas"],
+                   "sample_per_step": f"{per_step} sweeps of the workload"},
         "cpu_baseline": {"value": value, "unit": METRIC, "cores": 1, "kind": "oracle",
-                         "sample": f"{sweeps_per_step} sweeps per step of the L=160 1x2 lattice"},
+                         "sample": f"{per_step} sweeps per step of the L=160 1x2 lattice, single thread"},
         "e2e": {"value": value, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(out))
+    }))
     return 0
 
 
 # --------------------------------------------------------------- GPU --
-def main():
-    args = parse()
+class Timer:
+    def __init__(self, torch, stream):
+        self.torch, self.stream = torch, stream
+
+    def __call__(self, fn):
+        t = self.torch
+        e0, e1 = t.cuda.Event(enable_timing=True), t.cuda.Event(enable_timing=True)
+        e0.record(self.stream)
+        fn()
+        e1.record(self.stream)
+        t.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+
+def leg_roofline(micsa, timer, stream, L, peaks, n_plain=2000):
+    """Plain streaming half-sweep kernel: algorithmic bytes / mean launch time."""
+    R = 2
+    g = micsa.Micsa(L, 1, R, 7, stream=stream)
+    g.set_engine("stream")
+    g.run(np.full(1, 0.7), 10)  # t = 0 refresh; the timed sweeps below have none
+    g.run(np.full(50, 0.7), 2 ** 31 - 1)
+    ms = timer(lambda: g.run(np.full(n_plain, 0.7), 2 ** 31 - 1))
+    g.close()
+    launch_us = 1e3 * ms / (2 * n_plain)
+    half_sites = L ** 3 // 2
+    bytes_per_launch = half_sites * (5 * R + 1)  # per replica: s, m read + write, opposite s; bonds once
+    hbm = peaks.get("hbm_gbs")
+    peak = hbm if hbm else 6800.0
+    achieved = bytes_per_launch / (launch_us * 1e-6) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "peak_source": "measured" if hbm else "fallback",
+            "kernel": "micsa::half_sweep_kernel<4,false> (streaming MicSA half-sweep, no refresh)",
+            "L": L, "bytes_per_launch": bytes_per_launch, "launch_us": launch_us,
+            "flips_per_ns": updates(L, 1, R, n_plain) / (ms * 1e6)}
+
+
+def leg_metropolis(micsa, timer, stream, n=10_000):
+    w = WORKLOAD
+    g = micsa.Micsa(w["L"], 1, w["replicas"], 3, stream=stream)
+    g.run_metropolis(np.full(200, w["T"]))
+    ms_metro = timer(lambda: g.run_metropolis(np.full(n, w["T"])))
+    g.reinit(3)
+    g.run(np.full(200, w["T"]), w["refresh_interval"])
+    ms_micsa = timer(lambda: g.run(np.full(n, w["T"]), w["refresh_interval"]))
+    g.close()
+    u = updates(w["L"], 1, w["replicas"], n)
+    return {"value": u / (ms_metro * 1e6), "unit": METRIC, "sweeps": n,
+            "micsa_same_lattice": u / (ms_micsa * 1e6), "micsa_over_metropolis": ms_metro / ms_micsa}
+
+
+def leg_quench_l32(micsa, timer, stream):
+    L, S, R, T, n, r = 32, 64, 2, 0.7, 10_000, 10
+    N = L ** 3
+    grid = sorted(set([0] + [int(10 ** (k / 8)) for k in range(0, 33)]))
+    g = micsa.Micsa(L, S, R, 2, stream=stream)
+    from paper_2506_16240_gb300 import autotune
+    tuned = autotune.tune(g, __import__("torch"), stream, sweeps=200, use_cache=False)
+    g.reinit(2)
+    series, t_prev, total_ms = [], 0, 0.0
+    for tm in grid:
+        if tm > t_prev:
+            total_ms += timer(lambda: g.run(np.full(tm - t_prev, T), r))
+            t_prev = tm
+        e, a, q = g.measure()
+        series.append((tm, float(e.mean() / N), float(((q / N) ** 2).mean())))
+    eng = g.engine()
+    g.close()
+    return {"value": updates(L, S, R, n) / (total_ms * 1e6), "unit": METRIC, "engine": eng, "launch": tuned,
+            "workload": "L=32, 64 samples x 2 replicas, T=0.7, 1e4 sweeps, refresh every 10",
+            "e_final": series[-1][1], "q2_final": series[-1][2],
+            "e_q2_vs_t": [[t, round(e, 6), round(q2, 8)] for t, e, q2 in series[::4]] + [list(series[-1])]}
+
+
+def c4_instances():
+    rng = np.random.default_rng(4)
+    Ls = rng.choice([16, 24, 32, 48, 64], 256)
+    rs = rng.integers(5, 21, 256)
+    seeds = rng.integers(1, 2 ** 62, 256)
+    return [(int(L), int(r), int(s)) for L, r, s in zip(Ls, rs, seeds)]
+
+
+def leg_batched(micsa, torch, stream, n_sweeps=20_000, loop_sweeps=2_000):
+    inst = c4_instances()
+    total = sum(updates(L, 1, 2, n_sweeps) for L, _, _ in inst)
+    with micsa.Pool(8 << 30, 512, 256) as p:
+        ids = [p.submit(L, 2, s, n_sweeps, r, 2.5, 0.5) for L, r, s in inst]
+        assert all(i is not None for i in ids)
+        p.wait()
+        launches0 = p.stats()["launches"]
+        t0 = time.perf_counter()
+        left = set(ids)
+        while left:
+            p.tick()
+            p.wait_ticks(2)
+            for j in list(left):
+                if p.poll(j, best_spins=False) is not None:
+                    left.discard(j)
+        dt_pool = time.perf_counter() - t0
+        launches = p.stats()["launches"] - launches0
+    # the plain per-lattice launch loop (one handle per lattice, run back to back),
+    # timed on the first loop_sweeps sweeps of the same schedule
+    hs = [micsa.Micsa(L, 1, 2, s, stream=stream) for L, _, s in inst]
+    sched = micsa.linear_schedule(2.5, 0.5, n_sweeps)[:loop_sweeps]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for h, (L, r, _) in zip(hs, inst):
+        h.run(sched, r)
+    torch.cuda.synchronize()
+    dt_loop = time.perf_counter() - t0
+    loop_upd = sum(updates(L, 1, 2, loop_sweeps) for L, _, _ in inst)
+    for h in hs:
+        h.close()
+    batched, loop = total / (dt_pool * 1e9), loop_upd / (dt_loop * 1e9)
+    return {"value": batched, "unit": METRIC, "per_lattice_loop": loop, "speedup": batched / loop,
+            "wall_s": dt_pool, "launches": launches,
+            "workload": "256 lattices L in {16,24,32,48,64} x 2 replicas, anneal 2.5->0.5 over 2e4 sweeps, "
+                        "refresh 5..20; the loop is timed on its first 2e3 sweeps"}
+
+
+def leg_serving(micsa, n_jobs):
+    from paper_2506_16240_gb300 import serve
+    # offered load ~80% of the pool's throughput on this mix (measured first on a burst)
+    mean_upd = serve.mean_job_updates()
+    calib = serve.poisson_stream(24, 1e6, seed=55)
+    with micsa.Pool(16 << 30, 256, 128) as p:
+        t0 = time.perf_counter()
+        done = serve.Server(p).serve(calib, realtime=False)
+        capacity = sum(r.updates for r in done) / (time.perf_counter() - t0)  # updates/s
+    rate_hz = 0.8 * capacity / mean_upd
+    reqs = serve.poisson_stream(n_jobs, rate_hz, seed=5)
+    with micsa.Pool(16 << 30, 256, 128) as p:
+        server = serve.Server(p)
+        done = server.serve(reqs, realtime=True)
+    out = serve.summarize(done, server.wall)
+    out.update({"unit": METRIC, "arrival_rate_hz": rate_hz, "burst_capacity_flips_per_ns": capacity / 1e9,
+                "workload": f"{n_jobs} Poisson jobs: L even 16..96, sweeps log-uniform 1e3..1e5, "
+                            "1..4 replicas, anneal 3.0->0.3, refresh every 10"})
+    return out
+
+
+def main(argv=None):
+    args = parse(argv)
     if args.impl == "reference":
         return run_reference(args)
 
@@ -191,113 +358,61 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
+        torch.distributed.init_process_group("nccl", device_id=dev)
 
     def barrier():
         if world > 1:
-            import torch.distributed as dist
-            dist.barrier()
+            torch.distributed.barrier()
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        import torch.distributed as dist
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def gathered(x):
+        return gather_ms(torch, x, rank, world, dev)
 
     w = WORKLOAD
+    L, S, R = w["L"], w["samples"], w["replicas"]
     # a dedicated (non-default) stream: the library launches on it and the CUDA
     # events below are recorded on it
     stream = torch.cuda.Stream(device=dev)
     torch.cuda.set_stream(stream)
+    timer = Timer(torch, stream)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     sched = np.full(args.sweeps, w["T"])
-    base_seed = 3 + 1000 * rank  # independent lattice per rank
-    g = micsa.Micsa(w["L"], w["samples"], w["replicas"], base_seed, stream=stream)
-
-    def one_step(seed):
-        g.reinit(seed)
-        g.run(sched, w["refresh_interval"])
-        return g.measure()  # synchronous: exact H, H_aux, overlap
+    seed = rank_seed(rank)
+    g = micsa.Micsa(L, S, R, seed, stream=stream)
+    from paper_2506_16240_gb300 import autotune
+    tuned = autotune.tune(g, torch, stream, use_cache=False)  # launch shape for this lattice
 
     for k in range(args.warmup):
-        one_step(base_seed + k)
+        g.reinit(seed + k)
+        g.run(sched, w["refresh_interval"])
+        g.measure()
     torch.cuda.synchronize()
 
     clocks = ClockSampler(local)
-    launches0 = g.launch_count()
     barrier()
     torch.cuda.synchronize()
     clocks.start()
-    step_ms = []
-    last_obs = None
+    step_ms, launches, last_obs = [], 0, None
     for k in range(args.steps):
         flush.zero_()  # evict the previous step's lattice from L2 (512 MB > 129 MB)
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        g.reinit(base_seed + 100 + k)
-        g.run(sched, w["refresh_interval"])
-        ev1.record(stream)
+        n0 = g.launch_count()
+
+        def step():
+            g.reinit(seed + 100 + k)
+            g.run(sched, w["refresh_interval"])
+
+        step_ms.append(timer(step))
+        launches += g.launch_count() - n0
         last_obs = g.measure()
-        torch.cuda.synchronize()
-        step_ms.append(ev0.elapsed_time(ev1))
-    torch.cuda.synchronize()
     barrier()
     clock_info = clocks.stop()
-    launches = g.launch_count() - launches0 - args.steps  # measure kernels are outside the events
-    total_ms = max_over_ranks(sum(step_ms))
-    ms_per_step = total_ms / args.steps
-    value = world * updates_per_step(args.sweeps) * args.steps / (total_ms * 1e6)
+    value, total_ms = aggregate(world, gathered(sum(step_ms)), updates(L, S, R, args.sweeps) * args.steps)
 
-    # -- roofline of the plain half-sweep kernel: timed run without refreshes
-    n_plain = 2000
-    g.reinit(base_seed)
-    g.run(np.full(1, w["T"]), w["refresh_interval"])  # t = 0 refresh
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    g.run(np.full(n_plain, w["T"]), 2 ** 31 - 1)  # t = 1 .. n_plain: no refresh
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    plain_ms = ev0.elapsed_time(ev1)
-    launch_us = 1e3 * plain_ms / (2 * n_plain)
-    L, R, S = w["L"], w["replicas"], w["samples"]
-    half_sites = L ** 3 // 2 * S
-    bytes_per_launch = half_sites * (5 * R + 1)  # s, m read+write per replica, bond, opposite spins
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except OSError:
+    except (OSError, ValueError):
         pass
-    hbm_peak = peaks.get("hbm_gbs", 6800.0)
-    achieved = bytes_per_launch / (launch_us * 1e-6) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak, "traffic": None,
-                "kernel": "micsa::half_sweep_kernel<4,0> (plain MicSA half-sweep)",
-                "bytes_per_launch": bytes_per_launch, "launch_us": launch_us,
-                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback"}
-
-    # -- Metropolis on the same lattice and layout
-    n_metro = 10_000
-    g.reinit(base_seed)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    g.run_metropolis(np.full(n_metro, w["T"]))
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    metro_ms = ev0.elapsed_time(ev1)
-    metro = {"value": updates_per_step(n_metro) / (metro_ms * 1e6), "unit": METRIC,
-             "sweeps": n_metro, "ms": metro_ms}
-    g.reinit(base_seed)
-    g.run(np.full(n_metro, w["T"]), w["refresh_interval"])
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
-    g.run(np.full(n_metro, w["T"]), w["refresh_interval"])
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    micsa_same_ms = ev0.elapsed_time(ev1)
-    metro["micsa_same_sweeps_value"] = updates_per_step(n_metro) / (micsa_same_ms * 1e6)
+    roofline = leg_roofline(micsa, timer, stream, L, peaks)
 
     # -- end to end through the C ABI from pinned host buffers
     N = L ** 3
@@ -310,6 +425,7 @@ def main():
     s_out = torch.empty((S, R, N), dtype=torch.int8, pin_memory=True).numpy()
     m_out = torch.empty((S, R, N), dtype=torch.uint8, pin_memory=True).numpy()
     e2e_steps = max(1, min(args.steps, 2))
+    import ctypes
     barrier()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -317,42 +433,54 @@ def main():
         g.set_couplings(J_host)
         g.set_state(s_host, m_host, 0)
         g.run(sched, w["refresh_interval"])
-        e, a, q = g.measure()
-        _lib = micsa.lib()
-        import ctypes
+        g.measure()
         t_out = ctypes.c_int64()
-        micsa._check(_lib.micsa_get_state(g.h, s_out.ctypes.data_as(ctypes.c_void_p),
-                                          m_out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(t_out)), g.h)
+        micsa._check(micsa.lib().micsa_get_state(g.h, s_out.ctypes.data_as(ctypes.c_void_p),
+                                                 m_out.ctypes.data_as(ctypes.c_void_p), ctypes.byref(t_out)), g.h)
     torch.cuda.synchronize()
-    e2e_s = max_over_ranks(time.perf_counter() - t0)
-    e2e = {"value": world * updates_per_step(args.sweeps) * e2e_steps / (e2e_s * 1e9), "unit": METRIC,
+    e2e_value, _ = aggregate(world, gathered(1e3 * (time.perf_counter() - t0)),
+                             updates(L, S, R, args.sweeps) * e2e_steps)
+    e2e = {"value": e2e_value, "unit": METRIC,
            "h2d_bytes_per_step": int(J_host.nbytes + s_host.nbytes + m_host.nbytes),
            "d2h_bytes_per_step": int(s_out.nbytes + m_out.nbytes + 8 * (2 * S * R + S * R * (R - 1) // 2))}
+    g.close()
+
+    extras = {}
+    if rank == 0 and not args.no_extras:
+        legs = [("dram_point", lambda: leg_roofline(micsa, timer, stream, 320, peaks, n_plain=500)),
+                ("metropolis", lambda: leg_metropolis(micsa, timer, stream)),
+                ("quench_l32", lambda: leg_quench_l32(micsa, timer, stream)),
+                ("batched", lambda: leg_batched(micsa, torch, stream)),
+                ("serving", lambda: leg_serving(micsa, args.serving_jobs))]
+        for name, fn in legs:
+            try:
+                extras[name] = fn()
+            except Exception as exc:  # a failed side leg is reported, not hidden
+                extras[name] = {"error": f"{type(exc).__name__}: {exc}"}
 
     base = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         base = cpu_baseline()
 
     if rank == 0:
-        e_last, a_last, q_last = last_obs
+        e_last, _, q_last = last_obs
         out = {
             "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
             "config": {"workload": w["name"], "L": L, "samples": S, "replicas": R, "T": w["T"],
                        "sweeps_per_step": args.sweeps, "refresh_interval": w["refresh_interval"],
-                       "parallelism": f"replicas{world}",
+                       "parallelism": f"replicas{world}", "launch": tuned,
                        "l2": "flushed between steps (512 MB write); the 20.5 MB lattice stays L2-resident within a step"},
             "e2e": e2e, "gpu_launches": int(launches), "roofline": roofline, "clocks": clock_info,
-            "metropolis": metro, "cpu_baseline": base,
+            "cpu_baseline": base,
             "final_energy_per_spin": [float(v) / N for v in e_last],
             "final_q2": [float(v / N) ** 2 for v in q_last],
         }
+        out.update(extras)
         print(json.dumps(out))
-    g.close()
     if world > 1:
-        import torch.distributed as dist
-        dist.destroy_process_group()
+        torch.distributed.destroy_process_group()
     return 0
 
 

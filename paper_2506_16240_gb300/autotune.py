@@ -1,0 +1,91 @@
+"""Autotuner for the launch shape of the sweep kernels.
+
+For a lattice shape (L, samples, replicas) it times the candidate launch
+shapes (32-bit words per thread, threads per block, grid-stride cap) and, for
+lattices that fit in shared memory, the resident engines, on a short run of
+sweeps of that very shape, and keeps the fastest. Every choice computes the
+same bits, so tuning never changes results. Choices are cached in a JSON file
+keyed by device name and shape (``MICSA_AUTOTUNE_CACHE``, default
+``~/.cache/micsa_autotune.json``).
+"""
+import itertools
+import json
+import os
+
+import numpy as np
+
+from . import Micsa
+
+CACHE = os.environ.get("MICSA_AUTOTUNE_CACHE",
+                       os.path.join(os.path.expanduser("~"), ".cache", "micsa_autotune.json"))
+
+
+def _key(device_name, L, S, R):
+    return f"{device_name}|L={L}|S={S}|R={R}"
+
+
+def _load():
+    try:
+        with open(CACHE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(cache):
+    try:
+        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+        tmp = f"{CACHE}.{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(cache, f, indent=1, sort_keys=True)
+        os.replace(tmp, CACHE)
+    except OSError:
+        pass  # a read-only home only loses the cache
+
+
+def candidates(L):
+    out = [{"engine": "stream", "words_per_thread": nw, "block": blk, "blocks_per_sm": bps}
+           for nw, blk, bps in itertools.product([4, 2], [64, 128, 256], [-1, 0])]
+    if L <= 40:
+        out.append({"engine": "resident"})
+    if L <= 32:
+        out.append({"engine": "multispin"})
+    return out
+
+
+def apply(g, choice, resident_sweeps=256):
+    if choice["engine"] == "stream":
+        g.set_engine("stream")
+        g.set_launch_config(choice["words_per_thread"], choice["block"], choice["blocks_per_sm"], True, 64)
+    else:
+        g.set_engine(choice["engine"], resident_sweeps)
+
+
+def tune(g, torch, stream, sweeps=400, T=0.7, refresh_interval=10, use_cache=True):
+    """Pick and apply the fastest launch shape for handle g; returns the choice
+    with its measured spin-flips/ns. The handle's state is advanced (t moves)."""
+    name = torch.cuda.get_device_name()
+    key = _key(name, g.L, g.S, g.R)
+    cache = _load() if use_cache else {}
+    if key in cache:
+        apply(g, cache[key])
+        return dict(cache[key], cached=True)
+    sched = np.full(sweeps, T)
+    best = None
+    for c in candidates(g.L):
+        apply(g, c)
+        g.run(sched[: max(10, sweeps // 10)], refresh_interval)  # warm-up of this shape
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.run(sched, refresh_interval)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        rate = g.L ** 3 * g.S * g.R * sweeps / (e0.elapsed_time(e1) * 1e6)
+        if best is None or rate > best[1]:
+            best = (c, rate)
+    choice = dict(best[0], flips_per_ns=best[1])
+    apply(g, choice)
+    if use_cache:
+        cache[key] = choice
+        _store(cache)
+    return dict(choice, cached=False)

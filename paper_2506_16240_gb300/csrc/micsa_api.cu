@@ -33,7 +33,7 @@ struct micsa_ctx {
     cudaStream_t capture_stream = nullptr;  // graphs are captured here (never the legacy stream)
     int sm_count = 0;
     LaunchConfig lc;                // requested launch shape
-    int blocks_per_sm = 0;          // -1: resident capacity (grid-stride), 0: no cap
+    int blocks_per_sm = -1;         // -1: resident capacity (grid-stride), 0: no cap
     // per-run sweep parameter table: pinned host copy, device copy
     SweepParam *h_params = nullptr;
     SweepParam *d_params = nullptr;

@@ -42,6 +42,32 @@ __device__ __forceinline__ uint32_t lane_of(uint4 w, int lane) {
     return lane == 0 ? w.x : lane == 1 ? w.y : lane == 2 ? w.z : w.w;
 }
 
+// ------------------------------------------------------------ division --
+// Division of n < 2^31 by a fixed d >= 1 as a multiply-high, add and shift
+// (the round-up multiplier of Granlund and Montgomery, "Division by invariant
+// integers using multiplication", PLDI 1994): l = ceil(log2 d),
+// m = floor(2^32 (2^l - d) / d) + 1, n / d = (mulhi(n, m) + n) >> l.
+struct FastDiv {
+    uint32_t d, m, l;
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+    uint32_t l = 0;
+    while ((1ull << l) < d) ++l;
+    const uint64_t m = ((((uint64_t)1 << l) - d) << 32) / d + 1;
+    return FastDiv{d, (uint32_t)m, l};
+}
+
+__device__ __forceinline__ FastDiv make_fastdiv_dev(uint32_t d) {
+    const uint32_t l = d <= 1 ? 0u : 32u - __clz(d - 1);
+    const uint64_t m = ((((uint64_t)1 << l) - d) << 32) / d + 1;
+    return FastDiv{d, (uint32_t)m, l};
+}
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t n, const FastDiv &f) {
+    return (__umulhi(n, f.m) + n) >> f.l;
+}
+
 // ------------------------------------------------------------- geometry --
 struct Geometry {
     int L;        // linear size (even)

@@ -31,6 +31,8 @@ struct SweepArgs {
     const SweepParam *params;    // the run's table
     const int64_t *cursor;       // graph replays: base index into params; else nullptr
     int64_t k;                   // this sweep's index relative to *cursor (or absolute)
+    FastDiv div_chunks;          // row -> (row, chunk): divide by chunks per row
+    FastDiv div_L;               // row -> (z, y): divide by L
 };
 
 // Launch shape of the half-sweep kernels (picked by the autotuner; results are
@@ -58,6 +60,7 @@ struct JobDesc {
     int64_t n_sweeps;
     int32_t interval;
     int32_t live;
+    uint32_t divL_m, divL_l;  // FastDiv by L
 };
 
 // One lattice (a replica of a sample or of a pool job) that a CTA keeps in

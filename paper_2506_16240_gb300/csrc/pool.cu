@@ -65,9 +65,10 @@ __device__ __forceinline__ void pool_item(const JobDesc &J, int64_t item, int p,
         th1 = q[1];
         th2 = q[2];
     }
+    const FastDiv divL{(uint32_t)J.geo.L, J.divL_m, J.divL_l};
     update_chunk<NW, false>(J.geo, J.spins + (int64_t)r * 2 * J.geo.half,
                             J.daemons + (int64_t)r * 2 * J.geo.half, J.bonds, p, row, c, (uint32_t)r,
-                            J.key0, J.key1, t, refresh, th0, th1, th2);
+                            J.key0, J.key1, t, refresh, th0, th1, th2, divL);
 }
 
 // One half-sweep (parity p) of sweep k of the tick for every live job.
@@ -648,6 +649,9 @@ int micsa_pool_submit(micsa_pool_t p, const micsa_job_desc *job, int64_t *job_id
     D.n_sweeps = d.n_sweeps;
     D.interval = d.refresh_interval;
     D.live = 1;
+    const FastDiv fdL = make_fastdiv((uint32_t)d.L);
+    D.divL_m = fdL.m;
+    D.divL_l = fdL.l;
     D.resident = (p->resident_smem && multispin_smem_bytes(s.g) && multispin_smem_bytes(s.g) <= p->resident_smem) ? 1 : 0;
     p->tables_dirty = true;
     *job_id = J.id;

@@ -38,10 +38,11 @@ __device__ __forceinline__ void resident_half(const Geometry &g, int8_t *sp, uin
                                               bool refresh, uint64_t th0, uint64_t th1, uint64_t th2) {
     const int chunks = g.W / NW;
     const int items = g.L * g.L * chunks;
+    const FastDiv divL = make_fastdiv_dev((uint32_t)g.L);
     for (int it = threadIdx.x; it < items; it += blockDim.x) {
         const int row = it / chunks;
         const int c = it - row * chunks;
-        update_chunk<NW, false, true>(g, sp, dm, bd, p, row, c, gid, k0, k1, t, refresh, th0, th1, th2);
+        update_chunk<NW, false, true>(g, sp, dm, bd, p, row, c, gid, k0, k1, t, refresh, th0, th1, th2, divL);
     }
 }
 

@@ -29,8 +29,8 @@ __device__ __forceinline__ void update_chunk(const Geometry &g, int8_t *spins, u
                                              const uint8_t *bonds, int p, int row, int c,
                                              uint32_t gid, uint32_t key0, uint32_t key1, int64_t t,
                                              bool refresh, uint64_t th0, uint64_t th1,
-                                             uint64_t th2) {
-    const int y = row % g.L, z = row / g.L;
+                                             uint64_t th2, const FastDiv &divL) {
+    const int z = (int)fdiv((uint32_t)row, divL), y = row - z * g.L;
     const int o = (p + y + z) & 1;
     const int b0 = c * 4 * NW;  // first byte of this thread's range within the row
     const int yp = (y + 1 == g.L) ? 0 : y + 1, ym = (y == 0) ? g.L - 1 : y - 1;

@@ -31,27 +31,24 @@ __global__ void __launch_bounds__(256) half_sweep_kernel(SweepArgs a) {
     grid_dependency_wait();  // the previous half-sweep's writes are visible after this
     grid_launch_dependents();
     const Geometry g = a.geo;
-    const int chunks = g.W / NW;
-    const int64_t per_sample = (int64_t)g.L * g.L * chunks;
-    const int64_t total = per_sample * a.S;
+    const uint32_t per_sample = (uint32_t)g.L * g.L * (g.W / NW);  // < 2^31 for L <= 1600
     const int64_t kidx = a.k + (a.cursor ? *a.cursor : 0);
     const SweepParam prm = a.params[kidx];
     const bool refresh = !METRO && prm.mode == kModeRefresh;
 
-    // thread row y of the block takes replicas y, y + blockDim.y, ...
-    for (int r = threadIdx.y; r < a.R; r += blockDim.y)
-        for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total;
-             q += (int64_t)gridDim.x * blockDim.x) {
-            const int sample = (int)(q / per_sample);
-            const int64_t rem = q - (int64_t)sample * per_sample;
-            const int row = (int)(rem / chunks);
-            const int c = (int)(rem - (int64_t)row * chunks);
-            const int64_t gid = (int64_t)sample * a.R + r;
-            update_chunk<NW, METRO>(g, a.spins + gid * 2 * g.half, a.daemons + gid * 2 * g.half,
-                                    a.bonds + (int64_t)sample * 2 * g.half, a.parity, row, c,
-                                    (uint32_t)gid, a.key0, a.key1, prm.t, refresh, prm.th0, prm.th1,
-                                    prm.th2);
-        }
+    // grid: x over the chunks of one sample, y over samples; thread row y of
+    // the block takes replicas threadIdx.y, threadIdx.y + blockDim.y, ...
+    for (int sample = blockIdx.y; sample < a.S; sample += gridDim.y)
+        for (int r = threadIdx.y; r < a.R; r += blockDim.y)
+            for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < per_sample; q += gridDim.x * blockDim.x) {
+                const uint32_t row = fdiv(q, a.div_chunks);
+                const int c = (int)(q - row * a.div_chunks.d);
+                const int64_t gid = (int64_t)sample * a.R + r;
+                update_chunk<NW, METRO>(g, a.spins + gid * 2 * g.half, a.daemons + gid * 2 * g.half,
+                                        a.bonds + (int64_t)sample * 2 * g.half, a.parity, (int)row, c,
+                                        (uint32_t)gid, a.key0, a.key1, prm.t, refresh, prm.th0, prm.th1,
+                                        prm.th2, a.div_L);
+            }
 }
 
 // Advance the graph replay cursor by `step` sweeps (the last node of a graph).
@@ -72,13 +69,20 @@ dim3 block_shape(int R, int block) {
 }
 
 template <int NW, bool METRO>
-static cudaError_t launch_variant(const SweepArgs &a, const LaunchConfig &lc, cudaStream_t st) {
-    const int64_t chunks = (int64_t)a.S * a.geo.L * a.geo.L * (a.geo.W / NW);
+static cudaError_t launch_variant(const SweepArgs &a0, const LaunchConfig &lc, cudaStream_t st) {
+    SweepArgs a = a0;
+    const int chunks = a.geo.W / NW;
+    a.div_chunks = make_fastdiv((uint32_t)chunks);
+    a.div_L = make_fastdiv((uint32_t)a.geo.L);
+    const int64_t per_sample = (int64_t)a.geo.L * a.geo.L * chunks;
     const dim3 blk = block_shape(a.R, lc.block);
-    int64_t grid = (chunks + blk.x - 1) / blk.x;
-    if (lc.max_blocks > 0 && grid > lc.max_blocks) grid = lc.max_blocks;
+    int64_t gx = (per_sample + blk.x - 1) / blk.x;
+    int64_t gy = a.S < 65535 ? a.S : 65535;
+    if (lc.max_blocks > 0 && gx * gy > lc.max_blocks) {  // grid-stride cap over chunks
+        gx = lc.max_blocks / gy > 0 ? lc.max_blocks / gy : 1;
+    }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)grid);
+    cfg.gridDim = dim3((unsigned)gx, (unsigned)gy);
     cfg.blockDim = blk;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];

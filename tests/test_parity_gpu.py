@@ -235,3 +235,20 @@ def test_launch_configs_agree(L):
             np.testing.assert_array_equal(s, ref[0], err_msg=str(cfg))
             np.testing.assert_array_equal(m, ref[1], err_msg=str(cfg))
             assert t == ref[2]
+
+
+def test_autotuner_choice_keeps_results():
+    import torch
+    from paper_2506_16240_gb300 import autotune
+    stream = torch.cuda.Stream()
+    for L in (16, 34):
+        with micsa.Micsa(L, 2, 2, 5, stream=stream) as g:
+            choice = autotune.tune(g, torch, stream, sweeps=40, use_cache=False)
+            assert choice["engine"] in ("stream", "resident", "multispin") and choice["flips_per_ns"] > 0
+            g.reinit(5)
+            g.run(np.linspace(2.0, 0.6, 30), 4)
+            s, m, t = g.get_state()
+        st = O.create(L, 2, 2, 5)
+        O.run(st, np.linspace(2.0, 0.6, 30), 4)
+        np.testing.assert_array_equal(s, st["s"])
+        np.testing.assert_array_equal(m, st["m"])
