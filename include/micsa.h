@@ -124,12 +124,15 @@ int micsa_device_bytes(micsa_t h, size_t *bytes);
 
 /* Launch shape of the sweep kernels (the autotuner's knobs; results are
  * bit-identical for every choice): words_per_thread 1, 2 or 4 (32-bit words of
- * sites per thread, reduced to what the row pitch allows), block 32..256 in
+ * sites per thread, reduced to what the row pitch allows), optionally ORed with
+ * MICSA_LAUNCH_REGCAP for the kernel variant whose registers are capped at 64
+ * per thread (blocks of at most 128 threads, 8 per SM), block 32..256 in
  * steps of 32, blocks_per_sm -1 (grid-stride loop over the resident capacity),
  * 0 (one thread per chunk) or a positive cap, pdl != 0 chains consecutive
  * half-sweeps with programmatic dependent launch, graph_sweeps > 0 replays a
  * captured CUDA graph of that many sweeps (0: direct launches). Synchronizes
  * the handle's stream. */
+#define MICSA_LAUNCH_REGCAP 256
 int micsa_set_launch_config(micsa_t h, int words_per_thread, int block, int blocks_per_sm, int pdl,
                             int graph_sweeps);
 
@@ -153,8 +156,8 @@ int micsa_set_engine(micsa_t h, int engine, int resident_sweeps);
 /* The engine that the next micsa_run will use (STREAM, RESIDENT or MULTISPIN). */
 int micsa_get_engine(micsa_t h, int *engine);
 
-/* The launch shape in effect (blocks_per_sm reports the grid cap / SM count).
- * Any pointer may be NULL. */
+/* The launch shape requested (words_per_thread as set, reduced to what the row
+ * pitch allows, with MICSA_LAUNCH_REGCAP if chosen). Any pointer may be NULL. */
 int micsa_get_launch_config(micsa_t h, int *words_per_thread, int *block, int *blocks_per_sm,
                             int *pdl, int *graph_sweeps);
 
@@ -261,6 +264,10 @@ int micsa_pool_wait_ticks(micsa_pool_t p, int max_pending);
  * may be NULL), free its slot and memory, return MICSA_OK. MICSA_E_BUSY if it
  * is still running, MICSA_E_NOT_FOUND for an unknown (or already polled) id. */
 int micsa_pool_poll(micsa_pool_t p, int64_t job_id, micsa_job_result *res, int8_t *best_spins);
+
+/* Ids of up to max_ids finished jobs whose last tick has run (ready to poll
+ * without waiting), in *n_ids. Non-blocking. */
+int micsa_pool_finished(micsa_pool_t p, int64_t *ids, int max_ids, int *n_ids);
 
 /* Jobs resident, free arena bytes, kernels launched so far. Any pointer may be NULL. */
 int micsa_pool_stats(micsa_pool_t p, int *live_jobs, size_t *free_bytes, int64_t *launches);

@@ -278,6 +278,7 @@ SIGNATURES.update({
     "micsa_pool_wait_ticks": (_c.c_int, [_P, _c.c_int]),
     "micsa_pool_poll": (_c.c_int, [_P, _c.c_int64, ctypes.POINTER(JobResult), _P]),
     "micsa_pool_stats": (_c.c_int, [_P, ctypes.POINTER(_c.c_int), ctypes.POINTER(ctypes.c_size_t), _i64p]),
+    "micsa_pool_finished": (_c.c_int, [_P, _i64p, _c.c_int, ctypes.POINTER(_c.c_int)]),
     "micsa_pool_set_launch_config": (_c.c_int, [_P, _c.c_int, _c.c_int, _c.c_int]),
     "micsa_pool_last_error": (_c.c_char_p, [_P]),
     "micsa_pool_destroy": (None, [_P]),
@@ -370,6 +371,13 @@ class Pool:
         if best_spins:
             out["best_spins"] = spins
         return out
+
+    def finished(self, max_ids=4096):
+        """Ids of finished jobs that can be polled now (non-blocking)."""
+        ids = (ctypes.c_int64 * max_ids)()
+        n = ctypes.c_int()
+        self._check(lib().micsa_pool_finished(self.h, ids, int(max_ids), ctypes.byref(n)))
+        return [ids[i] for i in range(n.value)]
 
     def stats(self):
         n = ctypes.c_int()

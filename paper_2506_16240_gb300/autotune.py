@@ -45,7 +45,10 @@ def _store(cache):
 
 def candidates(L):
     out = [{"engine": "stream", "words_per_thread": nw, "block": blk, "blocks_per_sm": bps}
-           for nw, blk, bps in itertools.product([4, 2], [64, 128, 256], [-1, 0])]
+           for nw, blk, bps in itertools.product([4, 2], [64, 128, 256], [-1, 0, 2, 3, 4, 5])]
+    # register-capped variant (64 registers, up to 8 blocks of 128 per SM)
+    out += [{"engine": "stream", "words_per_thread": nw | 256, "block": blk, "blocks_per_sm": bps}
+            for nw, blk, bps in itertools.product([4, 2], [64, 128], [-1, 0, 4, 6, 8])]
     if L <= 40:
         out.append({"engine": "resident"})
     if L <= 32:

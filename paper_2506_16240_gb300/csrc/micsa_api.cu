@@ -139,8 +139,8 @@ LaunchConfig effective_config(micsa_t h, bool metro) {
     LaunchConfig lc = h->lc;
     lc.nw = vector_words(h->geo, lc.nw);
     if (h->blocks_per_sm < 0) {
-        const dim3 b = block_shape(h->R, lc.block);
-        const int per_sm = max_resident_blocks(metro, lc.nw, (int)(b.x * b.y));
+        const dim3 b = block_shape(h->R, lc.regcap && lc.block > 128 ? 128 : lc.block);
+        const int per_sm = max_resident_blocks(metro, lc.nw, (int)(b.x * b.y), lc.regcap);
         lc.max_blocks = per_sm > 0 ? per_sm * h->sm_count : 0;
     } else {
         lc.max_blocks = h->blocks_per_sm * h->sm_count;
@@ -525,6 +525,8 @@ int micsa_run_metropolis(micsa_t h, const double *schedule, int64_t n_sweeps) {
 int micsa_set_launch_config(micsa_t h, int words_per_thread, int block, int blocks_per_sm, int pdl,
                             int graph_sweeps) {
     if (!h) return MICSA_E_INVALID_ARG;
+    const bool regcap = (words_per_thread & MICSA_LAUNCH_REGCAP) != 0;
+    words_per_thread &= ~MICSA_LAUNCH_REGCAP;
     if ((words_per_thread != 1 && words_per_thread != 2 && words_per_thread != 4) ||
         block < 32 || block > 256 || block % 32 || blocks_per_sm < -1 || blocks_per_sm > 64 ||
         graph_sweeps < 0 || graph_sweeps > 4096)
@@ -533,6 +535,7 @@ int micsa_set_launch_config(micsa_t h, int words_per_thread, int block, int bloc
     CK(h, cudaStreamSynchronize(h->stream), "synchronize before reconfiguring");
     drop_graphs(h);
     h->lc.nw = words_per_thread;
+    h->lc.regcap = regcap;
     h->lc.block = block;
     h->lc.pdl = pdl != 0;
     h->lc.graph_sweeps = graph_sweeps;
@@ -565,9 +568,9 @@ int micsa_get_launch_config(micsa_t h, int *words_per_thread, int *block, int *b
                             int *pdl, int *graph_sweeps) {
     if (!h) return MICSA_E_INVALID_ARG;
     const LaunchConfig lc = effective_config(h, false);
-    if (words_per_thread) *words_per_thread = lc.nw;
+    if (words_per_thread) *words_per_thread = lc.nw | (lc.regcap ? MICSA_LAUNCH_REGCAP : 0);
     if (block) *block = lc.block;
-    if (blocks_per_sm) *blocks_per_sm = h->sm_count ? lc.max_blocks / h->sm_count : 0;
+    if (blocks_per_sm) *blocks_per_sm = h->blocks_per_sm;
     if (pdl) *pdl = lc.pdl;
     if (graph_sweeps) *graph_sweeps = lc.graph_sweeps;
     return MICSA_OK;

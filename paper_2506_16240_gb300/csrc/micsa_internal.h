@@ -43,6 +43,7 @@ struct LaunchConfig {
     int max_blocks = 0;  // grid cap for the grid-stride loop (0: one thread per chunk)
     bool pdl = true;     // programmatic dependent launch between consecutive grids
     int graph_sweeps = 64;  // sweeps per captured CUDA graph (0: no graphs)
+    bool regcap = false;    // kernel variant with registers capped at 64 (blocks of <= 128)
 };
 
 // One job of the batched pool (device-resident descriptor).
@@ -61,6 +62,7 @@ struct JobDesc {
     int32_t interval;
     int32_t live;
     uint32_t divL_m, divL_l;  // FastDiv by L
+    uint32_t divC_m, divC_l;  // FastDiv by chunks per row (W / nw)
 };
 
 // One lattice (a replica of a sample or of a pool job) that a CTA keeps in
@@ -145,7 +147,7 @@ cudaError_t launch_multispin(const ResidentArgs &a, bool pool, size_t smem, int 
 int multispin_blocks_per_sm(bool pool, size_t smem);
 cudaError_t launch_advance_cursor(int64_t *cursor, int64_t step, bool pdl, cudaStream_t st);
 int vector_words(const Geometry &g, int want);
-int max_resident_blocks(bool metro, int nw, int block);
+int max_resident_blocks(bool metro, int nw, int block, bool regcap);
 dim3 block_shape(int R, int block);
 
 // initialisation, layout conversion and measurement (init_measure.cu)

@@ -33,7 +33,9 @@ constexpr int kVBlock = 128;  // chunk items per virtual block
 
 struct VBlock {
     int32_t slot;
-    int32_t chunk0;
+    int16_t replica;
+    int16_t pad;
+    int32_t chunk0;  // first chunk of the replica's half-lattice in this block
 };
 
 struct PoolTables {
@@ -50,13 +52,10 @@ __device__ __forceinline__ void pool_wait() { asm volatile("griddepcontrol.wait;
 __device__ __forceinline__ void pool_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 template <int NW>
-__device__ __forceinline__ void pool_item(const JobDesc &J, int64_t item, int p, int64_t t) {
-    const int chunks = J.geo.W / NW;
-    const int64_t per_rep = (int64_t)J.geo.L * J.geo.L * chunks;
-    const int r = (int)(item / per_rep);
-    const int64_t rem = item - (int64_t)r * per_rep;
-    const int row = (int)(rem / chunks);
-    const int c = (int)(rem - (int64_t)row * chunks);
+__device__ __forceinline__ void pool_item(const JobDesc &J, int r, uint32_t chunk, int p, int64_t t) {
+    const FastDiv dc{(uint32_t)(J.geo.W / NW), J.divC_m, J.divC_l};
+    const uint32_t row = fdiv(chunk, dc);
+    const int c = (int)(chunk - row * dc.d);
     const bool refresh = (t % J.interval) == 0;
     uint64_t th0 = 0, th1 = 0, th2 = 0;
     if (refresh) {
@@ -67,7 +66,7 @@ __device__ __forceinline__ void pool_item(const JobDesc &J, int64_t item, int p,
     }
     const FastDiv divL{(uint32_t)J.geo.L, J.divL_m, J.divL_l};
     update_chunk<NW, false>(J.geo, J.spins + (int64_t)r * 2 * J.geo.half,
-                            J.daemons + (int64_t)r * 2 * J.geo.half, J.bonds, p, row, c, (uint32_t)r,
+                            J.daemons + (int64_t)r * 2 * J.geo.half, J.bonds, p, (int)row, c, (uint32_t)r,
                             J.key0, J.key1, t, refresh, th0, th1, th2, divL);
 }
 
@@ -81,11 +80,12 @@ __global__ void __launch_bounds__(kVBlock) pool_half_sweep_kernel(PoolTables T, 
         const JobDesc &J = T.jobs[b.slot];
         const int64_t t = J.t + k;
         if (!J.live || t >= J.n_sweeps) continue;
-        const int64_t items = (int64_t)J.R * J.geo.L * J.geo.L * (J.geo.W / J.nw);
-        const int64_t item = (int64_t)b.chunk0 + threadIdx.x;
-        if (item >= items) continue;
-        if (J.nw == 4) pool_item<4>(J, item, p, t);
-        else pool_item<1>(J, item, p, t);
+        const uint32_t chunks = (uint32_t)J.geo.L * J.geo.L * (J.geo.W / J.nw);
+        const uint32_t chunk = (uint32_t)b.chunk0 + threadIdx.x;
+        if (chunk >= chunks) continue;
+        if (J.nw == 4) pool_item<4>(J, b.replica, chunk, p, t);
+        else if (J.nw == 2) pool_item<2>(J, b.replica, chunk, p, t);
+        else pool_item<1>(J, b.replica, chunk, p, t);
     }
 }
 
@@ -232,6 +232,8 @@ struct micsa_pool {
     int64_t launches = 0;
     cudaStream_t stream = nullptr;
     cudaStream_t capture_stream = nullptr;
+    cudaStream_t aux_stream = nullptr;       // forked branch of a tick (resident kernel)
+    cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
     bool tables_dirty = true;
     cudaEvent_t tables_free = nullptr;  // the last table upload has been consumed
     // per slot: pinned staging of the job's initial data (cut points + result
@@ -333,7 +335,7 @@ struct JobSizes {
 JobSizes job_sizes(const micsa_job_desc &d) {
     JobSizes s;
     s.g = make_geometry(d.L);
-    s.nw = s.g.W % 4 == 0 ? 4 : 1;
+    s.nw = s.g.W % 4 == 0 ? 4 : s.g.W % 2 == 0 ? 2 : 1;
     s.bonds = (size_t)2 * s.g.half;
     s.state = (size_t)d.n_replicas * 2 * s.g.half;
     s.best = (size_t)d.n_replicas * d.L * d.L * d.L;
@@ -366,11 +368,12 @@ int upload_tables(micsa_pool_t p) {
             }
             continue;
         }
-        const int64_t items = (int64_t)J.R * J.geo.L * J.geo.L * (J.geo.W / J.nw);
-        for (int64_t c = 0; c < items; c += kVBlock) {
-            if (nvb >= p->max_vblocks) return pfail(p, MICSA_E_BUSY, "virtual block table full");
-            p->h_vblocks[nvb++] = VBlock{i, (int32_t)c};
-        }
+        const int64_t chunks = (int64_t)J.geo.L * J.geo.L * (J.geo.W / J.nw);
+        for (int r = 0; r < J.R; ++r)
+            for (int64_t c = 0; c < chunks; c += kVBlock) {
+                if (nvb >= p->max_vblocks) return pfail(p, MICSA_E_BUSY, "virtual block table full");
+                p->h_vblocks[nvb++] = VBlock{i, (int16_t)r, 0, (int32_t)c};
+            }
     }
     *p->h_nvb = nvb;
     *p->h_nunits = nunits;
@@ -397,6 +400,16 @@ int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
     long long *R0 = p->d_results;
     const size_t rows = (size_t)p->max_jobs * kPoolMaxR;
     PoolTables T{p->d_jobs, p->d_vblocks, p->d_nvb, R0, R0 + rows, R0 + 2 * rows, R0 + 3 * rows};
+    // both parts present: the resident kernel runs on a forked branch, concurrently
+    // with the streaming half-sweeps (they touch disjoint jobs), joined before
+    // the measure and advance nodes
+    const bool fork = (mask & 3) == 3 && p->resident_smem;
+    cudaStream_t rs = st;
+    if (fork) {
+        PCK(p, cudaEventRecord(p->fork_ev, st), "fork event");
+        PCK(p, cudaStreamWaitEvent(p->aux_stream, p->fork_ev, 0), "fork wait");
+        rs = p->aux_stream;
+    }
     if ((mask & 1) && p->resident_smem) {
         ResidentArgs ra{};
         ra.units = p->d_units;
@@ -406,7 +419,7 @@ int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
         ra.jobs = p->d_jobs;
         ra.results = p->d_results;
         ra.max_jobs = p->max_jobs;
-        PCK(p, launch_multispin(ra, true, p->resident_smem, p->resident_grid, p->pdl, st), "pool multispin launch");
+        PCK(p, launch_multispin(ra, true, p->resident_smem, p->resident_grid, p->pdl && !fork, rs), "pool multispin launch");
     }
     if (mask & 2) {
         for (int k = 0; k < p->K; ++k)
@@ -418,9 +431,13 @@ int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
         void *margs[] = {&T, &K};
         PCK(p, launch_pdl((const void *)pool_measure_kernel, dim3(p->max_jobs, kPoolMaxR), dim3(256), st, margs, p->pdl), "pool measure launch");
     }
+    if (fork) {
+        PCK(p, cudaEventRecord(p->join_ev, p->aux_stream), "join event");
+        PCK(p, cudaStreamWaitEvent(st, p->join_ev, 0), "join wait");
+    }
     int K = p->K, mj = p->max_jobs;
     void *aargs[] = {&p->d_jobs, &mj, &K, &p->d_counter};
-    PCK(p, launch_pdl((const void *)pool_advance_kernel, dim3((p->max_jobs + 255) / 256), dim3(256), st, aargs, p->pdl), "pool advance launch");
+    PCK(p, launch_pdl((const void *)pool_advance_kernel, dim3((p->max_jobs + 255) / 256), dim3(256), st, aargs, p->pdl && !fork), "pool advance launch");
     return MICSA_OK;
 }
 
@@ -486,6 +503,9 @@ int micsa_pool_create(size_t arena_bytes, int max_jobs, int tick_sweeps, micsa_p
         if ((e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         if ((e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         if ((e = cudaStreamCreateWithFlags(&p->capture_stream, cudaStreamNonBlocking)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+        if ((e = cudaStreamCreateWithFlags(&p->aux_stream, cudaStreamNonBlocking)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+        if ((e = cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&p->join_ev, cudaEventDisableTiming)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         if ((e = cudaEventCreateWithFlags(&p->tables_free, cudaEventDisableTiming)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         if ((e = cudaMalloc(&p->arena, p->arena_bytes)) != cudaSuccess) { bail(MICSA_E_OOM); break; }
         p->free_list[0] = p->arena_bytes;
@@ -559,6 +579,12 @@ void micsa_pool_destroy(micsa_pool_t p) {
     cudaFreeHost(p->h_vblocks);
     cudaFreeHost(p->h_nvb);
     if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
+    if (p->aux_stream) {
+        cudaStreamSynchronize(p->aux_stream);
+        cudaStreamDestroy(p->aux_stream);
+    }
+    if (p->fork_ev) cudaEventDestroy(p->fork_ev);
+    if (p->join_ev) cudaEventDestroy(p->join_ev);
     if (p->stream) cudaStreamDestroy(p->stream);
     delete p;
 }
@@ -652,6 +678,9 @@ int micsa_pool_submit(micsa_pool_t p, const micsa_job_desc *job, int64_t *job_id
     const FastDiv fdL = make_fastdiv((uint32_t)d.L);
     D.divL_m = fdL.m;
     D.divL_l = fdL.l;
+    const FastDiv fdC = make_fastdiv((uint32_t)(s.g.W / s.nw));
+    D.divC_m = fdC.m;
+    D.divC_l = fdC.l;
     D.resident = (p->resident_smem && multispin_smem_bytes(s.g) && multispin_smem_bytes(s.g) <= p->resident_smem) ? 1 : 0;
     p->tables_dirty = true;
     *job_id = J.id;
@@ -740,6 +769,25 @@ int micsa_pool_poll(micsa_pool_t p, int64_t job_id, micsa_job_result *res, int8_
     }
     // the slot's device memory may be reused only after its last tick has run
     release_slot(p, slot);
+    return MICSA_OK;
+}
+
+int micsa_pool_finished(micsa_pool_t p, int64_t *ids, int max_ids, int *n_ids) {
+    if (!p || !n_ids || max_ids < 0 || (max_ids > 0 && !ids)) return MICSA_E_INVALID_ARG;
+    int n = 0;
+    const int64_t ring = (int64_t)p->tick_events.size();
+    for (int i = 0; i < p->max_jobs && n < max_ids; ++i) {
+        const PoolJob &J = p->slots[i];
+        if (J.id < 0 || J.done_tick < 0) continue;
+        bool done = true;
+        if (J.done_tick + ring > p->ticks_queued - 1) {  // its event has not been reused: ask it
+            const cudaError_t q = cudaEventQuery(p->tick_events[J.done_tick % ring]);
+            if (q == cudaErrorNotReady) done = false;
+            else PCK(p, q, "tick event query");
+        }
+        if (done) ids[n++] = J.id;
+    }
+    *n_ids = n;
     return MICSA_OK;
 }
 

@@ -27,7 +27,7 @@ __device__ __forceinline__ void grid_launch_dependents() {
 }
 
 template <int NW, bool METRO>
-__global__ void __launch_bounds__(256) half_sweep_kernel(SweepArgs a) {
+__device__ __forceinline__ void half_sweep_body(const SweepArgs &a) {
     grid_dependency_wait();  // the previous half-sweep's writes are visible after this
     grid_launch_dependents();
     const Geometry g = a.geo;
@@ -49,6 +49,18 @@ __global__ void __launch_bounds__(256) half_sweep_kernel(SweepArgs a) {
                                         (uint32_t)gid, a.key0, a.key1, prm.t, refresh, prm.th0, prm.th1,
                                         prm.th2, a.div_L);
             }
+}
+
+template <int NW, bool METRO>
+__global__ void __launch_bounds__(256) half_sweep_kernel(SweepArgs a) {
+    half_sweep_body<NW, METRO>(a);
+}
+
+// The same kernel with registers capped at 64 per thread (8 blocks of 128
+// threads per SM): more warps in flight for the latency-bound L2-resident case.
+template <int NW, bool METRO>
+__global__ void __launch_bounds__(128, 8) half_sweep_kernel_rc(SweepArgs a) {
+    half_sweep_body<NW, METRO>(a);
 }
 
 // Advance the graph replay cursor by `step` sweeps (the last node of a graph).
@@ -75,7 +87,7 @@ static cudaError_t launch_variant(const SweepArgs &a0, const LaunchConfig &lc, c
     a.div_chunks = make_fastdiv((uint32_t)chunks);
     a.div_L = make_fastdiv((uint32_t)a.geo.L);
     const int64_t per_sample = (int64_t)a.geo.L * a.geo.L * chunks;
-    const dim3 blk = block_shape(a.R, lc.block);
+    const dim3 blk = block_shape(a.R, lc.regcap && lc.block > 128 ? 128 : lc.block);
     int64_t gx = (per_sample + blk.x - 1) / blk.x;
     int64_t gy = a.S < 65535 ? a.S : 65535;
     if (lc.max_blocks > 0 && gx * gy > lc.max_blocks) {  // grid-stride cap over chunks
@@ -90,6 +102,7 @@ static cudaError_t launch_variant(const SweepArgs &a0, const LaunchConfig &lc, c
     attr[0].val.programmaticStreamSerializationAllowed = lc.pdl ? 1 : 0;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    if (lc.regcap) return cudaLaunchKernelEx(&cfg, half_sweep_kernel_rc<NW, METRO>, a);
     return cudaLaunchKernelEx(&cfg, half_sweep_kernel<NW, METRO>, a);
 }
 
@@ -124,18 +137,19 @@ cudaError_t launch_advance_cursor(int64_t *cursor, int64_t step, bool pdl, cudaS
     return cudaLaunchKernelEx(&cfg, advance_cursor_kernel, cursor, step);
 }
 
-int max_resident_blocks(bool metro, int nw, int block) {
+template <int NW, bool METRO>
+static int occupancy(bool rc, int block) {
     int n = 0;
-    cudaError_t e;
-    if (metro)
-        e = nw == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, half_sweep_kernel<4, true>, block, 0)
-          : nw == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, half_sweep_kernel<2, true>, block, 0)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, half_sweep_kernel<1, true>, block, 0);
-    else
-        e = nw == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, half_sweep_kernel<4, false>, block, 0)
-          : nw == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, half_sweep_kernel<2, false>, block, 0)
-                    : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, half_sweep_kernel<1, false>, block, 0);
+    const cudaError_t e = rc ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, half_sweep_kernel_rc<NW, METRO>, block, 0)
+                             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, half_sweep_kernel<NW, METRO>, block, 0);
     return e == cudaSuccess ? n : 0;
+}
+
+int max_resident_blocks(bool metro, int nw, int block, bool regcap) {
+    if (metro) return nw == 4 ? occupancy<4, true>(regcap, block) : nw == 2 ? occupancy<2, true>(regcap, block)
+                                                                   : occupancy<1, true>(regcap, block);
+    return nw == 4 ? occupancy<4, false>(regcap, block) : nw == 2 ? occupancy<2, false>(regcap, block)
+                                                        : occupancy<1, false>(regcap, block);
 }
 
 }  // namespace micsa

@@ -90,13 +90,12 @@ class Server:
             if live:
                 self.pool.tick()
                 self.pool.wait_ticks(self.max_pending)
-                for jid in list(live):
+                for jid in self.pool.finished():
                     res = self.pool.poll(jid, best_spins=self.keep_spins)
-                    if res is not None:
-                        r = live.pop(jid)
-                        r.done = time.perf_counter() - t0
-                        r.result = res
-                        done.append(r)
+                    r = live.pop(jid)
+                    r.done = time.perf_counter() - t0
+                    r.result = res
+                    done.append(r)
             elif i < len(pending):
                 time.sleep(max(0.0, min(pending[i].arrival - now, 0.01)))
         self.wall = time.perf_counter() - t0

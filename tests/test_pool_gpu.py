@@ -114,6 +114,21 @@ def test_admission_is_limited_by_arena_memory():
         assert p.stats()["live_jobs"] == 0
 
 
+def test_finished_lists_exactly_the_completed_jobs():
+    with micsa.Pool(1 << 26, 8, 16) as p:
+        short = p.submit(8, 1, 1, 16, 4, 2.0, 1.0)   # one tick
+        long_ = p.submit(34, 1, 2, 64, 4, 2.0, 1.0)  # four ticks (streaming part)
+        p.tick()
+        p.wait()
+        assert p.finished() == [short]
+        assert p.poll(short) is not None and p.poll(long_) is None
+        for _ in range(3):
+            p.tick()
+        p.wait()
+        assert p.finished() == [long_]
+        assert p.poll(long_)["sweeps_done"] == 64
+
+
 def test_pool_rejects_bad_jobs():
     with micsa.Pool(1 << 24, 4, 8) as p:
         with pytest.raises(micsa.MicsaError):
