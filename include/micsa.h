@@ -68,6 +68,18 @@ typedef struct micsa_ctx *micsa_t;
  * first refresh; t = 0. *out receives the handle. 1 <= n_replicas <= 32. */
 int micsa_create(int L, int n_samples, int n_replicas, uint64_t seed, micsa_t *out);
 
+/* As micsa_create with gamma (1..8) daemons per spin, or walkers if walkers != 0
+ * (Sec. 2.6, 2.8): a timestep is gamma sweeps, sweep alpha uses daemon family
+ * alpha, and with walkers every timestep t ends with the wandering step of
+ * parity t & 1 for each family, direction alpha mod 6 in the order +x, +y, +z,
+ * -x, -y, -z. micsa_run and micsa_run_logrefresh then count timesteps (t is the
+ * timestep index; a refresh draws all gamma families, family alpha with Philox
+ * id gid * gamma + alpha); daemons in micsa_get_state / micsa_set_state are
+ * [S][R][gamma][N] and H_aux sums all families. The shared-memory engines need
+ * gamma == 1 without walkers; otherwise the streaming kernel runs. */
+int micsa_create_ex(int L, int n_samples, int n_replicas, int gamma, int walkers, uint64_t seed,
+                    micsa_t *out);
+
 /* Start over on the resident memory: redraw couplings and spins from `seed`
  * exactly as micsa_create does, zero the daemons, set t = 0. Asynchronous on
  * the handle's stream; no host data moves. */

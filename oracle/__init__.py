@@ -39,6 +39,9 @@ def _declare(lib):
                               _c_i64p, _f64p, c.c_int64, c.c_int32, c.c_int]),
         "orc_run_logrefresh": (c.c_int, [c.c_int, c.c_int, c.c_int, c.c_uint64, _i8p, _i8p,
                                          _u8p, _c_i64p, _f64p, c.c_int64]),
+        "orc_wander": (None, [c.c_int, _u8p, c.c_int, c.c_int]),
+        "orc_run_ex": (c.c_int, [c.c_int, c.c_int, c.c_int, c.c_int, c.c_int, c.c_uint64, _i8p, _i8p,
+                                 _u8p, _c_i64p, _f64p, c.c_int64, c.c_int32]),
         "orc_run_metropolis": (c.c_int, [c.c_int, c.c_int, c.c_int, c.c_uint64, _i8p, _i8p,
                                          _c_i64p, _f64p, c.c_int64, c.c_int]),
         "orc_measure": (None, [c.c_int, c.c_int, c.c_int, _i8p, _i8p, _u8p,
@@ -116,13 +119,30 @@ class Oracle:
     def serial_sweep(self, L, J, s, m):
         self.lib.orc_serial_sweep(L, J, s, m)
 
-    def create(self, L, S, R, seed):
-        """Initial state of micsa_create: couplings and spins from the seed, t = 0."""
+    def create(self, L, S, R, seed, gamma=1, walkers=False):
+        """Initial state of micsa_create: couplings and spins from the seed, t = 0.
+        With gamma > 1 the daemons are m[S, R, gamma, N]."""
         N = L ** 3
         J = np.stack([self.couplings(L, seed, a) for a in range(S)])
         s = np.stack([self.spins(L, seed, g) for g in range(S * R)]).reshape(S, R, N)
-        m = np.zeros((S, R, N), np.uint8)
-        return {"L": L, "S": S, "R": R, "seed": seed, "J": J, "s": s, "m": m, "t": 0}
+        m = np.zeros((S, R, N) if gamma == 1 else (S, R, gamma, N), np.uint8)
+        return {"L": L, "S": S, "R": R, "seed": seed, "J": J, "s": s, "m": m, "t": 0,
+                "gamma": gamma, "walkers": bool(walkers)}
+
+    def wander(self, L, m, direction, parity):
+        self.lib.orc_wander(L, m, int(direction), int(parity))
+
+    def run_ex(self, st, schedule, interval):
+        """gamma daemons / walkers per spin (interval 0: the log refresh schedule)."""
+        sched = np.ascontiguousarray(schedule, np.float64)
+        t = ctypes.c_int64(st["t"])
+        rc = self.lib.orc_run_ex(st["L"], st["S"], st["R"], st.get("gamma", 1), int(st.get("walkers", False)),
+                                 st["seed"], st["J"], st["s"], st["m"], ctypes.byref(t), sched, len(sched),
+                                 int(interval))
+        if rc:
+            raise ValueError("orc_run_ex rejected its arguments")
+        st["t"] = t.value
+        return st
 
     def run(self, st, schedule, interval, serial=False):
         sched = np.ascontiguousarray(schedule, np.float64)
@@ -160,8 +180,13 @@ class Oracle:
         e = np.zeros(S * R, np.int64)
         a = np.zeros(S * R, np.int64)
         q = np.zeros(max(1, S * R * (R - 1) // 2), np.int64)
-        self.lib.orc_measure(st["L"], S, R, st["J"], st["s"], st["m"],
+        m = st["m"]
+        gamma = st.get("gamma", 1)
+        m0 = m if gamma == 1 else np.ascontiguousarray(m[:, :, 0, :])
+        self.lib.orc_measure(st["L"], S, R, st["J"], st["s"], m0,
                              e.ctypes.data, a.ctypes.data, q.ctypes.data)
+        if gamma > 1:  # H_aux sums every daemon of every family
+            a = 4 * m.reshape(S * R, -1).astype(np.int64).sum(axis=1)
         return e, a, q[: S * R * (R - 1) // 2]
 
     # -- exact enumeration ---------------------------------------------------

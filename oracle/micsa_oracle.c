@@ -299,6 +299,54 @@ int orc_run_logrefresh(int L, int S, int R, uint64_t seed, const int8_t *J, int8
     return 0;
 }
 
+/* ------------------------------------------------- daemons and walkers -- */
+
+static const int DIR_DX[6] = {1, 0, 0, -1, 0, 0};
+static const int DIR_DY[6] = {0, 1, 0, 0, -1, 0};
+static const int DIR_DZ[6] = {0, 0, 1, 0, 0, -1};
+
+void orc_wander(int L, uint8_t *m, int dir, int parity) {
+    for (int z = 0; z < L; ++z)
+        for (int y = 0; y < L; ++y)
+            for (int x = 0; x < L; ++x) {
+                if (((x + y + z) & 1) != parity) continue;
+                int64_t a = site_of(L, x, y, z);
+                int64_t b = site_of(L, wrap(x + DIR_DX[dir], L), wrap(y + DIR_DY[dir], L),
+                                    wrap(z + DIR_DZ[dir], L));
+                uint8_t tmp = m[a];
+                m[a] = m[b];
+                m[b] = tmp;
+            }
+}
+
+int orc_run_ex(int L, int S, int R, int gamma, int walkers, uint64_t seed, const int8_t *J, int8_t *s,
+               uint8_t *m, int64_t *t_io, const double *schedule, int64_t n_steps, int32_t interval) {
+    if (check_args(L, S, R, n_steps, 0) || gamma < 1 || interval < 0) return -1;
+    int64_t N = (int64_t)L * L * L;
+    for (int64_t k = 0; k < n_steps; ++k) {
+        int64_t t = *t_io + k;
+        int refresh = interval > 0 ? (t % interval == 0) : is_log_refresh_time(t);
+        for (int a = 0; a < S; ++a)
+            for (int r = 0; r < R; ++r) {
+                int64_t gid = (int64_t)a * R + r;
+                const int8_t *Ja = J + (int64_t)a * N * 3;
+                int8_t *sr = s + gid * N;
+                uint8_t *mr = m + gid * gamma * N;  /* daemon alpha at mr + alpha * N */
+                if (refresh)
+                    for (int al = 0; al < gamma; ++al)
+                        if (orc_refresh(L, seed, gid * gamma + al, t, schedule[k], mr + al * N)) return -1;
+                for (int al = 0; al < gamma; ++al) {
+                    orc_half_sweep(L, Ja, sr, mr + al * N, 0);
+                    orc_half_sweep(L, Ja, sr, mr + al * N, 1);
+                }
+                if (walkers)
+                    for (int al = 0; al < gamma; ++al) orc_wander(L, mr + al * N, al % 6, (int)(t & 1));
+            }
+    }
+    *t_io += n_steps;
+    return 0;
+}
+
 /* ---------------------------------------------------------- Metropolis -- */
 
 static void metro_move(int L, uint64_t seed, int64_t gid, int64_t t, const uint64_t theta[3],

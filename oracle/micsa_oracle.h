@@ -93,6 +93,22 @@ int orc_run(int L, int S, int R, uint64_t seed, const int8_t *J, int8_t *s, uint
 int orc_run_logrefresh(int L, int S, int R, uint64_t seed, const int8_t *J, int8_t *s,
                        uint8_t *m, int64_t *t_io, const double *schedule, int64_t n_sweeps);
 
+/* Wandering of one family of walkers (Sec. 2.6): every site of the given parity
+ * exchanges its walker with the one on its nearest neighbour in direction dir
+ * (0: +x, 1: +y, 2: +z, 3: -x, 4: -y, 5: -z), periodic. m: [N], even L. */
+void orc_wander(int L, uint8_t *m, int dir, int parity);
+
+/* The procedure of Sec. 2.8 with gamma daemons or walkers per spin. A timestep is
+ * gamma sweeps; sweep alpha uses daemon alpha (even sites, then odd sites).
+ * With walkers != 0 every timestep ends with the wandering step of parity
+ * t & 1 for each family alpha, direction alpha mod 6 in the order +x, +y, +z,
+ * -x, -y, -z (the table of Sec. 2.8). Refresh before timestep t iff
+ * t % interval == 0, or, for interval == 0, iff t = 2^s - 1; all gamma daemons
+ * are drawn, daemon alpha with gid' = gid * gamma + alpha in the counter.
+ * m: [S][R][gamma][N]; schedule[k] is the temperature of timestep k. */
+int orc_run_ex(int L, int S, int R, int gamma, int walkers, uint64_t seed, const int8_t *J, int8_t *s,
+               uint8_t *m, int64_t *t_io, const double *schedule, int64_t n_steps, int32_t interval);
+
 /* Checkerboard Metropolis at T = schedule[k] for sweep k, drawing one uniform
  * per update attempt with dE > 0. Same layout as orc_run; no daemons. */
 int orc_run_metropolis(int L, int S, int R, uint64_t seed, const int8_t *J, int8_t *s,

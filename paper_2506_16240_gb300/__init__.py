@@ -50,6 +50,8 @@ _ip = ctypes.POINTER(ctypes.c_int)
 # name -> (restype, argtypes); every symbol of include/micsa.h
 SIGNATURES = {
     "micsa_create": (_c.c_int, [_c.c_int, _c.c_int, _c.c_int, _c.c_uint64, ctypes.POINTER(_P)]),
+    "micsa_create_ex": (_c.c_int, [_c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_int, _c.c_uint64,
+                                   ctypes.POINTER(_P)]),
     "micsa_reinit": (_c.c_int, [_P, _c.c_uint64]),
     "micsa_set_couplings": (_c.c_int, [_P, _P]),
     "micsa_get_couplings": (_c.c_int, [_P, _P]),
@@ -133,11 +135,16 @@ def measure_noalloc(spins_ptr, daemons_ptr, J_ptr, L, n_samples, n_replicas, str
 class Micsa:
     """One handle of the C ABI: S disorder samples x R replicas of an L^3 lattice."""
 
-    def __init__(self, L, n_samples=1, n_replicas=2, seed=0, stream=None):
+    def __init__(self, L, n_samples=1, n_replicas=2, seed=0, stream=None, gamma=1, walkers=False):
         self.L, self.S, self.R, self.seed = int(L), int(n_samples), int(n_replicas), int(seed)
+        self.gamma, self.walkers = int(gamma), bool(walkers)
         self.N = self.L ** 3
         h = ctypes.c_void_p()
-        rc = lib().micsa_create(self.L, self.S, self.R, ctypes.c_uint64(self.seed), ctypes.byref(h))
+        if self.gamma == 1 and not self.walkers:
+            rc = lib().micsa_create(self.L, self.S, self.R, ctypes.c_uint64(self.seed), ctypes.byref(h))
+        else:
+            rc = lib().micsa_create_ex(self.L, self.S, self.R, self.gamma, int(self.walkers),
+                                       ctypes.c_uint64(self.seed), ctypes.byref(h))
         if rc != MICSA_OK:
             raise MicsaError(rc, f"micsa_create(L={L}, S={n_samples}, R={n_replicas})")
         self.h = h
@@ -203,7 +210,7 @@ class Micsa:
 
     def get_state(self):
         s = np.zeros((self.S, self.R, self.N), np.int8)
-        m = np.zeros((self.S, self.R, self.N), np.uint8)
+        m = np.zeros((self.S, self.R, self.N) if self.gamma == 1 else (self.S, self.R, self.gamma, self.N), np.uint8)
         t = ctypes.c_int64()
         _check(lib().micsa_get_state(self.h, _ptr(s), _ptr(m), ctypes.byref(t)), self.h)
         return s, m, t.value

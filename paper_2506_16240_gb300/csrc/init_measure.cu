@@ -178,7 +178,7 @@ cudaError_t launch_convert_sites(uint8_t *split, uint8_t *natural, Geometry g, i
 // quantity into out = [energy S*R | aux S*R | overlap S*R(R-1)/2].
 __global__ void __launch_bounds__(256) measure_kernel(const int8_t *spins, const uint8_t *daemons,
                                                       const uint8_t *bonds, Geometry g, int S, int R,
-                                                      unsigned long long *out) {
+                                                      int gamma, unsigned long long *out) {
     extern __shared__ long long acc[];  // [2R + R(R-1)/2]
     const int npair = R * (R - 1) / 2;
     const int nq = 2 * R + npair;
@@ -231,9 +231,12 @@ __global__ void __launch_bounds__(256) measure_kernel(const int8_t *spins, const
             const uint32_t u32 = unsatisfied32(negative_terms(bp, xp[0], xm[0], Oyp, Oym, Ozp, Ozm), S0) & valid;
             const uint32_t usum = ((u32 >> 5) * 0x01010101u) >> 24;  // sum of the four lanes
             e_part = 2 * (int)usum - 6 * nvalid;
-            const uint32_t D0 = *reinterpret_cast<const uint32_t *>(daemons + (gid * 2) * g.half + off_c);
-            const uint32_t D1 = *reinterpret_cast<const uint32_t *>(daemons + (gid * 2 + 1) * g.half + off_c);
-            a_part = 4 * (int)((((D0 & valid) * 0x01010101u) >> 24) + (((D1 & valid) * 0x01010101u) >> 24));
+            for (int al = 0; al < gamma; ++al) {  // every daemon family (Sec. 2.2: H_aux sums them all)
+                const int64_t fam = gid * gamma + al;
+                const uint32_t D0 = *reinterpret_cast<const uint32_t *>(daemons + (fam * 2) * g.half + off_c);
+                const uint32_t D1 = *reinterpret_cast<const uint32_t *>(daemons + (fam * 2 + 1) * g.half + off_c);
+                a_part += 4 * (int)((((D0 & valid) * 0x01010101u) >> 24) + (((D1 & valid) * 0x01010101u) >> 24));
+            }
         }
         e_part = __reduce_add_sync(0xFFFFFFFFu, e_part);
         a_part = __reduce_add_sync(0xFFFFFFFFu, a_part);
@@ -272,11 +275,11 @@ __global__ void __launch_bounds__(256) measure_kernel(const int8_t *spins, const
 }
 
 cudaError_t launch_measure(const int8_t *spins, const uint8_t *daemons, const uint8_t *bonds,
-                           Geometry g, int S, int R, unsigned long long *out, cudaStream_t st) {
+                           Geometry g, int S, int R, int gamma, unsigned long long *out, cudaStream_t st) {
     const int64_t words = (int64_t)g.L * g.L * g.W;
     const int nq = 2 * R + R * (R - 1) / 2;
     dim3 grid(blocks_for(words, 256), (unsigned)S);
-    measure_kernel<<<grid, 256, sizeof(long long) * nq, st>>>(spins, daemons, bonds, g, S, R, out);
+    measure_kernel<<<grid, 256, sizeof(long long) * nq, st>>>(spins, daemons, bonds, g, S, R, gamma, out);
     return cudaGetLastError();
 }
 

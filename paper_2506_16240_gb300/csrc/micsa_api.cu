@@ -16,6 +16,8 @@ using namespace micsa;
 
 struct micsa_ctx {
     int L = 0, S = 0, R = 0;
+    int gamma = 1;       // daemons (or walkers) per spin; a timestep is gamma sweeps
+    int walkers = 0;     // walkers wander after every timestep (Sec. 2.6)
     uint64_t seed = 0;
     int64_t t = 0;
     Geometry geo{};
@@ -120,6 +122,7 @@ SweepArgs sweep_args(const micsa_ctx *h) {
     a.geo = h->geo;
     a.S = h->S;
     a.R = h->R;
+    a.gamma = h->gamma;
     a.key0 = (uint32_t)(h->seed & 0xFFFFFFFFu);
     a.key1 = (uint32_t)(h->seed >> 32);
     return a;
@@ -208,7 +211,7 @@ int capture_graph(micsa_t h, bool metro, int G, const LaunchConfig &lc) {
 
 // The engine a MicSA run uses now.
 int active_engine(micsa_t h) {
-    if (!h->d_units || h->engine == MICSA_ENGINE_STREAM) return MICSA_ENGINE_STREAM;
+    if (!h->d_units || h->engine == MICSA_ENGINE_STREAM || h->gamma > 1 || h->walkers) return MICSA_ENGINE_STREAM;
     if (h->engine == MICSA_ENGINE_RESIDENT) return MICSA_ENGINE_RESIDENT;
     if (multispin_smem_bytes(h->geo) > 0) return MICSA_ENGINE_MULTISPIN;
     return h->engine == MICSA_ENGINE_MULTISPIN ? MICSA_ENGINE_STREAM : MICSA_ENGINE_RESIDENT;
@@ -295,7 +298,7 @@ bool schedule_ok(micsa_t h, const double *schedule, int64_t n_sweeps) {
 // Couplings and spins from the seed (Sec. 2.1 and the disordered start of
 // Sec. 3), daemons zero, t = 0.
 int init_from_seed(micsa_t h, uint64_t seed) {
-    const size_t state = (size_t)h->S * h->R * 2 * h->geo.half;
+    const size_t state = (size_t)h->S * h->R * h->gamma * 2 * h->geo.half;
     const uint32_t k0 = (uint32_t)(seed & 0xFFFFFFFFu), k1 = (uint32_t)(seed >> 32);
     h->seed = seed;
     CK(h, cudaMemsetAsync(h->d_daemons, 0, state, h->stream), "memset daemons");
@@ -306,30 +309,69 @@ int init_from_seed(micsa_t h, uint64_t seed) {
     return MICSA_OK;
 }
 
-// MicSA run with refresh before sweep t iff is_refresh(t) (Sec. 2.7, 2.8).
+// Timesteps with gamma daemon families or walkers (Sec. 2.8): sweep alpha of
+// timestep k is table entry k * gamma + alpha; walkers wander after the last
+// sweep of each timestep. Direct launches.
+int run_families(micsa_t h, int64_t n_steps, const LaunchConfig &lc) {
+    SweepArgs a = sweep_args(h);
+    a.params = h->d_params;
+    a.cursor = nullptr;
+    for (int64_t k = 0; k < n_steps; ++k) {
+        for (int al = 0; al < h->gamma; ++al)
+            for (int p = 0; p < 2; ++p) {
+                a.k = k * h->gamma + al;
+                a.parity = p;
+                CK(h, launch_half_sweep(a, false, lc, h->stream), "half-sweep launch");
+                ++h->launches;
+            }
+        if (h->walkers) {
+            const int parity = (int)((h->t + k) & 1);
+            CK(h, launch_wander(h->d_daemons, h->geo, (int64_t)h->S * h->R, h->gamma, parity, h->stream),
+               "wander launch");
+            ++h->launches;
+        }
+    }
+    return MICSA_OK;
+}
+
+// MicSA run of n_steps timesteps with refresh before timestep t iff
+// is_refresh(t) (Sec. 2.7, 2.8); a timestep is gamma sweeps.
 template <class IsRefresh>
 int run_micsa(micsa_t h, const double *schedule, int64_t n_sweeps, IsRefresh is_refresh) {
     if (!h) return MICSA_E_INVALID_ARG;
     if (!schedule_ok(h, schedule, n_sweeps)) return MICSA_E_INVALID_ARG;
     if (n_sweeps == 0) return MICSA_OK;
     DeviceGuard dg(h->device);
-    if (int rc = ensure_params(h, n_sweeps)) return rc;
+    const int G = h->gamma;
+    if (int rc = ensure_params(h, n_sweeps * G)) return rc;
     double last_T = -1.0;
     uint64_t th[3] = {0, 0, 0};
     for (int64_t k = 0; k < n_sweeps; ++k) {
-        SweepParam &q = h->h_params[k];
-        q.t = h->t + k;
-        q.mode = is_refresh(q.t) ? kModeRefresh : kModeMicsa;
-        if (q.mode == kModeRefresh && schedule[k] != last_T) {
+        const int64_t t = h->t + k;
+        const int mode = is_refresh(t) ? kModeRefresh : kModeMicsa;
+        if (mode == kModeRefresh && schedule[k] != last_T) {
             micsa_daemon_thresholds(schedule[k], th);
             last_T = schedule[k];
         }
-        q.th0 = th[0];
-        q.th1 = th[1];
-        q.th2 = th[2];
-        q.pad = 0;
+        for (int al = 0; al < G; ++al) {
+            SweepParam &q = h->h_params[k * G + al];
+            q.t = t;
+            q.mode = mode;
+            q.th0 = th[0];
+            q.th1 = th[1];
+            q.th2 = th[2];
+            q.alpha = al;
+        }
     }
-    if (int rc = run_table(h, false, n_sweeps)) return rc;
+    if (G == 1 && !h->walkers) {
+        if (int rc = run_table(h, false, n_sweeps)) return rc;
+    } else {
+        const LaunchConfig lc = effective_config(h, false);
+        CK(h, cudaMemcpyAsync(h->d_params, h->h_params, sizeof(SweepParam) * (size_t)(n_sweeps * G),
+                              cudaMemcpyHostToDevice, h->stream), "upload sweep parameters");
+        CK(h, cudaEventRecord(h->params_free, h->stream), "record parameter event");
+        if (int rc = run_families(h, n_sweeps, lc)) return rc;
+    }
     h->t += n_sweeps;
     return MICSA_OK;
 }
@@ -394,16 +436,22 @@ void micsa_destroy(micsa_t h) {
 }
 
 int micsa_create(int L, int n_samples, int n_replicas, uint64_t seed, micsa_t *out) {
+    return micsa_create_ex(L, n_samples, n_replicas, 1, 0, seed, out);
+}
+
+int micsa_create_ex(int L, int n_samples, int n_replicas, int gamma, int walkers, uint64_t seed, micsa_t *out) {
     if (!out) return MICSA_E_INVALID_ARG;
     *out = nullptr;
-    if (L < 2 || L > 1600 || (L & 1) || n_samples < 1 || n_replicas < 1 || n_replicas > 32 ||
-        (int64_t)n_samples * n_replicas >= (1ll << 30))
+    if (L < 2 || L > 1600 || (L & 1) || n_samples < 1 || n_replicas < 1 || n_replicas > 32 || gamma < 1 ||
+        gamma > 8 || (int64_t)n_samples * n_replicas * gamma >= (1ll << 30))
         return MICSA_E_INVALID_ARG;
     micsa_ctx *h = new (std::nothrow) micsa_ctx;
     if (!h) return MICSA_E_OOM;
     h->L = L;
     h->S = n_samples;
     h->R = n_replicas;
+    h->gamma = gamma;
+    h->walkers = walkers ? 1 : 0;
     h->seed = seed;
     h->geo = make_geometry(L);
     int rc = MICSA_OK;
@@ -417,10 +465,11 @@ int micsa_create(int L, int n_samples, int n_replicas, uint64_t seed, micsa_t *o
         if ((e = cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device)) != cudaSuccess) { rc = cuda_fail(h, e, "SM count"); break; }
         if ((e = cudaMalloc(&h->d_cursor, sizeof(int64_t))) != cudaSuccess) { rc = cuda_fail(h, e, "cudaMalloc cursor"); break; }
         const size_t state = (size_t)h->S * h->R * 2 * h->geo.half;
+        const size_t dstate = state * (size_t)h->gamma;
         const size_t bonds = (size_t)h->S * 2 * h->geo.half;
         const size_t meas = sizeof(unsigned long long) * ((size_t)2 * h->S * h->R + (size_t)h->S * h->R * (h->R - 1) / 2);
         if ((e = cudaMalloc(&h->d_spins, state)) != cudaSuccess) { rc = cuda_fail(h, e, "cudaMalloc spins"); break; }
-        if ((e = cudaMalloc(&h->d_daemons, state)) != cudaSuccess) { rc = cuda_fail(h, e, "cudaMalloc daemons"); break; }
+        if ((e = cudaMalloc(&h->d_daemons, dstate)) != cudaSuccess) { rc = cuda_fail(h, e, "cudaMalloc daemons"); break; }
         if ((e = cudaMalloc(&h->d_bonds, bonds)) != cudaSuccess) { rc = cuda_fail(h, e, "cudaMalloc bonds"); break; }
         if ((e = cudaMalloc(&h->d_meas, meas)) != cudaSuccess) { rc = cuda_fail(h, e, "cudaMalloc measure"); break; }
         if (resident_smem_bytes(h->geo) > 0) {
@@ -434,9 +483,9 @@ int micsa_create(int L, int n_samples, int n_replicas, uint64_t seed, micsa_t *o
             if ((e = cudaMalloc(&h->d_units, sizeof(ResidentUnit) * units.size())) != cudaSuccess) { rc = cuda_fail(h, e, "cudaMalloc units"); break; }
             if ((e = cudaMemcpy(h->d_units, units.data(), sizeof(ResidentUnit) * units.size(), cudaMemcpyHostToDevice)) != cudaSuccess) { rc = cuda_fail(h, e, "upload units"); break; }
         }
-        h->device_bytes = 2 * state + bonds + meas;
+        h->device_bytes = state + dstate + bonds + meas;
         if ((e = cudaMemsetAsync(h->d_spins, 0, state, h->stream)) != cudaSuccess ||
-            (e = cudaMemsetAsync(h->d_daemons, 0, state, h->stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(h->d_daemons, 0, dstate, h->stream)) != cudaSuccess ||
             (e = cudaMemsetAsync(h->d_bonds, 0, bonds, h->stream)) != cudaSuccess) { rc = cuda_fail(h, e, "cudaMemset"); break; }
         if ((rc = init_from_seed(h, seed)) != MICSA_OK) break;
         if ((e = cudaStreamSynchronize(h->stream)) != cudaSuccess) { rc = cuda_fail(h, e, "create synchronize"); break; }
@@ -508,6 +557,7 @@ int micsa_run_metropolis(micsa_t h, const double *schedule, int64_t n_sweeps) {
         SweepParam &q = h->h_params[k];
         q.t = h->t + k;
         q.mode = kModeMetro;
+        q.alpha = 0;
         if (schedule[k] != last_T) {
             micsa_metro_thresholds(schedule[k], th);
             last_T = schedule[k];
@@ -515,7 +565,6 @@ int micsa_run_metropolis(micsa_t h, const double *schedule, int64_t n_sweeps) {
         q.th0 = th[0];
         q.th1 = th[1];
         q.th2 = th[2];
-        q.pad = 0;
     }
     if (int rc = run_table(h, true, n_sweeps)) return rc;
     h->t += n_sweeps;
@@ -583,7 +632,7 @@ int micsa_measure(micsa_t h, int64_t *energy, int64_t *aux, int64_t *overlap) {
     const size_t npair = (size_t)h->S * h->R * (h->R - 1) / 2;
     const size_t n = 2 * SR + npair;
     CK(h, cudaMemsetAsync(h->d_meas, 0, n * sizeof(unsigned long long), h->stream), "memset measure");
-    CK(h, launch_measure(h->d_spins, h->d_daemons, h->d_bonds, h->geo, h->S, h->R, h->d_meas, h->stream), "measure launch");
+    CK(h, launch_measure(h->d_spins, h->d_daemons, h->d_bonds, h->geo, h->S, h->R, h->gamma, h->d_meas, h->stream), "measure launch");
     ++h->launches;
     std::vector<long long> host(n);
     CK(h, cudaMemcpyAsync(host.data(), h->d_meas, n * sizeof(long long), cudaMemcpyDeviceToHost, h->stream), "copy measure");
@@ -599,8 +648,9 @@ int micsa_get_state(micsa_t h, int8_t *spins, uint8_t *daemons, int64_t *t) {
     DeviceGuard dg(h->device);
     const int64_t n = (int64_t)h->S * h->R;
     const size_t bytes = (size_t)(n * sites(h));
+    const size_t dbytes = bytes * (size_t)h->gamma;
     if (spins || daemons) {
-        if (int rc = ensure_stage(h, bytes)) return rc;
+        if (int rc = ensure_stage(h, dbytes)) return rc;
     }
     if (spins) {
         CK(h, launch_convert_sites(reinterpret_cast<uint8_t *>(h->d_spins), h->d_stage, h->geo, n, false, h->stream), "gather spins");
@@ -609,9 +659,9 @@ int micsa_get_state(micsa_t h, int8_t *spins, uint8_t *daemons, int64_t *t) {
         CK(h, cudaStreamSynchronize(h->stream), "get_state synchronize");
     }
     if (daemons) {
-        CK(h, launch_convert_sites(h->d_daemons, h->d_stage, h->geo, n, false, h->stream), "gather daemons");
+        CK(h, launch_convert_sites(h->d_daemons, h->d_stage, h->geo, n * h->gamma, false, h->stream), "gather daemons");
         ++h->launches;
-        CK(h, cudaMemcpyAsync(daemons, h->d_stage, bytes, cudaMemcpyDeviceToHost, h->stream), "copy daemons");
+        CK(h, cudaMemcpyAsync(daemons, h->d_stage, dbytes, cudaMemcpyDeviceToHost, h->stream), "copy daemons");
         CK(h, cudaStreamSynchronize(h->stream), "get_state synchronize");
     }
     if (t) *t = h->t;
@@ -623,15 +673,16 @@ int micsa_set_state(micsa_t h, const int8_t *spins, const uint8_t *daemons, int6
     if (t < 0) return fail(h, MICSA_E_INVALID_ARG, "t must be >= 0");
     const int64_t n = (int64_t)h->S * h->R;
     const size_t bytes = (size_t)(n * sites(h));
+    const size_t dbytes = bytes * (size_t)h->gamma;
     if (spins)
         for (size_t i = 0; i < bytes; ++i)
             if (spins[i] != 1 && spins[i] != -1) return fail(h, MICSA_E_INVALID_ARG, "spins[%zu] = %d is not +-1", i, spins[i]);
     if (daemons)
-        for (size_t i = 0; i < bytes; ++i)
+        for (size_t i = 0; i < dbytes; ++i)
             if (daemons[i] > 3) return fail(h, MICSA_E_INVALID_ARG, "daemons[%zu] = %u exceeds 3", i, daemons[i]);
     DeviceGuard dg(h->device);
     if (spins || daemons) {
-        if (int rc = ensure_stage(h, bytes)) return rc;
+        if (int rc = ensure_stage(h, dbytes)) return rc;
     }
     if (spins) {
         CK(h, cudaMemcpyAsync(h->d_stage, spins, bytes, cudaMemcpyHostToDevice, h->stream), "copy spins");
@@ -640,8 +691,8 @@ int micsa_set_state(micsa_t h, const int8_t *spins, const uint8_t *daemons, int6
         CK(h, cudaStreamSynchronize(h->stream), "set_state synchronize");
     }
     if (daemons) {
-        CK(h, cudaMemcpyAsync(h->d_stage, daemons, bytes, cudaMemcpyHostToDevice, h->stream), "copy daemons");
-        CK(h, launch_convert_sites(h->d_daemons, h->d_stage, h->geo, n, true, h->stream), "scatter daemons");
+        CK(h, cudaMemcpyAsync(h->d_stage, daemons, dbytes, cudaMemcpyHostToDevice, h->stream), "copy daemons");
+        CK(h, launch_convert_sites(h->d_daemons, h->d_stage, h->geo, n * h->gamma, true, h->stream), "scatter daemons");
         ++h->launches;
         CK(h, cudaStreamSynchronize(h->stream), "set_state synchronize");
     }

@@ -17,7 +17,7 @@ struct SweepParam {
     int64_t t;               // global sweep index (Philox counter word)
     uint64_t th0, th1, th2;  // refresh (daemon) or Metropolis cut points
     int32_t mode;            // kModeMicsa or kModeRefresh; unused by Metropolis
-    int32_t pad;
+    int32_t alpha;           // daemon family used by this sweep (0 .. gamma-1)
 };
 
 struct SweepArgs {
@@ -26,6 +26,7 @@ struct SweepArgs {
     const uint8_t *bonds; // [S][2][half]
     Geometry geo;
     int S, R;
+    int gamma;                   // daemon families per spin (daemons: [S][R][gamma][2][half])
     int parity;
     uint32_t key0, key1;         // Philox key = seed
     const SweepParam *params;    // the run's table
@@ -146,6 +147,8 @@ size_t multispin_smem_bytes(const Geometry &g);  // 0 when L > 32
 cudaError_t launch_multispin(const ResidentArgs &a, bool pool, size_t smem, int grid, bool pdl, cudaStream_t st);
 int multispin_blocks_per_sm(bool pool, size_t smem);
 cudaError_t launch_advance_cursor(int64_t *cursor, int64_t step, bool pdl, cudaStream_t st);
+// wandering of every walker family after timestep t (parity t & 1), Sec. 2.6
+cudaError_t launch_wander(uint8_t *daemons, Geometry g, int64_t n_rep, int gamma, int parity, cudaStream_t st);
 int vector_words(const Geometry &g, int want);
 int max_resident_blocks(bool metro, int nw, int block, bool regcap);
 dim3 block_shape(int R, int block);
@@ -163,6 +166,6 @@ cudaError_t launch_unpack_couplings(int8_t *J_nat, const uint8_t *bonds, Geometr
 cudaError_t launch_convert_sites(uint8_t *split, uint8_t *natural, Geometry g, int64_t n,
                                  bool to_split, cudaStream_t st);
 cudaError_t launch_measure(const int8_t *spins, const uint8_t *daemons, const uint8_t *bonds,
-                           Geometry g, int S, int R, unsigned long long *out, cudaStream_t st);
+                           Geometry g, int S, int R, int gamma, unsigned long long *out, cudaStream_t st);
 
 }  // namespace micsa

@@ -44,10 +44,13 @@ __device__ __forceinline__ void half_sweep_body(const SweepArgs &a) {
                 const uint32_t row = fdiv(q, a.div_chunks);
                 const int c = (int)(q - row * a.div_chunks.d);
                 const int64_t gid = (int64_t)sample * a.R + r;
-                update_chunk<NW, METRO>(g, a.spins + gid * 2 * g.half, a.daemons + gid * 2 * g.half,
+                // daemon family alpha of this replica; its Philox id is gid * gamma + alpha
+                // (Metropolis draws use gid itself)
+                const int64_t fam = gid * a.gamma + prm.alpha;
+                update_chunk<NW, METRO>(g, a.spins + gid * 2 * g.half, a.daemons + fam * 2 * g.half,
                                         a.bonds + (int64_t)sample * 2 * g.half, a.parity, (int)row, c,
-                                        (uint32_t)gid, a.key0, a.key1, prm.t, refresh, prm.th0, prm.th1,
-                                        prm.th2, a.div_L);
+                                        (uint32_t)(METRO ? gid : fam), a.key0, a.key1, prm.t, refresh, prm.th0,
+                                        prm.th1, prm.th2, a.div_L);
             }
 }
 
@@ -61,6 +64,43 @@ __global__ void __launch_bounds__(256) half_sweep_kernel(SweepArgs a) {
 template <int NW, bool METRO>
 __global__ void __launch_bounds__(128, 8) half_sweep_kernel_rc(SweepArgs a) {
     half_sweep_body<NW, METRO>(a);
+}
+
+// Wandering (Sec. 2.6): every site of parity p exchanges the walker of family
+// alpha with its neighbour along direction alpha mod 6 (+x, +y, +z, -x, -y, -z,
+// the table of Sec. 2.8). One thread per (replica family, site of parity p);
+// each exchange pair belongs to exactly one thread, and the bytes are moved
+// one by one, so no two threads touch the same byte.
+__global__ void wander_kernel(uint8_t *daemons, Geometry g, int64_t n_fam, int gamma, int p) {
+    const int64_t per = (int64_t)g.L * g.L * g.Lh;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= per * n_fam) return;
+    const int64_t fam = tid / per;
+    const int64_t rem = tid - fam * per;
+    const int row = (int)(rem / g.Lh), i = (int)(rem - (int64_t)row * g.Lh);
+    const int y = row % g.L, z = row / g.L;
+    const int o = (p + y + z) & 1;
+    const int dir = (int)(fam % gamma) % 6;
+    int yn = y, zn = z, in = i;
+    switch (dir) {
+        case 0: in = o ? (i + 1 == g.Lh ? 0 : i + 1) : i; break;   // +x
+        case 1: yn = (y + 1 == g.L) ? 0 : y + 1; break;            // +y
+        case 2: zn = (z + 1 == g.L) ? 0 : z + 1; break;            // +z
+        case 3: in = o ? i : (i == 0 ? g.Lh - 1 : i - 1); break;   // -x
+        case 4: yn = (y == 0) ? g.L - 1 : y - 1; break;            // -y
+        default: zn = (z == 0) ? g.L - 1 : z - 1; break;           // -z
+    }
+    uint8_t *own = daemons + (fam * 2 + p) * g.half + (int64_t)row * g.P + i;
+    uint8_t *nb = daemons + (fam * 2 + (1 - p)) * g.half + ((int64_t)zn * g.L + yn) * g.P + in;
+    const uint8_t a = *own, b = *nb;
+    *own = b;
+    *nb = a;
+}
+
+cudaError_t launch_wander(uint8_t *daemons, Geometry g, int64_t n_rep, int gamma, int parity, cudaStream_t st) {
+    const int64_t n = (int64_t)g.L * g.L * g.Lh * n_rep * gamma;
+    wander_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(daemons, g, n_rep * gamma, gamma, parity);
+    return cudaGetLastError();
 }
 
 // Advance the graph replay cursor by `step` sweeps (the last node of a graph).

@@ -385,3 +385,80 @@ def test_planted_refresh_mistake_breaks_distribution():
     expected = counts.sum() * paper_daemon_probs(T)
     chi2 = ((counts - expected) ** 2 / expected).sum()
     assert chi2 > 100
+
+
+# ------------------------------------------- gamma daemons and walkers --
+
+def test_run_ex_reduces_to_gamma_one():
+    sched = np.linspace(2.5, 0.5, 45)
+    a = O.create(6, 2, 2, 41)
+    b = O.create(6, 2, 2, 41, gamma=1, walkers=False)
+    O.run(a, sched, 7)
+    O.run_ex(b, sched, 7)
+    np.testing.assert_array_equal(a["s"], b["s"])
+    np.testing.assert_array_equal(a["m"], b["m"])
+    c = O.create(6, 1, 2, 42)
+    d = O.create(6, 1, 2, 42)
+    O.run_logrefresh(c, sched)
+    O.run_ex(d, sched, 0)
+    np.testing.assert_array_equal(c["s"], d["s"])
+    np.testing.assert_array_equal(c["m"], d["m"])
+
+
+@pytest.mark.parametrize("direction", range(6))
+def test_wandering_cycle_moves_walkers_two_sites(direction):
+    """Sec. 2.6: in a two-timestep cycle the even sites, then the odd sites,
+    exchange their walker with the neighbour along the direction. A walker that
+    starts on an even site ends two sites on along the direction, one that
+    starts on an odd site two sites back; after L/2 cycles (L timesteps) every
+    walker is back where it started."""
+    L = 6
+    rng = np.random.default_rng(direction)
+    m0 = rng.integers(0, 4, L ** 3).astype(np.uint8)
+    m = m0.copy()
+    O.wander(L, m, direction, 0)
+    O.wander(L, m, direction, 1)
+    z, y, x = np.meshgrid(np.arange(L), np.arange(L), np.arange(L), indexing="ij")
+    even = ((x + y + z) % 2 == 0).reshape(-1)
+    step = np.zeros(3, int)
+    step[direction % 3] = 1 if direction < 3 else -1  # (dx, dy, dz)
+    expect = np.zeros_like(m0)
+    for site in range(L ** 3):
+        sz, sy, sx = np.unravel_index(site, (L, L, L))
+        k = 2 if even[site] else -2
+        tx, ty, tz = (sx + k * step[0]) % L, (sy + k * step[1]) % L, (sz + k * step[2]) % L
+        expect[(tz * L + ty) * L + tx] = m0[site]
+    np.testing.assert_array_equal(m, expect)
+    for _ in range(L // 2 - 1):
+        O.wander(L, m, direction, 0)
+        O.wander(L, m, direction, 1)
+    np.testing.assert_array_equal(m, m0)
+
+
+@pytest.mark.parametrize("gamma,walkers", [(3, False), (2, True), (6, True)])
+def test_total_energy_conserved_with_gamma_and_walkers(gamma, walkers):
+    st = O.create(4, 1, 2, 23, gamma=gamma, walkers=walkers)
+    totals = None
+    for _ in range(25):
+        O.run_ex(st, [1.2], 1000)
+        e, a, _ = O.measure(st)
+        if totals is None:
+            totals = e + a
+        np.testing.assert_array_equal(e + a, totals)
+
+
+@pytest.mark.parametrize("gamma,walkers", [(2, False), (1, True), (6, True)])
+def test_long_run_gamma_walkers_match_enumeration(gamma, walkers):
+    """Refreshes and sweeps leave the canonical measure of spins and all gamma
+    daemons invariant, and wandering only permutes daemons, so long-run averages
+    are canonical."""
+    L, N, T = 2, 8, 2.0
+    st = O.create(L, 1, 1, 900 + gamma, gamma=gamma, walkers=walkers)
+    exact = _exact_mean_energy(O.dos(L, st["J"][0]), N, T)
+    es = []
+    for k in range(600):
+        O.run_ex(st, np.full(40, T), 10)
+        if k >= 20:
+            es.append(O.measure(st)[0][0] / N)
+    mean, err = _batch_mean(es)
+    assert abs(mean - exact) < 5 * err + 1e-3, (mean, err, exact)

@@ -252,3 +252,21 @@ def test_autotuner_choice_keeps_results():
         O.run(st, np.linspace(2.0, 0.6, 30), 4)
         np.testing.assert_array_equal(s, st["s"])
         np.testing.assert_array_equal(m, st["m"])
+
+
+@pytest.mark.parametrize("L,S,R,gamma,walkers,interval", [
+    (4, 1, 2, 2, False, 3), (6, 2, 1, 3, True, 5), (8, 1, 2, 6, True, 4), (10, 1, 1, 1, True, 2),
+    (16, 1, 2, 4, False, 10), (18, 1, 1, 6, True, 7), (30, 1, 1, 2, True, 3), (32, 1, 2, 2, True, 10),
+])
+def test_gamma_daemons_and_walkers_bit_exact(L, S, R, gamma, walkers, interval):
+    """gamma daemon families per spin and walkers (Sec. 2.6, 2.8): every sweep,
+    refresh and wandering step matches the oracle bit for bit."""
+    seed = 17 * L + gamma
+    sched = np.linspace(2.4, 0.6, 30)
+    with micsa.Micsa(L, S, R, seed, gamma=gamma, walkers=walkers) as g:
+        st = O.create(L, S, R, seed, gamma=gamma, walkers=walkers)
+        g.run(sched[:20], interval)
+        O.run_ex(st, sched[:20], interval)
+        g.run_logrefresh(sched[20:])
+        O.run_ex(st, sched[20:], 0)
+        assert_same_state(g, st, f"gamma={gamma} walkers={walkers}")
