@@ -272,8 +272,10 @@ def leg_quench_l32(micsa, timer, stream):
         e, a, q = g.measure()
         series.append((tm, float(e.mean() / N), float(((q / N) ** 2).mean())))
     eng = g.engine()
+    c4 = g.c4().mean(axis=0)  # four-point correlation at t = 1e4, averaged over samples
     g.close()
     return {"value": updates(L, S, R, n) / (total_ms * 1e6), "unit": METRIC, "engine": eng, "launch": tuned,
+            "c4_final": [round(float(v), 6) for v in c4[: L // 2 + 1]],
             "workload": "L=32, 64 samples x 2 replicas, T=0.7, 1e4 sweeps, refresh every 10",
             "e_final": series[-1][1], "q2_final": series[-1][2],
             "e_q2_vs_t": [[t, round(e, 6), round(q2, 8)] for t, e, q2 in series[::4]] + [list(series[-1])]}

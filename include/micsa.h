@@ -118,6 +118,14 @@ int micsa_run_metropolis(micsa_t h, const double *schedule, int64_t n_sweeps);
  * Host arrays; any may be NULL. Synchronous. */
 int micsa_measure(micsa_t h, int64_t *energy, int64_t *aux, int64_t *overlap);
 
+/* Four-point correlation of Sec. 3 as exact integer sums: for each sample,
+ * G[sample*L + r] = sum over replica pairs a < b, the three lattice axes d and
+ * all sites x of q_x q_{x + r e_d}, with q_x = s^a_x s^b_x, periodic, r = 0..L-1.
+ * C4(r) = G / (3 N R(R-1)/2) (the paper's sum over a != b normalised by
+ * N R(R-1)/2 counts each unordered pair once, so that C4(0) = 1). Host array
+ * G[S][L]; needs R >= 2 and L <= 1024. Synchronous. */
+int micsa_correlation(micsa_t h, int64_t *G);
+
 /* Copy the state to / from host arrays in natural layout: spins[S*R*N] int8
  * +-1, daemons[S*R*N] uint8 in {0..3}, and the global sweep index t. Any
  * pointer may be NULL (that part is skipped). set_state validates values. */

@@ -46,6 +46,7 @@ def _declare(lib):
                                          _c_i64p, _f64p, c.c_int64, c.c_int]),
         "orc_measure": (None, [c.c_int, c.c_int, c.c_int, _i8p, _i8p, _u8p,
                                c.c_void_p, c.c_void_p, c.c_void_p]),
+        "orc_correlation": (c.c_int, [c.c_int, c.c_int, c.c_int, _i8p, _i64p]),
         "orc_enumerate_dos": (c.c_int, [c.c_int, _i8p, _i64p]),
         "orc_all_energies": (c.c_int, [c.c_int, _i8p, _i64p]),
         "orc_l2_transition_micsa": (c.c_int, [_i8p, _f64p, _f64p]),
@@ -188,6 +189,13 @@ class Oracle:
         if gamma > 1:  # H_aux sums every daemon of every family
             a = 4 * m.reshape(S * R, -1).astype(np.int64).sum(axis=1)
         return e, a, q[: S * R * (R - 1) // 2]
+
+    def correlation(self, st):
+        """G[S, L]: sum over pairs, axes and sites of q_x q_{x + r e_d} (Sec. 3)."""
+        G = np.zeros((st["S"], st["L"]), np.int64)
+        if self.lib.orc_correlation(st["L"], st["S"], st["R"], np.ascontiguousarray(st["s"], np.int8), G):
+            raise ValueError("correlation needs two replicas or more")
+        return G
 
     # -- exact enumeration ---------------------------------------------------
     def dos(self, L, J):

@@ -420,6 +420,35 @@ void orc_measure(int L, int S, int R, const int8_t *J, const int8_t *s, const ui
     }
 }
 
+/* --------------------------------------------------------- correlation -- */
+
+int orc_correlation(int L, int S, int R, const int8_t *s, int64_t *G) {
+    if (R < 2) return -1;
+    int64_t N = (int64_t)L * L * L;
+    for (int a = 0; a < S; ++a) {
+        int64_t *Ga = G + (int64_t)a * L;
+        for (int r = 0; r < L; ++r) Ga[r] = 0;
+        for (int ra = 0; ra < R; ++ra)
+            for (int rb = ra + 1; rb < R; ++rb) {
+                const int8_t *sa = s + ((int64_t)a * R + ra) * N;
+                const int8_t *sb = s + ((int64_t)a * R + rb) * N;
+                for (int z = 0; z < L; ++z)
+                    for (int y = 0; y < L; ++y)
+                        for (int x = 0; x < L; ++x) {
+                            int64_t c = site_of(L, x, y, z);
+                            int qx = sa[c] * sb[c];
+                            for (int r = 0; r < L; ++r) {
+                                int64_t ex = site_of(L, wrap(x + r, L), y, z);
+                                int64_t ey = site_of(L, x, wrap(y + r, L), z);
+                                int64_t ez = site_of(L, x, y, wrap(z + r, L));
+                                Ga[r] += qx * (sa[ex] * sb[ex] + sa[ey] * sb[ey] + sa[ez] * sb[ez]);
+                            }
+                        }
+            }
+    }
+    return 0;
+}
+
 /* --------------------------------------------------------- enumeration -- */
 
 int orc_enumerate_dos(int L, const int8_t *J, int64_t *counts) {

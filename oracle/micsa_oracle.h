@@ -120,6 +120,12 @@ int orc_run_metropolis(int L, int S, int R, uint64_t seed, const int8_t *J, int8
 void orc_measure(int L, int S, int R, const int8_t *J, const int8_t *s, const uint8_t *m,
                  int64_t *energy, int64_t *aux, int64_t *overlap);
 
+/* Four-point correlation of Sec. 3, exact integer sums: for each sample,
+ * G[sample*L + r] = sum over replica pairs a < b, the three axes d and all
+ * sites x of q_x q_{x + r e_d}, q_x = s^a_x s^b_x, periodic, r = 0 .. L-1.
+ * C4(r) = G / (3 N R(R-1)/2). Requires R >= 2. */
+int orc_correlation(int L, int S, int R, const int8_t *s, int64_t *G);
+
 /* Exact enumeration of all 2^N spin states (N <= 30) by Gray code:
  * counts[E + 3N] = number of states with H_EA = E (density of states). */
 int orc_enumerate_dos(int L, const int8_t *J, int64_t *counts);

@@ -59,6 +59,7 @@ SIGNATURES = {
     "micsa_run_logrefresh": (_c.c_int, [_P, _P, _c.c_int64]),
     "micsa_run_metropolis": (_c.c_int, [_P, _P, _c.c_int64]),
     "micsa_measure": (_c.c_int, [_P, _P, _P, _P]),
+    "micsa_correlation": (_c.c_int, [_P, _P]),
     "micsa_get_state": (_c.c_int, [_P, _P, _P, _i64p]),
     "micsa_set_state": (_c.c_int, [_P, _P, _P, _c.c_int64]),
     "micsa_set_stream": (_c.c_int, [_P, _P]),
@@ -207,6 +208,16 @@ class Micsa:
         q = np.zeros(self.S * self.R * (self.R - 1) // 2, np.int64)
         _check(lib().micsa_measure(self.h, _ptr(e), _ptr(a), _ptr(q) if q.size else None), self.h)
         return e, a, q
+
+    def correlation(self):
+        """G[S, L] integer sums of the four-point correlation (Sec. 3)."""
+        G = np.zeros((self.S, self.L), np.int64)
+        _check(lib().micsa_correlation(self.h, _ptr(G)), self.h)
+        return G
+
+    def c4(self):
+        """C4(r) per sample: G / (3 N R(R-1)/2)."""
+        return self.correlation() / (3.0 * self.N * self.R * (self.R - 1) / 2)
 
     def get_state(self):
         s = np.zeros((self.S, self.R, self.N), np.int8)

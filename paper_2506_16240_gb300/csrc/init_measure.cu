@@ -274,6 +274,81 @@ __global__ void __launch_bounds__(256) measure_kernel(const int8_t *spins, const
     }
 }
 
+// ------------------------------------------------- four-point correlation --
+// q_x = s^a_x s^b_x of every replica pair a < b of every sample, natural layout:
+// q[(sample * npair + pair) * N + site].
+__global__ void overlap_field_kernel(int8_t *q, const int8_t *spins, Geometry g, int S, int R) {
+    const int64_t N = (int64_t)g.L * g.L * g.L;
+    const int npair = R * (R - 1) / 2;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= N * S * npair) return;
+    const int64_t item = tid / N;
+    const int64_t site = tid - item * N;
+    const int sample = (int)(item / npair);
+    int pair = (int)(item - (int64_t)sample * npair), ra = 0;
+    while (pair >= R - 1 - ra) {  // pair index -> (ra, rb), lexicographic
+        pair -= R - 1 - ra;
+        ++ra;
+    }
+    const int rb = ra + 1 + pair;
+    int x, y, z;
+    site_xyz(g, site, x, y, z);
+    int p;
+    const int64_t in_half = split_offset(g, x, y, z, &p);
+    const int64_t off = in_half + (int64_t)p * g.half;
+    const int8_t sa = spins[(((int64_t)sample * R + ra) * 2) * g.half + off];
+    const int8_t sb = spins[(((int64_t)sample * R + rb) * 2) * g.half + off];
+    q[tid] = (int8_t)(sa * sb);
+}
+
+// G[sample][r] += sum over the block's lines along axis d of sum_i q_i q_{i+r}.
+// Block: x = r (L threads), y = lines; grid: (line groups, axis, sample * pair).
+__global__ void correlation_kernel(const int8_t *q, int L, int npair, unsigned long long *G) {
+    extern __shared__ long long gsum[];  // [L]
+    const int r = threadIdx.x;
+    for (int i = threadIdx.y * blockDim.x + threadIdx.x; i < L; i += blockDim.x * blockDim.y) gsum[i] = 0;
+    __syncthreads();
+    const int64_t N = (int64_t)L * L * L;
+    const int axis = blockIdx.y;
+    const int item = blockIdx.z;  // sample * npair + pair
+    const int64_t line = (int64_t)blockIdx.x * blockDim.y + threadIdx.y;
+    if (line < (int64_t)L * L) {
+        // the line's first site and stride along the axis
+        const int u = (int)(line % L), v = (int)(line / L);
+        int64_t base, stride;
+        if (axis == 0) { base = ((int64_t)v * L + u) * L; stride = 1; }
+        else if (axis == 1) { base = (int64_t)v * L * L + u; stride = L; }
+        else { base = (int64_t)v * L + u; stride = (int64_t)L * L; }
+        const int8_t *ql = q + (int64_t)item * N + base;
+        int acc = 0;
+        int j = r;
+        for (int i = 0; i < L; ++i) {
+            acc += ql[i * stride] * ql[j * stride];
+            j = (j + 1 == L) ? 0 : j + 1;
+        }
+        atomicAdd(reinterpret_cast<unsigned long long *>(&gsum[r]), (unsigned long long)(long long)acc);
+    }
+    __syncthreads();
+    const int sample = item / npair;
+    for (int i = threadIdx.y * blockDim.x + threadIdx.x; i < L; i += blockDim.x * blockDim.y)
+        if (gsum[i]) atomicAdd(G + (int64_t)sample * L + i, (unsigned long long)gsum[i]);
+}
+
+cudaError_t launch_correlation(const int8_t *spins, Geometry g, int S, int R, int8_t *q_scratch,
+                               unsigned long long *G, cudaStream_t st) {
+    const int64_t N = (int64_t)g.L * g.L * g.L;
+    const int npair = R * (R - 1) / 2;
+    const int64_t total = N * S * npair;
+    overlap_field_kernel<<<blocks_for(total, 256), 256, 0, st>>>(q_scratch, spins, g, S, R);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int ly = g.L >= 1024 ? 1 : 1024 / g.L;
+    const dim3 block((unsigned)g.L, (unsigned)ly);
+    const dim3 grid((unsigned)(((int64_t)g.L * g.L + ly - 1) / ly), 3, (unsigned)(S * npair));
+    correlation_kernel<<<grid, block, sizeof(long long) * g.L, st>>>(q_scratch, g.L, npair, G);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_measure(const int8_t *spins, const uint8_t *daemons, const uint8_t *bonds,
                            Geometry g, int S, int R, int gamma, unsigned long long *out, cudaStream_t st) {
     const int64_t words = (int64_t)g.L * g.L * g.W;

@@ -643,6 +643,28 @@ int micsa_measure(micsa_t h, int64_t *energy, int64_t *aux, int64_t *overlap) {
     return MICSA_OK;
 }
 
+int micsa_correlation(micsa_t h, int64_t *G) {
+    if (!h) return MICSA_E_INVALID_ARG;
+    if (!G) return fail(h, MICSA_E_INVALID_ARG, "G is NULL");
+    if (h->R < 2) return fail(h, MICSA_E_INVALID_ARG, "the correlation needs two replicas or more");
+    if (h->L > 1024) return fail(h, MICSA_E_INVALID_ARG, "the correlation supports L <= 1024");
+    DeviceGuard dg(h->device);
+    const int64_t npair = (int64_t)h->R * (h->R - 1) / 2;
+    const size_t qbytes = (size_t)(sites(h) * h->S * npair);
+    const size_t gbytes = sizeof(long long) * (size_t)h->S * h->L;
+    // scratch: the overlap fields, then the sums (16-byte aligned)
+    const size_t goff = (qbytes + 15) / 16 * 16;
+    if (int rc = ensure_stage(h, goff + gbytes)) return rc;
+    unsigned long long *dG = reinterpret_cast<unsigned long long *>(h->d_stage + goff);
+    CK(h, cudaMemsetAsync(dG, 0, gbytes, h->stream), "clear correlation sums");
+    CK(h, launch_correlation(h->d_spins, h->geo, h->S, h->R, reinterpret_cast<int8_t *>(h->d_stage), dG, h->stream),
+       "correlation launch");
+    h->launches += 2;
+    CK(h, cudaMemcpyAsync(G, dG, gbytes, cudaMemcpyDeviceToHost, h->stream), "copy correlation");
+    CK(h, cudaStreamSynchronize(h->stream), "correlation synchronize");
+    return MICSA_OK;
+}
+
 int micsa_get_state(micsa_t h, int8_t *spins, uint8_t *daemons, int64_t *t) {
     if (!h) return MICSA_E_INVALID_ARG;
     DeviceGuard dg(h->device);

@@ -167,5 +167,8 @@ cudaError_t launch_convert_sites(uint8_t *split, uint8_t *natural, Geometry g, i
                                  bool to_split, cudaStream_t st);
 cudaError_t launch_measure(const int8_t *spins, const uint8_t *daemons, const uint8_t *bonds,
                            Geometry g, int S, int R, int gamma, unsigned long long *out, cudaStream_t st);
+// C4 sums G[S][L] (Sec. 3); q_scratch holds N * S * R(R-1)/2 bytes
+cudaError_t launch_correlation(const int8_t *spins, Geometry g, int S, int R, int8_t *q_scratch,
+                               unsigned long long *G, cudaStream_t st);
 
 }  // namespace micsa

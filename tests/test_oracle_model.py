@@ -462,3 +462,33 @@ def test_long_run_gamma_walkers_match_enumeration(gamma, walkers):
             es.append(O.measure(st)[0][0] / N)
     mean, err = _batch_mean(es)
     assert abs(mean - exact) < 5 * err + 1e-3, (mean, err, exact)
+
+
+# ------------------------------------------------ four-point correlation --
+
+def test_correlation_matches_fft_autocorrelation():
+    """C4 of Sec. 3 is a circular autocorrelation of the overlap field q along
+    each axis; numpy's FFT computes it independently."""
+    L, S, R = 6, 2, 3
+    st = O.create(L, S, R, 61)
+    O.run(st, np.linspace(2.0, 1.0, 15), 4)
+    G = O.correlation(st)
+    for a in range(S):
+        ref = np.zeros(L)
+        for ra in range(R):
+            for rb in range(ra + 1, R):
+                q = (st["s"][a, ra].astype(np.int64) * st["s"][a, rb]).reshape(L, L, L)
+                for axis in range(3):
+                    f = np.fft.fft(q, axis=axis)
+                    ac = np.fft.ifft(f * np.conj(f), axis=axis).real  # sum_x q_x q_{x + r}
+                    ref += np.moveaxis(ac, axis, 0).reshape(L, -1).sum(axis=1)
+        np.testing.assert_array_equal(G[a], np.rint(ref).astype(np.int64))
+    npairs = R * (R - 1) // 2
+    np.testing.assert_array_equal(G[:, 0], 3 * L ** 3 * npairs)  # C4(0) = 1
+
+
+def test_correlation_identical_replicas_is_one():
+    L = 4
+    st = O.create(L, 1, 2, 5)
+    st["s"][0, 1] = st["s"][0, 0]
+    np.testing.assert_array_equal(O.correlation(st)[0], 3 * L ** 3)

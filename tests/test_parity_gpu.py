@@ -270,3 +270,16 @@ def test_gamma_daemons_and_walkers_bit_exact(L, S, R, gamma, walkers, interval):
         g.run_logrefresh(sched[20:])
         O.run_ex(st, sched[20:], 0)
         assert_same_state(g, st, f"gamma={gamma} walkers={walkers}")
+
+
+@pytest.mark.parametrize("L,S,R", [(4, 2, 2), (6, 1, 3), (16, 3, 2), (18, 1, 4), (32, 2, 2)])
+def test_correlation_bit_exact(L, S, R):
+    """C4(r, t) sums of Sec. 3 on the GPU equal the oracle's, exactly."""
+    with micsa.Micsa(L, S, R, 300 + L) as g:
+        st = O.create(L, S, R, 300 + L)
+        for chunk in (np.full(5, 1.5), np.full(20, 0.8)):
+            g.run(chunk, 4)
+            O.run(st, chunk, 4)
+            np.testing.assert_array_equal(g.correlation(), O.correlation(st))
+        c4 = g.c4()
+        np.testing.assert_allclose(c4[:, 0], 1.0, rtol=1e-12)
