@@ -28,6 +28,13 @@ Legs on the same JSON line:
   serving      Poisson stream of annealing jobs (L 16..96, 10^3..10^5 sweeps,
                1..4 replicas, anneal 3.0 -> 0.3) through the continuous-batching
                pool: p50/p99 latency and aggregate spin-flips/ns
+  multispin_l160  the headline workload (bounded sweep count) on the bit-plane
+               engine (multispin coding in HBM, 32 z per word), its launch shape
+               tuned; roofline of its half-sweep kernel: algorithmic bytes
+               half_sites * (7 R + 6) / 8 per launch over the mean launch time
+  paper_shape  L = 160, 1 sample x 128 replicas (the shape of the paper's GPU
+               timings), T = 0.7, refresh every 10: bit-plane engine and the
+               byte streaming engine
   cpu_baseline the CPU oracle (single thread) on a bounded sample of sweeps
 
 --impl reference times the oracle itself (the deliberately slow reference).
@@ -242,6 +249,90 @@ def leg_roofline(micsa, timer, stream, L, peaks, n_plain=2000):
             "flips_per_ns": updates(L, 1, R, n_plain) / (ms * 1e6)}
 
 
+def plane_roofline(micsa, timer, stream, g, peaks, n_plain=2000):
+    """Bit-plane half-sweep kernel of handle g (engine and shape already set):
+    algorithmic bytes / mean launch time over sweeps without refresh."""
+    L, S, R = g.L, g.S, g.R
+    g.run(np.full(50, 0.7), 2 ** 31 - 1)
+    ms = timer(lambda: g.run(np.full(n_plain, 0.7), 2 ** 31 - 1))
+    launch_us = 1e3 * ms / (2 * n_plain)  # conversions at both ends included (2 of 2 n_plain + 3 launches)
+    half_sites = L ** 3 // 2
+    # per replica: own spin, m0, m1 planes read and written, opposite spin plane read (7 bits);
+    # per sample: six bond planes (6 bits)
+    bytes_per_launch = half_sites * (7 * R + 6) * S // 8
+    hbm = peaks.get("hbm_gbs")
+    peak = hbm if hbm else 6800.0
+    achieved = bytes_per_launch / (launch_us * 1e-6) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": None, "peak_source": "measured" if hbm else "fallback",
+            "kernel": "micsa::msg_half_kernel (bit-plane MicSA half-sweep, no refresh)",
+            "L": L, "replicas": R, "bytes_per_launch": bytes_per_launch, "launch_us": launch_us,
+            "flips_per_ns": updates(L, S, R, n_plain) / (ms * 1e6)}
+
+
+def tune_planes(g, timer, sweeps=300):
+    """Fastest (words per thread, replicas per thread) of the bit-plane engine."""
+    best = None
+    rpts = sorted({0} | {r for r in (1, 2, 4, 8, 16) if r <= g.R})
+    for nw in (1, 2, 4):
+        for rpt in rpts:
+            g.set_launch_config(nw, 128, -1, True, 64)
+            g.set_multispin_replicas(rpt)
+            g.run(np.full(20, 0.7), 10)
+            ms = timer(lambda: g.run(np.full(sweeps, 0.7), 10))
+            if best is None or ms < best[0]:
+                best = (ms, nw, rpt)
+    g.set_launch_config(best[1], 128, -1, True, 64)
+    g.set_multispin_replicas(best[2])
+    return {"words_per_thread": best[1], "replicas_per_thread": best[2]}
+
+
+def leg_multispin_l160(micsa, timer, stream, peaks, sweeps=20_000):
+    """The headline lattice and schedule on the bit-plane engine."""
+    w = WORKLOAD
+    L, S, R = w["L"], w["samples"], w["replicas"]
+    g = micsa.Micsa(L, S, R, 5, stream=stream)
+    g.set_engine("multispin_global")
+    shape = tune_planes(g, timer)
+    sched = np.full(sweeps, w["T"])
+    g.reinit(6)
+    g.run(sched[:1000], w["refresh_interval"])
+    g.reinit(7)
+    ms = timer(lambda: g.run(sched, w["refresh_interval"]))
+    e, _, q = g.measure()
+    roof = plane_roofline(micsa, timer, stream, g, peaks)
+    g.close()
+    return {"flips_per_ns": updates(L, S, R, sweeps) / (ms * 1e6), "sweeps": sweeps, "launch": shape,
+            "energy_per_spin": [float(v) / L ** 3 for v in e], "roofline": roof,
+            "note": "same bits as the byte engine (parity-tested); state converted to planes and back per run"}
+
+
+def leg_paper_shape(micsa, timer, stream, peaks, L=160, R=128, sweeps=400):
+    """L = 160, 128 replicas of one sample, T = 0.7, refresh every 10."""
+    out = {"L": L, "replicas": R, "sweeps": sweeps, "T": 0.7, "refresh_interval": 10}
+    sched = np.full(sweeps, 0.7)
+    g = micsa.Micsa(L, 1, R, 9, stream=stream)
+    g.set_engine("multispin_global")
+    out["multispin_launch"] = tune_planes(g, timer, sweeps=60)
+    g.reinit(10)
+    g.run(sched[:40], 10)
+    ms = timer(lambda: g.run(sched, 10))
+    out["multispin_flips_per_ns"] = updates(L, 1, R, sweeps) / (ms * 1e6)
+    out["multispin_ns_per_sweep"] = 1e6 * ms / sweeps
+    out["multispin_roofline"] = plane_roofline(micsa, timer, stream, g, peaks, n_plain=200)
+    g.set_engine("stream")
+    g.set_launch_config(4, 128, -1, True, 64)
+    g.reinit(10)
+    g.run(sched[:10], 10)
+    n_s = max(10, sweeps // 4)
+    ms = timer(lambda: g.run(sched[:n_s], 10))
+    out["stream_flips_per_ns"] = updates(L, 1, R, n_s) / (ms * 1e6)
+    g.close()
+    out["paper_h100_spin_update_kernel_ns_per_sweep"] = 121554
+    out["paper_h100_flips_per_ns"] = 128 * 160 ** 3 / 121554.0
+    return out
+
+
 def leg_metropolis(micsa, timer, stream, n=10_000):
     w = WORKLOAD
     g = micsa.Micsa(w["L"], 1, w["replicas"], 3, stream=stream)
@@ -396,7 +487,9 @@ def main(argv=None):
     seed = rank_seed(rank)
     g = micsa.Micsa(L, S, R, seed, stream=stream)
     from paper_2506_16240_gb300 import autotune
-    tuned = autotune.tune(g, torch, stream, use_cache=False)  # launch shape for this lattice
+    # launch shape of the byte-layout engine for this lattice (int8 spins, uint8
+    # daemons); the bit-plane engine is timed on the same workload in its own leg
+    tuned = autotune.tune(g, torch, stream, use_cache=False, engines=("stream", "resident", "multispin"))
 
     for k in range(args.warmup):
         g.reinit(seed + k)
@@ -468,7 +561,9 @@ def main(argv=None):
                 ("metropolis", lambda: leg_metropolis(micsa, timer, stream)),
                 ("quench_l32", lambda: leg_quench_l32(micsa, timer, stream)),
                 ("batched", lambda: leg_batched(micsa, torch, stream)),
-                ("serving", lambda: leg_serving(micsa, torch, stream, args.serving_jobs))]
+                ("serving", lambda: leg_serving(micsa, torch, stream, args.serving_jobs)),
+                ("multispin_l160", lambda: leg_multispin_l160(micsa, timer, stream, peaks)),
+                ("paper_shape", lambda: leg_paper_shape(micsa, timer, stream, peaks))]
         for name, fn in legs:
             try:
                 extras[name] = fn()

@@ -65,7 +65,7 @@ typedef struct micsa_ctx *micsa_t;
 /* Allocate the state of n_samples disorder samples x n_replicas replicas of an
  * L^3 lattice on the current CUDA device; draw the couplings (Sec. 2.1) and a
  * fully disordered start (Sec. 3) from `seed`; daemons are zero until the
- * first refresh; t = 0. *out receives the handle. 1 <= n_replicas <= 32. */
+ * first refresh; t = 0. *out receives the handle. 1 <= n_replicas <= 128. */
 int micsa_create(int L, int n_samples, int n_replicas, uint64_t seed, micsa_t *out);
 
 /* As micsa_create with gamma (1..8) daemons per spin, or walkers if walkers != 0
@@ -123,7 +123,9 @@ int micsa_measure(micsa_t h, int64_t *energy, int64_t *aux, int64_t *overlap);
  * all sites x of q_x q_{x + r e_d}, with q_x = s^a_x s^b_x, periodic, r = 0..L-1.
  * C4(r) = G / (3 N R(R-1)/2) (the paper's sum over a != b normalised by
  * N R(R-1)/2 counts each unordered pair once, so that C4(0) = 1). Host array
- * G[S][L]; needs R >= 2 and L <= 1024. Synchronous. */
+ * G[S][L]; needs R >= 2 and L <= 1024; the device scratch of the overlap
+ * fields, N * S * R(R-1)/2 bytes, is limited to 4 GiB (MICSA_E_TOO_LARGE
+ * beyond). Synchronous. */
 int micsa_correlation(micsa_t h, int64_t *G);
 
 /* Copy the state to / from host arrays in natural layout: spins[S*R*N] int8
@@ -165,15 +167,31 @@ int micsa_set_launch_config(micsa_t h, int words_per_thread, int block, int bloc
  *                          L <= 40) for resident_sweeps sweeps per launch
  *   MICSA_ENGINE_MULTISPIN as RESIDENT with the replica held as bit planes
  *                          (32 sites per word, Boolean update; L <= 32)
- * An engine whose size limit the lattice exceeds is rejected.
- * Metropolis runs always use the streaming kernel. Synchronizes. */
+ *   MICSA_ENGINE_MULTISPIN_GLOBAL
+ *                          bit planes in HBM (32 z per word) for L a multiple
+ *                          of 32: each micsa_run converts the byte state to
+ *                          planes, runs one launch per half-sweep on them
+ *                          (graphs, PDL) and converts back. Needs gamma = 1
+ *                          and no walkers; extra device memory: 0.375 bytes
+ *                          per spin per replica and 0.75 per spin per sample.
+ * An engine whose size limit the lattice exceeds is rejected. Runs with gamma
+ * > 1 or walkers, and Metropolis runs, always use the streaming kernel.
+ * resident_sweeps only matters to RESIDENT and MULTISPIN. Synchronizes.
+ * (App. B and Sec. 2.5 describe the multispin Boolean update.) */
 #define MICSA_ENGINE_AUTO 0
 #define MICSA_ENGINE_STREAM 1
 #define MICSA_ENGINE_RESIDENT 2
 #define MICSA_ENGINE_MULTISPIN 3
+#define MICSA_ENGINE_MULTISPIN_GLOBAL 4
 int micsa_set_engine(micsa_t h, int engine, int resident_sweeps);
 
-/* The engine that the next micsa_run will use (STREAM, RESIDENT or MULTISPIN). */
+/* Replicas one thread of the MULTISPIN_GLOBAL engine runs over the same bond
+ * words (1 .. n_replicas; 0 = automatic: as few as keep about 2048 threads per
+ * SM busy). Results do not depend on it. Synchronizes. */
+int micsa_set_multispin_replicas(micsa_t h, int replicas_per_thread);
+
+/* The engine that the next micsa_run will use (STREAM, RESIDENT, MULTISPIN or
+ * MULTISPIN_GLOBAL). */
 int micsa_get_engine(micsa_t h, int *engine);
 
 /* The launch shape requested (words_per_thread as set, reduced to what the row

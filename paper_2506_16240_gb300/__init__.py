@@ -26,6 +26,9 @@ MICSA_E_BUSY = -5
 MICSA_E_NOT_FOUND = -6
 MICSA_E_TOO_LARGE = -7
 MICSA_ENGINE_AUTO, MICSA_ENGINE_STREAM, MICSA_ENGINE_RESIDENT, MICSA_ENGINE_MULTISPIN = 0, 1, 2, 3
+MICSA_ENGINE_MULTISPIN_GLOBAL = 4
+ENGINES = {"auto": MICSA_ENGINE_AUTO, "stream": MICSA_ENGINE_STREAM, "resident": MICSA_ENGINE_RESIDENT,
+           "multispin": MICSA_ENGINE_MULTISPIN, "multispin_global": MICSA_ENGINE_MULTISPIN_GLOBAL}
 MICSA_NOALLOC_MAX_TERMS = 8192
 
 _ERRNAMES = {-1: "MICSA_E_INVALID_ARG", -2: "MICSA_E_OOM", -3: "MICSA_E_CUDA",
@@ -70,6 +73,7 @@ SIGNATURES = {
     "micsa_get_launch_config": (_c.c_int, [_P, _ip, _ip, _ip, _ip, _ip]),
     "micsa_set_engine": (_c.c_int, [_P, _c.c_int, _c.c_int]),
     "micsa_get_engine": (_c.c_int, [_P, _ip]),
+    "micsa_set_multispin_replicas": (_c.c_int, [_P, _c.c_int]),
     "micsa_destroy": (None, [_P]),
     "micsa_last_error": (_c.c_char_p, [_P]),
     "micsa_measure_noalloc": (_c.c_int, [_P, _P, _P, _c.c_int, _c.c_int, _c.c_int, _P, _P, _P, _P]),
@@ -247,15 +251,16 @@ class Micsa:
         return {k: x.value for k, x in zip(keys, v)}
 
     def set_engine(self, engine="auto", resident_sweeps=64):
-        code = {"auto": MICSA_ENGINE_AUTO, "stream": MICSA_ENGINE_STREAM,
-                "resident": MICSA_ENGINE_RESIDENT, "multispin": MICSA_ENGINE_MULTISPIN}[engine]
-        _check(lib().micsa_set_engine(self.h, code, int(resident_sweeps)), self.h)
+        _check(lib().micsa_set_engine(self.h, ENGINES[engine], int(resident_sweeps)), self.h)
+
+    def set_multispin_replicas(self, replicas_per_thread=0):
+        """Replicas per thread of the multispin_global engine (0: automatic)."""
+        _check(lib().micsa_set_multispin_replicas(self.h, int(replicas_per_thread)), self.h)
 
     def engine(self):
         v = ctypes.c_int()
         _check(lib().micsa_get_engine(self.h, ctypes.byref(v)), self.h)
-        return {MICSA_ENGINE_STREAM: "stream", MICSA_ENGINE_RESIDENT: "resident",
-                MICSA_ENGINE_MULTISPIN: "multispin"}[v.value]
+        return {code: name for name, code in ENGINES.items()}[v.value]
 
     def launch_count(self):
         n = ctypes.c_int64()

@@ -2,7 +2,8 @@
 
 For a lattice shape (L, samples, replicas) it times the candidate launch
 shapes (32-bit words per thread, threads per block, grid-stride cap) and, for
-lattices that fit in shared memory, the resident engines, on a short run of
+lattices that fit in shared memory, the resident engines, and for L a multiple
+of 32 the bit-plane engine (words per thread, replicas per thread), on a short run of
 sweeps of that very shape, and keeps the fastest. Every choice computes the
 same bits, so tuning never changes results. Choices are cached in a JSON file
 keyed by device name and shape (``MICSA_AUTOTUNE_CACHE``, default
@@ -43,7 +44,7 @@ def _store(cache):
         pass  # a read-only home only loses the cache
 
 
-def candidates(L):
+def candidates(L, R=1):
     out = [{"engine": "stream", "words_per_thread": nw, "block": blk, "blocks_per_sm": bps}
            for nw, blk, bps in itertools.product([4, 2], [64, 128, 256], [-1, 0, 2, 3, 4, 5])]
     # register-capped variant (64 registers, up to 8 blocks of 128 per SM)
@@ -53,6 +54,10 @@ def candidates(L):
         out.append({"engine": "resident"})
     if L <= 32:
         out.append({"engine": "multispin"})
+    if L % 32 == 0:
+        rpts = sorted({0} | {r for r in (1, 2, 4, 8, 16, 32) if r <= R})
+        out += [{"engine": "multispin_global", "words_per_thread": nw, "replicas_per_thread": rpt}
+                for nw, rpt in itertools.product([1, 2, 4], rpts)]
     return out
 
 
@@ -60,22 +65,29 @@ def apply(g, choice, resident_sweeps=256):
     if choice["engine"] == "stream":
         g.set_engine("stream")
         g.set_launch_config(choice["words_per_thread"], choice["block"], choice["blocks_per_sm"], True, 64)
+    elif choice["engine"] == "multispin_global":
+        g.set_engine("multispin_global")
+        g.set_launch_config(choice["words_per_thread"], 128, -1, True, 64)
+        g.set_multispin_replicas(choice["replicas_per_thread"])
     else:
         g.set_engine(choice["engine"], resident_sweeps)
 
 
-def tune(g, torch, stream, sweeps=400, T=0.7, refresh_interval=10, use_cache=True):
+def tune(g, torch, stream, sweeps=400, T=0.7, refresh_interval=10, use_cache=True, engines=None):
     """Pick and apply the fastest launch shape for handle g; returns the choice
-    with its measured spin-flips/ns. The handle's state is advanced (t moves)."""
+    with its measured spin-flips/ns. The handle's state is advanced (t moves).
+    engines: the engine names to consider (None: all)."""
     name = torch.cuda.get_device_name()
-    key = _key(name, g.L, g.S, g.R)
+    key = _key(name, g.L, g.S, g.R) + ("" if engines is None else "|" + ",".join(sorted(engines)))
     cache = _load() if use_cache else {}
     if key in cache:
         apply(g, cache[key])
         return dict(cache[key], cached=True)
     sched = np.full(sweeps, T)
     best = None
-    for c in candidates(g.L):
+    for c in candidates(g.L, g.R):
+        if engines is not None and c["engine"] not in engines:
+            continue
         apply(g, c)
         g.run(sched[: max(10, sweeps // 10)], refresh_interval)  # warm-up of this shape
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

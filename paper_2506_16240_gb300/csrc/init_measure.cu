@@ -354,7 +354,12 @@ cudaError_t launch_measure(const int8_t *spins, const uint8_t *daemons, const ui
     const int64_t words = (int64_t)g.L * g.L * g.W;
     const int nq = 2 * R + R * (R - 1) / 2;
     dim3 grid(blocks_for(words, 256), (unsigned)S);
-    measure_kernel<<<grid, 256, sizeof(long long) * nq, st>>>(spins, daemons, bonds, g, S, R, gamma, out);
+    const size_t smem = sizeof(long long) * nq;  // 67 KB at R = 128
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(measure_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    measure_kernel<<<grid, 256, smem, st>>>(spins, daemons, bonds, g, S, R, gamma, out);
     return cudaGetLastError();
 }
 

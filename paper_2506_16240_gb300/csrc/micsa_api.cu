@@ -42,11 +42,14 @@ struct micsa_ctx {
     int64_t params_cap = 0;
     cudaEvent_t params_free = nullptr;  // the last upload of h_params has been consumed
     int64_t *d_cursor = nullptr;
-    cudaGraphExec_t graph[2] = {nullptr, nullptr};  // [metro]: G sweeps + cursor advance
+    cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};  // [kind]: G sweeps + cursor advance
     int engine = MICSA_ENGINE_AUTO;  // which kernel runs MicSA sweeps
     int resident_sweeps = 256;       // sweeps per resident launch
     ResidentUnit *d_units = nullptr; // one unit per (sample, replica)
-    int graph_g[2] = {0, 0};
+    int graph_g[3] = {0, 0, 0};
+    uint32_t *d_planes = nullptr;    // multispin planes [S*R][3][2][L^3/64] (MULTISPIN_GLOBAL)
+    uint32_t *d_bplanes = nullptr;   // bond planes [S][6][2][L^3/64]
+    int msg_rpt = 0;                 // replicas per thread of MULTISPIN_GLOBAL (0: automatic)
     std::string err;
 };
 
@@ -129,7 +132,7 @@ SweepArgs sweep_args(const micsa_ctx *h) {
 }
 
 void drop_graphs(micsa_t h) {
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 3; ++i) {
         if (h->graph[i]) cudaGraphExecDestroy(h->graph[i]);
         h->graph[i] = nullptr;
         h->graph_g[i] = 0;
@@ -173,10 +176,24 @@ int ensure_params(micsa_t h, int64_t n) {
     return MICSA_OK;
 }
 
+enum GraphKind { kGraphMicsa = 0, kGraphMetro = 1, kGraphPlanes = 2 };
+
+int msg_rpt(const micsa_ctx *h, int nw) {
+    return h->msg_rpt > 0 ? h->msg_rpt : msg_default_rpt(h->geo, h->S, h->R, nw, h->sm_count);
+}
+
+// One half-sweep of the bit-plane engine reading params[*cursor + k].
+cudaError_t launch_planes_half(micsa_t h, const LaunchConfig &lc, int parity, const int64_t *cursor, int64_t k,
+                               cudaStream_t st) {
+    return launch_msg_half(h->d_planes, h->d_bplanes, h->geo, h->S, h->R, msg_rpt(h, lc.nw), lc.nw, parity,
+                           (uint32_t)(h->seed & 0xFFFFFFFFu), (uint32_t)(h->seed >> 32), h->d_params, cursor, k,
+                           lc.pdl, st);
+}
+
 // Capture G sweeps (2G half-sweeps reading params[*cursor + k]) and the cursor
 // advance into an executable graph.
-int capture_graph(micsa_t h, bool metro, int G, const LaunchConfig &lc) {
-    const int gi = metro ? 1 : 0;
+int capture_graph(micsa_t h, int gi, int G, const LaunchConfig &lc) {
+    const bool metro = gi == kGraphMetro;
     if (h->graph[gi] && h->graph_g[gi] == G) return MICSA_OK;
     if (h->graph[gi]) cudaGraphExecDestroy(h->graph[gi]);
     h->graph[gi] = nullptr;
@@ -189,7 +206,8 @@ int capture_graph(micsa_t h, bool metro, int G, const LaunchConfig &lc) {
         for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
             a.k = k;
             a.parity = p;
-            e = launch_half_sweep(a, metro, lc, h->capture_stream);
+            e = gi == kGraphPlanes ? launch_planes_half(h, lc, p, h->d_cursor, k, h->capture_stream)
+                                   : launch_half_sweep(a, metro, lc, h->capture_stream);
         }
     if (e == cudaSuccess) e = launch_advance_cursor(h->d_cursor, G, lc.pdl, h->capture_stream);
     cudaGraph_t graph = nullptr;
@@ -211,13 +229,65 @@ int capture_graph(micsa_t h, bool metro, int G, const LaunchConfig &lc) {
 
 // The engine a MicSA run uses now.
 int active_engine(micsa_t h) {
-    if (!h->d_units || h->engine == MICSA_ENGINE_STREAM || h->gamma > 1 || h->walkers) return MICSA_ENGINE_STREAM;
+    if (h->engine == MICSA_ENGINE_STREAM || h->gamma > 1 || h->walkers) return MICSA_ENGINE_STREAM;
+    if (h->engine == MICSA_ENGINE_MULTISPIN_GLOBAL)
+        return msg_supported(h->geo) ? MICSA_ENGINE_MULTISPIN_GLOBAL : MICSA_ENGINE_STREAM;
+    if (!h->d_units) return MICSA_ENGINE_STREAM;
     if (h->engine == MICSA_ENGINE_RESIDENT) return MICSA_ENGINE_RESIDENT;
     if (multispin_smem_bytes(h->geo) > 0) return MICSA_ENGINE_MULTISPIN;
     return h->engine == MICSA_ENGINE_MULTISPIN ? MICSA_ENGINE_STREAM : MICSA_ENGINE_RESIDENT;
 }
 
-bool use_resident(micsa_t h) { return active_engine(h) != MICSA_ENGINE_STREAM; }
+bool use_resident(micsa_t h) {
+    const int e = active_engine(h);
+    return e == MICSA_ENGINE_RESIDENT || e == MICSA_ENGINE_MULTISPIN;
+}
+
+// Device memory of the bit-plane engine, allocated on first use.
+int ensure_planes(micsa_t h) {
+    if (h->d_planes) return MICSA_OK;
+    const size_t WP = (size_t)msg_plane_words(h->geo);
+    const size_t state = sizeof(uint32_t) * (size_t)h->S * h->R * 6 * WP;
+    const size_t bonds = sizeof(uint32_t) * (size_t)h->S * 12 * WP;
+    CK(h, cudaMalloc(&h->d_planes, state), "cudaMalloc planes");
+    cudaError_t e = cudaMalloc(&h->d_bplanes, bonds);
+    if (e != cudaSuccess) {
+        cudaFree(h->d_planes);
+        h->d_planes = nullptr;
+        return cuda_fail(h, e, "cudaMalloc bond planes");
+    }
+    h->device_bytes += state + bonds;
+    return MICSA_OK;
+}
+
+// MicSA sweeps [0, n) of the uploaded table on bit planes in HBM: bytes ->
+// planes, whole blocks of G sweeps by graph replay, the rest directly, planes
+// -> bytes. Each sweep is the even half-sweep followed by the odd one.
+int run_planes(micsa_t h, int64_t n, const LaunchConfig &lc) {
+    if (int rc = ensure_planes(h)) return rc;
+    CK(h, msg_convert(h->d_planes, h->d_bplanes, h->d_spins, h->d_daemons, h->d_bonds, h->geo, h->S, h->R, true,
+                      h->stream), "convert to planes");
+    h->launches += 2;
+    const int G = lc.graph_sweeps;
+    int64_t done = 0;
+    if (G > 0 && n >= 2 * (int64_t)G) {
+        if (int rc = capture_graph(h, kGraphPlanes, G, lc)) return rc;
+        CK(h, cudaMemsetAsync(h->d_cursor, 0, sizeof(int64_t), h->stream), "reset cursor");
+        const int64_t reps = n / G;
+        for (int64_t r = 0; r < reps; ++r) CK(h, cudaGraphLaunch(h->graph[kGraphPlanes], h->stream), "graph launch");
+        h->launches += reps * (2 * (int64_t)G + 1);
+        done = reps * G;
+    }
+    for (int64_t k = done; k < n; ++k)
+        for (int p = 0; p < 2; ++p) {
+            CK(h, launch_planes_half(h, lc, p, nullptr, k, h->stream), "plane half-sweep launch");
+            ++h->launches;
+        }
+    CK(h, msg_convert(h->d_planes, nullptr, h->d_spins, h->d_daemons, nullptr, h->geo, h->S, h->R, false,
+                      h->stream), "convert from planes");
+    ++h->launches;
+    return MICSA_OK;
+}
 
 // MicSA sweeps [0, n) of the uploaded table with the shared-memory resident
 // kernel, resident_sweeps per launch; every (sample, replica) is one unit.
@@ -257,10 +327,11 @@ int run_table(micsa_t h, bool metro, int64_t n) {
                           cudaMemcpyHostToDevice, h->stream), "upload sweep parameters");
     CK(h, cudaEventRecord(h->params_free, h->stream), "record parameter event");
     if (!metro && use_resident(h)) return run_resident(h, n, lc);
+    if (!metro && active_engine(h) == MICSA_ENGINE_MULTISPIN_GLOBAL) return run_planes(h, n, lc);
     const int G = lc.graph_sweeps;
     int64_t done = 0;
     if (G > 0 && n >= 2 * (int64_t)G) {
-        if (int rc = capture_graph(h, metro, G, lc)) return rc;
+        if (int rc = capture_graph(h, metro ? kGraphMetro : kGraphMicsa, G, lc)) return rc;
         CK(h, cudaMemsetAsync(h->d_cursor, 0, sizeof(int64_t), h->stream), "reset cursor");
         const int64_t reps = n / G;
         for (int64_t r = 0; r < reps; ++r)
@@ -426,6 +497,8 @@ void micsa_destroy(micsa_t h) {
     cudaFree(h->d_stage);
     cudaFree(h->d_cursor);
     cudaFree(h->d_units);
+    cudaFree(h->d_planes);
+    cudaFree(h->d_bplanes);
     cudaFree(h->d_params);
     cudaFreeHost(h->h_params);
     drop_graphs(h);
@@ -442,7 +515,7 @@ int micsa_create(int L, int n_samples, int n_replicas, uint64_t seed, micsa_t *o
 int micsa_create_ex(int L, int n_samples, int n_replicas, int gamma, int walkers, uint64_t seed, micsa_t *out) {
     if (!out) return MICSA_E_INVALID_ARG;
     *out = nullptr;
-    if (L < 2 || L > 1600 || (L & 1) || n_samples < 1 || n_replicas < 1 || n_replicas > 32 || gamma < 1 ||
+    if (L < 2 || L > 1600 || (L & 1) || n_samples < 1 || n_replicas < 1 || n_replicas > 128 || gamma < 1 ||
         gamma > 8 || (int64_t)n_samples * n_replicas * gamma >= (1ll << 30))
         return MICSA_E_INVALID_ARG;
     micsa_ctx *h = new (std::nothrow) micsa_ctx;
@@ -594,8 +667,11 @@ int micsa_set_launch_config(micsa_t h, int words_per_thread, int block, int bloc
 
 int micsa_set_engine(micsa_t h, int engine, int resident_sweeps) {
     if (!h) return MICSA_E_INVALID_ARG;
-    if (engine < MICSA_ENGINE_AUTO || engine > MICSA_ENGINE_MULTISPIN || resident_sweeps < 1 || resident_sweeps > 1 << 20)
+    if (engine < MICSA_ENGINE_AUTO || engine > MICSA_ENGINE_MULTISPIN_GLOBAL || resident_sweeps < 1 ||
+        resident_sweeps > 1 << 20)
         return fail(h, MICSA_E_INVALID_ARG, "bad engine selection");
+    if (engine == MICSA_ENGINE_MULTISPIN_GLOBAL && !msg_supported(h->geo))
+        return fail(h, MICSA_E_INVALID_ARG, "the global multispin engine needs L a multiple of 32 (L=%d)", h->L);
     if (engine == MICSA_ENGINE_RESIDENT && resident_smem_bytes(h->geo) == 0)
         return fail(h, MICSA_E_INVALID_ARG, "an L=%d replica does not fit in shared memory", h->L);
     if (engine == MICSA_ENGINE_MULTISPIN && multispin_smem_bytes(h->geo) == 0)
@@ -604,6 +680,17 @@ int micsa_set_engine(micsa_t h, int engine, int resident_sweeps) {
     CK(h, cudaStreamSynchronize(h->stream), "synchronize before reconfiguring");
     h->engine = engine;
     h->resident_sweeps = resident_sweeps;
+    return MICSA_OK;
+}
+
+int micsa_set_multispin_replicas(micsa_t h, int replicas_per_thread) {
+    if (!h) return MICSA_E_INVALID_ARG;
+    if (replicas_per_thread < 0 || replicas_per_thread > h->R)
+        return fail(h, MICSA_E_INVALID_ARG, "replicas per thread must be in 0..%d", h->R);
+    DeviceGuard dg(h->device);
+    CK(h, cudaStreamSynchronize(h->stream), "synchronize before reconfiguring");
+    drop_graphs(h);
+    h->msg_rpt = replicas_per_thread;
     return MICSA_OK;
 }
 
@@ -651,6 +738,8 @@ int micsa_correlation(micsa_t h, int64_t *G) {
     DeviceGuard dg(h->device);
     const int64_t npair = (int64_t)h->R * (h->R - 1) / 2;
     const size_t qbytes = (size_t)(sites(h) * h->S * npair);
+    if (qbytes > ((size_t)4 << 30))
+        return fail(h, MICSA_E_TOO_LARGE, "the overlap fields need %zu bytes of scratch (limit 4 GiB)", qbytes);
     const size_t gbytes = sizeof(long long) * (size_t)h->S * h->L;
     // scratch: the overlap fields, then the sums (16-byte aligned)
     const size_t goff = (qbytes + 15) / 16 * 16;

@@ -146,6 +146,16 @@ int resident_blocks_per_sm(bool pool, size_t smem);
 size_t multispin_smem_bytes(const Geometry &g);  // 0 when L > 32
 cudaError_t launch_multispin(const ResidentArgs &a, bool pool, size_t smem, int grid, bool pdl, cudaStream_t st);
 int multispin_blocks_per_sm(bool pool, size_t smem);
+
+// multispin planes in global memory for L % 32 == 0 (multispin.cu)
+bool msg_supported(const Geometry &g);
+int64_t msg_plane_words(const Geometry &g);  // words per parity plane, L^3 / 64
+cudaError_t msg_convert(uint32_t *planes, uint32_t *bplanes, int8_t *spins, uint8_t *daemons, const uint8_t *bonds,
+                        const Geometry &g, int S, int R, bool to_planes, cudaStream_t st);
+int msg_default_rpt(const Geometry &g, int S, int R, int nw, int sm_count);
+cudaError_t launch_msg_half(uint32_t *planes, const uint32_t *bplanes, const Geometry &g, int S, int R, int rpt,
+                            int nw, int parity, uint32_t key0, uint32_t key1, const SweepParam *params,
+                            const int64_t *cursor, int64_t k, bool pdl, cudaStream_t st);
 cudaError_t launch_advance_cursor(int64_t *cursor, int64_t step, bool pdl, cudaStream_t st);
 // wandering of every walker family after timestep t (parity t & 1), Sec. 2.6
 cudaError_t launch_wander(uint8_t *daemons, Geometry g, int64_t n_rep, int gamma, int parity, cudaStream_t st);

@@ -20,6 +20,8 @@
 // m' = u + m - 3 (dH = 12 - 4u), evaluated with Boolean operations only. The
 // daemon refresh draws the same Philox words as every other kernel, so the
 // results are bit-identical to them.
+#include <algorithm>
+
 #include "sweep_body.cuh"
 #include "../../include/micsa.h"
 
@@ -445,6 +447,320 @@ int multispin_blocks_per_sm(bool pool, size_t smem) {
     int n = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, kMsThreads, smem) != cudaSuccess) return 0;
     return n;
+}
+
+}  // namespace micsa
+
+// ===================================================================
+// Global-memory multispin engine (L a multiple of 32): the lattice lives in
+// bit planes in HBM for the whole run. Plane word (p, zw, y, i) holds, in bit
+// b, the site x = 2i + ((p + y + z) & 1), y, z = 32 zw + b of parity p (the
+// site the byte layout keeps at row (z, y), byte i). Word index within a
+// parity plane: (zw * L + y) * Lh + i, WP = L^3 / 64 words per parity. Per
+// replica the planes are [spin | m0 | m1][parity][WP]; per sample the bond
+// planes are [6][parity][WP] (bit set <=> J = -1, order +x +y +z -x -y -z).
+//
+// A thread owns NW consecutive words i = i0 .. i0+NW-1 of one (zw, y) and runs
+// the replicas r = blockIdx.y * rpt .. of its sample over them, so one load
+// of the bond words serves rpt replicas. The z neighbours of bit 31 (bit 0)
+// sit in bit 0 (bit 31) of the word of z-word zw + 1 (zw - 1): funnel shifts.
+// A refresh draws the Philox block of quad ((p L + z) L + y) W + i/4 for
+// every z (the library's counter contract); the 4 / NW lanes that share a
+// block of words split the 32 z between them and OR their partial planes
+// together with shuffles.
+// ===================================================================
+namespace micsa {
+
+struct MsgArgs {
+    uint32_t *planes;        // [S*R][3][2][WP]
+    const uint32_t *bonds;   // [S][6][2][WP]
+    int L, Lh, nzw, W4;      // W4 = Lh / 4 Philox blocks per row
+    int64_t WP;
+    int S, R, rpt, parity;
+    uint32_t key0, key1;
+    const SweepParam *params;
+    const int64_t *cursor;
+    int64_t k;
+};
+
+template <int NW> struct Vec;
+template <> struct Vec<1> {
+    static __device__ __forceinline__ void ld(const uint32_t *p, uint32_t *v) { v[0] = *p; }
+    static __device__ __forceinline__ void st(uint32_t *p, const uint32_t *v) { *p = v[0]; }
+};
+template <> struct Vec<2> {
+    static __device__ __forceinline__ void ld(const uint32_t *p, uint32_t *v) {
+        const uint2 a = *reinterpret_cast<const uint2 *>(p);
+        v[0] = a.x;
+        v[1] = a.y;
+    }
+    static __device__ __forceinline__ void st(uint32_t *p, const uint32_t *v) {
+        *reinterpret_cast<uint2 *>(p) = make_uint2(v[0], v[1]);
+    }
+};
+template <> struct Vec<4> {
+    static __device__ __forceinline__ void ld(const uint32_t *p, uint32_t *v) {
+        const uint4 a = *reinterpret_cast<const uint4 *>(p);
+        v[0] = a.x;
+        v[1] = a.y;
+        v[2] = a.z;
+        v[3] = a.w;
+    }
+    static __device__ __forceinline__ void st(uint32_t *p, const uint32_t *v) {
+        *reinterpret_cast<uint4 *>(p) = make_uint4(v[0], v[1], v[2], v[3]);
+    }
+};
+
+template <int NW>
+__global__ void __launch_bounds__(128) msg_half_kernel(MsgArgs a) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    constexpr int G = 4 / NW;  // lanes sharing one Philox block of words
+    const int64_t kidx = a.k + (a.cursor ? *a.cursor : 0);
+    const SweepParam prm = a.params[kidx];
+    const bool refresh = prm.mode == kModeRefresh;
+    const int groups = a.Lh / NW;
+    const int64_t per_sample = (int64_t)a.L * a.nzw * groups;
+    // the grid covers S * per_sample threads exactly (a multiple of 128 for L % 32 == 0)
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int sample = (int)(tid / per_sample);
+    int64_t rem = tid - (int64_t)sample * per_sample;
+    const int ig = (int)(rem % groups);
+    rem /= groups;
+    const int y = (int)(rem % a.L);
+    const int zw = (int)(rem / a.L);
+    const int p = a.parity, o = 1 - p;
+    const int L = a.L, Lh = a.Lh;
+    const int i0 = NW * ig;
+    const int yp = (y + 1 == L) ? 0 : y + 1, ym = (y == 0) ? L - 1 : y - 1;
+    const int zwp = (zw + 1 == a.nzw) ? 0 : zw + 1, zwm = (zw == 0) ? a.nzw - 1 : zw - 1;
+    const int ip = (i0 + NW == Lh) ? 0 : i0 + NW, im = (i0 == 0) ? Lh - 1 : i0 - 1;
+    const int64_t row = (int64_t)zw * L;
+    const int64_t wc = (row + y) * Lh + i0;
+    const int64_t w_yp = (row + yp) * Lh + i0, w_ym = (row + ym) * Lh + i0;
+    const int64_t w_zp = ((int64_t)zwp * L + y) * Lh + i0, w_zm = ((int64_t)zwm * L + y) * Lh + i0;
+    const int64_t w_ip = (row + y) * Lh + ip, w_im = (row + y) * Lh + im;
+    const uint32_t M = ((p + y) & 1) ? 0x55555555u : 0xAAAAAAAAu;  // bits whose site has x offset 1
+
+    uint32_t B[6][NW];
+    const uint32_t *bs = a.bonds + (int64_t)sample * 12 * a.WP;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) Vec<NW>::ld(bs + ((int64_t)k * 2 + p) * a.WP + wc, B[k]);
+    const RoundKeys rk = round_keys(a.key0, a.key1);
+    const Cuts cut = make_cuts(prm.th0, prm.th1, prm.th2);
+    const int lig = (int)(threadIdx.x & (G - 1));  // this lane's share of the Philox block
+    const uint32_t quad0 = (uint32_t)(((int64_t)p * L + 32 * zw) * L + y) * a.W4 + (uint32_t)(i0 >> 2);
+
+    const int r_end = min(a.R, (int)(blockIdx.y + 1) * a.rpt);
+    for (int r = blockIdx.y * a.rpt; r < r_end; ++r) {
+        const int64_t gid = (int64_t)sample * a.R + r;
+        uint32_t *pl = a.planes + gid * 6 * a.WP;
+        const uint32_t *O = pl + (int64_t)o * a.WP;  // spins of the opposite parity
+        uint32_t *Sp = pl + (int64_t)p * a.WP;
+        uint32_t *M0 = pl + (int64_t)(2 + p) * a.WP;
+        uint32_t *M1 = pl + (int64_t)(4 + p) * a.WP;
+        uint32_t Oc[NW], Oyp[NW], Oym[NW], Ozp[NW], Ozm[NW], Sg[NW], m0v[NW], m1v[NW];
+        Vec<NW>::ld(O + wc, Oc);
+        Vec<NW>::ld(O + w_yp, Oyp);
+        Vec<NW>::ld(O + w_ym, Oym);
+        Vec<NW>::ld(O + w_zp, Ozp);
+        Vec<NW>::ld(O + w_zm, Ozm);
+        const uint32_t Oip = O[w_ip], Oim = O[w_im];
+        Vec<NW>::ld(Sp + wc, Sg);
+        if (refresh) {  // fresh daemons of parity p before its half-sweep (Sec. 2.7)
+            uint32_t a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0};
+            for (int c = 0; c < 32 / G; ++c) {
+                const int b = lig * (32 / G) + c;
+                const uint4 w = philox_rk(make_uint4(quad0 + (uint32_t)b * (uint32_t)L * (uint32_t)a.W4, (uint32_t)prm.t,
+                                                     ((uint32_t)gid << 2) | kTagDaemon,
+                                                     (uint32_t)((uint64_t)prm.t >> 32)), rk);
+                const uint32_t mm[4] = {daemon_cut(w.x, cut), daemon_cut(w.y, cut), daemon_cut(w.z, cut),
+                                        daemon_cut(w.w, cut)};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    a0[j] |= (mm[j] & 1u) << b;
+                    a1[j] |= (mm[j] >> 1) << b;
+                }
+            }
+#pragma unroll
+            for (int off = 1; off < G; off <<= 1)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    a0[j] |= __shfl_xor_sync(0xFFFFFFFFu, a0[j], off);
+                    a1[j] |= __shfl_xor_sync(0xFFFFFFFFu, a1[j], off);
+                }
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {  // word i0 + w is lane (i0 + w) & 3 of the block
+                const int j = (i0 + w) & 3;
+                m0v[w] = j == 0 ? a0[0] : j == 1 ? a0[1] : j == 2 ? a0[2] : a0[3];
+                m1v[w] = j == 0 ? a1[0] : j == 1 ? a1[1] : j == 2 ? a1[2] : a1[3];
+            }
+        } else {
+            Vec<NW>::ld(M0 + wc, m0v);
+            Vec<NW>::ld(M1 + wc, m1v);
+        }
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            const uint32_t oc = Oc[w];
+            const uint32_t o_next = w + 1 < NW ? Oc[w + 1 < NW ? w + 1 : 0] : Oip;  // word i + 1
+            const uint32_t o_prev = w > 0 ? Oc[w > 0 ? w - 1 : 0] : Oim;            // word i - 1
+            const uint32_t nxp = (oc & ~M) | (o_next & M);
+            const uint32_t nxm = (o_prev & ~M) | (oc & M);
+            const uint32_t nzp = __funnelshift_r(oc, Ozp[w], 1);  // bit b <- site z + 1
+            const uint32_t nzm = __funnelshift_l(Ozm[w], oc, 1);  // bit b <- site z - 1
+            const uint32_t sg = Sg[w];
+            // unsatisfied bond indicators (J s s_nb = -1)
+            const uint32_t q0 = sg ^ nxp ^ B[0][w];
+            const uint32_t q1 = sg ^ Oyp[w] ^ B[1][w];
+            const uint32_t q2 = sg ^ nzp ^ B[2][w];
+            const uint32_t q3 = sg ^ nxm ^ B[3][w];
+            const uint32_t q4 = sg ^ Oym[w] ^ B[4][w];
+            const uint32_t q5 = sg ^ nzm ^ B[5][w];
+            // u = q0 + ... + q5, then v = u + m, bit-sliced
+            const uint32_t s1 = q0 ^ q1 ^ q2, c1 = (q0 & q1) | (q2 & (q0 ^ q1));
+            const uint32_t s2 = q3 ^ q4 ^ q5, c2 = (q3 & q4) | (q5 & (q3 ^ q4));
+            const uint32_t u0 = s1 ^ s2, kk = s1 & s2;
+            const uint32_t u1 = c1 ^ c2 ^ kk, u2 = (c1 & c2) | (kk & (c1 ^ c2));
+            const uint32_t m0 = m0v[w], m1 = m1v[w];
+            const uint32_t v0 = u0 ^ m0, k0 = u0 & m0;
+            const uint32_t v1 = u1 ^ m1 ^ k0, k1 = (u1 & m1) | (k0 & (u1 ^ m1));
+            const uint32_t v2 = u2 ^ k1, v3 = u2 & k1;
+            // Eq. (Creutz) with Eq. (flip-OK): accept <=> 3 <= u + m <= 6, m' = u + m - 3
+            const uint32_t acc = (v2 ^ (v1 & v0)) & ~v3;
+            m0v[w] = (m0 & ~acc) | (~v0 & acc);
+            m1v[w] = (m1 & ~acc) | (v2 & (v1 | v0) & acc);
+            Sg[w] = sg ^ acc;
+        }
+        Vec<NW>::st(Sp + wc, Sg);
+        Vec<NW>::st(M0 + wc, m0v);
+        Vec<NW>::st(M1 + wc, m1v);
+    }
+}
+
+// bytes <-> planes. One thread per plane word (n_rep replicas, two parities,
+// WP words); the 32 bits of a word are the 32 z of one (y, i).
+__global__ void msg_convert_state_kernel(uint32_t *planes, int8_t *spins, uint8_t *daemons, Geometry g,
+                                         int64_t n_rep, int64_t WP, bool to_planes) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= n_rep * 2 * WP) return;
+    const int64_t rep = tid / (2 * WP);
+    const int64_t rem = tid - rep * 2 * WP;
+    const int p = (int)(rem / WP);
+    const int64_t w = rem - (int64_t)p * WP;
+    const int i = (int)(w % g.Lh);
+    const int y = (int)((w / g.Lh) % g.L);
+    const int zw = (int)(w / ((int64_t)g.Lh * g.L));
+    const int64_t base = (rep * 2 + p) * g.half + ((int64_t)32 * zw * g.L + y) * g.P + i;
+    const int64_t zstep = (int64_t)g.L * g.P;
+    uint32_t *pl = planes + rep * 6 * WP;
+    if (to_planes) {
+        uint32_t s = 0, m0 = 0, m1 = 0;
+        for (int b = 0; b < 32; ++b) {
+            const int64_t off = base + b * zstep;
+            s |= (((uint32_t)(uint8_t)spins[off] >> 7) & 1u) << b;
+            const uint32_t m = daemons[off];
+            m0 |= (m & 1u) << b;
+            m1 |= ((m >> 1) & 1u) << b;
+        }
+        pl[(int64_t)p * WP + w] = s;
+        pl[(int64_t)(2 + p) * WP + w] = m0;
+        pl[(int64_t)(4 + p) * WP + w] = m1;
+    } else {
+        const uint32_t s = pl[(int64_t)p * WP + w], m0 = pl[(int64_t)(2 + p) * WP + w],
+                       m1 = pl[(int64_t)(4 + p) * WP + w];
+        for (int b = 0; b < 32; ++b) {
+            const int64_t off = base + b * zstep;
+            spins[off] = ((s >> b) & 1u) ? (int8_t)-1 : (int8_t)1;
+            daemons[off] = (uint8_t)(((m0 >> b) & 1u) | (((m1 >> b) & 1u) << 1));
+        }
+    }
+}
+
+__global__ void msg_convert_bonds_kernel(uint32_t *bplanes, const uint8_t *bonds, Geometry g, int64_t S, int64_t WP) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= S * 2 * WP) return;
+    const int64_t smp = tid / (2 * WP);
+    const int64_t rem = tid - smp * 2 * WP;
+    const int p = (int)(rem / WP);
+    const int64_t w = rem - (int64_t)p * WP;
+    const int i = (int)(w % g.Lh);
+    const int y = (int)((w / g.Lh) % g.L);
+    const int zw = (int)(w / ((int64_t)g.Lh * g.L));
+    const int64_t base = (smp * 2 + p) * g.half + ((int64_t)32 * zw * g.L + y) * g.P + i;
+    const int64_t zstep = (int64_t)g.L * g.P;
+    uint32_t bk[6] = {0, 0, 0, 0, 0, 0};
+    for (int b = 0; b < 32; ++b) {
+        const uint32_t v = bonds[base + b * zstep];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) bk[k] |= ((v >> k) & 1u) << b;
+    }
+#pragma unroll
+    for (int k = 0; k < 6; ++k) bplanes[((smp * 6 + k) * 2 + p) * WP + w] = bk[k];
+}
+
+bool msg_supported(const Geometry &g) { return g.L >= 32 && g.L % 32 == 0 && g.P == g.Lh; }
+
+int64_t msg_plane_words(const Geometry &g) { return (int64_t)g.L * g.L * g.L / 64; }
+
+cudaError_t msg_convert(uint32_t *planes, uint32_t *bplanes, int8_t *spins, uint8_t *daemons, const uint8_t *bonds,
+                        const Geometry &g, int S, int R, bool to_planes, cudaStream_t st) {
+    const int64_t WP = msg_plane_words(g);
+    const int64_t n = (int64_t)S * R * 2 * WP;
+    msg_convert_state_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(planes, spins, daemons, g, (int64_t)S * R,
+                                                                             WP, to_planes);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || !to_planes || !bplanes) return e;
+    const int64_t nb = (int64_t)S * 2 * WP;
+    msg_convert_bonds_kernel<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(bplanes, bonds, g, S, WP);
+    return cudaGetLastError();
+}
+
+int msg_default_rpt(const Geometry &g, int S, int R, int nw, int sm_count) {
+    // enough replica groups to fill the GPU (about 2048 threads per SM), the
+    // rest of the replicas looped over inside a thread
+    const int64_t threads = (int64_t)S * g.L * (g.L / 32) * (g.Lh / nw);
+    const int64_t want = (int64_t)sm_count * 2048;
+    int groups = (int)std::min<int64_t>(R, std::max<int64_t>(1, (want + threads - 1) / threads));
+    return (R + groups - 1) / groups;
+}
+
+cudaError_t launch_msg_half(uint32_t *planes, const uint32_t *bplanes, const Geometry &g, int S, int R, int rpt,
+                            int nw, int parity, uint32_t key0, uint32_t key1, const SweepParam *params,
+                            const int64_t *cursor, int64_t k, bool pdl, cudaStream_t st) {
+    MsgArgs a{};
+    a.planes = planes;
+    a.bonds = bplanes;
+    a.L = g.L;
+    a.Lh = g.Lh;
+    a.nzw = g.L / 32;
+    a.W4 = g.Lh / 4;
+    a.WP = msg_plane_words(g);
+    a.S = S;
+    a.R = R;
+    a.rpt = rpt;
+    a.parity = parity;
+    a.key0 = key0;
+    a.key1 = key1;
+    a.params = params;
+    a.cursor = cursor;
+    a.k = k;
+    const int64_t threads = (int64_t)S * g.L * (g.L / 32) * (g.Lh / nw);
+    if (threads % 128 != 0 || rpt < 1) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(threads / 128), (unsigned)((R + rpt - 1) / rpt));
+    cfg.blockDim = dim3(128);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    switch (nw) {
+        case 1: return cudaLaunchKernelEx(&cfg, msg_half_kernel<1>, a);
+        case 2: return cudaLaunchKernelEx(&cfg, msg_half_kernel<2>, a);
+        case 4: return cudaLaunchKernelEx(&cfg, msg_half_kernel<4>, a);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace micsa

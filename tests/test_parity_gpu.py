@@ -165,7 +165,7 @@ def test_invalid_arguments_fail_cleanly():
     with pytest.raises(micsa.MicsaError):
         micsa.Micsa(7, 1, 1, 0)  # odd L
     with pytest.raises(micsa.MicsaError):
-        micsa.Micsa(8, 1, 33, 0)
+        micsa.Micsa(8, 1, 129, 0)  # more than 128 replicas
     with micsa.Micsa(8, 1, 1, 0) as g:
         with pytest.raises(micsa.MicsaError):
             g.run([1.0, 0.0], 10)
@@ -244,7 +244,7 @@ def test_autotuner_choice_keeps_results():
     for L in (16, 34):
         with micsa.Micsa(L, 2, 2, 5, stream=stream) as g:
             choice = autotune.tune(g, torch, stream, sweeps=40, use_cache=False)
-            assert choice["engine"] in ("stream", "resident", "multispin") and choice["flips_per_ns"] > 0
+            assert choice["engine"] in ("stream", "resident", "multispin", "multispin_global") and choice["flips_per_ns"] > 0
             g.reinit(5)
             g.run(np.linspace(2.0, 0.6, 30), 4)
             s, m, t = g.get_state()
@@ -283,3 +283,78 @@ def test_correlation_bit_exact(L, S, R):
             np.testing.assert_array_equal(g.correlation(), O.correlation(st))
         c4 = g.c4()
         np.testing.assert_allclose(c4[:, 0], 1.0, rtol=1e-12)
+
+
+@pytest.mark.parametrize("L,S,R,nw,rpt", [
+    (32, 2, 3, 1, 0), (32, 1, 2, 2, 1), (32, 2, 3, 4, 2), (64, 1, 2, 1, 0), (64, 2, 1, 4, 1), (96, 1, 2, 2, 2),
+])
+def test_global_multispin_matches_oracle(L, S, R, nw, rpt):
+    """Bit planes in HBM (App. B multispin update, L a multiple of 32): refresh
+    at a fixed interval, the log schedule and graph replay (140 sweeps > 2 x 64)
+    reproduce the oracle bit for bit; the state is converted back after each run."""
+    seed = 1000 + L + nw
+    sched = np.linspace(2.2, 0.6, 170)
+    with micsa.Micsa(L, S, R, seed) as g:
+        g.set_engine("multispin_global")
+        g.set_launch_config(nw, 128, -1, True, 64)
+        g.set_multispin_replicas(rpt)
+        assert g.engine() == "multispin_global"
+        st = O.create(L, S, R, seed)
+        g.run(sched[:140], 7)
+        O.run(st, sched[:140], 7)
+        assert_same_state(g, st, "fixed interval")
+        g.run_logrefresh(sched[140:160])
+        O.run_logrefresh(st, sched[140:160])
+        g.run(sched[160:], 1)
+        O.run(st, sched[160:], 1)
+        assert_same_state(g, st, "log schedule and refresh every sweep")
+
+
+def test_global_multispin_matches_streaming_l160():
+    """At the headline size (L = 160, two replicas) every words-per-thread and
+    replicas-per-thread choice gives the streaming engine's bits."""
+    sched = np.linspace(1.6, 0.7, 150)
+    out = []
+    for engine, nw, rpt in [("stream", 4, 0), ("multispin_global", 1, 0), ("multispin_global", 4, 2),
+                            ("multispin_global", 2, 1)]:
+        with micsa.Micsa(160, 1, 2, 77) as g:
+            g.set_engine(engine)
+            g.set_launch_config(nw, 128, -1, True, 64)
+            if engine == "multispin_global":
+                g.set_multispin_replicas(rpt)
+            g.run(sched, 10)
+            out.append(g.get_state() + (g.measure(),))
+    for s, m, t, meas in out[1:]:
+        np.testing.assert_array_equal(s, out[0][0])
+        np.testing.assert_array_equal(m, out[0][1])
+        for a, b in zip(meas, out[0][3]):
+            np.testing.assert_array_equal(a, b)
+
+
+def test_global_multispin_limits():
+    """L not a multiple of 32 is rejected; gamma > 1 and walkers fall back to the
+    streaming kernel; replicas per thread is range-checked."""
+    with micsa.Micsa(48, 1, 2, 3) as g:
+        with pytest.raises(micsa.MicsaError):
+            g.set_engine("multispin_global")
+    with micsa.Micsa(32, 1, 2, 3, gamma=2) as g:
+        g.set_engine("multispin_global")
+        assert g.engine() == "stream"
+    with micsa.Micsa(32, 1, 2, 3) as g:
+        with pytest.raises(micsa.MicsaError):
+            g.set_multispin_replicas(3)
+        g.set_multispin_replicas(2)
+
+
+@pytest.mark.parametrize("engine", ["stream", "multispin_global"])
+def test_many_replicas_bit_exact(engine):
+    """128 replicas of one sample (the paper's benchmark shape of Sec. 4, at
+    L = 32): sweeps, 8128 overlaps and the 67 KB measure reduction match the oracle."""
+    L, S, R = 32, 1, 128
+    sched = np.linspace(1.8, 0.7, 24)
+    with micsa.Micsa(L, S, R, 128) as g:
+        g.set_engine(engine)
+        st = O.create(L, S, R, 128)
+        g.run(sched, 5)
+        O.run(st, sched, 5)
+        assert_same_state(g, st, engine)
