@@ -32,6 +32,8 @@ Legs on the same JSON line:
                engine (multispin coding in HBM, 32 z per word), its launch shape
                tuned; roofline of its half-sweep kernel: algorithmic bytes
                half_sites * (7 R + 6) / 8 per launch over the mean launch time
+  onchip_l160  the headline workload on the on-chip engine (the state in the
+               shared memory of all SMs, halo rows exchanged through L2)
   paper_shape  L = 160, 1 sample x 128 replicas (the shape of the paper's GPU
                timings), T = 0.7, refresh every 10: bit-plane engine and the
                byte streaming engine
@@ -227,14 +229,21 @@ class Timer:
         return e0.elapsed_time(e1)
 
 
-def leg_roofline(micsa, timer, stream, L, peaks, n_plain=2000):
-    """Plain streaming half-sweep kernel: algorithmic bytes / mean launch time."""
+def leg_roofline(micsa, timer, stream, L, peaks, n_plain=2000, choice=None):
+    """Streaming half-sweep kernel in the launch shape `choice` (the tuned one;
+    default shape if None): algorithmic bytes of one half-sweep of all
+    replicas / mean time per half-sweep. With replica chains the half-sweep is
+    two concurrent launches (one replica each) and the time is their span."""
     R = 2
     g = micsa.Micsa(L, 1, R, 7, stream=stream)
     g.set_engine("stream")
+    if choice is not None and choice.get("engine") == "stream":
+        from paper_2506_16240_gb300 import autotune
+        autotune.apply(g, choice)
     g.run(np.full(1, 0.7), 10)  # t = 0 refresh; the timed sweeps below have none
     g.run(np.full(50, 0.7), 2 ** 31 - 1)
     ms = timer(lambda: g.run(np.full(n_plain, 0.7), 2 ** 31 - 1))
+    shape = g.launch_config()
     g.close()
     launch_us = 1e3 * ms / (2 * n_plain)
     half_sites = L ** 3 // 2
@@ -245,7 +254,8 @@ def leg_roofline(micsa, timer, stream, L, peaks, n_plain=2000):
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": None, "peak_source": "measured" if hbm else "fallback",
             "kernel": "micsa::half_sweep_kernel<4,false> (streaming MicSA half-sweep, no refresh)",
-            "L": L, "bytes_per_launch": bytes_per_launch, "launch_us": launch_us,
+            "L": L, "bytes_per_launch": bytes_per_launch, "launch_us": launch_us, "launch": shape,
+            "replica_chains": (choice or {}).get("chains", 1),
             "flips_per_ns": updates(L, 1, R, n_plain) / (ms * 1e6)}
 
 
@@ -305,6 +315,25 @@ def leg_multispin_l160(micsa, timer, stream, peaks, sweeps=20_000):
     return {"flips_per_ns": updates(L, S, R, sweeps) / (ms * 1e6), "sweeps": sweeps, "launch": shape,
             "energy_per_spin": [float(v) / L ** 3 for v in e], "roofline": roof,
             "note": "same bits as the byte engine (parity-tested); state converted to planes and back per run"}
+
+
+def leg_onchip_l160(micsa, timer, stream, sweeps=5_000):
+    """The headline lattice and schedule on the on-chip engine (state in the
+    shared memory of all SMs, neighbour-CTA synchronisation)."""
+    w = WORKLOAD
+    L, S, R = w["L"], w["samples"], w["replicas"]
+    g = micsa.Micsa(L, S, R, 5, stream=stream)
+    best = None
+    for nw in (4, 2, 1):
+        g.set_launch_config(nw, 128, -1, True, 64)
+        g.set_engine("onchip", 2048)
+        g.run(np.full(200, w["T"]), w["refresh_interval"])
+        ms = timer(lambda: g.run(np.full(sweeps, w["T"]), w["refresh_interval"]))
+        if best is None or ms < best[0]:
+            best = (ms, nw)
+    g.close()
+    return {"flips_per_ns": updates(L, S, R, sweeps) / (best[0] * 1e6), "sweeps": sweeps,
+            "words_per_thread": best[1], "us_per_sweep": 1e3 * best[0] / sweeps}
 
 
 def leg_paper_shape(micsa, timer, stream, peaks, L=160, R=128, sweeps=400):
@@ -489,7 +518,7 @@ def main(argv=None):
     from paper_2506_16240_gb300 import autotune
     # launch shape of the byte-layout engine for this lattice (int8 spins, uint8
     # daemons); the bit-plane engine is timed on the same workload in its own leg
-    tuned = autotune.tune(g, torch, stream, use_cache=False, engines=("stream", "resident", "multispin"))
+    tuned = autotune.tune(g, torch, stream, use_cache=False, engines=("stream", "resident", "multispin", "onchip"))
 
     for k in range(args.warmup):
         g.reinit(seed + k)
@@ -522,7 +551,7 @@ def main(argv=None):
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
-    roofline = leg_roofline(micsa, timer, stream, L, peaks)
+    roofline = leg_roofline(micsa, timer, stream, L, peaks, choice=tuned)
 
     # -- end to end through the C ABI from pinned host buffers
     N = L ** 3
@@ -557,12 +586,13 @@ def main(argv=None):
 
     extras = {}
     if rank == 0 and not args.no_extras:
-        legs = [("dram_point", lambda: leg_roofline(micsa, timer, stream, 320, peaks, n_plain=500)),
+        legs = [("dram_point", lambda: leg_roofline(micsa, timer, stream, 320, peaks, n_plain=500, choice=tuned)),
                 ("metropolis", lambda: leg_metropolis(micsa, timer, stream)),
                 ("quench_l32", lambda: leg_quench_l32(micsa, timer, stream)),
                 ("batched", lambda: leg_batched(micsa, torch, stream)),
                 ("serving", lambda: leg_serving(micsa, torch, stream, args.serving_jobs)),
                 ("multispin_l160", lambda: leg_multispin_l160(micsa, timer, stream, peaks)),
+                ("onchip_l160", lambda: leg_onchip_l160(micsa, timer, stream)),
                 ("paper_shape", lambda: leg_paper_shape(micsa, timer, stream, peaks))]
         for name, fn in legs:
             try:

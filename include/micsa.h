@@ -167,6 +167,16 @@ int micsa_set_launch_config(micsa_t h, int words_per_thread, int block, int bloc
  *                          L <= 40) for resident_sweeps sweeps per launch
  *   MICSA_ENGINE_MULTISPIN as RESIDENT with the replica held as bit planes
  *                          (32 sites per word, Boolean update; L <= 32)
+ *   MICSA_ENGINE_ONCHIP    the whole state in the shared memory of all SMs:
+ *                          each CTA of one cooperative launch owns a range of
+ *                          (z, y) rows of one sample, exchanges the halo rows
+ *                          with its neighbour CTAs through L2 and synchronizes
+ *                          only with them (bounded waits), resident_sweeps
+ *                          sweeps per launch. Needs gamma = 1, no walkers,
+ *                          L >= 8, S <= number of SMs and a state that fits
+ *                          (L = 160 with R <= 2). A wait that runs out makes
+ *                          the next micsa_sync / micsa_measure /
+ *                          micsa_get_state return MICSA_E_TIMEOUT.
  *   MICSA_ENGINE_MULTISPIN_GLOBAL
  *                          bit planes in HBM (32 z per word) for L a multiple
  *                          of 32: each micsa_run converts the byte state to
@@ -176,22 +186,36 @@ int micsa_set_launch_config(micsa_t h, int words_per_thread, int block, int bloc
  *                          per spin per replica and 0.75 per spin per sample.
  * An engine whose size limit the lattice exceeds is rejected. Runs with gamma
  * > 1 or walkers, and Metropolis runs, always use the streaming kernel.
- * resident_sweeps only matters to RESIDENT and MULTISPIN. Synchronizes.
+ * resident_sweeps only matters to RESIDENT, MULTISPIN and ONCHIP. Synchronizes.
  * (App. B and Sec. 2.5 describe the multispin Boolean update.) */
 #define MICSA_ENGINE_AUTO 0
 #define MICSA_ENGINE_STREAM 1
 #define MICSA_ENGINE_RESIDENT 2
 #define MICSA_ENGINE_MULTISPIN 3
 #define MICSA_ENGINE_MULTISPIN_GLOBAL 4
+#define MICSA_ENGINE_ONCHIP 5
 int micsa_set_engine(micsa_t h, int engine, int resident_sweeps);
+
+/* Graph replays of the STREAM and MULTISPIN_GLOBAL engines split the replicas
+ * into `chains` groups (1..4, at most n_replicas; default 1) whose half-sweeps
+ * are captured as concurrent kernel chains joined at the end of each graph:
+ * the groups touch disjoint replicas, so one chain's launch gaps overlap the
+ * others' work. Results do not depend on it. Synchronizes. */
+int micsa_set_replica_chains(micsa_t h, int chains);
 
 /* Replicas one thread of the MULTISPIN_GLOBAL engine runs over the same bond
  * words (1 .. n_replicas; 0 = automatic: as few as keep about 2048 threads per
  * SM busy). Results do not depend on it. Synchronizes. */
 int micsa_set_multispin_replicas(micsa_t h, int replicas_per_thread);
 
-/* The engine that the next micsa_run will use (STREAM, RESIDENT, MULTISPIN or
- * MULTISPIN_GLOBAL). */
+/* Self-test of the bounded wait of the ONCHIP engine: one CTA waits on an
+ * epoch flag that nothing sets, giving up after `polls` polls. *timed_out
+ * receives 1 when the wait ran out and reported it (the expected result).
+ * Uses the current device; synchronous. */
+int micsa_wait_selftest(int64_t polls, int *timed_out);
+
+/* The engine that the next micsa_run will use (STREAM, RESIDENT, MULTISPIN,
+ * MULTISPIN_GLOBAL or ONCHIP). */
 int micsa_get_engine(micsa_t h, int *engine);
 
 /* The launch shape requested (words_per_thread as set, reduced to what the row

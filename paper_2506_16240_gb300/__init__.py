@@ -27,8 +27,10 @@ MICSA_E_NOT_FOUND = -6
 MICSA_E_TOO_LARGE = -7
 MICSA_ENGINE_AUTO, MICSA_ENGINE_STREAM, MICSA_ENGINE_RESIDENT, MICSA_ENGINE_MULTISPIN = 0, 1, 2, 3
 MICSA_ENGINE_MULTISPIN_GLOBAL = 4
+MICSA_ENGINE_ONCHIP = 5
 ENGINES = {"auto": MICSA_ENGINE_AUTO, "stream": MICSA_ENGINE_STREAM, "resident": MICSA_ENGINE_RESIDENT,
-           "multispin": MICSA_ENGINE_MULTISPIN, "multispin_global": MICSA_ENGINE_MULTISPIN_GLOBAL}
+           "multispin": MICSA_ENGINE_MULTISPIN, "multispin_global": MICSA_ENGINE_MULTISPIN_GLOBAL,
+           "onchip": MICSA_ENGINE_ONCHIP}
 MICSA_NOALLOC_MAX_TERMS = 8192
 
 _ERRNAMES = {-1: "MICSA_E_INVALID_ARG", -2: "MICSA_E_OOM", -3: "MICSA_E_CUDA",
@@ -74,6 +76,8 @@ SIGNATURES = {
     "micsa_set_engine": (_c.c_int, [_P, _c.c_int, _c.c_int]),
     "micsa_get_engine": (_c.c_int, [_P, _ip]),
     "micsa_set_multispin_replicas": (_c.c_int, [_P, _c.c_int]),
+    "micsa_wait_selftest": (_c.c_int, [_c.c_int64, _ip]),
+    "micsa_set_replica_chains": (_c.c_int, [_P, _c.c_int]),
     "micsa_destroy": (None, [_P]),
     "micsa_last_error": (_c.c_char_p, [_P]),
     "micsa_measure_noalloc": (_c.c_int, [_P, _P, _P, _c.c_int, _c.c_int, _c.c_int, _P, _P, _P, _P]),
@@ -119,6 +123,14 @@ def metro_thresholds(T):
     th = (ctypes.c_uint64 * 3)()
     _check(lib().micsa_metro_thresholds(float(T), th))
     return np.array(list(th), np.uint64)
+
+
+def wait_selftest(polls=1000):
+    """Run the on-chip engine's bounded wait on a flag nothing sets; True when
+    it gave up and reported the time-out."""
+    out = ctypes.c_int()
+    _check(lib().micsa_wait_selftest(int(polls), ctypes.byref(out)))
+    return bool(out.value)
 
 
 def measure_noalloc(spins_ptr, daemons_ptr, J_ptr, L, n_samples, n_replicas, stream_ptr=None):
@@ -250,8 +262,16 @@ class Micsa:
         keys = ("words_per_thread", "block", "blocks_per_sm", "pdl", "graph_sweeps")
         return {k: x.value for k, x in zip(keys, v)}
 
-    def set_engine(self, engine="auto", resident_sweeps=64):
+    def set_engine(self, engine="auto", resident_sweeps=None):
+        """resident_sweeps: sweeps per launch of the resident, multispin and
+        onchip engines (default 64, and 2048 for onchip)."""
+        if resident_sweeps is None:
+            resident_sweeps = 2048 if engine == "onchip" else 64
         _check(lib().micsa_set_engine(self.h, ENGINES[engine], int(resident_sweeps)), self.h)
+
+    def set_replica_chains(self, chains=1):
+        """Replica groups captured as concurrent kernel chains (1..4)."""
+        _check(lib().micsa_set_replica_chains(self.h, int(chains)), self.h)
 
     def set_multispin_replicas(self, replicas_per_thread=0):
         """Replicas per thread of the multispin_global engine (0: automatic)."""

@@ -15,7 +15,7 @@ import os
 
 import numpy as np
 
-from . import Micsa
+from . import Micsa, MicsaError
 
 CACHE = os.environ.get("MICSA_AUTOTUNE_CACHE",
                        os.path.join(os.path.expanduser("~"), ".cache", "micsa_autotune.json"))
@@ -50,6 +50,10 @@ def candidates(L, R=1):
     # register-capped variant (64 registers, up to 8 blocks of 128 per SM)
     out += [{"engine": "stream", "words_per_thread": nw | 256, "block": blk, "blocks_per_sm": bps}
             for nw, blk, bps in itertools.product([4, 2], [64, 128], [-1, 0, 4, 6, 8])]
+    if R >= 2:  # replica groups as concurrent kernel chains in the graphs
+        out += [{"engine": "stream", "words_per_thread": 4, "block": blk, "blocks_per_sm": bps, "chains": 2}
+                for blk, bps in itertools.product([128, 256], [-1, 2, 3, 4])]
+    out += [{"engine": "onchip", "words_per_thread": nw} for nw in (4, 1)]  # where the state fits on chip
     if L <= 40:
         out.append({"engine": "resident"})
     if L <= 32:
@@ -58,13 +62,20 @@ def candidates(L, R=1):
         rpts = sorted({0} | {r for r in (1, 2, 4, 8, 16, 32) if r <= R})
         out += [{"engine": "multispin_global", "words_per_thread": nw, "replicas_per_thread": rpt}
                 for nw, rpt in itertools.product([1, 2, 4], rpts)]
+        if R >= 2:
+            out += [{"engine": "multispin_global", "words_per_thread": nw, "replicas_per_thread": 0, "chains": 2}
+                    for nw in (1, 2, 4)]
     return out
 
 
 def apply(g, choice, resident_sweeps=256):
+    g.set_replica_chains(choice.get("chains", 1))
     if choice["engine"] == "stream":
         g.set_engine("stream")
         g.set_launch_config(choice["words_per_thread"], choice["block"], choice["blocks_per_sm"], True, 64)
+    elif choice["engine"] == "onchip":
+        g.set_launch_config(choice["words_per_thread"], 128, -1, True, 64)
+        g.set_engine("onchip", 2048)
     elif choice["engine"] == "multispin_global":
         g.set_engine("multispin_global")
         g.set_launch_config(choice["words_per_thread"], 128, -1, True, 64)
@@ -88,7 +99,10 @@ def tune(g, torch, stream, sweeps=400, T=0.7, refresh_interval=10, use_cache=Tru
     for c in candidates(g.L, g.R):
         if engines is not None and c["engine"] not in engines:
             continue
-        apply(g, c)
+        try:
+            apply(g, c)
+        except MicsaError:  # the lattice does not fit this engine
+            continue
         g.run(sched[: max(10, sweeps // 10)], refresh_interval)  # warm-up of this shape
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)

@@ -47,9 +47,18 @@ struct micsa_ctx {
     int resident_sweeps = 256;       // sweeps per resident launch
     ResidentUnit *d_units = nullptr; // one unit per (sample, replica)
     int graph_g[3] = {0, 0, 0};
+    int64_t graph_kernels[3] = {0, 0, 0};  // kernels per replay of each graph
+    int chains = 1;                  // replica groups captured as concurrent chains
+    cudaStream_t aux_stream[3] = {nullptr, nullptr, nullptr};  // capture streams of chains 1..3
+    cudaEvent_t fork_ev = nullptr, join_ev[3] = {nullptr, nullptr, nullptr};
     uint32_t *d_planes = nullptr;    // multispin planes [S*R][3][2][L^3/64] (MULTISPIN_GLOBAL)
     uint32_t *d_bplanes = nullptr;   // bond planes [S][6][2][L^3/64]
     int msg_rpt = 0;                 // replicas per thread of MULTISPIN_GLOBAL (0: automatic)
+    OnchipPlan oc;                   // partition of the ONCHIP engine (oc.grid == 0: not planned)
+    int16_t *d_oc_nbrs = nullptr;    // its neighbour table
+    unsigned *d_oc_flags = nullptr;  // its epoch flags
+    int *d_error = nullptr;          // device-side wait time-outs (ONCHIP)
+    long long wait_limit = 1ll << 22;  // polls per wait
     std::string err;
 };
 
@@ -128,7 +137,15 @@ SweepArgs sweep_args(const micsa_ctx *h) {
     a.gamma = h->gamma;
     a.key0 = (uint32_t)(h->seed & 0xFFFFFFFFu);
     a.key1 = (uint32_t)(h->seed >> 32);
+    a.r0 = 0;
+    a.r1 = h->R;
     return a;
+}
+
+// Replicas [r0, r1) of replica group c of n (as even as possible).
+void replica_group(const micsa_ctx *h, int c, int n, int &r0, int &r1) {
+    r0 = c * h->R / n;
+    r1 = (c + 1) * h->R / n;
 }
 
 void drop_graphs(micsa_t h) {
@@ -178,37 +195,66 @@ int ensure_params(micsa_t h, int64_t n) {
 
 enum GraphKind { kGraphMicsa = 0, kGraphMetro = 1, kGraphPlanes = 2 };
 
-int msg_rpt(const micsa_ctx *h, int nw) {
-    return h->msg_rpt > 0 ? h->msg_rpt : msg_default_rpt(h->geo, h->S, h->R, nw, h->sm_count);
+int msg_rpt(const micsa_ctx *h, int nw, int n_rep) {
+    return h->msg_rpt > 0 ? h->msg_rpt : msg_default_rpt(h->geo, h->S, n_rep, nw, h->sm_count);
 }
 
-// One half-sweep of the bit-plane engine reading params[*cursor + k].
+// One half-sweep of the bit-plane engine over replicas [r0, r1), reading
+// params[*cursor + k].
 cudaError_t launch_planes_half(micsa_t h, const LaunchConfig &lc, int parity, const int64_t *cursor, int64_t k,
-                               cudaStream_t st) {
-    return launch_msg_half(h->d_planes, h->d_bplanes, h->geo, h->S, h->R, msg_rpt(h, lc.nw), lc.nw, parity,
-                           (uint32_t)(h->seed & 0xFFFFFFFFu), (uint32_t)(h->seed >> 32), h->d_params, cursor, k,
-                           lc.pdl, st);
+                               int r0, int r1, cudaStream_t st) {
+    return launch_msg_half(h->d_planes, h->d_bplanes, h->geo, h->S, h->R, r0, r1, msg_rpt(h, lc.nw, r1 - r0), lc.nw,
+                           parity, (uint32_t)(h->seed & 0xFFFFFFFFu), (uint32_t)(h->seed >> 32), h->d_params, cursor,
+                           k, lc.pdl, st);
+}
+
+// One half-sweep of graph kind gi over replica group c of `chains`.
+cudaError_t launch_group_half(micsa_t h, int gi, const LaunchConfig &lc, SweepArgs a, int c, int chains,
+                              cudaStream_t st) {
+    replica_group(h, c, chains, a.r0, a.r1);
+    if (gi == kGraphPlanes) return launch_planes_half(h, lc, a.parity, a.cursor, a.k, a.r0, a.r1, st);
+    return launch_half_sweep(a, gi == kGraphMetro, lc, st);
 }
 
 // Capture G sweeps (2G half-sweeps reading params[*cursor + k]) and the cursor
-// advance into an executable graph.
+// advance into an executable graph. With chains > 1 the replica groups are
+// independent chains of half-sweeps on forked capture streams (they touch
+// disjoint replicas), joined before the cursor advance, so that one chain's
+// launch gap and tail overlap the other chains' work.
 int capture_graph(micsa_t h, int gi, int G, const LaunchConfig &lc) {
-    const bool metro = gi == kGraphMetro;
     if (h->graph[gi] && h->graph_g[gi] == G) return MICSA_OK;
     if (h->graph[gi]) cudaGraphExecDestroy(h->graph[gi]);
     h->graph[gi] = nullptr;
+    const int chains = std::min(h->chains, h->R);
+    for (int c = 1; c < chains; ++c) {
+        if (!h->aux_stream[c - 1])
+            CK(h, cudaStreamCreateWithFlags(&h->aux_stream[c - 1], cudaStreamNonBlocking), "cudaStreamCreate");
+        if (!h->join_ev[c - 1])
+            CK(h, cudaEventCreateWithFlags(&h->join_ev[c - 1], cudaEventDisableTiming), "cudaEventCreate");
+    }
+    if (!h->fork_ev) CK(h, cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming), "cudaEventCreate");
     SweepArgs a = sweep_args(h);
     a.params = h->d_params;
     a.cursor = h->d_cursor;
     CK(h, cudaStreamBeginCapture(h->capture_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
     cudaError_t e = cudaSuccess;
-    for (int k = 0; k < G && e == cudaSuccess; ++k)
-        for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
-            a.k = k;
-            a.parity = p;
-            e = gi == kGraphPlanes ? launch_planes_half(h, lc, p, h->d_cursor, k, h->capture_stream)
-                                   : launch_half_sweep(a, metro, lc, h->capture_stream);
-        }
+    if (chains > 1) {
+        e = cudaEventRecord(h->fork_ev, h->capture_stream);
+        for (int c = 1; c < chains && e == cudaSuccess; ++c) e = cudaStreamWaitEvent(h->aux_stream[c - 1], h->fork_ev, 0);
+    }
+    for (int c = 0; c < chains && e == cudaSuccess; ++c) {
+        cudaStream_t st = c == 0 ? h->capture_stream : h->aux_stream[c - 1];
+        for (int k = 0; k < G && e == cudaSuccess; ++k)
+            for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
+                a.k = k;
+                a.parity = p;
+                e = launch_group_half(h, gi, lc, a, c, chains, st);
+            }
+    }
+    for (int c = 1; c < chains && e == cudaSuccess; ++c) {
+        e = cudaEventRecord(h->join_ev[c - 1], h->aux_stream[c - 1]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(h->capture_stream, h->join_ev[c - 1], 0);
+    }
     if (e == cudaSuccess) e = launch_advance_cursor(h->d_cursor, G, lc.pdl, h->capture_stream);
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(h->capture_stream, &graph);
@@ -224,6 +270,7 @@ int capture_graph(micsa_t h, int gi, int G, const LaunchConfig &lc) {
         return cuda_fail(h, e, "graph instantiate");
     }
     h->graph_g[gi] = G;
+    h->graph_kernels[gi] = 2 * (int64_t)G * chains + 1;
     return MICSA_OK;
 }
 
@@ -232,6 +279,7 @@ int active_engine(micsa_t h) {
     if (h->engine == MICSA_ENGINE_STREAM || h->gamma > 1 || h->walkers) return MICSA_ENGINE_STREAM;
     if (h->engine == MICSA_ENGINE_MULTISPIN_GLOBAL)
         return msg_supported(h->geo) ? MICSA_ENGINE_MULTISPIN_GLOBAL : MICSA_ENGINE_STREAM;
+    if (h->engine == MICSA_ENGINE_ONCHIP) return h->oc.grid > 0 ? MICSA_ENGINE_ONCHIP : MICSA_ENGINE_STREAM;
     if (!h->d_units) return MICSA_ENGINE_STREAM;
     if (h->engine == MICSA_ENGINE_RESIDENT) return MICSA_ENGINE_RESIDENT;
     if (multispin_smem_bytes(h->geo) > 0) return MICSA_ENGINE_MULTISPIN;
@@ -275,12 +323,12 @@ int run_planes(micsa_t h, int64_t n, const LaunchConfig &lc) {
         CK(h, cudaMemsetAsync(h->d_cursor, 0, sizeof(int64_t), h->stream), "reset cursor");
         const int64_t reps = n / G;
         for (int64_t r = 0; r < reps; ++r) CK(h, cudaGraphLaunch(h->graph[kGraphPlanes], h->stream), "graph launch");
-        h->launches += reps * (2 * (int64_t)G + 1);
+        h->launches += reps * h->graph_kernels[kGraphPlanes];
         done = reps * G;
     }
     for (int64_t k = done; k < n; ++k)
         for (int p = 0; p < 2; ++p) {
-            CK(h, launch_planes_half(h, lc, p, nullptr, k, h->stream), "plane half-sweep launch");
+            CK(h, launch_planes_half(h, lc, p, nullptr, k, 0, h->R, h->stream), "plane half-sweep launch");
             ++h->launches;
         }
     CK(h, msg_convert(h->d_planes, nullptr, h->d_spins, h->d_daemons, nullptr, h->geo, h->S, h->R, false,
@@ -317,6 +365,59 @@ int run_resident(micsa_t h, int64_t n, const LaunchConfig &lc) {
     return MICSA_OK;
 }
 
+// Partition, neighbour table and flags of the ONCHIP engine for words-per-item nw.
+int plan_onchip(micsa_t h, int nw) {
+    if (h->oc.grid > 0 && h->oc.nw == nw) return MICSA_OK;
+    OnchipPlan plan;
+    if (h->gamma > 1 || h->walkers || !onchip_plan(h->geo, h->S, h->R, h->sm_count, nw, plan))
+        return fail(h, MICSA_E_INVALID_ARG, "the on-chip engine does not fit this lattice (L=%d S=%d R=%d)", h->L,
+                    h->S, h->R);
+    CK(h, cudaStreamSynchronize(h->stream), "synchronize before planning");
+    cudaFree(h->d_oc_nbrs);
+    cudaFree(h->d_oc_flags);
+    h->d_oc_nbrs = nullptr;
+    h->d_oc_flags = nullptr;
+    h->oc = OnchipPlan();
+    CK(h, cudaMalloc(&h->d_oc_nbrs, sizeof(int16_t) * plan.table.size()), "cudaMalloc neighbour table");
+    CK(h, cudaMemcpy(h->d_oc_nbrs, plan.table.data(), sizeof(int16_t) * plan.table.size(), cudaMemcpyHostToDevice),
+       "upload neighbour table");
+    CK(h, cudaMalloc(&h->d_oc_flags, sizeof(unsigned) * onchip_flag_words(plan.grid)), "cudaMalloc flags");
+    if (!h->d_error) {
+        CK(h, cudaMalloc(&h->d_error, sizeof(int)), "cudaMalloc error word");
+        CK(h, cudaMemset(h->d_error, 0, sizeof(int)), "clear error word");
+    }
+    h->oc = std::move(plan);
+    return MICSA_OK;
+}
+
+// MicSA sweeps [0, n) of the uploaded table with the on-chip engine,
+// resident_sweeps sweeps per cooperative launch.
+int run_onchip(micsa_t h, int64_t n, const LaunchConfig &lc) {
+    if (int rc = plan_onchip(h, lc.nw)) return rc;
+    for (int64_t k0 = 0; k0 < n; k0 += h->resident_sweeps) {
+        const int K = (int)std::min<int64_t>(h->resident_sweeps, n - k0);
+        CK(h, launch_onchip(h->oc, h->d_spins, h->d_daemons, h->d_bonds, h->geo, h->S, h->R,
+                            (uint32_t)(h->seed & 0xFFFFFFFFu), (uint32_t)(h->seed >> 32), h->d_params, k0, K,
+                            h->d_oc_flags, h->d_error, h->d_oc_nbrs, h->wait_limit, h->stream),
+           "on-chip launch");
+        ++h->launches;
+    }
+    return MICSA_OK;
+}
+
+// A device-side wait that ran out since the last check (ONCHIP engine).
+int check_device_error(micsa_t h) {
+    if (!h->d_error) return MICSA_OK;
+    int v = 0;
+    CK(h, cudaMemcpyAsync(&v, h->d_error, sizeof(int), cudaMemcpyDeviceToHost, h->stream), "read error word");
+    CK(h, cudaStreamSynchronize(h->stream), "synchronize error word");
+    if (v) {
+        CK(h, cudaMemsetAsync(h->d_error, 0, sizeof(int), h->stream), "clear error word");
+        return fail(h, MICSA_E_TIMEOUT, "a device-side wait of the on-chip engine ran out; the state is not valid");
+    }
+    return MICSA_OK;
+}
+
 // Upload the table of n sweeps and run them: whole blocks of G sweeps by graph
 // replay, the rest by direct launches. Every sweep is the even half-sweep
 // followed by the odd one (Sec. 2.8 steps (i), (ii)).
@@ -328,6 +429,7 @@ int run_table(micsa_t h, bool metro, int64_t n) {
     CK(h, cudaEventRecord(h->params_free, h->stream), "record parameter event");
     if (!metro && use_resident(h)) return run_resident(h, n, lc);
     if (!metro && active_engine(h) == MICSA_ENGINE_MULTISPIN_GLOBAL) return run_planes(h, n, lc);
+    if (!metro && active_engine(h) == MICSA_ENGINE_ONCHIP) return run_onchip(h, n, lc);
     const int G = lc.graph_sweeps;
     int64_t done = 0;
     if (G > 0 && n >= 2 * (int64_t)G) {
@@ -336,7 +438,7 @@ int run_table(micsa_t h, bool metro, int64_t n) {
         const int64_t reps = n / G;
         for (int64_t r = 0; r < reps; ++r)
             CK(h, cudaGraphLaunch(h->graph[metro ? 1 : 0], h->stream), "graph launch");
-        h->launches += reps * (2 * (int64_t)G + 1);
+        h->launches += reps * h->graph_kernels[metro ? 1 : 0];
         done = reps * G;
     }
     SweepArgs a = sweep_args(h);
@@ -499,6 +601,14 @@ void micsa_destroy(micsa_t h) {
     cudaFree(h->d_units);
     cudaFree(h->d_planes);
     cudaFree(h->d_bplanes);
+    cudaFree(h->d_oc_nbrs);
+    cudaFree(h->d_oc_flags);
+    cudaFree(h->d_error);
+    for (int c = 0; c < 3; ++c) {
+        if (h->aux_stream[c]) cudaStreamDestroy(h->aux_stream[c]);
+        if (h->join_ev[c]) cudaEventDestroy(h->join_ev[c]);
+    }
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
     cudaFree(h->d_params);
     cudaFreeHost(h->h_params);
     drop_graphs(h);
@@ -667,7 +777,7 @@ int micsa_set_launch_config(micsa_t h, int words_per_thread, int block, int bloc
 
 int micsa_set_engine(micsa_t h, int engine, int resident_sweeps) {
     if (!h) return MICSA_E_INVALID_ARG;
-    if (engine < MICSA_ENGINE_AUTO || engine > MICSA_ENGINE_MULTISPIN_GLOBAL || resident_sweeps < 1 ||
+    if (engine < MICSA_ENGINE_AUTO || engine > MICSA_ENGINE_ONCHIP || resident_sweeps < 1 ||
         resident_sweeps > 1 << 20)
         return fail(h, MICSA_E_INVALID_ARG, "bad engine selection");
     if (engine == MICSA_ENGINE_MULTISPIN_GLOBAL && !msg_supported(h->geo))
@@ -678,8 +788,20 @@ int micsa_set_engine(micsa_t h, int engine, int resident_sweeps) {
         return fail(h, MICSA_E_INVALID_ARG, "the multispin engine needs L <= 32 (L=%d)", h->L);
     DeviceGuard dg(h->device);
     CK(h, cudaStreamSynchronize(h->stream), "synchronize before reconfiguring");
+    if (engine == MICSA_ENGINE_ONCHIP)
+        if (int rc = plan_onchip(h, effective_config(h, false).nw)) return rc;
     h->engine = engine;
     h->resident_sweeps = resident_sweeps;
+    return MICSA_OK;
+}
+
+int micsa_set_replica_chains(micsa_t h, int chains) {
+    if (!h) return MICSA_E_INVALID_ARG;
+    if (chains < 1 || chains > 4) return fail(h, MICSA_E_INVALID_ARG, "replica chains must be in 1..4");
+    DeviceGuard dg(h->device);
+    CK(h, cudaStreamSynchronize(h->stream), "synchronize before reconfiguring");
+    drop_graphs(h);
+    h->chains = chains;
     return MICSA_OK;
 }
 
@@ -715,6 +837,7 @@ int micsa_get_launch_config(micsa_t h, int *words_per_thread, int *block, int *b
 int micsa_measure(micsa_t h, int64_t *energy, int64_t *aux, int64_t *overlap) {
     if (!h) return MICSA_E_INVALID_ARG;
     DeviceGuard dg(h->device);
+    if (int rc = check_device_error(h)) return rc;
     const size_t SR = (size_t)h->S * h->R;
     const size_t npair = (size_t)h->S * h->R * (h->R - 1) / 2;
     const size_t n = 2 * SR + npair;
@@ -757,6 +880,7 @@ int micsa_correlation(micsa_t h, int64_t *G) {
 int micsa_get_state(micsa_t h, int8_t *spins, uint8_t *daemons, int64_t *t) {
     if (!h) return MICSA_E_INVALID_ARG;
     DeviceGuard dg(h->device);
+    if (int rc = check_device_error(h)) return rc;
     const int64_t n = (int64_t)h->S * h->R;
     const size_t bytes = (size_t)(n * sites(h));
     const size_t dbytes = bytes * (size_t)h->gamma;
@@ -823,7 +947,24 @@ int micsa_sync(micsa_t h) {
     if (!h) return MICSA_E_INVALID_ARG;
     DeviceGuard dg(h->device);
     CK(h, cudaStreamSynchronize(h->stream), "synchronize");
-    return MICSA_OK;
+    return check_device_error(h);
+}
+
+int micsa_wait_selftest(int64_t polls, int *timed_out) {
+    if (!timed_out || polls < 0) return MICSA_E_INVALID_ARG;
+    *timed_out = 0;
+    unsigned *flag = nullptr;
+    int *err = nullptr;
+    int v = 0, rc = MICSA_OK;
+    if (cudaMalloc(&flag, sizeof(unsigned)) != cudaSuccess || cudaMalloc(&err, sizeof(int)) != cudaSuccess ||
+        cudaMemset(flag, 0, sizeof(unsigned)) != cudaSuccess || cudaMemset(err, 0, sizeof(int)) != cudaSuccess ||
+        launch_wait_selftest(flag, err, (long long)polls, nullptr) != cudaSuccess ||
+        cudaMemcpy(&v, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        rc = MICSA_E_CUDA;
+    cudaFree(flag);
+    cudaFree(err);
+    *timed_out = v;
+    return rc;
 }
 
 int micsa_launch_count(micsa_t h, int64_t *count) {

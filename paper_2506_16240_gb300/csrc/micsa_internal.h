@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "micsa_device.cuh"
 
@@ -32,6 +33,7 @@ struct SweepArgs {
     const SweepParam *params;    // the run's table
     const int64_t *cursor;       // graph replays: base index into params; else nullptr
     int64_t k;                   // this sweep's index relative to *cursor (or absolute)
+    int r0, r1;                  // replicas [r0, r1) of every sample are updated (0, R: all)
     FastDiv div_chunks;          // row -> (row, chunk): divide by chunks per row
     FastDiv div_L;               // row -> (z, y): divide by L
 };
@@ -45,6 +47,7 @@ struct LaunchConfig {
     bool pdl = true;     // programmatic dependent launch between consecutive grids
     int graph_sweeps = 64;  // sweeps per captured CUDA graph (0: no graphs)
     bool regcap = false;    // kernel variant with registers capped at 64 (blocks of <= 128)
+    int chains = 1;         // replica groups captured as concurrent kernel chains in one graph
 };
 
 // One job of the batched pool (device-resident descriptor).
@@ -147,14 +150,29 @@ size_t multispin_smem_bytes(const Geometry &g);  // 0 when L > 32
 cudaError_t launch_multispin(const ResidentArgs &a, bool pool, size_t smem, int grid, bool pdl, cudaStream_t st);
 int multispin_blocks_per_sm(bool pool, size_t smem);
 
+// persistent engine with the state in the shared memory of all SMs (onchip.cu)
+struct OnchipPlan {
+    int grid = 0, k = 0, qmax = 0, nw = 0;  // CTAs, CTAs per sample, rows per CTA, words per item
+    size_t smem = 0;
+    std::vector<int16_t> table;  // [grid][max neighbours], -1 terminated
+};
+bool onchip_plan(const Geometry &g, int S, int R, int ctas, int nw, OnchipPlan &plan);
+size_t onchip_flag_words(int grid);
+int onchip_max_neighbours();
+cudaError_t launch_onchip(const OnchipPlan &plan, int8_t *spins, uint8_t *daemons, const uint8_t *bonds,
+                          const Geometry &g, int S, int R, uint32_t key0, uint32_t key1, const SweepParam *params,
+                          int64_t k0, int K, unsigned *flags, int *error, const int16_t *nbrs, long long wait_limit,
+                          cudaStream_t st);
+cudaError_t launch_wait_selftest(unsigned *flag, int *error, long long wait_limit, cudaStream_t st);
+
 // multispin planes in global memory for L % 32 == 0 (multispin.cu)
 bool msg_supported(const Geometry &g);
 int64_t msg_plane_words(const Geometry &g);  // words per parity plane, L^3 / 64
 cudaError_t msg_convert(uint32_t *planes, uint32_t *bplanes, int8_t *spins, uint8_t *daemons, const uint8_t *bonds,
                         const Geometry &g, int S, int R, bool to_planes, cudaStream_t st);
 int msg_default_rpt(const Geometry &g, int S, int R, int nw, int sm_count);
-cudaError_t launch_msg_half(uint32_t *planes, const uint32_t *bplanes, const Geometry &g, int S, int R, int rpt,
-                            int nw, int parity, uint32_t key0, uint32_t key1, const SweepParam *params,
+cudaError_t launch_msg_half(uint32_t *planes, const uint32_t *bplanes, const Geometry &g, int S, int R, int r0,
+                            int r1, int rpt, int nw, int parity, uint32_t key0, uint32_t key1, const SweepParam *params,
                             const int64_t *cursor, int64_t k, bool pdl, cudaStream_t st);
 cudaError_t launch_advance_cursor(int64_t *cursor, int64_t step, bool pdl, cudaStream_t st);
 // wandering of every walker family after timestep t (parity t & 1), Sec. 2.6

@@ -476,7 +476,7 @@ struct MsgArgs {
     const uint32_t *bonds;   // [S][6][2][WP]
     int L, Lh, nzw, W4;      // W4 = Lh / 4 Philox blocks per row
     int64_t WP;
-    int S, R, rpt, parity;
+    int S, R, r0, r1, rpt, parity;  // replicas [r0, r1) of every sample, rpt per thread
     uint32_t key0, key1;
     const SweepParam *params;
     const int64_t *cursor;
@@ -551,8 +551,8 @@ __global__ void __launch_bounds__(128) msg_half_kernel(MsgArgs a) {
     const int lig = (int)(threadIdx.x & (G - 1));  // this lane's share of the Philox block
     const uint32_t quad0 = (uint32_t)(((int64_t)p * L + 32 * zw) * L + y) * a.W4 + (uint32_t)(i0 >> 2);
 
-    const int r_end = min(a.R, (int)(blockIdx.y + 1) * a.rpt);
-    for (int r = blockIdx.y * a.rpt; r < r_end; ++r) {
+    const int r_end = min(a.r1, a.r0 + (int)(blockIdx.y + 1) * a.rpt);
+    for (int r = a.r0 + blockIdx.y * a.rpt; r < r_end; ++r) {
         const int64_t gid = (int64_t)sample * a.R + r;
         uint32_t *pl = a.planes + gid * 6 * a.WP;
         const uint32_t *O = pl + (int64_t)o * a.WP;  // spins of the opposite parity
@@ -724,8 +724,8 @@ int msg_default_rpt(const Geometry &g, int S, int R, int nw, int sm_count) {
     return (R + groups - 1) / groups;
 }
 
-cudaError_t launch_msg_half(uint32_t *planes, const uint32_t *bplanes, const Geometry &g, int S, int R, int rpt,
-                            int nw, int parity, uint32_t key0, uint32_t key1, const SweepParam *params,
+cudaError_t launch_msg_half(uint32_t *planes, const uint32_t *bplanes, const Geometry &g, int S, int R, int r0,
+                            int r1, int rpt, int nw, int parity, uint32_t key0, uint32_t key1, const SweepParam *params,
                             const int64_t *cursor, int64_t k, bool pdl, cudaStream_t st) {
     MsgArgs a{};
     a.planes = planes;
@@ -737,6 +737,8 @@ cudaError_t launch_msg_half(uint32_t *planes, const uint32_t *bplanes, const Geo
     a.WP = msg_plane_words(g);
     a.S = S;
     a.R = R;
+    a.r0 = r0;
+    a.r1 = r1;
     a.rpt = rpt;
     a.parity = parity;
     a.key0 = key0;
@@ -745,9 +747,9 @@ cudaError_t launch_msg_half(uint32_t *planes, const uint32_t *bplanes, const Geo
     a.cursor = cursor;
     a.k = k;
     const int64_t threads = (int64_t)S * g.L * (g.L / 32) * (g.Lh / nw);
-    if (threads % 128 != 0 || rpt < 1) return cudaErrorInvalidValue;
+    if (threads % 128 != 0 || rpt < 1 || r0 < 0 || r1 > R || r0 >= r1) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(threads / 128), (unsigned)((R + rpt - 1) / rpt));
+    cfg.gridDim = dim3((unsigned)(threads / 128), (unsigned)((r1 - r0 + rpt - 1) / rpt));
     cfg.blockDim = dim3(128);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];

@@ -37,9 +37,9 @@ __device__ __forceinline__ void half_sweep_body(const SweepArgs &a) {
     const bool refresh = !METRO && prm.mode == kModeRefresh;
 
     // grid: x over the chunks of one sample, y over samples; thread row y of
-    // the block takes replicas threadIdx.y, threadIdx.y + blockDim.y, ...
+    // the block takes replicas r0 + threadIdx.y, r0 + threadIdx.y + blockDim.y, ... < r1
     for (int sample = blockIdx.y; sample < a.S; sample += gridDim.y)
-        for (int r = threadIdx.y; r < a.R; r += blockDim.y)
+        for (int r = a.r0 + threadIdx.y; r < a.r1; r += blockDim.y)
             for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < per_sample; q += gridDim.x * blockDim.x) {
                 const uint32_t row = fdiv(q, a.div_chunks);
                 const int c = (int)(q - row * a.div_chunks.d);
@@ -127,7 +127,7 @@ static cudaError_t launch_variant(const SweepArgs &a0, const LaunchConfig &lc, c
     a.div_chunks = make_fastdiv((uint32_t)chunks);
     a.div_L = make_fastdiv((uint32_t)a.geo.L);
     const int64_t per_sample = (int64_t)a.geo.L * a.geo.L * chunks;
-    const dim3 blk = block_shape(a.R, lc.regcap && lc.block > 128 ? 128 : lc.block);
+    const dim3 blk = block_shape(a.r1 - a.r0, lc.regcap && lc.block > 128 ? 128 : lc.block);
     int64_t gx = (per_sample + blk.x - 1) / blk.x;
     int64_t gy = a.S < 65535 ? a.S : 65535;
     if (lc.max_blocks > 0 && gx * gy > lc.max_blocks) {  // grid-stride cap over chunks

@@ -1,7 +1,10 @@
 """Small fixed workloads for profiler captures (ncu) of the main kernels.
 
     python -m paper_2506_16240_gb300.profile_run stream     # L=160, 1 x 2: 30 MicSA + 4 Metropolis sweeps
+    python -m paper_2506_16240_gb300.profile_run chains     # the same with the two replicas as two chains
     python -m paper_2506_16240_gb300.profile_run multispin  # L=32, 64 x 2: 128 sweeps, blocks of 64
+    python -m paper_2506_16240_gb300.profile_run planes     # L=160, 1 x 128, bit planes: 12 sweeps
+    python -m paper_2506_16240_gb300.profile_run onchip     # L=160, 1 x 2, on-chip engine: 2 x 64 sweeps
     python -m paper_2506_16240_gb300.profile_run pool       # 64 mixed jobs, 2 ticks of 64 sweeps
 
 Each run is a few milliseconds of GPU work on a few tens of MB, sized for
@@ -19,6 +22,30 @@ def stream():
     g.set_engine("stream")
     g.run(np.full(30, 0.7), 10)
     g.run_metropolis(np.full(4, 0.7))
+    return g.measure()[0]
+
+
+def chains():
+    g = micsa.Micsa(160, 1, 2, 3)
+    g.set_engine("stream")
+    g.set_replica_chains(2)
+    g.run(np.full(140, 0.7), 10)  # 2 graph replays of 64 sweeps + 12 direct
+    return g.measure()[0]
+
+
+def planes():
+    g = micsa.Micsa(160, 1, 128, 3)
+    g.set_engine("multispin_global")
+    g.set_launch_config(4, 128, -1, True, 0)  # direct launches
+    g.run(np.full(12, 0.7), 10)
+    return g.measure()[0][:4]
+
+
+def onchip():
+    g = micsa.Micsa(160, 1, 2, 3)
+    g.set_launch_config(4, 128, -1, True, 64)
+    g.set_engine("onchip", 64)
+    g.run(np.full(128, 0.7), 10)
     return g.measure()[0]
 
 
@@ -42,4 +69,6 @@ def pool():
 
 if __name__ == "__main__":
     mode = sys.argv[1] if len(sys.argv) > 1 else "stream"
-    print(mode, {"stream": stream, "multispin": multispin, "pool": pool}[mode]())
+    modes = {"stream": stream, "chains": chains, "multispin": multispin, "planes": planes, "onchip": onchip,
+             "pool": pool}
+    print(mode, modes[mode]())

@@ -358,3 +358,83 @@ def test_many_replicas_bit_exact(engine):
         g.run(sched, 5)
         O.run(st, sched, 5)
         assert_same_state(g, st, engine)
+
+
+@pytest.mark.parametrize("L,S,R,nw,per_launch", [
+    (8, 1, 2, 4, 2048), (16, 3, 2, 2, 7), (18, 2, 3, 1, 64), (10, 1, 4, 2, 5), (32, 2, 2, 4, 33), (64, 1, 2, 1, 50),
+    (48, 2, 2, 4, 2048),
+])
+def test_onchip_engine_matches_oracle(L, S, R, nw, per_launch):
+    """The state held in the shared memory of all SMs, halo rows exchanged
+    between neighbour CTAs each half-sweep: bit-exact with the oracle across
+    launch boundaries, a fixed refresh interval and the log schedule."""
+    seed = 2000 + L + R
+    sched = np.linspace(2.4, 0.6, 120)
+    with micsa.Micsa(L, S, R, seed) as g:
+        g.set_launch_config(nw, 128, -1, True, 64)
+        g.set_engine("onchip", per_launch)
+        assert g.engine() == "onchip"
+        st = O.create(L, S, R, seed)
+        g.run(sched[:90], 6)
+        O.run(st, sched[:90], 6)
+        assert_same_state(g, st, "fixed interval")
+        g.run_logrefresh(sched[90:])
+        O.run_logrefresh(st, sched[90:])
+        assert_same_state(g, st, "log schedule")
+
+
+def test_onchip_engine_matches_streaming_l160():
+    """The headline lattice (L = 160, two replicas) on the on-chip engine gives
+    the streaming engine's bits and observables."""
+    sched = np.linspace(1.6, 0.7, 150)
+    out = []
+    for engine, nw in [("stream", 4), ("onchip", 4), ("onchip", 1)]:
+        with micsa.Micsa(160, 1, 2, 78) as g:
+            g.set_launch_config(nw, 128, -1, True, 64)
+            g.set_engine(engine, 64)
+            g.run(sched, 10)
+            out.append(g.get_state() + (g.measure(),))
+    for s, m, t, meas in out[1:]:
+        np.testing.assert_array_equal(s, out[0][0])
+        np.testing.assert_array_equal(m, out[0][1])
+        for a, b in zip(meas, out[0][3]):
+            np.testing.assert_array_equal(a, b)
+
+
+def test_onchip_limits_and_bounded_wait():
+    """Shapes that do not fit are rejected; the engine's bounded wait on a flag
+    that nothing sets gives up and reports it (no fault, no hang)."""
+    with micsa.Micsa(160, 1, 3, 1) as g:
+        with pytest.raises(micsa.MicsaError):
+            g.set_engine("onchip")
+    with micsa.Micsa(16, 1, 2, 1, gamma=2) as g:
+        with pytest.raises(micsa.MicsaError):
+            g.set_engine("onchip")
+    assert micsa.wait_selftest(2000)
+
+
+@pytest.mark.parametrize("engine,L,R,chains", [("stream", 16, 2, 2), ("stream", 18, 3, 3), ("stream", 160, 2, 2),
+                                               ("multispin_global", 32, 3, 2), ("multispin_global", 160, 2, 2)])
+def test_replica_chains_keep_results(engine, L, R, chains):
+    """Replica groups captured as concurrent kernel chains (graph replays of
+    140 sweeps, a Metropolis stretch and a remainder) give the same bits;
+    against the oracle for small L."""
+    sched = np.linspace(2.0, 0.6, 150)
+    out = []
+    for c in (1, chains):
+        with micsa.Micsa(L, 1, R, 55 + L) as g:
+            g.set_engine(engine)
+            g.set_replica_chains(c)
+            g.run(sched[:140], 10)
+            g.run_metropolis(sched[140:145])
+            g.run(sched[145:], 2)
+            out.append(g.get_state())
+    np.testing.assert_array_equal(out[0][0], out[1][0])
+    np.testing.assert_array_equal(out[0][1], out[1][1])
+    if L <= 32:
+        st = O.create(L, 1, R, 55 + L)
+        O.run(st, sched[:140], 10)
+        O.run_metropolis(st, sched[140:145])
+        O.run(st, sched[145:], 2)
+        np.testing.assert_array_equal(out[1][0], st["s"])
+        np.testing.assert_array_equal(out[1][1], st["m"])
