@@ -251,8 +251,12 @@ def leg_roofline(micsa, timer, stream, L, peaks, n_plain=2000, choice=None):
     hbm = peaks.get("hbm_gbs")
     peak = hbm if hbm else 6800.0
     achieved = bytes_per_launch / (launch_us * 1e-6) / 1e9
+    # DRAM bytes of one half-sweep from the ncu capture of this kernel in this shape
+    # (profiles/half_sweep_L160_full.md: two launches of 8.21 MB); null for other shapes
+    profiled = (L == 160 and choice is not None and choice.get("engine") == "stream" and choice.get("chains") == 2
+                and choice.get("words_per_thread") == 4 and choice.get("block") == 128)
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "peak_source": "measured" if hbm else "fallback",
+            "traffic": 2 * 8.21e6 if profiled else None, "peak_source": "measured" if hbm else "fallback",
             "kernel": "micsa::half_sweep_kernel<4,false> (streaming MicSA half-sweep, no refresh)",
             "L": L, "bytes_per_launch": bytes_per_launch, "launch_us": launch_us, "launch": shape,
             "replica_chains": (choice or {}).get("chains", 1),
@@ -273,8 +277,12 @@ def plane_roofline(micsa, timer, stream, g, peaks, n_plain=2000):
     hbm = peaks.get("hbm_gbs")
     peak = hbm if hbm else 6800.0
     achieved = bytes_per_launch / (launch_us * 1e-6) / 1e9
+    # DRAM bytes per launch from the ncu capture at L = 160, 128 replicas, 4 words per
+    # thread (profiles/msg_half_L160x128_full.md: 132.68 MB read + 44.6 MB written)
+    shape = g.launch_config()
+    traffic = 177.3e6 if (L == 160 and R == 128 and shape["words_per_thread"] == 4) else None
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "peak_source": "measured" if hbm else "fallback",
+            "traffic": traffic, "peak_source": "measured" if hbm else "fallback",
             "kernel": "micsa::msg_half_kernel (bit-plane MicSA half-sweep, no refresh)",
             "L": L, "replicas": R, "bytes_per_launch": bytes_per_launch, "launch_us": launch_us,
             "flips_per_ns": updates(L, S, R, n_plain) / (ms * 1e6)}
