@@ -36,7 +36,8 @@ Legs on the same JSON line:
                shared memory of all SMs, halo rows exchanged through L2)
   paper_shape  L = 160, 1 sample x 128 replicas (the shape of the paper's GPU
                timings), T = 0.7, refresh every 10: bit-plane engine and the
-               byte streaming engine
+               byte streaming engine; and one walker per spin on the log refresh
+               schedule (the paper's timed configuration), bit-plane engine
   cpu_baseline the CPU oracle (single thread) on a bounded sample of sweeps
 
 --impl reference times the oracle itself (the deliberately slow reference).
@@ -383,7 +384,19 @@ def leg_paper_shape(micsa, timer, stream, peaks, L=160, R=128, sweeps=400):
     n_s = max(10, sweeps // 4)
     ms = timer(lambda: g.run(sched[:n_s], 10))
     out["stream_flips_per_ns"] = updates(L, 1, R, n_s) / (ms * 1e6)
+    nw = g.launch_config()["words_per_thread"]
     g.close()
+    # one walker per spin (gamma = 1) wandering along +x after every timestep, refreshed on the
+    # paper's log schedule t = 2^s - 1 (Sec. 2.6, 2.8): the configuration of the paper's timings
+    gw = micsa.Micsa(L, 1, R, 11, stream=stream, walkers=True)
+    gw.set_engine("multispin_global")
+    gw.set_launch_config(out["multispin_launch"]["words_per_thread"], 128, -1, True, 64)
+    gw.run_logrefresh(sched[:64])
+    ms = timer(lambda: gw.run_logrefresh(np.full(256, 0.7)))
+    gw.close()
+    out["walkers_log_refresh_flips_per_ns"] = updates(L, 1, R, 256) / (ms * 1e6)
+    out["walkers_ns_per_timestep"] = 1e6 * ms / 256
+    out["paper_h100_walkers_total_ns_per_sweep"] = 121554 + 97378
     out["paper_h100_spin_update_kernel_ns_per_sweep"] = 121554
     out["paper_h100_flips_per_ns"] = 128 * 160 ** 3 / 121554.0
     return out

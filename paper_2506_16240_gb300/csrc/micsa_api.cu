@@ -204,9 +204,24 @@ int msg_rpt(const micsa_ctx *h, int nw, int n_rep) {
 cudaError_t launch_planes_half(micsa_t h, const LaunchConfig &lc, int parity, const int64_t *cursor, int64_t k,
                                int r0, int r1, cudaStream_t st) {
     return launch_msg_half(h->d_planes, h->d_bplanes, h->geo, h->S, h->R, r0, r1, msg_rpt(h, lc.nw, r1 - r0), lc.nw,
-                           parity, (uint32_t)(h->seed & 0xFFFFFFFFu), (uint32_t)(h->seed >> 32), h->d_params, cursor,
-                           k, lc.pdl, st);
+                           parity, h->gamma, h->walkers, (uint32_t)(h->seed & 0xFFFFFFFFu), (uint32_t)(h->seed >> 32),
+                           h->d_params, cursor, k, lc.pdl, st);
 }
+
+// One timestep of the bit-plane engine for replicas [r0, r1): gamma sweeps
+// (table entries k*gamma + alpha). With walkers the wandering step of the
+// previous timestep is applied by these half-sweeps as they read their daemons
+// (the table's gather flag); the last one of a run by run_planes.
+cudaError_t launch_planes_timestep(micsa_t h, const LaunchConfig &lc, const int64_t *cursor, int64_t k, int r0,
+                                   int r1, cudaStream_t st) {
+    cudaError_t e = cudaSuccess;
+    for (int al = 0; al < h->gamma && e == cudaSuccess; ++al)
+        for (int p = 0; p < 2 && e == cudaSuccess; ++p)
+            e = launch_planes_half(h, lc, p, cursor, k * h->gamma + al, r0, r1, st);
+    return e;
+}
+
+int64_t planes_timestep_kernels(const micsa_ctx *h) { return 2 * (int64_t)h->gamma; }
 
 // One half-sweep of graph kind gi over replica group c of `chains`.
 cudaError_t launch_group_half(micsa_t h, int gi, const LaunchConfig &lc, SweepArgs a, int c, int chains,
@@ -244,6 +259,12 @@ int capture_graph(micsa_t h, int gi, int G, const LaunchConfig &lc) {
     }
     for (int c = 0; c < chains && e == cudaSuccess; ++c) {
         cudaStream_t st = c == 0 ? h->capture_stream : h->aux_stream[c - 1];
+        if (gi == kGraphPlanes) {  // G timesteps
+            int r0, r1;
+            replica_group(h, c, chains, r0, r1);
+            for (int k = 0; k < G && e == cudaSuccess; ++k) e = launch_planes_timestep(h, lc, h->d_cursor, k, r0, r1, st);
+            continue;
+        }
         for (int k = 0; k < G && e == cudaSuccess; ++k)
             for (int p = 0; p < 2 && e == cudaSuccess; ++p) {
                 a.k = k;
@@ -255,7 +276,8 @@ int capture_graph(micsa_t h, int gi, int G, const LaunchConfig &lc) {
         e = cudaEventRecord(h->join_ev[c - 1], h->aux_stream[c - 1]);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(h->capture_stream, h->join_ev[c - 1], 0);
     }
-    if (e == cudaSuccess) e = launch_advance_cursor(h->d_cursor, G, lc.pdl, h->capture_stream);
+    const int64_t step = gi == kGraphPlanes ? (int64_t)G * h->gamma : G;
+    if (e == cudaSuccess) e = launch_advance_cursor(h->d_cursor, step, lc.pdl, h->capture_stream);
     cudaGraph_t graph = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(h->capture_stream, &graph);
     if (e != cudaSuccess) {
@@ -270,15 +292,15 @@ int capture_graph(micsa_t h, int gi, int G, const LaunchConfig &lc) {
         return cuda_fail(h, e, "graph instantiate");
     }
     h->graph_g[gi] = G;
-    h->graph_kernels[gi] = 2 * (int64_t)G * chains + 1;
+    h->graph_kernels[gi] = (gi == kGraphPlanes ? planes_timestep_kernels(h) : 2) * (int64_t)G * chains + 1;
     return MICSA_OK;
 }
 
 // The engine a MicSA run uses now.
 int active_engine(micsa_t h) {
-    if (h->engine == MICSA_ENGINE_STREAM || h->gamma > 1 || h->walkers) return MICSA_ENGINE_STREAM;
-    if (h->engine == MICSA_ENGINE_MULTISPIN_GLOBAL)
+    if (h->engine == MICSA_ENGINE_MULTISPIN_GLOBAL)  // gamma families and walkers included
         return msg_supported(h->geo) ? MICSA_ENGINE_MULTISPIN_GLOBAL : MICSA_ENGINE_STREAM;
+    if (h->engine == MICSA_ENGINE_STREAM || h->gamma > 1 || h->walkers) return MICSA_ENGINE_STREAM;
     if (h->engine == MICSA_ENGINE_ONCHIP) return h->oc.grid > 0 ? MICSA_ENGINE_ONCHIP : MICSA_ENGINE_STREAM;
     if (!h->d_units) return MICSA_ENGINE_STREAM;
     if (h->engine == MICSA_ENGINE_RESIDENT) return MICSA_ENGINE_RESIDENT;
@@ -295,7 +317,8 @@ bool use_resident(micsa_t h) {
 int ensure_planes(micsa_t h) {
     if (h->d_planes) return MICSA_OK;
     const size_t WP = (size_t)msg_plane_words(h->geo);
-    const size_t state = sizeof(uint32_t) * (size_t)h->S * h->R * 6 * WP;
+    const size_t state =
+        sizeof(uint32_t) * (size_t)h->S * h->R * (size_t)msg_planes_per_replica(h->gamma, h->walkers) * WP;
     const size_t bonds = sizeof(uint32_t) * (size_t)h->S * 12 * WP;
     CK(h, cudaMalloc(&h->d_planes, state), "cudaMalloc planes");
     cudaError_t e = cudaMalloc(&h->d_bplanes, bonds);
@@ -308,13 +331,15 @@ int ensure_planes(micsa_t h) {
     return MICSA_OK;
 }
 
-// MicSA sweeps [0, n) of the uploaded table on bit planes in HBM: bytes ->
-// planes, whole blocks of G sweeps by graph replay, the rest directly, planes
-// -> bytes. Each sweep is the even half-sweep followed by the odd one.
+// MicSA timesteps [0, n) of the uploaded table (n * gamma entries) on bit
+// planes in HBM: bytes -> planes, whole blocks of G timesteps by graph replay,
+// the rest directly, planes -> bytes. A timestep is gamma sweeps (each the even
+// half-sweep followed by the odd one) and, with walkers, the wandering step.
 int run_planes(micsa_t h, int64_t n, const LaunchConfig &lc) {
     if (int rc = ensure_planes(h)) return rc;
-    CK(h, msg_convert(h->d_planes, h->d_bplanes, h->d_spins, h->d_daemons, h->d_bonds, h->geo, h->S, h->R, true,
-                      h->stream), "convert to planes");
+    const int buf0 = h->walkers ? (int)(h->t & 1) : 0, buf1 = h->walkers ? (int)((h->t + n) & 1) : 0;
+    CK(h, msg_convert(h->d_planes, h->d_bplanes, h->d_spins, h->d_daemons, h->d_bonds, h->geo, h->S, h->R, h->gamma,
+                      h->walkers, buf0, true, h->stream), "convert to planes");
     h->launches += 2;
     const int G = lc.graph_sweeps;
     int64_t done = 0;
@@ -326,13 +351,17 @@ int run_planes(micsa_t h, int64_t n, const LaunchConfig &lc) {
         h->launches += reps * h->graph_kernels[kGraphPlanes];
         done = reps * G;
     }
-    for (int64_t k = done; k < n; ++k)
-        for (int p = 0; p < 2; ++p) {
-            CK(h, launch_planes_half(h, lc, p, nullptr, k, 0, h->R, h->stream), "plane half-sweep launch");
-            ++h->launches;
-        }
-    CK(h, msg_convert(h->d_planes, nullptr, h->d_spins, h->d_daemons, nullptr, h->geo, h->S, h->R, false,
-                      h->stream), "convert from planes");
+    for (int64_t k = done; k < n; ++k) {
+        CK(h, launch_planes_timestep(h, lc, nullptr, k, 0, h->R, h->stream), "plane timestep launch");
+        h->launches += planes_timestep_kernels(h);
+    }
+    if (h->walkers) {  // the wandering step after the run's last timestep
+        CK(h, launch_msg_wander(h->d_planes, h->geo, h->S, h->R, 0, h->R, h->gamma, h->d_params, nullptr,
+                                (n - 1) * h->gamma, lc.pdl, h->stream), "wander launch");
+        ++h->launches;
+    }
+    CK(h, msg_convert(h->d_planes, nullptr, h->d_spins, h->d_daemons, nullptr, h->geo, h->S, h->R, h->gamma,
+                      h->walkers, buf1, false, h->stream), "convert from planes");
     ++h->launches;
     return MICSA_OK;
 }
@@ -526,6 +555,7 @@ int run_micsa(micsa_t h, const double *schedule, int64_t n_sweeps, IsRefresh is_
             micsa_daemon_thresholds(schedule[k], th);
             last_T = schedule[k];
         }
+        const bool gather = h->walkers && k > 0 && active_engine(h) == MICSA_ENGINE_MULTISPIN_GLOBAL;
         for (int al = 0; al < G; ++al) {
             SweepParam &q = h->h_params[k * G + al];
             q.t = t;
@@ -534,10 +564,18 @@ int run_micsa(micsa_t h, const double *schedule, int64_t n_sweeps, IsRefresh is_
             q.th1 = th[1];
             q.th2 = th[2];
             q.alpha = al;
+            q.gather = gather ? 1 : 0;
+            q.reserved = 0;
         }
     }
     if (G == 1 && !h->walkers) {
         if (int rc = run_table(h, false, n_sweeps)) return rc;
+    } else if (active_engine(h) == MICSA_ENGINE_MULTISPIN_GLOBAL) {
+        const LaunchConfig lc = effective_config(h, false);
+        CK(h, cudaMemcpyAsync(h->d_params, h->h_params, sizeof(SweepParam) * (size_t)(n_sweeps * G),
+                              cudaMemcpyHostToDevice, h->stream), "upload sweep parameters");
+        CK(h, cudaEventRecord(h->params_free, h->stream), "record parameter event");
+        if (int rc = run_planes(h, n_sweeps, lc)) return rc;
     } else {
         const LaunchConfig lc = effective_config(h, false);
         CK(h, cudaMemcpyAsync(h->d_params, h->h_params, sizeof(SweepParam) * (size_t)(n_sweeps * G),

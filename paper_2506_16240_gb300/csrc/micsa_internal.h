@@ -19,6 +19,9 @@ struct SweepParam {
     uint64_t th0, th1, th2;  // refresh (daemon) or Metropolis cut points
     int32_t mode;            // kModeMicsa or kModeRefresh; unused by Metropolis
     int32_t alpha;           // daemon family used by this sweep (0 .. gamma-1)
+    int32_t gather;          // bit planes with walkers: the previous timestep's wandering step is
+                             // applied on read (daemons gathered from the other buffer)
+    int32_t reserved;
 };
 
 struct SweepArgs {
@@ -168,11 +171,15 @@ cudaError_t launch_wait_selftest(unsigned *flag, int *error, long long wait_limi
 // multispin planes in global memory for L % 32 == 0 (multispin.cu)
 bool msg_supported(const Geometry &g);
 int64_t msg_plane_words(const Geometry &g);  // words per parity plane, L^3 / 64
+int msg_planes_per_replica(int gamma, int walkers);  // 2 spin + 4 gamma daemon planes (x 2 buffers)
 cudaError_t msg_convert(uint32_t *planes, uint32_t *bplanes, int8_t *spins, uint8_t *daemons, const uint8_t *bonds,
-                        const Geometry &g, int S, int R, bool to_planes, cudaStream_t st);
+                        const Geometry &g, int S, int R, int gamma, int walkers, int buf, bool to_planes,
+                        cudaStream_t st);
+cudaError_t launch_msg_wander(uint32_t *planes, const Geometry &g, int S, int R, int r0, int r1, int gamma,
+                              const SweepParam *params, const int64_t *cursor, int64_t k, bool pdl, cudaStream_t st);
 int msg_default_rpt(const Geometry &g, int S, int R, int nw, int sm_count);
 cudaError_t launch_msg_half(uint32_t *planes, const uint32_t *bplanes, const Geometry &g, int S, int R, int r0,
-                            int r1, int rpt, int nw, int parity, uint32_t key0, uint32_t key1, const SweepParam *params,
+                            int r1, int rpt, int nw, int parity, int gamma, int walkers, uint32_t key0, uint32_t key1, const SweepParam *params,
                             const int64_t *cursor, int64_t k, bool pdl, cudaStream_t st);
 cudaError_t launch_advance_cursor(int64_t *cursor, int64_t step, bool pdl, cudaStream_t st);
 // wandering of every walker family after timestep t (parity t & 1), Sec. 2.6

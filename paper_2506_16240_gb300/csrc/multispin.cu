@@ -460,6 +460,13 @@ int multispin_blocks_per_sm(bool pool, size_t smem) {
 // replica the planes are [spin | m0 | m1][parity][WP]; per sample the bond
 // planes are [6][parity][WP] (bit set <=> J = -1, order +x +y +z -x -y -z).
 //
+// With gamma daemon families (Sec. 2.8) the daemon planes are
+// [buffer][family][m0 | m1][parity] after the two spin planes; family alpha of
+// replica gid draws with Philox id gid * gamma + alpha. With walkers (Sec. 2.6)
+// there are two buffers: the sweeps of timestep t use buffer t & 1 and the
+// wandering step after timestep t gathers buffer t & 1 into buffer (t + 1) & 1
+// (a permutation of the daemon bits, so out of place is race-free).
+//
 // A thread owns NW consecutive words i = i0 .. i0+NW-1 of one (zw, y) and runs
 // the replicas r = blockIdx.y * rpt .. of its sample over them, so one load
 // of the bond words serves rpt replicas. The z neighbours of bit 31 (bit 0)
@@ -472,15 +479,17 @@ int multispin_blocks_per_sm(bool pool, size_t smem) {
 namespace micsa {
 
 struct MsgArgs {
-    uint32_t *planes;        // [S*R][3][2][WP]
+    uint32_t *planes;        // [S*R][NP][WP], NP = 2 + 4 gamma (x 2 buffers with walkers)
     const uint32_t *bonds;   // [S][6][2][WP]
     int L, Lh, nzw, W4;      // W4 = Lh / 4 Philox blocks per row
     int64_t WP;
     int S, R, r0, r1, rpt, parity;  // replicas [r0, r1) of every sample, rpt per thread
+    int gamma, walkers, np;         // daemon families, two daemon buffers, planes per replica
     uint32_t key0, key1;
     const SweepParam *params;
     const int64_t *cursor;
     int64_t k;
+    FastDiv div_groups, div_L;  // thread index -> (zw, y, word group)
 };
 
 template <int NW> struct Vec;
@@ -511,6 +520,37 @@ template <> struct Vec<4> {
     }
 };
 
+// Daemon words of the NW own words after a wandering step along direction dd
+// (0 +x, 1 +y, 2 +z, 3 -x, 4 -y, 5 -z): the words of the other parity's plane
+// Sx at that neighbour, assembled like the spin neighbours of the update (M:
+// bits whose own site has x offset 1; w_*: the neighbour word indices).
+template <int NW>
+__device__ __forceinline__ void gather_words(const uint32_t *Sx, int dd, int64_t wc, int64_t w_ip, int64_t w_im,
+                                             int64_t w_yp, int64_t w_ym, int64_t w_zp, int64_t w_zm, uint32_t M,
+                                             uint32_t (&out)[NW]) {
+    uint32_t c[NW], n[NW];
+    Vec<NW>::ld(Sx + wc, c);
+    if (dd == 0 || dd == 3) {
+        const uint32_t edge = Sx[dd == 0 ? w_ip : w_im];
+#pragma unroll
+        for (int w = 0; w < NW; ++w) {
+            if (dd == 0) {
+                const uint32_t nx = w + 1 < NW ? c[w + 1 < NW ? w + 1 : 0] : edge;
+                out[w] = (c[w] & ~M) | (nx & M);
+            } else {
+                const uint32_t pv = w > 0 ? c[w > 0 ? w - 1 : 0] : edge;
+                out[w] = (pv & ~M) | (c[w] & M);
+            }
+        }
+        return;
+    }
+    const int64_t wn = dd == 1 ? w_yp : dd == 4 ? w_ym : dd == 2 ? w_zp : w_zm;
+    Vec<NW>::ld(Sx + wn, n);
+#pragma unroll
+    for (int w = 0; w < NW; ++w)
+        out[w] = dd == 1 || dd == 4 ? n[w] : dd == 2 ? __funnelshift_r(c[w], n[w], 1) : __funnelshift_l(n[w], c[w], 1);
+}
+
 template <int NW>
 __global__ void __launch_bounds__(128) msg_half_kernel(MsgArgs a) {
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -519,16 +559,15 @@ __global__ void __launch_bounds__(128) msg_half_kernel(MsgArgs a) {
     const int64_t kidx = a.k + (a.cursor ? *a.cursor : 0);
     const SweepParam prm = a.params[kidx];
     const bool refresh = prm.mode == kModeRefresh;
-    const int groups = a.Lh / NW;
-    const int64_t per_sample = (int64_t)a.L * a.nzw * groups;
-    // the grid covers S * per_sample threads exactly (a multiple of 128 for L % 32 == 0)
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int sample = (int)(tid / per_sample);
-    int64_t rem = tid - (int64_t)sample * per_sample;
-    const int ig = (int)(rem % groups);
-    rem /= groups;
-    const int y = (int)(rem % a.L);
-    const int zw = (int)(rem / a.L);
+    // grid: x covers the L * nzw * Lh / NW threads of one sample exactly (a
+    // multiple of 128 for L % 32 == 0), y the replica groups, z the samples
+    const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int sample = (int)blockIdx.z;
+    const uint32_t rowi = fdiv(tid, a.div_groups);
+    const int ig = (int)(tid - rowi * a.div_groups.d);
+    const uint32_t zw_u = fdiv(rowi, a.div_L);
+    const int y = (int)(rowi - zw_u * a.div_L.d);
+    const int zw = (int)zw_u;
     const int p = a.parity, o = 1 - p;
     const int L = a.L, Lh = a.Lh;
     const int i0 = NW * ig;
@@ -551,14 +590,22 @@ __global__ void __launch_bounds__(128) msg_half_kernel(MsgArgs a) {
     const int lig = (int)(threadIdx.x & (G - 1));  // this lane's share of the Philox block
     const uint32_t quad0 = (uint32_t)(((int64_t)p * L + 32 * zw) * L + y) * a.W4 + (uint32_t)(i0 >> 2);
 
+    const int alpha = prm.alpha, buf = a.walkers ? (int)(prm.t & 1) : 0;
+    const int mplane = 2 + ((buf * a.gamma + alpha) * 2) * 2 + p;  // m0 of (buffer, family, parity p)
+    const bool gather = prm.gather != 0 && !refresh;
+    // gather source: m0 of (the other buffer, family, the other parity); the direction of the
+    // previous wandering step seen from parity p
+    const int gplane = 2 + (((1 - buf) * a.gamma + alpha) * 2) * 2 + o;
+    const int gq = (int)((prm.t - 1) & 1), gd0 = alpha % 6, gdd = (p == gq) ? gd0 : (gd0 + 3) % 6;
     const int r_end = min(a.r1, a.r0 + (int)(blockIdx.y + 1) * a.rpt);
     for (int r = a.r0 + blockIdx.y * a.rpt; r < r_end; ++r) {
         const int64_t gid = (int64_t)sample * a.R + r;
-        uint32_t *pl = a.planes + gid * 6 * a.WP;
+        const uint32_t fam = (uint32_t)(gid * a.gamma + alpha);  // Philox id of this daemon family
+        uint32_t *pl = a.planes + gid * a.np * a.WP;
         const uint32_t *O = pl + (int64_t)o * a.WP;  // spins of the opposite parity
         uint32_t *Sp = pl + (int64_t)p * a.WP;
-        uint32_t *M0 = pl + (int64_t)(2 + p) * a.WP;
-        uint32_t *M1 = pl + (int64_t)(4 + p) * a.WP;
+        uint32_t *M0 = pl + (int64_t)mplane * a.WP;
+        uint32_t *M1 = pl + (int64_t)(mplane + 2) * a.WP;
         uint32_t Oc[NW], Oyp[NW], Oym[NW], Ozp[NW], Ozm[NW], Sg[NW], m0v[NW], m1v[NW];
         Vec<NW>::ld(O + wc, Oc);
         Vec<NW>::ld(O + w_yp, Oyp);
@@ -572,7 +619,7 @@ __global__ void __launch_bounds__(128) msg_half_kernel(MsgArgs a) {
             for (int c = 0; c < 32 / G; ++c) {
                 const int b = lig * (32 / G) + c;
                 const uint4 w = philox_rk(make_uint4(quad0 + (uint32_t)b * (uint32_t)L * (uint32_t)a.W4, (uint32_t)prm.t,
-                                                     ((uint32_t)gid << 2) | kTagDaemon,
+                                                     (fam << 2) | kTagDaemon,
                                                      (uint32_t)((uint64_t)prm.t >> 32)), rk);
                 const uint32_t mm[4] = {daemon_cut(w.x, cut), daemon_cut(w.y, cut), daemon_cut(w.z, cut),
                                         daemon_cut(w.w, cut)};
@@ -595,6 +642,10 @@ __global__ void __launch_bounds__(128) msg_half_kernel(MsgArgs a) {
                 m0v[w] = j == 0 ? a0[0] : j == 1 ? a0[1] : j == 2 ? a0[2] : a0[3];
                 m1v[w] = j == 0 ? a1[0] : j == 1 ? a1[1] : j == 2 ? a1[2] : a1[3];
             }
+        } else if (gather) {  // the walkers arrive through the previous wandering step
+            const uint32_t *G0 = pl + (int64_t)gplane * a.WP;
+            gather_words<NW>(G0, gdd, wc, w_ip, w_im, w_yp, w_ym, w_zp, w_zm, M, m0v);
+            gather_words<NW>(G0 + 2 * a.WP, gdd, wc, w_ip, w_im, w_yp, w_ym, w_zp, w_zm, M, m1v);
         } else {
             Vec<NW>::ld(M0 + wc, m0v);
             Vec<NW>::ld(M1 + wc, m1v);
@@ -638,9 +689,10 @@ __global__ void __launch_bounds__(128) msg_half_kernel(MsgArgs a) {
 }
 
 // bytes <-> planes. One thread per plane word (n_rep replicas, two parities,
-// WP words); the 32 bits of a word are the 32 z of one (y, i).
+// WP words); the 32 bits of a word are the 32 z of one (y, i). Daemons: the
+// gamma families of buffer buf.
 __global__ void msg_convert_state_kernel(uint32_t *planes, int8_t *spins, uint8_t *daemons, Geometry g,
-                                         int64_t n_rep, int64_t WP, bool to_planes) {
+                                         int64_t n_rep, int64_t WP, int gamma, int np, int buf, bool to_planes) {
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= n_rep * 2 * WP) return;
     const int64_t rep = tid / (2 * WP);
@@ -650,29 +702,83 @@ __global__ void msg_convert_state_kernel(uint32_t *planes, int8_t *spins, uint8_
     const int i = (int)(w % g.Lh);
     const int y = (int)((w / g.Lh) % g.L);
     const int zw = (int)(w / ((int64_t)g.Lh * g.L));
-    const int64_t base = (rep * 2 + p) * g.half + ((int64_t)32 * zw * g.L + y) * g.P + i;
+    const int64_t in_half = ((int64_t)32 * zw * g.L + y) * g.P + i;
     const int64_t zstep = (int64_t)g.L * g.P;
-    uint32_t *pl = planes + rep * 6 * WP;
+    uint32_t *pl = planes + rep * np * WP;
+    const int64_t sbase = (rep * 2 + p) * g.half + in_half;
     if (to_planes) {
-        uint32_t s = 0, m0 = 0, m1 = 0;
-        for (int b = 0; b < 32; ++b) {
-            const int64_t off = base + b * zstep;
-            s |= (((uint32_t)(uint8_t)spins[off] >> 7) & 1u) << b;
-            const uint32_t m = daemons[off];
-            m0 |= (m & 1u) << b;
-            m1 |= ((m >> 1) & 1u) << b;
-        }
-        pl[(int64_t)p * WP + w] = s;
-        pl[(int64_t)(2 + p) * WP + w] = m0;
-        pl[(int64_t)(4 + p) * WP + w] = m1;
+        uint32_t sv = 0;
+        for (int b = 0; b < 32; ++b) sv |= (((uint32_t)(uint8_t)spins[sbase + b * zstep] >> 7) & 1u) << b;
+        pl[(int64_t)p * WP + w] = sv;
     } else {
-        const uint32_t s = pl[(int64_t)p * WP + w], m0 = pl[(int64_t)(2 + p) * WP + w],
-                       m1 = pl[(int64_t)(4 + p) * WP + w];
-        for (int b = 0; b < 32; ++b) {
-            const int64_t off = base + b * zstep;
-            spins[off] = ((s >> b) & 1u) ? (int8_t)-1 : (int8_t)1;
-            daemons[off] = (uint8_t)(((m0 >> b) & 1u) | (((m1 >> b) & 1u) << 1));
+        const uint32_t sv = pl[(int64_t)p * WP + w];
+        for (int b = 0; b < 32; ++b) spins[sbase + b * zstep] = ((sv >> b) & 1u) ? (int8_t)-1 : (int8_t)1;
+    }
+    for (int al = 0; al < gamma; ++al) {
+        const int64_t dbase = ((rep * gamma + al) * 2 + p) * g.half + in_half;
+        const int mp = 2 + ((buf * gamma + al) * 2) * 2 + p;
+        if (to_planes) {
+            uint32_t m0 = 0, m1 = 0;
+            for (int b = 0; b < 32; ++b) {
+                const uint32_t m = daemons[dbase + b * zstep];
+                m0 |= (m & 1u) << b;
+                m1 |= ((m >> 1) & 1u) << b;
+            }
+            pl[(int64_t)mp * WP + w] = m0;
+            pl[(int64_t)(mp + 2) * WP + w] = m1;
+        } else {
+            const uint32_t m0 = pl[(int64_t)mp * WP + w], m1 = pl[(int64_t)(mp + 2) * WP + w];
+            for (int b = 0; b < 32; ++b)
+                daemons[dbase + b * zstep] = (uint8_t)(((m0 >> b) & 1u) | (((m1 >> b) & 1u) << 1));
         }
+    }
+}
+
+// Wandering step on the daemon planes (Sec. 2.6), out of place: after timestep
+// t every site of parity q = t & 1 exchanges its walker of family alpha with
+// its neighbour along direction alpha mod 6 (+x, +y, +z, -x, -y, -z). A site
+// of parity q takes the walker of its neighbour at +d, a site of parity 1 - q
+// that of its neighbour at -d; the neighbour word is assembled from the other
+// parity's plane exactly as the spin neighbours of the update. One thread per
+// output word (replica, family, parity, word), both daemon bits.
+// Grid: x over the WP words, y over (replica of [r0, r1), family, parity), z
+// over samples.
+__global__ void msg_wander_kernel(uint32_t *planes, Geometry g, int R, int r0, int gamma, int np, uint32_t WP,
+                                  FastDiv div_Lh, FastDiv div_L, const SweepParam *params, const int64_t *cursor,
+                                  int64_t k) {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    const int64_t t = params[k + (cursor ? *cursor : 0)].t;
+    const int q = (int)(t & 1), src = (int)(t & 1), dst = 1 - src;
+    const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
+    if (w >= WP) return;
+    const int P = (int)(blockIdx.y & 1);
+    const int fr = (int)(blockIdx.y >> 1);
+    const int al = fr % gamma;
+    const int r = r0 + fr / gamma;
+    const int sample = (int)blockIdx.z;
+    const uint32_t row = fdiv(w, div_Lh);
+    const int i = (int)(w - row * div_Lh.d);
+    const uint32_t zw_u = fdiv(row, div_L);
+    const int y = (int)(row - zw_u * div_L.d);
+    const int zw = (int)zw_u;
+    const int L = g.L, Lh = g.Lh, nzw = g.L / 32;
+    const int d0 = al % 6, dd = (P == q) ? d0 : (d0 + 3) % 6;
+    const uint32_t M = ((P + y) & 1) ? 0x55555555u : 0xAAAAAAAAu;  // bits whose site has x offset 1
+    uint32_t *pl = planes + ((int64_t)sample * R + r) * np * WP;
+#pragma unroll
+    for (int bit = 0; bit < 2; ++bit) {
+        const uint32_t *Sx = pl + (int64_t)(2 + ((src * gamma + al) * 2 + bit) * 2 + (1 - P)) * WP;
+        uint32_t out;
+        switch (dd) {
+            case 0: out = (Sx[w] & ~M) | (Sx[w - i + (i + 1 == Lh ? 0 : i + 1)] & M); break;
+            case 3: out = (Sx[w - i + (i == 0 ? Lh - 1 : i - 1)] & ~M) | (Sx[w] & M); break;
+            case 1: out = Sx[((int64_t)zw * L + (y + 1 == L ? 0 : y + 1)) * Lh + i]; break;
+            case 4: out = Sx[((int64_t)zw * L + (y == 0 ? L - 1 : y - 1)) * Lh + i]; break;
+            case 2: out = __funnelshift_r(Sx[w], Sx[((int64_t)(zw + 1 == nzw ? 0 : zw + 1) * L + y) * Lh + i], 1); break;
+            default: out = __funnelshift_l(Sx[((int64_t)(zw == 0 ? nzw - 1 : zw - 1) * L + y) * Lh + i], Sx[w], 1); break;
+        }
+        pl[(int64_t)(2 + ((dst * gamma + al) * 2 + bit) * 2 + P) * WP + w] = out;
     }
 }
 
@@ -702,12 +808,15 @@ bool msg_supported(const Geometry &g) { return g.L >= 32 && g.L % 32 == 0 && g.P
 
 int64_t msg_plane_words(const Geometry &g) { return (int64_t)g.L * g.L * g.L / 64; }
 
+int msg_planes_per_replica(int gamma, int walkers) { return 2 + 4 * gamma * (walkers ? 2 : 1); }
+
 cudaError_t msg_convert(uint32_t *planes, uint32_t *bplanes, int8_t *spins, uint8_t *daemons, const uint8_t *bonds,
-                        const Geometry &g, int S, int R, bool to_planes, cudaStream_t st) {
+                        const Geometry &g, int S, int R, int gamma, int walkers, int buf, bool to_planes,
+                        cudaStream_t st) {
     const int64_t WP = msg_plane_words(g);
     const int64_t n = (int64_t)S * R * 2 * WP;
-    msg_convert_state_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(planes, spins, daemons, g, (int64_t)S * R,
-                                                                             WP, to_planes);
+    msg_convert_state_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+        planes, spins, daemons, g, (int64_t)S * R, WP, gamma, msg_planes_per_replica(gamma, walkers), buf, to_planes);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || !to_planes || !bplanes) return e;
     const int64_t nb = (int64_t)S * 2 * WP;
@@ -715,7 +824,7 @@ cudaError_t msg_convert(uint32_t *planes, uint32_t *bplanes, int8_t *spins, uint
     return cudaGetLastError();
 }
 
-int msg_default_rpt(const Geometry &g, int S, int R, int nw, int sm_count) {
+int msg_default_rpt(const Geometry &g, int S, int R, int nw, int sm_count) {  // grid.y = ceil(R / rpt)
     // enough replica groups to fill the GPU (about 2048 threads per SM), the
     // rest of the replicas looped over inside a thread
     const int64_t threads = (int64_t)S * g.L * (g.L / 32) * (g.Lh / nw);
@@ -724,10 +833,31 @@ int msg_default_rpt(const Geometry &g, int S, int R, int nw, int sm_count) {
     return (R + groups - 1) / groups;
 }
 
+cudaError_t launch_msg_wander(uint32_t *planes, const Geometry &g, int S, int R, int r0, int r1, int gamma,
+                              const SweepParam *params, const int64_t *cursor, int64_t k, bool pdl, cudaStream_t st) {
+    const int64_t WP = msg_plane_words(g);
+    if (S > 65535 || (int64_t)(r1 - r0) * gamma * 2 > 65535) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)((WP + 255) / 256), (unsigned)((r1 - r0) * gamma * 2), (unsigned)S);
+    cfg.blockDim = dim3(256);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, msg_wander_kernel, planes, g, R, r0, gamma, msg_planes_per_replica(gamma, 1),
+                              (uint32_t)WP, make_fastdiv((uint32_t)g.Lh), make_fastdiv((uint32_t)g.L), params, cursor,
+                              k);
+}
+
 cudaError_t launch_msg_half(uint32_t *planes, const uint32_t *bplanes, const Geometry &g, int S, int R, int r0,
-                            int r1, int rpt, int nw, int parity, uint32_t key0, uint32_t key1, const SweepParam *params,
-                            const int64_t *cursor, int64_t k, bool pdl, cudaStream_t st) {
+                            int r1, int rpt, int nw, int parity, int gamma, int walkers, uint32_t key0, uint32_t key1,
+                            const SweepParam *params, const int64_t *cursor, int64_t k, bool pdl, cudaStream_t st) {
     MsgArgs a{};
+    a.gamma = gamma;
+    a.walkers = walkers;
+    a.np = msg_planes_per_replica(gamma, walkers);
     a.planes = planes;
     a.bonds = bplanes;
     a.L = g.L;
@@ -746,10 +876,13 @@ cudaError_t launch_msg_half(uint32_t *planes, const uint32_t *bplanes, const Geo
     a.params = params;
     a.cursor = cursor;
     a.k = k;
-    const int64_t threads = (int64_t)S * g.L * (g.L / 32) * (g.Lh / nw);
-    if (threads % 128 != 0 || rpt < 1 || r0 < 0 || r1 > R || r0 >= r1) return cudaErrorInvalidValue;
+    a.div_groups = make_fastdiv((uint32_t)(g.Lh / nw));
+    a.div_L = make_fastdiv((uint32_t)g.L);
+    const int64_t per_sample = (int64_t)g.L * (g.L / 32) * (g.Lh / nw);
+    if (per_sample % 128 != 0 || per_sample >= (1ll << 31) || S > 65535 || rpt < 1 || r0 < 0 || r1 > R || r0 >= r1)
+        return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)(threads / 128), (unsigned)((r1 - r0 + rpt - 1) / rpt));
+    cfg.gridDim = dim3((unsigned)(per_sample / 128), (unsigned)((r1 - r0 + rpt - 1) / rpt), (unsigned)S);
     cfg.blockDim = dim3(128);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];

@@ -332,14 +332,14 @@ def test_global_multispin_matches_streaming_l160():
 
 
 def test_global_multispin_limits():
-    """L not a multiple of 32 is rejected; gamma > 1 and walkers fall back to the
-    streaming kernel; replicas per thread is range-checked."""
+    """L not a multiple of 32 is rejected; gamma > 1 and walkers stay on the
+    bit-plane engine; replicas per thread is range-checked."""
     with micsa.Micsa(48, 1, 2, 3) as g:
         with pytest.raises(micsa.MicsaError):
             g.set_engine("multispin_global")
-    with micsa.Micsa(32, 1, 2, 3, gamma=2) as g:
+    with micsa.Micsa(32, 1, 2, 3, gamma=2, walkers=True) as g:
         g.set_engine("multispin_global")
-        assert g.engine() == "stream"
+        assert g.engine() == "multispin_global"
     with micsa.Micsa(32, 1, 2, 3) as g:
         with pytest.raises(micsa.MicsaError):
             g.set_multispin_replicas(3)
@@ -438,3 +438,27 @@ def test_replica_chains_keep_results(engine, L, R, chains):
         O.run(st, sched[145:], 2)
         np.testing.assert_array_equal(out[1][0], st["s"])
         np.testing.assert_array_equal(out[1][1], st["m"])
+
+
+@pytest.mark.parametrize("L,S,R,gamma,walkers,interval,chains", [
+    (32, 1, 2, 2, False, 3, 1), (32, 2, 1, 1, True, 5, 1), (32, 1, 2, 6, True, 4, 2), (64, 1, 1, 3, True, 7, 1),
+    (32, 1, 3, 4, True, 9, 3),
+])
+def test_global_multispin_gamma_walkers(L, S, R, gamma, walkers, interval, chains):
+    """gamma daemon families and walkers on the bit planes (Sec. 2.6, 2.8): the
+    wandering step is a gather between two daemon buffers; 140 timesteps (graph
+    replays), the log schedule and odd run lengths match the oracle bit for bit."""
+    seed = 31 * L + gamma
+    sched = np.linspace(2.4, 0.6, 161)
+    with micsa.Micsa(L, S, R, seed, gamma=gamma, walkers=walkers) as g:
+        g.set_engine("multispin_global")
+        g.set_replica_chains(chains)
+        st = O.create(L, S, R, seed, gamma=gamma, walkers=walkers)
+        g.run(sched[:140], interval)
+        O.run_ex(st, sched[:140], interval)
+        assert_same_state(g, st, f"gamma={gamma} walkers={walkers}")
+        g.run_logrefresh(sched[140:151])
+        O.run_ex(st, sched[140:151], 0)
+        g.run(sched[151:], interval)
+        O.run_ex(st, sched[151:], interval)
+        assert_same_state(g, st, "log schedule, odd lengths")
