@@ -492,6 +492,29 @@ struct MsgArgs {
     FastDiv div_groups, div_L;  // thread index -> (zw, y, word group)
 };
 
+// Philox4x32-10 as philox_rk, each round's two products taken as one 32 x 32
+// -> 64-bit multiply (high word and low word of the same product).
+__device__ __forceinline__ uint4 philox_wide(uint4 c, const RoundKeys &rk) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x, p1 = (uint64_t)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk.k0[r], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ rk.k1[r],
+                       (uint32_t)p0);
+    }
+    return c;
+}
+
+// Refresh cut points as strict 32-bit compares: [u >= c] = [u > c - 1]. Valid
+// for 1 <= c <= 2^32; every cut point is >= floor(2^32 p(0)) >= 2^30, since
+// p(0) = 1 / (1 + x + x^2 + x^3) >= 1/4 for x = exp(-4 beta) <= 1.
+struct CutsGt {
+    uint32_t c0m, c1m, c2m;
+};
+
+__device__ __forceinline__ CutsGt make_cuts_gt(uint64_t th0, uint64_t th1, uint64_t th2) {
+    return {(uint32_t)(th0 - 1), (uint32_t)(th1 - 1), (uint32_t)(th2 - 1)};
+}
+
 template <int NW> struct Vec;
 template <> struct Vec<1> {
     static __device__ __forceinline__ void ld(const uint32_t *p, uint32_t *v) { v[0] = *p; }
@@ -586,7 +609,7 @@ __global__ void __launch_bounds__(128) msg_half_kernel(MsgArgs a) {
 #pragma unroll
     for (int k = 0; k < 6; ++k) Vec<NW>::ld(bs + ((int64_t)k * 2 + p) * a.WP + wc, B[k]);
     const RoundKeys rk = round_keys(a.key0, a.key1);
-    const Cuts cut = make_cuts(prm.th0, prm.th1, prm.th2);
+    const CutsGt gcut = make_cuts_gt(prm.th0, prm.th1, prm.th2);
     const int lig = (int)(threadIdx.x & (G - 1));  // this lane's share of the Philox block
     const uint32_t quad0 = (uint32_t)(((int64_t)p * L + 32 * zw) * L + y) * a.W4 + (uint32_t)(i0 >> 2);
 
@@ -615,19 +638,28 @@ __global__ void __launch_bounds__(128) msg_half_kernel(MsgArgs a) {
         const uint32_t Oip = O[w_ip], Oim = O[w_im];
         Vec<NW>::ld(Sp + wc, Sg);
         if (refresh) {  // fresh daemons of parity p before its half-sweep (Sec. 2.7)
+            // z = 32 zw + b for b in this lane's range, from the top down: each new
+            // bit enters at the bottom (a = 2 a + bit); m1 = [u >= c1], m0 = the parity
+            // of [u >= c0] + [u >= c1] + [u >= c2]
             uint32_t a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0};
-            for (int c = 0; c < 32 / G; ++c) {
+#pragma unroll 2
+            for (int c = 32 / G - 1; c >= 0; --c) {
                 const int b = lig * (32 / G) + c;
-                const uint4 w = philox_rk(make_uint4(quad0 + (uint32_t)b * (uint32_t)L * (uint32_t)a.W4, (uint32_t)prm.t,
-                                                     (fam << 2) | kTagDaemon,
-                                                     (uint32_t)((uint64_t)prm.t >> 32)), rk);
-                const uint32_t mm[4] = {daemon_cut(w.x, cut), daemon_cut(w.y, cut), daemon_cut(w.z, cut),
-                                        daemon_cut(w.w, cut)};
+                const uint4 w = philox_wide(make_uint4(quad0 + (uint32_t)b * (uint32_t)L * (uint32_t)a.W4, (uint32_t)prm.t,
+                                                       (fam << 2) | kTagDaemon, (uint32_t)((uint64_t)prm.t >> 32)),
+                                            rk);
+                const uint32_t u[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
-                    a0[j] |= (mm[j] & 1u) << b;
-                    a1[j] |= (mm[j] >> 1) << b;
+                    const uint32_t g0 = u[j] > gcut.c0m, g1 = u[j] > gcut.c1m, g2 = u[j] > gcut.c2m;
+                    a0[j] = 2 * a0[j] + (g0 ^ g1 ^ g2);
+                    a1[j] = 2 * a1[j] + g1;
                 }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                a0[j] <<= lig * (32 / G);
+                a1[j] <<= lig * (32 / G);
             }
 #pragma unroll
             for (int off = 1; off < G; off <<= 1)
