@@ -29,9 +29,9 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     constexpr uint32_t kW0 = 0x9E3779B9u, kW1 = 0xBB67AE85u;
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t hi0 = __umulhi(kM0, c.x), lo0 = kM0 * c.x;
-        const uint32_t hi1 = __umulhi(kM1, c.z), lo1 = kM1 * c.z;
-        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        // high and low words of each 32 x 32 -> 64-bit product
+        const uint64_t p0 = (uint64_t)kM0 * c.x, p1 = (uint64_t)kM1 * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
         k0 += kW0;
         k1 += kW1;
     }
@@ -172,11 +172,14 @@ __device__ __forceinline__ uint32_t creutz4(uint32_t u32, uint32_t &D, uint32_t 
     return am;
 }
 
-// Daemon value from a uniform word and the three refresh cut points.
+// Daemon value from a uniform word and the three refresh cut points:
+// m = [u >= c0] + [u >= c1] + [u >= c2], taken as strict 32-bit compares
+// [u > c - 1]. Valid for 1 <= c <= 2^32; every refresh cut point is
+// >= floor(2^32 p(0)) >= 2^30, since p(0) = 1 / (1 + x + x^2 + x^3) >= 1/4.
 __device__ __forceinline__ uint32_t daemon_from_uniform(uint32_t u, uint64_t c0, uint64_t c1,
                                                         uint64_t c2) {
-    const uint64_t v = u;
-    return (uint32_t)(v >= c0) + (uint32_t)(v >= c1) + (uint32_t)(v >= c2);
+    return (uint32_t)(u > (uint32_t)(c0 - 1)) + (uint32_t)(u > (uint32_t)(c1 - 1)) +
+           (uint32_t)(u > (uint32_t)(c2 - 1));
 }
 
 }  // namespace micsa
