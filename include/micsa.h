@@ -147,8 +147,9 @@ int micsa_device_bytes(micsa_t h, size_t *bytes);
 /* Launch shape of the sweep kernels (the autotuner's knobs; results are
  * bit-identical for every choice): words_per_thread 1, 2 or 4 (32-bit words of
  * sites per thread, reduced to what the row pitch allows), optionally ORed with
- * MICSA_LAUNCH_REGCAP for the kernel variant whose registers are capped at 64
- * per thread (blocks of at most 128 threads, 8 per SM), block 32..256 in
+ * MICSA_LAUNCH_REGCAP for the kernel variant whose registers are capped (the
+ * streaming kernel: 64 per thread, blocks of at most 128 threads, 8 per SM;
+ * the bit-plane kernel: 102, 5 blocks of 128 per SM), block 32..256 in
  * steps of 32, blocks_per_sm -1 (grid-stride loop over the resident capacity),
  * 0 (one thread per chunk) or a positive cap, pdl != 0 chains consecutive
  * half-sweeps with programmatic dependent launch, graph_sweeps > 0 replays a

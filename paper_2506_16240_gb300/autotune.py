@@ -52,7 +52,9 @@ def candidates(L, R=1):
             for nw, blk, bps in itertools.product([4, 2], [64, 128], [-1, 0, 4, 6, 8])]
     if R >= 2:  # replica groups as concurrent kernel chains in the graphs
         out += [{"engine": "stream", "words_per_thread": 4, "block": blk, "blocks_per_sm": bps, "chains": 2}
-                for blk, bps in itertools.product([128, 256], [-1, 2, 3, 4])]
+                for blk, bps in itertools.product([64, 128, 256], [-1, 3, 4])]
+        out += [{"engine": "stream", "words_per_thread": 4, "block": blk, "blocks_per_sm": -1, "chains": 2,
+                 "graph_sweeps": 256} for blk in (64, 128)]
     out += [{"engine": "onchip", "words_per_thread": nw} for nw in (4, 1)]  # where the state fits on chip
     if L <= 40:
         out.append({"engine": "resident"})
@@ -61,7 +63,7 @@ def candidates(L, R=1):
     if L % 32 == 0:
         rpts = sorted({0} | {r for r in (1, 2, 4, 8, 16, 32) if r <= R})
         out += [{"engine": "multispin_global", "words_per_thread": nw, "replicas_per_thread": rpt}
-                for nw, rpt in itertools.product([1, 2, 4], rpts)]
+                for nw, rpt in itertools.product([1, 2, 4, 2 | 256, 4 | 256], rpts)]
         if R >= 2:
             out += [{"engine": "multispin_global", "words_per_thread": nw, "replicas_per_thread": 0, "chains": 2}
                     for nw in (1, 2, 4)]
@@ -72,7 +74,8 @@ def apply(g, choice, resident_sweeps=256):
     g.set_replica_chains(choice.get("chains", 1))
     if choice["engine"] == "stream":
         g.set_engine("stream")
-        g.set_launch_config(choice["words_per_thread"], choice["block"], choice["blocks_per_sm"], True, 64)
+        g.set_launch_config(choice["words_per_thread"], choice["block"], choice["blocks_per_sm"], True,
+                            choice.get("graph_sweeps", 64))
     elif choice["engine"] == "onchip":
         g.set_launch_config(choice["words_per_thread"], 128, -1, True, 64)
         g.set_engine("onchip", 2048)

@@ -204,7 +204,7 @@ int msg_rpt(const micsa_ctx *h, int nw, int n_rep) {
 cudaError_t launch_planes_half(micsa_t h, const LaunchConfig &lc, int parity, const int64_t *cursor, int64_t k,
                                int r0, int r1, cudaStream_t st) {
     return launch_msg_half(h->d_planes, h->d_bplanes, h->geo, h->S, h->R, r0, r1, msg_rpt(h, lc.nw, r1 - r0), lc.nw,
-                           parity, h->gamma, h->walkers, (uint32_t)(h->seed & 0xFFFFFFFFu), (uint32_t)(h->seed >> 32),
+                           lc.regcap, parity, h->gamma, h->walkers, (uint32_t)(h->seed & 0xFFFFFFFFu), (uint32_t)(h->seed >> 32),
                            h->d_params, cursor, k, lc.pdl, st);
 }
 

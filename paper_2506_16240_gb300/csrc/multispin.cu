@@ -574,8 +574,10 @@ __device__ __forceinline__ void gather_words(const uint32_t *Sx, int dd, int64_t
         out[w] = dd == 1 || dd == 4 ? n[w] : dd == 2 ? __funnelshift_r(c[w], n[w], 1) : __funnelshift_l(n[w], c[w], 1);
 }
 
-template <int NW>
-__global__ void __launch_bounds__(128) msg_half_kernel(MsgArgs a) {
+// MINB: minimum resident blocks of 128 per SM the register allocation must
+// allow (1: unconstrained; 5: the register-capped variant, at most 102 registers).
+template <int NW, int MINB>
+__global__ void __launch_bounds__(128, MINB) msg_half_kernel(MsgArgs a) {
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     constexpr int G = 4 / NW;  // lanes sharing one Philox block of words
@@ -884,8 +886,9 @@ cudaError_t launch_msg_wander(uint32_t *planes, const Geometry &g, int S, int R,
 }
 
 cudaError_t launch_msg_half(uint32_t *planes, const uint32_t *bplanes, const Geometry &g, int S, int R, int r0,
-                            int r1, int rpt, int nw, int parity, int gamma, int walkers, uint32_t key0, uint32_t key1,
-                            const SweepParam *params, const int64_t *cursor, int64_t k, bool pdl, cudaStream_t st) {
+                            int r1, int rpt, int nw, bool regcap, int parity, int gamma, int walkers, uint32_t key0,
+                            uint32_t key1, const SweepParam *params, const int64_t *cursor, int64_t k, bool pdl,
+                            cudaStream_t st) {
     MsgArgs a{};
     a.gamma = gamma;
     a.walkers = walkers;
@@ -922,10 +925,13 @@ cudaError_t launch_msg_half(uint32_t *planes, const uint32_t *bplanes, const Geo
     attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    switch (nw) {
-        case 1: return cudaLaunchKernelEx(&cfg, msg_half_kernel<1>, a);
-        case 2: return cudaLaunchKernelEx(&cfg, msg_half_kernel<2>, a);
-        case 4: return cudaLaunchKernelEx(&cfg, msg_half_kernel<4>, a);
+    switch (nw * (regcap ? -1 : 1)) {
+        case 1: return cudaLaunchKernelEx(&cfg, msg_half_kernel<1, 1>, a);
+        case 2: return cudaLaunchKernelEx(&cfg, msg_half_kernel<2, 1>, a);
+        case 4: return cudaLaunchKernelEx(&cfg, msg_half_kernel<4, 1>, a);
+        case -1: return cudaLaunchKernelEx(&cfg, msg_half_kernel<1, 5>, a);
+        case -2: return cudaLaunchKernelEx(&cfg, msg_half_kernel<2, 5>, a);
+        case -4: return cudaLaunchKernelEx(&cfg, msg_half_kernel<4, 5>, a);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -287,6 +287,7 @@ def test_correlation_bit_exact(L, S, R):
 
 @pytest.mark.parametrize("L,S,R,nw,rpt", [
     (32, 2, 3, 1, 0), (32, 1, 2, 2, 1), (32, 2, 3, 4, 2), (64, 1, 2, 1, 0), (64, 2, 1, 4, 1), (96, 1, 2, 2, 2),
+    (32, 1, 3, 4 | 256, 2), (64, 1, 2, 2 | 256, 0),
 ])
 def test_global_multispin_matches_oracle(L, S, R, nw, rpt):
     """Bit planes in HBM (App. B multispin update, L a multiple of 32): refresh
