@@ -558,7 +558,7 @@ def main(argv=None):
     from paper_2506_16240_gb300 import autotune
     # launch shape of the byte-layout engine for this lattice (int8 spins, uint8
     # daemons); the bit-plane engine is timed on the same workload in its own leg
-    tuned = autotune.tune(g, torch, stream, use_cache=False, engines=("stream", "resident", "multispin", "onchip"))
+    tuned = autotune.tune(g, torch, stream, use_cache=False, engines=("stream", "resident", "multispin", "onchip", "tma"))
 
     for k in range(args.warmup):
         g.reinit(seed + k)

@@ -178,6 +178,14 @@ int micsa_set_launch_config(micsa_t h, int words_per_thread, int block, int bloc
  *                          (L = 160 with R <= 2). A wait that runs out makes
  *                          the next micsa_sync / micsa_measure /
  *                          micsa_get_state return MICSA_E_TIMEOUT.
+ *   MICSA_ENGINE_TMA       as STREAM with the tiles (8 x 8 rows of a group of
+ *                          two replicas, with their periodic halo rows) staged
+ *                          in shared memory by TMA tensor copies into a ring
+ *                          of mbarrier-tracked stages in persistent CTAs
+ *                          (bounded waits, MICSA_E_TIMEOUT as ONCHIP). Needs
+ *                          L % 8 == 0, a row pitch P = 4 ceil(L/8) that is a
+ *                          multiple of 16 and at most 256, gamma = 1 and no
+ *                          walkers.
  *   MICSA_ENGINE_MULTISPIN_GLOBAL
  *                          bit planes in HBM (32 z per word) for L a multiple
  *                          of 32: each micsa_run converts the byte state to
@@ -195,6 +203,7 @@ int micsa_set_launch_config(micsa_t h, int words_per_thread, int block, int bloc
 #define MICSA_ENGINE_MULTISPIN 3
 #define MICSA_ENGINE_MULTISPIN_GLOBAL 4
 #define MICSA_ENGINE_ONCHIP 5
+#define MICSA_ENGINE_TMA 6
 int micsa_set_engine(micsa_t h, int engine, int resident_sweeps);
 
 /* Graph replays of the STREAM and MULTISPIN_GLOBAL engines split the replicas
@@ -216,7 +225,7 @@ int micsa_set_multispin_replicas(micsa_t h, int replicas_per_thread);
 int micsa_wait_selftest(int64_t polls, int *timed_out);
 
 /* The engine that the next micsa_run will use (STREAM, RESIDENT, MULTISPIN,
- * MULTISPIN_GLOBAL or ONCHIP). */
+ * MULTISPIN_GLOBAL, ONCHIP or TMA). */
 int micsa_get_engine(micsa_t h, int *engine);
 
 /* The launch shape requested (words_per_thread as set, reduced to what the row

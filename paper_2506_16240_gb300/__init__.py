@@ -28,9 +28,10 @@ MICSA_E_TOO_LARGE = -7
 MICSA_ENGINE_AUTO, MICSA_ENGINE_STREAM, MICSA_ENGINE_RESIDENT, MICSA_ENGINE_MULTISPIN = 0, 1, 2, 3
 MICSA_ENGINE_MULTISPIN_GLOBAL = 4
 MICSA_ENGINE_ONCHIP = 5
+MICSA_ENGINE_TMA = 6
 ENGINES = {"auto": MICSA_ENGINE_AUTO, "stream": MICSA_ENGINE_STREAM, "resident": MICSA_ENGINE_RESIDENT,
            "multispin": MICSA_ENGINE_MULTISPIN, "multispin_global": MICSA_ENGINE_MULTISPIN_GLOBAL,
-           "onchip": MICSA_ENGINE_ONCHIP}
+           "onchip": MICSA_ENGINE_ONCHIP, "tma": MICSA_ENGINE_TMA}
 MICSA_NOALLOC_MAX_TERMS = 8192
 
 _ERRNAMES = {-1: "MICSA_E_INVALID_ARG", -2: "MICSA_E_OOM", -3: "MICSA_E_CUDA",

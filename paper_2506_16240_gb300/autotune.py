@@ -56,6 +56,7 @@ def candidates(L, R=1):
         out += [{"engine": "stream", "words_per_thread": 4, "block": blk, "blocks_per_sm": -1, "chains": 2,
                  "graph_sweeps": 256} for blk in (64, 128)]
     out += [{"engine": "onchip", "words_per_thread": nw} for nw in (4, 1)]  # where the state fits on chip
+    out += [{"engine": "tma", "chains": c} for c in (1, 2) if c <= R]  # where the row pitch allows TMA tiles
     if L <= 40:
         out.append({"engine": "resident"})
     if L <= 32:
@@ -76,6 +77,8 @@ def apply(g, choice, resident_sweeps=256):
         g.set_engine("stream")
         g.set_launch_config(choice["words_per_thread"], choice["block"], choice["blocks_per_sm"], True,
                             choice.get("graph_sweeps", 64))
+    elif choice["engine"] == "tma":
+        g.set_engine("tma")
     elif choice["engine"] == "onchip":
         g.set_launch_config(choice["words_per_thread"], 128, -1, True, 64)
         g.set_engine("onchip", 2048)

@@ -57,7 +57,9 @@ struct micsa_ctx {
     OnchipPlan oc;                   // partition of the ONCHIP engine (oc.grid == 0: not planned)
     int16_t *d_oc_nbrs = nullptr;    // its neighbour table
     unsigned *d_oc_flags = nullptr;  // its epoch flags
-    int *d_error = nullptr;          // device-side wait time-outs (ONCHIP)
+    int *d_error = nullptr;          // device-side wait time-outs (ONCHIP, TMA)
+    TmaMaps tma;                     // tensor maps of the TMA engine (tma.valid: encoded)
+    int tma_ctas = 0;                // its persistent grid
     long long wait_limit = 1ll << 22;  // polls per wait
     std::string err;
 };
@@ -228,6 +230,9 @@ cudaError_t launch_group_half(micsa_t h, int gi, const LaunchConfig &lc, SweepAr
                               cudaStream_t st) {
     replica_group(h, c, chains, a.r0, a.r1);
     if (gi == kGraphPlanes) return launch_planes_half(h, lc, a.parity, a.cursor, a.k, a.r0, a.r1, st);
+    if (gi == kGraphMicsa && h->engine == MICSA_ENGINE_TMA && h->tma.valid)
+        return launch_tma_half(h->tma, h->d_spins, h->d_daemons, h->geo, h->S, h->R, a.r0, a.r1, a.parity, a.key0,
+                               a.key1, a.params, a.cursor, a.k, h->d_error, h->wait_limit, h->tma_ctas, lc.pdl, st);
     return launch_half_sweep(a, gi == kGraphMetro, lc, st);
 }
 
@@ -302,6 +307,7 @@ int active_engine(micsa_t h) {
         return msg_supported(h->geo) ? MICSA_ENGINE_MULTISPIN_GLOBAL : MICSA_ENGINE_STREAM;
     if (h->engine == MICSA_ENGINE_STREAM || h->gamma > 1 || h->walkers) return MICSA_ENGINE_STREAM;
     if (h->engine == MICSA_ENGINE_ONCHIP) return h->oc.grid > 0 ? MICSA_ENGINE_ONCHIP : MICSA_ENGINE_STREAM;
+    if (h->engine == MICSA_ENGINE_TMA) return h->tma.valid ? MICSA_ENGINE_TMA : MICSA_ENGINE_STREAM;
     if (!h->d_units) return MICSA_ENGINE_STREAM;
     if (h->engine == MICSA_ENGINE_RESIDENT) return MICSA_ENGINE_RESIDENT;
     if (multispin_smem_bytes(h->geo) > 0) return MICSA_ENGINE_MULTISPIN;
@@ -394,6 +400,27 @@ int run_resident(micsa_t h, int64_t n, const LaunchConfig &lc) {
     return MICSA_OK;
 }
 
+int ensure_error_word(micsa_t h) {
+    if (h->d_error) return MICSA_OK;
+    CK(h, cudaMalloc(&h->d_error, sizeof(int)), "cudaMalloc error word");
+    CK(h, cudaMemset(h->d_error, 0, sizeof(int)), "clear error word");
+    return MICSA_OK;
+}
+
+// Tensor maps and grid of the TMA engine.
+int plan_tma(micsa_t h) {
+    if (h->tma.valid) return MICSA_OK;
+    if (!tma_supported(h->geo, h->gamma, h->walkers) || tma_stages(h->geo) < 2)
+        return fail(h, MICSA_E_INVALID_ARG, "the TMA engine needs L %% 8 == 0, a row pitch of 16..256 bytes in "
+                                            "steps of 16, gamma = 1 and no walkers (L=%d)", h->L);
+    if (int rc = ensure_error_word(h)) return rc;
+    const int ctas = tma_max_ctas(h->geo, h->sm_count);
+    if (ctas < 1) return fail(h, MICSA_E_CUDA, "the TMA kernel cannot be resident");
+    CK(h, tma_encode(h->tma, h->d_spins, h->d_daemons, h->d_bonds, h->geo, h->S, h->R), "encode tensor maps");
+    h->tma_ctas = ctas;
+    return MICSA_OK;
+}
+
 // Partition, neighbour table and flags of the ONCHIP engine for words-per-item nw.
 int plan_onchip(micsa_t h, int nw) {
     if (h->oc.grid > 0 && h->oc.nw == nw) return MICSA_OK;
@@ -411,10 +438,7 @@ int plan_onchip(micsa_t h, int nw) {
     CK(h, cudaMemcpy(h->d_oc_nbrs, plan.table.data(), sizeof(int16_t) * plan.table.size(), cudaMemcpyHostToDevice),
        "upload neighbour table");
     CK(h, cudaMalloc(&h->d_oc_flags, sizeof(unsigned) * onchip_flag_words(plan.grid)), "cudaMalloc flags");
-    if (!h->d_error) {
-        CK(h, cudaMalloc(&h->d_error, sizeof(int)), "cudaMalloc error word");
-        CK(h, cudaMemset(h->d_error, 0, sizeof(int)), "clear error word");
-    }
+    if (int rc = ensure_error_word(h)) return rc;
     h->oc = std::move(plan);
     return MICSA_OK;
 }
@@ -477,7 +501,7 @@ int run_table(micsa_t h, bool metro, int64_t n) {
         for (int p = 0; p < 2; ++p) {
             a.k = k;
             a.parity = p;
-            CK(h, launch_half_sweep(a, metro, lc, h->stream), "half-sweep launch");
+            CK(h, launch_group_half(h, metro ? kGraphMetro : kGraphMicsa, lc, a, 0, 1, h->stream), "half-sweep launch");
             ++h->launches;
         }
     return MICSA_OK;
@@ -815,7 +839,7 @@ int micsa_set_launch_config(micsa_t h, int words_per_thread, int block, int bloc
 
 int micsa_set_engine(micsa_t h, int engine, int resident_sweeps) {
     if (!h) return MICSA_E_INVALID_ARG;
-    if (engine < MICSA_ENGINE_AUTO || engine > MICSA_ENGINE_ONCHIP || resident_sweeps < 1 ||
+    if (engine < MICSA_ENGINE_AUTO || engine > MICSA_ENGINE_TMA || resident_sweeps < 1 ||
         resident_sweeps > 1 << 20)
         return fail(h, MICSA_E_INVALID_ARG, "bad engine selection");
     if (engine == MICSA_ENGINE_MULTISPIN_GLOBAL && !msg_supported(h->geo))
@@ -828,6 +852,9 @@ int micsa_set_engine(micsa_t h, int engine, int resident_sweeps) {
     CK(h, cudaStreamSynchronize(h->stream), "synchronize before reconfiguring");
     if (engine == MICSA_ENGINE_ONCHIP)
         if (int rc = plan_onchip(h, effective_config(h, false).nw)) return rc;
+    if (engine == MICSA_ENGINE_TMA)
+        if (int rc = plan_tma(h)) return rc;
+    drop_graphs(h);  // captured graphs hold the previous engine's kernels
     h->engine = engine;
     h->resident_sweeps = resident_sweeps;
     return MICSA_OK;

@@ -1,6 +1,7 @@
 // micsa_internal.h -- declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -167,6 +168,21 @@ cudaError_t launch_onchip(const OnchipPlan &plan, int8_t *spins, uint8_t *daemon
                           int64_t k0, int K, unsigned *flags, int *error, const int16_t *nbrs, long long wait_limit,
                           cudaStream_t st);
 cudaError_t launch_wait_selftest(unsigned *flag, int *error, long long wait_limit, cudaStream_t st);
+
+// half-sweep with TMA-staged tiles (tma_sweep.cu)
+struct TmaMaps {
+    CUtensorMap m_int, m_yh, m_zh, m_dmn, m_bond;  // spins (3 box shapes), daemons, bonds
+    bool valid = false;
+};
+bool tma_supported(const Geometry &g, int gamma, int walkers);
+cudaError_t tma_encode(TmaMaps &m, int8_t *spins, uint8_t *daemons, const uint8_t *bonds, const Geometry &g, int S,
+                       int R);
+int tma_stages(const Geometry &g);
+int tma_max_ctas(const Geometry &g, int sm_count);
+cudaError_t launch_tma_half(const TmaMaps &m, int8_t *spins, uint8_t *daemons, const Geometry &g, int S, int R,
+                            int r0, int r1, int parity, uint32_t key0, uint32_t key1, const SweepParam *params,
+                            const int64_t *cursor, int64_t k, int *error, long long wait_limit, int max_ctas,
+                            bool pdl, cudaStream_t st);
 
 // multispin planes in global memory for L % 32 == 0 (multispin.cu)
 bool msg_supported(const Geometry &g);

@@ -463,3 +463,52 @@ def test_global_multispin_gamma_walkers(L, S, R, gamma, walkers, interval, chain
         g.run(sched[151:], interval)
         O.run_ex(st, sched[151:], interval)
         assert_same_state(g, st, "log schedule, odd lengths")
+
+
+@pytest.mark.parametrize("L,S,R,chains", [(32, 2, 3, 1), (32, 1, 3, 2), (64, 1, 2, 1), (96, 2, 1, 1)])
+def test_tma_engine_matches_oracle(L, S, R, chains):
+    """Tiles staged by TMA tensor copies (periodic halo boxes, mbarrier ring):
+    bit-exact with the oracle over graph replays, the log schedule and a refresh
+    every sweep."""
+    seed = 4000 + L + R
+    sched = np.linspace(2.4, 0.6, 170)
+    with micsa.Micsa(L, S, R, seed) as g:
+        g.set_engine("tma")
+        g.set_replica_chains(chains)
+        assert g.engine() == "tma"
+        st = O.create(L, S, R, seed)
+        g.run(sched[:140], 7)
+        O.run(st, sched[:140], 7)
+        assert_same_state(g, st, "fixed interval")
+        g.run_logrefresh(sched[140:160])
+        O.run_logrefresh(st, sched[140:160])
+        g.run(sched[160:], 1)
+        O.run(st, sched[160:], 1)
+        assert_same_state(g, st, "log schedule and refresh every sweep")
+
+
+def test_tma_engine_matches_streaming_l160():
+    """L = 160, two replicas: the TMA engine (one and two replica chains) gives
+    the streaming engine's bits and observables."""
+    sched = np.linspace(1.6, 0.7, 150)
+    out = []
+    for engine, chains in [("stream", 1), ("tma", 1), ("tma", 2)]:
+        with micsa.Micsa(160, 1, 2, 79) as g:
+            g.set_engine(engine)
+            g.set_replica_chains(chains)
+            g.run(sched, 10)
+            out.append(g.get_state() + (g.measure(),))
+    for s, m, t, meas in out[1:]:
+        np.testing.assert_array_equal(s, out[0][0])
+        np.testing.assert_array_equal(m, out[0][1])
+        for a, b in zip(meas, out[0][3]):
+            np.testing.assert_array_equal(a, b)
+
+
+def test_tma_engine_limits():
+    """Row pitches that are not a multiple of 16 bytes, gamma > 1 and walkers
+    are rejected."""
+    for L, kw in [(48, {}), (32, {"gamma": 2}), (32, {"walkers": True})]:
+        with micsa.Micsa(L, 1, 2, 1, **kw) as g:
+            with pytest.raises(micsa.MicsaError):
+                g.set_engine("tma")
