@@ -52,7 +52,7 @@ def candidates(L, R=1):
             for nw, blk, bps in itertools.product([4, 2], [64, 128], [-1, 0, 4, 6, 8])]
     if R >= 2:  # replica groups as concurrent kernel chains in the graphs
         out += [{"engine": "stream", "words_per_thread": 4, "block": blk, "blocks_per_sm": bps, "chains": 2}
-                for blk, bps in itertools.product([64, 128, 256], [-1, 3, 4])]
+                for blk, bps in itertools.product([64, 128, 256], [-1, 0, 3, 4])]
         out += [{"engine": "stream", "words_per_thread": 4, "block": blk, "blocks_per_sm": -1, "chains": 2,
                  "graph_sweeps": 256} for blk in (64, 128)]
     out += [{"engine": "onchip", "words_per_thread": nw} for nw in (4, 1)]  # where the state fits on chip

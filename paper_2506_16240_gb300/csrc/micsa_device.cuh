@@ -85,8 +85,10 @@ struct Geometry {
 // neighbour is O[i] and its -x neighbour O[i-1]; for o = 1 (x = 2i + 1) they
 // are O[i+1] and O[i]. `edge` is the byte just before the range (o = 0) or
 // just after it (o = 1), `first` and `last` the row's bytes 0 and Lh - 1 for
-// the periodic wrap.
-template <int NW>
+// the periodic wrap. INSERT = false: the caller has already passed the row's
+// first byte as `edge` when the range ends at the row's last site (rows
+// without padding), so no wrap byte needs inserting.
+template <int NW, bool INSERT = true>
 __device__ __forceinline__ void x_neighbours(const uint32_t (&O)[NW], int o, int b0, int Lh,
                                              uint32_t edge, uint32_t first, uint32_t last,
                                              uint32_t (&xp)[NW], uint32_t (&xm)[NW]) {
@@ -103,16 +105,18 @@ __device__ __forceinline__ void x_neighbours(const uint32_t (&O)[NW], int o, int
             xm[j] = O[j];
             xp[j] = (O[j] >> 8) | ((j + 1 < NW ? (O[j + 1] & 0xFFu) : edge) << 24);
         }
-        // the row's last site takes the row's first byte as its +x neighbour;
-        // written branch-free per word so that xp stays in registers
-        const int e = Lh - 1 - b0;  // position of the row's last site in this range
+        if constexpr (INSERT) {
+            // the row's last site takes the row's first byte as its +x neighbour;
+            // written branch-free per word so that xp stays in registers
+            const int e = Lh - 1 - b0;  // position of the row's last site in this range
 #pragma unroll
-        for (int j = 0; j < NW; ++j) {
-            const int pos = e - 4 * j;
-            const bool here = pos >= 0 && pos < 4;
-            const uint32_t sh = here ? 8u * (uint32_t)pos : 0u;
-            const uint32_t m = here ? (0xFFu << sh) : 0u;
-            xp[j] = (xp[j] & ~m) | ((first << sh) & m);
+            for (int j = 0; j < NW; ++j) {
+                const int pos = e - 4 * j;
+                const bool here = pos >= 0 && pos < 4;
+                const uint32_t sh = here ? 8u * (uint32_t)pos : 0u;
+                const uint32_t m = here ? (0xFFu << sh) : 0u;
+                xp[j] = (xp[j] & ~m) | ((first << sh) & m);
+            }
         }
     }
 }
@@ -167,7 +171,7 @@ __device__ __forceinline__ uint32_t creutz4(uint32_t u32, uint32_t &D, uint32_t 
     const uint32_t t = (u32 >> 5) + D;         // u + m in 0..9 per lane
     const uint32_t v = t + 0x7D7D7D7Du;         // 0x80..0x83 <=> accepted
     const uint32_t ok = v & ~(v << 5) & 0x80808080u;
-    const uint32_t am = lanes_from_msb(ok) & valid;
+    const uint32_t am = ((ok >> 7) * 0xFFu) & valid;  // ok has bit 7 of a lane at most
     D = (D & ~am) | (v & 0x03030303u & am);
     return am;
 }

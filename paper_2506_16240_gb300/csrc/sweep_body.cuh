@@ -24,7 +24,9 @@ __device__ __forceinline__ uint32_t load_byte(const int8_t *p) {
     else return (uint8_t)__ldg(p);
 }
 
-template <int NW, bool METRO, bool SMEM = false>
+// FULL: rows without padding (P == Lh, so every lane is a site and a range of
+// 4 NW bytes that reaches the row's end ends exactly at its last site).
+template <int NW, bool METRO, bool SMEM = false, bool FULL = false>
 __device__ __forceinline__ void update_chunk(const Geometry &g, int8_t *spins, uint8_t *daemons,
                                              const uint8_t *bonds, int p, int row, int c,
                                              uint32_t gid, uint32_t key0, uint32_t key1, int64_t t,
@@ -53,7 +55,13 @@ __device__ __forceinline__ void update_chunk(const Geometry &g, int8_t *spins, u
 
     // edge bytes for the x shift and the periodic wrap of the row
     uint32_t edge = 0, first = 0, last = 0;
-    if (o == 0) {
+    if constexpr (FULL) {
+        // o = 0: the byte before the range, or the row's last byte at the row's start
+        // o = 1: the byte after the range, or the row's first byte at the row's end
+        const int8_t *e = o == 0 ? (b0 == 0 ? opp + row0 + g.Lh - 1 : opp + off_c - 1)
+                                 : (b0 + 4 * NW < g.Lh ? opp + off_c + 4 * NW : opp + row0);
+        edge = last = load_byte<SMEM>(e);
+    } else if (o == 0) {
         if (b0 == 0) last = load_byte<SMEM>(opp + row0 + g.Lh - 1);
         else edge = load_byte<SMEM>(opp + off_c - 1);
     } else {
@@ -61,7 +69,7 @@ __device__ __forceinline__ void update_chunk(const Geometry &g, int8_t *spins, u
         else first = (b0 == 0) ? (O[0] & 0xFFu) : load_byte<SMEM>(opp + row0);
     }
     uint32_t xp[NW], xm[NW];
-    x_neighbours<NW>(O, o, b0, g.Lh, edge, first, last, xp, xm);
+    x_neighbours<NW, !FULL>(O, o, b0, g.Lh, edge, first, last, xp, xm);
     const uint32_t quad0 = (uint32_t)((((int64_t)p * g.L + z) * g.L + y) * g.W + c * NW);
 
 #pragma unroll
@@ -69,7 +77,7 @@ __device__ __forceinline__ void update_chunk(const Geometry &g, int8_t *spins, u
         const BondPlanes bp = bond_planes(Bw[j]);
         const uint32_t neg = negative_terms(bp, xp[j], xm[j], Oyp[j], Oym[j], Ozp[j], Ozm[j]);
         const uint32_t u32 = unsatisfied32(neg, S[j]);
-        const uint32_t valid = valid_mask(b0, j, g.Lh);
+        const uint32_t valid = FULL ? 0xFFFFFFFFu : valid_mask(b0, j, g.Lh);
         if (METRO) {
             // dH = 12 - 4u > 0 <=> u < 3; accept iff a fresh uniform is below
             // the Metropolis cut point of dH (index 2 - u).

@@ -26,7 +26,7 @@ __device__ __forceinline__ void grid_launch_dependents() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
-template <int NW, bool METRO>
+template <int NW, bool METRO, bool FULL>
 __device__ __forceinline__ void half_sweep_body(const SweepArgs &a) {
     grid_dependency_wait();  // the previous half-sweep's writes are visible after this
     grid_launch_dependents();
@@ -47,23 +47,24 @@ __device__ __forceinline__ void half_sweep_body(const SweepArgs &a) {
                 // daemon family alpha of this replica; its Philox id is gid * gamma + alpha
                 // (Metropolis draws use gid itself)
                 const int64_t fam = gid * a.gamma + prm.alpha;
-                update_chunk<NW, METRO>(g, a.spins + gid * 2 * g.half, a.daemons + fam * 2 * g.half,
+                update_chunk<NW, METRO, false, FULL>(g, a.spins + gid * 2 * g.half, a.daemons + fam * 2 * g.half,
                                         a.bonds + (int64_t)sample * 2 * g.half, a.parity, (int)row, c,
                                         (uint32_t)(METRO ? gid : fam), a.key0, a.key1, prm.t, refresh, prm.th0,
                                         prm.th1, prm.th2, a.div_L);
             }
 }
 
-template <int NW, bool METRO>
+// FULL: rows without padding (P == L / 2), see update_chunk.
+template <int NW, bool METRO, bool FULL = false>
 __global__ void __launch_bounds__(256) half_sweep_kernel(SweepArgs a) {
-    half_sweep_body<NW, METRO>(a);
+    half_sweep_body<NW, METRO, FULL>(a);
 }
 
 // The same kernel with registers capped at 64 per thread (8 blocks of 128
 // threads per SM): more warps in flight for the latency-bound L2-resident case.
-template <int NW, bool METRO>
+template <int NW, bool METRO, bool FULL = false>
 __global__ void __launch_bounds__(128, 8) half_sweep_kernel_rc(SweepArgs a) {
-    half_sweep_body<NW, METRO>(a);
+    half_sweep_body<NW, METRO, FULL>(a);
 }
 
 // Wandering (Sec. 2.6): every site of parity p exchanges the walker of family
@@ -142,8 +143,12 @@ static cudaError_t launch_variant(const SweepArgs &a0, const LaunchConfig &lc, c
     attr[0].val.programmaticStreamSerializationAllowed = lc.pdl ? 1 : 0;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (lc.regcap) return cudaLaunchKernelEx(&cfg, half_sweep_kernel_rc<NW, METRO>, a);
-    return cudaLaunchKernelEx(&cfg, half_sweep_kernel<NW, METRO>, a);
+    const bool full = a.geo.P == a.geo.Lh;
+    if (lc.regcap)
+        return full ? cudaLaunchKernelEx(&cfg, half_sweep_kernel_rc<NW, METRO, true>, a)
+                    : cudaLaunchKernelEx(&cfg, half_sweep_kernel_rc<NW, METRO, false>, a);
+    return full ? cudaLaunchKernelEx(&cfg, half_sweep_kernel<NW, METRO, true>, a)
+                : cudaLaunchKernelEx(&cfg, half_sweep_kernel<NW, METRO, false>, a);
 }
 
 int vector_words(const Geometry &g, int want) {
