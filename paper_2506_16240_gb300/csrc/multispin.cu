@@ -575,7 +575,8 @@ __device__ __forceinline__ void gather_words(const uint32_t *Sx, int dd, int64_t
 }
 
 // MINB: minimum resident blocks of 128 per SM the register allocation must
-// allow (1: unconstrained; 5: the register-capped variant, at most 102 registers).
+// allow (4: the default, at most 128 registers; 5: the register-capped
+// variant, at most 102).
 template <int NW, int MINB>
 __global__ void __launch_bounds__(128, MINB) msg_half_kernel(MsgArgs a) {
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -926,9 +927,9 @@ cudaError_t launch_msg_half(uint32_t *planes, const uint32_t *bplanes, const Geo
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     switch (nw * (regcap ? -1 : 1)) {
-        case 1: return cudaLaunchKernelEx(&cfg, msg_half_kernel<1, 1>, a);
-        case 2: return cudaLaunchKernelEx(&cfg, msg_half_kernel<2, 1>, a);
-        case 4: return cudaLaunchKernelEx(&cfg, msg_half_kernel<4, 1>, a);
+        case 1: return cudaLaunchKernelEx(&cfg, msg_half_kernel<1, 4>, a);
+        case 2: return cudaLaunchKernelEx(&cfg, msg_half_kernel<2, 4>, a);
+        case 4: return cudaLaunchKernelEx(&cfg, msg_half_kernel<4, 4>, a);
         case -1: return cudaLaunchKernelEx(&cfg, msg_half_kernel<1, 5>, a);
         case -2: return cudaLaunchKernelEx(&cfg, msg_half_kernel<2, 5>, a);
         case -4: return cudaLaunchKernelEx(&cfg, msg_half_kernel<4, 5>, a);

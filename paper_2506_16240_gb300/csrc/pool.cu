@@ -51,7 +51,7 @@ struct PoolTables {
 __device__ __forceinline__ void pool_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pool_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-template <int NW>
+template <int NW, bool FULL>
 __device__ __forceinline__ void pool_item(const JobDesc &J, int r, uint32_t chunk, int p, int64_t t) {
     const FastDiv dc{(uint32_t)(J.geo.W / NW), J.divC_m, J.divC_l};
     const uint32_t row = fdiv(chunk, dc);
@@ -65,7 +65,7 @@ __device__ __forceinline__ void pool_item(const JobDesc &J, int r, uint32_t chun
         th2 = q[2];
     }
     const FastDiv divL{(uint32_t)J.geo.L, J.divL_m, J.divL_l};
-    update_chunk<NW, false>(J.geo, J.spins + (int64_t)r * 2 * J.geo.half,
+    update_chunk<NW, false, false, FULL>(J.geo, J.spins + (int64_t)r * 2 * J.geo.half,
                             J.daemons + (int64_t)r * 2 * J.geo.half, J.bonds, p, (int)row, c, (uint32_t)r,
                             J.key0, J.key1, t, refresh, th0, th1, th2, divL);
 }
@@ -83,9 +83,10 @@ __global__ void __launch_bounds__(kVBlock) pool_half_sweep_kernel(PoolTables T, 
         const uint32_t chunks = (uint32_t)J.geo.L * J.geo.L * (J.geo.W / J.nw);
         const uint32_t chunk = (uint32_t)b.chunk0 + threadIdx.x;
         if (chunk >= chunks) continue;
-        if (J.nw == 4) pool_item<4>(J, b.replica, chunk, p, t);
-        else if (J.nw == 2) pool_item<2>(J, b.replica, chunk, p, t);
-        else pool_item<1>(J, b.replica, chunk, p, t);
+        const bool full = J.geo.P == J.geo.Lh;  // rows without padding
+        if (J.nw == 4) full ? pool_item<4, true>(J, b.replica, chunk, p, t) : pool_item<4, false>(J, b.replica, chunk, p, t);
+        else if (J.nw == 2) full ? pool_item<2, true>(J, b.replica, chunk, p, t) : pool_item<2, false>(J, b.replica, chunk, p, t);
+        else full ? pool_item<1, true>(J, b.replica, chunk, p, t) : pool_item<1, false>(J, b.replica, chunk, p, t);
     }
 }
 
