@@ -579,11 +579,12 @@ __device__ __forceinline__ void gather_words(const uint32_t *Sx, int dd, int64_t
 // variant, at most 102).
 template <int NW, int MINB>
 __global__ void __launch_bounds__(128, MINB) msg_half_kernel(MsgArgs a) {
+    // parameters first: no kernel of a graph replay writes the table or the cursor
+    const int64_t kidx = a.k + (a.cursor ? *a.cursor : 0);
+    const SweepParam prm = a.params[kidx];
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     constexpr int G = 4 / NW;  // lanes sharing one Philox block of words
-    const int64_t kidx = a.k + (a.cursor ? *a.cursor : 0);
-    const SweepParam prm = a.params[kidx];
     const bool refresh = prm.mode == kModeRefresh;
     // grid: x covers the L * nzw * Lh / NW threads of one sample exactly (a
     // multiple of 128 for L % 32 == 0), y the replica groups, z the samples

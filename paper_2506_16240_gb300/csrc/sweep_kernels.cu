@@ -28,12 +28,16 @@ __device__ __forceinline__ void grid_launch_dependents() {
 
 template <int NW, bool METRO, bool FULL>
 __device__ __forceinline__ void half_sweep_body(const SweepArgs &a) {
+    // The sweep's parameters are read before waiting for the previous grid: no
+    // kernel of a graph replay writes the table or the replay cursor (the
+    // cursor is advanced by the replay's last node, and replays are ordered by
+    // the stream), so the two dependent loads overlap the wait.
+    const int64_t kidx = a.k + (a.cursor ? *a.cursor : 0);
+    const SweepParam prm = a.params[kidx];
     grid_dependency_wait();  // the previous half-sweep's writes are visible after this
     grid_launch_dependents();
     const Geometry g = a.geo;
     const uint32_t per_sample = (uint32_t)g.L * g.L * (g.W / NW);  // < 2^31 for L <= 1600
-    const int64_t kidx = a.k + (a.cursor ? *a.cursor : 0);
-    const SweepParam prm = a.params[kidx];
     const bool refresh = !METRO && prm.mode == kModeRefresh;
 
     // grid: x over the chunks of one sample, y over samples; thread row y of

@@ -141,9 +141,10 @@ __global__ void __launch_bounds__(kTmaThreads, 1) tma_half_kernel(const __grid_c
     __shared__ __align__(8) uint64_t bars[kTmaMaxStages];
     // TMA destinations 128-byte aligned (128 bytes of slack are allocated)
     uint8_t *sm = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(sm_raw) + 127) & ~(uintptr_t)127);
+    // parameters first: no kernel of a graph replay writes the table or the cursor
+    const SweepParam prm = a.params[a.k + (a.cursor ? *a.cursor : 0)];
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-    const SweepParam prm = a.params[a.k + (a.cursor ? *a.cursor : 0)];
     const bool refresh = prm.mode == kModeRefresh;
     const Geometry &g = a.g;
     const int P = g.P, L = g.L, p = a.parity;
