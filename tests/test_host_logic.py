@@ -1,0 +1,190 @@
+"""Host logic without a GPU: the continuous-batching request loop (against a
+fake pool that enforces slot and memory limits), the synthetic request stream
+and the autotuner's choice (against a fake handle and fake timing events)."""
+import numpy as np
+import pytest
+
+from paper_2506_16240_gb300 import autotune, serve
+
+
+class FakePool:
+    """Slots, an arena budget of L^3 * R bytes per job, K sweeps per tick."""
+
+    def __init__(self, max_jobs=3, arena=3 * 32 ** 3 * 2, tick_sweeps=1000):
+        self.max_jobs, self.arena, self.K = max_jobs, arena, tick_sweeps
+        self.live, self.next_id, self.used, self.ticks = {}, 0, 0, 0
+        self.admitted, self.peak_jobs, self.peak_bytes = [], 0, 0
+
+    def submit(self, L, R, seed, n_sweeps, interval, T0, T1):
+        need = L ** 3 * R
+        if len(self.live) >= self.max_jobs or self.used + need > self.arena:
+            return None
+        jid = self.next_id
+        self.next_id += 1
+        self.live[jid] = {"need": need, "left": n_sweeps, "seed": seed, "done": False}
+        self.used += need
+        self.admitted.append(seed)
+        self.peak_jobs = max(self.peak_jobs, len(self.live))
+        self.peak_bytes = max(self.peak_bytes, self.used)
+        return jid
+
+    def tick(self):
+        self.ticks += 1
+        for j in self.live.values():
+            j["left"] -= self.K
+            j["done"] = j["left"] <= 0
+
+    def wait_ticks(self, n):
+        pass
+
+    def finished(self):
+        return [jid for jid, j in self.live.items() if j["done"]]
+
+    def poll(self, jid, best_spins=False):
+        j = self.live.pop(jid)
+        self.used -= j["need"]
+        return {"energy": [-j["seed"]], "seed": j["seed"]}
+
+
+def _requests(n, seed=0):
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        L = int(rng.choice([16, 24, 32]))
+        out.append(serve.Request(arrival=0.001 * k, L=L, n_replicas=int(rng.integers(1, 3)), seed=k + 1,
+                                 n_sweeps=int(rng.integers(500, 5000)), refresh_interval=10, T_start=3.0,
+                                 T_end=0.3))
+    return out
+
+
+def test_serving_loop_admits_in_order_within_limits_and_completes_every_job():
+    pool = FakePool()
+    reqs = _requests(25)
+    done = serve.Server(pool).serve(reqs, realtime=False)
+    assert len(done) == len(reqs) and {r.seed for r in done} == {r.seed for r in reqs}
+    assert pool.admitted == sorted(pool.admitted)          # FIFO admission
+    assert pool.peak_jobs <= pool.max_jobs and pool.peak_bytes <= pool.arena
+    assert pool.used == 0 and not pool.live                 # everything freed
+    for r in done:
+        assert r.result["seed"] == r.seed and r.job_id >= 0
+        assert 0.0 <= r.admitted <= r.done
+    s = serve.summarize(done, 1.0)
+    lat = np.array([r.done - r.arrival for r in done])
+    assert s["jobs"] == 25 and s["p50_latency_s"] == pytest.approx(np.percentile(lat, 50))
+    assert s["updates"] == sum(r.L ** 3 * r.n_replicas * r.n_sweeps for r in reqs)
+
+
+def test_serving_loop_respects_arrival_times():
+    pool = FakePool(max_jobs=8, arena=1 << 30)
+    reqs = _requests(6)
+    for k, r in enumerate(reqs):
+        r.arrival = 0.02 * k
+    done = serve.Server(pool).serve(reqs, realtime=True)
+    assert len(done) == 6
+    for r in done:
+        assert r.admitted >= r.arrival - 1e-3  # never admitted before it arrived
+
+
+def test_poisson_stream_follows_its_distributions():
+    reqs = serve.poisson_stream(4000, rate_hz=50.0, seed=5)
+    assert reqs == serve.poisson_stream(4000, rate_hz=50.0, seed=5)  # deterministic per seed
+    arr = np.array([r.arrival for r in reqs])
+    gaps = np.diff(np.concatenate([[0.0], arr]))
+    assert np.all(gaps > 0) and gaps.mean() == pytest.approx(1 / 50.0, rel=0.06)
+    Ls = np.array([r.L for r in reqs])
+    assert np.all(Ls % 2 == 0) and Ls.min() >= 16 and Ls.max() <= 96
+    assert len(set(Ls)) == 41  # every even L in 16..96 appears
+    sw = np.array([r.n_sweeps for r in reqs])
+    assert sw.min() >= 999 and sw.max() <= 100_000
+    assert np.mean(np.log(sw)) == pytest.approx(np.mean([np.log(1e3), np.log(1e5)]), abs=0.1)
+    R = np.array([r.n_replicas for r in reqs])
+    assert set(R) == {1, 2, 3, 4}
+    mc = np.mean([r.updates for r in serve.poisson_stream(40000, 1.0, 9)])
+    assert serve.mean_job_updates() == pytest.approx(mc, rel=0.05)
+
+
+class FakeHandle:
+    """Records the launch shape applied; run() charges a fake time per shape."""
+
+    def __init__(self, L, S, R, cost):
+        self.L, self.S, self.R, self.cost = L, S, R, cost
+        self.engine, self.shape, self.chains, self.rpt, self.log = "stream", None, 1, 0, []
+
+    def set_engine(self, engine, resident_sweeps=None):
+        if engine == "tma" and self.L % 32:
+            raise autotune.MicsaError(-1, "does not fit")
+        self.engine = engine
+
+    def set_launch_config(self, nw, block, bps, pdl, graph):
+        self.shape = (nw, block, bps, graph)
+
+    def set_replica_chains(self, c):
+        self.chains = c
+
+    def set_multispin_replicas(self, r):
+        self.rpt = r
+
+    def key(self):
+        return (self.engine, self.shape, self.chains, self.rpt)
+
+    def run(self, sched, interval):
+        self.log.append(self.key())
+
+
+class FakeEvent:
+    clock = []
+
+    def __init__(self, enable_timing=True):
+        self.t = None
+
+    def record(self, stream=None):
+        self.t = len(FakeEvent.clock)
+        FakeEvent.clock.append(None)
+
+    def elapsed_time(self, other):
+        return FakeEvent.costs[other.t]
+
+
+class FakeTorch:
+    class cuda:
+        Event = FakeEvent
+
+        @staticmethod
+        def synchronize():
+            pass
+
+        @staticmethod
+        def get_device_name():
+            return "fake"
+
+
+def test_autotuner_keeps_the_fastest_shape_and_skips_engines_that_do_not_fit(monkeypatch):
+    best = ("multispin_global", (2, 128, -1, 64), 1, 4)
+    h = FakeHandle(160, 1, 8, None)
+    FakeEvent.clock, FakeEvent.costs = [], {}
+    orig_record = FakeEvent.record
+
+    def record(self, stream=None):  # the stop event of a timed run carries the shape's cost
+        orig_record(self)
+        FakeEvent.costs[self.t] = 1.0 if h.key() == best else 2.0
+
+    monkeypatch.setattr(FakeEvent, "record", record)
+    choice = autotune.tune(h, FakeTorch, None, sweeps=20, use_cache=False)
+    assert (choice["engine"], choice["words_per_thread"], choice["replicas_per_thread"]) == ("multispin_global", 2, 4)
+    assert h.key() == best  # the choice is applied at the end
+    engines = {k[0] for k in h.log}
+    assert {"stream", "multispin_global", "onchip", "tma"} <= engines
+    h2 = FakeHandle(48, 1, 2, None)  # tma does not fit: skipped, not fatal
+    FakeEvent.clock, FakeEvent.costs = [], {}
+    autotune.tune(h2, FakeTorch, None, sweeps=20, use_cache=False, engines=("stream", "tma"))
+    assert {k[0] for k in h2.log} == {"stream"}
+
+
+def test_autotune_candidates_are_gated_by_lattice_shape():
+    c160 = autotune.candidates(160, 2)
+    assert not any(c["engine"] in ("resident", "multispin") for c in c160)
+    assert any(c["engine"] == "multispin_global" for c in c160)
+    assert any(c.get("chains") == 2 for c in c160)
+    c18 = autotune.candidates(18, 1)
+    assert any(c["engine"] == "resident" for c in c18) and any(c["engine"] == "multispin" for c in c18)
+    assert not any(c["engine"] == "multispin_global" or c.get("chains", 1) > 1 for c in c18)
