@@ -46,6 +46,8 @@ struct PoolTables {
     long long *aux;
     long long *best_energy;
     long long *best_t;
+    unsigned long long *acc;  // [max_jobs][kPoolMaxR][2] energy and daemon sums of the tick (zero between ticks)
+    int32_t *improved;        // [max_jobs][kPoolMaxR] the tick's energy is the lowest so far
 };
 
 __device__ __forceinline__ void pool_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
@@ -90,87 +92,140 @@ __global__ void __launch_bounds__(kVBlock) pool_half_sweep_kernel(PoolTables T, 
     }
 }
 
-// Exact energy and daemon energy of every (live, advancing) job replica after
-// the tick; keeps the lowest energy and its configuration. One block per
-// (slot, replica).
-__global__ void __launch_bounds__(256) pool_measure_kernel(PoolTables T, int K) {
+// Energy of the even sites and daemon energy of NW words of one chunk of row
+// (z, y) of one replica: H_EA = sum over even sites of (2u - 6), every bond
+// having exactly one even end for even L; H_aux = 4 * sum of m over both
+// parities. Same neighbour assembly as update_chunk.
+template <int NW, bool FULL>
+__device__ __forceinline__ void chunk_measure(const Geometry &g, const int8_t *sp, const uint8_t *dm,
+                                              const uint8_t *bonds, int row, int c, const FastDiv &divL, int &e,
+                                              int &a) {
+    const int z = (int)fdiv((uint32_t)row, divL), y = row - z * g.L;
+    const int o = (y + z) & 1;
+    const int b0 = c * 4 * NW;
+    const int yp = (y + 1 == g.L) ? 0 : y + 1, ym = (y == 0) ? g.L - 1 : y - 1;
+    const int zp = (z + 1 == g.L) ? 0 : z + 1, zm = (z == 0) ? g.L - 1 : z - 1;
+    const int64_t row0 = (int64_t)row * g.P, off = row0 + b0;
+    const int8_t *odd = sp + g.half;
+    uint32_t O[NW], Oyp[NW], Oym[NW], Ozp[NW], Ozm[NW], B[NW], S[NW], D0[NW], D1[NW];
+    load_words<NW>(odd + off, O);
+    load_words<NW>(odd + ((int64_t)z * g.L + yp) * g.P + b0, Oyp);
+    load_words<NW>(odd + ((int64_t)z * g.L + ym) * g.P + b0, Oym);
+    load_words<NW>(odd + ((int64_t)zp * g.L + y) * g.P + b0, Ozp);
+    load_words<NW>(odd + ((int64_t)zm * g.L + y) * g.P + b0, Ozm);
+    load_words<NW>(bonds + off, B);
+    load_words<NW>(sp + off, S);
+    load_words<NW>(dm + off, D0);
+    load_words<NW>(dm + g.half + off, D1);
+    uint32_t edge = 0, first = 0, last = 0;
+    if constexpr (FULL) {
+        const int8_t *ep = o == 0 ? (b0 == 0 ? odd + row0 + g.Lh - 1 : odd + off - 1)
+                                  : (b0 + 4 * NW < g.Lh ? odd + off + 4 * NW : odd + row0);
+        edge = last = (uint8_t)*ep;
+    } else if (o == 0) {
+        if (b0 == 0) last = (uint8_t)odd[row0 + g.Lh - 1];
+        else edge = (uint8_t)odd[off - 1];
+    } else {
+        if (b0 + 4 * NW <= g.Lh - 1) edge = (uint8_t)odd[off + 4 * NW];
+        else first = (b0 == 0) ? (O[0] & 0xFFu) : (uint8_t)odd[row0];
+    }
+    uint32_t xp[NW], xm[NW];
+    x_neighbours<NW, !FULL>(O, o, b0, g.Lh, edge, first, last, xp, xm);
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+        const uint32_t valid = FULL ? 0xFFFFFFFFu : valid_mask(b0, j, g.Lh);
+        const uint32_t u32 =
+            unsatisfied32(negative_terms(bond_planes(B[j]), xp[j], xm[j], Oyp[j], Oym[j], Ozp[j], Ozm[j]), S[j]) & valid;
+        e += 2 * (int)(((u32 >> 5) * 0x01010101u) >> 24) - 6 * (__popc(valid) / 8);
+        a += 4 * (int)((((D0[j] & valid) * 0x01010101u) >> 24) + (((D1[j] & valid) * 0x01010101u) >> 24));
+    }
+}
+
+// Energy and daemon sums of every (live, advancing) streaming job replica after
+// the tick, over the virtual-block table of the half-sweeps: per warp one
+// atomic into the (slot, replica) accumulators.
+__global__ void __launch_bounds__(kVBlock) pool_energy_kernel(PoolTables T) {
     pool_wait();
     pool_release();
-    const int slot = blockIdx.x, r = blockIdx.y;
+    const int nvb = *T.n_vblocks;
+    for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+        const VBlock b = T.vblocks[vb];
+        const JobDesc &J = T.jobs[b.slot];
+        if (!J.live || J.t >= J.n_sweeps) continue;
+        const Geometry g = J.geo;
+        const uint32_t chunks = (uint32_t)g.L * g.L * (g.W / J.nw);
+        const uint32_t chunk = (uint32_t)b.chunk0 + threadIdx.x;
+        int e = 0, a = 0;
+        if (chunk < chunks) {
+            const FastDiv dc{(uint32_t)(g.W / J.nw), J.divC_m, J.divC_l};
+            const FastDiv divL{(uint32_t)g.L, J.divL_m, J.divL_l};
+            const uint32_t row = fdiv(chunk, dc);
+            const int c = (int)(chunk - row * dc.d);
+            const int8_t *sp = J.spins + (int64_t)b.replica * 2 * g.half;
+            const uint8_t *dm = J.daemons + (int64_t)b.replica * 2 * g.half;
+            const bool full = g.P == g.Lh;
+            if (J.nw == 4) full ? chunk_measure<4, true>(g, sp, dm, J.bonds, (int)row, c, divL, e, a)
+                              : chunk_measure<4, false>(g, sp, dm, J.bonds, (int)row, c, divL, e, a);
+            else if (J.nw == 2) full ? chunk_measure<2, true>(g, sp, dm, J.bonds, (int)row, c, divL, e, a)
+                                     : chunk_measure<2, false>(g, sp, dm, J.bonds, (int)row, c, divL, e, a);
+            else full ? chunk_measure<1, true>(g, sp, dm, J.bonds, (int)row, c, divL, e, a)
+                      : chunk_measure<1, false>(g, sp, dm, J.bonds, (int)row, c, divL, e, a);
+        }
+        e = __reduce_add_sync(0xFFFFFFFFu, e);
+        a = __reduce_add_sync(0xFFFFFFFFu, a);
+        if ((threadIdx.x & 31) == 0) {
+            unsigned long long *acc = T.acc + ((size_t)b.slot * kPoolMaxR + b.replica) * 2;
+            atomicAdd(acc, (unsigned long long)(long long)e);
+            atomicAdd(acc + 1, (unsigned long long)(long long)a);
+        }
+    }
+}
+
+// Results of the tick per (slot, replica): energy, daemon energy, and whether
+// the energy is the lowest so far (then also the sweep count); the accumulators
+// are cleared for the next tick. One block of 32 threads per slot.
+__global__ void pool_best_kernel(PoolTables T, int K) {
+    pool_wait();
+    pool_release();
+    const int slot = blockIdx.x, r = threadIdx.x;
+    if (r >= kPoolMaxR) return;
     const JobDesc &J = T.jobs[slot];
+    const int cell = slot * kPoolMaxR + r;
+    T.improved[cell] = 0;
     if (!J.live || J.resident || r >= J.R || J.t >= J.n_sweeps) return;
-    const Geometry g = J.geo;
-    const int8_t *even = J.spins + (int64_t)r * 2 * g.half;
-    const int8_t *odd = even + g.half;
-    const uint8_t *d0 = J.daemons + (int64_t)r * 2 * g.half;
-    const int64_t words = (int64_t)g.L * g.L * g.W;
-    long long e_sum = 0, a_sum = 0;
-    for (int64_t w = threadIdx.x; w < words; w += blockDim.x) {
-        const int row = (int)(w / g.W);
-        const int b0 = (int)(w - (int64_t)row * g.W) * 4;
-        const int y = row % g.L, z = row / g.L;
-        const int o = (y + z) & 1;
-        const int yp = (y + 1 == g.L) ? 0 : y + 1, ym = (y == 0) ? g.L - 1 : y - 1;
-        const int zp = (z + 1 == g.L) ? 0 : z + 1, zm = (z == 0) ? g.L - 1 : z - 1;
-        const int64_t row0 = (int64_t)row * g.P, off = row0 + b0;
-        const uint32_t valid = valid_mask(b0, 0, g.Lh);
-        uint32_t O[1] = {*reinterpret_cast<const uint32_t *>(odd + off)};
-        uint32_t edge = 0, first = 0, last = 0;
-        if (o == 0) {
-            if (b0 == 0) last = (uint8_t)odd[row0 + g.Lh - 1];
-            else edge = (uint8_t)odd[off - 1];
-        } else {
-            if (b0 + 4 <= g.Lh - 1) edge = (uint8_t)odd[off + 4];
-            else first = (b0 == 0) ? (O[0] & 0xFFu) : (uint8_t)odd[row0];
-        }
-        uint32_t xp[1], xm[1];
-        x_neighbours<1>(O, o, b0, g.Lh, edge, first, last, xp, xm);
-        const BondPlanes bp = bond_planes(*reinterpret_cast<const uint32_t *>(J.bonds + off));
-        const uint32_t neg = negative_terms(
-            bp, xp[0], xm[0], *reinterpret_cast<const uint32_t *>(odd + ((int64_t)z * g.L + yp) * g.P + b0),
-            *reinterpret_cast<const uint32_t *>(odd + ((int64_t)z * g.L + ym) * g.P + b0),
-            *reinterpret_cast<const uint32_t *>(odd + ((int64_t)zp * g.L + y) * g.P + b0),
-            *reinterpret_cast<const uint32_t *>(odd + ((int64_t)zm * g.L + y) * g.P + b0));
-        const uint32_t u32 = unsatisfied32(neg, *reinterpret_cast<const uint32_t *>(even + off)) & valid;
-        e_sum += 2 * (int)((((u32 >> 5) * 0x01010101u) >> 24)) - 6 * (__popc(valid) / 8);
-        const uint32_t D0 = *reinterpret_cast<const uint32_t *>(d0 + off) & valid;
-        const uint32_t D1 = *reinterpret_cast<const uint32_t *>(d0 + g.half + off) & valid;
-        a_sum += 4 * (long long)(((D0 * 0x01010101u) >> 24) + ((D1 * 0x01010101u) >> 24));
+    const long long e = (long long)T.acc[2 * cell], a = (long long)T.acc[2 * cell + 1];
+    T.acc[2 * cell] = 0;
+    T.acc[2 * cell + 1] = 0;
+    T.energy[cell] = e;
+    T.aux[cell] = a;
+    if (e < T.best_energy[cell]) {
+        T.best_energy[cell] = e;
+        T.best_t[cell] = J.t + K < J.n_sweeps ? J.t + K : J.n_sweeps;
+        T.improved[cell] = 1;
     }
-    __shared__ long long red[2][8];
-    __shared__ int improved;
-    e_sum = __reduce_add_sync(0xFFFFFFFFu, (int)e_sum);
-    a_sum = __reduce_add_sync(0xFFFFFFFFu, (int)a_sum);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (lane == 0) {
-        red[0][warp] = e_sum;
-        red[1][warp] = a_sum;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        long long e = 0, a = 0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
-            e += red[0][i];
-            a += red[1][i];
-        }
-        const int64_t t_after = J.t + K < J.n_sweeps ? J.t + K : J.n_sweeps;
-        T.energy[slot * kPoolMaxR + r] = e;
-        T.aux[slot * kPoolMaxR + r] = a;
-        improved = e < T.best_energy[slot * kPoolMaxR + r];
-        if (improved) {
-            T.best_energy[slot * kPoolMaxR + r] = e;
-            T.best_t[slot * kPoolMaxR + r] = t_after;
-        }
-    }
-    __syncthreads();
-    if (!improved) return;
-    // copy the configuration to the natural-layout best buffer
-    const int64_t N = (int64_t)g.L * g.L * g.L;
-    int8_t *best = J.best + (int64_t)r * N;
-    for (int64_t site = threadIdx.x; site < N; site += blockDim.x) {
-        const int x = (int)(site % g.L), y = (int)((site / g.L) % g.L), z = (int)(site / ((int64_t)g.L * g.L));
-        const int par = (x + y + z) & 1;
-        best[site] = even[(int64_t)par * g.half + ((int64_t)z * g.L + y) * g.P + (x >> 1)];
+}
+
+// Copy of the configurations whose energy improved, in the split layout (the
+// natural layout is produced when the job is polled), over the virtual blocks.
+__global__ void __launch_bounds__(kVBlock) pool_best_copy_kernel(PoolTables T) {
+    pool_wait();
+    pool_release();
+    const int nvb = *T.n_vblocks;
+    for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+        const VBlock b = T.vblocks[vb];
+        if (!T.improved[b.slot * kPoolMaxR + b.replica]) continue;
+        const JobDesc &J = T.jobs[b.slot];
+        const Geometry g = J.geo;
+        const uint32_t chunks = (uint32_t)g.L * g.L * (g.W / J.nw);
+        const uint32_t chunk = (uint32_t)b.chunk0 + threadIdx.x;
+        if (chunk >= chunks) continue;
+        const int64_t off = (int64_t)chunk * 4 * J.nw;  // chunks tile the rows contiguously
+        const int8_t *src = J.spins + (int64_t)b.replica * 2 * g.half;
+        int8_t *dst = J.best + (int64_t)b.replica * 2 * g.half;
+        for (int par = 0; par < 2; ++par)
+            for (int w = 0; w < J.nw; ++w)
+                *reinterpret_cast<uint32_t *>(dst + par * g.half + off + 4 * w) =
+                    *reinterpret_cast<const uint32_t *>(src + par * g.half + off + 4 * w);
     }
 }
 
@@ -226,6 +281,8 @@ struct micsa_pool {
     int32_t *d_nvb = nullptr, *h_nvb = nullptr;
     int max_vblocks = 0;
     long long *d_results = nullptr;  // energy | aux | best_energy | best_t, [max_jobs][kPoolMaxR] each
+    unsigned long long *d_acc = nullptr;  // per-tick energy / daemon sums of the streaming jobs
+    int32_t *d_improved = nullptr;        // per (slot, replica): the last tick improved the best energy
     std::vector<PoolJob> slots;
     int64_t next_id = 1;
     int64_t ticks_queued = 0;
@@ -339,7 +396,8 @@ JobSizes job_sizes(const micsa_job_desc &d) {
     s.nw = s.g.W % 4 == 0 ? 4 : s.g.W % 2 == 0 ? 2 : 1;
     s.bonds = (size_t)2 * s.g.half;
     s.state = (size_t)d.n_replicas * 2 * s.g.half;
-    s.best = (size_t)d.n_replicas * d.L * d.L * d.L;
+    // natural layout (shared-memory jobs) or the split layout (streaming jobs)
+    s.best = (size_t)d.n_replicas * std::max<size_t>((size_t)d.L * d.L * d.L, (size_t)2 * s.g.half);
     s.n_refresh = (d.n_sweeps + d.refresh_interval - 1) / d.refresh_interval;
     if (s.n_refresh < 1) s.n_refresh = 1;
     s.thr = sizeof(uint64_t) * 3 * (size_t)s.n_refresh;
@@ -400,7 +458,8 @@ int upload_tables(micsa_pool_t p) {
 int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
     long long *R0 = p->d_results;
     const size_t rows = (size_t)p->max_jobs * kPoolMaxR;
-    PoolTables T{p->d_jobs, p->d_vblocks, p->d_nvb, R0, R0 + rows, R0 + 2 * rows, R0 + 3 * rows};
+    PoolTables T{p->d_jobs, p->d_vblocks, p->d_nvb, R0, R0 + rows, R0 + 2 * rows, R0 + 3 * rows, p->d_acc,
+                 p->d_improved};
     // both parts present: the resident kernel runs on a forked branch, concurrently
     // with the streaming half-sweeps (they touch disjoint jobs), joined before
     // the measure and advance nodes
@@ -429,8 +488,11 @@ int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
                 PCK(p, launch_pdl((const void *)pool_half_sweep_kernel, dim3(p->grid_blocks), dim3(kVBlock), st, args, p->pdl), "pool half-sweep launch");
             }
         int K = p->K;
-        void *margs[] = {&T, &K};
-        PCK(p, launch_pdl((const void *)pool_measure_kernel, dim3(p->max_jobs, kPoolMaxR), dim3(256), st, margs, p->pdl), "pool measure launch");
+        void *eargs[] = {&T};
+        void *bargs[] = {&T, &K};
+        PCK(p, launch_pdl((const void *)pool_energy_kernel, dim3(p->grid_blocks), dim3(kVBlock), st, eargs, p->pdl), "pool energy launch");
+        PCK(p, launch_pdl((const void *)pool_best_kernel, dim3(p->max_jobs), dim3(32), st, bargs, p->pdl), "pool best launch");
+        PCK(p, launch_pdl((const void *)pool_best_copy_kernel, dim3(p->grid_blocks), dim3(kVBlock), st, eargs, p->pdl), "pool best copy launch");
     }
     if (fork) {
         PCK(p, cudaEventRecord(p->join_ev, p->aux_stream), "join event");
@@ -443,7 +505,7 @@ int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
 }
 
 int tick_launches(micsa_pool_t p, int mask) {
-    return ((mask & 1) && p->resident_smem ? 1 : 0) + ((mask & 2) ? 2 * p->K + 1 : 0) + 1;
+    return ((mask & 1) && p->resident_smem ? 1 : 0) + ((mask & 2) ? 2 * p->K + 3 : 0) + 1;
 }
 
 int ensure_graph(micsa_pool_t p, int mask) {
@@ -514,7 +576,11 @@ int micsa_pool_create(size_t arena_bytes, int max_jobs, int tick_sweeps, micsa_p
         if ((e = cudaMalloc(&p->d_jobs, sizeof(JobDesc) * max_jobs)) != cudaSuccess ||
             (e = cudaMalloc(&p->d_vblocks, sizeof(VBlock) * (size_t)p->max_vblocks)) != cudaSuccess ||
             (e = cudaMalloc(&p->d_nvb, sizeof(int32_t))) != cudaSuccess ||
-            (e = cudaMalloc(&p->d_results, sizeof(long long) * 4 * (size_t)max_jobs * kPoolMaxR)) != cudaSuccess) { bail(MICSA_E_OOM); break; }
+            (e = cudaMalloc(&p->d_results, sizeof(long long) * 4 * (size_t)max_jobs * kPoolMaxR)) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_acc, sizeof(unsigned long long) * 2 * (size_t)max_jobs * kPoolMaxR)) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_improved, sizeof(int32_t) * (size_t)max_jobs * kPoolMaxR)) != cudaSuccess) { bail(MICSA_E_OOM); break; }
+        if ((e = cudaMemsetAsync(p->d_acc, 0, sizeof(unsigned long long) * 2 * (size_t)max_jobs * kPoolMaxR, p->stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(p->d_improved, 0, sizeof(int32_t) * (size_t)max_jobs * kPoolMaxR, p->stream)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         if ((e = cudaMallocHost(&p->h_jobs_stage, sizeof(JobDesc) * max_jobs)) != cudaSuccess ||
             (e = cudaMallocHost(&p->h_vblocks, sizeof(VBlock) * (size_t)p->max_vblocks)) != cudaSuccess ||
             (e = cudaMallocHost(&p->h_nvb, sizeof(int32_t))) != cudaSuccess) { bail(MICSA_E_OOM); break; }
@@ -571,6 +637,8 @@ void micsa_pool_destroy(micsa_pool_t p) {
     cudaFree(p->d_vblocks);
     cudaFree(p->d_nvb);
     cudaFree(p->d_results);
+    cudaFree(p->d_acc);
+    cudaFree(p->d_improved);
     cudaFreeHost(p->h_jobs_stage);
     cudaFree(p->d_units);
     cudaFree(p->d_nunits);
@@ -753,8 +821,23 @@ int micsa_pool_poll(micsa_pool_t p, int64_t job_id, micsa_job_result *res, int8_
         PCK(p, cudaMemcpy(vals[q], p->d_results + (size_t)q * p->max_jobs * kPoolMaxR + (size_t)slot * kPoolMaxR,
                           sizeof(long long) * kPoolMaxR, cudaMemcpyDeviceToHost), "copy results");
     if (best_spins) {
-        const size_t n = (size_t)R * J.desc.L * J.desc.L * J.desc.L;
-        PCK(p, cudaMemcpy(best_spins, p->arena + J.off_best, n, cudaMemcpyDeviceToHost), "copy best spins");
+        const int L = J.desc.L;
+        const size_t N = (size_t)L * L * L;
+        if (p->h_jobs[slot].resident) {  // kept in natural layout by the shared-memory kernel
+            PCK(p, cudaMemcpy(best_spins, p->arena + J.off_best, (size_t)R * N, cudaMemcpyDeviceToHost), "copy best spins");
+        } else {  // split layout: [R][parity][z][y][P bytes], byte i of row (z, y) is x = 2i + ((p + y + z) & 1)
+            const Geometry g = p->h_jobs[slot].geo;
+            std::vector<int8_t> split((size_t)R * 2 * g.half);
+            PCK(p, cudaMemcpy(split.data(), p->arena + J.off_best, split.size(), cudaMemcpyDeviceToHost), "copy best spins");
+            for (int r = 0; r < R; ++r)
+                for (int par = 0; par < 2; ++par)
+                    for (int z = 0; z < L; ++z)
+                        for (int y = 0; y < L; ++y) {
+                            const int8_t *row = split.data() + ((size_t)r * 2 + par) * g.half + ((size_t)z * L + y) * g.P;
+                            int8_t *out = best_spins + (size_t)r * N + ((size_t)z * L + y) * L + ((par + y + z) & 1);
+                            for (int i = 0; i < g.Lh; ++i) out[2 * i] = row[i];
+                        }
+        }
     }
     if (res) {
         std::memset(res, 0, sizeof(*res));
