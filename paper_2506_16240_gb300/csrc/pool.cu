@@ -77,7 +77,11 @@ __global__ void __launch_bounds__(kVBlock) pool_half_sweep_kernel(PoolTables T, 
     pool_wait();
     pool_release();
     const int nvb = *T.n_vblocks;
-    for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+    // a contiguous run of virtual blocks per CTA: mostly one job (its descriptor
+    // stays in L1) and neighbouring planes (their rows are re-read from L1)
+    const int per = (nvb + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int vb_end = min(nvb, ((int)blockIdx.x + 1) * per);
+    for (int vb = (int)blockIdx.x * per; vb < vb_end; ++vb) {
         const VBlock b = T.vblocks[vb];
         const JobDesc &J = T.jobs[b.slot];
         const int64_t t = J.t + k;
@@ -148,7 +152,11 @@ __global__ void __launch_bounds__(kVBlock) pool_energy_kernel(PoolTables T) {
     pool_wait();
     pool_release();
     const int nvb = *T.n_vblocks;
-    for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+    // a contiguous run of virtual blocks per CTA: mostly one job (its descriptor
+    // stays in L1) and neighbouring planes (their rows are re-read from L1)
+    const int per = (nvb + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int vb_end = min(nvb, ((int)blockIdx.x + 1) * per);
+    for (int vb = (int)blockIdx.x * per; vb < vb_end; ++vb) {
         const VBlock b = T.vblocks[vb];
         const JobDesc &J = T.jobs[b.slot];
         if (!J.live || J.t >= J.n_sweeps) continue;
@@ -211,7 +219,11 @@ __global__ void __launch_bounds__(kVBlock) pool_best_copy_kernel(PoolTables T) {
     pool_wait();
     pool_release();
     const int nvb = *T.n_vblocks;
-    for (int vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+    // a contiguous run of virtual blocks per CTA: mostly one job (its descriptor
+    // stays in L1) and neighbouring planes (their rows are re-read from L1)
+    const int per = (nvb + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int vb_end = min(nvb, ((int)blockIdx.x + 1) * per);
+    for (int vb = (int)blockIdx.x * per; vb < vb_end; ++vb) {
         const VBlock b = T.vblocks[vb];
         if (!T.improved[b.slot * kPoolMaxR + b.replica]) continue;
         const JobDesc &J = T.jobs[b.slot];
