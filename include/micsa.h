@@ -190,11 +190,15 @@ int micsa_set_launch_config(micsa_t h, int words_per_thread, int block, int bloc
  *                          bit planes in HBM (32 z per word) for L a multiple
  *                          of 32: each micsa_run converts the byte state to
  *                          planes, runs one launch per half-sweep on them
- *                          (graphs, PDL) and converts back. Needs gamma = 1
- *                          and no walkers; extra device memory: 0.375 bytes
- *                          per spin per replica and 0.75 per spin per sample.
+ *                          (graphs, PDL) and converts back. gamma daemon
+ *                          families and walkers included (the wandering step
+ *                          is applied as the next timestep reads its daemons,
+ *                          between two daemon buffers). Extra device memory
+ *                          per spin: (2 + 4 gamma) / 16 bytes per replica,
+ *                          (2 + 8 gamma) / 16 with walkers, 0.75 per sample.
  * An engine whose size limit the lattice exceeds is rejected. Runs with gamma
- * > 1 or walkers, and Metropolis runs, always use the streaming kernel.
+ * > 1 or walkers on any engine but MULTISPIN_GLOBAL, and Metropolis runs, use
+ * the streaming kernel.
  * resident_sweeps only matters to RESIDENT, MULTISPIN and ONCHIP. Synchronizes.
  * (App. B and Sec. 2.5 describe the multispin Boolean update.) */
 #define MICSA_ENGINE_AUTO 0
@@ -206,7 +210,7 @@ int micsa_set_launch_config(micsa_t h, int words_per_thread, int block, int bloc
 #define MICSA_ENGINE_TMA 6
 int micsa_set_engine(micsa_t h, int engine, int resident_sweeps);
 
-/* Graph replays of the STREAM and MULTISPIN_GLOBAL engines split the replicas
+/* Graph replays of the STREAM, TMA and MULTISPIN_GLOBAL engines split the replicas
  * into `chains` groups (1..4, at most n_replicas; default 1) whose half-sweeps
  * are captured as concurrent kernel chains joined at the end of each graph:
  * the groups touch disjoint replicas, so one chain's launch gaps overlap the

@@ -1,6 +1,8 @@
-// multispin.cu -- shared-memory resident MicSA with multispin coding (the
-// Boolean-only update the paper describes for its CUDA code, App. B and
-// Sec. 2.5), for lattices with L <= 32.
+// multispin.cu -- MicSA with multispin coding (the Boolean-only update the
+// paper describes for its CUDA code, App. B and Sec. 2.5) in two forms: the
+// shared-memory resident kernel for lattices with L <= 32 (first part of this
+// file) and the bit planes in HBM for L a multiple of 32, with gamma daemon
+// families and walkers (second part).
 //
 // A CTA converts one replica from the global byte layout into bit planes in
 // shared memory, runs a block of sweeps there, and converts back. Bit plane
