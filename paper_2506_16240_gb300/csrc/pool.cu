@@ -41,7 +41,7 @@ struct VBlock {
 struct PoolTables {
     JobDesc *jobs;          // [max_jobs]
     const VBlock *vblocks;  // [max_vblocks]
-    const int32_t *n_vblocks;
+    const int32_t *n_vblocks;  // [2]: the end of the first chain's part, the total
     long long *energy;      // [max_jobs][kPoolMaxR]
     long long *aux;
     long long *best_energy;
@@ -72,16 +72,19 @@ __device__ __forceinline__ void pool_item(const JobDesc &J, int r, uint32_t chun
                             J.key0, J.key1, t, refresh, th0, th1, th2, divL);
 }
 
-// One half-sweep (parity p) of sweep k of the tick for every live job.
-__global__ void __launch_bounds__(kVBlock) pool_half_sweep_kernel(PoolTables T, int k, int p) {
+// One half-sweep (parity p) of sweep k of the tick for every live job of part
+// `part` of the virtual-block table (the two parts hold disjoint (job,
+// replica) pairs and run as two concurrent kernel chains).
+__global__ void __launch_bounds__(kVBlock) pool_half_sweep_kernel(PoolTables T, int k, int p, int part) {
     pool_wait();
     pool_release();
-    const int nvb = *T.n_vblocks;
+    const int v0 = part == 0 ? 0 : T.n_vblocks[0];
+    const int nvb = (part == 0 ? T.n_vblocks[0] : T.n_vblocks[1]) - v0;
     // a contiguous run of virtual blocks per CTA: mostly one job (its descriptor
     // stays in L1) and neighbouring planes (their rows are re-read from L1)
     const int per = (nvb + (int)gridDim.x - 1) / (int)gridDim.x;
-    const int vb_end = min(nvb, ((int)blockIdx.x + 1) * per);
-    for (int vb = (int)blockIdx.x * per; vb < vb_end; ++vb) {
+    const int vb_end = v0 + min(nvb, ((int)blockIdx.x + 1) * per);
+    for (int vb = v0 + (int)blockIdx.x * per; vb < vb_end; ++vb) {
         const VBlock b = T.vblocks[vb];
         const JobDesc &J = T.jobs[b.slot];
         const int64_t t = J.t + k;
@@ -151,7 +154,7 @@ __device__ __forceinline__ void chunk_measure(const Geometry &g, const int8_t *s
 __global__ void __launch_bounds__(kVBlock) pool_energy_kernel(PoolTables T) {
     pool_wait();
     pool_release();
-    const int nvb = *T.n_vblocks;
+    const int nvb = T.n_vblocks[1];
     // a contiguous run of virtual blocks per CTA: mostly one job (its descriptor
     // stays in L1) and neighbouring planes (their rows are re-read from L1)
     const int per = (nvb + (int)gridDim.x - 1) / (int)gridDim.x;
@@ -218,7 +221,7 @@ __global__ void pool_best_kernel(PoolTables T, int K) {
 __global__ void __launch_bounds__(kVBlock) pool_best_copy_kernel(PoolTables T) {
     pool_wait();
     pool_release();
-    const int nvb = *T.n_vblocks;
+    const int nvb = T.n_vblocks[1];
     // a contiguous run of virtual blocks per CTA: mostly one job (its descriptor
     // stays in L1) and neighbouring planes (their rows are re-read from L1)
     const int per = (nvb + (int)gridDim.x - 1) / (int)gridDim.x;
@@ -304,6 +307,8 @@ struct micsa_pool {
     cudaStream_t capture_stream = nullptr;
     cudaStream_t aux_stream = nullptr;       // forked branch of a tick (resident kernel)
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+    cudaStream_t chain_stream = nullptr;     // forked branch: the second part of the streaming jobs
+    cudaEvent_t chain_fork = nullptr, chain_join = nullptr;
     bool tables_dirty = true;
     cudaEvent_t tables_free = nullptr;  // the last table upload has been consumed
     // per slot: pinned staging of the job's initial data (cut points + result
@@ -446,14 +451,25 @@ int upload_tables(micsa_pool_t p) {
                 p->h_vblocks[nvb++] = VBlock{i, (int16_t)r, 0, (int32_t)c};
             }
     }
-    *p->h_nvb = nvb;
+    // the two chains' parts: split at the (job, replica) boundary nearest the middle
+    int split = 0, best_gap = nvb + 1;
+    for (int v = 0; v <= nvb; ++v) {
+        const bool boundary = v == 0 || v == nvb || p->h_vblocks[v].slot != p->h_vblocks[v - 1].slot ||
+                              p->h_vblocks[v].replica != p->h_vblocks[v - 1].replica;
+        if (boundary && std::abs(2 * v - nvb) < best_gap) {
+            best_gap = std::abs(2 * v - nvb);
+            split = v;
+        }
+    }
+    p->h_nvb[0] = split;
+    p->h_nvb[1] = nvb;
     *p->h_nunits = nunits;
     p->has_stream_jobs = nvb > 0;
     p->has_resident_jobs = nunits > 0;
     std::memcpy(p->h_jobs_stage, p->h_jobs.data(), sizeof(JobDesc) * p->max_jobs);
     PCK(p, cudaMemcpyAsync(p->d_jobs, p->h_jobs_stage, sizeof(JobDesc) * p->max_jobs, cudaMemcpyHostToDevice, p->stream), "upload jobs");
     PCK(p, cudaMemcpyAsync(p->d_vblocks, p->h_vblocks, sizeof(VBlock) * (size_t)(nvb ? nvb : 1), cudaMemcpyHostToDevice, p->stream), "upload vblocks");
-    PCK(p, cudaMemcpyAsync(p->d_nvb, p->h_nvb, sizeof(int32_t), cudaMemcpyHostToDevice, p->stream), "upload vblock count");
+    PCK(p, cudaMemcpyAsync(p->d_nvb, p->h_nvb, 2 * sizeof(int32_t), cudaMemcpyHostToDevice, p->stream), "upload vblock counts");
     if (p->max_units) {
         PCK(p, cudaMemcpyAsync(p->d_units, p->h_units, sizeof(ResidentUnit) * (size_t)(nunits ? nunits : 1), cudaMemcpyHostToDevice, p->stream), "upload units");
         PCK(p, cudaMemcpyAsync(p->d_nunits, p->h_nunits, sizeof(int32_t), cudaMemcpyHostToDevice, p->stream), "upload unit count");
@@ -494,11 +510,22 @@ int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
         PCK(p, launch_multispin(ra, true, p->resident_smem, p->resident_grid, p->pdl && !fork, rs), "pool multispin launch");
     }
     if (mask & 2) {
-        for (int k = 0; k < p->K; ++k)
-            for (int par = 0; par < 2; ++par) {
-                void *args[] = {&T, &k, &par};
-                PCK(p, launch_pdl((const void *)pool_half_sweep_kernel, dim3(p->grid_blocks), dim3(kVBlock), st, args, p->pdl), "pool half-sweep launch");
-            }
+        // the two parts of the streaming jobs as two concurrent chains, joined
+        // before the measurement
+        PCK(p, cudaEventRecord(p->chain_fork, st), "chain fork event");
+        PCK(p, cudaStreamWaitEvent(p->chain_stream, p->chain_fork, 0), "chain fork wait");
+        for (int part = 0; part < 2; ++part) {
+            cudaStream_t cs = part == 0 ? st : p->chain_stream;
+            for (int k = 0; k < p->K; ++k)
+                for (int par = 0; par < 2; ++par) {
+                    void *args[] = {&T, &k, &par, &part};
+                    PCK(p, launch_pdl((const void *)pool_half_sweep_kernel, dim3(p->grid_blocks), dim3(kVBlock), cs, args,
+                                      p->pdl && (part == 0 || k + par > 0)),
+                        "pool half-sweep launch");
+                }
+        }
+        PCK(p, cudaEventRecord(p->chain_join, p->chain_stream), "chain join event");
+        PCK(p, cudaStreamWaitEvent(st, p->chain_join, 0), "chain join wait");
         int K = p->K;
         void *eargs[] = {&T};
         void *bargs[] = {&T, &K};
@@ -517,7 +544,7 @@ int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
 }
 
 int tick_launches(micsa_pool_t p, int mask) {
-    return ((mask & 1) && p->resident_smem ? 1 : 0) + ((mask & 2) ? 2 * p->K + 3 : 0) + 1;
+    return ((mask & 1) && p->resident_smem ? 1 : 0) + ((mask & 2) ? 4 * p->K + 3 : 0) + 1;
 }
 
 int ensure_graph(micsa_pool_t p, int mask) {
@@ -578,7 +605,10 @@ int micsa_pool_create(size_t arena_bytes, int max_jobs, int tick_sweeps, micsa_p
         if ((e = cudaDeviceGetAttribute(&p->sm_count, cudaDevAttrMultiProcessorCount, p->device)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         if ((e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         if ((e = cudaStreamCreateWithFlags(&p->capture_stream, cudaStreamNonBlocking)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
-        if ((e = cudaStreamCreateWithFlags(&p->aux_stream, cudaStreamNonBlocking)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+        if ((e = cudaStreamCreateWithFlags(&p->aux_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaStreamCreateWithFlags(&p->chain_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&p->chain_fork, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&p->chain_join, cudaEventDisableTiming)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         if ((e = cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&p->join_ev, cudaEventDisableTiming)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         if ((e = cudaEventCreateWithFlags(&p->tables_free, cudaEventDisableTiming)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
@@ -587,7 +617,7 @@ int micsa_pool_create(size_t arena_bytes, int max_jobs, int tick_sweeps, micsa_p
         p->max_vblocks = 1 << 22;
         if ((e = cudaMalloc(&p->d_jobs, sizeof(JobDesc) * max_jobs)) != cudaSuccess ||
             (e = cudaMalloc(&p->d_vblocks, sizeof(VBlock) * (size_t)p->max_vblocks)) != cudaSuccess ||
-            (e = cudaMalloc(&p->d_nvb, sizeof(int32_t))) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_nvb, 2 * sizeof(int32_t))) != cudaSuccess ||
             (e = cudaMalloc(&p->d_results, sizeof(long long) * 4 * (size_t)max_jobs * kPoolMaxR)) != cudaSuccess ||
             (e = cudaMalloc(&p->d_acc, sizeof(unsigned long long) * 2 * (size_t)max_jobs * kPoolMaxR)) != cudaSuccess ||
             (e = cudaMalloc(&p->d_improved, sizeof(int32_t) * (size_t)max_jobs * kPoolMaxR)) != cudaSuccess) { bail(MICSA_E_OOM); break; }
@@ -595,13 +625,13 @@ int micsa_pool_create(size_t arena_bytes, int max_jobs, int tick_sweeps, micsa_p
             (e = cudaMemsetAsync(p->d_improved, 0, sizeof(int32_t) * (size_t)max_jobs * kPoolMaxR, p->stream)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         if ((e = cudaMallocHost(&p->h_jobs_stage, sizeof(JobDesc) * max_jobs)) != cudaSuccess ||
             (e = cudaMallocHost(&p->h_vblocks, sizeof(VBlock) * (size_t)p->max_vblocks)) != cudaSuccess ||
-            (e = cudaMallocHost(&p->h_nvb, sizeof(int32_t))) != cudaSuccess) { bail(MICSA_E_OOM); break; }
-        *p->h_nvb = 0;
+            (e = cudaMallocHost(&p->h_nvb, 2 * sizeof(int32_t))) != cudaSuccess) { bail(MICSA_E_OOM); break; }
+        p->h_nvb[0] = p->h_nvb[1] = 0;
         for (auto &ev : p->stage_free)
             if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         if (rc) break;
         if ((e = cudaMemsetAsync(p->d_jobs, 0, sizeof(JobDesc) * max_jobs, p->stream)) != cudaSuccess ||
-            (e = cudaMemsetAsync(p->d_nvb, 0, sizeof(int32_t), p->stream)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+            (e = cudaMemsetAsync(p->d_nvb, 0, 2 * sizeof(int32_t), p->stream)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         // jobs of L <= 32 live in shared memory as bit planes (multispin kernel)
         p->resident_smem = multispin_smem_bytes(make_geometry(32));
         const int res_per_sm = multispin_blocks_per_sm(true, p->resident_smem);
@@ -666,6 +696,12 @@ void micsa_pool_destroy(micsa_pool_t p) {
     }
     if (p->fork_ev) cudaEventDestroy(p->fork_ev);
     if (p->join_ev) cudaEventDestroy(p->join_ev);
+    if (p->chain_stream) {
+        cudaStreamSynchronize(p->chain_stream);
+        cudaStreamDestroy(p->chain_stream);
+    }
+    if (p->chain_fork) cudaEventDestroy(p->chain_fork);
+    if (p->chain_join) cudaEventDestroy(p->chain_join);
     if (p->stream) cudaStreamDestroy(p->stream);
     delete p;
 }
