@@ -28,6 +28,7 @@ namespace micsa {
 
 constexpr int kPoolMaxR = MICSA_POOL_MAX_REPLICAS;
 constexpr int kVBlock = 128;  // chunk items per virtual block
+constexpr int kPoolChains = 2;  // parts of the streaming jobs run as concurrent kernel chains (4 measured no faster)
 
 
 
@@ -41,7 +42,7 @@ struct VBlock {
 struct PoolTables {
     JobDesc *jobs;          // [max_jobs]
     const VBlock *vblocks;  // [max_vblocks]
-    const int32_t *n_vblocks;  // [2]: the end of the first chain's part, the total
+    const int32_t *n_vblocks;  // [kPoolChains]: the end of each chain's part (the last: the total)
     long long *energy;      // [max_jobs][kPoolMaxR]
     long long *aux;
     long long *best_energy;
@@ -73,13 +74,13 @@ __device__ __forceinline__ void pool_item(const JobDesc &J, int r, uint32_t chun
 }
 
 // One half-sweep (parity p) of sweep k of the tick for every live job of part
-// `part` of the virtual-block table (the two parts hold disjoint (job,
-// replica) pairs and run as two concurrent kernel chains).
+// `part` of the virtual-block table (the parts hold disjoint (job, replica)
+// pairs and run as concurrent kernel chains).
 __global__ void __launch_bounds__(kVBlock) pool_half_sweep_kernel(PoolTables T, int k, int p, int part) {
     pool_wait();
     pool_release();
-    const int v0 = part == 0 ? 0 : T.n_vblocks[0];
-    const int nvb = (part == 0 ? T.n_vblocks[0] : T.n_vblocks[1]) - v0;
+    const int v0 = part == 0 ? 0 : T.n_vblocks[part - 1];
+    const int nvb = T.n_vblocks[part] - v0;
     // a contiguous run of virtual blocks per CTA: mostly one job (its descriptor
     // stays in L1) and neighbouring planes (their rows are re-read from L1)
     const int per = (nvb + (int)gridDim.x - 1) / (int)gridDim.x;
@@ -154,7 +155,7 @@ __device__ __forceinline__ void chunk_measure(const Geometry &g, const int8_t *s
 __global__ void __launch_bounds__(kVBlock) pool_energy_kernel(PoolTables T) {
     pool_wait();
     pool_release();
-    const int nvb = T.n_vblocks[1];
+    const int nvb = T.n_vblocks[kPoolChains - 1];
     // a contiguous run of virtual blocks per CTA: mostly one job (its descriptor
     // stays in L1) and neighbouring planes (their rows are re-read from L1)
     const int per = (nvb + (int)gridDim.x - 1) / (int)gridDim.x;
@@ -221,7 +222,7 @@ __global__ void pool_best_kernel(PoolTables T, int K) {
 __global__ void __launch_bounds__(kVBlock) pool_best_copy_kernel(PoolTables T) {
     pool_wait();
     pool_release();
-    const int nvb = T.n_vblocks[1];
+    const int nvb = T.n_vblocks[kPoolChains - 1];
     // a contiguous run of virtual blocks per CTA: mostly one job (its descriptor
     // stays in L1) and neighbouring planes (their rows are re-read from L1)
     const int per = (nvb + (int)gridDim.x - 1) / (int)gridDim.x;
@@ -307,8 +308,8 @@ struct micsa_pool {
     cudaStream_t capture_stream = nullptr;
     cudaStream_t aux_stream = nullptr;       // forked branch of a tick (resident kernel)
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
-    cudaStream_t chain_stream = nullptr;     // forked branch: the second part of the streaming jobs
-    cudaEvent_t chain_fork = nullptr, chain_join = nullptr;
+    cudaStream_t chain_stream[kPoolChains] = {};  // forked branches: parts 1.. of the streaming jobs
+    cudaEvent_t chain_fork = nullptr, chain_join[kPoolChains] = {};
     bool tables_dirty = true;
     cudaEvent_t tables_free = nullptr;  // the last table upload has been consumed
     // per slot: pinned staging of the job's initial data (cut points + result
@@ -451,25 +452,32 @@ int upload_tables(micsa_pool_t p) {
                 p->h_vblocks[nvb++] = VBlock{i, (int16_t)r, 0, (int32_t)c};
             }
     }
-    // the two chains' parts: split at the (job, replica) boundary nearest the middle
-    int split = 0, best_gap = nvb + 1;
-    for (int v = 0; v <= nvb; ++v) {
-        const bool boundary = v == 0 || v == nvb || p->h_vblocks[v].slot != p->h_vblocks[v - 1].slot ||
-                              p->h_vblocks[v].replica != p->h_vblocks[v - 1].replica;
-        if (boundary && std::abs(2 * v - nvb) < best_gap) {
-            best_gap = std::abs(2 * v - nvb);
-            split = v;
+    // the chains' parts: ends at the (job, replica) boundaries nearest c * nvb / chains
+    std::vector<int> bounds;
+    for (int v = 0; v <= nvb; ++v)
+        if (v == 0 || v == nvb || p->h_vblocks[v].slot != p->h_vblocks[v - 1].slot ||
+            p->h_vblocks[v].replica != p->h_vblocks[v - 1].replica)
+            bounds.push_back(v);
+    int prev = 0;
+    for (int c = 0; c < kPoolChains; ++c) {
+        int end = nvb;
+        if (c + 1 < kPoolChains) {
+            const double target = (double)(c + 1) * nvb / kPoolChains;
+            int best = nvb;
+            for (int v : bounds)
+                if (v >= prev && std::fabs(v - target) < std::fabs(best - target)) best = v;
+            end = best;
         }
+        p->h_nvb[c] = end;
+        prev = end;
     }
-    p->h_nvb[0] = split;
-    p->h_nvb[1] = nvb;
     *p->h_nunits = nunits;
     p->has_stream_jobs = nvb > 0;
     p->has_resident_jobs = nunits > 0;
     std::memcpy(p->h_jobs_stage, p->h_jobs.data(), sizeof(JobDesc) * p->max_jobs);
     PCK(p, cudaMemcpyAsync(p->d_jobs, p->h_jobs_stage, sizeof(JobDesc) * p->max_jobs, cudaMemcpyHostToDevice, p->stream), "upload jobs");
     PCK(p, cudaMemcpyAsync(p->d_vblocks, p->h_vblocks, sizeof(VBlock) * (size_t)(nvb ? nvb : 1), cudaMemcpyHostToDevice, p->stream), "upload vblocks");
-    PCK(p, cudaMemcpyAsync(p->d_nvb, p->h_nvb, 2 * sizeof(int32_t), cudaMemcpyHostToDevice, p->stream), "upload vblock counts");
+    PCK(p, cudaMemcpyAsync(p->d_nvb, p->h_nvb, kPoolChains * sizeof(int32_t), cudaMemcpyHostToDevice, p->stream), "upload vblock counts");
     if (p->max_units) {
         PCK(p, cudaMemcpyAsync(p->d_units, p->h_units, sizeof(ResidentUnit) * (size_t)(nunits ? nunits : 1), cudaMemcpyHostToDevice, p->stream), "upload units");
         PCK(p, cudaMemcpyAsync(p->d_nunits, p->h_nunits, sizeof(int32_t), cudaMemcpyHostToDevice, p->stream), "upload unit count");
@@ -510,12 +518,13 @@ int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
         PCK(p, launch_multispin(ra, true, p->resident_smem, p->resident_grid, p->pdl && !fork, rs), "pool multispin launch");
     }
     if (mask & 2) {
-        // the two parts of the streaming jobs as two concurrent chains, joined
-        // before the measurement
+        // the parts of the streaming jobs as concurrent chains, joined before
+        // the measurement
         PCK(p, cudaEventRecord(p->chain_fork, st), "chain fork event");
-        PCK(p, cudaStreamWaitEvent(p->chain_stream, p->chain_fork, 0), "chain fork wait");
-        for (int part = 0; part < 2; ++part) {
-            cudaStream_t cs = part == 0 ? st : p->chain_stream;
+        for (int c = 1; c < kPoolChains; ++c)
+            PCK(p, cudaStreamWaitEvent(p->chain_stream[c], p->chain_fork, 0), "chain fork wait");
+        for (int part = 0; part < kPoolChains; ++part) {
+            cudaStream_t cs = part == 0 ? st : p->chain_stream[part];
             for (int k = 0; k < p->K; ++k)
                 for (int par = 0; par < 2; ++par) {
                     void *args[] = {&T, &k, &par, &part};
@@ -524,8 +533,10 @@ int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
                         "pool half-sweep launch");
                 }
         }
-        PCK(p, cudaEventRecord(p->chain_join, p->chain_stream), "chain join event");
-        PCK(p, cudaStreamWaitEvent(st, p->chain_join, 0), "chain join wait");
+        for (int c = 1; c < kPoolChains; ++c) {
+            PCK(p, cudaEventRecord(p->chain_join[c], p->chain_stream[c]), "chain join event");
+            PCK(p, cudaStreamWaitEvent(st, p->chain_join[c], 0), "chain join wait");
+        }
         int K = p->K;
         void *eargs[] = {&T};
         void *bargs[] = {&T, &K};
@@ -544,7 +555,7 @@ int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
 }
 
 int tick_launches(micsa_pool_t p, int mask) {
-    return ((mask & 1) && p->resident_smem ? 1 : 0) + ((mask & 2) ? 4 * p->K + 3 : 0) + 1;
+    return ((mask & 1) && p->resident_smem ? 1 : 0) + ((mask & 2) ? 2 * kPoolChains * p->K + 3 : 0) + 1;
 }
 
 int ensure_graph(micsa_pool_t p, int mask) {
@@ -606,9 +617,11 @@ int micsa_pool_create(size_t arena_bytes, int max_jobs, int tick_sweeps, micsa_p
         if ((e = cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         if ((e = cudaStreamCreateWithFlags(&p->capture_stream, cudaStreamNonBlocking)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         if ((e = cudaStreamCreateWithFlags(&p->aux_stream, cudaStreamNonBlocking)) != cudaSuccess ||
-            (e = cudaStreamCreateWithFlags(&p->chain_stream, cudaStreamNonBlocking)) != cudaSuccess ||
-            (e = cudaEventCreateWithFlags(&p->chain_fork, cudaEventDisableTiming)) != cudaSuccess ||
-            (e = cudaEventCreateWithFlags(&p->chain_join, cudaEventDisableTiming)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+            (e = cudaEventCreateWithFlags(&p->chain_fork, cudaEventDisableTiming)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+        for (int c = 1; c < kPoolChains && e == cudaSuccess; ++c)
+            if ((e = cudaStreamCreateWithFlags(&p->chain_stream[c], cudaStreamNonBlocking)) == cudaSuccess)
+                e = cudaEventCreateWithFlags(&p->chain_join[c], cudaEventDisableTiming);
+        if (e != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         if ((e = cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&p->join_ev, cudaEventDisableTiming)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         if ((e = cudaEventCreateWithFlags(&p->tables_free, cudaEventDisableTiming)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
@@ -617,7 +630,7 @@ int micsa_pool_create(size_t arena_bytes, int max_jobs, int tick_sweeps, micsa_p
         p->max_vblocks = 1 << 22;
         if ((e = cudaMalloc(&p->d_jobs, sizeof(JobDesc) * max_jobs)) != cudaSuccess ||
             (e = cudaMalloc(&p->d_vblocks, sizeof(VBlock) * (size_t)p->max_vblocks)) != cudaSuccess ||
-            (e = cudaMalloc(&p->d_nvb, 2 * sizeof(int32_t))) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_nvb, kPoolChains * sizeof(int32_t))) != cudaSuccess ||
             (e = cudaMalloc(&p->d_results, sizeof(long long) * 4 * (size_t)max_jobs * kPoolMaxR)) != cudaSuccess ||
             (e = cudaMalloc(&p->d_acc, sizeof(unsigned long long) * 2 * (size_t)max_jobs * kPoolMaxR)) != cudaSuccess ||
             (e = cudaMalloc(&p->d_improved, sizeof(int32_t) * (size_t)max_jobs * kPoolMaxR)) != cudaSuccess) { bail(MICSA_E_OOM); break; }
@@ -625,13 +638,13 @@ int micsa_pool_create(size_t arena_bytes, int max_jobs, int tick_sweeps, micsa_p
             (e = cudaMemsetAsync(p->d_improved, 0, sizeof(int32_t) * (size_t)max_jobs * kPoolMaxR, p->stream)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         if ((e = cudaMallocHost(&p->h_jobs_stage, sizeof(JobDesc) * max_jobs)) != cudaSuccess ||
             (e = cudaMallocHost(&p->h_vblocks, sizeof(VBlock) * (size_t)p->max_vblocks)) != cudaSuccess ||
-            (e = cudaMallocHost(&p->h_nvb, 2 * sizeof(int32_t))) != cudaSuccess) { bail(MICSA_E_OOM); break; }
-        p->h_nvb[0] = p->h_nvb[1] = 0;
+            (e = cudaMallocHost(&p->h_nvb, kPoolChains * sizeof(int32_t))) != cudaSuccess) { bail(MICSA_E_OOM); break; }
+        for (int c = 0; c < kPoolChains; ++c) p->h_nvb[c] = 0;
         for (auto &ev : p->stage_free)
             if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         if (rc) break;
         if ((e = cudaMemsetAsync(p->d_jobs, 0, sizeof(JobDesc) * max_jobs, p->stream)) != cudaSuccess ||
-            (e = cudaMemsetAsync(p->d_nvb, 0, 2 * sizeof(int32_t), p->stream)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+            (e = cudaMemsetAsync(p->d_nvb, 0, kPoolChains * sizeof(int32_t), p->stream)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         // jobs of L <= 32 live in shared memory as bit planes (multispin kernel)
         p->resident_smem = multispin_smem_bytes(make_geometry(32));
         const int res_per_sm = multispin_blocks_per_sm(true, p->resident_smem);
@@ -696,12 +709,14 @@ void micsa_pool_destroy(micsa_pool_t p) {
     }
     if (p->fork_ev) cudaEventDestroy(p->fork_ev);
     if (p->join_ev) cudaEventDestroy(p->join_ev);
-    if (p->chain_stream) {
-        cudaStreamSynchronize(p->chain_stream);
-        cudaStreamDestroy(p->chain_stream);
+    for (int c = 0; c < kPoolChains; ++c) {
+        if (p->chain_stream[c]) {
+            cudaStreamSynchronize(p->chain_stream[c]);
+            cudaStreamDestroy(p->chain_stream[c]);
+        }
+        if (p->chain_join[c]) cudaEventDestroy(p->chain_join[c]);
     }
     if (p->chain_fork) cudaEventDestroy(p->chain_fork);
-    if (p->chain_join) cudaEventDestroy(p->chain_join);
     if (p->stream) cudaStreamDestroy(p->stream);
     delete p;
 }
