@@ -149,13 +149,16 @@ int micsa_device_bytes(micsa_t h, size_t *bytes);
  * sites per thread, reduced to what the row pitch allows), optionally ORed with
  * MICSA_LAUNCH_REGCAP for the kernel variant whose registers are capped (the
  * streaming kernel: 64 per thread, blocks of at most 128 threads, 8 per SM;
- * the bit-plane kernel: 102, 5 blocks of 128 per SM), block 32..256 in
+ * the bit-plane kernel: 102, 5 blocks of 128 per SM) and/or MICSA_LAUNCH_PAIRS
+ * for the streaming variant in which one thread updates two neighbouring rows
+ * (rows without padding, MicSA; sharing their opposite-parity rows), block 32..256 in
  * steps of 32, blocks_per_sm -1 (grid-stride loop over the resident capacity),
  * 0 (one thread per chunk) or a positive cap, pdl != 0 chains consecutive
  * half-sweeps with programmatic dependent launch, graph_sweeps > 0 replays a
  * captured CUDA graph of that many sweeps (0: direct launches). Synchronizes
  * the handle's stream. */
 #define MICSA_LAUNCH_REGCAP 256
+#define MICSA_LAUNCH_PAIRS 512
 int micsa_set_launch_config(micsa_t h, int words_per_thread, int block, int blocks_per_sm, int pdl,
                             int graph_sweeps);
 

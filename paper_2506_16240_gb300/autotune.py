@@ -55,6 +55,9 @@ def candidates(L, R=1):
                 for blk, bps in itertools.product([64, 128, 256], [-1, 0, 3, 4])]
         out += [{"engine": "stream", "words_per_thread": 4, "block": blk, "blocks_per_sm": -1, "chains": 2,
                  "graph_sweeps": 256} for blk in (64, 128)]
+        # two rows per thread (rows without padding)
+        out += [{"engine": "stream", "words_per_thread": nw | 512, "block": blk, "blocks_per_sm": -1, "chains": 2}
+                for nw, blk in itertools.product([2, 4], [64, 128])]
     out += [{"engine": "onchip", "words_per_thread": nw} for nw in (4, 1)]  # where the state fits on chip
     out += [{"engine": "tma", "chains": c} for c in (1, 2) if c <= R]  # where the row pitch allows TMA tiles
     if L <= 40:

@@ -38,7 +38,8 @@ struct SweepArgs {
     const int64_t *cursor;       // graph replays: base index into params; else nullptr
     int64_t k;                   // this sweep's index relative to *cursor (or absolute)
     int r0, r1;                  // replicas [r0, r1) of every sample are updated (0, R: all)
-    FastDiv div_chunks;          // row -> (row, chunk): divide by chunks per row
+    FastDiv div_chunks;          // row pairs: divide by chunks per row as well
+    FastDiv div_half_L;          // row pairs: divide by L / 2          // row -> (row, chunk): divide by chunks per row
     FastDiv div_L;               // row -> (z, y): divide by L
 };
 
@@ -52,6 +53,7 @@ struct LaunchConfig {
     int graph_sweeps = 64;  // sweeps per captured CUDA graph (0: no graphs)
     bool regcap = false;    // kernel variant with registers capped at 64 (blocks of <= 128)
     int chains = 1;         // replica groups captured as concurrent kernel chains in one graph
+    bool pairs = false;     // one thread updates two rows (rows without padding, MicSA only)
 };
 
 // One job of the batched pool (device-resident descriptor).
@@ -202,6 +204,7 @@ cudaError_t launch_advance_cursor(int64_t *cursor, int64_t step, bool pdl, cudaS
 cudaError_t launch_wander(uint8_t *daemons, Geometry g, int64_t n_rep, int gamma, int parity, cudaStream_t st);
 int vector_words(const Geometry &g, int want);
 int max_resident_blocks(bool metro, int nw, int block, bool regcap);
+int max_resident_blocks_pairs(int nw, int block);
 dim3 block_shape(int R, int block);
 
 // initialisation, layout conversion and measurement (init_measure.cu)

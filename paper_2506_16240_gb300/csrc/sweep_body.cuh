@@ -154,3 +154,89 @@ __device__ __forceinline__ int even_word_energy(const Geometry &g, const int8_t 
 }
 
 }  // namespace micsa
+
+namespace micsa {
+
+// The MicSA update of rows (z, y0) and (z, y0 + 1), y0 even, of parity p over
+// the same NW words, for rows without padding (P == Lh). Both rows read the
+// opposite-parity rows y0 and y0 + 1 (one as its own row, the other as its
+// y neighbour), so the pair loads 8 opposite-parity words of NW instead of
+// 10, and the row decode, addressing and loop overhead are shared.
+template <int NW>
+__device__ __forceinline__ void micsa_cells(const Geometry &g, uint32_t (&S)[NW], uint32_t (&D)[NW],
+                                            const uint32_t (&Bw)[NW], const uint32_t (&O)[NW],
+                                            const uint32_t (&Oyp)[NW], const uint32_t (&Oym)[NW],
+                                            const uint32_t (&Ozp)[NW], const uint32_t (&Ozm)[NW], int o,
+                                            uint32_t edge, uint32_t quad0, uint32_t gid, uint32_t key0,
+                                            uint32_t key1, int64_t t, bool refresh, uint64_t th0, uint64_t th1,
+                                            uint64_t th2) {
+    uint32_t xp[NW], xm[NW];
+    x_neighbours<NW, false>(O, o, 0, g.Lh, edge, 0u, edge, xp, xm);
+#pragma unroll
+    for (int j = 0; j < NW; ++j) {
+        if (refresh) {
+            const uint4 w = philox4x32_10(
+                make_uint4(quad0 + j, (uint32_t)t, (gid << 2) | kTagDaemon, (uint32_t)((uint64_t)t >> 32)), key0,
+                key1);
+            D[j] = daemon_from_uniform(w.x, th0, th1, th2) | (daemon_from_uniform(w.y, th0, th1, th2) << 8) |
+                   (daemon_from_uniform(w.z, th0, th1, th2) << 16) | (daemon_from_uniform(w.w, th0, th1, th2) << 24);
+        }
+        const uint32_t neg = negative_terms(bond_planes(Bw[j]), xp[j], xm[j], Oyp[j], Oym[j], Ozp[j], Ozm[j]);
+        const uint32_t am = creutz4(unsatisfied32(neg, S[j]), D[j], 0xFFFFFFFFu);
+        S[j] ^= am & 0xFEFEFEFEu;
+    }
+}
+
+template <int NW>
+__device__ __forceinline__ void update_pair(const Geometry &g, int8_t *spins, uint8_t *daemons,
+                                            const uint8_t *bonds, int p, int z, int y0, int c, uint32_t gid,
+                                            uint32_t key0, uint32_t key1, int64_t t, bool refresh, uint64_t th0,
+                                            uint64_t th1, uint64_t th2) {
+    const int L = g.L, P = g.P;
+    const int b0 = c * 4 * NW;
+    const int y1 = y0 + 1;
+    const int ym = (y0 == 0) ? L - 1 : y0 - 1, y2 = (y1 + 1 == L) ? 0 : y1 + 1;
+    const int zp = (z + 1 == L) ? 0 : z + 1, zm = (z == 0) ? L - 1 : z - 1;
+    const int8_t *__restrict__ opp = spins + (int64_t)(1 - p) * g.half;
+    int8_t *__restrict__ own_s = spins + (int64_t)p * g.half;
+    uint8_t *__restrict__ own_d = daemons + (int64_t)p * g.half;
+    const uint8_t *__restrict__ bnd = bonds + (int64_t)p * g.half;
+    const int64_t r0 = ((int64_t)z * L + y0) * P, r1 = r0 + P;  // rows (z, y0), (z, y0 + 1)
+
+    uint32_t A[NW], Bq[NW], C[NW], Dq[NW], Zp0[NW], Zm0[NW], Zp1[NW], Zm1[NW];
+    load_words_ro<NW>(opp + ((int64_t)z * L + ym) * P + b0, A);
+    load_words_ro<NW>(opp + r0 + b0, Bq);
+    load_words_ro<NW>(opp + r1 + b0, C);
+    load_words_ro<NW>(opp + ((int64_t)z * L + y2) * P + b0, Dq);
+    load_words_ro<NW>(opp + ((int64_t)zp * L + y0) * P + b0, Zp0);
+    load_words_ro<NW>(opp + ((int64_t)zm * L + y0) * P + b0, Zm0);
+    load_words_ro<NW>(opp + ((int64_t)zp * L + y1) * P + b0, Zp1);
+    load_words_ro<NW>(opp + ((int64_t)zm * L + y1) * P + b0, Zm1);
+    uint32_t B0[NW], B1[NW], S0[NW], S1[NW], D0[NW], D1[NW];
+    load_words_ro<NW>(bnd + r0 + b0, B0);
+    load_words_ro<NW>(bnd + r1 + b0, B1);
+    load_words<NW>(own_s + r0 + b0, S0);
+    load_words<NW>(own_s + r1 + b0, S1);
+    if (!refresh) {
+        load_words<NW>(own_d + r0 + b0, D0);
+        load_words<NW>(own_d + r1 + b0, D1);
+    }
+    // edge bytes: for x offset 0 the byte before the range (the row's last byte
+    // at the row's start), for offset 1 the byte after it (the row's first byte
+    // at the row's end); rows y0 and y0 + 1 have opposite offsets
+    const int o0 = (p + y0 + z) & 1;
+    const int before = b0 == 0 ? g.Lh - 1 : b0 - 1, after = b0 + 4 * NW < g.Lh ? b0 + 4 * NW : 0;
+    const uint32_t e0 = (uint8_t)__ldg(opp + r0 + (o0 == 0 ? before : after));
+    const uint32_t e1 = (uint8_t)__ldg(opp + r1 + (o0 == 0 ? after : before));
+    const uint32_t quad0 = (uint32_t)((((int64_t)p * L + z) * L + y0) * g.W + c * NW);
+    // x_neighbours with range start 0: the wrap is carried by the edge byte (rows without padding)
+    micsa_cells<NW>(g, S0, D0, B0, Bq, C, A, Zp0, Zm0, o0, e0, quad0, gid, key0, key1, t, refresh, th0, th1, th2);
+    micsa_cells<NW>(g, S1, D1, B1, C, Dq, Bq, Zp1, Zm1, 1 - o0, e1, quad0 + (uint32_t)g.W, gid, key0, key1, t,
+                    refresh, th0, th1, th2);
+    store_words<NW>(own_s + r0 + b0, S0);
+    store_words<NW>(own_d + r0 + b0, D0);
+    store_words<NW>(own_s + r1 + b0, S1);
+    store_words<NW>(own_d + r1 + b0, D1);
+}
+
+}  // namespace micsa

@@ -71,6 +71,32 @@ __global__ void __launch_bounds__(128, 8) half_sweep_kernel_rc(SweepArgs a) {
     half_sweep_body<NW, METRO, FULL>(a);
 }
 
+// Two rows per thread (rows without padding, MicSA): thread q of a sample takes
+// the row pair (z, 2j), (z, 2j + 1) and chunk c, q = (z L/2 + j) chunks + c.
+template <int NW>
+__global__ void __launch_bounds__(256) half_sweep_pair_kernel(SweepArgs a) {
+    const int64_t kidx = a.k + (a.cursor ? *a.cursor : 0);
+    const SweepParam prm = a.params[kidx];
+    grid_dependency_wait();
+    grid_launch_dependents();
+    const Geometry g = a.geo;
+    const uint32_t per_sample = (uint32_t)g.L * (g.L / 2) * (g.W / NW);
+    const bool refresh = prm.mode == kModeRefresh;
+    for (int sample = blockIdx.y; sample < a.S; sample += gridDim.y)
+        for (int r = a.r0 + threadIdx.y; r < a.r1; r += blockDim.y)
+            for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < per_sample; q += gridDim.x * blockDim.x) {
+                const uint32_t prow = fdiv(q, a.div_chunks);
+                const int c = (int)(q - prow * a.div_chunks.d);
+                const uint32_t z = fdiv(prow, a.div_half_L);
+                const int y0 = 2 * (int)(prow - z * a.div_half_L.d);
+                const int64_t gid = (int64_t)sample * a.R + r;
+                const int64_t fam = gid * a.gamma + prm.alpha;
+                update_pair<NW>(g, a.spins + gid * 2 * g.half, a.daemons + fam * 2 * g.half,
+                                a.bonds + (int64_t)sample * 2 * g.half, a.parity, (int)z, y0, c, (uint32_t)fam,
+                                a.key0, a.key1, prm.t, refresh, prm.th0, prm.th1, prm.th2);
+            }
+}
+
 // Wandering (Sec. 2.6): every site of parity p exchanges the walker of family
 // alpha with its neighbour along direction alpha mod 6 (+x, +y, +z, -x, -y, -z,
 // the table of Sec. 2.8). One thread per (replica family, site of parity p);
@@ -161,8 +187,38 @@ int vector_words(const Geometry &g, int want) {
     return 1;
 }
 
+template <int NW>
+static cudaError_t launch_pairs(const SweepArgs &a0, const LaunchConfig &lc, cudaStream_t st) {
+    SweepArgs a = a0;
+    const int chunks = a.geo.W / NW;
+    a.div_chunks = make_fastdiv((uint32_t)chunks);
+    a.div_half_L = make_fastdiv((uint32_t)(a.geo.L / 2));
+    const int64_t per_sample = (int64_t)a.geo.L * (a.geo.L / 2) * chunks;
+    const dim3 blk = block_shape(a.r1 - a.r0, lc.block);
+    int64_t gx = (per_sample + blk.x - 1) / blk.x;
+    int64_t gy = a.S < 65535 ? a.S : 65535;
+    if (lc.max_blocks > 0 && gx * gy > lc.max_blocks) gx = lc.max_blocks / gy > 0 ? lc.max_blocks / gy : 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)gx, (unsigned)gy);
+    cfg.blockDim = blk;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = lc.pdl ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, half_sweep_pair_kernel<NW>, a);
+}
+
+// Row pairs apply to MicSA half-sweeps of rows without padding.
+bool pairs_apply(const Geometry &g, bool metro, const LaunchConfig &lc) {
+    return lc.pairs && !metro && g.P == g.Lh && g.L % 2 == 0;
+}
+
 cudaError_t launch_half_sweep(const SweepArgs &a, bool metro, const LaunchConfig &lc, cudaStream_t st) {
     const int nw = vector_words(a.geo, lc.nw);
+    if (pairs_apply(a.geo, metro, lc))
+        return nw == 4 ? launch_pairs<4>(a, lc, st) : nw == 2 ? launch_pairs<2>(a, lc, st) : launch_pairs<1>(a, lc, st);
     if (metro) {
         if (nw == 4) return launch_variant<4, true>(a, lc, st);
         if (nw == 2) return launch_variant<2, true>(a, lc, st);
@@ -191,6 +247,15 @@ static int occupancy(bool rc, int block) {
     int n = 0;
     const cudaError_t e = rc ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, half_sweep_kernel_rc<NW, METRO>, block, 0)
                              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, half_sweep_kernel<NW, METRO>, block, 0);
+    return e == cudaSuccess ? n : 0;
+}
+
+int max_resident_blocks_pairs(int nw, int block) {
+    int n = 0;
+    const cudaError_t e =
+        nw == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, half_sweep_pair_kernel<4>, block, 0)
+        : nw == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, half_sweep_pair_kernel<2>, block, 0)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, half_sweep_pair_kernel<1>, block, 0);
     return e == cudaSuccess ? n : 0;
 }
 

@@ -214,7 +214,7 @@ def test_launch_configs_agree(L):
     sched = np.linspace(2.0, 0.6, n)
     ref = None
     configs = [(4, 256, -1, 1, 64), (2, 128, 0, 0, 0), (1, 256, -1, 1, 16), (4, 64, 3, 0, 7),
-               (2, 256, -1, 1, 64)]
+               (2, 256, -1, 1, 64), (4 | 512, 128, -1, 1, 64), (2 | 512, 64, 0, 1, 16), (1 | 512, 128, 2, 0, 0)]
     for cfg in configs:
         with micsa.Micsa(L, 1, R, 42) as g:
             g.set_launch_config(*cfg)
