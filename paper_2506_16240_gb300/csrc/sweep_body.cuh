@@ -37,8 +37,10 @@ __device__ __forceinline__ void update_chunk(const Geometry &g, int8_t *spins, u
     const int b0 = c * 4 * NW;  // first byte of this thread's range within the row
     const int yp = (y + 1 == g.L) ? 0 : y + 1, ym = (y == 0) ? g.L - 1 : y - 1;
     const int zp = (z + 1 == g.L) ? 0 : z + 1, zm = (z == 0) ? g.L - 1 : z - 1;
-    const int64_t row0 = (int64_t)row * g.P;
-    const int64_t off_c = row0 + b0;
+    // offsets within one parity half (L^2 P < 2^32 bytes for every allowed L)
+    const uint32_t P = (uint32_t)g.P, uL = (uint32_t)g.L;
+    const uint32_t row0 = (uint32_t)row * P;
+    const uint32_t off_c = row0 + (uint32_t)b0;
     const int8_t *__restrict__ opp = spins + (int64_t)(1 - p) * g.half;
     int8_t *__restrict__ own_s = spins + (int64_t)p * g.half;
     uint8_t *__restrict__ own_d = daemons + (int64_t)p * g.half;
@@ -46,10 +48,10 @@ __device__ __forceinline__ void update_chunk(const Geometry &g, int8_t *spins, u
     uint32_t Bw[NW], O[NW], Oyp[NW], Oym[NW], Ozp[NW], Ozm[NW], S[NW], D[NW];
     load_ro<NW, SMEM>(bonds + (int64_t)p * g.half + off_c, Bw);
     load_ro<NW, SMEM>(opp + off_c, O);
-    load_ro<NW, SMEM>(opp + ((int64_t)z * g.L + yp) * g.P + b0, Oyp);
-    load_ro<NW, SMEM>(opp + ((int64_t)z * g.L + ym) * g.P + b0, Oym);
-    load_ro<NW, SMEM>(opp + ((int64_t)zp * g.L + y) * g.P + b0, Ozp);
-    load_ro<NW, SMEM>(opp + ((int64_t)zm * g.L + y) * g.P + b0, Ozm);
+    load_ro<NW, SMEM>(opp + (((uint32_t)z * uL + (uint32_t)yp) * P + (uint32_t)b0), Oyp);
+    load_ro<NW, SMEM>(opp + (((uint32_t)z * uL + (uint32_t)ym) * P + (uint32_t)b0), Oym);
+    load_ro<NW, SMEM>(opp + (((uint32_t)zp * uL + (uint32_t)y) * P + (uint32_t)b0), Ozp);
+    load_ro<NW, SMEM>(opp + (((uint32_t)zm * uL + (uint32_t)y) * P + (uint32_t)b0), Ozm);
     load_words<NW>(own_s + off_c, S);
     if (!METRO && !refresh) load_words<NW>(own_d + off_c, D);
 
