@@ -2,6 +2,8 @@
 // by the single-handle half-sweep kernel and the batched (pool) kernel.
 #pragma once
 
+#include <type_traits>
+
 #include "micsa_internal.h"
 
 namespace micsa {
@@ -37,10 +39,13 @@ __device__ __forceinline__ void update_chunk(const Geometry &g, int8_t *spins, u
     const int b0 = c * 4 * NW;  // first byte of this thread's range within the row
     const int yp = (y + 1 == g.L) ? 0 : y + 1, ym = (y == 0) ? g.L - 1 : y - 1;
     const int zp = (z + 1 == g.L) ? 0 : z + 1, zm = (z == 0) ? g.L - 1 : z - 1;
-    // offsets within one parity half (L^2 P < 2^32 bytes for every allowed L)
-    const uint32_t P = (uint32_t)g.P, uL = (uint32_t)g.L;
-    const uint32_t row0 = (uint32_t)row * P;
-    const uint32_t off_c = row0 + (uint32_t)b0;
+    // offsets within one parity half: 32-bit for MicSA (L^2 P < 2^32 bytes for
+    // every allowed L; fewer instructions), 64-bit for the Metropolis variant
+    // (measured faster there)
+    using Off = typename std::conditional<METRO, int64_t, uint32_t>::type;
+    const Off P = (Off)g.P, uL = (Off)g.L;
+    const Off row0 = (Off)row * P;
+    const Off off_c = row0 + (Off)b0;
     const int8_t *__restrict__ opp = spins + (int64_t)(1 - p) * g.half;
     int8_t *__restrict__ own_s = spins + (int64_t)p * g.half;
     uint8_t *__restrict__ own_d = daemons + (int64_t)p * g.half;
@@ -48,10 +53,10 @@ __device__ __forceinline__ void update_chunk(const Geometry &g, int8_t *spins, u
     uint32_t Bw[NW], O[NW], Oyp[NW], Oym[NW], Ozp[NW], Ozm[NW], S[NW], D[NW];
     load_ro<NW, SMEM>(bonds + (int64_t)p * g.half + off_c, Bw);
     load_ro<NW, SMEM>(opp + off_c, O);
-    load_ro<NW, SMEM>(opp + (((uint32_t)z * uL + (uint32_t)yp) * P + (uint32_t)b0), Oyp);
-    load_ro<NW, SMEM>(opp + (((uint32_t)z * uL + (uint32_t)ym) * P + (uint32_t)b0), Oym);
-    load_ro<NW, SMEM>(opp + (((uint32_t)zp * uL + (uint32_t)y) * P + (uint32_t)b0), Ozp);
-    load_ro<NW, SMEM>(opp + (((uint32_t)zm * uL + (uint32_t)y) * P + (uint32_t)b0), Ozm);
+    load_ro<NW, SMEM>(opp + (((Off)z * uL + (Off)yp) * P + (Off)b0), Oyp);
+    load_ro<NW, SMEM>(opp + (((Off)z * uL + (Off)ym) * P + (Off)b0), Oym);
+    load_ro<NW, SMEM>(opp + (((Off)zp * uL + (Off)y) * P + (Off)b0), Ozp);
+    load_ro<NW, SMEM>(opp + (((Off)zm * uL + (Off)y) * P + (Off)b0), Ozm);
     load_words<NW>(own_s + off_c, S);
     if (!METRO && !refresh) load_words<NW>(own_d + off_c, D);
 
