@@ -110,14 +110,14 @@ def tune(g, torch, stream, sweeps=400, T=0.7, refresh_interval=10, use_cache=Tru
             continue
         try:
             apply(g, c)
-        except MicsaError:  # the lattice does not fit this engine
+            g.run(sched[: max(10, sweeps // 10)], refresh_interval)  # warm-up of this shape
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.run(sched, refresh_interval)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        except MicsaError:  # the lattice does not fit this engine, or its launch was refused
             continue
-        g.run(sched[: max(10, sweeps // 10)], refresh_interval)  # warm-up of this shape
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        g.run(sched, refresh_interval)
-        e1.record(stream)
-        torch.cuda.synchronize()
         rate = g.L ** 3 * g.S * g.R * sweeps / (e0.elapsed_time(e1) * 1e6)
         if best is None or rate > best[1]:
             best = (c, rate)

@@ -128,6 +128,8 @@ class FakeHandle:
         return (self.engine, self.shape, self.chains, self.rpt)
 
     def run(self, sched, interval):
+        if self.engine == "onchip" and self.L == 160:
+            raise autotune.MicsaError(-3, "launch refused")  # a candidate that fails when it runs
         self.log.append(self.key())
 
 
@@ -173,7 +175,7 @@ def test_autotuner_keeps_the_fastest_shape_and_skips_engines_that_do_not_fit(mon
     assert (choice["engine"], choice["words_per_thread"], choice["replicas_per_thread"]) == ("multispin_global", 2, 4)
     assert h.key() == best  # the choice is applied at the end
     engines = {k[0] for k in h.log}
-    assert {"stream", "multispin_global", "onchip", "tma"} <= engines
+    assert {"stream", "multispin_global", "tma"} <= engines and "onchip" not in engines  # failed runs skipped
     h2 = FakeHandle(48, 1, 2, None)  # tma does not fit: skipped, not fatal
     FakeEvent.clock, FakeEvent.costs = [], {}
     autotune.tune(h2, FakeTorch, None, sweeps=20, use_cache=False, engines=("stream", "tma"))
