@@ -396,6 +396,15 @@ def leg_paper_shape(micsa, timer, stream, peaks, L=160, R=128, sweeps=400):
     gw.close()
     out["walkers_log_refresh_flips_per_ns"] = updates(L, 1, R, 256) / (ms * 1e6)
     out["walkers_ns_per_timestep"] = 1e6 * ms / 256
+    # six walker families (a timestep is six sweeps, family alpha wanders along
+    # direction alpha), the paper's best-performing variant (Sec. 3)
+    g6 = micsa.Micsa(L, 1, R, 12, stream=stream, gamma=6, walkers=True)
+    g6.set_engine("multispin_global")
+    g6.set_launch_config(out["multispin_launch"]["words_per_thread"], 128, -1, True, 64)
+    g6.run_logrefresh(np.full(16, 0.7))
+    ms = timer(lambda: g6.run_logrefresh(np.full(32, 0.7)))
+    g6.close()
+    out["walkers_gamma6_flips_per_ns"] = updates(L, 1, R, 32 * 6) / (ms * 1e6)
     out["paper_h100_walkers_total_ns_per_sweep"] = 121554 + 97378
     out["paper_h100_spin_update_kernel_ns_per_sweep"] = 121554
     out["paper_h100_flips_per_ns"] = 128 * 160 ** 3 / 121554.0
