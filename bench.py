@@ -261,7 +261,10 @@ def leg_roofline(micsa, timer, stream, L, peaks, n_plain=2000, choice=None):
         from paper_2506_16240_gb300 import autotune
         autotune.apply(g, choice)
     g.run(np.full(1, 0.7), 10)  # t = 0 refresh; the timed sweeps below have none
-    g.run(np.full(50, 0.7), 2 ** 31 - 1)
+    # warm-up as long as the timed run (and longer than two graph lengths), so that
+    # the sweep table is sized and the sweep graph captured before the timed
+    # region (one-time setup costs)
+    g.run(np.full(max(600, n_plain), 0.7), 2 ** 31 - 1)
     ms = timer(lambda: g.run(np.full(n_plain, 0.7), 2 ** 31 - 1))
     shape = g.launch_config()
     g.close()
@@ -287,7 +290,7 @@ def plane_roofline(micsa, timer, stream, g, peaks, n_plain=2000):
     """Bit-plane half-sweep kernel of handle g (engine and shape already set):
     algorithmic bytes / mean launch time over sweeps without refresh."""
     L, S, R = g.L, g.S, g.R
-    g.run(np.full(50, 0.7), 2 ** 31 - 1)
+    g.run(np.full(max(600, n_plain), 0.7), 2 ** 31 - 1)  # table sized, graph captured (setup costs)
     ms = timer(lambda: g.run(np.full(n_plain, 0.7), 2 ** 31 - 1))
     launch_us = 1e3 * ms / (2 * n_plain)  # conversions at both ends included (2 of 2 n_plain + 3 launches)
     half_sites = L ** 3 // 2
@@ -334,7 +337,7 @@ def leg_multispin_l160(micsa, timer, stream, peaks, sweeps=20_000):
     shape = tune_planes(g, timer)
     sched = np.full(sweeps, w["T"])
     g.reinit(6)
-    g.run(sched[:1000], w["refresh_interval"])
+    g.run(sched, w["refresh_interval"])  # as long as the timed run: table sized, graph captured
     g.reinit(7)
     ms = timer(lambda: g.run(sched, w["refresh_interval"]))
     e, _, q = g.measure()
@@ -355,7 +358,7 @@ def leg_onchip_l160(micsa, timer, stream, sweeps=5_000):
     for nw in (4, 2, 1):
         g.set_launch_config(nw, 128, -1, True, 64)
         g.set_engine("onchip", 2048)
-        g.run(np.full(200, w["T"]), w["refresh_interval"])
+        g.run(np.full(sweeps, w["T"]), w["refresh_interval"])
         ms = timer(lambda: g.run(np.full(sweeps, w["T"]), w["refresh_interval"]))
         if best is None or ms < best[0]:
             best = (ms, nw)
@@ -372,7 +375,7 @@ def leg_paper_shape(micsa, timer, stream, peaks, L=160, R=128, sweeps=400):
     g.set_engine("multispin_global")
     out["multispin_launch"] = tune_planes(g, timer, sweeps=60)
     g.reinit(10)
-    g.run(sched[:40], 10)
+    g.run(sched, 10)  # as long as the timed run: table sized, graph captured
     ms = timer(lambda: g.run(sched, 10))
     out["multispin_flips_per_ns"] = updates(L, 1, R, sweeps) / (ms * 1e6)
     out["multispin_ns_per_sweep"] = 1e6 * ms / sweeps
@@ -380,8 +383,8 @@ def leg_paper_shape(micsa, timer, stream, peaks, L=160, R=128, sweeps=400):
     g.set_engine("stream")
     g.set_launch_config(4, 128, -1, True, 64)
     g.reinit(10)
-    g.run(sched[:10], 10)
     n_s = max(10, sweeps // 4)
+    g.run(sched[:n_s], 10)
     ms = timer(lambda: g.run(sched[:n_s], 10))
     out["stream_flips_per_ns"] = updates(L, 1, R, n_s) / (ms * 1e6)
     nw = g.launch_config()["words_per_thread"]
@@ -391,7 +394,7 @@ def leg_paper_shape(micsa, timer, stream, peaks, L=160, R=128, sweeps=400):
     gw = micsa.Micsa(L, 1, R, 11, stream=stream, walkers=True)
     gw.set_engine("multispin_global")
     gw.set_launch_config(out["multispin_launch"]["words_per_thread"], 128, -1, True, 64)
-    gw.run_logrefresh(sched[:64])
+    gw.run_logrefresh(np.full(256, 0.7))
     ms = timer(lambda: gw.run_logrefresh(np.full(256, 0.7)))
     gw.close()
     out["walkers_log_refresh_flips_per_ns"] = updates(L, 1, R, 256) / (ms * 1e6)
@@ -414,10 +417,11 @@ def leg_paper_shape(micsa, timer, stream, peaks, L=160, R=128, sweeps=400):
 def leg_metropolis(micsa, timer, stream, n=10_000):
     w = WORKLOAD
     g = micsa.Micsa(w["L"], 1, w["replicas"], 3, stream=stream)
-    g.run_metropolis(np.full(200, w["T"]))
+    # warm-ups as long as the timed runs: sweep table sized, graphs captured (setup costs)
+    g.run_metropolis(np.full(n, w["T"]))
     ms_metro = timer(lambda: g.run_metropolis(np.full(n, w["T"])))
     g.reinit(3)
-    g.run(np.full(200, w["T"]), w["refresh_interval"])
+    g.run(np.full(n, w["T"]), w["refresh_interval"])
     ms_micsa = timer(lambda: g.run(np.full(n, w["T"]), w["refresh_interval"]))
     g.close()
     u = updates(w["L"], 1, w["replicas"], n)
