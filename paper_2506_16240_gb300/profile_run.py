@@ -5,6 +5,7 @@
     python -m paper_2506_16240_gb300.profile_run multispin  # L=32, 64 x 2: 128 sweeps, blocks of 64
     python -m paper_2506_16240_gb300.profile_run planes     # L=160, 1 x 128, bit planes: 12 sweeps
     python -m paper_2506_16240_gb300.profile_run onchip     # L=160, 1 x 2, on-chip engine: 2 x 64 sweeps
+    python -m paper_2506_16240_gb300.profile_run tma        # L=160, 1 x 2, TMA engine: 12 sweeps
     python -m paper_2506_16240_gb300.profile_run pool       # 64 mixed jobs, 2 ticks of 64 sweeps
 
 Each run is a few milliseconds of GPU work on a few tens of MB, sized for
@@ -49,6 +50,14 @@ def onchip():
     return g.measure()[0]
 
 
+def tma():
+    g = micsa.Micsa(160, 1, 2, 3)
+    g.set_engine("tma")
+    g.set_launch_config(4, 128, -1, True, 0)  # direct launches
+    g.run(np.full(12, 0.7), 10)
+    return g.measure()[0]
+
+
 def multispin():
     g = micsa.Micsa(32, 64, 2, 2)
     g.set_engine("multispin", 64)
@@ -70,5 +79,5 @@ def pool():
 if __name__ == "__main__":
     mode = sys.argv[1] if len(sys.argv) > 1 else "stream"
     modes = {"stream": stream, "chains": chains, "multispin": multispin, "planes": planes, "onchip": onchip,
-             "pool": pool}
+             "tma": tma, "pool": pool}
     print(mode, modes[mode]())
