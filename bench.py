@@ -38,7 +38,10 @@ Legs on the same JSON line:
                timings), T = 0.7, refresh every 10: bit-plane engine and the
                byte streaming engine; and one walker per spin on the log refresh
                schedule (the paper's timed configuration), bit-plane engine
-  cpu_baseline the CPU oracle (single thread) on a bounded sample of sweeps
+  kstar        same-GPU Metropolis against MicSA with six walkers per spin on the
+               same samples (L = 64, T = 0.7): the time-rescaling factor k* fitted
+               to the energy relaxation
+  cpu_baseline the CPU oracle on the host cores on a bounded sample of sweeps
 
 --impl reference times the oracle itself (the deliberately slow reference).
 Multi-GPU (torchrun): one independent lattice per rank (weak scaling, no
@@ -414,6 +417,46 @@ def leg_paper_shape(micsa, timer, stream, peaks, L=160, R=128, sweeps=400):
     return out
 
 
+def leg_kstar(micsa, L=64, S=4, R=2, T=0.7, t_max=4096, gamma=6, stream=None):
+    """Same-GPU Metropolis against MicSA with gamma walkers per spin on the same
+    synthetic samples (couplings and starts from one seed) at T = 0.7: the energy
+    per spin on a log time grid, and the factor k with e_MicSA(t) =
+    e_Metropolis(k t), t in sweeps for Metropolis and in timesteps of gamma
+    sweeps for MicSA (the paper's k*, from xi_12 there, is 6.034 for six walkers
+    at T = 0.7)."""
+    from paper_2506_16240_gb300 import analysis
+    grid = sorted({int(round(10 ** (x / 10))) for x in range(0, int(10 * np.log10(t_max)) + 1)})
+    N = L ** 3
+
+    def curve(g, run, times):
+        out, t_prev = [], 0
+        for tm in times:
+            if tm > t_prev:
+                run(g, tm - t_prev)
+                t_prev = tm
+            e, _, _ = g.measure()
+            out.append(float(e.mean()) / N)
+        return np.array(out)
+
+    gm = micsa.Micsa(L, S, R, 21, stream=stream)
+    e_met = curve(gm, lambda g, n: g.run_metropolis(np.full(n, T)), grid)
+    gm.close()
+    gw = micsa.Micsa(L, S, R, 21, stream=stream, gamma=gamma, walkers=True)
+    gw.set_engine("multispin_global")
+    grid_w = [t for t in grid if t <= t_max // 3]
+    e_mic = curve(gw, lambda g, n: g.run_logrefresh(np.full(n, T)), grid_w)
+    gw.close()
+    tw = np.array(grid_w, np.float64)
+    sel = tw >= 16  # the refreshes at t = 2^s - 1 perturb the early energies
+    k, mis, npts = analysis.fit_time_rescaling(np.array(grid, np.float64), e_met, tw[sel], e_mic[sel], k_range=(1, 30))
+    return {"k_star_energy": k, "rms_mismatch": float(np.sqrt(mis)), "points": npts, "gamma": gamma,
+            "workload": f"L={L}, {S} samples x {R} replicas, T={T}: Metropolis to {t_max} sweeps, "
+                        f"MicSA with {gamma} walkers per spin (log refresh) to {grid_w[-1]} timesteps",
+            "paper_k_star_xi12": 6.034,
+            "e_metropolis": [[t, round(v, 6)] for t, v in zip(grid, e_met)][::3],
+            "e_micsa": [[t, round(v, 6)] for t, v in zip(grid_w, e_mic)][::3]}
+
+
 def leg_metropolis(micsa, timer, stream, n=10_000):
     w = WORKLOAD
     g = micsa.Micsa(w["L"], 1, w["replicas"], 3, stream=stream)
@@ -646,7 +689,8 @@ def main(argv=None):
                 ("serving", lambda: leg_serving(micsa, torch, stream, args.serving_jobs)),
                 ("multispin_l160", lambda: leg_multispin_l160(micsa, timer, stream, peaks)),
                 ("onchip_l160", lambda: leg_onchip_l160(micsa, timer, stream)),
-                ("paper_shape", lambda: leg_paper_shape(micsa, timer, stream, peaks))]
+                ("paper_shape", lambda: leg_paper_shape(micsa, timer, stream, peaks)),
+                ("kstar", lambda: leg_kstar(micsa, stream=stream))]
         for name, fn in legs:
             try:
                 extras[name] = fn()

@@ -190,3 +190,26 @@ def test_autotune_candidates_are_gated_by_lattice_shape():
     c18 = autotune.candidates(18, 1)
     assert any(c["engine"] == "resident" for c in c18) and any(c["engine"] == "multispin" for c in c18)
     assert not any(c["engine"] == "multispin_global" or c.get("chains", 1) > 1 for c in c18)
+
+
+def test_time_rescaling_fit_recovers_a_planted_factor():
+    """A power-law relaxation e(t) = e_inf + b t^-c sampled on a log grid, and the
+    same curve with time rescaled by k = 6.034 (the paper's k* for six walkers at
+    T = 0.7): the fit returns k; shifted curves or curves without overlap are
+    handled."""
+    from paper_2506_16240_gb300 import analysis
+    t_ref = np.unique(np.round(np.logspace(0, 4, 60)))
+    e_ref = -1.70 + 0.4 * t_ref ** -0.35
+    for k_true in (6.034, 1.0, 2.5):
+        t = np.unique(np.round(np.logspace(0, 4 - np.log10(k_true) - 0.01, 40)))
+        e = -1.70 + 0.4 * (k_true * t) ** -0.35
+        k, m, n = analysis.fit_time_rescaling(t_ref, e_ref, t, e)
+        assert k == pytest.approx(k_true, rel=5e-3) and n >= 30 and m < 1e-6  # log-t interpolation bias
+    # noise does not move the estimate much
+    rng = np.random.default_rng(1)
+    t = np.unique(np.round(np.logspace(0, 3, 40)))
+    e = -1.70 + 0.4 * (6.0 * t) ** -0.35 + rng.normal(0, 1e-4, t.size)
+    k, _, _ = analysis.fit_time_rescaling(t_ref, e_ref, t, e)
+    assert k == pytest.approx(6.0, rel=0.05)
+    with pytest.raises(ValueError):
+        analysis.fit_time_rescaling(t_ref, e_ref, t * 1e9, e, k_range=(1.0, 2.0))
