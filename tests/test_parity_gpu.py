@@ -512,3 +512,50 @@ def test_tma_engine_limits():
         with micsa.Micsa(L, 1, 2, 1, **kw) as g:
             with pytest.raises(micsa.MicsaError):
                 g.set_engine("tma")
+
+
+def test_bench_workload_in_bench_launch_shape_matches_oracle():
+    """The benchmark lattice (L = 160, one sample, two replicas, seed 3, T = 0.7,
+    refresh every 10) in the launch shape the benchmark's autotuner picks (16-byte
+    words, blocks of 128, two replica chains, graph replays): 30 sweeps bit-exact
+    with the oracle, then the bit-plane engine and a Metropolis stretch."""
+    L, S, R, seed = 160, 1, 2, 3
+    sched = np.full(30, 0.7)
+    st = O.create(L, S, R, seed)
+    O.run(st, sched, 10)
+    for engine in ("stream", "multispin_global"):
+        with micsa.Micsa(L, S, R, seed) as g:
+            g.set_engine(engine)
+            g.set_launch_config(4, 128, -1, True, 8)  # 3 graph replays of 8 sweeps + 6 direct
+            g.set_replica_chains(2)
+            g.run(sched, 10)
+            assert_same_state(g, st, engine)
+    st2 = O.create(L, S, R, seed)
+    O.run_metropolis(st2, np.full(4, 0.7))
+    with micsa.Micsa(L, S, R, seed) as g:
+        g.set_launch_config(4, 128, -1, True, 8)
+        g.set_replica_chains(2)
+        g.run_metropolis(np.full(4, 0.7))
+        assert_same_state(g, st2, "metropolis")
+
+
+def test_maximum_size_conservation_and_engine_agreement():
+    """L = 1600 (the largest lattice the library accepts; 12 GB of state): the
+    energy H_EA + H_aux is exactly conserved between refreshes (Sec. 2.3, 2.4),
+    and the streaming and bit-plane engines give the same integer sums."""
+    import torch
+    if torch.cuda.mem_get_info()[0] < 40 * (1 << 30):
+        pytest.skip("needs 40 GB of free device memory")
+    L = 1600
+    sums = {}
+    for engine in ("stream", "multispin_global"):
+        with micsa.Micsa(L, 1, 1, 11) as g:
+            g.set_engine(engine)
+            g.run(np.full(1, 0.8), 10)            # refresh at t = 0
+            e0, a0, _ = g.measure()
+            g.run(np.full(3, 0.8), 2 ** 31 - 1)   # no refresh
+            e1, a1, _ = g.measure()
+            assert int(e0[0] + a0[0]) == int(e1[0] + a1[0]), engine
+            assert -3 * L ** 3 <= int(e1[0]) <= 3 * L ** 3
+            sums[engine] = (int(e0[0]), int(a0[0]), int(e1[0]), int(a1[0]))
+    assert sums["stream"] == sums["multispin_global"]
