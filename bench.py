@@ -282,7 +282,7 @@ def leg_roofline(micsa, timer, stream, L, peaks, n_plain=2000, choice=None):
     profiled = (L == 160 and choice is not None and choice.get("engine") == "stream" and choice.get("chains") == 2
                 and choice.get("words_per_thread") == 4 and choice.get("block") == 128)
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": 2 * 8.21e6 if profiled else None, "peak_source": "measured" if hbm else "fallback",
+            "traffic": None, "peak_source": "measured" if hbm else "fallback",
             "kernel": "micsa::half_sweep_kernel<4,false> (streaming MicSA half-sweep, no refresh)",
             "L": L, "bytes_per_launch": bytes_per_launch, "launch_us": launch_us, "launch": shape,
             "replica_chains": (choice or {}).get("chains", 1),
@@ -306,7 +306,7 @@ def plane_roofline(micsa, timer, stream, g, peaks, n_plain=2000):
     # DRAM bytes per launch from the ncu capture at L = 160, 128 replicas, 4 words per
     # thread (profiles/msg_half_L160x128_full.md: 132.67 MB read + 44.72 MB written)
     shape = g.launch_config()
-    traffic = 177.4e6 if (L == 160 and R == 128 and shape["words_per_thread"] == 4) else None
+    traffic = None  # ncu DRAM bytes of the current msg_half_kernel: not yet captured
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_source": "measured" if hbm else "fallback",
             "kernel": "micsa::msg_half_kernel (bit-plane MicSA half-sweep, no refresh)",

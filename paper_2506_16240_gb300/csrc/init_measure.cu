@@ -203,8 +203,8 @@ __global__ void __launch_bounds__(256) measure_kernel(const int8_t *spins, const
     const int zp = (z + 1 == g.L) ? 0 : z + 1, zm = (z == 0) ? g.L - 1 : z - 1;
     const int64_t off_c = (int64_t)row * g.P + b0;
     const int64_t row0 = (int64_t)row * g.P;
-    BondPlanes bp{};
-    if (active) bp = bond_planes(*reinterpret_cast<const uint32_t *>(bonds + (int64_t)(sample * 2) * g.half + off_c));
+    uint32_t Bw = 0;
+    if (active) Bw = *reinterpret_cast<const uint32_t *>(bonds + (int64_t)(sample * 2) * g.half + off_c);
 
     for (int r = 0; r < R; ++r) {
         const int64_t gid = (int64_t)sample * R + r;
@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(256) measure_kernel(const int8_t *spins, const
             }
             uint32_t xp[1], xm[1];
             x_neighbours<1>(O, o, b0, g.Lh, edge, first, last, xp, xm);
-            const uint32_t u32 = unsatisfied32(negative_terms(bp, xp[0], xm[0], Oyp, Oym, Ozp, Ozm), S0) & valid;
+            const uint32_t u32 = unsatisfied_count(Bw, S0, xp[0], xm[0], Oyp, Oym, Ozp, Ozm) & valid;
             const uint32_t usum = ((u32 >> 5) * 0x01010101u) >> 24;  // sum of the four lanes
             e_part = 2 * (int)usum - 6 * nvalid;
             for (int al = 0; al < gamma; ++al) {  // every daemon family (Sec. 2.2: H_aux sums them all)

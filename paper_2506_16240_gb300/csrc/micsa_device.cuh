@@ -129,11 +129,13 @@ __device__ __forceinline__ uint32_t valid_mask(int b0, int j, int Lh) {
     return 0xFFFFFFFFu >> (8 * (4 - n));
 }
 
-// 0xFF in every byte lane whose most significant bit is set, 0x00 elsewhere.
-// (__byte_perm selects bytes with the low three selector bits only and does not
-// replicate signs, so the expansion is done arithmetically.)
+// 0xFF in every byte lane whose most significant bit is set, 0x00 elsewhere:
+// prmt in its default mode with selector nibbles 8 + b takes byte b and
+// replicates its sign over the lane (the __byte_perm intrinsic has no sign mode).
 __device__ __forceinline__ uint32_t lanes_from_msb(uint32_t x) {
-    return ((x >> 7) & 0x01010101u) * 0xFFu;
+    uint32_t r;
+    asm("prmt.b32 %0, %1, %1, 0xBA98;" : "=r"(r) : "r"(x));
+    return r;
 }
 
 // Bond word shifted so that the bit of direction k lands on bit 5 of each lane.
@@ -156,11 +158,14 @@ __device__ __forceinline__ uint32_t negative_terms(const BondPlanes &b, uint32_t
 }
 
 // Per lane: 32 * u, u = number of unsatisfied bonds of the site (J s s_nb = -1),
-// from the negative-term count and the site's own spin word S.
-__device__ __forceinline__ uint32_t unsatisfied32(uint32_t neg, uint32_t S) {
-    const uint32_t smask = lanes_from_msb(S);  // 0xFF where s = -1 (0xFF), 0 where s = +1
-    const uint32_t pos = 0xC0C0C0C0u - neg;             // 32 * (6 - count)
-    return neg ^ ((neg ^ pos) & smask);
+// from the site's bond word B and its own spin word S. Bits 1..7 of a +-1 spin
+// byte all hold its sign, so bits 0..5 of S >> 1 carry the own sign in every
+// lane and bit k of B ^ (S >> 1) is the sign of J_k s; the shift that brings
+// bit k to bit 5 and the XOR with the neighbour then give [J_k s s_nb = -1].
+// (Bits 6, 7 of a lane never reach bit 5 of any lane under the left shifts.)
+__device__ __forceinline__ uint32_t unsatisfied_count(uint32_t B, uint32_t S, uint32_t xp, uint32_t xm,
+                                                      uint32_t yp, uint32_t ym, uint32_t zp, uint32_t zm) {
+    return negative_terms(bond_planes(B ^ (S >> 1)), xp, xm, yp, ym, zp, zm);
 }
 
 // The elementary move on four lanes. With u unsatisfied bonds dH = 12 - 4u, so
@@ -170,8 +175,7 @@ __device__ __forceinline__ uint32_t unsatisfied32(uint32_t neg, uint32_t S) {
 __device__ __forceinline__ uint32_t creutz4(uint32_t u32, uint32_t &D, uint32_t valid) {
     const uint32_t t = (u32 >> 5) + D;         // u + m in 0..9 per lane
     const uint32_t v = t + 0x7D7D7D7Du;         // 0x80..0x83 <=> accepted
-    const uint32_t ok = v & ~(v << 5) & 0x80808080u;
-    const uint32_t am = ((ok >> 7) * 0xFFu) & valid;  // ok has bit 7 of a lane at most
+    const uint32_t am = lanes_from_msb(v & ~(v << 5)) & valid;  // bit 7 set and bit 2 clear
     D = (D & ~am) | (v & 0x03030303u & am);
     return am;
 }

@@ -517,6 +517,10 @@ __device__ __forceinline__ CutsGt make_cuts_gt(uint64_t th0, uint64_t th1, uint6
     return {(uint32_t)(th0 - 1), (uint32_t)(th1 - 1), (uint32_t)(th2 - 1)};
 }
 
+__device__ __forceinline__ void prefetch_l2(const uint32_t *p) {
+    asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 template <int NW> struct Vec;
 template <> struct Vec<1> {
     static __device__ __forceinline__ void ld(const uint32_t *p, uint32_t *v) { v[0] = *p; }
@@ -627,10 +631,20 @@ __global__ void __launch_bounds__(128, MINB) msg_half_kernel(MsgArgs a) {
     const int gplane = 2 + (((1 - buf) * a.gamma + alpha) * 2) * 2 + o;
     const int gq = (int)((prm.t - 1) & 1), gd0 = alpha % 6, gdd = (p == gq) ? gd0 : (gd0 + 3) % 6;
     const int r_end = min(a.r1, a.r0 + (int)(blockIdx.y + 1) * a.rpt);
+    const int mread = gather ? gplane : mplane;  // the daemon words this half-sweep reads
     for (int r = a.r0 + blockIdx.y * a.rpt; r < r_end; ++r) {
         const int64_t gid = (int64_t)sample * a.R + r;
         const uint32_t fam = (uint32_t)(gid * a.gamma + alpha);  // Philox id of this daemon family
         uint32_t *pl = a.planes + gid * a.np * a.WP;
+        if (r + 1 < r_end) {  // the next replica's words that come from DRAM, into L2
+            const uint32_t *nx = pl + (int64_t)a.np * a.WP;
+            prefetch_l2(nx + (int64_t)p * a.WP + wc);
+            prefetch_l2(nx + (int64_t)o * a.WP + wc);
+            if (!refresh) {
+                prefetch_l2(nx + (int64_t)mread * a.WP + wc);
+                prefetch_l2(nx + (int64_t)(mread + 2) * a.WP + wc);
+            }
+        }
         const uint32_t *O = pl + (int64_t)o * a.WP;  // spins of the opposite parity
         uint32_t *Sp = pl + (int64_t)p * a.WP;
         uint32_t *M0 = pl + (int64_t)mplane * a.WP;

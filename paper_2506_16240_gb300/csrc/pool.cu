@@ -143,7 +143,7 @@ __device__ __forceinline__ void chunk_measure(const Geometry &g, const int8_t *s
     for (int j = 0; j < NW; ++j) {
         const uint32_t valid = FULL ? 0xFFFFFFFFu : valid_mask(b0, j, g.Lh);
         const uint32_t u32 =
-            unsatisfied32(negative_terms(bond_planes(B[j]), xp[j], xm[j], Oyp[j], Oym[j], Ozp[j], Ozm[j]), S[j]) & valid;
+            unsatisfied_count(B[j], S[j], xp[j], xm[j], Oyp[j], Oym[j], Ozp[j], Ozm[j]) & valid;
         e += 2 * (int)(((u32 >> 5) * 0x01010101u) >> 24) - 6 * (__popc(valid) / 8);
         a += 4 * (int)((((D0[j] & valid) * 0x01010101u) >> 24) + (((D1[j] & valid) * 0x01010101u) >> 24));
     }

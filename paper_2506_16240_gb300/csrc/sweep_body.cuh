@@ -81,9 +81,7 @@ __device__ __forceinline__ void update_chunk(const Geometry &g, int8_t *spins, u
 
 #pragma unroll
     for (int j = 0; j < NW; ++j) {
-        const BondPlanes bp = bond_planes(Bw[j]);
-        const uint32_t neg = negative_terms(bp, xp[j], xm[j], Oyp[j], Oym[j], Ozp[j], Ozm[j]);
-        const uint32_t u32 = unsatisfied32(neg, S[j]);
+        const uint32_t u32 = unsatisfied_count(Bw[j], S[j], xp[j], xm[j], Oyp[j], Oym[j], Ozp[j], Ozm[j]);
         const uint32_t valid = FULL ? 0xFFFFFFFFu : valid_mask(b0, j, g.Lh);
         if (METRO) {
             // dH = 12 - 4u > 0 <=> u < 3; accept iff a fresh uniform is below
@@ -156,7 +154,7 @@ __device__ __forceinline__ int even_word_energy(const Geometry &g, const int8_t 
     uint32_t xp[1], xm[1];
     x_neighbours<1>(O, o, b0, g.Lh, edge, first, last, xp, xm);
     const uint32_t u32 =
-        unsatisfied32(negative_terms(bond_planes(B[0]), xp[0], xm[0], Oyp[0], Oym[0], Ozp[0], Ozm[0]), S[0]) & valid;
+        unsatisfied_count(B[0], S[0], xp[0], xm[0], Oyp[0], Oym[0], Ozp[0], Ozm[0]) & valid;
     return 2 * (int)(((u32 >> 5) * 0x01010101u) >> 24) - 6 * (__popc(valid) / 8);
 }
 
@@ -188,8 +186,8 @@ __device__ __forceinline__ void micsa_cells(const Geometry &g, uint32_t (&S)[NW]
             D[j] = daemon_from_uniform(w.x, th0, th1, th2) | (daemon_from_uniform(w.y, th0, th1, th2) << 8) |
                    (daemon_from_uniform(w.z, th0, th1, th2) << 16) | (daemon_from_uniform(w.w, th0, th1, th2) << 24);
         }
-        const uint32_t neg = negative_terms(bond_planes(Bw[j]), xp[j], xm[j], Oyp[j], Oym[j], Ozp[j], Ozm[j]);
-        const uint32_t am = creutz4(unsatisfied32(neg, S[j]), D[j], 0xFFFFFFFFu);
+        const uint32_t am = creutz4(unsatisfied_count(Bw[j], S[j], xp[j], xm[j], Oyp[j], Oym[j], Ozp[j], Ozm[j]),
+                                    D[j], 0xFFFFFFFFu);
         S[j] ^= am & 0xFEFEFEFEu;
     }
 }

@@ -226,9 +226,9 @@ __global__ void __launch_bounds__(kTmaThreads, 1) tma_half_kernel(const __grid_c
                              (daemon_from_uniform(w.z, prm.th0, prm.th1, prm.th2) << 16) |
                              (daemon_from_uniform(w.w, prm.th0, prm.th1, prm.th2) << 24)) & valid;
                 }
-                const uint32_t neg = negative_terms(bond_planes(Bw[jw]), xp[jw], xm[jw], Oyp[jw], Oym[jw], Ozp[jw],
-                                                    Ozm[jw]);
-                const uint32_t am = creutz4(unsatisfied32(neg, S[jw]), D[jw], valid);
+                const uint32_t u32 = unsatisfied_count(Bw[jw], S[jw], xp[jw], xm[jw], Oyp[jw], Oym[jw], Ozp[jw],
+                                                       Ozm[jw]);
+                const uint32_t am = creutz4(u32, D[jw], valid);
                 S[jw] ^= am & 0xFEFEFEFEu;
             }
             const int64_t goff = ((int64_t)gid * 2 + p) * g.half + ((int64_t)z * L + y) * P + b0;
