@@ -282,7 +282,7 @@ def leg_roofline(micsa, timer, stream, L, peaks, n_plain=2000, choice=None):
     profiled = (L == 160 and choice is not None and choice.get("engine") == "stream" and choice.get("chains") == 2
                 and choice.get("words_per_thread") == 4 and choice.get("block") == 128)
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": None, "peak_source": "measured" if hbm else "fallback",
+            "traffic": 2 * 8.21e6 if profiled else None, "peak_source": "measured" if hbm else "fallback",
             "kernel": "micsa::half_sweep_kernel<4,false> (streaming MicSA half-sweep, no refresh)",
             "L": L, "bytes_per_launch": bytes_per_launch, "launch_us": launch_us, "launch": shape,
             "replica_chains": (choice or {}).get("chains", 1),
@@ -304,9 +304,9 @@ def plane_roofline(micsa, timer, stream, g, peaks, n_plain=2000):
     peak = hbm if hbm else 6800.0
     achieved = bytes_per_launch / (launch_us * 1e-6) / 1e9
     # DRAM bytes per launch from the ncu capture at L = 160, 128 replicas, 4 words per
-    # thread (profiles/msg_half_L160x128_full.md: 132.67 MB read + 44.72 MB written)
+    # thread (profiles/msg_half_L160x128_full.md: 132.69 MB read + 44.69 MB written)
     shape = g.launch_config()
-    traffic = None  # ncu DRAM bytes of the current msg_half_kernel: not yet captured
+    traffic = 177.4e6 if (L == 160 and R == 128 and shape["words_per_thread"] == 4) else None
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_source": "measured" if hbm else "fallback",
             "kernel": "micsa::msg_half_kernel (bit-plane MicSA half-sweep, no refresh)",
@@ -457,18 +457,35 @@ def leg_kstar(micsa, L=64, S=4, R=2, T=0.7, t_max=4096, gamma=6, stream=None):
             "e_micsa": [[t, round(v, 6)] for t, v in zip(grid_w, e_mic)][::3]}
 
 
-def leg_metropolis(micsa, timer, stream, n=10_000):
+def leg_metropolis(micsa, timer, stream, choice=None, n=10_000):
+    """Same lattice under the RNG-per-update Metropolis kernel, in the fastest of a
+    few launch shapes for that kernel, next to MicSA in the benchmark's tuned shape."""
+    from paper_2506_16240_gb300 import autotune
     w = WORKLOAD
+    T = w["T"]
     g = micsa.Micsa(w["L"], 1, w["replicas"], 3, stream=stream)
-    # warm-ups as long as the timed runs: sweep table sized, graphs captured (setup costs)
-    g.run_metropolis(np.full(n, w["T"]))
-    ms_metro = timer(lambda: g.run_metropolis(np.full(n, w["T"])))
+    shapes = []
+    for nw, blk, ch in [(4, 128, 2), (4, 128, 1), (2, 128, 2), (4, 256, 2), (2, 256, 1)]:
+        g.set_launch_config(nw, blk, -1, True, 64)
+        g.set_replica_chains(ch)
+        g.run_metropolis(np.full(1000, T))
+        shapes.append((timer(lambda: g.run_metropolis(np.full(1000, T))), nw, blk, ch))
+    _, nw, blk, ch = min(shapes)
+    g.set_launch_config(nw, blk, -1, True, 64)
+    g.set_replica_chains(ch)
     g.reinit(3)
-    g.run(np.full(n, w["T"]), w["refresh_interval"])
-    ms_micsa = timer(lambda: g.run(np.full(n, w["T"]), w["refresh_interval"]))
+    # warm-ups as long as the timed runs: sweep table sized, graphs captured (setup costs)
+    g.run_metropolis(np.full(n, T))
+    ms_metro = timer(lambda: g.run_metropolis(np.full(n, T)))
+    if choice is not None:
+        autotune.apply(g, choice)
+    g.reinit(3)
+    g.run(np.full(n, T), w["refresh_interval"])
+    ms_micsa = timer(lambda: g.run(np.full(n, T), w["refresh_interval"]))
     g.close()
     u = updates(w["L"], 1, w["replicas"], n)
     return {"value": u / (ms_metro * 1e6), "unit": METRIC, "sweeps": n,
+            "metropolis_launch": {"words_per_thread": nw, "block": blk, "replica_chains": ch},
             "micsa_same_lattice": u / (ms_micsa * 1e6), "micsa_over_metropolis": ms_metro / ms_micsa}
 
 
@@ -683,7 +700,7 @@ def main(argv=None):
     extras = {}
     if rank == 0 and not args.no_extras:
         legs = [("dram_point", lambda: leg_roofline(micsa, timer, stream, 320, peaks, n_plain=500, choice=tuned)),
-                ("metropolis", lambda: leg_metropolis(micsa, timer, stream)),
+                ("metropolis", lambda: leg_metropolis(micsa, timer, stream, choice=tuned)),
                 ("quench_l32", lambda: leg_quench_l32(micsa, timer, stream)),
                 ("batched", lambda: leg_batched(micsa, torch, stream)),
                 ("serving", lambda: leg_serving(micsa, torch, stream, args.serving_jobs)),
