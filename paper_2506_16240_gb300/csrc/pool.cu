@@ -54,49 +54,81 @@ struct PoolTables {
 __device__ __forceinline__ void pool_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
 __device__ __forceinline__ void pool_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
-template <int NW, bool FULL>
-__device__ __forceinline__ void pool_item(const JobDesc &J, int r, uint32_t chunk, int p, int64_t t) {
-    const FastDiv dc{(uint32_t)(J.geo.W / NW), J.divC_m, J.divC_l};
-    const uint32_t row = fdiv(chunk, dc);
-    const int c = (int)(chunk - row * dc.d);
-    const bool refresh = (t % J.interval) == 0;
-    uint64_t th0 = 0, th1 = 0, th2 = 0;
-    if (refresh) {
-        const uint64_t *q = J.thr + 3 * (t / J.interval);
-        th0 = q[0];
-        th1 = q[1];
-        th2 = q[2];
+// The job-level values of one half-sweep of a job, read from its descriptor
+// once per run of virtual blocks of that job.
+struct PoolJobState {
+    Geometry geo;
+    int8_t *spins;
+    uint8_t *daemons;
+    const uint8_t *bonds;
+    int64_t t;
+    uint32_t c0m, c1m, c2m;  // refresh cut points minus one (each in [2^30, 2^32])
+    uint32_t key0, key1, chunks;
+    FastDiv dc, divL;
+    int nw;
+    bool active, refresh, full;
+};
+
+__device__ __forceinline__ void load_job_state(const JobDesc &J, int k, PoolJobState &s) {
+    s.t = J.t + k;
+    s.active = J.live && s.t < J.n_sweeps;
+    s.geo = J.geo;
+    s.spins = J.spins;
+    s.daemons = J.daemons;
+    s.bonds = J.bonds;
+    s.key0 = J.key0;
+    s.key1 = J.key1;
+    s.nw = J.nw;
+    s.full = s.geo.P == s.geo.Lh;  // rows without padding
+    s.chunks = (uint32_t)s.geo.L * s.geo.L * (s.geo.W / s.nw);
+    s.dc = FastDiv{(uint32_t)(s.geo.W / s.nw), J.divC_m, J.divC_l};
+    s.divL = FastDiv{(uint32_t)s.geo.L, J.divL_m, J.divL_l};
+    s.refresh = s.active && (s.t % J.interval) == 0;
+    s.c0m = s.c1m = s.c2m = 0;
+    if (s.refresh) {
+        const uint64_t *q = J.thr + 3 * (s.t / J.interval);
+        s.c0m = (uint32_t)(q[0] - 1);
+        s.c1m = (uint32_t)(q[1] - 1);
+        s.c2m = (uint32_t)(q[2] - 1);
     }
-    const FastDiv divL{(uint32_t)J.geo.L, J.divL_m, J.divL_l};
-    update_chunk<NW, false, false, FULL>(J.geo, J.spins + (int64_t)r * 2 * J.geo.half,
-                            J.daemons + (int64_t)r * 2 * J.geo.half, J.bonds, p, (int)row, c, (uint32_t)r,
-                            J.key0, J.key1, t, refresh, th0, th1, th2, divL);
+}
+
+template <int NW, bool FULL>
+__device__ __forceinline__ void pool_item(const PoolJobState &s, int r, uint32_t chunk, int p) {
+    const uint32_t row = fdiv(chunk, s.dc);
+    const int c = (int)(chunk - row * s.dc.d);
+    const int64_t roff = (int64_t)r * 2 * s.geo.half;
+    update_chunk<NW, false, false, FULL>(s.geo, s.spins + roff, s.daemons + roff, s.bonds, p, (int)row, c,
+                                         (uint32_t)r, s.key0, s.key1, s.t, s.refresh, (uint64_t)s.c0m + 1,
+                                         (uint64_t)s.c1m + 1, (uint64_t)s.c2m + 1, s.divL);
 }
 
 // One half-sweep (parity p) of sweep k of the tick for every live job of part
 // `part` of the virtual-block table (the parts hold disjoint (job, replica)
 // pairs and run as concurrent kernel chains).
-__global__ void __launch_bounds__(kVBlock) pool_half_sweep_kernel(PoolTables T, int k, int p, int part) {
+__global__ void __launch_bounds__(kVBlock, 5) pool_half_sweep_kernel(PoolTables T, int k, int p, int part) {
     pool_wait();
     pool_release();
     const int v0 = part == 0 ? 0 : T.n_vblocks[part - 1];
     const int nvb = T.n_vblocks[part] - v0;
-    // a contiguous run of virtual blocks per CTA: mostly one job (its descriptor
-    // stays in L1) and neighbouring planes (their rows are re-read from L1)
+    // a contiguous run of virtual blocks per CTA: mostly one job (its state is
+    // read once per run) and neighbouring planes (their rows are re-read from L1)
     const int per = (nvb + (int)gridDim.x - 1) / (int)gridDim.x;
     const int vb_end = v0 + min(nvb, ((int)blockIdx.x + 1) * per);
+    PoolJobState s;
+    int slot = -1;  // the job whose state s holds (the same for every thread of the CTA)
     for (int vb = v0 + (int)blockIdx.x * per; vb < vb_end; ++vb) {
         const VBlock b = T.vblocks[vb];
-        const JobDesc &J = T.jobs[b.slot];
-        const int64_t t = J.t + k;
-        if (!J.live || t >= J.n_sweeps) continue;
-        const uint32_t chunks = (uint32_t)J.geo.L * J.geo.L * (J.geo.W / J.nw);
+        if (b.slot != slot) {
+            slot = b.slot;
+            load_job_state(T.jobs[slot], k, s);
+        }
+        if (!s.active) continue;
         const uint32_t chunk = (uint32_t)b.chunk0 + threadIdx.x;
-        if (chunk >= chunks) continue;
-        const bool full = J.geo.P == J.geo.Lh;  // rows without padding
-        if (J.nw == 4) full ? pool_item<4, true>(J, b.replica, chunk, p, t) : pool_item<4, false>(J, b.replica, chunk, p, t);
-        else if (J.nw == 2) full ? pool_item<2, true>(J, b.replica, chunk, p, t) : pool_item<2, false>(J, b.replica, chunk, p, t);
-        else full ? pool_item<1, true>(J, b.replica, chunk, p, t) : pool_item<1, false>(J, b.replica, chunk, p, t);
+        if (chunk >= s.chunks) continue;
+        if (s.nw == 4) s.full ? pool_item<4, true>(s, b.replica, chunk, p) : pool_item<4, false>(s, b.replica, chunk, p);
+        else if (s.nw == 2) s.full ? pool_item<2, true>(s, b.replica, chunk, p) : pool_item<2, false>(s, b.replica, chunk, p);
+        else s.full ? pool_item<1, true>(s, b.replica, chunk, p) : pool_item<1, false>(s, b.replica, chunk, p);
     }
 }
 
