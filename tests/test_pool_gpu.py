@@ -69,7 +69,61 @@ def test_pool_result_independent_of_slot_and_neighbours():
     np.testing.assert_array_equal(alone["best_spins"], mixed["best_spins"])
 
 
-@pytest.mark.parametrize("job", [JOBS[0], JOBS[2], JOBS[5], JOBS[8]])
+# streamed by the pool half-sweep kernel (too big for the shared-memory kernel):
+# one job per (words per thread, rows with or without padding) variant
+JOBS_STREAMED = [  # (L, R, seed, n_sweeps, interval, T_start, T_end)
+    (42, 1, 21, 12, 5, 2.0, 0.8),   # 2 words per thread, padded rows
+    (48, 2, 22, 13, 4, 2.5, 0.5),   # 2 words, rows without padding
+    (50, 1, 23, 9, 3, 2.0, 1.0),    # 1 word, padded rows
+    (56, 1, 26, 7, 2, 1.5, 1.5),    # 1 word, rows without padding
+    (58, 1, 24, 11, 10, 2.0, 0.6),  # 4 words, padded rows
+    (64, 2, 25, 12, 6, 2.5, 0.5),   # 4 words, rows without padding
+]
+
+
+def test_pool_streamed_variants_match_oracle():
+    res = run_pool(JOBS_STREAMED, K=5)
+    for idx, (L, R, seed, n, interval, T0, T1) in enumerate(JOBS_STREAMED):
+        st = O.create(L, 1, R, seed)
+        O.run(st, micsa.linear_schedule(T0, T1, n), interval)
+        e, a, _ = O.measure(st)
+        np.testing.assert_array_equal(res[idx]["energy"], e, err_msg=str(JOBS_STREAMED[idx]))
+        np.testing.assert_array_equal(res[idx]["aux"], a, err_msg=str(JOBS_STREAMED[idx]))
+        assert res[idx]["sweeps_done"] == n
+
+
+def test_batched_workload_in_one_pool_sampled_jobs_match_oracle():
+    """The batched workload's 256 lattices (L drawn from {16, 24, 32, 48, 64}, 2
+    replicas, refresh interval 5..20, a seed each, from the same generator) in one
+    pool with ticks of 256 sweeps, on a short anneal 2.5 -> 0.5 of 40 sweeps: for
+    one job of each L the final energies equal the oracle's."""
+    rng = np.random.default_rng(4)
+    Ls = rng.choice([16, 24, 32, 48, 64], 256)
+    rs = rng.integers(5, 21, 256)
+    seeds = rng.integers(1, 2 ** 62, 256)
+    n = 40
+    with micsa.Pool(8 << 30, 512, 256) as p:
+        ids = [p.submit(int(L), 2, int(s), n, int(r), 2.5, 0.5) for L, r, s in zip(Ls, rs, seeds)]
+        assert all(i is not None for i in ids)
+        res = {}
+        while len(res) < len(ids):
+            p.tick()
+            for i, jid in enumerate(ids):
+                if i not in res:
+                    r = p.poll(jid, best_spins=False)
+                    if r is not None:
+                        res[i] = r
+    for L in (16, 24, 32, 48, 64):
+        i = int(np.flatnonzero(Ls == L)[0])
+        st = O.create(L, 1, 2, int(seeds[i]))
+        O.run(st, micsa.linear_schedule(2.5, 0.5, n), int(rs[i]))
+        e, a, _ = O.measure(st)
+        np.testing.assert_array_equal(res[i]["energy"], e, err_msg=f"L={L}")
+        np.testing.assert_array_equal(res[i]["aux"], a, err_msg=f"L={L}")
+
+
+@pytest.mark.parametrize("job", [JOBS[0], JOBS[2], JOBS[5], JOBS[8], JOBS_STREAMED[1], JOBS_STREAMED[4],
+                                 JOBS_STREAMED[5]])
 def test_pool_best_configuration_matches_oracle(job):
     L, R, seed, n, interval, T0, T1 = job
     K = 16
