@@ -523,10 +523,15 @@ def c4_instances():
 
 
 def leg_batched(micsa, torch, stream, n_sweeps=20_000, loop_sweeps=2_000):
+    from paper_2506_16240_gb300 import autotune
     inst = c4_instances()
     total = sum(updates(L, 1, 2, n_sweeps) for L, _, _ in inst)
+    jobs = [(L, 2, s, n_sweeps, r, 2.5, 0.5) for L, r, s in inst]
+    # pool shape (words per thread, chains, grid) from the autotuner, on a scratch pool of the same jobs
+    choice = autotune.tune_pool_for_jobs(lambda: micsa.Pool(8 << 30, 512, 32), jobs)
     with micsa.Pool(8 << 30, 512, 256) as p:
-        ids = [p.submit(L, 2, s, n_sweeps, r, 2.5, 0.5) for L, r, s in inst]
+        autotune.apply_pool(p, choice)
+        ids = [p.submit(*j) for j in jobs]
         assert all(i is not None for i in ids)
         p.wait()
         launches0 = p.stats()["launches"]
@@ -555,16 +560,20 @@ def leg_batched(micsa, torch, stream, n_sweeps=20_000, loop_sweeps=2_000):
         h.close()
     batched, loop = total / (dt_pool * 1e9), loop_upd / (dt_loop * 1e9)
     return {"value": batched, "unit": METRIC, "per_lattice_loop": loop, "speedup": batched / loop,
-            "wall_s": dt_pool, "launches": launches,
+            "wall_s": dt_pool, "launches": launches, "launch": choice,
             "workload": "256 lattices L in {16,24,32,48,64} x 2 replicas, anneal 2.5->0.5 over 2e4 sweeps, "
                         "refresh 5..20; the loop is timed on its first 2e3 sweeps"}
 
 
 def leg_serving(micsa, torch, stream, n_jobs, n_cap=64):
-    from paper_2506_16240_gb300 import serve
+    from paper_2506_16240_gb300 import autotune, serve
     # saturated capacity of the pool on this job mix: n_cap jobs queued at once
     cap_reqs = serve.poisson_stream(n_cap, 1e6, seed=55)
+    choice = autotune.tune_pool_for_jobs(
+        lambda: micsa.Pool(16 << 30, 256, 32),
+        [(r.L, r.n_replicas, r.seed, r.n_sweeps, r.refresh_interval, r.T_start, r.T_end) for r in cap_reqs])
     with micsa.Pool(16 << 30, 256, 128) as p:
+        autotune.apply_pool(p, choice)
         srv = serve.Server(p)
         srv.serve(cap_reqs, realtime=False)
         capacity = sum(r.updates for r in cap_reqs) / srv.wall  # updates/s
@@ -584,10 +593,11 @@ def leg_serving(micsa, torch, stream, n_jobs, n_cap=64):
     rate_hz = 0.8 * capacity / serve.mean_job_updates()
     reqs = serve.poisson_stream(n_jobs, rate_hz, seed=5)
     with micsa.Pool(16 << 30, 256, 128) as p:
+        autotune.apply_pool(p, choice)
         server = serve.Server(p)
         done = server.serve(reqs, realtime=True)
     out = serve.summarize(done, server.wall)
-    out.update({"unit": METRIC, "arrival_rate_hz": rate_hz,
+    out.update({"unit": METRIC, "arrival_rate_hz": rate_hz, "launch": choice,
                 "saturated_pool_flips_per_ns": capacity / 1e9, "per_job_loop_flips_per_ns": loop_rate / 1e9,
                 "saturated_over_loop": capacity / loop_rate,
                 "workload": f"{n_jobs} Poisson jobs: L even 16..96, sweeps log-uniform 1e3..1e5, "

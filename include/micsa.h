@@ -351,10 +351,20 @@ int micsa_pool_finished(micsa_pool_t p, int64_t *ids, int max_ids, int *n_ids);
 /* Jobs resident, free arena bytes, kernels launched so far. Any pointer may be NULL. */
 int micsa_pool_stats(micsa_pool_t p, int *live_jobs, size_t *free_bytes, int64_t *launches);
 
-/* Grid of the batched kernels (blocks per SM, 1..64), programmatic dependent
+/* Grid of the batched kernels (blocks per SM, 1..64; 0: as many as fit, the
+ * default), programmatic dependent
  * launch on/off, CUDA graph replay of ticks on/off (the autotuner's knobs;
  * results are identical for every choice). Synchronizes. */
 int micsa_pool_set_launch_config(micsa_pool_t p, int blocks_per_sm, int pdl, int use_graph);
+
+/* Shape of the streaming jobs' half-sweeps (the autotuner's other knobs;
+ * results are identical for every choice): a streaming job's thread updates
+ * the largest of 4, 2, 1 words (4 sites each) that is at most max_words (1, 2
+ * or 4) and divides the words of its rows, for the jobs already admitted too;
+ * the virtual-block table is split at (job, replica) boundaries into `chains`
+ * (1..4) parts run as concurrent kernel chains. Default 4 and 2.
+ * MICSA_E_INVALID_ARG otherwise. Synchronizes. */
+int micsa_pool_set_shape(micsa_pool_t p, int max_words, int chains);
 
 /* Message of the last failure on p. */
 const char *micsa_pool_last_error(micsa_pool_t p);

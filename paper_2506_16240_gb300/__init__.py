@@ -325,6 +325,7 @@ SIGNATURES.update({
     "micsa_pool_stats": (_c.c_int, [_P, ctypes.POINTER(_c.c_int), ctypes.POINTER(ctypes.c_size_t), _i64p]),
     "micsa_pool_finished": (_c.c_int, [_P, _i64p, _c.c_int, ctypes.POINTER(_c.c_int)]),
     "micsa_pool_set_launch_config": (_c.c_int, [_P, _c.c_int, _c.c_int, _c.c_int]),
+    "micsa_pool_set_shape": (_c.c_int, [_P, _c.c_int, _c.c_int]),
     "micsa_pool_last_error": (_c.c_char_p, [_P]),
     "micsa_pool_destroy": (None, [_P]),
 })
@@ -434,3 +435,8 @@ class Pool:
     def set_launch_config(self, blocks_per_sm, pdl=True, use_graph=True):
         self._check(lib().micsa_pool_set_launch_config(self.h, int(blocks_per_sm), int(bool(pdl)),
                                                        int(bool(use_graph))))
+
+    def set_shape(self, max_words=4, chains=2):
+        """Words per thread (cap 1, 2 or 4) and concurrent kernel chains (1..4) of
+        the streaming jobs' half-sweeps; results do not depend on them."""
+        self._check(lib().micsa_pool_set_shape(self.h, int(max_words), int(chains)))

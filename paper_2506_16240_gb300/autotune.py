@@ -129,3 +129,67 @@ def tune(g, torch, stream, sweeps=400, T=0.7, refresh_interval=10, use_cache=Tru
         cache[key] = choice
         _store(cache)
     return dict(choice, cached=False)
+
+
+# ----------------------------------------------------------------- pool --
+def pool_candidates():
+    """(max_words, chains) shapes of the pool's streaming half-sweeps."""
+    return [{"max_words": w, "chains": c, "blocks_per_sm": 0} for w, c in itertools.product([4, 2, 1], [1, 2, 3, 4])]
+
+
+def apply_pool(pool, choice):
+    pool.set_shape(choice["max_words"], choice["chains"])
+    pool.set_launch_config(choice.get("blocks_per_sm", 0))  # 0: as many blocks as fit
+
+
+def time_pool_ticks(pool, ticks, clock):
+    """Seconds for `ticks` ticks of the pool after one untimed tick (which
+    uploads the tables and captures the tick's graph for the current shape)."""
+    pool.tick()
+    pool.wait()
+    t0 = clock()
+    for _ in range(ticks):
+        pool.tick()
+    pool.wait()
+    return clock() - t0
+
+
+def tune_pool(pool, ticks=2, blocks=(3, 4, 5, 6, 8), clock=None):
+    """Pick and apply the fastest pool shape for the jobs admitted to `pool`:
+    first (words per thread cap, chains) at the default grid, then blocks per SM
+    at the best shape. Every choice computes the same bits, so the jobs just
+    advance while they are timed; none of them should finish during the tuning
+    (give them more sweeps than (1 + ticks) x tick_sweeps x the candidates).
+    Returns the choice with its time per tick."""
+    import time
+    clock = clock or time.perf_counter
+    best = None
+    for c in pool_candidates():
+        apply_pool(pool, c)
+        dt = time_pool_ticks(pool, ticks, clock) / ticks
+        if best is None or dt < best[0]:
+            best = (dt, dict(c))
+    shape = best[1]
+    for bps in blocks:
+        c = dict(shape, blocks_per_sm=bps)
+        apply_pool(pool, c)
+        dt = time_pool_ticks(pool, ticks, clock) / ticks
+        if dt < best[0]:
+            best = (dt, c)
+    apply_pool(pool, best[1])
+    return dict(best[1], s_per_tick=best[0])
+
+
+def tune_pool_for_jobs(pool_factory, jobs, ticks=2, clock=None):
+    """Tune on a scratch pool: pool_factory() makes it, `jobs` are submit()
+    argument tuples (L, R, seed, n_sweeps, interval, T_start, T_end) whose sweep
+    counts are raised so that no job finishes while the candidates run. Returns
+    the choice (apply it to the real pool with apply_pool)."""
+    n_cand = len(pool_candidates()) + 5
+    with pool_factory() as p:
+        K = p.tick_sweeps
+        long = (1 + ticks) * K * (n_cand + 2)  # candidates x (warm-up + timed ticks), with a margin
+        for L, R, seed, _, interval, T0, T1 in jobs:
+            if p.submit(L, R, seed, long, interval, T0, T1) is None:
+                break  # the scratch pool is full: tune on what fits
+        return tune_pool(p, ticks=ticks, clock=clock)

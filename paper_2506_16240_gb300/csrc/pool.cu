@@ -28,7 +28,7 @@ namespace micsa {
 
 constexpr int kPoolMaxR = MICSA_POOL_MAX_REPLICAS;
 constexpr int kVBlock = 128;  // chunk items per virtual block
-constexpr int kPoolChains = 2;  // parts of the streaming jobs run as concurrent kernel chains (4 measured no faster)
+constexpr int kPoolMaxChains = 4;  // parts of the streaming jobs run as concurrent kernel chains (default 2)
 
 
 
@@ -42,7 +42,7 @@ struct VBlock {
 struct PoolTables {
     JobDesc *jobs;          // [max_jobs]
     const VBlock *vblocks;  // [max_vblocks]
-    const int32_t *n_vblocks;  // [kPoolChains]: the end of each chain's part (the last: the total)
+    const int32_t *n_vblocks;  // [kPoolMaxChains]: the end of each chain's part (unused parts and the last: the total)
     long long *energy;      // [max_jobs][kPoolMaxR]
     long long *aux;
     long long *best_energy;
@@ -187,7 +187,7 @@ __device__ __forceinline__ void chunk_measure(const Geometry &g, const int8_t *s
 __global__ void __launch_bounds__(kVBlock) pool_energy_kernel(PoolTables T) {
     pool_wait();
     pool_release();
-    const int nvb = T.n_vblocks[kPoolChains - 1];
+    const int nvb = T.n_vblocks[kPoolMaxChains - 1];
     // a contiguous run of virtual blocks per CTA: mostly one job (its descriptor
     // stays in L1) and neighbouring planes (their rows are re-read from L1)
     const int per = (nvb + (int)gridDim.x - 1) / (int)gridDim.x;
@@ -254,7 +254,7 @@ __global__ void pool_best_kernel(PoolTables T, int K) {
 __global__ void __launch_bounds__(kVBlock) pool_best_copy_kernel(PoolTables T) {
     pool_wait();
     pool_release();
-    const int nvb = T.n_vblocks[kPoolChains - 1];
+    const int nvb = T.n_vblocks[kPoolMaxChains - 1];
     // a contiguous run of virtual blocks per CTA: mostly one job (its descriptor
     // stays in L1) and neighbouring planes (their rows are re-read from L1)
     const int per = (nvb + (int)gridDim.x - 1) / (int)gridDim.x;
@@ -340,8 +340,10 @@ struct micsa_pool {
     cudaStream_t capture_stream = nullptr;
     cudaStream_t aux_stream = nullptr;       // forked branch of a tick (resident kernel)
     cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
-    cudaStream_t chain_stream[kPoolChains] = {};  // forked branches: parts 1.. of the streaming jobs
-    cudaEvent_t chain_fork = nullptr, chain_join[kPoolChains] = {};
+    cudaStream_t chain_stream[kPoolMaxChains] = {};  // forked branches: parts 1.. of the streaming jobs
+    cudaEvent_t chain_fork = nullptr, chain_join[kPoolMaxChains] = {};
+    int chains = 2;     // concurrent kernel chains over the streaming jobs (1..kPoolMaxChains)
+    int max_words = 4;  // words per thread of a streaming job: the largest of 4, 2, 1 <= max_words dividing W
     bool tables_dirty = true;
     cudaEvent_t tables_free = nullptr;  // the last table upload has been consumed
     // per slot: pinned staging of the job's initial data (cut points + result
@@ -435,7 +437,6 @@ double schedule_T(const micsa_job_desc &d, int64_t k) {
 
 struct JobSizes {
     Geometry g;
-    int nw;
     size_t bonds, state, best, thr;
     int64_t n_refresh;
 };
@@ -443,7 +444,6 @@ struct JobSizes {
 JobSizes job_sizes(const micsa_job_desc &d) {
     JobSizes s;
     s.g = make_geometry(d.L);
-    s.nw = s.g.W % 4 == 0 ? 4 : s.g.W % 2 == 0 ? 2 : 1;
     s.bonds = (size_t)2 * s.g.half;
     s.state = (size_t)d.n_replicas * 2 * s.g.half;
     // natural layout (shared-memory jobs) or the split layout (streaming jobs)
@@ -452,6 +452,14 @@ JobSizes job_sizes(const micsa_job_desc &d) {
     if (s.n_refresh < 1) s.n_refresh = 1;
     s.thr = sizeof(uint64_t) * 3 * (size_t)s.n_refresh;
     return s;
+}
+
+// Words per thread of a streaming job: the largest of 4, 2, 1 that is at most
+// max_words and divides the row's W words (chunks tile the rows exactly).
+int pool_words(const Geometry &g, int max_words) {
+    for (int nw = 4; nw > 1; nw >>= 1)
+        if (nw <= max_words && g.W % nw == 0) return nw;
+    return 1;
 }
 
 // Rebuild the virtual-block table and upload both tables (descriptor rows and
@@ -491,10 +499,10 @@ int upload_tables(micsa_pool_t p) {
             p->h_vblocks[v].replica != p->h_vblocks[v - 1].replica)
             bounds.push_back(v);
     int prev = 0;
-    for (int c = 0; c < kPoolChains; ++c) {
+    for (int c = 0; c < kPoolMaxChains; ++c) {
         int end = nvb;
-        if (c + 1 < kPoolChains) {
-            const double target = (double)(c + 1) * nvb / kPoolChains;
+        if (c + 1 < p->chains) {
+            const double target = (double)(c + 1) * nvb / p->chains;
             int best = nvb;
             for (int v : bounds)
                 if (v >= prev && std::fabs(v - target) < std::fabs(best - target)) best = v;
@@ -509,7 +517,7 @@ int upload_tables(micsa_pool_t p) {
     std::memcpy(p->h_jobs_stage, p->h_jobs.data(), sizeof(JobDesc) * p->max_jobs);
     PCK(p, cudaMemcpyAsync(p->d_jobs, p->h_jobs_stage, sizeof(JobDesc) * p->max_jobs, cudaMemcpyHostToDevice, p->stream), "upload jobs");
     PCK(p, cudaMemcpyAsync(p->d_vblocks, p->h_vblocks, sizeof(VBlock) * (size_t)(nvb ? nvb : 1), cudaMemcpyHostToDevice, p->stream), "upload vblocks");
-    PCK(p, cudaMemcpyAsync(p->d_nvb, p->h_nvb, kPoolChains * sizeof(int32_t), cudaMemcpyHostToDevice, p->stream), "upload vblock counts");
+    PCK(p, cudaMemcpyAsync(p->d_nvb, p->h_nvb, kPoolMaxChains * sizeof(int32_t), cudaMemcpyHostToDevice, p->stream), "upload vblock counts");
     if (p->max_units) {
         PCK(p, cudaMemcpyAsync(p->d_units, p->h_units, sizeof(ResidentUnit) * (size_t)(nunits ? nunits : 1), cudaMemcpyHostToDevice, p->stream), "upload units");
         PCK(p, cudaMemcpyAsync(p->d_nunits, p->h_nunits, sizeof(int32_t), cudaMemcpyHostToDevice, p->stream), "upload unit count");
@@ -553,9 +561,9 @@ int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
         // the parts of the streaming jobs as concurrent chains, joined before
         // the measurement
         PCK(p, cudaEventRecord(p->chain_fork, st), "chain fork event");
-        for (int c = 1; c < kPoolChains; ++c)
+        for (int c = 1; c < p->chains; ++c)
             PCK(p, cudaStreamWaitEvent(p->chain_stream[c], p->chain_fork, 0), "chain fork wait");
-        for (int part = 0; part < kPoolChains; ++part) {
+        for (int part = 0; part < p->chains; ++part) {
             cudaStream_t cs = part == 0 ? st : p->chain_stream[part];
             for (int k = 0; k < p->K; ++k)
                 for (int par = 0; par < 2; ++par) {
@@ -565,7 +573,7 @@ int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
                         "pool half-sweep launch");
                 }
         }
-        for (int c = 1; c < kPoolChains; ++c) {
+        for (int c = 1; c < p->chains; ++c) {
             PCK(p, cudaEventRecord(p->chain_join[c], p->chain_stream[c]), "chain join event");
             PCK(p, cudaStreamWaitEvent(st, p->chain_join[c], 0), "chain join wait");
         }
@@ -587,7 +595,7 @@ int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
 }
 
 int tick_launches(micsa_pool_t p, int mask) {
-    return ((mask & 1) && p->resident_smem ? 1 : 0) + ((mask & 2) ? 2 * kPoolChains * p->K + 3 : 0) + 1;
+    return ((mask & 1) && p->resident_smem ? 1 : 0) + ((mask & 2) ? 2 * p->chains * p->K + 3 : 0) + 1;
 }
 
 int ensure_graph(micsa_pool_t p, int mask) {
@@ -650,7 +658,7 @@ int micsa_pool_create(size_t arena_bytes, int max_jobs, int tick_sweeps, micsa_p
         if ((e = cudaStreamCreateWithFlags(&p->capture_stream, cudaStreamNonBlocking)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         if ((e = cudaStreamCreateWithFlags(&p->aux_stream, cudaStreamNonBlocking)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&p->chain_fork, cudaEventDisableTiming)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
-        for (int c = 1; c < kPoolChains && e == cudaSuccess; ++c)
+        for (int c = 1; c < kPoolMaxChains && e == cudaSuccess; ++c)
             if ((e = cudaStreamCreateWithFlags(&p->chain_stream[c], cudaStreamNonBlocking)) == cudaSuccess)
                 e = cudaEventCreateWithFlags(&p->chain_join[c], cudaEventDisableTiming);
         if (e != cudaSuccess) { bail(MICSA_E_CUDA); break; }
@@ -662,7 +670,7 @@ int micsa_pool_create(size_t arena_bytes, int max_jobs, int tick_sweeps, micsa_p
         p->max_vblocks = 1 << 22;
         if ((e = cudaMalloc(&p->d_jobs, sizeof(JobDesc) * max_jobs)) != cudaSuccess ||
             (e = cudaMalloc(&p->d_vblocks, sizeof(VBlock) * (size_t)p->max_vblocks)) != cudaSuccess ||
-            (e = cudaMalloc(&p->d_nvb, kPoolChains * sizeof(int32_t))) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_nvb, kPoolMaxChains * sizeof(int32_t))) != cudaSuccess ||
             (e = cudaMalloc(&p->d_results, sizeof(long long) * 4 * (size_t)max_jobs * kPoolMaxR)) != cudaSuccess ||
             (e = cudaMalloc(&p->d_acc, sizeof(unsigned long long) * 2 * (size_t)max_jobs * kPoolMaxR)) != cudaSuccess ||
             (e = cudaMalloc(&p->d_improved, sizeof(int32_t) * (size_t)max_jobs * kPoolMaxR)) != cudaSuccess) { bail(MICSA_E_OOM); break; }
@@ -670,13 +678,13 @@ int micsa_pool_create(size_t arena_bytes, int max_jobs, int tick_sweeps, micsa_p
             (e = cudaMemsetAsync(p->d_improved, 0, sizeof(int32_t) * (size_t)max_jobs * kPoolMaxR, p->stream)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         if ((e = cudaMallocHost(&p->h_jobs_stage, sizeof(JobDesc) * max_jobs)) != cudaSuccess ||
             (e = cudaMallocHost(&p->h_vblocks, sizeof(VBlock) * (size_t)p->max_vblocks)) != cudaSuccess ||
-            (e = cudaMallocHost(&p->h_nvb, kPoolChains * sizeof(int32_t))) != cudaSuccess) { bail(MICSA_E_OOM); break; }
-        for (int c = 0; c < kPoolChains; ++c) p->h_nvb[c] = 0;
+            (e = cudaMallocHost(&p->h_nvb, kPoolMaxChains * sizeof(int32_t))) != cudaSuccess) { bail(MICSA_E_OOM); break; }
+        for (int c = 0; c < kPoolMaxChains; ++c) p->h_nvb[c] = 0;
         for (auto &ev : p->stage_free)
             if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         if (rc) break;
         if ((e = cudaMemsetAsync(p->d_jobs, 0, sizeof(JobDesc) * max_jobs, p->stream)) != cudaSuccess ||
-            (e = cudaMemsetAsync(p->d_nvb, 0, kPoolChains * sizeof(int32_t), p->stream)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+            (e = cudaMemsetAsync(p->d_nvb, 0, kPoolMaxChains * sizeof(int32_t), p->stream)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         // jobs of L <= 32 live in shared memory as bit planes (multispin kernel)
         p->resident_smem = multispin_smem_bytes(make_geometry(32));
         const int res_per_sm = multispin_blocks_per_sm(true, p->resident_smem);
@@ -741,7 +749,7 @@ void micsa_pool_destroy(micsa_pool_t p) {
     }
     if (p->fork_ev) cudaEventDestroy(p->fork_ev);
     if (p->join_ev) cudaEventDestroy(p->join_ev);
-    for (int c = 0; c < kPoolChains; ++c) {
+    for (int c = 0; c < kPoolMaxChains; ++c) {
         if (p->chain_stream[c]) {
             cudaStreamSynchronize(p->chain_stream[c]);
             cudaStreamDestroy(p->chain_stream[c]);
@@ -832,7 +840,7 @@ int micsa_pool_submit(micsa_pool_t p, const micsa_job_desc *job, int64_t *job_id
     D.thr = reinterpret_cast<const uint64_t *>(base + J.off_thr);
     D.geo = s.g;
     D.R = d.n_replicas;
-    D.nw = s.nw;
+    D.nw = pool_words(s.g, p->max_words);
     D.key0 = k0;
     D.key1 = k1;
     D.t = 0;
@@ -842,7 +850,7 @@ int micsa_pool_submit(micsa_pool_t p, const micsa_job_desc *job, int64_t *job_id
     const FastDiv fdL = make_fastdiv((uint32_t)d.L);
     D.divL_m = fdL.m;
     D.divL_l = fdL.l;
-    const FastDiv fdC = make_fastdiv((uint32_t)(s.g.W / s.nw));
+    const FastDiv fdC = make_fastdiv((uint32_t)(s.g.W / D.nw));
     D.divC_m = fdC.m;
     D.divC_l = fdC.l;
     D.resident = (p->resident_smem && multispin_smem_bytes(s.g) && multispin_smem_bytes(s.g) <= p->resident_smem) ? 1 : 0;
@@ -983,12 +991,36 @@ int micsa_pool_stats(micsa_pool_t p, int *live_jobs, size_t *free_bytes, int64_t
 }
 
 int micsa_pool_set_launch_config(micsa_pool_t p, int blocks_per_sm, int pdl, int use_graph) {
-    if (!p || blocks_per_sm < 1 || blocks_per_sm > 64) return MICSA_E_INVALID_ARG;
+    if (!p || blocks_per_sm < 0 || blocks_per_sm > 64) return MICSA_E_INVALID_ARG;
     PCK(p, cudaStreamSynchronize(p->stream), "synchronize before reconfiguring");
     drop_pool_graphs(p);
+    if (blocks_per_sm == 0) {  // as many as fit
+        PCK(p, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, pool_half_sweep_kernel, kVBlock, 0),
+            "occupancy query");
+        if (blocks_per_sm < 1) blocks_per_sm = 4;
+    }
     p->grid_blocks = blocks_per_sm * p->sm_count;
     p->pdl = pdl != 0;
     p->use_graph = use_graph != 0;
+    return MICSA_OK;
+}
+
+int micsa_pool_set_shape(micsa_pool_t p, int max_words, int chains) {
+    if (!p || (max_words != 1 && max_words != 2 && max_words != 4) || chains < 1 || chains > kPoolMaxChains)
+        return MICSA_E_INVALID_ARG;
+    PCK(p, cudaStreamSynchronize(p->stream), "synchronize before reshaping");
+    drop_pool_graphs(p);
+    p->max_words = max_words;
+    p->chains = chains;
+    for (int i = 0; i < p->max_jobs; ++i) {  // admitted streaming jobs take the new chunking too
+        JobDesc &D = p->h_jobs[i];
+        if (!p->slots[i].live || D.resident) continue;
+        D.nw = pool_words(D.geo, max_words);
+        const FastDiv fdC = make_fastdiv((uint32_t)(D.geo.W / D.nw));
+        D.divC_m = fdC.m;
+        D.divC_l = fdC.l;
+    }
+    p->tables_dirty = true;
     return MICSA_OK;
 }
 

@@ -213,3 +213,59 @@ def test_time_rescaling_fit_recovers_a_planted_factor():
     assert k == pytest.approx(6.0, rel=0.05)
     with pytest.raises(ValueError):
         analysis.fit_time_rescaling(t_ref, e_ref, t * 1e9, e, k_range=(1.0, 2.0))
+
+
+class FakeShapedPool:
+    """Pool stand-in whose tick costs depend on its shape (seconds on a fake clock)."""
+
+    def __init__(self, cost, tick_sweeps=8):
+        self.cost, self.tick_sweeps = cost, tick_sweeps
+        self.shape, self.blocks, self.now, self.submitted, self.ticks = (4, 2), 0, 0.0, [], 0
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+    def set_shape(self, w, c):
+        assert w in (1, 2, 4) and 1 <= c <= 4
+        self.shape = (w, c)
+
+    def set_launch_config(self, b):
+        assert 0 <= b <= 64
+        self.blocks = b
+
+    def submit(self, L, R, seed, n, interval, T0, T1):
+        self.submitted.append(n)
+        return len(self.submitted)
+
+    def tick(self):
+        self.ticks += 1
+        self.now += self.cost(self.shape, self.blocks)
+
+    def wait(self):
+        pass
+
+
+def test_pool_autotuner_picks_the_fastest_shape_then_grid():
+    def cost(shape, blocks):  # fastest shape (2, 3); at that shape 5 blocks per SM beat the default
+        base = 1.0 + 0.1 * abs(shape[0] - 2) + 0.05 * abs(shape[1] - 3)
+        return base - (0.2 if (shape == (2, 3) and blocks == 5) else 0.0)
+    fake = FakeShapedPool(cost)
+    jobs = [(48, 2, 1, 100, 10, 2.5, 0.5), (64, 1, 2, 50, 5, 2.0, 1.0)]
+    choice = autotune.tune_pool_for_jobs(lambda: fake, jobs, ticks=2, clock=lambda: fake.now)
+    assert (choice["max_words"], choice["chains"], choice["blocks_per_sm"]) == (2, 3, 5)
+    assert fake.shape == (2, 3) and fake.blocks == 5  # applied
+    assert choice["s_per_tick"] == pytest.approx(0.8)
+    # no job may finish while the candidates run: every candidate ticks 1 + 2 times
+    n_cand = len(autotune.pool_candidates()) + 5
+    assert fake.ticks == 3 * n_cand
+    assert all(n >= fake.ticks * fake.tick_sweeps for n in fake.submitted)
+
+
+def test_pool_autotuner_keeps_the_default_grid_when_no_grid_is_faster():
+    fake = FakeShapedPool(lambda shape, blocks: 1.0 + (0.0 if shape == (1, 1) else 0.5) + (0.1 if blocks else 0.0))
+    choice = autotune.tune_pool(fake, ticks=1, clock=lambda: fake.now)
+    assert (choice["max_words"], choice["chains"], choice["blocks_per_sm"]) == (1, 1, 0)
+    assert fake.shape == (1, 1) and fake.blocks == 0

@@ -26,16 +26,26 @@ def single_handle(L, R, seed, n, interval, T0, T1):
     return e, a, s
 
 
-def run_pool(jobs, K=16, arena=1 << 28, max_jobs=64, order=None):
+def run_pool(jobs, K=16, arena=1 << 28, max_jobs=64, order=None, shape=None, reshape=None):
+    """Run jobs to completion; shape: (max_words, chains, blocks_per_sm) set
+    before the submissions, reshape: one set after the first tick."""
     with micsa.Pool(arena, max_jobs, K) as p:
+        if shape:
+            p.set_shape(shape[0], shape[1])
+            p.set_launch_config(shape[2])
         ids = {}
         for idx in (order or range(len(jobs))):
             jid = p.submit(*jobs[idx])
             assert jid is not None
             ids[idx] = jid
         results = {}
+        ticks = 0
         while len(results) < len(jobs):
             p.tick()
+            ticks += 1
+            if reshape and ticks == 1:
+                p.set_shape(reshape[0], reshape[1])
+                p.set_launch_config(reshape[2])
             for idx, jid in ids.items():
                 if idx not in results:
                     r = p.poll(jid)
@@ -209,3 +219,39 @@ def test_serving_stream_results_match_alone():
         np.testing.assert_array_equal(r.result["aux"], a)
     s = serve.summarize(done, 1.0)
     assert s["p99_latency_s"] >= s["p50_latency_s"] > 0
+
+
+@pytest.mark.parametrize("shape,reshape", [
+    ((1, 1, 0), None), ((2, 3, 3), None), ((4, 4, 8), None), ((4, 2, 0), (1, 3, 2)), ((1, 4, 5), (4, 1, 0)),
+])
+def test_pool_results_identical_for_every_shape(shape, reshape):
+    """Words per thread, chains and grid (also changed between ticks, while the
+    jobs are live) do not change any job's result."""
+    jobs = JOBS + JOBS_STREAMED
+    ref = run_pool(jobs, K=4)
+    res = run_pool(jobs, K=4, shape=shape, reshape=reshape)
+    for idx in range(len(jobs)):
+        for k in ("energy", "aux", "best_energy", "best_t", "sweeps_done"):
+            np.testing.assert_array_equal(res[idx][k], ref[idx][k], err_msg=f"{jobs[idx]} {k}")
+        np.testing.assert_array_equal(res[idx]["best_spins"], ref[idx]["best_spins"], err_msg=str(jobs[idx]))
+
+
+def test_pool_shape_rejects_bad_values():
+    with micsa.Pool(1 << 24, 4, 4) as p:
+        for w, c in [(3, 2), (0, 2), (8, 1), (4, 0), (4, 5)]:
+            with pytest.raises(micsa.MicsaError):
+                p.set_shape(w, c)
+        with pytest.raises(micsa.MicsaError):
+            p.set_launch_config(65)
+
+
+def test_pool_autotuner_choice_is_valid_and_exact():
+    from paper_2506_16240_gb300 import autotune
+    jobs = JOBS_STREAMED + JOBS[8:]
+    choice = autotune.tune_pool_for_jobs(lambda: micsa.Pool(1 << 28, 64, 4), jobs, ticks=1)
+    assert choice["max_words"] in (1, 2, 4) and 1 <= choice["chains"] <= 4
+    assert 0 <= choice["blocks_per_sm"] <= 64 and choice["s_per_tick"] > 0
+    ref = run_pool(jobs, K=4)
+    res = run_pool(jobs, K=4, shape=(choice["max_words"], choice["chains"], choice["blocks_per_sm"]))
+    for idx in range(len(jobs)):
+        np.testing.assert_array_equal(res[idx]["energy"], ref[idx]["energy"], err_msg=str(jobs[idx]))
