@@ -417,44 +417,50 @@ def leg_paper_shape(micsa, timer, stream, peaks, L=160, R=128, sweeps=400):
     return out
 
 
-def leg_kstar(micsa, L=64, S=4, R=2, T=0.7, t_max=4096, gamma=6, stream=None):
+def leg_kstar(micsa, L=64, S=16, R=2, T=0.7, t_max=4096, gamma=6, stream=None):
     """Same-GPU Metropolis against MicSA with gamma walkers per spin on the same
     synthetic samples (couplings and starts from one seed) at T = 0.7: the energy
-    per spin on a log time grid, and the factor k with e_MicSA(t) =
-    e_Metropolis(k t), t in sweeps for Metropolis and in timesteps of gamma
-    sweeps for MicSA (the paper's k*, from xi_12 there, is 6.034 for six walkers
-    at T = 0.7)."""
+    per spin and the coherence length xi_12 (from C4 averaged over the samples, the
+    integrals cut at three standard errors)
+    on a log time grid, and the factor k with y_MicSA(t) = y_Metropolis(k t) for
+    each, t in sweeps for Metropolis and in timesteps of gamma sweeps for MicSA
+    (the paper's k*, from xi_12, is 6.034 for six walkers at T = 0.7)."""
     from paper_2506_16240_gb300 import analysis
     grid = sorted({int(round(10 ** (x / 10))) for x in range(0, int(10 * np.log10(t_max)) + 1)})
     N = L ** 3
 
     def curve(g, run, times):
-        out, t_prev = [], 0
+        e_out, xi_out, t_prev = [], [], 0
         for tm in times:
             if tm > t_prev:
                 run(g, tm - t_prev)
                 t_prev = tm
             e, _, _ = g.measure()
-            out.append(float(e.mean()) / N)
-        return np.array(out)
+            e_out.append(float(e.mean()) / N)
+            xi_out.append(analysis.xi_of_samples(g.c4()))
+        return np.array(e_out), np.array(xi_out)
 
     gm = micsa.Micsa(L, S, R, 21, stream=stream)
-    e_met = curve(gm, lambda g, n: g.run_metropolis(np.full(n, T)), grid)
+    e_met, xi_met = curve(gm, lambda g, n: g.run_metropolis(np.full(n, T)), grid)
     gm.close()
     gw = micsa.Micsa(L, S, R, 21, stream=stream, gamma=gamma, walkers=True)
     gw.set_engine("multispin_global")
     grid_w = [t for t in grid if t <= t_max // 3]
-    e_mic = curve(gw, lambda g, n: g.run_logrefresh(np.full(n, T)), grid_w)
+    e_mic, xi_mic = curve(gw, lambda g, n: g.run_logrefresh(np.full(n, T)), grid_w)
     gw.close()
-    tw = np.array(grid_w, np.float64)
+    tg, tw = np.array(grid, np.float64), np.array(grid_w, np.float64)
     sel = tw >= 16  # the refreshes at t = 2^s - 1 perturb the early energies
-    k, mis, npts = analysis.fit_time_rescaling(np.array(grid, np.float64), e_met, tw[sel], e_mic[sel], k_range=(1, 30))
-    return {"k_star_energy": k, "rms_mismatch": float(np.sqrt(mis)), "points": npts, "gamma": gamma,
+    k, mis, npts = analysis.fit_time_rescaling(tg, e_met, tw[sel], e_mic[sel], k_range=(1, 30))
+    kx, misx, nx = analysis.fit_time_rescaling(tg, xi_met, tw[sel], xi_mic[sel], k_range=(1, 30))
+    return {"k_star_energy": k, "rms_mismatch": float(np.sqrt(mis)), "points": npts,
+            "k_star_xi12": kx, "rms_mismatch_xi12": float(np.sqrt(misx)), "points_xi12": nx, "gamma": gamma,
             "workload": f"L={L}, {S} samples x {R} replicas, T={T}: Metropolis to {t_max} sweeps, "
                         f"MicSA with {gamma} walkers per spin (log refresh) to {grid_w[-1]} timesteps",
             "paper_k_star_xi12": 6.034,
             "e_metropolis": [[t, round(v, 6)] for t, v in zip(grid, e_met)][::3],
-            "e_micsa": [[t, round(v, 6)] for t, v in zip(grid_w, e_mic)][::3]}
+            "e_micsa": [[t, round(v, 6)] for t, v in zip(grid_w, e_mic)][::3],
+            "xi12_metropolis": [[t, round(v, 4)] for t, v in zip(grid, xi_met)][::3],
+            "xi12_micsa": [[t, round(v, 4)] for t, v in zip(grid_w, xi_mic)][::3]}
 
 
 def leg_metropolis(micsa, timer, stream, choice=None, n=10_000):

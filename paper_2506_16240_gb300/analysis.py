@@ -53,3 +53,38 @@ def fit_time_rescaling(t_ref, e_ref, t, e, k_range=(0.5, 50.0), min_points=4):
     k = float(np.exp(0.5 * (a + b)))
     m, n = rescaled_mismatch(t_ref, e_ref, t, e, k)
     return k, m, n
+
+
+def c4_integrals(c4, n_max=3, err=None, k_sigma=3.0):
+    """I_n = integral over r of r^n C4(r) (Sec. 3), n = 0..n_max, for C4 given
+    at the lattice distances r = 0..L-1 of a periodic lattice (C4(r) = C4(L - r)).
+    The integral is taken as the sum over r = 0..L/2, stopped before the first
+    r at which C4 is no longer above its noise: not positive, or, when the
+    standard errors err[r] of C4 are given, not above k_sigma of them (the paper
+    leaves the estimation details to its references). Returns (I_0..I_n_max,
+    the last r summed)."""
+    c4 = np.asarray(c4, np.float64)
+    floor = np.zeros_like(c4) if err is None else k_sigma * np.asarray(err, np.float64)
+    r_max = len(c4) // 2
+    stop = r_max
+    for r in range(1, r_max + 1):
+        if c4[r] <= floor[r]:
+            stop = r - 1
+            break
+    r = np.arange(stop + 1, dtype=np.float64)
+    return np.array([np.sum(r ** n * c4[:stop + 1]) for n in range(n_max + 1)]), stop
+
+
+def xi(c4, n=1, err=None, k_sigma=3.0):
+    """Characteristic length xi_{n,n+1} = I_{n+1} / I_n (Eq. (xi-def)); n = 1
+    gives the coherence length xi_12."""
+    I, _ = c4_integrals(c4, n + 1, err, k_sigma)
+    return float(I[n + 1] / I[n])
+
+
+def xi_of_samples(c4_samples, n=1, k_sigma=3.0):
+    """xi_{n,n+1} of the sample average of C4 (rows: samples), the integrals cut
+    where the average falls below k_sigma standard errors of the mean."""
+    c = np.asarray(c4_samples, np.float64)
+    err = c.std(axis=0, ddof=1) / np.sqrt(c.shape[0]) if c.shape[0] > 1 else None
+    return xi(c.mean(axis=0), n, err, k_sigma)
