@@ -442,11 +442,15 @@ def leg_kstar(micsa, L=64, S=16, R=2, T=0.7, t_max=4096, gamma=6, stream=None):
 
     gm = micsa.Micsa(L, S, R, 21, stream=stream)
     e_met, xi_met = curve(gm, lambda g, n: g.run_metropolis(np.full(n, T)), grid)
+    c4m = gm.c4()
+    ratio_met = analysis.xi_of_samples(c4m, 2) / analysis.xi_of_samples(c4m, 1)  # xi_23 / xi_12 at the end
     gm.close()
     gw = micsa.Micsa(L, S, R, 21, stream=stream, gamma=gamma, walkers=True)
     gw.set_engine("multispin_global")
     grid_w = [t for t in grid if t <= t_max // 3]
     e_mic, xi_mic = curve(gw, lambda g, n: g.run_logrefresh(np.full(n, T)), grid_w)
+    c4w = gw.c4()
+    ratio_mic = analysis.xi_of_samples(c4w, 2) / analysis.xi_of_samples(c4w, 1)
     gw.close()
     tg, tw = np.array(grid, np.float64), np.array(grid_w, np.float64)
     sel = tw >= 16  # the refreshes at t = 2^s - 1 perturb the early energies
@@ -454,6 +458,7 @@ def leg_kstar(micsa, L=64, S=16, R=2, T=0.7, t_max=4096, gamma=6, stream=None):
     kx, misx, nx = analysis.fit_time_rescaling(tg, xi_met, tw[sel], xi_mic[sel], k_range=(1, 30))
     return {"k_star_energy": k, "rms_mismatch": float(np.sqrt(mis)), "points": npts,
             "k_star_xi12": kx, "rms_mismatch_xi12": float(np.sqrt(misx)), "points_xi12": nx, "gamma": gamma,
+            "xi23_over_xi12_final": {"metropolis": ratio_met, "micsa": ratio_mic},
             "workload": f"L={L}, {S} samples x {R} replicas, T={T}: Metropolis to {t_max} sweeps, "
                         f"MicSA with {gamma} walkers per spin (log refresh) to {grid_w[-1]} timesteps",
             "paper_k_star_xi12": 6.034,
@@ -496,6 +501,7 @@ def leg_metropolis(micsa, timer, stream, choice=None, n=10_000):
 
 
 def leg_quench_l32(micsa, timer, stream):
+    from paper_2506_16240_gb300 import analysis
     L, S, R, T, n, r = 32, 64, 2, 0.7, 10_000, 10
     N = L ** 3
     grid = sorted(set([0] + [int(10 ** (k / 8)) for k in range(0, 33)]))
@@ -509,15 +515,17 @@ def leg_quench_l32(micsa, timer, stream):
             total_ms += timer(lambda: g.run(np.full(tm - t_prev, T), r))
             t_prev = tm
         e, a, q = g.measure()
-        series.append((tm, float(e.mean() / N), float(((q / N) ** 2).mean())))
+        xi12 = analysis.xi_of_samples(g.c4()) if tm > 0 else 0.0  # outside the timed runs
+        series.append((tm, float(e.mean() / N), float(((q / N) ** 2).mean()), xi12))
     eng = g.engine()
     c4 = g.c4().mean(axis=0)  # four-point correlation at t = 1e4, averaged over samples
     g.close()
     return {"value": updates(L, S, R, n) / (total_ms * 1e6), "unit": METRIC, "engine": eng, "launch": tuned,
             "c4_final": [round(float(v), 6) for v in c4[: L // 2 + 1]],
             "workload": "L=32, 64 samples x 2 replicas, T=0.7, 1e4 sweeps, refresh every 10",
-            "e_final": series[-1][1], "q2_final": series[-1][2],
-            "e_q2_vs_t": [[t, round(e, 6), round(q2, 8)] for t, e, q2 in series[::4]] + [list(series[-1])]}
+            "e_final": series[-1][1], "q2_final": series[-1][2], "xi12_final": series[-1][3],
+            "e_q2_xi12_vs_t": [[t, round(e, 6), round(q2, 8), round(x, 4)] for t, e, q2, x in series[::4]]
+            + [list(series[-1])]}
 
 
 def c4_instances():

@@ -152,36 +152,30 @@ __device__ __forceinline__ RoundKeys round_keys(uint32_t key0, uint32_t key1) {
     return r;
 }
 
-__device__ __forceinline__ uint4 philox_rk(uint4 c, const RoundKeys &rk) {
+// Philox4x32-10 with the round keys precomputed, each round's two products
+// taken as one 32 x 32 -> 64-bit multiply (high word and low word of the same
+// product).
+__device__ __forceinline__ uint4 philox_wide(uint4 c, const RoundKeys &rk) {
 #pragma unroll
     for (int r = 0; r < 10; ++r) {
-        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
-        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
-        c = make_uint4(hi1 ^ c.y ^ rk.k0[r], lo1, hi0 ^ c.w ^ rk.k1[r], lo0);
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x, p1 = (uint64_t)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk.k0[r], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ rk.k1[r],
+                       (uint32_t)p0);
     }
     return c;
 }
 
-// Cut points as 32-bit compares: [u >= c] with c <= 2^32; c == 2^32 never holds.
-struct Cuts {
-    uint32_t c[3];
-    bool ok[3];
+// Refresh cut points as strict 32-bit compares: [u >= c] = [u > c - 1]. Valid
+// for 1 <= c <= 2^32; every cut point is >= floor(2^32 p(0)) >= 2^30, since
+// p(0) = 1 / (1 + x + x^2 + x^3) >= 1/4 for x = exp(-4 beta) <= 1. With the
+// cut points increasing, m = [u >= c0] + [u >= c1] + [u >= c2] has bit 1 =
+// [u >= c1] and bit 0 = the parity of the three.
+struct CutsGt {
+    uint32_t c0m, c1m, c2m;
 };
 
-__device__ __forceinline__ Cuts make_cuts(uint64_t th0, uint64_t th1, uint64_t th2) {
-    Cuts k;
-    const uint64_t t[3] = {th0, th1, th2};
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-        k.ok[i] = t[i] <= 0xFFFFFFFFull;
-        k.c[i] = (uint32_t)t[i];
-    }
-    return k;
-}
-
-__device__ __forceinline__ uint32_t daemon_cut(uint32_t u, const Cuts &k) {
-    return (uint32_t)(k.ok[0] & (u >= k.c[0])) + (uint32_t)(k.ok[1] & (u >= k.c[1])) +
-           (uint32_t)(k.ok[2] & (u >= k.c[2]));
+__device__ __forceinline__ CutsGt make_cuts_gt(uint64_t th0, uint64_t th1, uint64_t th2) {
+    return {(uint32_t)(th0 - 1), (uint32_t)(th1 - 1), (uint32_t)(th2 - 1)};
 }
 
 // Daemon bit planes of words (p, y, i), i = 4q .. 4q+3, for the refresh at
@@ -189,24 +183,21 @@ __device__ __forceinline__ uint32_t daemon_cut(uint32_t u, const Cuts &k) {
 // + q, lane i & 3 of the block for word i (the library's counter contract) --
 // and the warp votes the two daemon bit planes of the four words.
 __device__ __forceinline__ void ms_refresh_warp(const MsPlanes &P, const Geometry &g, int p, int y, int q,
-                                                uint32_t gid, const RoundKeys &rk, int64_t t, const Cuts &cut) {
+                                                uint32_t gid, const RoundKeys &rk, int64_t t, const CutsGt &cut) {
     const int lane = threadIdx.x & 31;
-    uint32_t m[4] = {0, 0, 0, 0};
+    uint4 w = make_uint4(0, 0, 0, 0);  // lanes z >= L: u = 0 is below every cut point, m = 0
     if (lane < g.L) {
         const uint32_t quad = (uint32_t)((((int64_t)p * g.L + lane) * g.L + y) * g.W + q);
-        const uint4 w = philox_rk(
-            make_uint4(quad, (uint32_t)t, (gid << 2) | kTagDaemon, (uint32_t)((uint64_t)t >> 32)), rk);
-        m[0] = daemon_cut(w.x, cut);
-        m[1] = daemon_cut(w.y, cut);
-        m[2] = daemon_cut(w.z, cut);
-        m[3] = daemon_cut(w.w, cut);
+        w = philox_wide(make_uint4(quad, (uint32_t)t, (gid << 2) | kTagDaemon, (uint32_t)((uint64_t)t >> 32)), rk);
     }
+    const uint32_t u[4] = {w.x, w.y, w.z, w.w};
     // planes (m0, m1) of the four words; lane j < 8 stores plane j & 1 of word j >> 1
     uint32_t mine = 0;
 #pragma unroll
     for (int l = 0; l < 4; ++l) {
-        const uint32_t a = __ballot_sync(0xFFFFFFFFu, m[l] & 1u);
-        const uint32_t c = __ballot_sync(0xFFFFFFFFu, m[l] >> 1);
+        const bool g0 = u[l] > cut.c0m, g1 = u[l] > cut.c1m, g2 = u[l] > cut.c2m;
+        const uint32_t a = __ballot_sync(0xFFFFFFFFu, g0 ^ g1 ^ g2);
+        const uint32_t c = __ballot_sync(0xFFFFFFFFu, g1);
         if (lane == 2 * l) mine = a;
         if (lane == 2 * l + 1) mine = c;
     }
@@ -352,7 +343,7 @@ __global__ void __launch_bounds__(kMsThreads, 2) multispin_kernel(ResidentArgs A
             }
             for (int p = 0; p < 2; ++p) {
                 if (refresh) {  // fresh daemons of parity p before its half-sweep (Sec. 2.7)
-                    const Cuts cut = make_cuts(th0, th1, th2);
+                    const CutsGt cut = make_cuts_gt(th0, th1, th2);
                     const int items = g.L * g.W;
                     for (int it = threadIdx.x >> 5; it < items; it += blockDim.x >> 5)
                         ms_refresh_warp(P, g, p, it / g.W, it % g.W, (uint32_t)U.gid, rk, t, cut);
@@ -493,29 +484,6 @@ struct MsgArgs {
     int64_t k;
     FastDiv div_groups, div_L;  // thread index -> (zw, y, word group)
 };
-
-// Philox4x32-10 as philox_rk, each round's two products taken as one 32 x 32
-// -> 64-bit multiply (high word and low word of the same product).
-__device__ __forceinline__ uint4 philox_wide(uint4 c, const RoundKeys &rk) {
-#pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x, p1 = (uint64_t)0xCD9E8D57u * c.z;
-        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk.k0[r], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ rk.k1[r],
-                       (uint32_t)p0);
-    }
-    return c;
-}
-
-// Refresh cut points as strict 32-bit compares: [u >= c] = [u > c - 1]. Valid
-// for 1 <= c <= 2^32; every cut point is >= floor(2^32 p(0)) >= 2^30, since
-// p(0) = 1 / (1 + x + x^2 + x^3) >= 1/4 for x = exp(-4 beta) <= 1.
-struct CutsGt {
-    uint32_t c0m, c1m, c2m;
-};
-
-__device__ __forceinline__ CutsGt make_cuts_gt(uint64_t th0, uint64_t th1, uint64_t th2) {
-    return {(uint32_t)(th0 - 1), (uint32_t)(th1 - 1), (uint32_t)(th2 - 1)};
-}
 
 __device__ __forceinline__ void prefetch_l2(const uint32_t *p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
