@@ -485,6 +485,18 @@ struct MsgArgs {
     FastDiv div_groups, div_L;  // thread index -> (zw, y, word group)
 };
 
+// x_k = 2 x_k + [u > c_k] for three cut points given as n_k = ~c_k: the carry
+// out of u + ~c is set exactly when u > c, and addc shifts it in.
+__device__ __forceinline__ void shift_in_cuts(uint32_t u, uint32_t n0, uint32_t n1, uint32_t n2, uint32_t &x0,
+                                              uint32_t &x1, uint32_t &x2) {
+    asm("{\n\t.reg .u32 t;\n\t"
+        "add.cc.u32 t, %3, %4;\n\taddc.u32 %0, %0, %0;\n\t"
+        "add.cc.u32 t, %3, %5;\n\taddc.u32 %1, %1, %1;\n\t"
+        "add.cc.u32 t, %3, %6;\n\taddc.u32 %2, %2, %2;\n\t}"
+        : "+r"(x0), "+r"(x1), "+r"(x2)
+        : "r"(u), "r"(n0), "r"(n1), "r"(n2));
+}
+
 __device__ __forceinline__ void prefetch_l2(const uint32_t *p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
@@ -629,7 +641,10 @@ __global__ void __launch_bounds__(128, MINB) msg_half_kernel(MsgArgs a) {
             // z = 32 zw + b for b in this lane's range, from the top down: each new
             // bit enters at the bottom (a = 2 a + bit); m1 = [u >= c1], m0 = the parity
             // of [u >= c0] + [u >= c1] + [u >= c2]
-            uint32_t a0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0};
+            // x_k collects [u > c_k - 1] for the three cut points, one bit per z;
+            // m0 = x_0 ^ x_1 ^ x_2 and m1 = x_1 (the cut points increase)
+            uint32_t x0[4] = {0, 0, 0, 0}, a1[4] = {0, 0, 0, 0}, x2[4] = {0, 0, 0, 0};
+            const uint32_t n0 = ~gcut.c0m, n1 = ~gcut.c1m, n2 = ~gcut.c2m;
 #pragma unroll 2
             for (int c = 32 / G - 1; c >= 0; --c) {
                 const int b = lig * (32 / G) + c;
@@ -638,15 +653,12 @@ __global__ void __launch_bounds__(128, MINB) msg_half_kernel(MsgArgs a) {
                                             rk);
                 const uint32_t u[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const uint32_t g0 = u[j] > gcut.c0m, g1 = u[j] > gcut.c1m, g2 = u[j] > gcut.c2m;
-                    a0[j] = 2 * a0[j] + (g0 ^ g1 ^ g2);
-                    a1[j] = 2 * a1[j] + g1;
-                }
+                for (int j = 0; j < 4; ++j) shift_in_cuts(u[j], n0, n1, n2, x0[j], a1[j], x2[j]);
             }
+            uint32_t a0[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                a0[j] <<= lig * (32 / G);
+                a0[j] = (x0[j] ^ a1[j] ^ x2[j]) << (lig * (32 / G));
                 a1[j] <<= lig * (32 / G);
             }
 #pragma unroll
