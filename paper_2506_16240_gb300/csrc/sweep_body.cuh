@@ -65,9 +65,10 @@ __device__ __forceinline__ void update_chunk(const Geometry &g, int8_t *spins, u
     if constexpr (FULL) {
         // o = 0: the byte before the range, or the row's last byte at the row's start
         // o = 1: the byte after the range, or the row's first byte at the row's end
-        const int8_t *e = o == 0 ? (b0 == 0 ? opp + row0 + g.Lh - 1 : opp + off_c - 1)
-                                 : (b0 + 4 * NW < g.Lh ? opp + off_c + 4 * NW : opp + row0);
-        edge = last = load_byte<SMEM>(e);
+        // selected as an offset within the parity half: one pointer add, not four
+        const Off eo = o == 0 ? (b0 == 0 ? row0 + (Off)(g.Lh - 1) : off_c - 1)
+                              : (b0 + 4 * NW < g.Lh ? off_c + (Off)(4 * NW) : row0);
+        edge = last = load_byte<SMEM>(opp + eo);
     } else if (o == 0) {
         if (b0 == 0) last = load_byte<SMEM>(opp + row0 + g.Lh - 1);
         else edge = load_byte<SMEM>(opp + off_c - 1);
