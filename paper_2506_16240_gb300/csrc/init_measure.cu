@@ -1,6 +1,8 @@
 // init_measure.cu -- coupling and spin initialisation from the seed, layout
 // conversion between the caller's natural order and the sublattice-split
 // device layout, and the exact integer observables of Sec. 3 / App. C.
+#include <algorithm>
+
 #include "micsa_internal.h"
 
 namespace micsa {
@@ -158,6 +160,24 @@ cudaError_t launch_unpack_couplings(int8_t *J_nat, const uint8_t *bonds, Geometr
                                     cudaStream_t st) {
     const int64_t n = (int64_t)g.L * g.L * g.L * S;
     unpack_couplings_kernel<<<blocks_for(n, 256), 256, 0, st>>>(J_nat, bonds, g, S);
+    return cudaGetLastError();
+}
+
+// Index of the first byte of v[0, n) that is not a spin or coupling (+-1,
+// mode 0) or not a daemon value (0..3, mode 1), min-reduced into *first, which
+// the launcher presets to all ones (no such byte).
+__global__ void first_invalid_kernel(const uint8_t *v, int64_t n, int mode, unsigned long long *first) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t b = v[i];
+        if (mode == 0 ? (b != 0x01u && b != 0xFFu) : (b > 3u)) atomicMin(first, (unsigned long long)i);
+    }
+}
+
+cudaError_t launch_first_invalid(const uint8_t *v, int64_t n, int mode, unsigned long long *first,
+                                 cudaStream_t st) {
+    if (cudaError_t e = cudaMemsetAsync(first, 0xFF, sizeof(unsigned long long), st)) return e;
+    const unsigned blocks = n <= 0 ? 1u : std::min(blocks_for(n, 256), 4096u);  // grid-stride beyond
+    first_invalid_kernel<<<blocks, 256, 0, st>>>(v, n, mode, first);
     return cudaGetLastError();
 }
 

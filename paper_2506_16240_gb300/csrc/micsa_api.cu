@@ -27,6 +27,7 @@ struct micsa_ctx {
     uint8_t *d_bonds = nullptr;
     unsigned long long *d_meas = nullptr;
     uint8_t *d_stage = nullptr;  // natural-layout staging for state / coupling copies
+    unsigned long long *d_first = nullptr;  // first invalid byte of a staged copy
     size_t stage_bytes = 0;
     size_t device_bytes = 0;
     int64_t launches = 0;  // kernels launched by this handle
@@ -125,6 +126,24 @@ int ensure_stage(micsa_t h, size_t bytes) {
     CK(h, cudaMalloc(&h->d_stage, bytes), "cudaMalloc staging");
     h->stage_bytes = bytes;
     h->device_bytes += bytes;
+    return MICSA_OK;
+}
+
+// Index of the first invalid byte of n staged bytes at dev (mode 0: +-1,
+// mode 1: 0..3) in *first, -1 if there is none; checked on the device, so that
+// a caller's buffer is read once (by the copy) and the state is untouched when
+// it is rejected.
+int staged_first_invalid(micsa_t h, const uint8_t *dev, int64_t n, int mode, int64_t *first) {
+    if (!h->d_first) {
+        CK(h, cudaMalloc(&h->d_first, sizeof(unsigned long long)), "cudaMalloc check word");
+        h->device_bytes += sizeof(unsigned long long);
+    }
+    CK(h, launch_first_invalid(dev, n, mode, h->d_first, h->stream), "validate staged bytes");
+    ++h->launches;
+    unsigned long long v = 0;
+    CK(h, cudaMemcpyAsync(&v, h->d_first, sizeof v, cudaMemcpyDeviceToHost, h->stream), "read check word");
+    CK(h, cudaStreamSynchronize(h->stream), "validate synchronize");
+    *first = v == ~0ull ? -1 : (int64_t)v;
     return MICSA_OK;
 }
 
@@ -661,6 +680,7 @@ void micsa_destroy(micsa_t h) {
     cudaFree(h->d_bonds);
     cudaFree(h->d_meas);
     cudaFree(h->d_stage);
+    cudaFree(h->d_first);
     cudaFree(h->d_cursor);
     cudaFree(h->d_units);
     cudaFree(h->d_planes);
@@ -755,11 +775,12 @@ int micsa_set_couplings(micsa_t h, const int8_t *J) {
     if (!h) return MICSA_E_INVALID_ARG;
     if (!J) return fail(h, MICSA_E_INVALID_ARG, "J is NULL");
     const int64_t n = sites(h) * 3 * h->S;
-    for (int64_t i = 0; i < n; ++i)
-        if (J[i] != 1 && J[i] != -1) return fail(h, MICSA_E_INVALID_ARG, "J[%lld] = %d is not +-1", (long long)i, J[i]);
     DeviceGuard dg(h->device);
     if (int rc = ensure_stage(h, (size_t)n)) return rc;
     CK(h, cudaMemcpyAsync(h->d_stage, J, (size_t)n, cudaMemcpyHostToDevice, h->stream), "copy J");
+    int64_t bad = -1;
+    if (int rc = staged_first_invalid(h, h->d_stage, n, 0, &bad)) return rc;
+    if (bad >= 0) return fail(h, MICSA_E_INVALID_ARG, "J[%lld] = %d is not +-1", (long long)bad, J[bad]);
     CK(h, launch_pack_couplings(h->d_bonds, reinterpret_cast<const int8_t *>(h->d_stage), h->geo, h->S, h->stream), "pack couplings");
     ++h->launches;
     CK(h, cudaStreamSynchronize(h->stream), "set_couplings synchronize");
@@ -979,28 +1000,33 @@ int micsa_set_state(micsa_t h, const int8_t *spins, const uint8_t *daemons, int6
     const int64_t n = (int64_t)h->S * h->R;
     const size_t bytes = (size_t)(n * sites(h));
     const size_t dbytes = bytes * (size_t)h->gamma;
-    if (spins)
-        for (size_t i = 0; i < bytes; ++i)
-            if (spins[i] != 1 && spins[i] != -1) return fail(h, MICSA_E_INVALID_ARG, "spins[%zu] = %d is not +-1", i, spins[i]);
-    if (daemons)
-        for (size_t i = 0; i < dbytes; ++i)
-            if (daemons[i] > 3) return fail(h, MICSA_E_INVALID_ARG, "daemons[%zu] = %u exceeds 3", i, daemons[i]);
     DeviceGuard dg(h->device);
-    if (spins || daemons) {
-        if (int rc = ensure_stage(h, dbytes)) return rc;
+    const size_t total = (spins ? bytes : 0) + (daemons ? dbytes : 0);
+    if (total) {
+        if (int rc = ensure_stage(h, total)) return rc;
     }
+    uint8_t *s_stage = h->d_stage, *m_stage = h->d_stage + (spins ? bytes : 0);
+    // both arrays are copied and checked on the device before either is written
+    int64_t bad = -1;
     if (spins) {
-        CK(h, cudaMemcpyAsync(h->d_stage, spins, bytes, cudaMemcpyHostToDevice, h->stream), "copy spins");
-        CK(h, launch_convert_sites(reinterpret_cast<uint8_t *>(h->d_spins), h->d_stage, h->geo, n, true, h->stream), "scatter spins");
-        ++h->launches;
-        CK(h, cudaStreamSynchronize(h->stream), "set_state synchronize");
+        CK(h, cudaMemcpyAsync(s_stage, spins, bytes, cudaMemcpyHostToDevice, h->stream), "copy spins");
+        if (int rc = staged_first_invalid(h, s_stage, (int64_t)bytes, 0, &bad)) return rc;
+        if (bad >= 0) return fail(h, MICSA_E_INVALID_ARG, "spins[%lld] = %d is not +-1", (long long)bad, spins[bad]);
     }
     if (daemons) {
-        CK(h, cudaMemcpyAsync(h->d_stage, daemons, dbytes, cudaMemcpyHostToDevice, h->stream), "copy daemons");
-        CK(h, launch_convert_sites(h->d_daemons, h->d_stage, h->geo, n * h->gamma, true, h->stream), "scatter daemons");
-        ++h->launches;
-        CK(h, cudaStreamSynchronize(h->stream), "set_state synchronize");
+        CK(h, cudaMemcpyAsync(m_stage, daemons, dbytes, cudaMemcpyHostToDevice, h->stream), "copy daemons");
+        if (int rc = staged_first_invalid(h, m_stage, (int64_t)dbytes, 1, &bad)) return rc;
+        if (bad >= 0) return fail(h, MICSA_E_INVALID_ARG, "daemons[%lld] = %u exceeds 3", (long long)bad, daemons[bad]);
     }
+    if (spins) {
+        CK(h, launch_convert_sites(reinterpret_cast<uint8_t *>(h->d_spins), s_stage, h->geo, n, true, h->stream), "scatter spins");
+        ++h->launches;
+    }
+    if (daemons) {
+        CK(h, launch_convert_sites(h->d_daemons, m_stage, h->geo, n * h->gamma, true, h->stream), "scatter daemons");
+        ++h->launches;
+    }
+    if (total) CK(h, cudaStreamSynchronize(h->stream), "set_state synchronize");
     h->t = t;
     return MICSA_OK;
 }

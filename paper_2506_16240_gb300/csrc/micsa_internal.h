@@ -217,6 +217,8 @@ cudaError_t launch_pack_couplings(uint8_t *bonds, const int8_t *J_nat, Geometry 
 cudaError_t launch_unpack_couplings(int8_t *J_nat, const uint8_t *bonds, Geometry g, int S,
                                     cudaStream_t st);
 // natural [n][N] <-> split [n][2][half]; `to_split` selects the direction
+cudaError_t launch_first_invalid(const uint8_t *v, int64_t n, int mode, unsigned long long *first,
+                                 cudaStream_t st);
 cudaError_t launch_convert_sites(uint8_t *split, uint8_t *natural, Geometry g, int64_t n,
                                  bool to_split, cudaStream_t st);
 cudaError_t launch_measure(const int8_t *spins, const uint8_t *daemons, const uint8_t *bonds,

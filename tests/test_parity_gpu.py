@@ -559,3 +559,35 @@ def test_maximum_size_conservation_and_engine_agreement():
             assert -3 * L ** 3 <= int(e1[0]) <= 3 * L ** 3
             sums[engine] = (int(e0[0]), int(a0[0]), int(e1[0]), int(a1[0]))
     assert sums["stream"] == sums["multispin_global"]
+
+
+def test_invalid_couplings_and_states_are_rejected_without_changing_the_state():
+    """Couplings must be +-1, spins +-1 and daemons 0..3: the first bad entry is
+    named and nothing on the device changes (checked on the device copy)."""
+    L, S, R = 12, 2, 2
+    N = L ** 3
+    with micsa.Micsa(L, S, R, 5) as g:
+        g.run(np.full(7, 1.2), 3)
+        s0, m0, t0 = g.get_state()
+        e0, a0, q0 = g.measure()
+        J0 = g.get_couplings()
+        J = np.ones((S, N, 3), np.int8)
+        J[1, 1000, 2] = 0
+        with pytest.raises(micsa.MicsaError, match=str(N * 3 + 1000 * 3 + 2)):
+            g.set_couplings(J)
+        spins = s0.copy()
+        spins[1, 0, 77] = 3
+        with pytest.raises(micsa.MicsaError, match=str(N * R + 77)):
+            g.set_state(spins, m0, t0)
+        daemons = m0.copy()
+        daemons[-1, -1, -1] = 4  # valid spins, bad daemons: neither is written
+        with pytest.raises(micsa.MicsaError, match=str(S * R * N - 1)):
+            g.set_state(-s0, daemons, t0)
+        s1, m1, t1 = g.get_state()
+        e1, a1, q1 = g.measure()
+        np.testing.assert_array_equal(s1, s0)
+        np.testing.assert_array_equal(m1, m0)
+        assert t1 == t0
+        np.testing.assert_array_equal(e1, e0)
+        np.testing.assert_array_equal(a1, a0)
+        np.testing.assert_array_equal(g.get_couplings(), J0)
