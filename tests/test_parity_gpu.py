@@ -591,3 +591,31 @@ def test_invalid_couplings_and_states_are_rejected_without_changing_the_state():
         np.testing.assert_array_equal(e1, e0)
         np.testing.assert_array_equal(a1, a0)
         np.testing.assert_array_equal(g.get_couplings(), J0)
+
+
+def test_equilibrium_energy_at_T14_is_the_canonical_value():
+    """Plausibility, not parity: at T = 1.4 (paramagnetic) the paper's canonical fit
+    (Table (fit-info), App. A) gives e_inf = -1.607026(4) per spin on its L = 160
+    sample; the energy is self-averaging (Sec. 3), so a synthetic L = 160 sample
+    lands within its sample-to-sample spread (~5e-4 at N = 4.1e6). MicSA with
+    daemons refreshed every 10 sweeps has the canonical measure as its stationary
+    measure (Creutz moves conserve H_EA + H_aux and are reversible; the refresh
+    draws canonical daemons), so MicSA and Metropolis settle at the same energy."""
+    L, T, relax, chunk, n_chunks = 160, 1.4, 20_000, 1_000, 8
+
+    def equilibrium(run):
+        with micsa.Micsa(L, 1, 2, 17) as g:
+            run(g, relax)
+            es = []
+            for _ in range(n_chunks):
+                run(g, chunk)
+                e, _, _ = g.measure()
+                es.append(e.mean() / L ** 3)
+            return float(np.mean(es))
+
+    e_mic = equilibrium(lambda g, n: g.run(np.full(n, T), 10))
+    e_met = equilibrium(lambda g, n: g.run_metropolis(np.full(n, T)))
+    print(f"T = 1.4, L = 160: e_MicSA = {e_mic:.6f}, e_Metropolis = {e_met:.6f}, canonical fit -1.607026")
+    assert abs(e_mic - -1.607026) < 2.5e-3, e_mic
+    assert abs(e_met - -1.607026) < 2.5e-3, e_met
+    assert abs(e_mic - e_met) < 1e-3, (e_mic, e_met)
