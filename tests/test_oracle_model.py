@@ -492,3 +492,55 @@ def test_correlation_identical_replicas_is_one():
     st = O.create(L, 1, 2, 5)
     st["s"][0, 1] = st["s"][0, 0]
     np.testing.assert_array_equal(O.correlation(st)[0], 3 * L ** 3)
+
+
+def acceptance_z_scores(orc, L=16, T=3.0, seed=41, refreshes=60):
+    """Per dE class over the even sites of an L lattice and `refreshes` fresh daemon
+    draws: (accepted fraction - closed form) / standard error, and the class counts."""
+    x = np.exp(-4.0 / T)
+    J = orc.couplings(L, seed)
+    s = orc.spins(L, seed, 0)
+    sites = np.arange(L ** 3)
+    xs, ys, zs = sites % L, (sites // L) % L, sites // (L * L)
+    even = sites[(xs + ys + zs) % 2 == 0]
+    acc, tot = {}, {}
+    for t in range(refreshes):
+        m = orc.refresh(L, seed, 0, t, T)
+        dE = np.array([orc.delta_h(L, J, s, int(i)) for i in even])
+        s_new, m_new = s.copy(), m.copy()
+        orc.half_sweep(L, J, s_new, m_new, 0)
+        flipped = s_new[even] != s[even]
+        for d in np.unique(dE):
+            sel = dE == d
+            acc[d] = acc.get(d, 0) + int(flipped[sel].sum())
+            tot[d] = tot.get(d, 0) + int(sel.sum())
+        orc.half_sweep(L, J, s_new, m_new, 1)  # move the odd sites too: new local fields
+        s = s_new
+    z = {}
+    for d in sorted(tot):
+        j = abs(d) // 4
+        p = (x ** j - x ** 4) / (1 - x ** 4) if d > 0 else (1 - x ** (4 - j)) / (1 - x ** 4)
+        se = np.sqrt(max(p * (1 - p), 1e-12) / tot[d])
+        z[d] = (acc[d] / tot[d] - p) / se
+    return z, tot
+
+
+def test_acceptance_with_fresh_daemons_follows_the_truncated_geometric_law():
+    """With the daemons drawn fresh before a half-sweep, p(m) = x^m / (1 + x + x^2 + x^3),
+    x = exp(-4/T), m = 0..3 (Eq. (prob-daemons-walkers)), and Eq. (flip-OK): a flip that
+    costs dE = 4j > 0 is accepted iff m >= j, with probability (x^j - x^4) / (1 - x^4);
+    one that gains dE = -4j <= 0 iff the daemon can hold the surplus, m <= 3 - j, with
+    probability (1 - x^(4 - j)) / (1 - x^4). Frequencies per dE class over the even
+    sites of an L = 16 lattice and 60 refreshes agree within 5 standard errors."""
+    z, tot = acceptance_z_scores(O)
+    assert set(tot) == {-12, -8, -4, 0, 4, 8, 12}
+    assert min(tot.values()) > 100  # every class is sampled
+    assert max(abs(v) for v in z.values()) <= 5.0, z
+
+
+@pytest.mark.parametrize("mutant", [1, 2, 4])
+def test_planted_mistakes_break_the_acceptance_law(mutant):
+    # capacity one step too large, the daemon absorbing the wrong sign, a wrong
+    # Boltzmann factor in the refresh: each moves some class far outside 5 errors
+    z, _ = acceptance_z_scores(oracle.Oracle(mutant=mutant))
+    assert max(abs(v) for v in z.values()) > 10.0, z
