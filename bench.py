@@ -407,10 +407,11 @@ def leg_paper_shape(micsa, timer, stream, peaks, L=160, R=128, sweeps=400):
     g6 = micsa.Micsa(L, 1, R, 12, stream=stream, gamma=6, walkers=True)
     g6.set_engine("multispin_global")
     g6.set_launch_config(out["multispin_launch"]["words_per_thread"], 128, -1, True, 64)
-    g6.run_logrefresh(np.full(16, 0.7))
-    ms = timer(lambda: g6.run_logrefresh(np.full(32, 0.7)))
+    # (runs of 128 timesteps: each run converts the state to bit planes and back once)
+    g6.run_logrefresh(np.full(128, 0.7))
+    ms = timer(lambda: g6.run_logrefresh(np.full(128, 0.7)))
     g6.close()
-    out["walkers_gamma6_flips_per_ns"] = updates(L, 1, R, 32 * 6) / (ms * 1e6)
+    out["walkers_gamma6_flips_per_ns"] = updates(L, 1, R, 128 * 6) / (ms * 1e6)
     out["paper_h100_walkers_total_ns_per_sweep"] = 121554 + 97378
     out["paper_h100_spin_update_kernel_ns_per_sweep"] = 121554
     out["paper_h100_flips_per_ns"] = 128 * 160 ** 3 / 121554.0
