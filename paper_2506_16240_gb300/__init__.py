@@ -326,6 +326,7 @@ SIGNATURES.update({
     "micsa_pool_finished": (_c.c_int, [_P, _i64p, _c.c_int, ctypes.POINTER(_c.c_int)]),
     "micsa_pool_set_launch_config": (_c.c_int, [_P, _c.c_int, _c.c_int, _c.c_int]),
     "micsa_pool_set_shape": (_c.c_int, [_P, _c.c_int, _c.c_int]),
+    "micsa_pool_set_planes": (_c.c_int, [_P, _c.c_int]),
     "micsa_pool_last_error": (_c.c_char_p, [_P]),
     "micsa_pool_destroy": (None, [_P]),
 })
@@ -440,3 +441,8 @@ class Pool:
         """Words per thread (cap 1, 2 or 4) and concurrent kernel chains (1..4) of
         the streaming jobs' half-sweeps; results do not depend on them."""
         self._check(lib().micsa_pool_set_shape(self.h, int(max_words), int(chains)))
+
+    def set_planes(self, on=True):
+        """Bit-plane half-sweeps for the jobs admitted from now on with L a
+        multiple of 32 (at least 64); results do not depend on it."""
+        self._check(lib().micsa_pool_set_planes(self.h, int(bool(on))))

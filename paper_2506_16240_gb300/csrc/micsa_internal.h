@@ -73,6 +73,12 @@ struct JobDesc {
     int32_t live;
     uint32_t divL_m, divL_l;  // FastDiv by L
     uint32_t divC_m, divC_l;  // FastDiv by chunks per row (W / nw)
+    // bit-plane jobs (L a multiple of 32): during a tick the state lives in
+    // planes [R][6][L^3/64] (spins, m0, m1 of both parities), the bonds in
+    // bplanes [6][2][L^3/64]; the byte arrays hold it between ticks
+    uint32_t *planes;
+    const uint32_t *bplanes;
+    int32_t use_planes;
 };
 
 // One lattice (a replica of a sample or of a pool job) that a CTA keeps in
@@ -193,6 +199,7 @@ int msg_planes_per_replica(int gamma, int walkers);  // 2 spin + 4 gamma daemon 
 cudaError_t msg_convert(uint32_t *planes, uint32_t *bplanes, int8_t *spins, uint8_t *daemons, const uint8_t *bonds,
                         const Geometry &g, int S, int R, int gamma, int walkers, int buf, bool to_planes,
                         cudaStream_t st);
+cudaError_t msg_convert_bonds(uint32_t *bplanes, const uint8_t *bonds, const Geometry &g, int S, cudaStream_t st);
 cudaError_t launch_msg_wander(uint32_t *planes, const Geometry &g, int S, int R, int r0, int r1, int gamma,
                               const SweepParam *params, const int64_t *cursor, int64_t k, bool pdl, cudaStream_t st);
 int msg_default_rpt(const Geometry &g, int S, int R, int nw, int sm_count);

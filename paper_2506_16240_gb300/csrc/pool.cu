@@ -22,6 +22,7 @@
 #include <vector>
 
 #include "sweep_body.cuh"
+#include "msg_body.cuh"
 #include "../../include/micsa.h"
 
 namespace micsa {
@@ -39,10 +40,21 @@ struct VBlock {
     int32_t chunk0;  // first chunk of the replica's half-lattice in this block
 };
 
+// 128 threads of one bit-plane job: thread q updates (and converts) the plane
+// words 4q .. 4q + 3 of every replica, q = chunk0 + threadIdx.x.
+struct PVBlock {
+    int32_t slot;
+    int32_t chunk0;
+};
+
 struct PoolTables {
     JobDesc *jobs;          // [max_jobs]
     const VBlock *vblocks;  // [max_vblocks]
-    const int32_t *n_vblocks;  // [kPoolMaxChains]: the end of each chain's part (unused parts and the last: the total)
+    const int32_t *n_vblocks;  // [kPoolMaxChains + 1]: the end of each chain's part over the byte-streamed
+                               // jobs (unused parts: their total); [kPoolMaxChains]: all the jobs measured
+                               // over the table (byte-streamed first, then the bit-plane jobs)
+    const PVBlock *pvblocks;   // the bit-plane jobs' half-sweep blocks
+    const int32_t *n_pvb;
     long long *energy;      // [max_jobs][kPoolMaxR]
     long long *aux;
     long long *best_energy;
@@ -181,13 +193,86 @@ __device__ __forceinline__ void chunk_measure(const Geometry &g, const int8_t *s
     }
 }
 
+// Bit-plane jobs, at the start and at the end of a tick: their byte state
+// to planes (to_planes) or back, each thread the 4 words of its half-sweep
+// position, both parities, every replica.
+__global__ void __launch_bounds__(kVBlock) pool_planes_convert_kernel(PoolTables T, int to_planes) {
+    pool_wait();
+    pool_release();
+    const int nvb = *T.n_pvb;
+    const int per = (nvb + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int vb_end = min(nvb, ((int)blockIdx.x + 1) * per);
+    for (int vb = (int)blockIdx.x * per; vb < vb_end; ++vb) {
+        const PVBlock b = T.pvblocks[vb];
+        const JobDesc &J = T.jobs[b.slot];
+        if (!J.live || J.t >= J.n_sweeps) continue;
+        const Geometry g = J.geo;
+        const int64_t WP = (int64_t)g.L * g.L * g.L / 64;
+        const int64_t w0 = 4 * ((int64_t)b.chunk0 + threadIdx.x);
+        if (w0 >= WP) continue;
+        for (int r = 0; r < J.R; ++r)
+            for (int par = 0; par < 2; ++par)
+                for (int j = 0; j < 4; ++j)
+                    msg_convert_word(J.planes, J.spins, J.daemons, g, WP, 1, 6, 0, to_planes != 0, r, par, w0 + j);
+    }
+}
+
+// One half-sweep (parity p) of sweep k of the tick for every live bit-plane
+// job: the bit-plane update of the single-handle engine (4 words per thread,
+// every replica of the job in one thread, the job's own clock, cut points and
+// Philox key; replica r is Philox id r, as in the byte path).
+__global__ void __launch_bounds__(kVBlock, 4) pool_msg_half_kernel(PoolTables T, int k, int p) {
+    pool_wait();
+    pool_release();
+    const int nvb = *T.n_pvb;
+    const int per = (nvb + (int)gridDim.x - 1) / (int)gridDim.x;
+    const int vb_end = min(nvb, ((int)blockIdx.x + 1) * per);
+    int slot = -1;  // the job whose state is held below (the same for the whole CTA)
+    MsgLattice lat{};
+    SweepParam prm{};
+    FastDiv dg{}, dL{};
+    int R = 0;
+    bool active = false;
+    for (int vb = (int)blockIdx.x * per; vb < vb_end; ++vb) {
+        const PVBlock b = T.pvblocks[vb];
+        if (b.slot != slot) {
+            slot = b.slot;
+            const JobDesc &J = T.jobs[slot];
+            const int64_t t = J.t + k;
+            active = J.live && t < J.n_sweeps;
+            const Geometry g = J.geo;
+            lat = MsgLattice{J.planes, J.bplanes, g.L, g.Lh, g.L / 32, g.Lh / 4, (int64_t)g.L * g.L * g.L / 64,
+                             6, 1, 0, 0, J.key0, J.key1};
+            prm = SweepParam{};
+            prm.t = t;
+            prm.mode = kModeMicsa;
+            if (active && t % J.interval == 0) {
+                const uint64_t *q = J.thr + 3 * (t / J.interval);
+                prm.th0 = q[0];
+                prm.th1 = q[1];
+                prm.th2 = q[2];
+                prm.mode = kModeRefresh;
+            }
+            dg = make_fastdiv_dev((uint32_t)(g.Lh / 4));
+            dL = make_fastdiv_dev((uint32_t)g.L);
+            R = J.R;
+        }
+        if (!active) continue;
+        const uint32_t q = (uint32_t)b.chunk0 + threadIdx.x;
+        if ((int64_t)q * 4 >= lat.WP) continue;  // (job thread counts are multiples of 128)
+        const uint32_t rowi = fdiv(q, dg);
+        const uint32_t zw = fdiv(rowi, dL);
+        msg_update<4>(lat, prm, p, (int)zw, (int)(rowi - zw * dL.d), (int)(q - rowi * dg.d), 0, R);
+    }
+}
+
 // Energy and daemon sums of every (live, advancing) streaming job replica after
 // the tick, over the virtual-block table of the half-sweeps: per warp one
 // atomic into the (slot, replica) accumulators.
 __global__ void __launch_bounds__(kVBlock) pool_energy_kernel(PoolTables T) {
     pool_wait();
     pool_release();
-    const int nvb = T.n_vblocks[kPoolMaxChains - 1];
+    const int nvb = T.n_vblocks[kPoolMaxChains];
     // a contiguous run of virtual blocks per CTA: mostly one job (its descriptor
     // stays in L1) and neighbouring planes (their rows are re-read from L1)
     const int per = (nvb + (int)gridDim.x - 1) / (int)gridDim.x;
@@ -254,7 +339,7 @@ __global__ void pool_best_kernel(PoolTables T, int K) {
 __global__ void __launch_bounds__(kVBlock) pool_best_copy_kernel(PoolTables T) {
     pool_wait();
     pool_release();
-    const int nvb = T.n_vblocks[kPoolMaxChains - 1];
+    const int nvb = T.n_vblocks[kPoolMaxChains];
     // a contiguous run of virtual blocks per CTA: mostly one job (its descriptor
     // stays in L1) and neighbouring planes (their rows are re-read from L1)
     const int per = (nvb + (int)gridDim.x - 1) / (int)gridDim.x;
@@ -310,7 +395,8 @@ using namespace micsa;
 struct PoolJob {
     int64_t id = -1;
     micsa_job_desc desc{};
-    size_t off_bonds = 0, off_spins = 0, off_daemons = 0, off_best = 0, off_thr = 0, bytes = 0;
+    size_t off_bonds = 0, off_spins = 0, off_daemons = 0, off_best = 0, off_thr = 0, off_planes = 0, off_bplanes = 0,
+           bytes = 0;
     int64_t t = 0;           // host mirror of sweeps done after the queued ticks
     int64_t done_tick = -1;  // tick index whose completion finishes the job
     bool live = false;
@@ -361,8 +447,16 @@ struct micsa_pool {
     int32_t *d_nunits = nullptr, *h_nunits = nullptr;
     int *d_counter = nullptr;
     int max_units = 0;
-    bool has_stream_jobs = false, has_resident_jobs = false;
-    cudaGraphExec_t graphs[4] = {nullptr, nullptr, nullptr, nullptr};  // by part mask
+    bool has_stream_jobs = false, has_resident_jobs = false, has_plane_jobs = false;
+    // bit-plane jobs (L a multiple of 32, at least 64): a forked branch of the tick
+    bool planes_on = true;  // for the jobs admitted from now on
+    PVBlock *d_pvblocks = nullptr, *h_pvblocks = nullptr;
+    int32_t *d_npvb = nullptr, *h_npvb = nullptr;
+    int max_pvblocks = 0;
+    int planes_grid = 0;
+    cudaStream_t planes_stream = nullptr;
+    cudaEvent_t planes_fork = nullptr, planes_join = nullptr;
+    cudaGraphExec_t graphs[8] = {};  // by part mask: 1 resident, 2 byte-streamed, 4 bit-plane jobs
     std::string err;
 };
 
@@ -437,9 +531,13 @@ double schedule_T(const micsa_job_desc &d, int64_t k) {
 
 struct JobSizes {
     Geometry g;
-    size_t bonds, state, best, thr;
+    size_t bonds, state, best, thr, planes, bplanes;  // planes, bplanes: 0 unless plane_eligible
     int64_t n_refresh;
 };
+
+// Jobs the bit-plane path can take: L a multiple of 32 (a z column per word)
+// and above the shared-memory kernel's sizes.
+bool plane_eligible(const micsa_job_desc &d) { return d.L % 32 == 0 && d.L >= 64; }
 
 JobSizes job_sizes(const micsa_job_desc &d) {
     JobSizes s;
@@ -451,6 +549,9 @@ JobSizes job_sizes(const micsa_job_desc &d) {
     s.n_refresh = (d.n_sweeps + d.refresh_interval - 1) / d.refresh_interval;
     if (s.n_refresh < 1) s.n_refresh = 1;
     s.thr = sizeof(uint64_t) * 3 * (size_t)s.n_refresh;
+    const size_t WP = (size_t)d.L * d.L * d.L / 64;
+    s.planes = plane_eligible(d) ? sizeof(uint32_t) * 6 * WP * (size_t)d.n_replicas : 0;
+    s.bplanes = plane_eligible(d) ? sizeof(uint32_t) * 12 * WP : 0;
     return s;
 }
 
@@ -475,6 +576,7 @@ int upload_tables(micsa_pool_t p) {
     std::sort(order.begin(), order.end(), [&](int a, int b) {
         return p->slots[a].desc.L * p->slots[a].desc.n_replicas > p->slots[b].desc.L * p->slots[b].desc.n_replicas;
     });
+    int npvb = 0;
     for (int i : order) {
         const JobDesc &J = p->h_jobs[i];
         if (J.resident) {
@@ -483,27 +585,44 @@ int upload_tables(micsa_pool_t p) {
                 p->h_units[nunits++] = ResidentUnit{J.spins + (int64_t)r * 2 * J.geo.half,
                                                     J.daemons + (int64_t)r * 2 * J.geo.half, J.bonds, r, i};
             }
-            continue;
         }
-        const int64_t chunks = (int64_t)J.geo.L * J.geo.L * (J.geo.W / J.nw);
-        for (int r = 0; r < J.R; ++r)
-            for (int64_t c = 0; c < chunks; c += kVBlock) {
-                if (nvb >= p->max_vblocks) return pfail(p, MICSA_E_BUSY, "virtual block table full");
-                p->h_vblocks[nvb++] = VBlock{i, (int16_t)r, 0, (int32_t)c};
-            }
     }
-    // the chains' parts: ends at the (job, replica) boundaries nearest c * nvb / chains
+    // byte-layout virtual blocks: the byte-streamed jobs first (their half-sweeps
+    // run over this part), then the bit-plane jobs (measured over it after the tick)
+    for (int pass = 0; pass < 2; ++pass)
+        for (int i : order) {
+            const JobDesc &J = p->h_jobs[i];
+            if (J.resident || (J.use_planes != 0) != (pass == 1)) continue;
+            const int64_t chunks = (int64_t)J.geo.L * J.geo.L * (J.geo.W / J.nw);
+            for (int r = 0; r < J.R; ++r)
+                for (int64_t c = 0; c < chunks; c += kVBlock) {
+                    if (nvb >= p->max_vblocks) return pfail(p, MICSA_E_BUSY, "virtual block table full");
+                    p->h_vblocks[nvb++] = VBlock{i, (int16_t)r, 0, (int32_t)c};
+                }
+            if (pass == 1) {
+                const int64_t threads = (int64_t)J.geo.L * J.geo.L * J.geo.L / 256;  // 4 plane words each
+                for (int64_t c = 0; c < threads; c += kVBlock) {
+                    if (npvb >= p->max_pvblocks) return pfail(p, MICSA_E_BUSY, "plane block table full");
+                    p->h_pvblocks[npvb++] = PVBlock{i, (int32_t)c};
+                }
+            }
+        }
+    int nvb_stream = 0;
+    for (int i = 0; i < nvb; ++i)
+        if (!p->h_jobs[p->h_vblocks[i].slot].use_planes) nvb_stream = i + 1;
+    // the chains' parts of the byte-streamed jobs: ends at the (job, replica)
+    // boundaries nearest c * nvb_stream / chains
     std::vector<int> bounds;
-    for (int v = 0; v <= nvb; ++v)
-        if (v == 0 || v == nvb || p->h_vblocks[v].slot != p->h_vblocks[v - 1].slot ||
+    for (int v = 0; v <= nvb_stream; ++v)
+        if (v == 0 || v == nvb_stream || p->h_vblocks[v].slot != p->h_vblocks[v - 1].slot ||
             p->h_vblocks[v].replica != p->h_vblocks[v - 1].replica)
             bounds.push_back(v);
     int prev = 0;
     for (int c = 0; c < kPoolMaxChains; ++c) {
-        int end = nvb;
+        int end = nvb_stream;
         if (c + 1 < p->chains) {
-            const double target = (double)(c + 1) * nvb / p->chains;
-            int best = nvb;
+            const double target = (double)(c + 1) * nvb_stream / p->chains;
+            int best = nvb_stream;
             for (int v : bounds)
                 if (v >= prev && std::fabs(v - target) < std::fabs(best - target)) best = v;
             end = best;
@@ -511,13 +630,18 @@ int upload_tables(micsa_pool_t p) {
         p->h_nvb[c] = end;
         prev = end;
     }
+    p->h_nvb[kPoolMaxChains] = nvb;
+    *p->h_npvb = npvb;
     *p->h_nunits = nunits;
-    p->has_stream_jobs = nvb > 0;
+    p->has_stream_jobs = nvb_stream > 0;
     p->has_resident_jobs = nunits > 0;
+    p->has_plane_jobs = npvb > 0;
     std::memcpy(p->h_jobs_stage, p->h_jobs.data(), sizeof(JobDesc) * p->max_jobs);
     PCK(p, cudaMemcpyAsync(p->d_jobs, p->h_jobs_stage, sizeof(JobDesc) * p->max_jobs, cudaMemcpyHostToDevice, p->stream), "upload jobs");
     PCK(p, cudaMemcpyAsync(p->d_vblocks, p->h_vblocks, sizeof(VBlock) * (size_t)(nvb ? nvb : 1), cudaMemcpyHostToDevice, p->stream), "upload vblocks");
-    PCK(p, cudaMemcpyAsync(p->d_nvb, p->h_nvb, kPoolMaxChains * sizeof(int32_t), cudaMemcpyHostToDevice, p->stream), "upload vblock counts");
+    PCK(p, cudaMemcpyAsync(p->d_nvb, p->h_nvb, (kPoolMaxChains + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, p->stream), "upload vblock counts");
+    PCK(p, cudaMemcpyAsync(p->d_pvblocks, p->h_pvblocks, sizeof(PVBlock) * (size_t)(npvb ? npvb : 1), cudaMemcpyHostToDevice, p->stream), "upload plane blocks");
+    PCK(p, cudaMemcpyAsync(p->d_npvb, p->h_npvb, sizeof(int32_t), cudaMemcpyHostToDevice, p->stream), "upload plane block count");
     if (p->max_units) {
         PCK(p, cudaMemcpyAsync(p->d_units, p->h_units, sizeof(ResidentUnit) * (size_t)(nunits ? nunits : 1), cudaMemcpyHostToDevice, p->stream), "upload units");
         PCK(p, cudaMemcpyAsync(p->d_nunits, p->h_nunits, sizeof(int32_t), cudaMemcpyHostToDevice, p->stream), "upload unit count");
@@ -534,19 +658,19 @@ int upload_tables(micsa_pool_t p) {
 int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
     long long *R0 = p->d_results;
     const size_t rows = (size_t)p->max_jobs * kPoolMaxR;
-    PoolTables T{p->d_jobs, p->d_vblocks, p->d_nvb, R0, R0 + rows, R0 + 2 * rows, R0 + 3 * rows, p->d_acc,
-                 p->d_improved};
-    // both parts present: the resident kernel runs on a forked branch, concurrently
-    // with the streaming half-sweeps (they touch disjoint jobs), joined before
-    // the measure and advance nodes
-    const bool fork = (mask & 3) == 3 && p->resident_smem;
+    PoolTables T{p->d_jobs, p->d_vblocks, p->d_nvb, p->d_pvblocks, p->d_npvb, R0, R0 + rows, R0 + 2 * rows,
+                 R0 + 3 * rows, p->d_acc, p->d_improved};
+    const bool resident = (mask & 1) && p->resident_smem, streamed = (mask & 2) != 0, planes = (mask & 4) != 0;
+    // the resident kernel runs on a forked branch, concurrently with the other
+    // parts (they touch disjoint jobs), joined before the advance node
+    const bool fork = resident && (streamed || planes);
     cudaStream_t rs = st;
     if (fork) {
         PCK(p, cudaEventRecord(p->fork_ev, st), "fork event");
         PCK(p, cudaStreamWaitEvent(p->aux_stream, p->fork_ev, 0), "fork wait");
         rs = p->aux_stream;
     }
-    if ((mask & 1) && p->resident_smem) {
+    if (resident) {
         ResidentArgs ra{};
         ra.units = p->d_units;
         ra.n_units_dev = p->d_nunits;
@@ -557,8 +681,31 @@ int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
         ra.max_jobs = p->max_jobs;
         PCK(p, launch_multispin(ra, true, p->resident_smem, p->resident_grid, p->pdl && !fork, rs), "pool multispin launch");
     }
-    if (mask & 2) {
-        // the parts of the streaming jobs as concurrent chains, joined before
+    if (planes) {
+        // the bit-plane jobs on their own branch: bytes -> planes, the K sweeps,
+        // planes -> bytes (the measurement below reads the bytes)
+        PCK(p, cudaEventRecord(p->planes_fork, st), "planes fork event");
+        PCK(p, cudaStreamWaitEvent(p->planes_stream, p->planes_fork, 0), "planes fork wait");
+        int to_planes = 1, to_bytes = 0;
+        void *cin[] = {&T, &to_planes};
+        PCK(p, launch_pdl((const void *)pool_planes_convert_kernel, dim3(p->grid_blocks), dim3(kVBlock), p->planes_stream,
+                          cin, false),
+            "pool planes in");
+        for (int k = 0; k < p->K; ++k)
+            for (int par = 0; par < 2; ++par) {
+                void *args[] = {&T, &k, &par};
+                PCK(p, launch_pdl((const void *)pool_msg_half_kernel, dim3(p->planes_grid), dim3(kVBlock), p->planes_stream,
+                                  args, p->pdl),
+                    "pool plane half-sweep launch");
+            }
+        void *cout[] = {&T, &to_bytes};
+        PCK(p, launch_pdl((const void *)pool_planes_convert_kernel, dim3(p->grid_blocks), dim3(kVBlock), p->planes_stream,
+                          cout, p->pdl),
+            "pool planes out");
+        PCK(p, cudaEventRecord(p->planes_join, p->planes_stream), "planes join event");
+    }
+    if (streamed) {
+        // the parts of the byte-streamed jobs as concurrent chains, joined before
         // the measurement
         PCK(p, cudaEventRecord(p->chain_fork, st), "chain fork event");
         for (int c = 1; c < p->chains; ++c)
@@ -577,6 +724,9 @@ int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
             PCK(p, cudaEventRecord(p->chain_join[c], p->chain_stream[c]), "chain join event");
             PCK(p, cudaStreamWaitEvent(st, p->chain_join[c], 0), "chain join wait");
         }
+    }
+    if (planes) PCK(p, cudaStreamWaitEvent(st, p->planes_join, 0), "planes join wait");
+    if (streamed || planes) {
         int K = p->K;
         void *eargs[] = {&T};
         void *bargs[] = {&T, &K};
@@ -595,7 +745,10 @@ int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
 }
 
 int tick_launches(micsa_pool_t p, int mask) {
-    return ((mask & 1) && p->resident_smem ? 1 : 0) + ((mask & 2) ? 2 * p->chains * p->K + 3 : 0) + 1;
+    const int resident = (mask & 1) && p->resident_smem ? 1 : 0;
+    const int streamed = (mask & 2) ? 2 * p->chains * p->K : 0;
+    const int planes = (mask & 4) ? 2 * p->K + 2 : 0;
+    return resident + streamed + planes + ((mask & 6) ? 3 : 0) + 1;
 }
 
 int ensure_graph(micsa_pool_t p, int mask) {
@@ -668,9 +821,12 @@ int micsa_pool_create(size_t arena_bytes, int max_jobs, int tick_sweeps, micsa_p
         if ((e = cudaMalloc(&p->arena, p->arena_bytes)) != cudaSuccess) { bail(MICSA_E_OOM); break; }
         p->free_list[0] = p->arena_bytes;
         p->max_vblocks = 1 << 22;
+        p->max_pvblocks = 1 << 20;
         if ((e = cudaMalloc(&p->d_jobs, sizeof(JobDesc) * max_jobs)) != cudaSuccess ||
             (e = cudaMalloc(&p->d_vblocks, sizeof(VBlock) * (size_t)p->max_vblocks)) != cudaSuccess ||
-            (e = cudaMalloc(&p->d_nvb, kPoolMaxChains * sizeof(int32_t))) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_nvb, (kPoolMaxChains + 1) * sizeof(int32_t))) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_pvblocks, sizeof(PVBlock) * (size_t)p->max_pvblocks)) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_npvb, sizeof(int32_t))) != cudaSuccess ||
             (e = cudaMalloc(&p->d_results, sizeof(long long) * 4 * (size_t)max_jobs * kPoolMaxR)) != cudaSuccess ||
             (e = cudaMalloc(&p->d_acc, sizeof(unsigned long long) * 2 * (size_t)max_jobs * kPoolMaxR)) != cudaSuccess ||
             (e = cudaMalloc(&p->d_improved, sizeof(int32_t) * (size_t)max_jobs * kPoolMaxR)) != cudaSuccess) { bail(MICSA_E_OOM); break; }
@@ -678,13 +834,17 @@ int micsa_pool_create(size_t arena_bytes, int max_jobs, int tick_sweeps, micsa_p
             (e = cudaMemsetAsync(p->d_improved, 0, sizeof(int32_t) * (size_t)max_jobs * kPoolMaxR, p->stream)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         if ((e = cudaMallocHost(&p->h_jobs_stage, sizeof(JobDesc) * max_jobs)) != cudaSuccess ||
             (e = cudaMallocHost(&p->h_vblocks, sizeof(VBlock) * (size_t)p->max_vblocks)) != cudaSuccess ||
-            (e = cudaMallocHost(&p->h_nvb, kPoolMaxChains * sizeof(int32_t))) != cudaSuccess) { bail(MICSA_E_OOM); break; }
-        for (int c = 0; c < kPoolMaxChains; ++c) p->h_nvb[c] = 0;
+            (e = cudaMallocHost(&p->h_nvb, (kPoolMaxChains + 1) * sizeof(int32_t))) != cudaSuccess ||
+            (e = cudaMallocHost(&p->h_pvblocks, sizeof(PVBlock) * (size_t)p->max_pvblocks)) != cudaSuccess ||
+            (e = cudaMallocHost(&p->h_npvb, sizeof(int32_t))) != cudaSuccess) { bail(MICSA_E_OOM); break; }
+        for (int c = 0; c <= kPoolMaxChains; ++c) p->h_nvb[c] = 0;
+        *p->h_npvb = 0;
         for (auto &ev : p->stage_free)
             if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         if (rc) break;
         if ((e = cudaMemsetAsync(p->d_jobs, 0, sizeof(JobDesc) * max_jobs, p->stream)) != cudaSuccess ||
-            (e = cudaMemsetAsync(p->d_nvb, 0, kPoolMaxChains * sizeof(int32_t), p->stream)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+            (e = cudaMemsetAsync(p->d_nvb, 0, (kPoolMaxChains + 1) * sizeof(int32_t), p->stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(p->d_npvb, 0, sizeof(int32_t), p->stream)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         // jobs of L <= 32 live in shared memory as bit planes (multispin kernel)
         p->resident_smem = multispin_smem_bytes(make_geometry(32));
         const int res_per_sm = multispin_blocks_per_sm(true, p->resident_smem);
@@ -701,6 +861,12 @@ int micsa_pool_create(size_t arena_bytes, int max_jobs, int tick_sweeps, micsa_p
             (e = cudaMemsetAsync(p->d_counter, 0, sizeof(int), p->stream)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pool_half_sweep_kernel, kVBlock, 0);
+        int per_sm_planes = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_planes, pool_msg_half_kernel, kVBlock, 0);
+        p->planes_grid = (per_sm_planes > 0 ? per_sm_planes : 4) * p->sm_count;
+        if ((e = cudaStreamCreateWithFlags(&p->planes_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&p->planes_fork, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&p->planes_join, cudaEventDisableTiming)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         p->grid_blocks = (per_sm > 0 ? per_sm : 4) * p->sm_count;
         p->tick_events.resize(64);
         for (auto &ev : p->tick_events)
@@ -742,6 +908,16 @@ void micsa_pool_destroy(micsa_pool_t p) {
     cudaFreeHost(p->h_nunits);
     cudaFreeHost(p->h_vblocks);
     cudaFreeHost(p->h_nvb);
+    cudaFree(p->d_pvblocks);
+    cudaFree(p->d_npvb);
+    cudaFreeHost(p->h_pvblocks);
+    cudaFreeHost(p->h_npvb);
+    if (p->planes_stream) {
+        cudaStreamSynchronize(p->planes_stream);
+        cudaStreamDestroy(p->planes_stream);
+    }
+    if (p->planes_fork) cudaEventDestroy(p->planes_fork);
+    if (p->planes_join) cudaEventDestroy(p->planes_join);
     if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
     if (p->aux_stream) {
         cudaStreamSynchronize(p->aux_stream);
@@ -766,7 +942,8 @@ const char *micsa_pool_last_error(micsa_pool_t p) { return p ? p->err.c_str() : 
 int micsa_pool_job_bytes(const micsa_job_desc *job, size_t *bytes) {
     if (!job || !bytes) return MICSA_E_INVALID_ARG;
     const JobSizes s = job_sizes(*job);
-    *bytes = align_up(s.bonds) + 2 * align_up(s.state) + align_up(s.best) + align_up(s.thr);
+    *bytes = align_up(s.bonds) + 2 * align_up(s.state) + align_up(s.best) + align_up(s.thr) + align_up(s.planes) +
+             align_up(s.bplanes);
     return MICSA_OK;
 }
 
@@ -795,6 +972,8 @@ int micsa_pool_submit(micsa_pool_t p, const micsa_job_desc *job, int64_t *job_id
     J.off_daemons = J.off_spins + align_up(s.state);
     J.off_best = J.off_daemons + align_up(s.state);
     J.off_thr = J.off_best + align_up(s.best);
+    J.off_planes = J.off_thr + align_up(s.thr);
+    J.off_bplanes = J.off_planes + align_up(s.planes);
     J.t = 0;
     J.live = true;
     J.done_tick = -1;
@@ -854,6 +1033,15 @@ int micsa_pool_submit(micsa_pool_t p, const micsa_job_desc *job, int64_t *job_id
     D.divC_m = fdC.m;
     D.divC_l = fdC.l;
     D.resident = (p->resident_smem && multispin_smem_bytes(s.g) && multispin_smem_bytes(s.g) <= p->resident_smem) ? 1 : 0;
+    D.use_planes = (p->planes_on && plane_eligible(d) && !D.resident) ? 1 : 0;
+    D.planes = D.use_planes ? reinterpret_cast<uint32_t *>(base + J.off_planes) : nullptr;
+    D.bplanes = D.use_planes ? reinterpret_cast<const uint32_t *>(base + J.off_bplanes) : nullptr;
+    if (D.use_planes) {  // the bonds never change: their planes are made once
+        PCK(p, msg_convert_bonds(reinterpret_cast<uint32_t *>(base + J.off_bplanes), base + J.off_bonds, s.g, 1,
+                                 p->stream),
+            "job bond planes");
+        ++p->launches;
+    }
     p->tables_dirty = true;
     *job_id = J.id;
     return MICSA_OK;
@@ -862,7 +1050,7 @@ int micsa_pool_submit(micsa_pool_t p, const micsa_job_desc *job, int64_t *job_id
 int micsa_pool_tick(micsa_pool_t p) {
     if (!p) return MICSA_E_INVALID_ARG;
     if (int rc = upload_tables(p)) return rc;
-    const int mask = (p->has_resident_jobs ? 1 : 0) | (p->has_stream_jobs ? 2 : 0);
+    const int mask = (p->has_resident_jobs ? 1 : 0) | (p->has_stream_jobs ? 2 : 0) | (p->has_plane_jobs ? 4 : 0);
     if (int rc = ensure_graph(p, mask)) return rc;
     if (p->graphs[mask]) {
         PCK(p, cudaGraphLaunch(p->graphs[mask], p->stream), "pool graph launch");
@@ -1002,6 +1190,12 @@ int micsa_pool_set_launch_config(micsa_pool_t p, int blocks_per_sm, int pdl, int
     p->grid_blocks = blocks_per_sm * p->sm_count;
     p->pdl = pdl != 0;
     p->use_graph = use_graph != 0;
+    return MICSA_OK;
+}
+
+int micsa_pool_set_planes(micsa_pool_t p, int on) {
+    if (!p) return MICSA_E_INVALID_ARG;
+    p->planes_on = on != 0;
     return MICSA_OK;
 }
 

@@ -26,10 +26,13 @@ def single_handle(L, R, seed, n, interval, T0, T1):
     return e, a, s
 
 
-def run_pool(jobs, K=16, arena=1 << 28, max_jobs=64, order=None, shape=None, reshape=None):
+def run_pool(jobs, K=16, arena=1 << 28, max_jobs=64, order=None, shape=None, reshape=None, planes=None):
     """Run jobs to completion; shape: (max_words, chains, blocks_per_sm) set
-    before the submissions, reshape: one set after the first tick."""
+    before the submissions, reshape: one set after the first tick; planes: the
+    bit-plane path on or off for the jobs (None: the pool's default, on)."""
     with micsa.Pool(arena, max_jobs, K) as p:
+        if planes is not None:
+            p.set_planes(planes)
         if shape:
             p.set_shape(shape[0], shape[1])
             p.set_launch_config(shape[2])
@@ -92,7 +95,7 @@ JOBS_STREAMED = [  # (L, R, seed, n_sweeps, interval, T_start, T_end)
 
 
 def test_pool_streamed_variants_match_oracle():
-    res = run_pool(JOBS_STREAMED, K=5)
+    res = run_pool(JOBS_STREAMED, K=5, planes=False)  # the byte kernel for every job
     for idx, (L, R, seed, n, interval, T0, T1) in enumerate(JOBS_STREAMED):
         st = O.create(L, 1, R, seed)
         O.run(st, micsa.linear_schedule(T0, T1, n), interval)
@@ -133,7 +136,7 @@ def test_batched_workload_in_one_pool_sampled_jobs_match_oracle():
 
 
 @pytest.mark.parametrize("job", [JOBS[0], JOBS[2], JOBS[5], JOBS[8], JOBS_STREAMED[1], JOBS_STREAMED[4],
-                                 JOBS_STREAMED[5]])
+                                 JOBS_STREAMED[5], (64, 2, 35, 40, 6, 2.5, 0.5)])
 def test_pool_best_configuration_matches_oracle(job):
     L, R, seed, n, interval, T0, T1 = job
     K = 16
@@ -255,3 +258,33 @@ def test_pool_autotuner_choice_is_valid_and_exact():
     res = run_pool(jobs, K=4, shape=(choice["max_words"], choice["chains"], choice["blocks_per_sm"]))
     for idx in range(len(jobs)):
         np.testing.assert_array_equal(res[idx]["energy"], ref[idx]["energy"], err_msg=str(jobs[idx]))
+
+
+# L a multiple of 32, at least 64: the pool's bit-plane path (on by default)
+JOBS_PLANES = [  # (L, R, seed, n_sweeps, interval, T_start, T_end)
+    (64, 2, 31, 23, 5, 2.5, 0.5), (96, 1, 32, 9, 3, 2.0, 1.0), (64, 3, 33, 17, 7, 3.0, 0.3), (128, 1, 34, 6, 2, 1.5, 1.5),
+]
+
+
+def test_pool_plane_jobs_match_oracle():
+    res = run_pool(JOBS_PLANES, K=4)
+    for idx, (L, R, seed, n, interval, T0, T1) in enumerate(JOBS_PLANES):
+        st = O.create(L, 1, R, seed)
+        O.run(st, micsa.linear_schedule(T0, T1, n), interval)
+        e, a, _ = O.measure(st)
+        np.testing.assert_array_equal(res[idx]["energy"], e, err_msg=str(JOBS_PLANES[idx]))
+        np.testing.assert_array_equal(res[idx]["aux"], a, err_msg=str(JOBS_PLANES[idx]))
+        assert res[idx]["sweeps_done"] == n
+
+
+@pytest.mark.parametrize("K", [3, 16])
+def test_pool_results_identical_with_and_without_planes(K):
+    """Resident, byte-streamed and bit-plane jobs in one pool: every result is
+    the same with the bit-plane path on and off."""
+    jobs = JOBS[:4] + JOBS_STREAMED + JOBS_PLANES
+    on = run_pool(jobs, K=K, planes=True)
+    off = run_pool(jobs, K=K, planes=False)
+    for idx in range(len(jobs)):
+        for k in ("energy", "aux", "best_energy", "best_t", "sweeps_done"):
+            np.testing.assert_array_equal(on[idx][k], off[idx][k], err_msg=f"{jobs[idx]} {k}")
+        np.testing.assert_array_equal(on[idx]["best_spins"], off[idx]["best_spins"], err_msg=str(jobs[idx]))
