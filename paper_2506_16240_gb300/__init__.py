@@ -444,5 +444,5 @@ class Pool:
 
     def set_planes(self, on=True):
         """Bit-plane half-sweeps for the jobs admitted from now on with L a
-        multiple of 32 (at least 64); results do not depend on it."""
+        multiple of 8 (at least 40); results do not depend on it."""
         self._check(lib().micsa_pool_set_planes(self.h, int(bool(on))))

@@ -194,7 +194,7 @@ cudaError_t launch_tma_half(const TmaMaps &m, int8_t *spins, uint8_t *daemons, c
 
 // multispin planes in global memory for L % 32 == 0 (multispin.cu)
 bool msg_supported(const Geometry &g);
-int64_t msg_plane_words(const Geometry &g);  // words per parity plane, L^3 / 64
+int64_t msg_plane_words(const Geometry &g);  // words per parity plane, L * ceil(L / 32) * Lh
 int msg_planes_per_replica(int gamma, int walkers);  // 2 spin + 4 gamma daemon planes (x 2 buffers)
 cudaError_t msg_convert(uint32_t *planes, uint32_t *bplanes, int8_t *spins, uint8_t *daemons, const uint8_t *bonds,
                         const Geometry &g, int S, int R, int gamma, int walkers, int buf, bool to_planes,

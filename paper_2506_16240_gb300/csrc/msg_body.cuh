@@ -148,20 +148,21 @@ __device__ __forceinline__ void msg_convert_word(uint32_t *planes, int8_t *spins
     const int64_t zstep = (int64_t)g.L * g.P;
     uint32_t *pl = planes + rep * np * WP;
     const int64_t sbase = (rep * 2 + p) * g.half + in_half;
+    const int nb = g.L - 32 * zw < 32 ? g.L - 32 * zw : 32;  // sites of the column in this word
     if (to_planes) {
         uint32_t sv = 0;
-        for (int b = 0; b < 32; ++b) sv |= (((uint32_t)(uint8_t)spins[sbase + b * zstep] >> 7) & 1u) << b;
+        for (int b = 0; b < nb; ++b) sv |= (((uint32_t)(uint8_t)spins[sbase + b * zstep] >> 7) & 1u) << b;
         pl[(int64_t)p * WP + w] = sv;
     } else {
         const uint32_t sv = pl[(int64_t)p * WP + w];
-        for (int b = 0; b < 32; ++b) spins[sbase + b * zstep] = ((sv >> b) & 1u) ? (int8_t)-1 : (int8_t)1;
+        for (int b = 0; b < nb; ++b) spins[sbase + b * zstep] = ((sv >> b) & 1u) ? (int8_t)-1 : (int8_t)1;
     }
     for (int al = 0; al < gamma; ++al) {
         const int64_t dbase = ((rep * gamma + al) * 2 + p) * g.half + in_half;
         const int mp = 2 + ((buf * gamma + al) * 2) * 2 + p;
         if (to_planes) {
             uint32_t m0 = 0, m1 = 0;
-            for (int b = 0; b < 32; ++b) {
+            for (int b = 0; b < nb; ++b) {
                 const uint32_t m = daemons[dbase + b * zstep];
                 m0 |= (m & 1u) << b;
                 m1 |= ((m >> 1) & 1u) << b;
@@ -170,7 +171,7 @@ __device__ __forceinline__ void msg_convert_word(uint32_t *planes, int8_t *spins
             pl[(int64_t)(mp + 2) * WP + w] = m1;
         } else {
             const uint32_t m0 = pl[(int64_t)mp * WP + w], m1 = pl[(int64_t)(mp + 2) * WP + w];
-            for (int b = 0; b < 32; ++b)
+            for (int b = 0; b < nb; ++b)
                 daemons[dbase + b * zstep] = (uint8_t)(((m0 >> b) & 1u) | (((m1 >> b) & 1u) << 1));
         }
     }
@@ -181,8 +182,11 @@ __device__ __forceinline__ void msg_convert_word(uint32_t *planes, int8_t *spins
 // with Eq. (flip-OK) on 32 sites per word, bit-sliced; at a refresh sweep the
 // daemons are drawn first (Sec. 2.7), with walkers the previous wandering step
 // is applied on read (Sec. 2.6). Lanes (threadIdx.x & (4 / NW - 1)) share one
-// Philox block, so the threads of a warp must all be active.
-template <int NW>
+// Philox block, so the threads of a warp must all be active. RAGGED: the last
+// word of a z column holds Lz = L - 32 (nzw - 1) sites (L a multiple of 8, any
+// L >= 32; no walkers): the z wrap goes through bit Lz - 1 of that word, and its
+// bits from Lz up stay zero.
+template <int NW, bool RAGGED = false>
 __device__ __forceinline__ void msg_update(const MsgLattice &a, const SweepParam &prm, int p, int zw, int y, int ig,
                                            int r_begin, int r_end) {
     constexpr int G = 4 / NW;  // lanes sharing one Philox block of words
@@ -199,6 +203,8 @@ __device__ __forceinline__ void msg_update(const MsgLattice &a, const SweepParam
     const int64_t w_zp = ((int64_t)zwp * L + y) * Lh + i0, w_zm = ((int64_t)zwm * L + y) * Lh + i0;
     const int64_t w_ip = (row + y) * Lh + ip, w_im = (row + y) * Lh + im;
     const uint32_t M = ((p + y) & 1) ? 0x55555555u : 0xAAAAAAAAu;  // bits whose site has x offset 1
+    const int Lz = RAGGED ? L - 32 * (a.nzw - 1) : 32;  // sites in the last word of a column
+    const uint32_t zmask = (RAGGED && zw == a.nzw - 1 && Lz < 32) ? ((1u << Lz) - 1u) : 0xFFFFFFFFu;
 
     uint32_t B[6][NW];
     const uint32_t *bs = a.bonds;
@@ -276,8 +282,8 @@ __device__ __forceinline__ void msg_update(const MsgLattice &a, const SweepParam
 #pragma unroll
             for (int w = 0; w < NW; ++w) {  // word i0 + w is lane (i0 + w) & 3 of the block
                 const int j = (i0 + w) & 3;
-                m0v[w] = j == 0 ? a0[0] : j == 1 ? a0[1] : j == 2 ? a0[2] : a0[3];
-                m1v[w] = j == 0 ? a1[0] : j == 1 ? a1[1] : j == 2 ? a1[2] : a1[3];
+                m0v[w] = (j == 0 ? a0[0] : j == 1 ? a0[1] : j == 2 ? a0[2] : a0[3]) & zmask;
+                m1v[w] = (j == 0 ? a1[0] : j == 1 ? a1[1] : j == 2 ? a1[2] : a1[3]) & zmask;
             }
         } else if (gather) {  // the walkers arrive through the previous wandering step
             const uint32_t *G0 = pl + (int64_t)gplane * a.WP;
@@ -294,8 +300,12 @@ __device__ __forceinline__ void msg_update(const MsgLattice &a, const SweepParam
             const uint32_t o_prev = w > 0 ? Oc[w > 0 ? w - 1 : 0] : Oim;            // word i - 1
             const uint32_t nxp = (oc & ~M) | (o_next & M);
             const uint32_t nxm = (o_prev & ~M) | (oc & M);
-            const uint32_t nzp = __funnelshift_r(oc, Ozp[w], 1);  // bit b <- site z + 1
-            const uint32_t nzm = __funnelshift_l(Ozm[w], oc, 1);  // bit b <- site z - 1
+            uint32_t nzp = __funnelshift_r(oc, Ozp[w], 1);  // bit b <- site z + 1
+            uint32_t nzm = __funnelshift_l(Ozm[w], oc, 1);  // bit b <- site z - 1
+            if (RAGGED) {  // the wrap through a partial last word (the same bits when Lz == 32)
+                if (zw == a.nzw - 1) nzp = (oc >> 1) | ((Ozp[w] & 1u) << (Lz - 1));
+                if (zw == 0) nzm = (oc << 1) | ((Ozm[w] >> (Lz - 1)) & 1u);
+            }
             const uint32_t sg = Sg[w];
             // unsatisfied bond indicators (J s s_nb = -1)
             const uint32_t q0 = sg ^ nxp ^ B[0][w];
@@ -314,7 +324,7 @@ __device__ __forceinline__ void msg_update(const MsgLattice &a, const SweepParam
             const uint32_t v1 = u1 ^ m1 ^ k0, k1 = (u1 & m1) | (k0 & (u1 ^ m1));
             const uint32_t v2 = u2 ^ k1, v3 = u2 & k1;
             // Eq. (Creutz) with Eq. (flip-OK): accept <=> 3 <= u + m <= 6, m' = u + m - 3
-            const uint32_t acc = (v2 ^ (v1 & v0)) & ~v3;
+            const uint32_t acc = (v2 ^ (v1 & v0)) & ~v3 & zmask;
             m0v[w] = (m0 & ~acc) | (~v0 & acc);
             m1v[w] = (m1 & ~acc) | (v2 & (v1 | v0) & acc);
             Sg[w] = sg ^ acc;

@@ -542,8 +542,9 @@ __global__ void msg_convert_bonds_kernel(uint32_t *bplanes, const uint8_t *bonds
     const int zw = (int)(w / ((int64_t)g.Lh * g.L));
     const int64_t base = (smp * 2 + p) * g.half + ((int64_t)32 * zw * g.L + y) * g.P + i;
     const int64_t zstep = (int64_t)g.L * g.P;
+    const int nb = g.L - 32 * zw < 32 ? g.L - 32 * zw : 32;  // sites of the column in this word
     uint32_t bk[6] = {0, 0, 0, 0, 0, 0};
-    for (int b = 0; b < 32; ++b) {
+    for (int b = 0; b < nb; ++b) {
         const uint32_t v = bonds[base + b * zstep];
 #pragma unroll
         for (int k = 0; k < 6; ++k) bk[k] |= ((v >> k) & 1u) << b;
@@ -554,7 +555,9 @@ __global__ void msg_convert_bonds_kernel(uint32_t *bplanes, const uint8_t *bonds
 
 bool msg_supported(const Geometry &g) { return g.L >= 32 && g.L % 32 == 0 && g.P == g.Lh; }
 
-int64_t msg_plane_words(const Geometry &g) { return (int64_t)g.L * g.L * g.L / 64; }
+// Words of one plane: L * ceil(L / 32) z words per row of Lh columns (L^3 / 64
+// when L is a multiple of 32).
+int64_t msg_plane_words(const Geometry &g) { return (int64_t)g.L * ((g.L + 31) / 32) * g.Lh; }
 
 int msg_planes_per_replica(int gamma, int walkers) { return 2 + 4 * gamma * (walkers ? 2 : 1); }
 

@@ -54,7 +54,7 @@ struct PoolTables {
                                // jobs (unused parts: their total); [kPoolMaxChains]: all the jobs measured
                                // over the table (byte-streamed first, then the bit-plane jobs)
     const PVBlock *pvblocks;   // the bit-plane jobs' half-sweep blocks
-    const int32_t *n_pvb;
+    const int32_t *n_pvb;      // [kPoolMaxChains]: the end of each chain's part (unused parts: the total)
     long long *energy;      // [max_jobs][kPoolMaxR]
     long long *aux;
     long long *best_energy;
@@ -196,18 +196,19 @@ __device__ __forceinline__ void chunk_measure(const Geometry &g, const int8_t *s
 // Bit-plane jobs, at the start and at the end of a tick: their byte state
 // to planes (to_planes) or back, each thread the 4 words of its half-sweep
 // position, both parities, every replica.
-__global__ void __launch_bounds__(kVBlock) pool_planes_convert_kernel(PoolTables T, int to_planes) {
+__global__ void __launch_bounds__(kVBlock) pool_planes_convert_kernel(PoolTables T, int to_planes, int part) {
     pool_wait();
     pool_release();
-    const int nvb = *T.n_pvb;
+    const int v0 = part == 0 ? 0 : T.n_pvb[part - 1];
+    const int nvb = T.n_pvb[part] - v0;
     const int per = (nvb + (int)gridDim.x - 1) / (int)gridDim.x;
-    const int vb_end = min(nvb, ((int)blockIdx.x + 1) * per);
-    for (int vb = (int)blockIdx.x * per; vb < vb_end; ++vb) {
+    const int vb_end = v0 + min(nvb, ((int)blockIdx.x + 1) * per);
+    for (int vb = v0 + (int)blockIdx.x * per; vb < vb_end; ++vb) {
         const PVBlock b = T.pvblocks[vb];
         const JobDesc &J = T.jobs[b.slot];
         if (!J.live || J.t >= J.n_sweeps) continue;
         const Geometry g = J.geo;
-        const int64_t WP = (int64_t)g.L * g.L * g.L / 64;
+        const int64_t WP = (int64_t)g.L * ((g.L + 31) / 32) * g.Lh;
         const int64_t w0 = 4 * ((int64_t)b.chunk0 + threadIdx.x);
         if (w0 >= WP) continue;
         for (int r = 0; r < J.R; ++r)
@@ -218,22 +219,24 @@ __global__ void __launch_bounds__(kVBlock) pool_planes_convert_kernel(PoolTables
 }
 
 // One half-sweep (parity p) of sweep k of the tick for every live bit-plane
-// job: the bit-plane update of the single-handle engine (4 words per thread,
+// job: the bit-plane update of the single-handle engine with ragged z columns
+// (4 words per thread,
 // every replica of the job in one thread, the job's own clock, cut points and
 // Philox key; replica r is Philox id r, as in the byte path).
-__global__ void __launch_bounds__(kVBlock, 4) pool_msg_half_kernel(PoolTables T, int k, int p) {
+__global__ void __launch_bounds__(kVBlock, 4) pool_msg_half_kernel(PoolTables T, int k, int p, int part) {
     pool_wait();
     pool_release();
-    const int nvb = *T.n_pvb;
+    const int v0 = part == 0 ? 0 : T.n_pvb[part - 1];
+    const int nvb = T.n_pvb[part] - v0;
     const int per = (nvb + (int)gridDim.x - 1) / (int)gridDim.x;
-    const int vb_end = min(nvb, ((int)blockIdx.x + 1) * per);
+    const int vb_end = v0 + min(nvb, ((int)blockIdx.x + 1) * per);
     int slot = -1;  // the job whose state is held below (the same for the whole CTA)
     MsgLattice lat{};
     SweepParam prm{};
     FastDiv dg{}, dL{};
     int R = 0;
     bool active = false;
-    for (int vb = (int)blockIdx.x * per; vb < vb_end; ++vb) {
+    for (int vb = v0 + (int)blockIdx.x * per; vb < vb_end; ++vb) {
         const PVBlock b = T.pvblocks[vb];
         if (b.slot != slot) {
             slot = b.slot;
@@ -241,7 +244,8 @@ __global__ void __launch_bounds__(kVBlock, 4) pool_msg_half_kernel(PoolTables T,
             const int64_t t = J.t + k;
             active = J.live && t < J.n_sweeps;
             const Geometry g = J.geo;
-            lat = MsgLattice{J.planes, J.bplanes, g.L, g.Lh, g.L / 32, g.Lh / 4, (int64_t)g.L * g.L * g.L / 64,
+            const int nzw = (g.L + 31) / 32;
+            lat = MsgLattice{J.planes, J.bplanes, g.L, g.Lh, nzw, g.Lh / 4, (int64_t)g.L * nzw * g.Lh,
                              6, 1, 0, 0, J.key0, J.key1};
             prm = SweepParam{};
             prm.t = t;
@@ -262,7 +266,7 @@ __global__ void __launch_bounds__(kVBlock, 4) pool_msg_half_kernel(PoolTables T,
         if ((int64_t)q * 4 >= lat.WP) continue;  // (job thread counts are multiples of 128)
         const uint32_t rowi = fdiv(q, dg);
         const uint32_t zw = fdiv(rowi, dL);
-        msg_update<4>(lat, prm, p, (int)zw, (int)(rowi - zw * dL.d), (int)(q - rowi * dg.d), 0, R);
+        msg_update<4, true>(lat, prm, p, (int)zw, (int)(rowi - zw * dL.d), (int)(q - rowi * dg.d), 0, R);
     }
 }
 
@@ -454,8 +458,8 @@ struct micsa_pool {
     int32_t *d_npvb = nullptr, *h_npvb = nullptr;
     int max_pvblocks = 0;
     int planes_grid = 0;
-    cudaStream_t planes_stream = nullptr;
-    cudaEvent_t planes_fork = nullptr, planes_join = nullptr;
+    cudaStream_t planes_stream[kPoolMaxChains] = {};  // the bit-plane jobs' parts as concurrent chains
+    cudaEvent_t planes_fork = nullptr, planes_join[kPoolMaxChains] = {};
     cudaGraphExec_t graphs[8] = {};  // by part mask: 1 resident, 2 byte-streamed, 4 bit-plane jobs
     std::string err;
 };
@@ -535,9 +539,10 @@ struct JobSizes {
     int64_t n_refresh;
 };
 
-// Jobs the bit-plane path can take: L a multiple of 32 (a z column per word)
-// and above the shared-memory kernel's sizes.
-bool plane_eligible(const micsa_job_desc &d) { return d.L % 32 == 0 && d.L >= 64; }
+// Jobs the bit-plane path can take: L a multiple of 8 (rows of Lh sites in
+// groups of 4 words; z columns in 32-bit words, the last one partial when L is
+// not a multiple of 32) and above the shared-memory kernel's sizes.
+bool plane_eligible(const micsa_job_desc &d) { return d.L % 8 == 0 && d.L >= 40; }
 
 JobSizes job_sizes(const micsa_job_desc &d) {
     JobSizes s;
@@ -549,7 +554,7 @@ JobSizes job_sizes(const micsa_job_desc &d) {
     s.n_refresh = (d.n_sweeps + d.refresh_interval - 1) / d.refresh_interval;
     if (s.n_refresh < 1) s.n_refresh = 1;
     s.thr = sizeof(uint64_t) * 3 * (size_t)s.n_refresh;
-    const size_t WP = (size_t)d.L * d.L * d.L / 64;
+    const size_t WP = (size_t)msg_plane_words(s.g);
     s.planes = plane_eligible(d) ? sizeof(uint32_t) * 6 * WP * (size_t)d.n_replicas : 0;
     s.bplanes = plane_eligible(d) ? sizeof(uint32_t) * 12 * WP : 0;
     return s;
@@ -600,7 +605,7 @@ int upload_tables(micsa_pool_t p) {
                     p->h_vblocks[nvb++] = VBlock{i, (int16_t)r, 0, (int32_t)c};
                 }
             if (pass == 1) {
-                const int64_t threads = (int64_t)J.geo.L * J.geo.L * J.geo.L / 256;  // 4 plane words each
+                const int64_t threads = msg_plane_words(J.geo) / 4;  // 4 plane words each
                 for (int64_t c = 0; c < threads; c += kVBlock) {
                     if (npvb >= p->max_pvblocks) return pfail(p, MICSA_E_BUSY, "plane block table full");
                     p->h_pvblocks[npvb++] = PVBlock{i, (int32_t)c};
@@ -631,7 +636,23 @@ int upload_tables(micsa_pool_t p) {
         prev = end;
     }
     p->h_nvb[kPoolMaxChains] = nvb;
-    *p->h_npvb = npvb;
+    // the bit-plane jobs' parts, split the same way at job boundaries
+    std::vector<int> pbounds;
+    for (int v = 0; v <= npvb; ++v)
+        if (v == 0 || v == npvb || p->h_pvblocks[v].slot != p->h_pvblocks[v - 1].slot) pbounds.push_back(v);
+    prev = 0;
+    for (int c = 0; c < kPoolMaxChains; ++c) {
+        int end = npvb;
+        if (c + 1 < p->chains) {
+            const double target = (double)(c + 1) * npvb / p->chains;
+            int best = npvb;
+            for (int v : pbounds)
+                if (v >= prev && std::fabs(v - target) < std::fabs(best - target)) best = v;
+            end = best;
+        }
+        p->h_npvb[c] = end;
+        prev = end;
+    }
     *p->h_nunits = nunits;
     p->has_stream_jobs = nvb_stream > 0;
     p->has_resident_jobs = nunits > 0;
@@ -641,7 +662,7 @@ int upload_tables(micsa_pool_t p) {
     PCK(p, cudaMemcpyAsync(p->d_vblocks, p->h_vblocks, sizeof(VBlock) * (size_t)(nvb ? nvb : 1), cudaMemcpyHostToDevice, p->stream), "upload vblocks");
     PCK(p, cudaMemcpyAsync(p->d_nvb, p->h_nvb, (kPoolMaxChains + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, p->stream), "upload vblock counts");
     PCK(p, cudaMemcpyAsync(p->d_pvblocks, p->h_pvblocks, sizeof(PVBlock) * (size_t)(npvb ? npvb : 1), cudaMemcpyHostToDevice, p->stream), "upload plane blocks");
-    PCK(p, cudaMemcpyAsync(p->d_npvb, p->h_npvb, sizeof(int32_t), cudaMemcpyHostToDevice, p->stream), "upload plane block count");
+    PCK(p, cudaMemcpyAsync(p->d_npvb, p->h_npvb, kPoolMaxChains * sizeof(int32_t), cudaMemcpyHostToDevice, p->stream), "upload plane block counts");
     if (p->max_units) {
         PCK(p, cudaMemcpyAsync(p->d_units, p->h_units, sizeof(ResidentUnit) * (size_t)(nunits ? nunits : 1), cudaMemcpyHostToDevice, p->stream), "upload units");
         PCK(p, cudaMemcpyAsync(p->d_nunits, p->h_nunits, sizeof(int32_t), cudaMemcpyHostToDevice, p->stream), "upload unit count");
@@ -682,27 +703,29 @@ int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
         PCK(p, launch_multispin(ra, true, p->resident_smem, p->resident_grid, p->pdl && !fork, rs), "pool multispin launch");
     }
     if (planes) {
-        // the bit-plane jobs on their own branch: bytes -> planes, the K sweeps,
-        // planes -> bytes (the measurement below reads the bytes)
+        // the bit-plane jobs' parts on their own branches: bytes -> planes, the K
+        // sweeps, planes -> bytes (the measurement below reads the bytes)
         PCK(p, cudaEventRecord(p->planes_fork, st), "planes fork event");
-        PCK(p, cudaStreamWaitEvent(p->planes_stream, p->planes_fork, 0), "planes fork wait");
-        int to_planes = 1, to_bytes = 0;
-        void *cin[] = {&T, &to_planes};
-        PCK(p, launch_pdl((const void *)pool_planes_convert_kernel, dim3(p->grid_blocks), dim3(kVBlock), p->planes_stream,
-                          cin, false),
-            "pool planes in");
-        for (int k = 0; k < p->K; ++k)
-            for (int par = 0; par < 2; ++par) {
-                void *args[] = {&T, &k, &par};
-                PCK(p, launch_pdl((const void *)pool_msg_half_kernel, dim3(p->planes_grid), dim3(kVBlock), p->planes_stream,
-                                  args, p->pdl),
-                    "pool plane half-sweep launch");
-            }
-        void *cout[] = {&T, &to_bytes};
-        PCK(p, launch_pdl((const void *)pool_planes_convert_kernel, dim3(p->grid_blocks), dim3(kVBlock), p->planes_stream,
-                          cout, p->pdl),
-            "pool planes out");
-        PCK(p, cudaEventRecord(p->planes_join, p->planes_stream), "planes join event");
+        for (int part = 0; part < p->chains; ++part) {
+            cudaStream_t ps = p->planes_stream[part];
+            PCK(p, cudaStreamWaitEvent(ps, p->planes_fork, 0), "planes fork wait");
+            int to_planes = 1, to_bytes = 0;
+            void *cin[] = {&T, &to_planes, &part};
+            PCK(p, launch_pdl((const void *)pool_planes_convert_kernel, dim3(p->grid_blocks), dim3(kVBlock), ps, cin, false),
+                "pool planes in");
+            for (int k = 0; k < p->K; ++k)
+                for (int par = 0; par < 2; ++par) {
+                    void *args[] = {&T, &k, &par, &part};
+                    PCK(p, launch_pdl((const void *)pool_msg_half_kernel, dim3(p->planes_grid), dim3(kVBlock), ps, args,
+                                      p->pdl),
+                        "pool plane half-sweep launch");
+                }
+            void *cout[] = {&T, &to_bytes, &part};
+            PCK(p, launch_pdl((const void *)pool_planes_convert_kernel, dim3(p->grid_blocks), dim3(kVBlock), ps, cout,
+                              p->pdl),
+                "pool planes out");
+            PCK(p, cudaEventRecord(p->planes_join[part], ps), "planes join event");
+        }
     }
     if (streamed) {
         // the parts of the byte-streamed jobs as concurrent chains, joined before
@@ -725,7 +748,9 @@ int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
             PCK(p, cudaStreamWaitEvent(st, p->chain_join[c], 0), "chain join wait");
         }
     }
-    if (planes) PCK(p, cudaStreamWaitEvent(st, p->planes_join, 0), "planes join wait");
+    if (planes)
+        for (int part = 0; part < p->chains; ++part)
+            PCK(p, cudaStreamWaitEvent(st, p->planes_join[part], 0), "planes join wait");
     if (streamed || planes) {
         int K = p->K;
         void *eargs[] = {&T};
@@ -747,7 +772,7 @@ int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
 int tick_launches(micsa_pool_t p, int mask) {
     const int resident = (mask & 1) && p->resident_smem ? 1 : 0;
     const int streamed = (mask & 2) ? 2 * p->chains * p->K : 0;
-    const int planes = (mask & 4) ? 2 * p->K + 2 : 0;
+    const int planes = (mask & 4) ? p->chains * (2 * p->K + 2) : 0;
     return resident + streamed + planes + ((mask & 6) ? 3 : 0) + 1;
 }
 
@@ -826,7 +851,7 @@ int micsa_pool_create(size_t arena_bytes, int max_jobs, int tick_sweeps, micsa_p
             (e = cudaMalloc(&p->d_vblocks, sizeof(VBlock) * (size_t)p->max_vblocks)) != cudaSuccess ||
             (e = cudaMalloc(&p->d_nvb, (kPoolMaxChains + 1) * sizeof(int32_t))) != cudaSuccess ||
             (e = cudaMalloc(&p->d_pvblocks, sizeof(PVBlock) * (size_t)p->max_pvblocks)) != cudaSuccess ||
-            (e = cudaMalloc(&p->d_npvb, sizeof(int32_t))) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_npvb, kPoolMaxChains * sizeof(int32_t))) != cudaSuccess ||
             (e = cudaMalloc(&p->d_results, sizeof(long long) * 4 * (size_t)max_jobs * kPoolMaxR)) != cudaSuccess ||
             (e = cudaMalloc(&p->d_acc, sizeof(unsigned long long) * 2 * (size_t)max_jobs * kPoolMaxR)) != cudaSuccess ||
             (e = cudaMalloc(&p->d_improved, sizeof(int32_t) * (size_t)max_jobs * kPoolMaxR)) != cudaSuccess) { bail(MICSA_E_OOM); break; }
@@ -836,15 +861,15 @@ int micsa_pool_create(size_t arena_bytes, int max_jobs, int tick_sweeps, micsa_p
             (e = cudaMallocHost(&p->h_vblocks, sizeof(VBlock) * (size_t)p->max_vblocks)) != cudaSuccess ||
             (e = cudaMallocHost(&p->h_nvb, (kPoolMaxChains + 1) * sizeof(int32_t))) != cudaSuccess ||
             (e = cudaMallocHost(&p->h_pvblocks, sizeof(PVBlock) * (size_t)p->max_pvblocks)) != cudaSuccess ||
-            (e = cudaMallocHost(&p->h_npvb, sizeof(int32_t))) != cudaSuccess) { bail(MICSA_E_OOM); break; }
+            (e = cudaMallocHost(&p->h_npvb, kPoolMaxChains * sizeof(int32_t))) != cudaSuccess) { bail(MICSA_E_OOM); break; }
         for (int c = 0; c <= kPoolMaxChains; ++c) p->h_nvb[c] = 0;
-        *p->h_npvb = 0;
+        for (int c = 0; c < kPoolMaxChains; ++c) p->h_npvb[c] = 0;
         for (auto &ev : p->stage_free)
             if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         if (rc) break;
         if ((e = cudaMemsetAsync(p->d_jobs, 0, sizeof(JobDesc) * max_jobs, p->stream)) != cudaSuccess ||
             (e = cudaMemsetAsync(p->d_nvb, 0, (kPoolMaxChains + 1) * sizeof(int32_t), p->stream)) != cudaSuccess ||
-            (e = cudaMemsetAsync(p->d_npvb, 0, sizeof(int32_t), p->stream)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+            (e = cudaMemsetAsync(p->d_npvb, 0, kPoolMaxChains * sizeof(int32_t), p->stream)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         // jobs of L <= 32 live in shared memory as bit planes (multispin kernel)
         p->resident_smem = multispin_smem_bytes(make_geometry(32));
         const int res_per_sm = multispin_blocks_per_sm(true, p->resident_smem);
@@ -864,9 +889,11 @@ int micsa_pool_create(size_t arena_bytes, int max_jobs, int tick_sweeps, micsa_p
         int per_sm_planes = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_planes, pool_msg_half_kernel, kVBlock, 0);
         p->planes_grid = (per_sm_planes > 0 ? per_sm_planes : 4) * p->sm_count;
-        if ((e = cudaStreamCreateWithFlags(&p->planes_stream, cudaStreamNonBlocking)) != cudaSuccess ||
-            (e = cudaEventCreateWithFlags(&p->planes_fork, cudaEventDisableTiming)) != cudaSuccess ||
-            (e = cudaEventCreateWithFlags(&p->planes_join, cudaEventDisableTiming)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+        if ((e = cudaEventCreateWithFlags(&p->planes_fork, cudaEventDisableTiming)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+        for (int c = 0; c < kPoolMaxChains && e == cudaSuccess; ++c)
+            if ((e = cudaStreamCreateWithFlags(&p->planes_stream[c], cudaStreamNonBlocking)) == cudaSuccess)
+                e = cudaEventCreateWithFlags(&p->planes_join[c], cudaEventDisableTiming);
+        if (e != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         p->grid_blocks = (per_sm > 0 ? per_sm : 4) * p->sm_count;
         p->tick_events.resize(64);
         for (auto &ev : p->tick_events)
@@ -912,12 +939,14 @@ void micsa_pool_destroy(micsa_pool_t p) {
     cudaFree(p->d_npvb);
     cudaFreeHost(p->h_pvblocks);
     cudaFreeHost(p->h_npvb);
-    if (p->planes_stream) {
-        cudaStreamSynchronize(p->planes_stream);
-        cudaStreamDestroy(p->planes_stream);
+    for (int c = 0; c < kPoolMaxChains; ++c) {
+        if (p->planes_stream[c]) {
+            cudaStreamSynchronize(p->planes_stream[c]);
+            cudaStreamDestroy(p->planes_stream[c]);
+        }
+        if (p->planes_join[c]) cudaEventDestroy(p->planes_join[c]);
     }
     if (p->planes_fork) cudaEventDestroy(p->planes_fork);
-    if (p->planes_join) cudaEventDestroy(p->planes_join);
     if (p->capture_stream) cudaStreamDestroy(p->capture_stream);
     if (p->aux_stream) {
         cudaStreamSynchronize(p->aux_stream);
