@@ -57,3 +57,29 @@ def test_bad_temperatures_rejected(lib):
             micsa.daemon_thresholds(T)
         with pytest.raises(micsa.MicsaError):
             micsa.metro_thresholds(T)
+
+
+def test_pool_job_bytes_counts_plane_storage_for_plane_jobs(lib):
+    """Host-only: a job's arena bytes are its bonds, spins, daemons, best
+    configuration and refresh cut points, plus bit-plane storage exactly for the
+    jobs the pool sweeps as bit planes (L a multiple of 8, at least 40)."""
+    def align(n):
+        return (n + 255) // 256 * 256
+
+    for L in (8, 16, 30, 32, 34, 40, 42, 48, 50, 64, 66, 72, 96, 128):
+        for R, n, r in ((1, 1000, 10), (2, 77, 5), (4, 10, 1)):
+            Lh = L // 2
+            P = 4 * ((Lh + 3) // 4)
+            half = L * L * P
+            n_refresh = max(1, (n + r - 1) // r)
+            expect = align(2 * half) + 2 * align(R * 2 * half) + align(R * max(L ** 3, 2 * half)) + align(24 * n_refresh)
+            if L % 8 == 0 and L >= 40:
+                WP = L * ((L + 31) // 32) * Lh
+                expect += align(4 * 6 * WP * R) + align(4 * 12 * WP)
+            assert micsa.Pool.job_bytes(L, R, n, r) == expect, (L, R, n, r)
+
+
+def test_pool_calls_reject_a_null_pool(lib):
+    assert lib.micsa_pool_set_planes(None, 1) == micsa.MICSA_E_INVALID_ARG
+    assert lib.micsa_pool_set_shape(None, 4, 2) == micsa.MICSA_E_INVALID_ARG
+    assert lib.micsa_pool_set_launch_config(None, 0, 1, 1) == micsa.MICSA_E_INVALID_ARG
