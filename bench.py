@@ -383,6 +383,12 @@ def leg_paper_shape(micsa, timer, stream, peaks, L=160, R=128, sweeps=400):
     out["multispin_flips_per_ns"] = updates(L, 1, R, sweeps) / (ms * 1e6)
     out["multispin_ns_per_sweep"] = 1e6 * ms / sweeps
     out["multispin_roofline"] = plane_roofline(micsa, timer, stream, g, peaks, n_plain=200)
+    # the RNG-per-update Metropolis on the same bit planes (one uniform per site and
+    # sweep from the same Philox counters): the paper's own comparison at this shape
+    n_m = max(10, sweeps // 4)
+    g.run_metropolis(np.full(n_m, 0.7))  # as long as the timed run
+    ms = timer(lambda: g.run_metropolis(np.full(n_m, 0.7)))
+    out["metropolis_planes_flips_per_ns"] = updates(L, 1, R, n_m) / (ms * 1e6)
     g.set_engine("stream")
     g.set_launch_config(4, 128, -1, True, 64)
     g.reinit(10)
@@ -412,6 +418,10 @@ def leg_paper_shape(micsa, timer, stream, peaks, L=160, R=128, sweeps=400):
     ms = timer(lambda: g6.run_logrefresh(np.full(128, 0.7)))
     g6.close()
     out["walkers_gamma6_flips_per_ns"] = updates(L, 1, R, 128 * 6) / (ms * 1e6)
+    out["micsa_over_metropolis_planes"] = {
+        "daemons_refresh_10": out["multispin_flips_per_ns"] / out["metropolis_planes_flips_per_ns"],
+        "one_walker_log_refresh": out["walkers_log_refresh_flips_per_ns"] / out["metropolis_planes_flips_per_ns"],
+        "paper_h100_walkers_vs_metropolis": 1.9}
     out["paper_h100_walkers_total_ns_per_sweep"] = 121554 + 97378
     out["paper_h100_spin_update_kernel_ns_per_sweep"] = 121554
     out["paper_h100_flips_per_ns"] = 128 * 160 ** 3 / 121554.0

@@ -200,8 +200,9 @@ int micsa_set_launch_config(micsa_t h, int words_per_thread, int block, int bloc
  *                          per spin: (2 + 4 gamma) / 16 bytes per replica,
  *                          (2 + 8 gamma) / 16 with walkers, 0.75 per sample.
  * An engine whose size limit the lattice exceeds is rejected. Runs with gamma
- * > 1 or walkers on any engine but MULTISPIN_GLOBAL, and Metropolis runs, use
- * the streaming kernel.
+ * > 1 or walkers on any engine but MULTISPIN_GLOBAL use the streaming kernel;
+ * Metropolis runs use it too, except on MULTISPIN_GLOBAL with gamma == 1 and no
+ * walkers, where they run on the bit planes (the same Philox counters).
  * resident_sweeps only matters to RESIDENT, MULTISPIN and ONCHIP. Synchronizes.
  * (App. B and Sec. 2.5 describe the multispin Boolean update.) */
 #define MICSA_ENGINE_AUTO 0

@@ -225,10 +225,10 @@ int msg_rpt(const micsa_ctx *h, int nw, int n_rep) {
 // One half-sweep of the bit-plane engine over replicas [r0, r1), reading
 // params[*cursor + k].
 cudaError_t launch_planes_half(micsa_t h, const LaunchConfig &lc, int parity, const int64_t *cursor, int64_t k,
-                               int r0, int r1, cudaStream_t st) {
+                               int r0, int r1, cudaStream_t st, bool metro = false) {
     return launch_msg_half(h->d_planes, h->d_bplanes, h->geo, h->S, h->R, r0, r1, msg_rpt(h, lc.nw, r1 - r0), lc.nw,
                            lc.regcap, parity, h->gamma, h->walkers, (uint32_t)(h->seed & 0xFFFFFFFFu), (uint32_t)(h->seed >> 32),
-                           h->d_params, cursor, k, lc.pdl, st);
+                           h->d_params, cursor, k, lc.pdl, st, metro);
 }
 
 // One timestep of the bit-plane engine for replicas [r0, r1): gamma sweeps
@@ -362,13 +362,13 @@ int ensure_planes(micsa_t h) {
 // planes in HBM: bytes -> planes, whole blocks of G timesteps by graph replay,
 // the rest directly, planes -> bytes. A timestep is gamma sweeps (each the even
 // half-sweep followed by the odd one) and, with walkers, the wandering step.
-int run_planes(micsa_t h, int64_t n, const LaunchConfig &lc) {
+int run_planes(micsa_t h, int64_t n, const LaunchConfig &lc, bool metro = false) {
     if (int rc = ensure_planes(h)) return rc;
     const int buf0 = h->walkers ? (int)(h->t & 1) : 0, buf1 = h->walkers ? (int)((h->t + n) & 1) : 0;
     CK(h, msg_convert(h->d_planes, h->d_bplanes, h->d_spins, h->d_daemons, h->d_bonds, h->geo, h->S, h->R, h->gamma,
                       h->walkers, buf0, true, h->stream), "convert to planes");
     h->launches += 2;
-    const int G = lc.graph_sweeps;
+    const int G = metro ? 0 : lc.graph_sweeps;  // Metropolis sweeps: direct launches
     int64_t done = 0;
     if (G > 0 && n >= 2 * (int64_t)G) {
         if (int rc = capture_graph(h, kGraphPlanes, G, lc)) return rc;
@@ -379,6 +379,12 @@ int run_planes(micsa_t h, int64_t n, const LaunchConfig &lc) {
         done = reps * G;
     }
     for (int64_t k = done; k < n; ++k) {
+        if (metro) {  // one sweep per timestep (gamma 1)
+            for (int p = 0; p < 2; ++p)
+                CK(h, launch_planes_half(h, lc, p, nullptr, k, 0, h->R, h->stream, true), "plane Metropolis launch");
+            h->launches += 2;
+            continue;
+        }
         CK(h, launch_planes_timestep(h, lc, nullptr, k, 0, h->R, h->stream), "plane timestep launch");
         h->launches += planes_timestep_kernels(h);
     }
@@ -502,7 +508,10 @@ int run_table(micsa_t h, bool metro, int64_t n) {
                           cudaMemcpyHostToDevice, h->stream), "upload sweep parameters");
     CK(h, cudaEventRecord(h->params_free, h->stream), "record parameter event");
     if (!metro && use_resident(h)) return run_resident(h, n, lc);
-    if (!metro && active_engine(h) == MICSA_ENGINE_MULTISPIN_GLOBAL) return run_planes(h, n, lc);
+    // bit planes: MicSA, and Metropolis with one daemon family and no walkers (a
+    // timestep is then one sweep; the daemon planes ride along unchanged)
+    if (active_engine(h) == MICSA_ENGINE_MULTISPIN_GLOBAL && (!metro || (h->gamma == 1 && !h->walkers)))
+        return run_planes(h, n, lc, metro);
     if (!metro && active_engine(h) == MICSA_ENGINE_ONCHIP) return run_onchip(h, n, lc);
     const int G = lc.graph_sweeps;
     int64_t done = 0;

@@ -205,7 +205,7 @@ cudaError_t launch_msg_wander(uint32_t *planes, const Geometry &g, int S, int R,
 int msg_default_rpt(const Geometry &g, int S, int R, int nw, int sm_count);
 cudaError_t launch_msg_half(uint32_t *planes, const uint32_t *bplanes, const Geometry &g, int S, int R, int r0,
                             int r1, int rpt, int nw, bool regcap, int parity, int gamma, int walkers, uint32_t key0, uint32_t key1, const SweepParam *params,
-                            const int64_t *cursor, int64_t k, bool pdl, cudaStream_t st);
+                            const int64_t *cursor, int64_t k, bool pdl, cudaStream_t st, bool metro = false);
 cudaError_t launch_advance_cursor(int64_t *cursor, int64_t step, bool pdl, cudaStream_t st);
 // wandering of every walker family after timestep t (parity t & 1), Sec. 2.6
 cudaError_t launch_wander(uint8_t *daemons, Geometry g, int64_t n_rep, int gamma, int parity, cudaStream_t st);

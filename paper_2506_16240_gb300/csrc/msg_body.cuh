@@ -61,6 +61,19 @@ __device__ __forceinline__ void shift_in_cuts(uint32_t u, uint32_t n0, uint32_t 
         : "r"(u), "r"(n0), "r"(n1), "r"(n2));
 }
 
+// x_k = 2 x_k + [u < t_k] for three Metropolis cut points: the carry out of
+// t_k + ~u is set exactly when t_k > u.
+__device__ __forceinline__ void shift_in_below(uint32_t u, uint32_t t0, uint32_t t1, uint32_t t2, uint32_t &x0,
+                                               uint32_t &x1, uint32_t &x2) {
+    const uint32_t nu = ~u;
+    asm("{\n\t.reg .u32 t;\n\t"
+        "add.cc.u32 t, %3, %6;\n\taddc.u32 %0, %0, %0;\n\t"
+        "add.cc.u32 t, %4, %6;\n\taddc.u32 %1, %1, %1;\n\t"
+        "add.cc.u32 t, %5, %6;\n\taddc.u32 %2, %2, %2;\n\t}"
+        : "+r"(x0), "+r"(x1), "+r"(x2)
+        : "r"(t0), "r"(t1), "r"(t2), "r"(nu));
+}
+
 __device__ __forceinline__ void prefetch_l2(const uint32_t *p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
@@ -185,12 +198,14 @@ __device__ __forceinline__ void msg_convert_word(uint32_t *planes, int8_t *spins
 // Philox block, so the threads of a warp must all be active. RAGGED: the last
 // word of a z column holds Lz = L - 32 (nzw - 1) sites (L a multiple of 8, any
 // L >= 32; no walkers): the z wrap goes through bit Lz - 1 of that word, and its
-// bits from Lz up stay zero.
-template <int NW, bool RAGGED = false>
+// bits from Lz up stay zero. METRO: the Metropolis sweep on the same planes
+// (the daemon planes are neither read nor written).
+template <int NW, bool RAGGED = false, bool METRO = false>
 __device__ __forceinline__ void msg_update(const MsgLattice &a, const SweepParam &prm, int p, int zw, int y, int ig,
                                            int r_begin, int r_end) {
     constexpr int G = 4 / NW;  // lanes sharing one Philox block of words
     const bool refresh = prm.mode == kModeRefresh;
+    constexpr bool metro = METRO;  // Metropolis sweeps (one daemon family, no walkers)
     const int o = 1 - p;
     const int L = a.L, Lh = a.Lh;
     const int i0 = NW * ig;
@@ -248,6 +263,7 @@ __device__ __forceinline__ void msg_update(const MsgLattice &a, const SweepParam
         Vec<NW>::ld(O + w_zm, Ozm);
         const uint32_t Oip = O[w_ip], Oim = O[w_im];
         Vec<NW>::ld(Sp + wc, Sg);
+        uint32_t a2v[NW];  // Metropolis: the acceptance bits of dH = 12 (of dH = 4, 8 in m0v, m1v)
         if (refresh) {  // fresh daemons of parity p before its half-sweep (Sec. 2.7)
             // z = 32 zw + b for b in this lane's range, from the top down: each new
             // bit enters at the bottom (a = 2 a + bit); m1 = [u >= c1], m0 = the parity
@@ -285,6 +301,44 @@ __device__ __forceinline__ void msg_update(const MsgLattice &a, const SweepParam
                 m0v[w] = (j == 0 ? a0[0] : j == 1 ? a0[1] : j == 2 ? a0[2] : a0[3]) & zmask;
                 m1v[w] = (j == 0 ? a1[0] : j == 1 ? a1[1] : j == 2 ? a1[2] : a1[3]) & zmask;
             }
+        } else if (metro) {
+            // Metropolis (the canonical baseline of Sec. 2.4): one uniform per site from
+            // the Philox block of its quad (lane i & 3, the Metropolis tag), z = 32 zw + b
+            // from the top down; x_k collects [u < theta_k], the acceptance of dH =
+            // 4 (k + 1), theta_k = 2^32 accepting every u. m0v, m1v, a2v take the planes.
+            uint32_t x0[4] = {0, 0, 0, 0}, x1[4] = {0, 0, 0, 0}, x2[4] = {0, 0, 0, 0};
+            const uint32_t mt0 = (uint32_t)prm.th0, mt1 = (uint32_t)prm.th1, mt2 = (uint32_t)prm.th2;
+#pragma unroll 2
+            for (int c = 32 / G - 1; c >= 0; --c) {
+                const int b = lig * (32 / G) + c;
+                const uint4 w = philox_wide(make_uint4(quad0 + (uint32_t)b * (uint32_t)L * (uint32_t)a.W4, (uint32_t)prm.t,
+                                                       ((uint32_t)gid << 2) | kTagMetro, (uint32_t)((uint64_t)prm.t >> 32)),
+                                            rk);
+                const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                for (int j = 0; j < 4; ++j) shift_in_below(u[j], mt0, mt1, mt2, x0[j], x1[j], x2[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                x0[j] = ((prm.th0 >> 32) ? ~0u : x0[j]) << (lig * (32 / G));
+                x1[j] = ((prm.th1 >> 32) ? ~0u : x1[j]) << (lig * (32 / G));
+                x2[j] = ((prm.th2 >> 32) ? ~0u : x2[j]) << (lig * (32 / G));
+            }
+#pragma unroll
+            for (int off = 1; off < G; off <<= 1)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    x0[j] |= __shfl_xor_sync(0xFFFFFFFFu, x0[j], off);
+                    x1[j] |= __shfl_xor_sync(0xFFFFFFFFu, x1[j], off);
+                    x2[j] |= __shfl_xor_sync(0xFFFFFFFFu, x2[j], off);
+                }
+#pragma unroll
+            for (int w = 0; w < NW; ++w) {
+                const int j = (i0 + w) & 3;
+                m0v[w] = (j == 0 ? x0[0] : j == 1 ? x0[1] : j == 2 ? x0[2] : x0[3]) & zmask;
+                m1v[w] = (j == 0 ? x1[0] : j == 1 ? x1[1] : j == 2 ? x1[2] : x1[3]) & zmask;
+                a2v[w] = (j == 0 ? x2[0] : j == 1 ? x2[1] : j == 2 ? x2[2] : x2[3]) & zmask;
+            }
         } else if (gather) {  // the walkers arrive through the previous wandering step
             const uint32_t *G0 = pl + (int64_t)gplane * a.WP;
             gather_words<NW>(G0, gdd, wc, w_ip, w_im, w_yp, w_ym, w_zp, w_zm, M, m0v);
@@ -320,18 +374,28 @@ __device__ __forceinline__ void msg_update(const MsgLattice &a, const SweepParam
             const uint32_t u0 = s1 ^ s2, kk = s1 & s2;
             const uint32_t u1 = c1 ^ c2 ^ kk, u2 = (c1 & c2) | (kk & (c1 ^ c2));
             const uint32_t m0 = m0v[w], m1 = m1v[w];
-            const uint32_t v0 = u0 ^ m0, k0 = u0 & m0;
-            const uint32_t v1 = u1 ^ m1 ^ k0, k1 = (u1 & m1) | (k0 & (u1 ^ m1));
-            const uint32_t v2 = u2 ^ k1, v3 = u2 & k1;
-            // Eq. (Creutz) with Eq. (flip-OK): accept <=> 3 <= u + m <= 6, m' = u + m - 3
-            const uint32_t acc = (v2 ^ (v1 & v0)) & ~v3 & zmask;
-            m0v[w] = (m0 & ~acc) | (~v0 & acc);
-            m1v[w] = (m1 & ~acc) | (v2 & (v1 | v0) & acc);
+            uint32_t acc;
+            if (metro) {
+                // dH = 12 - 4u: accepted when dH <= 0 (u >= 3), else by the site's bit of dH
+                const uint32_t nu2 = ~u2;
+                acc = (u2 | (u1 & u0)) | (nu2 & u1 & ~u0 & m0) | (nu2 & ~u1 & u0 & m1) | (nu2 & ~u1 & ~u0 & a2v[w]);
+                acc &= zmask;
+            } else {
+                const uint32_t v0 = u0 ^ m0, k0 = u0 & m0;
+                const uint32_t v1 = u1 ^ m1 ^ k0, k1 = (u1 & m1) | (k0 & (u1 ^ m1));
+                const uint32_t v2 = u2 ^ k1, v3 = u2 & k1;
+                // Eq. (Creutz) with Eq. (flip-OK): accept <=> 3 <= u + m <= 6, m' = u + m - 3
+                acc = (v2 ^ (v1 & v0)) & ~v3 & zmask;
+                m0v[w] = (m0 & ~acc) | (~v0 & acc);
+                m1v[w] = (m1 & ~acc) | (v2 & (v1 | v0) & acc);
+            }
             Sg[w] = sg ^ acc;
         }
         Vec<NW>::st(Sp + wc, Sg);
-        Vec<NW>::st(M0 + wc, m0v);
-        Vec<NW>::st(M1 + wc, m1v);
+        if (!metro) {
+            Vec<NW>::st(M0 + wc, m0v);
+            Vec<NW>::st(M1 + wc, m1v);
+        }
     }
 }
 

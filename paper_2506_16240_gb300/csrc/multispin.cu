@@ -447,7 +447,7 @@ struct MsgArgs {
 // MINB: minimum resident blocks of 128 per SM the register allocation must
 // allow (4: the default, at most 128 registers; 5: the register-capped
 // variant, at most 102).
-template <int NW, int MINB>
+template <int NW, int MINB, bool METRO = false>
 __global__ void __launch_bounds__(128, MINB) msg_half_kernel(MsgArgs a) {
     // parameters first: no kernel of a graph replay writes the table or the cursor
     const int64_t kidx = a.k + (a.cursor ? *a.cursor : 0);
@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(128, MINB) msg_half_kernel(MsgArgs a) {
                          a.L, a.Lh, a.nzw, a.W4, a.WP, a.np, a.gamma, a.walkers, (int64_t)sample * a.R,
                          a.key0, a.key1};
     const int r_begin = a.r0 + (int)blockIdx.y * a.rpt;
-    msg_update<NW>(lat, prm, a.parity, (int)zw_u, y, ig, r_begin, min(a.r1, r_begin + a.rpt));
+    msg_update<NW, false, METRO>(lat, prm, a.parity, (int)zw_u, y, ig, r_begin, min(a.r1, r_begin + a.rpt));
 }
 
 // bytes <-> planes. One thread per plane word (n_rep replicas, two parities,
@@ -610,7 +610,7 @@ cudaError_t launch_msg_wander(uint32_t *planes, const Geometry &g, int S, int R,
 cudaError_t launch_msg_half(uint32_t *planes, const uint32_t *bplanes, const Geometry &g, int S, int R, int r0,
                             int r1, int rpt, int nw, bool regcap, int parity, int gamma, int walkers, uint32_t key0,
                             uint32_t key1, const SweepParam *params, const int64_t *cursor, int64_t k, bool pdl,
-                            cudaStream_t st) {
+                            cudaStream_t st, bool metro) {
     MsgArgs a{};
     a.gamma = gamma;
     a.walkers = walkers;
@@ -647,6 +647,11 @@ cudaError_t launch_msg_half(uint32_t *planes, const uint32_t *bplanes, const Geo
     attr[0].val.programmaticStreamSerializationAllowed = pdl ? 1 : 0;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    if (metro) {  // Metropolis sweeps on the planes (gamma 1, no walkers)
+        if (nw == 4) return cudaLaunchKernelEx(&cfg, msg_half_kernel<4, 4, true>, a);
+        if (nw == 2) return cudaLaunchKernelEx(&cfg, msg_half_kernel<2, 4, true>, a);
+        return cudaLaunchKernelEx(&cfg, msg_half_kernel<1, 4, true>, a);
+    }
     switch (nw * (regcap ? -1 : 1)) {
         case 1: return cudaLaunchKernelEx(&cfg, msg_half_kernel<1, 4>, a);
         case 2: return cudaLaunchKernelEx(&cfg, msg_half_kernel<2, 4>, a);

@@ -619,3 +619,24 @@ def test_equilibrium_energy_at_T14_is_the_canonical_value():
     assert abs(e_mic - -1.607026) < 2.5e-3, e_mic
     assert abs(e_met - -1.607026) < 2.5e-3, e_met
     assert abs(e_mic - e_met) < 1e-3, (e_mic, e_met)
+
+
+@pytest.mark.parametrize("L,S,R,graph", [(32, 2, 3, 8), (64, 1, 2, 8), (32, 1, 1, 0), (96, 1, 2, 16)])
+def test_metropolis_on_bit_planes_matches_oracle(L, S, R, graph):
+    """Metropolis on the bit-plane engine (one uniform per site from the same Philox
+    counters as the byte kernel, the three acceptance planes of dH = 4, 8, 12),
+    interleaved with MicSA sweeps on the planes; T = 1e6 makes every cut point 2^32."""
+    seed = 5 * L + R
+    sched_m = np.concatenate([np.linspace(3.0, 0.6, 37), [1e6, 1e6, 0.9]])
+    sched_a = np.linspace(2.0, 0.7, 19)
+    st = O.create(L, S, R, seed)
+    O.run_metropolis(st, sched_m)
+    O.run(st, sched_a, 4)
+    O.run_metropolis(st, sched_m[:9])
+    with micsa.Micsa(L, S, R, seed) as g:
+        g.set_engine("multispin_global")
+        g.set_launch_config(4, 128, -1, True, graph)
+        g.run_metropolis(sched_m)
+        g.run(sched_a, 4)
+        g.run_metropolis(sched_m[:9])
+        assert_same_state(g, st, f"L={L} metropolis on planes")
