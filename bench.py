@@ -304,9 +304,9 @@ def plane_roofline(micsa, timer, stream, g, peaks, n_plain=2000):
     peak = hbm if hbm else 6800.0
     achieved = bytes_per_launch / (launch_us * 1e-6) / 1e9
     # DRAM bytes per launch from the ncu capture at L = 160, 128 replicas, 4 words per
-    # thread (profiles/msg_half_L160x128_full.md: 132.67 MB read + 44.27 MB written)
+    # thread (profiles/msg_half_L160x128_full.md: 132.67 MB read + 44.67 MB written)
     shape = g.launch_config()
-    traffic = 176.9e6 if (L == 160 and R == 128 and shape["words_per_thread"] == 4) else None
+    traffic = 177.3e6 if (L == 160 and R == 128 and shape["words_per_thread"] == 4) else None
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": traffic, "peak_source": "measured" if hbm else "fallback",
             "kernel": "micsa::msg_half_kernel (bit-plane MicSA half-sweep, no refresh)",
