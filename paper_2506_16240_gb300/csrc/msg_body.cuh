@@ -246,7 +246,7 @@ __device__ __forceinline__ void msg_update(const MsgLattice &a, const SweepParam
             const uint32_t *nx = pl + (int64_t)a.np * a.WP;
             prefetch_l2(nx + (int64_t)p * a.WP + wc);
             prefetch_l2(nx + (int64_t)o * a.WP + wc);
-            if (!refresh) {
+            if (!refresh && !metro) {  // (a Metropolis sweep reads no daemon words)
                 prefetch_l2(nx + (int64_t)mread * a.WP + wc);
                 prefetch_l2(nx + (int64_t)(mread + 2) * a.WP + wc);
             }

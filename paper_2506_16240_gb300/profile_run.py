@@ -4,6 +4,7 @@
     python -m paper_2506_16240_gb300.profile_run chains     # the same with the two replicas as two chains
     python -m paper_2506_16240_gb300.profile_run multispin  # L=32, 64 x 2: 128 sweeps, blocks of 64
     python -m paper_2506_16240_gb300.profile_run planes     # L=160, 1 x 128, bit planes: 12 sweeps
+    python -m paper_2506_16240_gb300.profile_run planes_metro  # the same lattice, 12 Metropolis sweeps
     python -m paper_2506_16240_gb300.profile_run onchip     # L=160, 1 x 2, on-chip engine: 2 x 64 sweeps
     python -m paper_2506_16240_gb300.profile_run tma        # L=160, 1 x 2, TMA engine: 12 sweeps
     python -m paper_2506_16240_gb300.profile_run pool       # 64 mixed jobs, 2 ticks of 64 sweeps
@@ -39,6 +40,14 @@ def planes():
     g.set_engine("multispin_global")
     g.set_launch_config(4, 128, -1, True, 0)  # direct launches
     g.run(np.full(12, 0.7), 10)
+    return g.measure()[0][:4]
+
+
+def planes_metro():
+    g = micsa.Micsa(160, 1, 128, 3)
+    g.set_engine("multispin_global")
+    g.set_launch_config(4, 128, -1, True, 0)  # direct launches
+    g.run_metropolis(np.full(12, 0.7))
     return g.measure()[0][:4]
 
 
@@ -78,6 +87,7 @@ def pool():
 
 if __name__ == "__main__":
     mode = sys.argv[1] if len(sys.argv) > 1 else "stream"
-    modes = {"stream": stream, "chains": chains, "multispin": multispin, "planes": planes, "onchip": onchip,
+    modes = {"stream": stream, "chains": chains, "multispin": multispin, "planes": planes,
+             "planes_metro": planes_metro, "onchip": onchip,
              "tma": tma, "pool": pool}
     print(mode, modes[mode]())
