@@ -102,7 +102,8 @@ def test_config_l32_quench_observables():
 def test_metropolis_bit_exact():
     for L, S, R, n in [(4, 2, 3, 20), (10, 1, 2, 15), (32, 1, 2, 8), (30, 2, 1, 7)]:
         seed = 31 * L
-        sched = np.linspace(2.0, 0.6, n)
+        # (T = 0.5 and 0.3 end with the cut points of dH = 12 and 8 at zero)
+        sched = np.concatenate([np.linspace(2.0, 0.6, n), [0.5, 0.3]])
         with micsa.Micsa(L, S, R, seed) as g:
             st = O.create(L, S, R, seed)
             g.run_metropolis(sched)
@@ -621,13 +622,16 @@ def test_equilibrium_energy_at_T14_is_the_canonical_value():
     assert abs(e_mic - e_met) < 1e-3, (e_mic, e_met)
 
 
-@pytest.mark.parametrize("L,S,R,graph", [(32, 2, 3, 8), (64, 1, 2, 8), (32, 1, 1, 0), (96, 1, 2, 16)])
-def test_metropolis_on_bit_planes_matches_oracle(L, S, R, graph):
+@pytest.mark.parametrize("L,S,R,graph,nw", [(32, 2, 3, 8, 4), (64, 1, 2, 8, 2), (32, 1, 1, 0, 1), (96, 1, 2, 16, 4)])
+def test_metropolis_on_bit_planes_matches_oracle(L, S, R, graph, nw):
     """Metropolis on the bit-plane engine (one uniform per site from the same Philox
     counters as the byte kernel, the three acceptance planes of dH = 4, 8, 12),
-    interleaved with MicSA sweeps on the planes; T = 1e6 makes every cut point 2^32."""
+    interleaved with MicSA sweeps on the planes, at 1, 2 and 4 plane words per thread
+    (1 and 2: the lanes sharing a Philox block split its uniforms); T = 1e6 makes
+    every cut point 2^32, T = 0.5 the cut point of dH = 12 zero and T = 0.3 that of
+    dH = 8 too."""
     seed = 5 * L + R
-    sched_m = np.concatenate([np.linspace(3.0, 0.6, 37), [1e6, 1e6, 0.9]])
+    sched_m = np.concatenate([np.linspace(3.0, 0.6, 37), [1e6, 1e6, 0.9, 0.5, 0.3, 0.3, 0.7]])
     sched_a = np.linspace(2.0, 0.7, 19)
     st = O.create(L, S, R, seed)
     O.run_metropolis(st, sched_m)
@@ -635,7 +639,7 @@ def test_metropolis_on_bit_planes_matches_oracle(L, S, R, graph):
     O.run_metropolis(st, sched_m[:9])
     with micsa.Micsa(L, S, R, seed) as g:
         g.set_engine("multispin_global")
-        g.set_launch_config(4, 128, -1, True, graph)
+        g.set_launch_config(nw, 128, -1, True, graph)
         g.run_metropolis(sched_m)
         g.run(sched_a, 4)
         g.run_metropolis(sched_m[:9])
