@@ -3,9 +3,11 @@
 The paper compares MicSA with the canonical (Metropolis) dynamics by a single
 time-rescaling factor k: after t_plot = k * t_MicSA the two relaxations coincide,
 and k* ~ gamma for gamma walkers per spin (Sec. 3, Table (k*), Fig. 1). The
-paper extracts k* from the coherence length xi_12; its integral estimators are
-not given there, so here k is fitted to the energy per spin, which the paper
-also compares after the rescaling (Fig. 1, Eq. (delta1)).
+paper extracts k* from the coherence length xi_12 = I_2 / I_1 (Eq. (xi-def)),
+with the integrals of C4 estimated as in its references. Here the integrals
+are lattice sums cut where C4 falls into its noise (c4_integrals), and the same
+fit of k (fit_time_rescaling) applies to xi_12(t) and to the energy per spin,
+which the paper also compares after the rescaling (Fig. 1, Eq. (delta1)).
 """
 import numpy as np
 
