@@ -229,6 +229,12 @@ def test_metro_cut_points():
         th = O.metro_thresholds(T)
         for k in range(3):
             assert abs(int(th[k]) - math.exp(-4 * (k + 1) / T) * 2 ** 32) <= 1
+    # the extremes: exp(-beta dH) rounds to 1 (every move accepted) once beta dH
+    # is below 2^-53, and e^-40 2^32, e^-80/3 2^32 are below 1 (never accepted)
+    assert [int(v) for v in O.metro_thresholds(1e20)] == [2 ** 32] * 3
+    assert [int(v) for v in O.metro_thresholds(1e6)] == [math.floor(math.exp(-4 * k * 1e-6) * 2 ** 32) for k in (1, 2, 3)]
+    assert [int(v) for v in O.metro_thresholds(0.3)] == [math.floor(math.exp(-4 / 0.3) * 2 ** 32), 0, 0]
+    assert int(O.metro_thresholds(0.5)[2]) == 0 < int(O.metro_thresholds(0.5)[1])
 
 
 # --------------------------------------------------- exact L = 2 dynamics --

@@ -102,8 +102,8 @@ def test_config_l32_quench_observables():
 def test_metropolis_bit_exact():
     for L, S, R, n in [(4, 2, 3, 20), (10, 1, 2, 15), (32, 1, 2, 8), (30, 2, 1, 7)]:
         seed = 31 * L
-        # (T = 0.5 and 0.3 end with the cut points of dH = 12 and 8 at zero)
-        sched = np.concatenate([np.linspace(2.0, 0.6, n), [0.5, 0.3]])
+        # (T = 1e20: every cut point 2^32; T = 0.5 and 0.3: those of dH = 12 and 8 zero)
+        sched = np.concatenate([[1e20], np.linspace(2.0, 0.6, n), [0.5, 0.3]])
         with micsa.Micsa(L, S, R, seed) as g:
             st = O.create(L, S, R, seed)
             g.run_metropolis(sched)
@@ -627,11 +627,11 @@ def test_metropolis_on_bit_planes_matches_oracle(L, S, R, graph, nw):
     """Metropolis on the bit-plane engine (one uniform per site from the same Philox
     counters as the byte kernel, the three acceptance planes of dH = 4, 8, 12),
     interleaved with MicSA sweeps on the planes, at 1, 2 and 4 plane words per thread
-    (1 and 2: the lanes sharing a Philox block split its uniforms); T = 1e6 makes
-    every cut point 2^32, T = 0.5 the cut point of dH = 12 zero and T = 0.3 that of
-    dH = 8 too."""
+    (1 and 2: the lanes sharing a Philox block split its uniforms); T = 1e20 makes
+    every cut point 2^32, T = 1e6 puts them just below it, T = 0.5 makes the cut
+    point of dH = 12 zero and T = 0.3 that of dH = 8 too."""
     seed = 5 * L + R
-    sched_m = np.concatenate([np.linspace(3.0, 0.6, 37), [1e6, 1e6, 0.9, 0.5, 0.3, 0.3, 0.7]])
+    sched_m = np.concatenate([np.linspace(3.0, 0.6, 37), [1e20, 1e6, 0.9, 0.5, 0.3, 0.3, 0.7]])
     sched_a = np.linspace(2.0, 0.7, 19)
     st = O.create(L, S, R, seed)
     O.run_metropolis(st, sched_m)
