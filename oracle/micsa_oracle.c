@@ -126,7 +126,11 @@ void orc_init_couplings(int L, uint64_t seed, int64_t sample, int8_t *J) {
     for (int64_t i = 0; i < N; ++i) {
         uint32_t w[4];
         philox_seeded(seed, (uint32_t)i, 0, (uint32_t)(sample << 2) | TAG_COUPLING, 0, w);
+#if ORC_MUTANT == 5
+        for (int d = 0; d < 3; ++d) J[i * 3 + d] = (w[0] >= 0x80000000u) ? -1 : 1;  /* planted: one word for all three bonds */
+#else
         for (int d = 0; d < 3; ++d) J[i * 3 + d] = (w[d] >= 0x80000000u) ? -1 : 1;
+#endif
     }
 }
 
@@ -135,7 +139,11 @@ void orc_init_spins(int L, uint64_t seed, int64_t gid, int8_t *s) {
     for (int64_t i = 0; i < N; ++i) {
         uint32_t w[4];
         philox_seeded(seed, (uint32_t)i, 0, (uint32_t)(gid << 2) | TAG_SPIN, 0, w);
+#if ORC_MUTANT == 6
+        s[i] = (w[0] >= 0x40000000u) ? -1 : 1;  /* planted: p(s = -1) = 3/4 */
+#else
         s[i] = (w[0] >= 0x80000000u) ? -1 : 1;
+#endif
     }
 }
 
@@ -414,7 +422,11 @@ void orc_measure(int L, int S, int R, const int8_t *J, const int8_t *s, const ui
                 const int8_t *sa = s + ((int64_t)a * R + ra) * N;
                 const int8_t *sb = s + ((int64_t)a * R + rb) * N;
                 int64_t q = 0;
+#if ORC_MUTANT == 7
+                for (int64_t i = 0; i < N; ++i) q += sa[i] * sa[i];  /* planted: replica a with itself */
+#else
                 for (int64_t i = 0; i < N; ++i) q += sa[i] * sb[i];
+#endif
                 overlap[pair] = q;
             }
     }

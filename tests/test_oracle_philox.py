@@ -7,49 +7,11 @@ seed ``s`` and output offset ``4q`` returns the Philox4x32-10 block of counter
 many (seed, offset) pairs pins every counter word the project uses (the fourth
 word is zero for sweep indices below 2^32) and both key words.
 """
-import ctypes
-import ctypes.util
-import os
-
 import numpy as np
 import pytest
 
 import oracle
-
-CURAND_RNG_PSEUDO_PHILOX4_32_10 = 161
-
-
-def _load_curand():
-    cands = []
-    for d in ("/usr/local/cuda/lib64", "/usr/local/cuda/targets/sbsa-linux/lib",
-              "/usr/local/cuda/targets/x86_64-linux/lib"):
-        cands += [os.path.join(d, "libcurand.so"), os.path.join(d, "libcurand.so.10")]
-    found = ctypes.util.find_library("curand")
-    if found:
-        cands.append(found)
-    for c in cands:
-        try:
-            return ctypes.CDLL(c)
-        except OSError:
-            continue
-    return None
-
-
-_curand = _load_curand()
-
-
-def _curand_blocks(seed, offset, nwords):
-    lib = _curand
-    gen = ctypes.c_void_p()
-    assert lib.curandCreateGeneratorHost(ctypes.byref(gen), CURAND_RNG_PSEUDO_PHILOX4_32_10) == 0
-    try:
-        assert lib.curandSetPseudoRandomGeneratorSeed(gen, ctypes.c_ulonglong(seed)) == 0
-        assert lib.curandSetGeneratorOffset(gen, ctypes.c_ulonglong(offset)) == 0
-        out = np.zeros(nwords, np.uint32)
-        assert lib.curandGenerate(gen, out.ctypes.data_as(ctypes.c_void_p), ctypes.c_size_t(nwords)) == 0
-    finally:
-        lib.curandDestroyGenerator(gen)
-    return out
+from curand_host import curand as _curand, curand_words as _curand_blocks
 
 
 @pytest.mark.skipif(_curand is None, reason="libcurand not found")
