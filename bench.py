@@ -78,6 +78,9 @@ def parse(argv=None):
                     help="sweeps per step (profiling runs only; reported numbers use the default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="headline leg only")
+    ap.add_argument("--profile-case", choices=["stream", "chains", "multispin", "planes", "planes_metro",
+                                               "onchip", "tma", "pool"],
+                    help="run one small fixed workload for a profiler capture and exit")
     ap.add_argument("--serving-jobs", type=int, default=300,
                     help="jobs in the serving stream (the full stream is 2000)")
     return ap.parse_args(argv)
@@ -631,10 +634,101 @@ def leg_serving(micsa, torch, stream, n_jobs, n_cap=64):
     return out
 
 
+# ------------------------------------------------------ profile cases --
+# Small fixed workloads for ncu captures of the main kernels (`--profile-case
+# NAME`): a few milliseconds of GPU work on a few tens of MB each, sized for
+# `ncu --set full -k <kernel> -c <n>` captures that end by themselves.
+#   stream        L=160, 1 x 2: 30 MicSA + 4 Metropolis sweeps
+#   chains        the same lattice with the two replicas as two chains, 140 sweeps
+#   multispin     L=32, 64 x 2: 128 sweeps, blocks of 64
+#   planes        L=160, 1 x 128, bit planes: 12 sweeps
+#   planes_metro  the same lattice, 12 Metropolis sweeps
+#   onchip        L=160, 1 x 2, on-chip engine: 2 x 64 sweeps
+#   tma           L=160, 1 x 2, TMA engine: 12 sweeps
+#   pool          64 mixed jobs, 2 ticks of 64 sweeps
+def _micsa():
+    import paper_2506_16240_gb300
+    return paper_2506_16240_gb300
+
+
+def case_stream():
+    g = _micsa().Micsa(160, 1, 2, 3)
+    g.set_engine("stream")
+    g.run(np.full(30, 0.7), 10)
+    g.run_metropolis(np.full(4, 0.7))
+    return g.measure()[0]
+
+
+def case_chains():
+    g = _micsa().Micsa(160, 1, 2, 3)
+    g.set_engine("stream")
+    g.set_replica_chains(2)
+    g.run(np.full(140, 0.7), 10)  # 2 graph replays of 64 sweeps + 12 direct
+    return g.measure()[0]
+
+
+def case_planes():
+    g = _micsa().Micsa(160, 1, 128, 3)
+    g.set_engine("multispin_global")
+    g.set_launch_config(4, 128, -1, True, 0)  # direct launches
+    g.run(np.full(12, 0.7), 10)
+    return g.measure()[0][:4]
+
+
+def case_planes_metro():
+    g = _micsa().Micsa(160, 1, 128, 3)
+    g.set_engine("multispin_global")
+    g.set_launch_config(4, 128, -1, True, 0)  # direct launches
+    g.run_metropolis(np.full(12, 0.7))
+    return g.measure()[0][:4]
+
+
+def case_onchip():
+    g = _micsa().Micsa(160, 1, 2, 3)
+    g.set_launch_config(4, 128, -1, True, 64)
+    g.set_engine("onchip", 64)
+    g.run(np.full(128, 0.7), 10)
+    return g.measure()[0]
+
+
+def case_tma():
+    g = _micsa().Micsa(160, 1, 2, 3)
+    g.set_engine("tma")
+    g.set_launch_config(4, 128, -1, True, 0)  # direct launches
+    g.run(np.full(12, 0.7), 10)
+    return g.measure()[0]
+
+
+def case_multispin():
+    g = _micsa().Micsa(32, 64, 2, 2)
+    g.set_engine("multispin", 64)
+    g.run(np.full(128, 0.7), 10)
+    return g.measure()[0][:4]
+
+
+def case_pool():
+    rng = np.random.default_rng(4)
+    with _micsa().Pool(1 << 30, 128, 64) as p:
+        ids = [p.submit(int(L), 2, int(s), 128, 10, 2.5, 0.5)
+               for L, s in zip(rng.choice([16, 24, 32, 48, 64], 64), rng.integers(1, 2 ** 62, 64))]
+        for _ in range(2):
+            p.tick()
+        p.wait()
+        return [p.poll(j, best_spins=False)["energy"][0] for j in ids[:4]]
+
+
+PROFILE_CASES = {"stream": case_stream, "chains": case_chains, "multispin": case_multispin,
+                 "planes": case_planes, "planes_metro": case_planes_metro, "onchip": case_onchip,
+                 "tma": case_tma, "pool": case_pool}
+
+
 def main(argv=None):
     args = parse(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_case:
+        print(args.profile_case, PROFILE_CASES[args.profile_case]())
+        return 0
 
     import torch
     import paper_2506_16240_gb300 as micsa

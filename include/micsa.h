@@ -128,6 +128,11 @@ int micsa_measure(micsa_t h, int64_t *energy, int64_t *aux, int64_t *overlap);
  * beyond). Synchronous. */
 int micsa_correlation(micsa_t h, int64_t *G);
 
+/* The four-point correlation itself, C4[sample*L + r] = G[sample*L + r] /
+ * (3 N R(R-1)/2) in double, G the sums of micsa_correlation (same limits and
+ * errors). Host array C4[S][L]. Synchronous. */
+int micsa_c4(micsa_t h, double *C4);
+
 /* Copy the state to / from host arrays in natural layout: spins[S*R*N] int8
  * +-1, daemons[S*R*N] uint8 in {0..3}, and the global sweep index t. Any
  * pointer may be NULL (that part is skipped). set_state validates values. */
@@ -262,16 +267,21 @@ const char *micsa_last_error(micsa_t h);
  *   energy[S*R], aux[S*R], overlap[S*R(R-1)/2]  HOST arrays, as micsa_measure;
  *            any may be NULL
  *   stream   cudaStream_t to run on (NULL: the legacy default stream)
- * The sums go through one fixed device array of MICSA_NOALLOC_MAX_TERMS 64-bit
- * counters (64 KiB) that every GPU loading the library holds until the process
- * exits; a call needs 2*S*R + S*R*(R-1)/2 of them and returns
- * MICSA_E_TOO_LARGE beyond that (or for S > 65535). No cudaMalloc, cudaFree or
- * other allocating routine is called. The first call on a device looks up the
- * array's device address (cudaGetSymbolAddress), so make it before any stream
- * capture. All calls share the array (each clears what it uses first): calls
+ * Limits (MICSA_E_INVALID_ARG outside them): 2 <= L <= 1600, odd L included
+ * (the energy is the sum over the three forward bonds of every site, which
+ * needs no checkerboard); 1 <= R <= 32; S >= 1. The sums go through one fixed
+ * device array of MICSA_NOALLOC_MAX_TERMS 64-bit counters (64 KiB) that every
+ * GPU loading the library holds until the process exits; a call needs
+ * 2*S*R + S*R*(R-1)/2 of them and returns MICSA_E_TOO_LARGE beyond that (or
+ * for S > 65535). No cudaMalloc, cudaFree or other allocating routine is
+ * called. The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) and keeps it for the life of the process, so make
+ * that first call before any stream capture begins, and make no call on a
+ * device after cudaDeviceReset of that device (the kept address is then
+ * stale). All calls share the array (each clears what it uses first): calls
  * whose GPU work overlaps -- other streams, other host threads -- race on it.
- * Synchronous: returns after the host arrays are written. Same rules as
- * micsa_create for L and R. */
+ * Each call synchronises `stream` and returns after the host arrays are
+ * written. */
 int micsa_measure_noalloc(const int8_t *spins, const uint8_t *daemons, const int8_t *J, int L,
                           int n_samples, int n_replicas, int64_t *energy, int64_t *aux,
                           int64_t *overlap, void *stream);

@@ -67,6 +67,7 @@ SIGNATURES = {
     "micsa_run_metropolis": (_c.c_int, [_P, _P, _c.c_int64]),
     "micsa_measure": (_c.c_int, [_P, _P, _P, _P]),
     "micsa_correlation": (_c.c_int, [_P, _P]),
+    "micsa_c4": (_c.c_int, [_P, _P]),
     "micsa_get_state": (_c.c_int, [_P, _P, _P, _i64p]),
     "micsa_set_state": (_c.c_int, [_P, _P, _P, _c.c_int64]),
     "micsa_set_stream": (_c.c_int, [_P, _P]),
@@ -234,8 +235,10 @@ class Micsa:
         return G
 
     def c4(self):
-        """C4(r) per sample: G / (3 N R(R-1)/2)."""
-        return self.correlation() / (3.0 * self.N * self.R * (self.R - 1) / 2)
+        """C4[S, L]: the four-point correlation per sample (micsa_c4)."""
+        C = np.zeros((self.S, self.L), np.float64)
+        _check(lib().micsa_c4(self.h, _ptr(C)), self.h)
+        return C
 
     def get_state(self):
         s = np.zeros((self.S, self.R, self.N), np.int8)

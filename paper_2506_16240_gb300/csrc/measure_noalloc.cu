@@ -31,8 +31,9 @@ __device__ __align__(256) unsigned long long g_noalloc_scratch[kMaxTerms];
 unsigned long long *g_scratch_ptr[kMaxDevices] = {};
 std::mutex g_scratch_mutex;
 
-// Device address of the scratch array on the current device (looked up on the
-// first call per device; a later stream capture needs that call to have happened).
+// Device address of the scratch array on the current device, looked up on the
+// first call per device (that call must come before any stream capture) and
+// kept for the life of the process (stale after cudaDeviceReset).
 cudaError_t scratch_address(unsigned long long **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

@@ -977,6 +977,17 @@ int micsa_correlation(micsa_t h, int64_t *G) {
     return MICSA_OK;
 }
 
+int micsa_c4(micsa_t h, double *C4) {
+    if (!h) return MICSA_E_INVALID_ARG;
+    if (!C4) return fail(h, MICSA_E_INVALID_ARG, "C4 is NULL");
+    std::vector<int64_t> G((size_t)h->S * h->L);
+    if (int rc = micsa_correlation(h, G.data())) return rc;
+    // each unordered replica pair once, the three axes averaged: C4(0) = 1
+    const double norm = 3.0 * (double)sites(h) * ((double)h->R * (h->R - 1) / 2);
+    for (size_t i = 0; i < G.size(); ++i) C4[i] = (double)G[i] / norm;
+    return MICSA_OK;
+}
+
 int micsa_get_state(micsa_t h, int8_t *spins, uint8_t *daemons, int64_t *t) {
     if (!h) return MICSA_E_INVALID_ARG;
     DeviceGuard dg(h->device);

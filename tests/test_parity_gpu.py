@@ -284,6 +284,8 @@ def test_correlation_bit_exact(L, S, R):
             np.testing.assert_array_equal(g.correlation(), O.correlation(st))
         c4 = g.c4()
         np.testing.assert_allclose(c4[:, 0], 1.0, rtol=1e-12)
+        # C4 = G / (3 N R(R-1)/2) (Sec. 3), within the 1e-9 of derived doubles
+        np.testing.assert_allclose(c4, O.correlation(st) / (3.0 * L ** 3 * R * (R - 1) / 2), rtol=1e-9, atol=0)
 
 
 @pytest.mark.parametrize("L,S,R,nw,rpt", [
