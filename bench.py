@@ -17,7 +17,8 @@ Legs on the same JSON line:
   roofline     the plain streaming half-sweep kernel at L = 160: algorithmic
                bytes per launch over its mean duration in a timed run of
                sweeps without refresh (CUDA events, launching stream)
-  dram_point   the same kernel at L = 320 (164 MB of state, larger than L2)
+  dram_point   the same kernel at L = 400 (320 MB of state; each launch reads
+               128 MB and writes 64 MB, so DRAM feeds it)
   metropolis   the random-number-per-update Metropolis kernel, same lattice
   quench_l32   L = 32, 64 samples x 2 replicas, T = 0.7, 10^4 sweeps, refresh
                every 10, e and q^2 measured on a log time grid (multispin
@@ -78,9 +79,11 @@ def parse(argv=None):
                     help="sweeps per step (profiling runs only; reported numbers use the default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="headline leg only")
-    ap.add_argument("--profile-case", choices=["stream", "chains", "multispin", "planes", "planes_metro",
-                                               "onchip", "tma", "pool"],
+    ap.add_argument("--profile-case", choices=["stream", "chains", "single", "chains_l320", "chains_l400",
+                                               "multispin", "planes", "planes_metro", "onchip", "tma", "pool"],
                     help="run one small fixed workload for a profiler capture and exit")
+    ap.add_argument("--source-digests", action="store_true",
+                    help="print the digests of the kernel sources that profiles/traffic.md rows carry")
     ap.add_argument("--serving-jobs", type=int, default=300,
                     help="jobs in the serving stream (the full stream is 2000)")
     return ap.parse_args(argv)
@@ -240,6 +243,43 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------ ncu traffic records --
+# DRAM bytes of a kernel come from an ncu capture summarised in
+# profiles/traffic.md, one row per (kernel, workload, launch shape), with the
+# digest of the kernel's source files at capture time. A row whose digest no
+# longer matches the sources describes an older kernel and is not used.
+KERNEL_SOURCES = {
+    "half_sweep": ["sweep_kernels.cu", "sweep_body.cuh", "micsa_device.cuh"],
+    "msg_half": ["multispin.cu", "msg_body.cuh", "micsa_device.cuh"],
+}
+
+
+def kernel_digest(kernel):
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_2506_16240_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_record(kernel, key):
+    """(dram bytes per half-sweep, L2 bytes per half-sweep, capture note) of the
+    row `key` of profiles/traffic.md if its digest matches the current sources,
+    else None."""
+    try:
+        lines = open(os.path.join(ROOT, "profiles", "traffic.md")).read().splitlines()
+    except OSError:
+        return None
+    for ln in lines:
+        cols = [c.strip() for c in ln.strip().strip("|").split("|")]
+        if len(cols) >= 6 and cols[0] == kernel and cols[1] == key:
+            if cols[2].strip("`") != kernel_digest(kernel):
+                return None
+            return float(cols[3]), float(cols[4]), cols[5]
+    return None
+
+
 # --------------------------------------------------------------- GPU --
 class Timer:
     def __init__(self, torch, stream):
@@ -280,16 +320,18 @@ def leg_roofline(micsa, timer, stream, L, peaks, n_plain=2000, choice=None):
     hbm = peaks.get("hbm_gbs")
     peak = hbm if hbm else 6800.0
     achieved = bytes_per_launch / (launch_us * 1e-6) / 1e9
-    # DRAM bytes of one half-sweep from the ncu capture of this kernel in this shape
-    # (profiles/half_sweep_L160_full.md: two launches of 8.21 MB); null for other shapes
-    profiled = (L == 160 and choice is not None and choice.get("engine") == "stream" and choice.get("chains") == 2
-                and choice.get("words_per_thread") == 4 and choice.get("block") == 128)
+    chains = (choice or {}).get("chains", 1)
+    key = f"L={L} R={R} chains={chains} nw={shape['words_per_thread']} block={shape['block']}"
+    rec = traffic_record("half_sweep", key)
+    state_bytes = L ** 3 * (2 * R + 1)  # spins and daemons of each replica, bond bytes of the sample
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": 2 * 8.21e6 if profiled else None, "peak_source": "measured" if hbm else "fallback",
-            "kernel": "micsa::half_sweep_kernel<4,false> (streaming MicSA half-sweep, no refresh)",
+            "traffic": rec[0] if rec else None, "traffic_l2": rec[1] if rec else None,
+            "traffic_capture": rec[2] if rec else f"no capture of the current kernel for {key}",
+            "l2_resident": state_bytes < 129e6, "state_bytes": state_bytes,
+            "peak_source": "measured" if hbm else "fallback",
+            "kernel": "micsa::half_sweep_kernel (streaming MicSA half-sweep, no refresh)",
             "L": L, "bytes_per_launch": bytes_per_launch, "launch_us": launch_us, "launch": shape,
-            "replica_chains": (choice or {}).get("chains", 1),
-            "flips_per_ns": updates(L, 1, R, n_plain) / (ms * 1e6)}
+            "replica_chains": chains, "flips_per_ns": updates(L, 1, R, n_plain) / (ms * 1e6)}
 
 
 def plane_roofline(micsa, timer, stream, g, peaks, n_plain=2000):
@@ -306,12 +348,14 @@ def plane_roofline(micsa, timer, stream, g, peaks, n_plain=2000):
     hbm = peaks.get("hbm_gbs")
     peak = hbm if hbm else 6800.0
     achieved = bytes_per_launch / (launch_us * 1e-6) / 1e9
-    # DRAM bytes per launch from the ncu capture at L = 160, 128 replicas, 4 words per
-    # thread (profiles/msg_half_L160x128_full.md: 132.67 MB read + 44.67 MB written)
     shape = g.launch_config()
-    traffic = 177.3e6 if (L == 160 and R == 128 and shape["words_per_thread"] == 4) else None
+    key = f"L={L} R={R} nw={shape['words_per_thread']}"
+    rec = traffic_record("msg_half", key)
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": traffic, "peak_source": "measured" if hbm else "fallback",
+            "traffic": rec[0] if rec else None, "traffic_l2": rec[1] if rec else None,
+            "traffic_capture": rec[2] if rec else f"no capture of the current kernel for {key}",
+            "l2_resident": L ** 3 * S * (3 * R + 6) // 16 < 129e6,
+            "peak_source": "measured" if hbm else "fallback",
             "kernel": "micsa::msg_half_kernel (bit-plane MicSA half-sweep, no refresh)",
             "L": L, "replicas": R, "bytes_per_launch": bytes_per_launch, "launch_us": launch_us,
             "flips_per_ns": updates(L, S, R, n_plain) / (ms * 1e6)}
@@ -640,6 +684,8 @@ def leg_serving(micsa, torch, stream, n_jobs, n_cap=64):
 # `ncu --set full -k <kernel> -c <n>` captures that end by themselves.
 #   stream        L=160, 1 x 2: 30 MicSA + 4 Metropolis sweeps
 #   chains        the same lattice with the two replicas as two chains, 140 sweeps
+#   single        the same with both replicas in each launch (one chain)
+#   chains_l320, chains_l400  as chains at L = 320 (164 MB of state) and L = 400 (320 MB)
 #   multispin     L=32, 64 x 2: 128 sweeps, blocks of 64
 #   planes        L=160, 1 x 128, bit planes: 12 sweeps
 #   planes_metro  the same lattice, 12 Metropolis sweeps
@@ -659,10 +705,11 @@ def case_stream():
     return g.measure()[0]
 
 
-def case_chains():
-    g = _micsa().Micsa(160, 1, 2, 3)
+def case_chains(L=160, chains=2):
+    g = _micsa().Micsa(L, 1, 2, 3)
     g.set_engine("stream")
-    g.set_replica_chains(2)
+    g.set_launch_config(4, 128, -1, True, 64)
+    g.set_replica_chains(chains)
     g.run(np.full(140, 0.7), 10)  # 2 graph replays of 64 sweeps + 12 direct
     return g.measure()[0]
 
@@ -718,6 +765,8 @@ def case_pool():
 
 
 PROFILE_CASES = {"stream": case_stream, "chains": case_chains, "multispin": case_multispin,
+                 "single": lambda: case_chains(160, 1), "chains_l320": lambda: case_chains(320),
+                 "chains_l400": lambda: case_chains(400),
                  "planes": case_planes, "planes_metro": case_planes_metro, "onchip": case_onchip,
                  "tma": case_tma, "pool": case_pool}
 
@@ -728,6 +777,9 @@ def main(argv=None):
         return run_reference(args)
     if args.profile_case:
         print(args.profile_case, PROFILE_CASES[args.profile_case]())
+        return 0
+    if args.source_digests:
+        print(json.dumps({k: kernel_digest(k) for k in KERNEL_SOURCES}))
         return 0
 
     import torch
@@ -828,7 +880,7 @@ def main(argv=None):
 
     extras = {}
     if rank == 0 and not args.no_extras:
-        legs = [("dram_point", lambda: leg_roofline(micsa, timer, stream, 320, peaks, n_plain=500, choice=tuned)),
+        legs = [("dram_point", lambda: leg_roofline(micsa, timer, stream, 400, peaks, n_plain=300, choice=tuned)),
                 ("metropolis", lambda: leg_metropolis(micsa, timer, stream, choice=tuned)),
                 ("quench_l32", lambda: leg_quench_l32(micsa, timer, stream)),
                 ("batched", lambda: leg_batched(micsa, torch, stream)),

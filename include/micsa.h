@@ -355,6 +355,13 @@ int micsa_pool_wait_ticks(micsa_pool_t p, int max_pending);
  * is still running, MICSA_E_NOT_FOUND for an unknown (or already polled) id. */
 int micsa_pool_poll(micsa_pool_t p, int64_t job_id, micsa_job_result *res, int8_t *best_spins);
 
+/* micsa_pool_poll that also copies the job's final state: spins[R][N] (int8
+ * +-1) and daemons[R][N] (uint8 m in {0..3}), host, natural layout, after its
+ * last sweep (the state micsa_get_state of the equivalent single handle
+ * returns). Either pointer may be NULL. Same return codes as micsa_pool_poll. */
+int micsa_pool_poll_state(micsa_pool_t p, int64_t job_id, micsa_job_result *res, int8_t *best_spins,
+                          int8_t *spins, uint8_t *daemons);
+
 /* Ids of up to max_ids finished jobs whose last tick has run (ready to poll
  * without waiting), in *n_ids. Non-blocking. */
 int micsa_pool_finished(micsa_pool_t p, int64_t *ids, int max_ids, int *n_ids);

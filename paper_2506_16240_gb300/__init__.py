@@ -325,6 +325,7 @@ SIGNATURES.update({
     "micsa_pool_wait": (_c.c_int, [_P]),
     "micsa_pool_wait_ticks": (_c.c_int, [_P, _c.c_int]),
     "micsa_pool_poll": (_c.c_int, [_P, _c.c_int64, ctypes.POINTER(JobResult), _P]),
+    "micsa_pool_poll_state": (_c.c_int, [_P, _c.c_int64, ctypes.POINTER(JobResult), _P, _P, _P]),
     "micsa_pool_stats": (_c.c_int, [_P, ctypes.POINTER(_c.c_int), ctypes.POINTER(ctypes.c_size_t), _i64p]),
     "micsa_pool_finished": (_c.c_int, [_P, _i64p, _c.c_int, ctypes.POINTER(_c.c_int)]),
     "micsa_pool_set_launch_config": (_c.c_int, [_P, _c.c_int, _c.c_int, _c.c_int]),
@@ -404,12 +405,15 @@ class Pool:
     def wait_ticks(self, max_pending):
         self._check(lib().micsa_pool_wait_ticks(self.h, int(max_pending)))
 
-    def poll(self, job_id, best_spins=True):
-        """Result dict of a finished job (and frees it), or None while it runs."""
+    def poll(self, job_id, best_spins=True, final_state=False):
+        """Result dict of a finished job (and frees it), or None while it runs.
+        final_state: also the final spins and daemons [R, N] (natural layout)."""
         L, R = self.jobs[job_id]
         res = JobResult()
         spins = np.zeros((R, L ** 3), np.int8) if best_spins else None
-        rc = lib().micsa_pool_poll(self.h, int(job_id), ctypes.byref(res), _ptr(spins))
+        fs = np.zeros((R, L ** 3), np.int8) if final_state else None
+        fm = np.zeros((R, L ** 3), np.uint8) if final_state else None
+        rc = lib().micsa_pool_poll_state(self.h, int(job_id), ctypes.byref(res), _ptr(spins), _ptr(fs), _ptr(fm))
         if rc == MICSA_E_BUSY:
             return None
         self._check(rc)
@@ -420,6 +424,8 @@ class Pool:
                "best_t": np.array(res.best_t[:R], np.int64)}
         if best_spins:
             out["best_spins"] = spins
+        if final_state:
+            out["spins"], out["daemons"] = fs, fm
         return out
 
     def finished(self, max_ids=4096):

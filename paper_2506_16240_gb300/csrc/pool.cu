@@ -1119,7 +1119,31 @@ int micsa_pool_wait_ticks(micsa_pool_t p, int max_pending) {
     return MICSA_OK;
 }
 
+namespace {
+
+// Split layout [R][parity][z][y][P bytes] (byte i of row (z, y) of parity p is
+// the site x = 2i + ((p + y + z) & 1)) to natural layout [R][N] on the host.
+void split_to_natural(const uint8_t *split, int R, const Geometry &g, uint8_t *out) {
+    const int L = g.L;
+    const size_t N = (size_t)L * L * L;
+    for (int r = 0; r < R; ++r)
+        for (int par = 0; par < 2; ++par)
+            for (int z = 0; z < L; ++z)
+                for (int y = 0; y < L; ++y) {
+                    const uint8_t *row = split + ((size_t)r * 2 + par) * g.half + ((size_t)z * L + y) * g.P;
+                    uint8_t *o = out + (size_t)r * N + ((size_t)z * L + y) * L + ((par + y + z) & 1);
+                    for (int i = 0; i < g.Lh; ++i) o[2 * i] = row[i];
+                }
+}
+
+}  // namespace
+
 int micsa_pool_poll(micsa_pool_t p, int64_t job_id, micsa_job_result *res, int8_t *best_spins) {
+    return micsa_pool_poll_state(p, job_id, res, best_spins, nullptr, nullptr);
+}
+
+int micsa_pool_poll_state(micsa_pool_t p, int64_t job_id, micsa_job_result *res, int8_t *best_spins,
+                          int8_t *spins, uint8_t *daemons) {
     if (!p) return MICSA_E_INVALID_ARG;
     int slot = -1;
     for (int i = 0; i < p->max_jobs; ++i)
@@ -1140,24 +1164,27 @@ int micsa_pool_poll(micsa_pool_t p, int64_t job_id, micsa_job_result *res, int8_
     for (int q = 0; q < 4; ++q)
         PCK(p, cudaMemcpy(vals[q], p->d_results + (size_t)q * p->max_jobs * kPoolMaxR + (size_t)slot * kPoolMaxR,
                           sizeof(long long) * kPoolMaxR, cudaMemcpyDeviceToHost), "copy results");
+    const Geometry g = p->h_jobs[slot].geo;
+    std::vector<uint8_t> split;
+    if (best_spins || spins || daemons) split.resize((size_t)R * 2 * g.half);
     if (best_spins) {
-        const int L = J.desc.L;
-        const size_t N = (size_t)L * L * L;
+        const size_t N = (size_t)g.L * g.L * g.L;
         if (p->h_jobs[slot].resident) {  // kept in natural layout by the shared-memory kernel
             PCK(p, cudaMemcpy(best_spins, p->arena + J.off_best, (size_t)R * N, cudaMemcpyDeviceToHost), "copy best spins");
-        } else {  // split layout: [R][parity][z][y][P bytes], byte i of row (z, y) is x = 2i + ((p + y + z) & 1)
-            const Geometry g = p->h_jobs[slot].geo;
-            std::vector<int8_t> split((size_t)R * 2 * g.half);
+        } else {
             PCK(p, cudaMemcpy(split.data(), p->arena + J.off_best, split.size(), cudaMemcpyDeviceToHost), "copy best spins");
-            for (int r = 0; r < R; ++r)
-                for (int par = 0; par < 2; ++par)
-                    for (int z = 0; z < L; ++z)
-                        for (int y = 0; y < L; ++y) {
-                            const int8_t *row = split.data() + ((size_t)r * 2 + par) * g.half + ((size_t)z * L + y) * g.P;
-                            int8_t *out = best_spins + (size_t)r * N + ((size_t)z * L + y) * L + ((par + y + z) & 1);
-                            for (int i = 0; i < g.Lh; ++i) out[2 * i] = row[i];
-                        }
+            split_to_natural(split.data(), R, g, reinterpret_cast<uint8_t *>(best_spins));
         }
+    }
+    // the final state: split layout for every job between ticks (bit-plane jobs
+    // are converted back at the end of each tick)
+    if (spins) {
+        PCK(p, cudaMemcpy(split.data(), p->arena + J.off_spins, split.size(), cudaMemcpyDeviceToHost), "copy spins");
+        split_to_natural(split.data(), R, g, reinterpret_cast<uint8_t *>(spins));
+    }
+    if (daemons) {
+        PCK(p, cudaMemcpy(split.data(), p->arena + J.off_daemons, split.size(), cudaMemcpyDeviceToHost), "copy daemons");
+        split_to_natural(split.data(), R, g, daemons);
     }
     if (res) {
         std::memset(res, 0, sizeof(*res));

@@ -61,10 +61,11 @@ def mean_job_updates(L_range=(16, 96), sweeps_range=(1e3, 1e5), replicas_range=(
 
 
 class Server:
-    def __init__(self, pool: Pool, max_pending_ticks=2, keep_spins=False):
+    def __init__(self, pool: Pool, max_pending_ticks=2, keep_spins=False, final_state=False):
         self.pool = pool
         self.max_pending = max_pending_ticks
         self.keep_spins = keep_spins
+        self.final_state = final_state
 
     def serve(self, requests, realtime=True):
         """Run the stream to completion; returns the requests with timings and results.
@@ -91,7 +92,7 @@ class Server:
                 self.pool.tick()
                 self.pool.wait_ticks(self.max_pending)
                 for jid in self.pool.finished():
-                    res = self.pool.poll(jid, best_spins=self.keep_spins)
+                    res = self.pool.poll(jid, best_spins=self.keep_spins, final_state=self.final_state)
                     r = live.pop(jid)
                     r.done = time.perf_counter() - t0
                     r.result = res

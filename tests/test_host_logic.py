@@ -40,7 +40,7 @@ class FakePool:
     def finished(self):
         return [jid for jid, j in self.live.items() if j["done"]]
 
-    def poll(self, jid, best_spins=False):
+    def poll(self, jid, best_spins=False, final_state=False):
         j = self.live.pop(jid)
         self.used -= j["need"]
         return {"energy": [-j["seed"]], "seed": j["seed"]}

@@ -9,12 +9,19 @@ import numpy as np
 import pytest
 
 import oracle
+import oracle_jobs
 import paper_2506_16240_gb300 as micsa
 from paper_2506_16240_gb300 import serve
 
 pytestmark = pytest.mark.gpu
 
 O = oracle.Oracle()
+
+
+def assert_final_state(res, st, what):
+    """Final spins and daemons of a pool job equal the oracle's, element by element."""
+    np.testing.assert_array_equal(res["spins"], st["s"][0], err_msg=f"spins {what}")
+    np.testing.assert_array_equal(res["daemons"], st["m"][0], err_msg=f"daemons {what}")
 
 
 def single_handle(L, R, seed, n, interval, T0, T1):
@@ -51,7 +58,7 @@ def run_pool(jobs, K=16, arena=1 << 28, max_jobs=64, order=None, shape=None, res
                 p.set_launch_config(reshape[2])
             for idx, jid in ids.items():
                 if idx not in results:
-                    r = p.poll(jid)
+                    r = p.poll(jid, final_state=True)
                     if r is not None:
                         results[idx] = r
         return results
@@ -102,6 +109,7 @@ def test_pool_streamed_variants_match_oracle():
         e, a, _ = O.measure(st)
         np.testing.assert_array_equal(res[idx]["energy"], e, err_msg=str(JOBS_STREAMED[idx]))
         np.testing.assert_array_equal(res[idx]["aux"], a, err_msg=str(JOBS_STREAMED[idx]))
+        assert_final_state(res[idx], st, JOBS_STREAMED[idx])
         assert res[idx]["sweeps_done"] == n
 
 
@@ -123,7 +131,7 @@ def test_batched_workload_in_one_pool_sampled_jobs_match_oracle():
             p.tick()
             for i, jid in enumerate(ids):
                 if i not in res:
-                    r = p.poll(jid, best_spins=False)
+                    r = p.poll(jid, best_spins=False, final_state=True)
                     if r is not None:
                         res[i] = r
     for L in (16, 24, 32, 48, 64):
@@ -133,6 +141,7 @@ def test_batched_workload_in_one_pool_sampled_jobs_match_oracle():
         e, a, _ = O.measure(st)
         np.testing.assert_array_equal(res[i]["energy"], e, err_msg=f"L={L}")
         np.testing.assert_array_equal(res[i]["aux"], a, err_msg=f"L={L}")
+        assert_final_state(res[i], st, f"L={L}")
 
 
 @pytest.mark.parametrize("job", [JOBS[0], JOBS[2], JOBS[5], JOBS[8], JOBS_STREAMED[1], JOBS_STREAMED[4],
@@ -158,6 +167,7 @@ def test_pool_best_configuration_matches_oracle(job):
     np.testing.assert_array_equal(r["best_spins"], best_s)
     np.testing.assert_array_equal(r["energy"], e)
     np.testing.assert_array_equal(r["aux"], a)
+    assert_final_state(r, st, job)
 
 
 def test_admission_is_limited_by_arena_memory():
@@ -224,6 +234,38 @@ def test_serving_stream_results_match_alone():
     assert s["p99_latency_s"] >= s["p50_latency_s"] > 0
 
 
+def test_served_stream_up_to_l96_r4_matches_oracle():
+    """The serving configuration's size range (even L up to 96, 1..4 replicas,
+    anneal 3.0 -> 0.3, refresh every 10) on short jobs: requests arrive while
+    others run and join the running batch; every result -- final energies,
+    daemon energies, final spins and daemons, the lowest energy, its time and
+    configuration -- equals the oracle's, element by element."""
+    import multiprocessing as mp
+    K = 16
+    reqs = serve.poisson_stream(14, rate_hz=300.0, seed=55, L_range=(16, 96), sweeps_range=(24, 90),
+                                replicas_range=(1, 4))
+    reqs[0].L, reqs[0].n_replicas = 96, 4  # the corner of the range, always present
+    reqs[1].L, reqs[1].n_replicas = 94, 3  # a ragged bit-plane-ineligible large job
+    with micsa.Pool(1 << 30, 5, K) as p:  # 5 slots: later requests queue and join mid-stream
+        done = serve.Server(p, keep_spins=True, final_state=True).serve(reqs, realtime=True)
+    assert len(done) == len(reqs)
+    overlapped = sum(1 for r in done if any(o.admitted < r.admitted < o.done for o in done if o is not r))
+    assert overlapped > 0
+    args = [(r.L, r.n_replicas, r.seed, micsa.linear_schedule(r.T_start, r.T_end, r.n_sweeps), r.refresh_interval, K)
+            for r in done]
+    with mp.get_context("spawn").Pool(min(len(args), 16)) as workers:  # spawn: this process holds a CUDA context
+        ref = workers.map(oracle_jobs.job_with_best, args, chunksize=1)
+    for r, (e, a, s, m, best, best_t, best_s) in zip(done, ref):
+        what = f"L={r.L} R={r.n_replicas} sweeps={r.n_sweeps}"
+        np.testing.assert_array_equal(r.result["energy"], e, err_msg=what)
+        np.testing.assert_array_equal(r.result["aux"], a, err_msg=what)
+        np.testing.assert_array_equal(r.result["spins"], s, err_msg=what)
+        np.testing.assert_array_equal(r.result["daemons"], m, err_msg=what)
+        np.testing.assert_array_equal(r.result["best_energy"], best, err_msg=what)
+        np.testing.assert_array_equal(r.result["best_t"], best_t, err_msg=what)
+        np.testing.assert_array_equal(r.result["best_spins"], best_s, err_msg=what)
+
+
 @pytest.mark.parametrize("shape,reshape", [
     ((1, 1, 0), None), ((2, 3, 3), None), ((4, 4, 8), None), ((4, 2, 0), (1, 3, 2)), ((1, 4, 5), (4, 1, 0)),
 ])
@@ -277,6 +319,7 @@ def test_pool_plane_jobs_match_oracle():
         e, a, _ = O.measure(st)
         np.testing.assert_array_equal(res[idx]["energy"], e, err_msg=str(JOBS_PLANES[idx]))
         np.testing.assert_array_equal(res[idx]["aux"], a, err_msg=str(JOBS_PLANES[idx]))
+        assert_final_state(res[idx], st, JOBS_PLANES[idx])
         assert res[idx]["sweeps_done"] == n
 
 
