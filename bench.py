@@ -80,12 +80,12 @@ def parse(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="headline leg only")
     ap.add_argument("--profile-case", choices=["stream", "chains", "single", "chains_l320", "chains_l400",
-                                               "multispin", "planes", "planes_metro", "onchip", "tma", "pool"],
+                                               "multispin", "planes", "planes_metro", "onchip", "tma", "pool",
+                                               "batched", "plane_jobs_smem", "plane_jobs_global"],
                     help="run one small fixed workload for a profiler capture and exit")
     ap.add_argument("--source-digests", action="store_true",
                     help="print the digests of the kernel sources that profiles/traffic.md rows carry")
-    ap.add_argument("--serving-jobs", type=int, default=300,
-                    help="jobs in the serving stream (the full stream is 2000)")
+    ap.add_argument("--serving-jobs", type=int, default=2000, help="jobs in the serving stream")
     return ap.parse_args(argv)
 
 
@@ -637,44 +637,54 @@ def leg_batched(micsa, torch, stream, n_sweeps=20_000, loop_sweeps=2_000):
                         "refresh 5..20; the loop is timed on its first 2e3 sweeps"}
 
 
-def leg_serving(micsa, torch, stream, n_jobs, n_cap=64):
+def leg_serving(micsa, torch, stream, n_jobs, n_cap=600, slots=256, K=128):
+    """The serving stream through the continuous-batching pool. Saturated capacity:
+    n_cap requests of the same mix queued at once, more than the pool's slots, so
+    that the pool stays full until the queue empties; the capacity is the attempts
+    run in that window over its length. The Poisson stream of n_jobs is then
+    offered at ~80% of that capacity (p50/p99 latency, aggregate rate)."""
     from paper_2506_16240_gb300 import autotune, serve
-    # saturated capacity of the pool on this job mix: n_cap jobs queued at once
     cap_reqs = serve.poisson_stream(n_cap, 1e6, seed=55)
-    choice = autotune.tune_pool_for_jobs(
-        lambda: micsa.Pool(16 << 30, 256, 32),
-        [(r.L, r.n_replicas, r.seed, r.n_sweeps, r.refresh_interval, r.T_start, r.T_end) for r in cap_reqs])
-    with micsa.Pool(16 << 30, 256, 128) as p:
+    desc = [(r.L, r.n_replicas, r.seed, r.n_sweeps, r.refresh_interval, r.T_start, r.T_end) for r in cap_reqs[:slots]]
+    choice = autotune.tune_pool_for_jobs(lambda: micsa.Pool(16 << 30, slots, 32), desc)
+    with micsa.Pool(16 << 30, slots, K) as p:
         autotune.apply_pool(p, choice)
         srv = serve.Server(p)
+        l0 = p.stats()["launches"]
         srv.serve(cap_reqs, realtime=False)
-        capacity = sum(r.updates for r in cap_reqs) / srv.wall  # updates/s
-    # the same jobs through the plain per-job loop: one handle per job, run one after another
+        cap_launches = p.stats()["launches"] - l0
+        sat_flips, sat_s = srv.saturated
+        capacity = sat_flips / sat_s  # updates/s with the pool full
+        drained = sum(r.updates for r in cap_reqs) / srv.wall  # the whole run, queue and tail included
+    # the plain per-job loop: one handle per job, run one after another (first 64 jobs of the mix)
+    loop_reqs = cap_reqs[:64]
     sched_cache = {}
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for r in cap_reqs:
+    for r in loop_reqs:
         key = (r.n_sweeps, r.T_start, r.T_end)
         if key not in sched_cache:
             sched_cache[key] = micsa.linear_schedule(r.T_start, r.T_end, r.n_sweeps)
         with micsa.Micsa(r.L, 1, r.n_replicas, r.seed, stream=stream) as h:
             h.run(sched_cache[key], r.refresh_interval)
             h.measure()
-    loop_rate = sum(r.updates for r in cap_reqs) / (time.perf_counter() - t0)
+    loop_rate = sum(r.updates for r in loop_reqs) / (time.perf_counter() - t0)
     # Poisson stream offered at ~80% of the saturated capacity
     rate_hz = 0.8 * capacity / serve.mean_job_updates()
     reqs = serve.poisson_stream(n_jobs, rate_hz, seed=5)
-    with micsa.Pool(16 << 30, 256, 128) as p:
+    with micsa.Pool(16 << 30, slots, K) as p:
         autotune.apply_pool(p, choice)
         server = serve.Server(p)
         done = server.serve(reqs, realtime=True)
     out = serve.summarize(done, server.wall)
-    out.update({"unit": METRIC, "arrival_rate_hz": rate_hz, "launch": choice,
-                "saturated_pool_flips_per_ns": capacity / 1e9, "per_job_loop_flips_per_ns": loop_rate / 1e9,
-                "saturated_over_loop": capacity / loop_rate,
+    out.update({"unit": METRIC, "arrival_rate_hz": rate_hz, "launch": choice, "slots": slots, "tick_sweeps": K,
+                "saturated_pool_flips_per_ns": capacity / 1e9, "saturated_window_s": sat_s,
+                "capacity_run_flips_per_ns": drained / 1e9, "capacity_run_launches": cap_launches,
+                "per_job_loop_flips_per_ns": loop_rate / 1e9, "saturated_over_loop": capacity / loop_rate,
                 "workload": f"{n_jobs} Poisson jobs: L even 16..96, sweeps log-uniform 1e3..1e5, "
-                            "1..4 replicas, anneal 3.0->0.3, refresh every 10; capacity and loop on "
-                            f"{n_cap} jobs of the same mix"})
+                            "1..4 replicas, anneal 3.0->0.3, refresh every 10; capacity on "
+                            f"{n_cap} jobs of the same mix queued at once ({slots} slots), "
+                            "the loop on 64 of them"})
     return out
 
 
@@ -692,6 +702,9 @@ def leg_serving(micsa, torch, stream, n_jobs, n_cap=64):
 #   onchip        L=160, 1 x 2, on-chip engine: 2 x 64 sweeps
 #   tma           L=160, 1 x 2, TMA engine: 12 sweeps
 #   pool          64 mixed jobs, 2 ticks of 64 sweeps
+#   batched       the 256 batched lattices in one pool, 2 ticks of 32 sweeps
+#   plane_jobs_smem, plane_jobs_global  16 bit-plane jobs (L = 64 and 48), one tick of
+#                 64 sweeps, in shared memory or on the global bit planes
 def _micsa():
     import paper_2506_16240_gb300
     return paper_2506_16240_gb300
@@ -764,9 +777,35 @@ def case_pool():
         return [p.poll(j, best_spins=False)["energy"][0] for j in ids[:4]]
 
 
+def case_batched(K=32, ticks=2):
+    """The 256 batched lattices in one pool (default shape), ticks of K sweeps."""
+    rng = np.random.default_rng(4)
+    inst = zip(rng.choice([16, 24, 32, 48, 64], 256), rng.integers(5, 21, 256), rng.integers(1, 2 ** 62, 256))
+    with _micsa().Pool(8 << 30, 512, K) as p:
+        ids = [p.submit(int(L), 2, int(s), 20_000, int(r), 2.5, 0.5) for L, r, s in inst]
+        for _ in range(ticks):
+            p.tick()
+        p.wait()
+        return len(ids), p.stats()["launches"]
+
+
+def case_plane_jobs(smem=True, K=64):
+    """16 bit-plane jobs (8 of L = 64, 8 of L = 48, 2 replicas, refresh every 10) in
+    one pool, one tick of K sweeps: the shared-memory kernel (smem) or the
+    per-half-sweep launches over the global bit planes."""
+    with _micsa().Pool(1 << 30, 64, K) as p:
+        if not smem:
+            p.set_smem_planes(0, 1)
+        ids = [p.submit(L, 2, 100 + j, 10 * K, 10, 2.5, 0.5) for j, L in enumerate([64] * 8 + [48] * 8)]
+        p.tick()
+        p.wait()
+        return len(ids), p.stats()["launches"]
+
+
 PROFILE_CASES = {"stream": case_stream, "chains": case_chains, "multispin": case_multispin,
                  "single": lambda: case_chains(160, 1), "chains_l320": lambda: case_chains(320),
-                 "chains_l400": lambda: case_chains(400),
+                 "chains_l400": lambda: case_chains(400), "batched": case_batched,
+                 "plane_jobs_smem": case_plane_jobs, "plane_jobs_global": lambda: case_plane_jobs(False),
                  "planes": case_planes, "planes_metro": case_planes_metro, "onchip": case_onchip,
                  "tma": case_tma, "pool": case_pool}
 

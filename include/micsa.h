@@ -394,6 +394,18 @@ int micsa_pool_set_shape(micsa_pool_t p, int max_words, int chains);
  * counters). micsa_pool_job_bytes counts the plane storage for such jobs. */
 int micsa_pool_set_planes(micsa_pool_t p, int on);
 
+/* Shared-memory path of the bit-plane jobs admitted from now on (on by
+ * default, at the largest budget the device allows): a job whose replicas'
+ * bit planes fit in smem_bytes of shared memory is advanced by one persistent
+ * launch per tick, in units of as many replicas as fit (with its bond planes
+ * when they fit too, else reading them from the arena): a CTA converts the
+ * unit's bytes to planes in its shared memory, runs the tick's sweeps there
+ * with the same bit-plane update and Philox counters, and converts back, so
+ * the results are identical either way. smem_bytes = 0 turns it off;
+ * blocks_per_sm (1..8) sets the launch's grid. MICSA_E_INVALID_ARG for a
+ * budget above the device's limit. Synchronizes. */
+int micsa_pool_set_smem_planes(micsa_pool_t p, size_t smem_bytes, int blocks_per_sm);
+
 /* Message of the last failure on p. */
 const char *micsa_pool_last_error(micsa_pool_t p);
 

@@ -331,6 +331,7 @@ SIGNATURES.update({
     "micsa_pool_set_launch_config": (_c.c_int, [_P, _c.c_int, _c.c_int, _c.c_int]),
     "micsa_pool_set_shape": (_c.c_int, [_P, _c.c_int, _c.c_int]),
     "micsa_pool_set_planes": (_c.c_int, [_P, _c.c_int]),
+    "micsa_pool_set_smem_planes": (_c.c_int, [_P, _c.c_size_t, _c.c_int]),
     "micsa_pool_last_error": (_c.c_char_p, [_P]),
     "micsa_pool_destroy": (None, [_P]),
 })
@@ -450,6 +451,12 @@ class Pool:
         """Words per thread (cap 1, 2 or 4) and concurrent kernel chains (1..4) of
         the streaming jobs' half-sweeps; results do not depend on them."""
         self._check(lib().micsa_pool_set_shape(self.h, int(max_words), int(chains)))
+
+    def set_smem_planes(self, smem_bytes, blocks_per_sm=1):
+        """Shared-memory budget (bytes, 0: off) and grid of the persistent kernel that
+        sweeps the bit-plane jobs admitted from now on in shared memory; results do
+        not depend on it."""
+        self._check(lib().micsa_pool_set_smem_planes(self.h, int(smem_bytes), int(blocks_per_sm)))
 
     def set_planes(self, on=True):
         """Bit-plane half-sweeps for the jobs admitted from now on with L a

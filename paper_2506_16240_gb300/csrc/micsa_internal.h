@@ -79,6 +79,8 @@ struct JobDesc {
     uint32_t *planes;
     const uint32_t *bplanes;
     int32_t use_planes;
+    int32_t smem_planes;  // bit-plane job swept in shared memory by the tick's persistent kernel: the
+                          // per-CTA shared-memory budget (bytes) it was admitted with; 0: not
 };
 
 // One lattice (a replica of a sample or of a pool job) that a CTA keeps in

@@ -199,8 +199,10 @@ __device__ __forceinline__ void msg_convert_word(uint32_t *planes, int8_t *spins
 // word of a z column holds Lz = L - 32 (nzw - 1) sites (L a multiple of 8, any
 // L >= 32; no walkers): the z wrap goes through bit Lz - 1 of that word, and its
 // bits from Lz up stay zero. METRO: the Metropolis sweep on the same planes
-// (the daemon planes are neither read nor written).
-template <int NW, bool RAGGED = false, bool METRO = false>
+// (the daemon planes are neither read nor written). PREFETCH: the next
+// replica's words are prefetched into L2 (planes in global memory only; a
+// caller whose planes live in shared memory passes false).
+template <int NW, bool RAGGED = false, bool METRO = false, bool PREFETCH = true>
 __device__ __forceinline__ void msg_update(const MsgLattice &a, const SweepParam &prm, int p, int zw, int y, int ig,
                                            int r_begin, int r_end) {
     constexpr int G = 4 / NW;  // lanes sharing one Philox block of words
@@ -242,7 +244,7 @@ __device__ __forceinline__ void msg_update(const MsgLattice &a, const SweepParam
         const int64_t gid = a.gid0 + r;
         const uint32_t fam = (uint32_t)(gid * a.gamma + alpha);  // Philox id of this daemon family
         uint32_t *pl = a.planes + (int64_t)r * a.np * a.WP;
-        if (r + 1 < r_end) {  // the next replica's words that come from DRAM, into L2
+        if (PREFETCH && r + 1 < r_end) {  // the next replica's words that come from DRAM, into L2
             const uint32_t *nx = pl + (int64_t)a.np * a.WP;
             prefetch_l2(nx + (int64_t)p * a.WP + wc);
             prefetch_l2(nx + (int64_t)o * a.WP + wc);

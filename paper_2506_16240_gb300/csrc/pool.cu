@@ -47,6 +47,18 @@ struct PVBlock {
     int32_t chunk0;
 };
 
+// One unit of the shared-memory bit-plane kernel: replicas [r0, r0 + nrep) of
+// the bit-plane job in `slot`, held in one CTA's shared memory for a tick;
+// bonds_smem: the job's bond planes are copied there too (else read from the
+// arena, where they stay in L2).
+struct PlaneUnit {
+    int32_t slot;
+    int16_t r0, nrep;
+    int32_t bonds_smem;
+};
+
+constexpr int kSmemPlaneThreads = 512;
+
 struct PoolTables {
     JobDesc *jobs;          // [max_jobs]
     const VBlock *vblocks;  // [max_vblocks]
@@ -270,6 +282,84 @@ __global__ void __launch_bounds__(kVBlock, 4) pool_msg_half_kernel(PoolTables T,
     }
 }
 
+// The tick of the bit-plane jobs whose state fits in shared memory: a
+// persistent kernel whose CTAs take units (a job's replica range) from a work
+// counter, convert the replicas' bytes to bit planes in shared memory (the
+// layout of the global bit planes: [replica][spin p0, p1, m0 p0, p1, m1 p0, p1][WP]),
+// run the job's K sweeps of this tick there -- the even half-sweep, then the
+// odd one, each the body of the global bit-plane kernel (msg_update) over the
+// CTA's word groups, the refresh at the job's refresh sweeps -- and convert
+// back. No state leaves the SM between the half-sweeps of a tick.
+__global__ void __launch_bounds__(kSmemPlaneThreads, 1)
+    pool_smem_planes_kernel(PoolTables T, const PlaneUnit *units, const int32_t *n_units, int *counter, int K) {
+    pool_wait();
+    pool_release();
+    extern __shared__ __align__(16) uint32_t spl[];
+    __shared__ int s_unit;
+    const int n = *n_units;
+    for (;;) {
+        if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1);
+        __syncthreads();
+        const int u = s_unit;
+        __syncthreads();  // every thread has read s_unit before thread 0 writes the next one
+        if (u >= n) break;
+        const PlaneUnit U = units[u];
+        const JobDesc &J = T.jobs[U.slot];
+        if (!J.live || J.t >= J.n_sweeps) continue;
+        const Geometry g = J.geo;
+        const int nzw = (g.L + 31) / 32;
+        const int64_t WP = (int64_t)g.L * nzw * g.Lh;
+        const int nrep = U.nrep;
+        int8_t *spins = J.spins + (int64_t)U.r0 * 2 * g.half;
+        uint8_t *daemons = J.daemons + (int64_t)U.r0 * 2 * g.half;
+        uint32_t *sb = spl + (int64_t)nrep * 6 * WP;  // bond planes, when they are held here
+        for (int64_t idx = threadIdx.x; idx < (int64_t)nrep * 2 * WP; idx += blockDim.x) {
+            const int rep = (int)(idx / (2 * WP));
+            const int64_t rem = idx - (int64_t)rep * 2 * WP;
+            const int par = (int)(rem / WP);
+            msg_convert_word(spl, spins, daemons, g, WP, 1, 6, 0, true, rep, par, rem - par * WP);
+        }
+        if (U.bonds_smem) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(J.bplanes);
+            uint4 *dst = reinterpret_cast<uint4 *>(sb);
+            for (int64_t i = threadIdx.x; i < 3 * WP; i += blockDim.x) dst[i] = src[i];  // 12 WP words
+        }
+        __syncthreads();
+        const MsgLattice lat{spl, U.bonds_smem ? sb : J.bplanes, g.L, g.Lh, nzw, g.Lh / 4, WP, 6, 1, 0,
+                             (int64_t)U.r0, J.key0, J.key1};
+        const int groups = (int)(WP / 4), W4 = g.Lh / 4;
+        for (int k = 0; k < K; ++k) {
+            const int64_t t = J.t + k;
+            if (t >= J.n_sweeps) break;
+            SweepParam prm{};
+            prm.t = t;
+            prm.mode = kModeMicsa;
+            if (t % J.interval == 0) {
+                const uint64_t *q = J.thr + 3 * (t / J.interval);
+                prm.th0 = q[0];
+                prm.th1 = q[1];
+                prm.th2 = q[2];
+                prm.mode = kModeRefresh;
+            }
+            for (int par = 0; par < 2; ++par) {
+                for (int q = threadIdx.x; q < groups; q += blockDim.x) {
+                    const int rowi = q / W4;
+                    const int zw = rowi / g.L;
+                    msg_update<4, true, false, false>(lat, prm, par, zw, rowi - zw * g.L, q - rowi * W4, 0, nrep);
+                }
+                __syncthreads();
+            }
+        }
+        for (int64_t idx = threadIdx.x; idx < (int64_t)nrep * 2 * WP; idx += blockDim.x) {
+            const int rep = (int)(idx / (2 * WP));
+            const int64_t rem = idx - (int64_t)rep * 2 * WP;
+            const int par = (int)(rem / WP);
+            msg_convert_word(spl, spins, daemons, g, WP, 1, 6, 0, false, rep, par, rem - par * WP);
+        }
+        __syncthreads();  // the planes are read out before the next unit overwrites them
+    }
+}
+
 // Energy and daemon sums of every (live, advancing) streaming job replica after
 // the tick, over the virtual-block table of the half-sweeps: per warp one
 // atomic into the (slot, replica) accumulators.
@@ -370,7 +460,7 @@ __global__ void __launch_bounds__(kVBlock) pool_best_copy_kernel(PoolTables T) {
 __global__ void pool_advance_kernel(JobDesc *jobs, int max_jobs, int K, int *counter) {
     pool_wait();
     pool_release();
-    if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;  // work counter of the next tick's resident launch
+    if (blockIdx.x == 0 && threadIdx.x < 2) counter[threadIdx.x] = 0;  // the next tick's persistent kernels' work counters
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max_jobs; i += gridDim.x * blockDim.x) {
         JobDesc &J = jobs[i];
         if (!J.live) continue;
@@ -460,7 +550,19 @@ struct micsa_pool {
     int planes_grid = 0;
     cudaStream_t planes_stream[kPoolMaxChains] = {};  // the bit-plane jobs' parts as concurrent chains
     cudaEvent_t planes_fork = nullptr, planes_join[kPoolMaxChains] = {};
-    cudaGraphExec_t graphs[8] = {};  // by part mask: 1 resident, 2 byte-streamed, 4 bit-plane jobs
+    // bit-plane jobs swept in shared memory (one persistent launch per tick)
+    size_t splanes_smem = 0;  // per-CTA shared-memory budget for the jobs admitted from now on; 0: off
+    size_t splanes_max_smem = 0;  // what the device allows the kernel
+    int splanes_grid = 0;
+    PlaneUnit *d_punits = nullptr, *h_punits = nullptr;
+    int32_t *d_npunits = nullptr, *h_npunits = nullptr;
+    int max_punits = 0;
+    size_t splanes_launch_smem = 0;  // the largest unit of the current table
+    bool has_splane_jobs = false;
+    cudaStream_t splanes_stream = nullptr;
+    cudaEvent_t splanes_fork = nullptr, splanes_join = nullptr;
+    cudaGraphExec_t graphs[16] = {};  // by part mask: 1 resident, 2 byte-streamed, 4 bit-plane jobs,
+                                      // 8 bit-plane jobs in shared memory
     std::string err;
 };
 
@@ -544,6 +646,31 @@ struct JobSizes {
 // not a multiple of 32) and above the shared-memory kernel's sizes.
 bool plane_eligible(const micsa_job_desc &d) { return d.L % 8 == 0 && d.L >= 40; }
 
+// Units of a bit-plane job in the shared-memory kernel for a per-CTA budget of
+// `smem` bytes: all replicas with the bond planes when they fit, else as many
+// replicas as fit beside the bond planes, else replicas without them; nrep = 0
+// if one replica's six planes do not fit.
+struct SplaneSplit {
+    int nrep;
+    bool bonds_smem;
+    size_t bytes;  // shared memory of one unit
+};
+
+SplaneSplit splane_split(int64_t WP, int R, size_t smem) {
+    const size_t wb = sizeof(uint32_t) * (size_t)WP;  // one plane
+    if (!smem) return {0, false, 0};
+    if ((6 * (size_t)R + 12) * wb <= smem) return {R, true, (6 * (size_t)R + 12) * wb};
+    if (18 * wb <= smem) {
+        const int n = (int)std::min<size_t>((size_t)R, (smem / wb - 12) / 6);
+        return {n, true, (6 * (size_t)n + 12) * wb};
+    }
+    if (6 * wb <= smem) {
+        const int n = (int)std::min<size_t>((size_t)R, smem / (6 * wb));
+        return {n, false, 6 * (size_t)n * wb};
+    }
+    return {0, false, 0};
+}
+
 JobSizes job_sizes(const micsa_job_desc &d) {
     JobSizes s;
     s.g = make_geometry(d.L);
@@ -568,6 +695,8 @@ int pool_words(const Geometry &g, int max_words) {
     return 1;
 }
 
+void drop_pool_graphs(micsa_pool_t p);
+
 // Rebuild the virtual-block table and upload both tables (descriptor rows and
 // vblocks) after the previous upload has been consumed.
 int upload_tables(micsa_pool_t p) {
@@ -581,7 +710,8 @@ int upload_tables(micsa_pool_t p) {
     std::sort(order.begin(), order.end(), [&](int a, int b) {
         return p->slots[a].desc.L * p->slots[a].desc.n_replicas > p->slots[b].desc.L * p->slots[b].desc.n_replicas;
     });
-    int npvb = 0;
+    int npvb = 0, npu = 0;
+    size_t unit_smem = 0;
     for (int i : order) {
         const JobDesc &J = p->h_jobs[i];
         if (J.resident) {
@@ -604,7 +734,15 @@ int upload_tables(micsa_pool_t p) {
                     if (nvb >= p->max_vblocks) return pfail(p, MICSA_E_BUSY, "virtual block table full");
                     p->h_vblocks[nvb++] = VBlock{i, (int16_t)r, 0, (int32_t)c};
                 }
-            if (pass == 1) {
+            if (pass == 1 && J.smem_planes) {
+                const SplaneSplit sp = splane_split(msg_plane_words(J.geo), J.R, J.smem_planes);
+                for (int r0 = 0; r0 < J.R; r0 += sp.nrep) {
+                    if (npu >= p->max_punits) return pfail(p, MICSA_E_BUSY, "plane unit table full");
+                    p->h_punits[npu++] = PlaneUnit{i, (int16_t)r0, (int16_t)std::min(sp.nrep, J.R - r0),
+                                                   sp.bonds_smem ? 1 : 0};
+                    unit_smem = std::max(unit_smem, sp.bytes);
+                }
+            } else if (pass == 1) {
                 const int64_t threads = msg_plane_words(J.geo) / 4;  // 4 plane words each
                 for (int64_t c = 0; c < threads; c += kVBlock) {
                     if (npvb >= p->max_pvblocks) return pfail(p, MICSA_E_BUSY, "plane block table full");
@@ -654,6 +792,12 @@ int upload_tables(micsa_pool_t p) {
         prev = end;
     }
     *p->h_nunits = nunits;
+    *p->h_npunits = npu;
+    p->has_splane_jobs = npu > 0;
+    if (unit_smem != p->splanes_launch_smem) {  // the launch's shared memory changes: recapture
+        p->splanes_launch_smem = unit_smem;
+        drop_pool_graphs(p);
+    }
     p->has_stream_jobs = nvb_stream > 0;
     p->has_resident_jobs = nunits > 0;
     p->has_plane_jobs = npvb > 0;
@@ -667,6 +811,8 @@ int upload_tables(micsa_pool_t p) {
         PCK(p, cudaMemcpyAsync(p->d_units, p->h_units, sizeof(ResidentUnit) * (size_t)(nunits ? nunits : 1), cudaMemcpyHostToDevice, p->stream), "upload units");
         PCK(p, cudaMemcpyAsync(p->d_nunits, p->h_nunits, sizeof(int32_t), cudaMemcpyHostToDevice, p->stream), "upload unit count");
     }
+    PCK(p, cudaMemcpyAsync(p->d_punits, p->h_punits, sizeof(PlaneUnit) * (size_t)(npu ? npu : 1), cudaMemcpyHostToDevice, p->stream), "upload plane units");
+    PCK(p, cudaMemcpyAsync(p->d_npunits, p->h_npunits, sizeof(int32_t), cudaMemcpyHostToDevice, p->stream), "upload plane unit count");
     PCK(p, cudaEventRecord(p->tables_free, p->stream), "record table event");
     p->tables_dirty = false;
     return MICSA_OK;
@@ -701,6 +847,22 @@ int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
         ra.results = p->d_results;
         ra.max_jobs = p->max_jobs;
         PCK(p, launch_multispin(ra, true, p->resident_smem, p->resident_grid, p->pdl && !fork, rs), "pool multispin launch");
+    }
+    const bool splanes = (mask & 8) != 0;
+    if (splanes) {
+        // the bit-plane jobs held in shared memory: one persistent launch on its own branch
+        PCK(p, cudaEventRecord(p->splanes_fork, st), "smem planes fork event");
+        PCK(p, cudaStreamWaitEvent(p->splanes_stream, p->splanes_fork, 0), "smem planes fork wait");
+        int K = p->K;
+        int *ctr = p->d_counter + 1;
+        void *args[] = {&T, &p->d_punits, &p->d_npunits, &ctr, &K};
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(p->splanes_grid);
+        cfg.blockDim = dim3(kSmemPlaneThreads);
+        cfg.dynamicSmemBytes = p->splanes_launch_smem;
+        cfg.stream = p->splanes_stream;
+        PCK(p, cudaLaunchKernelExC(&cfg, (const void *)pool_smem_planes_kernel, args), "pool smem planes launch");
+        PCK(p, cudaEventRecord(p->splanes_join, p->splanes_stream), "smem planes join event");
     }
     if (planes) {
         // the bit-plane jobs' parts on their own branches: bytes -> planes, the K
@@ -751,7 +913,8 @@ int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
     if (planes)
         for (int part = 0; part < p->chains; ++part)
             PCK(p, cudaStreamWaitEvent(st, p->planes_join[part], 0), "planes join wait");
-    if (streamed || planes) {
+    if (splanes) PCK(p, cudaStreamWaitEvent(st, p->splanes_join, 0), "smem planes join wait");
+    if (streamed || planes || splanes) {
         int K = p->K;
         void *eargs[] = {&T};
         void *bargs[] = {&T, &K};
@@ -773,7 +936,8 @@ int tick_launches(micsa_pool_t p, int mask) {
     const int resident = (mask & 1) && p->resident_smem ? 1 : 0;
     const int streamed = (mask & 2) ? 2 * p->chains * p->K : 0;
     const int planes = (mask & 4) ? p->chains * (2 * p->K + 2) : 0;
-    return resident + streamed + planes + ((mask & 6) ? 3 : 0) + 1;
+    const int splanes = (mask & 8) ? 1 : 0;
+    return resident + streamed + planes + splanes + ((mask & 14) ? 3 : 0) + 1;
 }
 
 int ensure_graph(micsa_pool_t p, int mask) {
@@ -878,12 +1042,36 @@ int micsa_pool_create(size_t arena_bytes, int max_jobs, int tick_sweeps, micsa_p
         p->max_units = max_jobs * kPoolMaxR;
         if ((e = cudaMalloc(&p->d_units, sizeof(ResidentUnit) * (size_t)p->max_units)) != cudaSuccess ||
             (e = cudaMalloc(&p->d_nunits, sizeof(int32_t))) != cudaSuccess ||
-            (e = cudaMalloc(&p->d_counter, sizeof(int))) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_counter, 2 * sizeof(int))) != cudaSuccess ||
             (e = cudaMallocHost(&p->h_units, sizeof(ResidentUnit) * (size_t)p->max_units)) != cudaSuccess ||
             (e = cudaMallocHost(&p->h_nunits, sizeof(int32_t))) != cudaSuccess) { bail(MICSA_E_OOM); break; }
         *p->h_nunits = 0;
         if ((e = cudaMemsetAsync(p->d_nunits, 0, sizeof(int32_t), p->stream)) != cudaSuccess ||
-            (e = cudaMemsetAsync(p->d_counter, 0, sizeof(int), p->stream)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+            (e = cudaMemsetAsync(p->d_counter, 0, 2 * sizeof(int), p->stream)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+        // bit-plane jobs in shared memory: one CTA of kSmemPlaneThreads per unit, the budget
+        // the device allows a block (opt-in) less the kernel's static shared memory
+        p->max_punits = max_jobs * kPoolMaxR;
+        if ((e = cudaMalloc(&p->d_punits, sizeof(PlaneUnit) * (size_t)p->max_punits)) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_npunits, sizeof(int32_t))) != cudaSuccess ||
+            (e = cudaMallocHost(&p->h_punits, sizeof(PlaneUnit) * (size_t)p->max_punits)) != cudaSuccess ||
+            (e = cudaMallocHost(&p->h_npunits, sizeof(int32_t))) != cudaSuccess) { bail(MICSA_E_OOM); break; }
+        *p->h_npunits = 0;
+        if ((e = cudaMemsetAsync(p->d_npunits, 0, sizeof(int32_t), p->stream)) != cudaSuccess ||
+            (e = cudaStreamCreateWithFlags(&p->splanes_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&p->splanes_fork, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&p->splanes_join, cudaEventDisableTiming)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+        {
+            int optin = 0;
+            cudaFuncAttributes fa{};
+            if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device)) != cudaSuccess ||
+                (e = cudaFuncGetAttributes(&fa, pool_smem_planes_kernel)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+            p->splanes_max_smem = (size_t)optin > fa.sharedSizeBytes ? ((size_t)optin - fa.sharedSizeBytes) / 16 * 16 : 0;
+            if (p->splanes_max_smem &&
+                (e = cudaFuncSetAttribute(pool_smem_planes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)p->splanes_max_smem)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+            p->splanes_smem = p->splanes_max_smem;
+            p->splanes_grid = p->sm_count;  // one CTA per SM at the full budget
+        }
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pool_half_sweep_kernel, kVBlock, 0);
         int per_sm_planes = 0;
@@ -931,6 +1119,16 @@ void micsa_pool_destroy(micsa_pool_t p) {
     cudaFree(p->d_units);
     cudaFree(p->d_nunits);
     cudaFree(p->d_counter);
+    cudaFree(p->d_punits);
+    cudaFree(p->d_npunits);
+    cudaFreeHost(p->h_punits);
+    cudaFreeHost(p->h_npunits);
+    if (p->splanes_stream) {
+        cudaStreamSynchronize(p->splanes_stream);
+        cudaStreamDestroy(p->splanes_stream);
+    }
+    if (p->splanes_fork) cudaEventDestroy(p->splanes_fork);
+    if (p->splanes_join) cudaEventDestroy(p->splanes_join);
     cudaFreeHost(p->h_units);
     cudaFreeHost(p->h_nunits);
     cudaFreeHost(p->h_vblocks);
@@ -1063,6 +1261,8 @@ int micsa_pool_submit(micsa_pool_t p, const micsa_job_desc *job, int64_t *job_id
     D.divC_l = fdC.l;
     D.resident = (p->resident_smem && multispin_smem_bytes(s.g) && multispin_smem_bytes(s.g) <= p->resident_smem) ? 1 : 0;
     D.use_planes = (p->planes_on && plane_eligible(d) && !D.resident) ? 1 : 0;
+    D.smem_planes = (D.use_planes && splane_split(msg_plane_words(s.g), d.n_replicas, p->splanes_smem).nrep > 0)
+                        ? (int32_t)p->splanes_smem : 0;
     D.planes = D.use_planes ? reinterpret_cast<uint32_t *>(base + J.off_planes) : nullptr;
     D.bplanes = D.use_planes ? reinterpret_cast<const uint32_t *>(base + J.off_bplanes) : nullptr;
     if (D.use_planes) {  // the bonds never change: their planes are made once
@@ -1079,7 +1279,8 @@ int micsa_pool_submit(micsa_pool_t p, const micsa_job_desc *job, int64_t *job_id
 int micsa_pool_tick(micsa_pool_t p) {
     if (!p) return MICSA_E_INVALID_ARG;
     if (int rc = upload_tables(p)) return rc;
-    const int mask = (p->has_resident_jobs ? 1 : 0) | (p->has_stream_jobs ? 2 : 0) | (p->has_plane_jobs ? 4 : 0);
+    const int mask = (p->has_resident_jobs ? 1 : 0) | (p->has_stream_jobs ? 2 : 0) | (p->has_plane_jobs ? 4 : 0) |
+                     (p->has_splane_jobs ? 8 : 0);
     if (int rc = ensure_graph(p, mask)) return rc;
     if (p->graphs[mask]) {
         PCK(p, cudaGraphLaunch(p->graphs[mask], p->stream), "pool graph launch");
@@ -1252,6 +1453,18 @@ int micsa_pool_set_launch_config(micsa_pool_t p, int blocks_per_sm, int pdl, int
 int micsa_pool_set_planes(micsa_pool_t p, int on) {
     if (!p) return MICSA_E_INVALID_ARG;
     p->planes_on = on != 0;
+    return MICSA_OK;
+}
+
+int micsa_pool_set_smem_planes(micsa_pool_t p, size_t smem_bytes, int blocks_per_sm) {
+    if (!p || blocks_per_sm < 1 || blocks_per_sm > 8) return MICSA_E_INVALID_ARG;
+    if (smem_bytes > p->splanes_max_smem)
+        return pfail(p, MICSA_E_INVALID_ARG, "shared-memory budget %zu above the device's %zu bytes", smem_bytes,
+                     p->splanes_max_smem);
+    PCK(p, cudaStreamSynchronize(p->stream), "synchronize before reshaping");
+    drop_pool_graphs(p);
+    p->splanes_smem = smem_bytes / 16 * 16;
+    p->splanes_grid = blocks_per_sm * p->sm_count;
     return MICSA_OK;
 }
 

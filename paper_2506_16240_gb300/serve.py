@@ -69,9 +69,19 @@ class Server:
 
     def serve(self, requests, realtime=True):
         """Run the stream to completion; returns the requests with timings and results.
-        realtime=False admits every request immediately (arrival times ignored)."""
+        realtime=False admits every request immediately (arrival times ignored).
+
+        Also records the saturated window: from the start until the queue first
+        empties after every request has arrived, with the spin-flip attempts the
+        device had completed by then (self.saturated = (updates, seconds)). With
+        realtime=False and more requests than the pool holds, the pool is full for
+        that whole window, so updates / seconds is its saturated capacity."""
         pending = sorted(requests, key=lambda r: r.arrival)
         queue, live, done = [], {}, []
+        K = self.pool.tick_sweeps
+        flips = 0  # attempts of the queued ticks (each live job advances min(K, sweeps left))
+        left = {}
+        self.saturated = None
         t0 = time.perf_counter()
         i = 0
         while i < len(pending) or queue or live:
@@ -87,8 +97,16 @@ class Server:
                     break
                 r.job_id, r.admitted = jid, time.perf_counter() - t0
                 live[jid] = r
+                left[jid] = r.n_sweeps
                 queue.pop(0)
+            if self.saturated is None and i == len(pending) and not queue:
+                self.pool.wait()  # the device has run every queued tick
+                self.saturated = (flips, time.perf_counter() - t0)
             if live:
+                for jid, r in live.items():
+                    step = min(K, left[jid])
+                    left[jid] -= step
+                    flips += step * r.L ** 3 * r.n_replicas
                 self.pool.tick()
                 self.pool.wait_ticks(self.max_pending)
                 for jid in self.pool.finished():

@@ -12,8 +12,10 @@ class FakePool:
 
     def __init__(self, max_jobs=3, arena=3 * 32 ** 3 * 2, tick_sweeps=1000):
         self.max_jobs, self.arena, self.K = max_jobs, arena, tick_sweeps
+        self.tick_sweeps = tick_sweeps
         self.live, self.next_id, self.used, self.ticks = {}, 0, 0, 0
         self.admitted, self.peak_jobs, self.peak_bytes = [], 0, 0
+        self.flips, self.flips_at_wait = 0, []
 
     def submit(self, L, R, seed, n_sweeps, interval, T0, T1):
         need = L ** 3 * R
@@ -21,7 +23,7 @@ class FakePool:
             return None
         jid = self.next_id
         self.next_id += 1
-        self.live[jid] = {"need": need, "left": n_sweeps, "seed": seed, "done": False}
+        self.live[jid] = {"need": need, "left": n_sweeps, "seed": seed, "done": False, "LR": L ** 3 * R}
         self.used += need
         self.admitted.append(seed)
         self.peak_jobs = max(self.peak_jobs, len(self.live))
@@ -31,11 +33,15 @@ class FakePool:
     def tick(self):
         self.ticks += 1
         for j in self.live.values():
+            self.flips += min(self.K, max(j["left"], 0)) * j["LR"]
             j["left"] -= self.K
             j["done"] = j["left"] <= 0
 
     def wait_ticks(self, n):
         pass
+
+    def wait(self):
+        self.flips_at_wait.append(self.flips)
 
     def finished(self):
         return [jid for jid, j in self.live.items() if j["done"]]
@@ -72,6 +78,19 @@ def test_serving_loop_admits_in_order_within_limits_and_completes_every_job():
     lat = np.array([r.done - r.arrival for r in done])
     assert s["jobs"] == 25 and s["p50_latency_s"] == pytest.approx(np.percentile(lat, 50))
     assert s["updates"] == sum(r.L ** 3 * r.n_replicas * r.n_sweeps for r in reqs)
+
+
+def test_serving_loop_records_the_saturated_window():
+    """With every request queued at once and more requests than slots, the pool is
+    full until the queue empties: the window's attempts are those of the ticks run
+    by then (counted by the pool itself), less than the whole stream's."""
+    pool = FakePool()
+    reqs = _requests(25)
+    srv = serve.Server(pool)
+    srv.serve(reqs, realtime=False)
+    flips, secs = srv.saturated
+    assert pool.flips_at_wait and flips == pool.flips_at_wait[0]
+    assert 0 < flips < sum(r.updates for r in reqs) and secs > 0
 
 
 def test_serving_loop_respects_arrival_times():

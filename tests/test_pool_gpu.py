@@ -33,13 +33,17 @@ def single_handle(L, R, seed, n, interval, T0, T1):
     return e, a, s
 
 
-def run_pool(jobs, K=16, arena=1 << 28, max_jobs=64, order=None, shape=None, reshape=None, planes=None):
+def run_pool(jobs, K=16, arena=1 << 28, max_jobs=64, order=None, shape=None, reshape=None, planes=None, smem=None):
     """Run jobs to completion; shape: (max_words, chains, blocks_per_sm) set
     before the submissions, reshape: one set after the first tick; planes: the
-    bit-plane path on or off for the jobs (None: the pool's default, on)."""
+    bit-plane path on or off for the jobs (None: the pool's default, on); smem:
+    (budget bytes, blocks per SM) of the shared-memory bit-plane kernel (None:
+    the default, the device's largest budget)."""
     with micsa.Pool(arena, max_jobs, K) as p:
         if planes is not None:
             p.set_planes(planes)
+        if smem is not None:
+            p.set_smem_planes(*smem)
         if shape:
             p.set_shape(shape[0], shape[1])
             p.set_launch_config(shape[2])
@@ -321,6 +325,41 @@ def test_pool_plane_jobs_match_oracle():
         np.testing.assert_array_equal(res[idx]["aux"], a, err_msg=str(JOBS_PLANES[idx]))
         assert_final_state(res[idx], st, JOBS_PLANES[idx])
         assert res[idx]["sweeps_done"] == n
+
+
+_PLANE_REF = {}
+
+
+def _plane_oracle(idx):
+    if idx not in _PLANE_REF:
+        L, R, seed, n, interval, T0, T1 = JOBS_PLANES[idx]
+        st = O.create(L, 1, R, seed)
+        O.run(st, micsa.linear_schedule(T0, T1, n), interval)
+        _PLANE_REF[idx] = (st, O.measure(st))
+    return _PLANE_REF[idx]
+
+
+@pytest.mark.parametrize("smem", [(0, 1), (60 << 10, 2), (120 << 10, 1), (120 << 10, 2)])
+def test_pool_smem_plane_budgets_match_oracle(smem):
+    """The shared-memory bit-plane kernel at several budgets: off; 60 KB (one
+    replica per unit, bonds from the arena, the larger jobs on the global bit
+    planes); 120 KB (one replica beside its bond planes for L = 40, two replicas
+    without them for L = 48, one for L = 56 and 64), one or two CTAs per SM; the
+    default budget is covered by every other pool test. Final state, energies
+    and daemon energies equal the oracle's."""
+    res = run_pool(JOBS_PLANES, K=4, smem=smem)
+    for idx, job in enumerate(JOBS_PLANES):
+        st, (e, a, _) = _plane_oracle(idx)
+        np.testing.assert_array_equal(res[idx]["energy"], e, err_msg=f"{job} {smem}")
+        np.testing.assert_array_equal(res[idx]["aux"], a, err_msg=f"{job} {smem}")
+        assert_final_state(res[idx], st, f"{job} {smem}")
+
+
+def test_pool_smem_planes_rejects_bad_values():
+    with micsa.Pool(1 << 24, 4, 4) as p:
+        for budget, bps in [(1 << 30, 1), (1 << 16, 0), (1 << 16, 9)]:
+            with pytest.raises(micsa.MicsaError):
+                p.set_smem_planes(budget, bps)
 
 
 @pytest.mark.parametrize("K", [3, 16])
