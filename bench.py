@@ -354,7 +354,7 @@ def plane_roofline(micsa, timer, stream, g, peaks, n_plain=2000):
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": rec[0] if rec else None, "traffic_l2": rec[1] if rec else None,
             "traffic_capture": rec[2] if rec else f"no capture of the current kernel for {key}",
-            "l2_resident": L ** 3 * S * (3 * R + 6) // 16 < 129e6,
+            "l2_resident": L ** 3 * S * (6 * R + 12) // 16 < 129e6,  # six planes per replica, twelve of bonds
             "peak_source": "measured" if hbm else "fallback",
             "kernel": "micsa::msg_half_kernel (bit-plane MicSA half-sweep, no refresh)",
             "L": L, "replicas": R, "bytes_per_launch": bytes_per_launch, "launch_us": launch_us,
@@ -594,15 +594,53 @@ def c4_instances():
     return [(int(L), int(r), int(s)) for L, r, s in zip(Ls, rs, seeds)]
 
 
-def leg_batched(micsa, torch, stream, n_sweeps=20_000, loop_sweeps=2_000):
+def pool_job_path(L, R, planes_budget):
+    """Which part of a pool tick advances a job (the pool's own rules): 'smem'
+    (L <= 32: the shared-memory multispin kernel), 'smem_planes' (L a multiple of 8,
+    at least 40, one replica's six bit planes within the shared-memory budget),
+    'planes' (the other such L: global bit planes), 'bytes' (byte streaming)."""
+    if L <= 32:
+        return "smem"
+    if L % 8 == 0 and L >= 40:
+        WP = L * ((L + 31) // 32) * (L // 2)
+        return "smem_planes" if planes_budget and 6 * 4 * WP <= planes_budget else "planes"
+    return "bytes"
+
+
+def pool_roofline(jobs, seconds, K, planes_budget, peaks):
+    """Algorithmic bytes per second of a pool run against the HBM peak. Per site
+    update: byte streaming 5 + 1/R B (spin and daemon read and written, the
+    opposite spin, the bond byte shared by R replicas); global bit planes
+    (7 + 6/R) / 8 B; shared memory (both kernels): the state in and out once per
+    tick, (4 + 1/R) / K B. jobs: (L, R, sweeps run)."""
+    per_path, total_bytes, total_upd = {}, 0.0, 0
+    for L, R, n in jobs:
+        path = pool_job_path(L, R, planes_budget)
+        b = {"bytes": 5 + 1 / R, "planes": (7 + 6 / R) / 8}.get(path, (4 + 1 / R) / K)
+        upd = L ** 3 * R * n
+        total_bytes += b * upd
+        total_upd += upd
+        per_path[path] = per_path.get(path, 0) + upd
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    achieved = total_bytes / seconds / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": None, "peak_source": "measured" if peaks.get("hbm_gbs") else "fallback",
+            "bytes_per_update": total_bytes / total_upd,
+            "updates_by_path": {k: v / total_upd for k, v in per_path.items()},
+            "note": "most updates run in shared memory (state in and out once per tick): far below the HBM "
+                    "roofline, bound by integer/logic issue"}
+
+
+def leg_batched(micsa, torch, stream, peaks, n_sweeps=20_000, loop_sweeps=2_000):
     from paper_2506_16240_gb300 import autotune
     inst = c4_instances()
     total = sum(updates(L, 1, 2, n_sweeps) for L, _, _ in inst)
     jobs = [(L, 2, s, n_sweeps, r, 2.5, 0.5) for L, r, s in inst]
     # pool shape (words per thread, chains, grid) from the autotuner, on a scratch pool of the same jobs
-    choice = autotune.tune_pool_for_jobs(lambda: micsa.Pool(8 << 30, 512, 32), jobs)
+    choice = autotune.tune_pool_for_jobs(lambda: micsa.Pool(8 << 30, 512, 256), jobs, ticks=1)
     with micsa.Pool(8 << 30, 512, 256) as p:
         autotune.apply_pool(p, choice)
+        budget = p.smem_planes()[0]
         ids = [p.submit(*j) for j in jobs]
         assert all(i is not None for i in ids)
         p.wait()
@@ -633,11 +671,12 @@ def leg_batched(micsa, torch, stream, n_sweeps=20_000, loop_sweeps=2_000):
     batched, loop = total / (dt_pool * 1e9), loop_upd / (dt_loop * 1e9)
     return {"value": batched, "unit": METRIC, "per_lattice_loop": loop, "speedup": batched / loop,
             "wall_s": dt_pool, "launches": launches, "launch": choice,
+            "roofline": pool_roofline([(L, 2, n_sweeps) for L, _, _ in inst], dt_pool, 256, budget, peaks),
             "workload": "256 lattices L in {16,24,32,48,64} x 2 replicas, anneal 2.5->0.5 over 2e4 sweeps, "
                         "refresh 5..20; the loop is timed on its first 2e3 sweeps"}
 
 
-def leg_serving(micsa, torch, stream, n_jobs, n_cap=600, slots=256, K=128):
+def leg_serving(micsa, torch, stream, n_jobs, peaks, n_cap=600, slots=256, K=128):
     """The serving stream through the continuous-batching pool. Saturated capacity:
     n_cap requests of the same mix queued at once, more than the pool's slots, so
     that the pool stays full until the queue empties; the capacity is the attempts
@@ -649,6 +688,7 @@ def leg_serving(micsa, torch, stream, n_jobs, n_cap=600, slots=256, K=128):
     choice = autotune.tune_pool_for_jobs(lambda: micsa.Pool(16 << 30, slots, 32), desc)
     with micsa.Pool(16 << 30, slots, K) as p:
         autotune.apply_pool(p, choice)
+        budget = p.smem_planes()[0]
         srv = serve.Server(p)
         l0 = p.stats()["launches"]
         srv.serve(cap_reqs, realtime=False)
@@ -678,6 +718,7 @@ def leg_serving(micsa, torch, stream, n_jobs, n_cap=600, slots=256, K=128):
         done = server.serve(reqs, realtime=True)
     out = serve.summarize(done, server.wall)
     out.update({"unit": METRIC, "arrival_rate_hz": rate_hz, "launch": choice, "slots": slots, "tick_sweeps": K,
+                "roofline": pool_roofline([(r.L, r.n_replicas, r.n_sweeps) for r in done], server.wall, K, budget, peaks),
                 "saturated_pool_flips_per_ns": capacity / 1e9, "saturated_window_s": sat_s,
                 "capacity_run_flips_per_ns": drained / 1e9, "capacity_run_launches": cap_launches,
                 "per_job_loop_flips_per_ns": loop_rate / 1e9, "saturated_over_loop": capacity / loop_rate,
@@ -922,8 +963,8 @@ def main(argv=None):
         legs = [("dram_point", lambda: leg_roofline(micsa, timer, stream, 400, peaks, n_plain=300, choice=tuned)),
                 ("metropolis", lambda: leg_metropolis(micsa, timer, stream, choice=tuned)),
                 ("quench_l32", lambda: leg_quench_l32(micsa, timer, stream)),
-                ("batched", lambda: leg_batched(micsa, torch, stream)),
-                ("serving", lambda: leg_serving(micsa, torch, stream, args.serving_jobs)),
+                ("batched", lambda: leg_batched(micsa, torch, stream, peaks)),
+                ("serving", lambda: leg_serving(micsa, torch, stream, args.serving_jobs, peaks)),
                 ("multispin_l160", lambda: leg_multispin_l160(micsa, timer, stream, peaks)),
                 ("onchip_l160", lambda: leg_onchip_l160(micsa, timer, stream)),
                 ("paper_shape", lambda: leg_paper_shape(micsa, timer, stream, peaks)),

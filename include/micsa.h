@@ -402,9 +402,14 @@ int micsa_pool_set_planes(micsa_pool_t p, int on);
  * unit's bytes to planes in its shared memory, runs the tick's sweeps there
  * with the same bit-plane update and Philox counters, and converts back, so
  * the results are identical either way. smem_bytes = 0 turns it off;
- * blocks_per_sm (1..8) sets the launch's grid. MICSA_E_INVALID_ARG for a
- * budget above the device's limit. Synchronizes. */
+ * blocks_per_sm (1..8) sets the launch's grid (CTAs of 512 threads for one per
+ * SM, of 256 for more). MICSA_E_INVALID_ARG for a budget above the device's
+ * limit. Synchronizes. */
 int micsa_pool_set_smem_planes(micsa_pool_t p, size_t smem_bytes, int blocks_per_sm);
+
+/* The current budget, the largest the device allows, and the blocks per SM of
+ * the shared-memory bit-plane path. Any pointer may be NULL. */
+int micsa_pool_get_smem_planes(micsa_pool_t p, size_t *smem_bytes, size_t *max_smem_bytes, int *blocks_per_sm);
 
 /* Message of the last failure on p. */
 const char *micsa_pool_last_error(micsa_pool_t p);

@@ -332,6 +332,8 @@ SIGNATURES.update({
     "micsa_pool_set_shape": (_c.c_int, [_P, _c.c_int, _c.c_int]),
     "micsa_pool_set_planes": (_c.c_int, [_P, _c.c_int]),
     "micsa_pool_set_smem_planes": (_c.c_int, [_P, _c.c_size_t, _c.c_int]),
+    "micsa_pool_get_smem_planes": (_c.c_int, [_P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
+                                              ctypes.POINTER(_c.c_int)]),
     "micsa_pool_last_error": (_c.c_char_p, [_P]),
     "micsa_pool_destroy": (None, [_P]),
 })
@@ -457,6 +459,13 @@ class Pool:
         sweeps the bit-plane jobs admitted from now on in shared memory; results do
         not depend on it."""
         self._check(lib().micsa_pool_set_smem_planes(self.h, int(smem_bytes), int(blocks_per_sm)))
+
+    def smem_planes(self):
+        """(budget bytes, the device's largest budget, blocks per SM) of the
+        shared-memory bit-plane path."""
+        b, m, n = ctypes.c_size_t(), ctypes.c_size_t(), ctypes.c_int()
+        self._check(lib().micsa_pool_get_smem_planes(self.h, ctypes.byref(b), ctypes.byref(m), ctypes.byref(n)))
+        return b.value, m.value, n.value
 
     def set_planes(self, on=True):
         """Bit-plane half-sweeps for the jobs admitted from now on with L a

@@ -138,8 +138,22 @@ def pool_candidates():
 
 
 def apply_pool(pool, choice):
+    """Apply a pool choice (the shared-memory bit-plane setting applies to the
+    jobs admitted afterwards: apply it before submitting)."""
     pool.set_shape(choice["max_words"], choice["chains"])
     pool.set_launch_config(choice.get("blocks_per_sm", 0))  # 0: as many blocks as fit
+    if "smem_planes" in choice:
+        budget, bps = choice["smem_planes"]
+        pool.set_smem_planes(min(budget, pool.smem_planes()[1]), bps)
+
+
+def smem_plane_candidates(max_budget):
+    """(budget bytes, CTAs per SM) of the shared-memory bit-plane path: off; the
+    whole budget (a unit takes as many replicas of a job as fit); 100 KB (units of
+    one replica up to L = 64: more, shorter units, so the tick is not held up by
+    the longest one); 60 KB (one replica of L <= 48, the L = 56 and 64 jobs on the
+    global bit planes). One CTA of 512 threads per SM."""
+    return [(0, 1), (max_budget, 1), (min(max_budget, 100 << 10), 1), (min(max_budget, 60 << 10), 1)]
 
 
 def time_pool_ticks(pool, ticks, clock):
@@ -180,16 +194,29 @@ def tune_pool(pool, ticks=2, blocks=(3, 4, 5, 6, 8), clock=None):
     return dict(best[1], s_per_tick=best[0])
 
 
-def tune_pool_for_jobs(pool_factory, jobs, ticks=2, clock=None):
-    """Tune on a scratch pool: pool_factory() makes it, `jobs` are submit()
+def tune_pool_for_jobs(pool_factory, jobs, ticks=2, clock=None, smem=None):
+    """Tune on scratch pools: pool_factory() makes one, `jobs` are submit()
     argument tuples (L, R, seed, n_sweeps, interval, T_start, T_end) whose sweep
-    counts are raised so that no job finishes while the candidates run. Returns
-    the choice (apply it to the real pool with apply_pool)."""
+    counts are raised so that no job finishes while the candidates run. For each
+    shared-memory bit-plane setting (smem: list of (budget, CTAs per SM); None:
+    smem_plane_candidates) the jobs are admitted to a fresh scratch pool and its
+    shape tuned (tune_pool). Returns the fastest choice (apply it to the real pool
+    with apply_pool before submitting)."""
     n_cand = len(pool_candidates()) + 5
-    with pool_factory() as p:
-        K = p.tick_sweeps
-        long = (1 + ticks) * K * (n_cand + 2)  # candidates x (warm-up + timed ticks), with a margin
-        for L, R, seed, _, interval, T0, T1 in jobs:
-            if p.submit(L, R, seed, long, interval, T0, T1) is None:
-                break  # the scratch pool is full: tune on what fits
-        return tune_pool(p, ticks=ticks, clock=clock)
+    best = None
+    settings = smem
+    for k in range(len(settings) if settings is not None else 4):
+        with pool_factory() as p:
+            if settings is None:
+                settings = smem_plane_candidates(p.smem_planes()[1])
+            budget, bps = settings[k]
+            p.set_smem_planes(budget, bps)
+            K = p.tick_sweeps
+            long = (1 + ticks) * K * (n_cand + 2)  # candidates x (warm-up + timed ticks), with a margin
+            for L, R, seed, _, interval, T0, T1 in jobs:
+                if p.submit(L, R, seed, long, interval, T0, T1) is None:
+                    break  # the scratch pool is full: tune on what fits
+            c = dict(tune_pool(p, ticks=ticks, clock=clock), smem_planes=[budget, bps])
+        if best is None or c["s_per_tick"] < best["s_per_tick"]:
+            best = c
+    return best

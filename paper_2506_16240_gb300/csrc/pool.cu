@@ -57,7 +57,10 @@ struct PlaneUnit {
     int32_t bonds_smem;
 };
 
+// CTA sizes of the shared-memory bit-plane kernel: 512 threads for one CTA per
+// SM, 256 threads for two or more (registers: about 120 per thread)
 constexpr int kSmemPlaneThreads = 512;
+constexpr int kSmemPlaneThreadsSmall = 256;
 
 struct PoolTables {
     JobDesc *jobs;          // [max_jobs]
@@ -290,7 +293,8 @@ __global__ void __launch_bounds__(kVBlock, 4) pool_msg_half_kernel(PoolTables T,
 // odd one, each the body of the global bit-plane kernel (msg_update) over the
 // CTA's word groups, the refresh at the job's refresh sweeps -- and convert
 // back. No state leaves the SM between the half-sweeps of a tick.
-__global__ void __launch_bounds__(kSmemPlaneThreads, 1)
+template <int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
     pool_smem_planes_kernel(PoolTables T, const PlaneUnit *units, const int32_t *n_units, int *counter, int K) {
     pool_wait();
     pool_release();
@@ -856,12 +860,15 @@ int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
         int K = p->K;
         int *ctr = p->d_counter + 1;
         void *args[] = {&T, &p->d_punits, &p->d_npunits, &ctr, &K};
+        const bool small = p->splanes_grid > p->sm_count;  // two or more CTAs per SM
         cudaLaunchConfig_t cfg = {};
         cfg.gridDim = dim3(p->splanes_grid);
-        cfg.blockDim = dim3(kSmemPlaneThreads);
+        cfg.blockDim = dim3(small ? kSmemPlaneThreadsSmall : kSmemPlaneThreads);
         cfg.dynamicSmemBytes = p->splanes_launch_smem;
         cfg.stream = p->splanes_stream;
-        PCK(p, cudaLaunchKernelExC(&cfg, (const void *)pool_smem_planes_kernel, args), "pool smem planes launch");
+        const void *fn = small ? (const void *)pool_smem_planes_kernel<kSmemPlaneThreadsSmall, 2>
+                               : (const void *)pool_smem_planes_kernel<kSmemPlaneThreads, 1>;
+        PCK(p, cudaLaunchKernelExC(&cfg, fn, args), "pool smem planes launch");
         PCK(p, cudaEventRecord(p->splanes_join, p->splanes_stream), "smem planes join event");
     }
     if (planes) {
@@ -1064,11 +1071,16 @@ int micsa_pool_create(size_t arena_bytes, int max_jobs, int tick_sweeps, micsa_p
             int optin = 0;
             cudaFuncAttributes fa{};
             if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, p->device)) != cudaSuccess ||
-                (e = cudaFuncGetAttributes(&fa, pool_smem_planes_kernel)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+                (e = cudaFuncGetAttributes(&fa, pool_smem_planes_kernel<kSmemPlaneThreads, 1>)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
             p->splanes_max_smem = (size_t)optin > fa.sharedSizeBytes ? ((size_t)optin - fa.sharedSizeBytes) / 16 * 16 : 0;
             if (p->splanes_max_smem &&
-                (e = cudaFuncSetAttribute(pool_smem_planes_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)p->splanes_max_smem)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+                ((e = cudaFuncSetAttribute(pool_smem_planes_kernel<kSmemPlaneThreads, 1>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->splanes_max_smem)) != cudaSuccess ||
+                 (e = cudaFuncSetAttribute(pool_smem_planes_kernel<kSmemPlaneThreadsSmall, 2>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->splanes_max_smem)) != cudaSuccess)) {
+                bail(MICSA_E_CUDA);
+                break;
+            }
             p->splanes_smem = p->splanes_max_smem;
             p->splanes_grid = p->sm_count;  // one CTA per SM at the full budget
         }
@@ -1465,6 +1477,14 @@ int micsa_pool_set_smem_planes(micsa_pool_t p, size_t smem_bytes, int blocks_per
     drop_pool_graphs(p);
     p->splanes_smem = smem_bytes / 16 * 16;
     p->splanes_grid = blocks_per_sm * p->sm_count;
+    return MICSA_OK;
+}
+
+int micsa_pool_get_smem_planes(micsa_pool_t p, size_t *smem_bytes, size_t *max_smem_bytes, int *blocks_per_sm) {
+    if (!p) return MICSA_E_INVALID_ARG;
+    if (smem_bytes) *smem_bytes = p->splanes_smem;
+    if (max_smem_bytes) *max_smem_bytes = p->splanes_max_smem;
+    if (blocks_per_sm) *blocks_per_sm = p->splanes_grid / (p->sm_count > 0 ? p->sm_count : 1);
     return MICSA_OK;
 }
 

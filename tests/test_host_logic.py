@@ -240,6 +240,14 @@ class FakeShapedPool:
     def __init__(self, cost, tick_sweeps=8):
         self.cost, self.tick_sweeps = cost, tick_sweeps
         self.shape, self.blocks, self.now, self.submitted, self.ticks = (4, 2), 0, 0.0, [], 0
+        self.smem = (200_000, 1)
+
+    def smem_planes(self):
+        return self.smem[0], 200_000, self.smem[1]
+
+    def set_smem_planes(self, budget, bps):
+        assert 0 <= budget <= 200_000 and 1 <= bps <= 8
+        self.smem = (budget, bps)
 
     def __enter__(self):
         return self
@@ -261,7 +269,7 @@ class FakeShapedPool:
 
     def tick(self):
         self.ticks += 1
-        self.now += self.cost(self.shape, self.blocks)
+        self.now += self.cost(self.shape, self.blocks) * (self.smem_cost(self.smem) if hasattr(self, "smem_cost") else 1.0)
 
     def wait(self):
         pass
@@ -273,7 +281,7 @@ def test_pool_autotuner_picks_the_fastest_shape_then_grid():
         return base - (0.2 if (shape == (2, 3) and blocks == 5) else 0.0)
     fake = FakeShapedPool(cost)
     jobs = [(48, 2, 1, 100, 10, 2.5, 0.5), (64, 1, 2, 50, 5, 2.0, 1.0)]
-    choice = autotune.tune_pool_for_jobs(lambda: fake, jobs, ticks=2, clock=lambda: fake.now)
+    choice = autotune.tune_pool_for_jobs(lambda: fake, jobs, ticks=2, clock=lambda: fake.now, smem=[(0, 1)])
     assert (choice["max_words"], choice["chains"], choice["blocks_per_sm"]) == (2, 3, 5)
     assert fake.shape == (2, 3) and fake.blocks == 5  # applied
     assert choice["s_per_tick"] == pytest.approx(0.8)
@@ -281,6 +289,26 @@ def test_pool_autotuner_picks_the_fastest_shape_then_grid():
     n_cand = len(autotune.pool_candidates()) + 5
     assert fake.ticks == 3 * n_cand
     assert all(n >= fake.ticks * fake.tick_sweeps for n in fake.submitted)
+
+
+def test_pool_autotuner_picks_the_fastest_shared_memory_setting():
+    """Each shared-memory bit-plane setting is set on a fresh scratch pool before
+    the jobs are admitted; the fastest setting wins and is part of the choice."""
+    fake = FakeShapedPool(lambda shape, blocks: 1.0)
+    fake.smem_cost = lambda sm: {(0, 1): 1.0, (200_000, 1): 0.9, (100 << 10, 1): 0.6, (60 << 10, 1): 0.7}[sm]
+    seen = []
+
+    def factory():
+        seen.append(len(fake.submitted))  # a fresh pool: the jobs come after the setting
+        return fake
+    jobs = [(48, 2, 1, 100, 10, 2.5, 0.5)]
+    choice = autotune.tune_pool_for_jobs(factory, jobs, ticks=1, clock=lambda: fake.now)
+    assert choice["smem_planes"] == [100 << 10, 1]
+    assert seen == [0, 1, 2, 3]
+    assert choice["s_per_tick"] == pytest.approx(0.6)
+    applied = FakeShapedPool(lambda shape, blocks: 1.0)
+    autotune.apply_pool(applied, choice)
+    assert applied.smem == (100 << 10, 1)
 
 
 def test_pool_autotuner_keeps_the_default_grid_when_no_grid_is_faster():
