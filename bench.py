@@ -595,16 +595,14 @@ def c4_instances():
 
 
 def pool_job_path(L, R, planes_budget):
-    """Which part of a pool tick advances a job (the pool's own rules): 'smem'
-    (L <= 32: the shared-memory multispin kernel), 'smem_planes' (L a multiple of 8,
-    at least 40, one replica's six bit planes within the shared-memory budget),
-    'planes' (the other such L: global bit planes), 'bytes' (byte streaming)."""
+    """Which part of a pool tick advances a job (the pool's own rules, bit-plane
+    path on): 'smem' (L <= 32: the shared-memory multispin kernel), 'smem_planes'
+    (L > 32 with one replica's six bit planes within the shared-memory budget; rows
+    of 4 ceil(L/8) words), 'planes' (the other L > 32: global bit planes)."""
     if L <= 32:
         return "smem"
-    if L % 8 == 0 and L >= 40:
-        WP = L * ((L + 31) // 32) * (L // 2)
-        return "smem_planes" if planes_budget and 6 * 4 * WP <= planes_budget else "planes"
-    return "bytes"
+    WP = L * ((L + 31) // 32) * 4 * ((L // 2 + 3) // 4)
+    return "smem_planes" if planes_budget and 6 * 4 * WP <= planes_budget else "planes"
 
 
 def pool_roofline(jobs, seconds, K, planes_budget, peaks):

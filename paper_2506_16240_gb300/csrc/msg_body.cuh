@@ -142,11 +142,12 @@ __device__ __forceinline__ void gather_words(const uint32_t *Sx, int dd, int64_t
 struct MsgLattice {
     uint32_t *planes;
     const uint32_t *bonds;
-    int L, Lh, nzw, W4;  // W4 = Lh / 4 Philox blocks per row
+    int L, Lh, nzw, W4;  // Lh: plane words per row (the row stride); W4 = Lh / 4 Philox blocks per row
     int64_t WP;
     int np, gamma, walkers;  // planes per replica, daemon families, two daemon buffers
     int64_t gid0;            // Philox id of replica 0 (sample * R)
     uint32_t key0, key1;
+    int Lr;  // sites per row of one parity, L / 2; below Lh when the row is padded to whole Philox blocks
 };
 
 // Plane word w of parity p of replica rep <-> the 32 sites of its z column in
@@ -154,12 +155,25 @@ struct MsgLattice {
 __device__ __forceinline__ void msg_convert_word(uint32_t *planes, int8_t *spins, uint8_t *daemons, const Geometry &g,
                                                  int64_t WP, int gamma, int np, int buf, bool to_planes, int64_t rep,
                                                  int p, int64_t w) {
-    const int i = (int)(w % g.Lh);
-    const int y = (int)((w / g.Lh) % g.L);
-    const int zw = (int)(w / ((int64_t)g.Lh * g.L));
+    // rows of g.P plane words (the byte layout's pitch, whole Philox blocks); the
+    // words from g.Lh on hold no site and stay zero in the planes
+    const int i = (int)(w % g.P);
+    const int y = (int)((w / g.P) % g.L);
+    const int zw = (int)(w / ((int64_t)g.P * g.L));
     const int64_t in_half = ((int64_t)32 * zw * g.L + y) * g.P + i;
     const int64_t zstep = (int64_t)g.L * g.P;
     uint32_t *pl = planes + rep * np * WP;
+    if (i >= g.Lh) {
+        if (to_planes) {
+            pl[(int64_t)p * WP + w] = 0;
+            for (int al = 0; al < gamma; ++al) {
+                const int mp = 2 + ((buf * gamma + al) * 2) * 2 + p;
+                pl[(int64_t)mp * WP + w] = 0;
+                pl[(int64_t)(mp + 2) * WP + w] = 0;
+            }
+        }
+        return;
+    }
     const int64_t sbase = (rep * 2 + p) * g.half + in_half;
     const int nb = g.L - 32 * zw < 32 ? g.L - 32 * zw : 32;  // sites of the column in this word
     if (to_planes) {
@@ -202,7 +216,10 @@ __device__ __forceinline__ void msg_convert_word(uint32_t *planes, int8_t *spins
 // (the daemon planes are neither read nor written). PREFETCH: the next
 // replica's words are prefetched into L2 (planes in global memory only; a
 // caller whose planes live in shared memory passes false).
-template <int NW, bool RAGGED = false, bool METRO = false, bool PREFETCH = true>
+// PADDED: rows of a.Lh words hold a.Lr < a.Lh sites (the words from a.Lr on
+// are padding: never flipped, never a neighbour of a site; the +x wrap of the
+// row's last site comes from word 0).
+template <int NW, bool RAGGED = false, bool METRO = false, bool PREFETCH = true, bool PADDED = false>
 __device__ __forceinline__ void msg_update(const MsgLattice &a, const SweepParam &prm, int p, int zw, int y, int ig,
                                            int r_begin, int r_end) {
     constexpr int G = 4 / NW;  // lanes sharing one Philox block of words
@@ -210,10 +227,11 @@ __device__ __forceinline__ void msg_update(const MsgLattice &a, const SweepParam
     constexpr bool metro = METRO;  // Metropolis sweeps (one daemon family, no walkers)
     const int o = 1 - p;
     const int L = a.L, Lh = a.Lh;
+    const int Lr = PADDED ? a.Lr : Lh;  // sites per row
     const int i0 = NW * ig;
     const int yp = (y + 1 == L) ? 0 : y + 1, ym = (y == 0) ? L - 1 : y - 1;
     const int zwp = (zw + 1 == a.nzw) ? 0 : zw + 1, zwm = (zw == 0) ? a.nzw - 1 : zw - 1;
-    const int ip = (i0 + NW == Lh) ? 0 : i0 + NW, im = (i0 == 0) ? Lh - 1 : i0 - 1;
+    const int ip = (i0 + NW >= Lr) ? 0 : i0 + NW, im = (i0 == 0) ? Lr - 1 : i0 - 1;
     const int64_t row = (int64_t)zw * L;
     const int64_t wc = (row + y) * Lh + i0;
     const int64_t w_yp = (row + yp) * Lh + i0, w_ym = (row + ym) * Lh + i0;
@@ -300,8 +318,9 @@ __device__ __forceinline__ void msg_update(const MsgLattice &a, const SweepParam
 #pragma unroll
             for (int w = 0; w < NW; ++w) {  // word i0 + w is lane (i0 + w) & 3 of the block
                 const int j = (i0 + w) & 3;
-                m0v[w] = (j == 0 ? a0[0] : j == 1 ? a0[1] : j == 2 ? a0[2] : a0[3]) & zmask;
-                m1v[w] = (j == 0 ? a1[0] : j == 1 ? a1[1] : j == 2 ? a1[2] : a1[3]) & zmask;
+                const uint32_t wm = (!PADDED || i0 + w < Lr) ? zmask : 0u;  // padding words keep m = 0
+                m0v[w] = (j == 0 ? a0[0] : j == 1 ? a0[1] : j == 2 ? a0[2] : a0[3]) & wm;
+                m1v[w] = (j == 0 ? a1[0] : j == 1 ? a1[1] : j == 2 ? a1[2] : a1[3]) & wm;
             }
         } else if (metro) {
             // Metropolis (the canonical baseline of Sec. 2.4): one uniform per site from
@@ -352,7 +371,8 @@ __device__ __forceinline__ void msg_update(const MsgLattice &a, const SweepParam
 #pragma unroll
         for (int w = 0; w < NW; ++w) {
             const uint32_t oc = Oc[w];
-            const uint32_t o_next = w + 1 < NW ? Oc[w + 1 < NW ? w + 1 : 0] : Oip;  // word i + 1
+            uint32_t o_next = w + 1 < NW ? Oc[w + 1 < NW ? w + 1 : 0] : Oip;  // word i + 1
+            if (PADDED && i0 + w + 1 == Lr) o_next = Oip;  // the row's last site wraps to word 0
             const uint32_t o_prev = w > 0 ? Oc[w > 0 ? w - 1 : 0] : Oim;            // word i - 1
             const uint32_t nxp = (oc & ~M) | (o_next & M);
             const uint32_t nxm = (o_prev & ~M) | (oc & M);
@@ -388,6 +408,7 @@ __device__ __forceinline__ void msg_update(const MsgLattice &a, const SweepParam
                 const uint32_t v2 = u2 ^ k1, v3 = u2 & k1;
                 // Eq. (Creutz) with Eq. (flip-OK): accept <=> 3 <= u + m <= 6, m' = u + m - 3
                 acc = (v2 ^ (v1 & v0)) & ~v3 & zmask;
+                if (PADDED && i0 + w >= Lr) acc = 0;  // a padding word holds no site
                 m0v[w] = (m0 & ~acc) | (~v0 & acc);
                 m1v[w] = (m1 & ~acc) | (v2 & (v1 | v0) & acc);
             }

@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(128, MINB) msg_half_kernel(MsgArgs a) {
     const int y = (int)(rowi - zw_u * a.div_L.d);
     const MsgLattice lat{a.planes + (int64_t)sample * a.R * a.np * a.WP, a.bonds + (int64_t)sample * 12 * a.WP,
                          a.L, a.Lh, a.nzw, a.W4, a.WP, a.np, a.gamma, a.walkers, (int64_t)sample * a.R,
-                         a.key0, a.key1};
+                         a.key0, a.key1, a.Lh};
     const int r_begin = a.r0 + (int)blockIdx.y * a.rpt;
     msg_update<NW, false, METRO>(lat, prm, a.parity, (int)zw_u, y, ig, r_begin, min(a.r1, r_begin + a.rpt));
 }
@@ -539,12 +539,13 @@ __global__ void msg_convert_bonds_kernel(uint32_t *bplanes, const uint8_t *bonds
     const int64_t rem = tid - smp * 2 * WP;
     const int p = (int)(rem / WP);
     const int64_t w = rem - (int64_t)p * WP;
-    const int i = (int)(w % g.Lh);
-    const int y = (int)((w / g.Lh) % g.L);
-    const int zw = (int)(w / ((int64_t)g.Lh * g.L));
+    // rows of g.P words; the words from g.Lh on hold no site (zero bond planes)
+    const int i = (int)(w % g.P);
+    const int y = (int)((w / g.P) % g.L);
+    const int zw = (int)(w / ((int64_t)g.P * g.L));
     const int64_t base = (smp * 2 + p) * g.half + ((int64_t)32 * zw * g.L + y) * g.P + i;
     const int64_t zstep = (int64_t)g.L * g.P;
-    const int nb = g.L - 32 * zw < 32 ? g.L - 32 * zw : 32;  // sites of the column in this word
+    const int nb = i >= g.Lh ? 0 : (g.L - 32 * zw < 32 ? g.L - 32 * zw : 32);  // sites of the column in this word
     uint32_t bk[6] = {0, 0, 0, 0, 0, 0};
     for (int b = 0; b < nb; ++b) {
         const uint32_t v = bonds[base + b * zstep];
@@ -557,9 +558,10 @@ __global__ void msg_convert_bonds_kernel(uint32_t *bplanes, const uint8_t *bonds
 
 bool msg_supported(const Geometry &g) { return g.L >= 32 && g.L % 32 == 0 && g.P == g.Lh; }
 
-// Words of one plane: L * ceil(L / 32) z words per row of Lh columns (L^3 / 64
+// Words of one plane: L * ceil(L / 32) z words per row of P columns, the byte
+// layout's row pitch (Lh rounded up to whole Philox blocks of four; L^3 / 64
 // when L is a multiple of 32).
-int64_t msg_plane_words(const Geometry &g) { return (int64_t)g.L * ((g.L + 31) / 32) * g.Lh; }
+int64_t msg_plane_words(const Geometry &g) { return (int64_t)g.L * ((g.L + 31) / 32) * g.P; }
 
 int msg_planes_per_replica(int gamma, int walkers) { return 2 + 4 * gamma * (walkers ? 2 : 1); }
 

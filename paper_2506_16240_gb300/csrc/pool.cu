@@ -223,7 +223,7 @@ __global__ void __launch_bounds__(kVBlock) pool_planes_convert_kernel(PoolTables
         const JobDesc &J = T.jobs[b.slot];
         if (!J.live || J.t >= J.n_sweeps) continue;
         const Geometry g = J.geo;
-        const int64_t WP = (int64_t)g.L * ((g.L + 31) / 32) * g.Lh;
+        const int64_t WP = (int64_t)g.L * ((g.L + 31) / 32) * g.P;
         const int64_t w0 = 4 * ((int64_t)b.chunk0 + threadIdx.x);
         if (w0 >= WP) continue;
         for (int r = 0; r < J.R; ++r)
@@ -260,8 +260,8 @@ __global__ void __launch_bounds__(kVBlock, 4) pool_msg_half_kernel(PoolTables T,
             active = J.live && t < J.n_sweeps;
             const Geometry g = J.geo;
             const int nzw = (g.L + 31) / 32;
-            lat = MsgLattice{J.planes, J.bplanes, g.L, g.Lh, nzw, g.Lh / 4, (int64_t)g.L * nzw * g.Lh,
-                             6, 1, 0, 0, J.key0, J.key1};
+            lat = MsgLattice{J.planes, J.bplanes, g.L, g.P, nzw, g.P / 4, (int64_t)g.L * nzw * g.P,
+                             6, 1, 0, 0, J.key0, J.key1, g.Lh};
             prm = SweepParam{};
             prm.t = t;
             prm.mode = kModeMicsa;
@@ -272,7 +272,7 @@ __global__ void __launch_bounds__(kVBlock, 4) pool_msg_half_kernel(PoolTables T,
                 prm.th2 = q[2];
                 prm.mode = kModeRefresh;
             }
-            dg = make_fastdiv_dev((uint32_t)(g.Lh / 4));
+            dg = make_fastdiv_dev((uint32_t)(g.P / 4));
             dL = make_fastdiv_dev((uint32_t)g.L);
             R = J.R;
         }
@@ -281,7 +281,7 @@ __global__ void __launch_bounds__(kVBlock, 4) pool_msg_half_kernel(PoolTables T,
         if ((int64_t)q * 4 >= lat.WP) continue;  // (job thread counts are multiples of 128)
         const uint32_t rowi = fdiv(q, dg);
         const uint32_t zw = fdiv(rowi, dL);
-        msg_update<4, true>(lat, prm, p, (int)zw, (int)(rowi - zw * dL.d), (int)(q - rowi * dg.d), 0, R);
+        msg_update<4, true, false, true, true>(lat, prm, p, (int)zw, (int)(rowi - zw * dL.d), (int)(q - rowi * dg.d), 0, R);
     }
 }
 
@@ -312,7 +312,7 @@ __global__ void __launch_bounds__(NT, MINB)
         if (!J.live || J.t >= J.n_sweeps) continue;
         const Geometry g = J.geo;
         const int nzw = (g.L + 31) / 32;
-        const int64_t WP = (int64_t)g.L * nzw * g.Lh;
+        const int64_t WP = (int64_t)g.L * nzw * g.P;  // rows of P words (padded to whole Philox blocks)
         const int nrep = U.nrep;
         int8_t *spins = J.spins + (int64_t)U.r0 * 2 * g.half;
         uint8_t *daemons = J.daemons + (int64_t)U.r0 * 2 * g.half;
@@ -329,9 +329,9 @@ __global__ void __launch_bounds__(NT, MINB)
             for (int64_t i = threadIdx.x; i < 3 * WP; i += blockDim.x) dst[i] = src[i];  // 12 WP words
         }
         __syncthreads();
-        const MsgLattice lat{spl, U.bonds_smem ? sb : J.bplanes, g.L, g.Lh, nzw, g.Lh / 4, WP, 6, 1, 0,
-                             (int64_t)U.r0, J.key0, J.key1};
-        const int groups = (int)(WP / 4), W4 = g.Lh / 4;
+        const MsgLattice lat{spl, U.bonds_smem ? sb : J.bplanes, g.L, g.P, nzw, g.P / 4, WP, 6, 1, 0,
+                             (int64_t)U.r0, J.key0, J.key1, g.Lh};
+        const int groups = (int)(WP / 4), W4 = g.P / 4;
         for (int k = 0; k < K; ++k) {
             const int64_t t = J.t + k;
             if (t >= J.n_sweeps) break;
@@ -349,7 +349,7 @@ __global__ void __launch_bounds__(NT, MINB)
                 for (int q = threadIdx.x; q < groups; q += blockDim.x) {
                     const int rowi = q / W4;
                     const int zw = rowi / g.L;
-                    msg_update<4, true, false, false>(lat, prm, par, zw, rowi - zw * g.L, q - rowi * W4, 0, nrep);
+                    msg_update<4, true, false, false, true>(lat, prm, par, zw, rowi - zw * g.L, q - rowi * W4, 0, nrep);
                 }
                 __syncthreads();
             }
@@ -645,10 +645,11 @@ struct JobSizes {
     int64_t n_refresh;
 };
 
-// Jobs the bit-plane path can take: L a multiple of 8 (rows of Lh sites in
-// groups of 4 words; z columns in 32-bit words, the last one partial when L is
-// not a multiple of 32) and above the shared-memory kernel's sizes.
-bool plane_eligible(const micsa_job_desc &d) { return d.L % 8 == 0 && d.L >= 40; }
+// Jobs the bit-plane path can take: every even L above the shared-memory
+// multispin kernel's sizes (L > 32): rows of P = 4 ceil(Lh / 4) plane words (whole
+// Philox blocks; the words from Lh on are padding), z columns in 32-bit words,
+// the last one partial when L is not a multiple of 32.
+bool plane_eligible(const micsa_job_desc &d) { return d.L % 2 == 0 && d.L > 32; }
 
 // Units of a bit-plane job in the shared-memory kernel for a per-CTA budget of
 // `smem` bytes: all replicas with the bond planes when they fit, else as many

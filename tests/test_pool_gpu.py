@@ -306,12 +306,15 @@ def test_pool_autotuner_choice_is_valid_and_exact():
         np.testing.assert_array_equal(res[idx]["energy"], ref[idx]["energy"], err_msg=str(jobs[idx]))
 
 
-# L a multiple of 8, at least 40: the pool's bit-plane path (on by default); z
-# columns of L = 40, 48, 56, 72, 88 end in a partial word
+# every even L > 32 takes the pool's bit-plane path (on by default); z columns
+# of L = 34..62 (except 64), 72, 88, 94 end in a partial word
 JOBS_PLANES = [  # (L, R, seed, n_sweeps, interval, T_start, T_end)
     (64, 2, 31, 23, 5, 2.5, 0.5), (96, 1, 32, 9, 3, 2.0, 1.0), (64, 3, 33, 17, 7, 3.0, 0.3), (128, 1, 34, 6, 2, 1.5, 1.5),
     (40, 2, 36, 11, 4, 2.5, 0.5), (48, 1, 37, 13, 5, 2.0, 0.8), (56, 2, 38, 9, 3, 3.0, 0.3), (72, 1, 39, 7, 2, 1.5, 1.5),
     (88, 1, 40, 5, 5, 2.0, 1.0),
+    # L not a multiple of 8: plane rows padded to whole Philox blocks (P = 4 ceil(L/8) words)
+    (34, 2, 41, 9, 3, 2.5, 0.5), (36, 1, 42, 7, 2, 2.0, 1.0), (38, 3, 43, 6, 4, 3.0, 0.3), (42, 2, 44, 8, 5, 2.0, 0.8),
+    (46, 1, 45, 5, 1, 1.5, 1.5), (50, 2, 46, 6, 3, 2.5, 0.5), (62, 1, 47, 7, 7, 2.0, 1.0), (94, 1, 48, 4, 2, 2.0, 1.0),
 ]
 
 
