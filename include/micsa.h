@@ -384,10 +384,11 @@ int micsa_pool_set_launch_config(micsa_pool_t p, int blocks_per_sm, int pdl, int
  * MICSA_E_INVALID_ARG otherwise. Synchronizes. */
 int micsa_pool_set_shape(micsa_pool_t p, int max_words, int chains);
 
-/* Bit-plane path for the jobs admitted from now on whose L is a multiple of 8
- * and at least 40 (on by default): during a tick such a job's state is held as
- * bit planes (32 sites of a z column per word, the last word of a column partial
- * when L is not a multiple of 32; multispin coding, App. B) and swept by the
+/* Bit-plane path for the jobs admitted from now on with L above 32 (on by
+ * default): during a tick such a job's state is held as bit planes (32 sites of
+ * a z column per word, the last word of a column partial when L is not a
+ * multiple of 32; rows of 4 ceil(L/8) words, padded to whole Philox blocks;
+ * multispin coding, App. B) and swept by the
  * bit-plane update, converted from and back to the byte layout at the tick's
  * ends; these jobs run as the same number of concurrent chains as the
  * byte-streamed ones. Results are identical either way (the same Philox

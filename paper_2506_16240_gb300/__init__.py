@@ -468,6 +468,6 @@ class Pool:
         return b.value, m.value, n.value
 
     def set_planes(self, on=True):
-        """Bit-plane half-sweeps for the jobs admitted from now on with L a
-        multiple of 8 (at least 40); results do not depend on it."""
+        """Bit-plane half-sweeps for the jobs admitted from now on with L above
+        32; results do not depend on it."""
         self._check(lib().micsa_pool_set_planes(self.h, int(bool(on))))

@@ -210,8 +210,8 @@ __device__ __forceinline__ void msg_convert_word(uint32_t *planes, int8_t *spins
 // daemons are drawn first (Sec. 2.7), with walkers the previous wandering step
 // is applied on read (Sec. 2.6). Lanes (threadIdx.x & (4 / NW - 1)) share one
 // Philox block, so the threads of a warp must all be active. RAGGED: the last
-// word of a z column holds Lz = L - 32 (nzw - 1) sites (L a multiple of 8, any
-// L >= 32; no walkers): the z wrap goes through bit Lz - 1 of that word, and its
+// word of a z column holds Lz = L - 32 (nzw - 1) sites (any even L > 32; no
+// walkers): the z wrap goes through bit Lz - 1 of that word, and its
 // bits from Lz up stay zero. METRO: the Metropolis sweep on the same planes
 // (the daemon planes are neither read nor written). PREFETCH: the next
 // replica's words are prefetched into L2 (planes in global memory only; a

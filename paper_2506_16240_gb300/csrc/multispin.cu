@@ -409,8 +409,9 @@ int multispin_blocks_per_sm(bool pool, size_t smem) {
 // b, the site x = 2i + ((p + y + z) & 1), y, z = 32 zw + b of parity p (the
 // site the byte layout keeps at row (z, y), byte i). Word index within a
 // parity plane: (zw * L + y) * Lh + i, WP = L^3 / 64 words per parity (the
-// pool's bit-plane jobs, any L that is a multiple of 8, use the same layout
-// with ceil(L / 32) z words, the last one partial, and rows of P = Lh words). Per
+// pool's bit-plane jobs, any even L > 32, use the same layout with ceil(L / 32)
+// z words, the last one partial, and rows of P = 4 ceil(Lh / 4) words, the words
+// from Lh on padding). Per
 // replica the planes are [spin | m0 | m1][parity][WP]; per sample the bond
 // planes are [6][parity][WP] (bit set <=> J = -1, order +x +y +z -x -y -z).
 //

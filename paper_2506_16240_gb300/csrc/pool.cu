@@ -546,7 +546,7 @@ struct micsa_pool {
     int *d_counter = nullptr;
     int max_units = 0;
     bool has_stream_jobs = false, has_resident_jobs = false, has_plane_jobs = false;
-    // bit-plane jobs (L a multiple of 8, at least 40): forked branches of the tick
+    // bit-plane jobs (even L above 32): forked branches of the tick
     bool planes_on = true;  // for the jobs admitted from now on
     PVBlock *d_pvblocks = nullptr, *h_pvblocks = nullptr;
     int32_t *d_npvb = nullptr, *h_npvb = nullptr;

@@ -62,7 +62,7 @@ def test_bad_temperatures_rejected(lib):
 def test_pool_job_bytes_counts_plane_storage_for_plane_jobs(lib):
     """Host-only: a job's arena bytes are its bonds, spins, daemons, best
     configuration and refresh cut points, plus bit-plane storage exactly for the
-    jobs the pool sweeps as bit planes (L a multiple of 8, at least 40)."""
+    jobs the pool sweeps as bit planes (even L above 32)."""
     def align(n):
         return (n + 255) // 256 * 256
 
@@ -73,8 +73,8 @@ def test_pool_job_bytes_counts_plane_storage_for_plane_jobs(lib):
             half = L * L * P
             n_refresh = max(1, (n + r - 1) // r)
             expect = align(2 * half) + 2 * align(R * 2 * half) + align(R * max(L ** 3, 2 * half)) + align(24 * n_refresh)
-            if L % 8 == 0 and L >= 40:
-                WP = L * ((L + 31) // 32) * Lh
+            if L % 2 == 0 and L > 32:  # rows of P plane words
+                WP = L * ((L + 31) // 32) * P
                 expect += align(4 * 6 * WP * R) + align(4 * 12 * WP)
             assert micsa.Pool.job_bytes(L, R, n, r) == expect, (L, R, n, r)
 
