@@ -81,7 +81,8 @@ def parse(argv=None):
     ap.add_argument("--no-extras", action="store_true", help="headline leg only")
     ap.add_argument("--profile-case", choices=["stream", "chains", "single", "chains_l320", "chains_l400",
                                                "multispin", "planes", "planes_metro", "onchip", "tma", "pool",
-                                               "batched", "plane_jobs_smem", "plane_jobs_global"],
+                                               "batched", "plane_jobs_smem", "plane_jobs_global",
+                                               "plane_jobs_smem_norefresh"],
                     help="run one small fixed workload for a profiler capture and exit")
     ap.add_argument("--source-digests", action="store_true",
                     help="print the digests of the kernel sources that profiles/traffic.md rows carry")
@@ -744,6 +745,7 @@ def leg_serving(micsa, torch, stream, n_jobs, peaks, n_cap=600, slots=256, K=128
 #   batched       the 256 batched lattices in one pool, 2 ticks of 32 sweeps
 #   plane_jobs_smem, plane_jobs_global  16 bit-plane jobs (L = 64 and 48), one tick of
 #                 64 sweeps, in shared memory or on the global bit planes
+#   plane_jobs_smem_norefresh  the same in shared memory with one refresh (t = 0)
 def _micsa():
     import paper_2506_16240_gb300
     return paper_2506_16240_gb300
@@ -817,10 +819,12 @@ def case_pool():
 
 
 def case_batched(K=32, ticks=2):
-    """The 256 batched lattices in one pool (default shape), ticks of K sweeps."""
+    """The 256 batched lattices in one pool (default shape, the bit-plane jobs in
+    shared memory in units of one replica: a 100 KB budget), ticks of K sweeps."""
     rng = np.random.default_rng(4)
     inst = zip(rng.choice([16, 24, 32, 48, 64], 256), rng.integers(5, 21, 256), rng.integers(1, 2 ** 62, 256))
     with _micsa().Pool(8 << 30, 512, K) as p:
+        p.set_smem_planes(100 << 10, 1)
         ids = [p.submit(int(L), 2, int(s), 20_000, int(r), 2.5, 0.5) for L, r, s in inst]
         for _ in range(ticks):
             p.tick()
@@ -828,14 +832,14 @@ def case_batched(K=32, ticks=2):
         return len(ids), p.stats()["launches"]
 
 
-def case_plane_jobs(smem=True, K=64):
-    """16 bit-plane jobs (8 of L = 64, 8 of L = 48, 2 replicas, refresh every 10) in
-    one pool, one tick of K sweeps: the shared-memory kernel (smem) or the
-    per-half-sweep launches over the global bit planes."""
+def case_plane_jobs(smem=True, K=64, interval=10):
+    """16 bit-plane jobs (8 of L = 64, 8 of L = 48, 2 replicas, refresh every
+    `interval` sweeps) in one pool, one tick of K sweeps: the shared-memory kernel
+    (smem, units of one replica) or the per-half-sweep launches over the global
+    bit planes."""
     with _micsa().Pool(1 << 30, 64, K) as p:
-        if not smem:
-            p.set_smem_planes(0, 1)
-        ids = [p.submit(L, 2, 100 + j, 10 * K, 10, 2.5, 0.5) for j, L in enumerate([64] * 8 + [48] * 8)]
+        p.set_smem_planes((100 << 10) if smem else 0, 1)
+        ids = [p.submit(L, 2, 100 + j, 10 * K, interval, 2.5, 0.5) for j, L in enumerate([64] * 8 + [48] * 8)]
         p.tick()
         p.wait()
         return len(ids), p.stats()["launches"]
@@ -845,6 +849,7 @@ PROFILE_CASES = {"stream": case_stream, "chains": case_chains, "multispin": case
                  "single": lambda: case_chains(160, 1), "chains_l320": lambda: case_chains(320),
                  "chains_l400": lambda: case_chains(400), "batched": case_batched,
                  "plane_jobs_smem": case_plane_jobs, "plane_jobs_global": lambda: case_plane_jobs(False),
+                 "plane_jobs_smem_norefresh": lambda: case_plane_jobs(True, interval=1 << 20),
                  "planes": case_planes, "planes_metro": case_planes_metro, "onchip": case_onchip,
                  "tma": case_tma, "pool": case_pool}
 

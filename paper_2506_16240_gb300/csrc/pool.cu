@@ -285,6 +285,155 @@ __global__ void __launch_bounds__(kVBlock, 4) pool_msg_half_kernel(PoolTables T,
     }
 }
 
+// ------------------------------------------ bit-plane jobs in shared memory --
+// Dynamic shared memory of pool_smem_planes_kernel: the unit's planes
+// [replica][spin p0, p1, m0 p0, p1, m1 p0, p1][WP], then (when held here) the
+// bond planes [direction][parity][WP].
+extern __shared__ __align__(16) uint32_t pool_spl[];
+
+// One unit's geometry as the shared-memory update sees it: rows of P plane words
+// (Lr of them sites), nzw z words per column (Lz sites in the last), W4 = P / 4
+// Philox blocks per row.
+struct SplaneGeo {
+    int L, P, Lr, nzw, W4, Lz;
+    uint32_t WP;
+    FastDiv dW4, dL;
+    uint32_t bonds_off;  // word offset of the bond planes in shared memory
+};
+
+__device__ __forceinline__ void lds4(uint32_t idx, uint32_t (&v)[4]) {
+    const uint4 a = *reinterpret_cast<const uint4 *>(&pool_spl[idx]);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = a.z;
+    v[3] = a.w;
+}
+
+__device__ __forceinline__ void sts4(uint32_t idx, const uint32_t (&v)[4]) {
+    *reinterpret_cast<uint4 *>(&pool_spl[idx]) = make_uint4(v[0], v[1], v[2], v[3]);
+}
+
+// Half-sweep (parity p) of word group q (the plane words i0 .. i0 + 3 of one
+// (zw, y) row, i0 = 4 (q mod W4)) for replicas [0, nrep) of the unit held in
+// shared memory: the same move as the global bit-plane update (Eq. (Creutz)
+// with Eq. (flip-OK), bit-sliced; at a refresh sweep the daemons of the words
+// are drawn first from the same Philox blocks, Sec. 2.7), with 32-bit shared
+// memory indices. BSMEM: the bond planes are in shared memory, else at gb.
+template <bool BSMEM>
+__device__ __forceinline__ void splane_group(const SplaneGeo &G, const uint32_t *gb, int p, uint32_t q, int nrep,
+                                             int64_t t, bool refresh, const CutsGt &cut, const RoundKeys &rk,
+                                             uint32_t gid0) {
+    const uint32_t rowi = fdiv(q, G.dW4);
+    const uint32_t zw = fdiv(rowi, G.dL);
+    const int L = G.L;
+    const int y = (int)(rowi - zw * (uint32_t)L);
+    const int i0 = 4 * (int)(q - rowi * (uint32_t)G.W4);
+    const int o = 1 - p;
+    const int yp = (y + 1 == L) ? 0 : y + 1, ym = (y == 0) ? L - 1 : y - 1;
+    const uint32_t zwp = (zw + 1 == (uint32_t)G.nzw) ? 0u : zw + 1, zwm = (zw == 0) ? (uint32_t)G.nzw - 1 : zw - 1;
+    const int ip = (i0 + 4 >= G.Lr) ? 0 : i0 + 4, im = (i0 == 0) ? G.Lr - 1 : i0 - 1;
+    const uint32_t P = (uint32_t)G.P, row = zw * (uint32_t)L;
+    const uint32_t wc = (row + y) * P + i0;
+    const uint32_t w_yp = (row + yp) * P + i0, w_ym = (row + ym) * P + i0;
+    const uint32_t w_zp = (zwp * L + y) * P + i0, w_zm = (zwm * L + y) * P + i0;
+    const uint32_t w_ip = (row + y) * P + ip, w_im = (row + y) * P + im;
+    const uint32_t M = ((p + y) & 1) ? 0x55555555u : 0xAAAAAAAAu;  // bits whose site has x offset 1
+    const bool zlast = zw + 1 == (uint32_t)G.nzw, zfirst = zw == 0;
+    const int Lz = G.Lz;
+    const uint32_t zmask = (zlast && Lz < 32) ? ((1u << Lz) - 1u) : 0xFFFFFFFFu;
+    uint32_t wmask[4];  // words from Lr on are padding: no site
+#pragma unroll
+    for (int w = 0; w < 4; ++w) wmask[w] = i0 + w < G.Lr ? zmask : 0u;
+
+    uint32_t B[6][4];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const uint32_t bi = (uint32_t)(k * 2 + p) * G.WP + wc;
+        if constexpr (BSMEM) {
+            lds4(G.bonds_off + bi, B[k]);
+        } else {
+            const uint4 a = __ldg(reinterpret_cast<const uint4 *>(gb + bi));
+            B[k][0] = a.x;
+            B[k][1] = a.y;
+            B[k][2] = a.z;
+            B[k][3] = a.w;
+        }
+    }
+    const uint32_t quad0 = (((uint32_t)p * L + 32 * zw) * L + y) * (uint32_t)G.W4 + (uint32_t)(i0 >> 2);
+    for (int r = 0; r < nrep; ++r) {
+        const uint32_t base = (uint32_t)r * 6 * G.WP;
+        const uint32_t Ob = base + (uint32_t)o * G.WP, Sb = base + (uint32_t)p * G.WP;
+        const uint32_t M0b = base + (uint32_t)(2 + p) * G.WP, M1b = base + (uint32_t)(4 + p) * G.WP;
+        uint32_t Oc[4], Oyp[4], Oym[4], Ozp[4], Ozm[4], Sg[4], m0v[4], m1v[4];
+        lds4(Ob + wc, Oc);
+        lds4(Ob + w_yp, Oyp);
+        lds4(Ob + w_ym, Oym);
+        lds4(Ob + w_zp, Ozp);
+        lds4(Ob + w_zm, Ozm);
+        const uint32_t Oip = pool_spl[Ob + w_ip], Oim = pool_spl[Ob + w_im];
+        lds4(Sb + wc, Sg);
+        if (refresh) {
+            // fresh daemons of parity p (Sec. 2.7): the Philox block of z = 32 zw + b
+            // holds the uniforms of the four words; bits enter from the top z down
+            uint32_t x0[4] = {0, 0, 0, 0}, x1[4] = {0, 0, 0, 0}, x2[4] = {0, 0, 0, 0};
+            const uint32_t n0 = ~cut.c0m, n1 = ~cut.c1m, n2 = ~cut.c2m;
+            const uint32_t fam = gid0 + (uint32_t)r;
+#pragma unroll 2
+            for (int b = 31; b >= 0; --b) {
+                const uint4 u = philox_wide(make_uint4(quad0 + (uint32_t)b * (uint32_t)L * (uint32_t)G.W4, (uint32_t)t,
+                                                       (fam << 2) | kTagDaemon, (uint32_t)((uint64_t)t >> 32)),
+                                            rk);
+                shift_in_cuts(u.x, n0, n1, n2, x0[0], x1[0], x2[0]);
+                shift_in_cuts(u.y, n0, n1, n2, x0[1], x1[1], x2[1]);
+                shift_in_cuts(u.z, n0, n1, n2, x0[2], x1[2], x2[2]);
+                shift_in_cuts(u.w, n0, n1, n2, x0[3], x1[3], x2[3]);
+            }
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {  // m = [u >= c0] + [u >= c1] + [u >= c2]: m1 = x1, m0 = the parity
+                m0v[w] = (x0[w] ^ x1[w] ^ x2[w]) & wmask[w];
+                m1v[w] = x1[w] & wmask[w];
+            }
+        } else {
+            lds4(M0b + wc, m0v);
+            lds4(M1b + wc, m1v);
+        }
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const uint32_t oc = Oc[w];
+            const uint32_t o_next = (w + 1 < 4 && i0 + w + 1 < G.Lr) ? Oc[w + 1 < 4 ? w + 1 : 0] : Oip;
+            const uint32_t o_prev = w > 0 ? Oc[w > 0 ? w - 1 : 0] : Oim;
+            const uint32_t nxp = (oc & ~M) | (o_next & M);
+            const uint32_t nxm = (o_prev & ~M) | (oc & M);
+            const uint32_t nzp = zlast ? (oc >> 1) | ((Ozp[w] & 1u) << (Lz - 1)) : __funnelshift_r(oc, Ozp[w], 1);
+            const uint32_t nzm = zfirst ? (oc << 1) | ((Ozm[w] >> (Lz - 1)) & 1u) : __funnelshift_l(Ozm[w], oc, 1);
+            const uint32_t sg = Sg[w];
+            // unsatisfied bond indicators (J s s_nb = -1), their count u, v = u + m
+            const uint32_t q0 = sg ^ nxp ^ B[0][w];
+            const uint32_t q1 = sg ^ Oyp[w] ^ B[1][w];
+            const uint32_t q2 = sg ^ nzp ^ B[2][w];
+            const uint32_t q3 = sg ^ nxm ^ B[3][w];
+            const uint32_t q4 = sg ^ Oym[w] ^ B[4][w];
+            const uint32_t q5 = sg ^ nzm ^ B[5][w];
+            const uint32_t s1 = q0 ^ q1 ^ q2, c1 = (q0 & q1) | (q2 & (q0 ^ q1));
+            const uint32_t s2 = q3 ^ q4 ^ q5, c2 = (q3 & q4) | (q5 & (q3 ^ q4));
+            const uint32_t u0 = s1 ^ s2, kk = s1 & s2;
+            const uint32_t u1 = c1 ^ c2 ^ kk, u2 = (c1 & c2) | (kk & (c1 ^ c2));
+            const uint32_t m0 = m0v[w], m1 = m1v[w];
+            const uint32_t v0 = u0 ^ m0, k0 = u0 & m0;
+            const uint32_t v1 = u1 ^ m1 ^ k0, k1 = (u1 & m1) | (k0 & (u1 ^ m1));
+            const uint32_t v2 = u2 ^ k1, v3 = u2 & k1;
+            // Eq. (Creutz) with Eq. (flip-OK): accept <=> 3 <= u + m <= 6, m' = u + m - 3
+            const uint32_t acc = (v2 ^ (v1 & v0)) & ~v3 & wmask[w];
+            m0v[w] = (m0 & ~acc) | (~v0 & acc);
+            m1v[w] = (m1 & ~acc) | (v2 & (v1 | v0) & acc);
+            Sg[w] = sg ^ acc;
+        }
+        sts4(Sb + wc, Sg);
+        sts4(M0b + wc, m0v);
+        sts4(M1b + wc, m1v);
+    }
+}
+
 // The tick of the bit-plane jobs whose state fits in shared memory: a
 // persistent kernel whose CTAs take units (a job's replica range) from a work
 // counter, convert the replicas' bytes to bit planes in shared memory (the
@@ -298,7 +447,7 @@ __global__ void __launch_bounds__(NT, MINB)
     pool_smem_planes_kernel(PoolTables T, const PlaneUnit *units, const int32_t *n_units, int *counter, int K) {
     pool_wait();
     pool_release();
-    extern __shared__ __align__(16) uint32_t spl[];
+    uint32_t *spl = pool_spl;
     __shared__ int s_unit;
     const int n = *n_units;
     for (;;) {
@@ -329,28 +478,40 @@ __global__ void __launch_bounds__(NT, MINB)
             for (int64_t i = threadIdx.x; i < 3 * WP; i += blockDim.x) dst[i] = src[i];  // 12 WP words
         }
         __syncthreads();
-        const MsgLattice lat{spl, U.bonds_smem ? sb : J.bplanes, g.L, g.P, nzw, g.P / 4, WP, 6, 1, 0,
-                             (int64_t)U.r0, J.key0, J.key1, g.Lh};
-        const int groups = (int)(WP / 4), W4 = g.P / 4;
+        SplaneGeo G;
+        G.L = g.L;
+        G.P = g.P;
+        G.Lr = g.Lh;
+        G.nzw = nzw;
+        G.W4 = g.P / 4;
+        G.Lz = g.L - 32 * (nzw - 1);
+        G.WP = (uint32_t)WP;
+        G.dW4 = make_fastdiv_dev((uint32_t)G.W4);
+        G.dL = make_fastdiv_dev((uint32_t)g.L);
+        G.bonds_off = (uint32_t)(nrep * 6 * WP);
+        const RoundKeys rk = round_keys(J.key0, J.key1);
+        const uint32_t groups = (uint32_t)(WP / 4);
+        // a thread's word groups: ceil(groups / threads) each, spread over as many
+        // threads as that needs, so that no pass runs with a few threads only
+        const uint32_t per = (groups + blockDim.x - 1) / blockDim.x;
+        const uint32_t span = (groups + per - 1) / per;  // threads in use
         for (int k = 0; k < K; ++k) {
             const int64_t t = J.t + k;
             if (t >= J.n_sweeps) break;
-            SweepParam prm{};
-            prm.t = t;
-            prm.mode = kModeMicsa;
-            if (t % J.interval == 0) {
-                const uint64_t *q = J.thr + 3 * (t / J.interval);
-                prm.th0 = q[0];
-                prm.th1 = q[1];
-                prm.th2 = q[2];
-                prm.mode = kModeRefresh;
+            const bool refresh = t % J.interval == 0;
+            CutsGt cut{0, 0, 0};
+            if (refresh) {
+                const uint64_t *th = J.thr + 3 * (t / J.interval);
+                cut = make_cuts_gt(th[0], th[1], th[2]);
             }
             for (int par = 0; par < 2; ++par) {
-                for (int q = threadIdx.x; q < groups; q += blockDim.x) {
-                    const int rowi = q / W4;
-                    const int zw = rowi / g.L;
-                    msg_update<4, true, false, false, true>(lat, prm, par, zw, rowi - zw * g.L, q - rowi * W4, 0, nrep);
-                }
+                if (threadIdx.x < span)
+                    for (uint32_t q = threadIdx.x; q < groups; q += span) {
+                        if (U.bonds_smem)
+                            splane_group<true>(G, nullptr, par, q, nrep, t, refresh, cut, rk, (uint32_t)U.r0);
+                        else
+                            splane_group<false>(G, J.bplanes, par, q, nrep, t, refresh, cut, rk, (uint32_t)U.r0);
+                    }
                 __syncthreads();
             }
         }
