@@ -84,6 +84,8 @@ def parse(argv=None):
                                                "batched", "plane_jobs_smem", "plane_jobs_global",
                                                "plane_jobs_smem_norefresh"],
                     help="run one small fixed workload for a profiler capture and exit")
+    ap.add_argument("--pool-breakdown", action="store_true",
+                    help="print tick times of the batched pool by content and shared-memory setting, and exit")
     ap.add_argument("--source-digests", action="store_true",
                     help="print the digests of the kernel sources that profiles/traffic.md rows carry")
     ap.add_argument("--serving-jobs", type=int, default=2000, help="jobs in the serving stream")
@@ -845,6 +847,38 @@ def case_plane_jobs(smem=True, K=64, interval=10):
         return len(ids), p.stats()["launches"]
 
 
+def pool_breakdown(ticks=6, K=256):
+    """Tick times of the batched workload's pool by content and shared-memory
+    bit-plane setting (wall clock over `ticks` ticks after two untimed ones); one
+    JSON line per row."""
+    import time as _t
+    micsa = _micsa()
+    rng = np.random.default_rng(4)
+    inst = [(int(L), int(r), int(s)) for L, r, s in
+            zip(rng.choice([16, 24, 32, 48, 64], 256), rng.integers(5, 21, 256), rng.integers(1, 2 ** 62, 256))]
+    rows = [("all", lambda L: True, (0, 1)), ("all", lambda L: True, (100 << 10, 1)),
+            ("L >= 48", lambda L: L >= 48, (0, 1)), ("L >= 48", lambda L: L >= 48, (100 << 10, 1)),
+            ("L >= 48", lambda L: L >= 48, None), ("L <= 32", lambda L: L <= 32, (0, 1))]
+    for label, sel, smem in rows:
+        with micsa.Pool(8 << 30, 512, K) as p:
+            if smem is not None:
+                p.set_smem_planes(*smem)
+            for L, r, s in inst:
+                if sel(L):
+                    p.submit(L, 2, s, 10 ** 6, r, 2.5, 0.5)
+            p.tick()
+            p.tick()
+            p.wait()
+            t0 = _t.perf_counter()
+            for _ in range(ticks):
+                p.tick()
+            p.wait()
+            dt = (_t.perf_counter() - t0) / ticks
+            upd = sum(L ** 3 * 2 for L, _, _ in inst if sel(L)) * K
+            print(json.dumps({"jobs": label, "smem_planes": list(smem) if smem else "default (whole budget)",
+                              "ms_per_tick": 1e3 * dt, "flips_per_ns": upd / (dt * 1e9)}))
+
+
 PROFILE_CASES = {"stream": case_stream, "chains": case_chains, "multispin": case_multispin,
                  "single": lambda: case_chains(160, 1), "chains_l320": lambda: case_chains(320),
                  "chains_l400": lambda: case_chains(400), "batched": case_batched,
@@ -860,6 +894,9 @@ def main(argv=None):
         return run_reference(args)
     if args.profile_case:
         print(args.profile_case, PROFILE_CASES[args.profile_case]())
+        return 0
+    if args.pool_breakdown:
+        pool_breakdown()
         return 0
     if args.source_digests:
         print(json.dumps({k: kernel_digest(k) for k in KERNEL_SOURCES}))
