@@ -156,7 +156,10 @@ int micsa_device_bytes(micsa_t h, size_t *bytes);
  * streaming kernel: 64 per thread, blocks of at most 128 threads, 8 per SM;
  * the bit-plane kernel: 102, 5 blocks of 128 per SM) and/or MICSA_LAUNCH_PAIRS
  * for the streaming variant in which one thread updates two neighbouring rows
- * (rows without padding, MicSA; sharing their opposite-parity rows), block 32..256 in
+ * (rows without padding, MicSA; sharing their opposite-parity rows), or
+ * MICSA_LAUNCH_REPS for the streaming variant in which one thread updates its
+ * words for every replica of its sample (rows without padding, MicSA; the bond
+ * words and the neighbour offsets shared by the replicas), block 32..256 in
  * steps of 32, blocks_per_sm -1 (grid-stride loop over the resident capacity),
  * 0 (one thread per chunk) or a positive cap, pdl != 0 chains consecutive
  * half-sweeps with programmatic dependent launch, graph_sweeps > 0 replays a
@@ -164,6 +167,7 @@ int micsa_device_bytes(micsa_t h, size_t *bytes);
  * the handle's stream. */
 #define MICSA_LAUNCH_REGCAP 256
 #define MICSA_LAUNCH_PAIRS 512
+#define MICSA_LAUNCH_REPS 1024
 int micsa_set_launch_config(micsa_t h, int words_per_thread, int block, int blocks_per_sm, int pdl,
                             int graph_sweeps);
 

@@ -33,7 +33,7 @@ ENGINES = {"auto": MICSA_ENGINE_AUTO, "stream": MICSA_ENGINE_STREAM, "resident":
            "multispin": MICSA_ENGINE_MULTISPIN, "multispin_global": MICSA_ENGINE_MULTISPIN_GLOBAL,
            "onchip": MICSA_ENGINE_ONCHIP, "tma": MICSA_ENGINE_TMA}
 MICSA_NOALLOC_MAX_TERMS = 8192
-MICSA_LAUNCH_REGCAP, MICSA_LAUNCH_PAIRS = 256, 512
+MICSA_LAUNCH_REGCAP, MICSA_LAUNCH_PAIRS, MICSA_LAUNCH_REPS = 256, 512, 1024
 
 _ERRNAMES = {-1: "MICSA_E_INVALID_ARG", -2: "MICSA_E_OOM", -3: "MICSA_E_CUDA",
              -4: "MICSA_E_TIMEOUT", -5: "MICSA_E_BUSY", -6: "MICSA_E_NOT_FOUND",

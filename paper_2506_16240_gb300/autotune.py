@@ -58,6 +58,9 @@ def candidates(L, R=1):
         # two rows per thread (rows without padding)
         out += [{"engine": "stream", "words_per_thread": nw | 512, "block": blk, "blocks_per_sm": -1, "chains": 2}
                 for nw, blk in itertools.product([2, 4], [64, 128])]
+        # every replica of a chunk in one thread (rows without padding)
+        out += [{"engine": "stream", "words_per_thread": nw | 1024, "block": blk, "blocks_per_sm": bps}
+                for nw, blk, bps in itertools.product([2, 4], [64, 128, 256], [-1, 0])]
     out += [{"engine": "onchip", "words_per_thread": nw} for nw in (4, 1)]  # where the state fits on chip
     out += [{"engine": "tma", "chains": c} for c in (1, 2) if c <= R]  # where the row pitch allows TMA tiles
     if L <= 40:

@@ -184,9 +184,10 @@ LaunchConfig effective_config(micsa_t h, bool metro) {
     lc.nw = vector_words(h->geo, lc.nw);
     if (h->blocks_per_sm < 0) {
         const dim3 b = block_shape(h->R, lc.regcap && lc.block > 128 ? 128 : lc.block);
-        const int per_sm = lc.pairs && !metro && h->geo.P == h->geo.Lh
-                               ? max_resident_blocks_pairs(lc.nw, (int)(b.x * b.y))
-                               : max_resident_blocks(metro, lc.nw, (int)(b.x * b.y), lc.regcap);
+        const bool full = !metro && h->geo.P == h->geo.Lh;
+        const int per_sm = lc.pairs && full  ? max_resident_blocks_pairs(lc.nw, (int)(b.x * b.y))
+                           : lc.reps && full ? max_resident_blocks_reps(lc.nw, lc.block)
+                                             : max_resident_blocks(metro, lc.nw, (int)(b.x * b.y), lc.regcap);
         lc.max_blocks = per_sm > 0 ? per_sm * h->sm_count : 0;
     } else {
         lc.max_blocks = h->blocks_per_sm * h->sm_count;
@@ -853,7 +854,8 @@ int micsa_set_launch_config(micsa_t h, int words_per_thread, int block, int bloc
     if (!h) return MICSA_E_INVALID_ARG;
     const bool regcap = (words_per_thread & MICSA_LAUNCH_REGCAP) != 0;
     const bool pairs = (words_per_thread & MICSA_LAUNCH_PAIRS) != 0;
-    words_per_thread &= ~(MICSA_LAUNCH_REGCAP | MICSA_LAUNCH_PAIRS);
+    const bool reps = (words_per_thread & MICSA_LAUNCH_REPS) != 0;
+    words_per_thread &= ~(MICSA_LAUNCH_REGCAP | MICSA_LAUNCH_PAIRS | MICSA_LAUNCH_REPS);
     if ((words_per_thread != 1 && words_per_thread != 2 && words_per_thread != 4) ||
         block < 32 || block > 256 || block % 32 || blocks_per_sm < -1 || blocks_per_sm > 64 ||
         graph_sweeps < 0 || graph_sweeps > 4096)
@@ -864,6 +866,7 @@ int micsa_set_launch_config(micsa_t h, int words_per_thread, int block, int bloc
     h->lc.nw = words_per_thread;
     h->lc.regcap = regcap;
     h->lc.pairs = pairs;
+    h->lc.reps = reps && !pairs;
     h->lc.block = block;
     h->lc.pdl = pdl != 0;
     h->lc.graph_sweeps = graph_sweeps;
@@ -926,7 +929,8 @@ int micsa_get_launch_config(micsa_t h, int *words_per_thread, int *block, int *b
     if (!h) return MICSA_E_INVALID_ARG;
     const LaunchConfig lc = effective_config(h, false);
     if (words_per_thread)
-        *words_per_thread = lc.nw | (lc.regcap ? MICSA_LAUNCH_REGCAP : 0) | (lc.pairs ? MICSA_LAUNCH_PAIRS : 0);
+        *words_per_thread = lc.nw | (lc.regcap ? MICSA_LAUNCH_REGCAP : 0) | (lc.pairs ? MICSA_LAUNCH_PAIRS : 0) |
+                            (lc.reps ? MICSA_LAUNCH_REPS : 0);
     if (block) *block = lc.block;
     if (blocks_per_sm) *blocks_per_sm = h->blocks_per_sm;
     if (pdl) *pdl = lc.pdl;

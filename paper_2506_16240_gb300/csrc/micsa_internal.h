@@ -54,6 +54,7 @@ struct LaunchConfig {
     bool regcap = false;    // kernel variant with registers capped at 64 (blocks of <= 128)
     int chains = 1;         // replica groups captured as concurrent kernel chains in one graph
     bool pairs = false;     // one thread updates two rows (rows without padding, MicSA only)
+    bool reps = false;      // one thread updates its chunk for every replica (rows without padding, MicSA only)
 };
 
 // One job of the batched pool (device-resident descriptor).
@@ -214,6 +215,7 @@ cudaError_t launch_wander(uint8_t *daemons, Geometry g, int64_t n_rep, int gamma
 int vector_words(const Geometry &g, int want);
 int max_resident_blocks(bool metro, int nw, int block, bool regcap);
 int max_resident_blocks_pairs(int nw, int block);
+int max_resident_blocks_reps(int nw, int block);
 dim3 block_shape(int R, int block);
 
 // initialisation, layout conversion and measurement (init_measure.cu)

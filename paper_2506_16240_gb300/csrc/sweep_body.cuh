@@ -245,4 +245,56 @@ __device__ __forceinline__ void update_pair(const Geometry &g, int8_t *spins, ui
     store_words<NW>(own_d + r1 + b0, D1);
 }
 
+// The MicSA update of one chunk (NW words of row `row`, parity p) for the
+// replicas [0, nrep) of one sample in one thread, rows without padding: the
+// bond words, the row decode and the neighbour offsets are computed once and
+// shared by the replicas. spins / daemons point at replica 0's [2][half] block
+// (daemon family of the sweep already applied), rep_stride bytes between
+// consecutive replicas' blocks; fam0 is replica 0's Philox id, fam_step the
+// step between replicas' ids.
+template <int NW>
+__device__ __forceinline__ void update_reps(const Geometry &g, int8_t *spins, uint8_t *daemons, int64_t rep_stride,
+                                            int64_t drep_stride, const uint8_t *bonds, int p, int row, int c,
+                                            int nrep, uint32_t fam0, uint32_t fam_step, uint32_t key0,
+                                            uint32_t key1, int64_t t, bool refresh, uint64_t th0, uint64_t th1,
+                                            uint64_t th2, const FastDiv &divL) {
+    const int z = (int)fdiv((uint32_t)row, divL), y = row - z * g.L;
+    const int o = (p + y + z) & 1;
+    const int b0 = c * 4 * NW;
+    const int yp = (y + 1 == g.L) ? 0 : y + 1, ym = (y == 0) ? g.L - 1 : y - 1;
+    const int zp = (z + 1 == g.L) ? 0 : z + 1, zm = (z == 0) ? g.L - 1 : z - 1;
+    const uint32_t P = (uint32_t)g.P, uL = (uint32_t)g.L;
+    const uint32_t row0 = (uint32_t)row * P;
+    const uint32_t off_c = row0 + (uint32_t)b0;
+    const uint32_t off_yp = ((uint32_t)z * uL + (uint32_t)yp) * P + (uint32_t)b0;
+    const uint32_t off_ym = ((uint32_t)z * uL + (uint32_t)ym) * P + (uint32_t)b0;
+    const uint32_t off_zp = ((uint32_t)zp * uL + (uint32_t)y) * P + (uint32_t)b0;
+    const uint32_t off_zm = ((uint32_t)zm * uL + (uint32_t)y) * P + (uint32_t)b0;
+    // the edge byte of the x shift: before the range (offset 0) or after it (offset 1),
+    // the row's other end at its ends
+    const uint32_t eo = o == 0 ? (b0 == 0 ? row0 + (uint32_t)(g.Lh - 1) : off_c - 1)
+                               : (b0 + 4 * NW < g.Lh ? off_c + (uint32_t)(4 * NW) : row0);
+    uint32_t Bw[NW];
+    load_words_ro<NW>(bonds + (int64_t)p * g.half + off_c, Bw);
+    const uint32_t quad0 = (uint32_t)((((int64_t)p * g.L + z) * g.L + y) * g.W + c * NW);
+    for (int r = 0; r < nrep; ++r) {
+        const int8_t *__restrict__ opp = spins + r * rep_stride + (int64_t)(1 - p) * g.half;
+        int8_t *__restrict__ own_s = spins + r * rep_stride + (int64_t)p * g.half;
+        uint8_t *__restrict__ own_d = daemons + r * drep_stride + (int64_t)p * g.half;
+        uint32_t O[NW], Oyp[NW], Oym[NW], Ozp[NW], Ozm[NW], S[NW], D[NW];
+        load_words_ro<NW>(opp + off_c, O);
+        load_words_ro<NW>(opp + off_yp, Oyp);
+        load_words_ro<NW>(opp + off_ym, Oym);
+        load_words_ro<NW>(opp + off_zp, Ozp);
+        load_words_ro<NW>(opp + off_zm, Ozm);
+        load_words<NW>(own_s + off_c, S);
+        if (!refresh) load_words<NW>(own_d + off_c, D);
+        const uint32_t edge = (uint8_t)__ldg(opp + eo);
+        micsa_cells<NW>(g, S, D, Bw, O, Oyp, Oym, Ozp, Ozm, o, edge, quad0, fam0 + (uint32_t)r * fam_step, key0,
+                        key1, t, refresh, th0, th1, th2);
+        store_words<NW>(own_s + off_c, S);
+        store_words<NW>(own_d + off_c, D);
+    }
+}
+
 }  // namespace micsa

@@ -97,6 +97,32 @@ __global__ void __launch_bounds__(256) half_sweep_pair_kernel(SweepArgs a) {
             }
 }
 
+// All replicas of a sample in one thread (rows without padding, MicSA): thread
+// q of a sample takes chunk q of the half-lattice for the replicas [r0, r1),
+// loading the bond words and computing the row's offsets once for all of them.
+template <int NW>
+__global__ void __launch_bounds__(256) half_sweep_reps_kernel(SweepArgs a) {
+    const int64_t kidx = a.k + (a.cursor ? *a.cursor : 0);
+    const SweepParam prm = a.params[kidx];
+    grid_dependency_wait();
+    grid_launch_dependents();
+    const Geometry g = a.geo;
+    const uint32_t per_sample = (uint32_t)g.L * g.L * (g.W / NW);
+    const bool refresh = prm.mode == kModeRefresh;
+    const int nrep = a.r1 - a.r0;
+    for (int sample = blockIdx.y; sample < a.S; sample += gridDim.y)
+        for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < per_sample; q += gridDim.x * blockDim.x) {
+            const uint32_t row = fdiv(q, a.div_chunks);
+            const int c = (int)(q - row * a.div_chunks.d);
+            const int64_t gid0 = (int64_t)sample * a.R + a.r0;
+            const int64_t fam0 = gid0 * a.gamma + prm.alpha;  // daemon family of the sweep, replica r0
+            update_reps<NW>(g, a.spins + gid0 * 2 * g.half, a.daemons + fam0 * 2 * g.half, 2 * g.half,
+                            (int64_t)a.gamma * 2 * g.half, a.bonds + (int64_t)sample * 2 * g.half, a.parity,
+                            (int)row, c, nrep, (uint32_t)fam0, (uint32_t)a.gamma, a.key0, a.key1, prm.t, refresh,
+                            prm.th0, prm.th1, prm.th2, a.div_L);
+        }
+}
+
 // Wandering (Sec. 2.6): every site of parity p exchanges the walker of family
 // alpha with its neighbour along direction alpha mod 6 (+x, +y, +z, -x, -y, -z,
 // the table of Sec. 2.8). One thread per (replica family, site of parity p);
@@ -210,13 +236,43 @@ static cudaError_t launch_pairs(const SweepArgs &a0, const LaunchConfig &lc, cud
     return cudaLaunchKernelEx(&cfg, half_sweep_pair_kernel<NW>, a);
 }
 
+template <int NW>
+static cudaError_t launch_reps(const SweepArgs &a0, const LaunchConfig &lc, cudaStream_t st) {
+    SweepArgs a = a0;
+    const int chunks = a.geo.W / NW;
+    a.div_chunks = make_fastdiv((uint32_t)chunks);
+    a.div_L = make_fastdiv((uint32_t)a.geo.L);
+    const int64_t per_sample = (int64_t)a.geo.L * a.geo.L * chunks;
+    const int blk = lc.block;
+    int64_t gx = (per_sample + blk - 1) / blk;
+    int64_t gy = a.S < 65535 ? a.S : 65535;
+    if (lc.max_blocks > 0 && gx * gy > lc.max_blocks) gx = lc.max_blocks / gy > 0 ? lc.max_blocks / gy : 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)gx, (unsigned)gy);
+    cfg.blockDim = dim3((unsigned)blk);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = lc.pdl ? 1 : 0;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, half_sweep_reps_kernel<NW>, a);
+}
+
 // Row pairs apply to MicSA half-sweeps of rows without padding.
 bool pairs_apply(const Geometry &g, bool metro, const LaunchConfig &lc) {
     return lc.pairs && !metro && g.P == g.Lh && g.L % 2 == 0;
 }
 
+// Replicas in one thread apply to MicSA half-sweeps of rows without padding.
+bool reps_apply(const Geometry &g, bool metro, const LaunchConfig &lc) {
+    return lc.reps && !lc.pairs && !metro && g.P == g.Lh;
+}
+
 cudaError_t launch_half_sweep(const SweepArgs &a, bool metro, const LaunchConfig &lc, cudaStream_t st) {
     const int nw = vector_words(a.geo, lc.nw);
+    if (reps_apply(a.geo, metro, lc))
+        return nw == 4 ? launch_reps<4>(a, lc, st) : nw == 2 ? launch_reps<2>(a, lc, st) : launch_reps<1>(a, lc, st);
     if (pairs_apply(a.geo, metro, lc))
         return nw == 4 ? launch_pairs<4>(a, lc, st) : nw == 2 ? launch_pairs<2>(a, lc, st) : launch_pairs<1>(a, lc, st);
     if (metro) {
@@ -256,6 +312,15 @@ int max_resident_blocks_pairs(int nw, int block) {
         nw == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, half_sweep_pair_kernel<4>, block, 0)
         : nw == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, half_sweep_pair_kernel<2>, block, 0)
                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, half_sweep_pair_kernel<1>, block, 0);
+    return e == cudaSuccess ? n : 0;
+}
+
+int max_resident_blocks_reps(int nw, int block) {
+    int n = 0;
+    const cudaError_t e =
+        nw == 4 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, half_sweep_reps_kernel<4>, block, 0)
+        : nw == 2 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, half_sweep_reps_kernel<2>, block, 0)
+                  : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, half_sweep_reps_kernel<1>, block, 0);
     return e == cudaSuccess ? n : 0;
 }
 

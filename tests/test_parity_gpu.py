@@ -207,6 +207,33 @@ def test_resident_engine_matches_streaming_and_oracle(L, S, R):
     np.testing.assert_array_equal(out[0][1], st["m"])
 
 
+@pytest.mark.parametrize("L,S,R,gamma", [(16, 2, 3, 1), (32, 1, 2, 1), (24, 2, 2, 2), (64, 1, 4, 1), (18, 1, 2, 1)])
+@pytest.mark.parametrize("cfg", [(4 | 1024, 128, -1, 1, 64), (2 | 1024, 256, 0, 1, 0), (1 | 1024, 64, 2, 0, 16)])
+def test_replicas_in_one_thread_match_oracle(L, S, R, gamma, cfg):
+    """The streaming variant that updates a chunk for every replica of its sample
+    in one thread (bonds and offsets shared): same bits as the oracle, with a
+    refresh, Metropolis sweeps between MicSA runs, several samples, gamma daemon
+    families; L = 18 (padded rows) falls back to the plain kernel."""
+    n, interval = 45, 7
+    sched = np.linspace(2.5, 0.6, n)
+    with micsa.Micsa(L, S, R, 77 + L, gamma=gamma) as g:
+        g.set_engine("stream")
+        g.set_launch_config(*cfg)
+        assert g.launch_config()["words_per_thread"] & 1024
+        st = O.create(L, S, R, 77 + L, gamma=gamma)
+        if gamma == 1:
+            g.run(sched[:20], interval)
+            O.run(st, sched[:20], interval)
+            g.run_metropolis(sched[20:30])
+            O.run_metropolis(st, sched[20:30])
+            g.run(sched[30:], interval)
+            O.run(st, sched[30:], interval)
+        else:
+            g.run(sched, interval)
+            O.run_ex(st, sched, interval)
+        assert_same_state(g, st, f"L={L} S={S} R={R} gamma={gamma} {cfg}")
+
+
 @pytest.mark.parametrize("L", [16, 18, 32, 160])
 def test_launch_configs_agree(L):
     """Every launch shape (vector width, block, grid-stride cap, PDL, graph
@@ -215,9 +242,11 @@ def test_launch_configs_agree(L):
     sched = np.linspace(2.0, 0.6, n)
     ref = None
     configs = [(4, 256, -1, 1, 64), (2, 128, 0, 0, 0), (1, 256, -1, 1, 16), (4, 64, 3, 0, 7),
-               (2, 256, -1, 1, 64), (4 | 512, 128, -1, 1, 64), (2 | 512, 64, 0, 1, 16), (1 | 512, 128, 2, 0, 0)]
+               (2, 256, -1, 1, 64), (4 | 512, 128, -1, 1, 64), (2 | 512, 64, 0, 1, 16), (1 | 512, 128, 2, 0, 0),
+               (4 | 1024, 128, -1, 1, 64), (2 | 1024, 64, 0, 0, 0)]
     for cfg in configs:
         with micsa.Micsa(L, 1, R, 42) as g:
+            g.set_engine("stream")
             g.set_launch_config(*cfg)
             g.run(sched[:70], interval)
             g.run_metropolis(sched[70:90])
