@@ -1003,17 +1003,6 @@ int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
         PCK(p, cudaStreamWaitEvent(p->aux_stream, p->fork_ev, 0), "fork wait");
         rs = p->aux_stream;
     }
-    if (resident) {
-        ResidentArgs ra{};
-        ra.units = p->d_units;
-        ra.n_units_dev = p->d_nunits;
-        ra.K = p->K;
-        ra.counter = p->d_counter;
-        ra.jobs = p->d_jobs;
-        ra.results = p->d_results;
-        ra.max_jobs = p->max_jobs;
-        PCK(p, launch_multispin(ra, true, p->resident_smem, p->resident_grid, p->pdl && !fork, rs), "pool multispin launch");
-    }
     const bool splanes = (mask & 8) != 0;
     if (splanes) {
         // the bit-plane jobs held in shared memory: one persistent launch on its own branch
@@ -1032,6 +1021,19 @@ int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
                                : (const void *)pool_smem_planes_kernel<kSmemPlaneThreads, 1>;
         PCK(p, cudaLaunchKernelExC(&cfg, fn, args), "pool smem planes launch");
         PCK(p, cudaEventRecord(p->splanes_join, p->splanes_stream), "smem planes join event");
+    }
+    // the shared-memory multispin kernel after the longer bit-plane units: its CTAs take the
+    // SMs that the bit-plane kernel leaves as its queue drains
+    if (resident) {
+        ResidentArgs ra{};
+        ra.units = p->d_units;
+        ra.n_units_dev = p->d_nunits;
+        ra.K = p->K;
+        ra.counter = p->d_counter;
+        ra.jobs = p->d_jobs;
+        ra.results = p->d_results;
+        ra.max_jobs = p->max_jobs;
+        PCK(p, launch_multispin(ra, true, p->resident_smem, p->resident_grid, p->pdl && !fork, rs), "pool multispin launch");
     }
     if (planes) {
         // the bit-plane jobs' parts on their own branches: bytes -> planes, the K

@@ -358,6 +358,23 @@ def test_pool_smem_plane_budgets_match_oracle(smem):
         assert_final_state(res[idx], st, f"{job} {smem}")
 
 
+@pytest.mark.parametrize("smem", [None, (100 << 10, 1)])
+def test_pool_smem_plane_units_split_replicas_match_oracle(smem):
+    """Jobs with more replicas than one shared-memory unit holds are split into
+    replica ranges (the default budget: L = 48 x 8 replicas in units of two, L = 40
+    x 5 in units of two and one; 100 KB: one replica per unit); each range draws
+    its own replicas' Philox streams."""
+    jobs = [(48, 8, 61, 9, 4, 2.5, 0.5), (40, 5, 62, 11, 3, 3.0, 0.3), (34, 7, 63, 6, 2, 2.0, 1.0)]
+    res = run_pool(jobs, K=4, smem=smem)
+    for idx, (L, R, seed, n, interval, T0, T1) in enumerate(jobs):
+        st = O.create(L, 1, R, seed)
+        O.run(st, micsa.linear_schedule(T0, T1, n), interval)
+        e, a, _ = O.measure(st)
+        np.testing.assert_array_equal(res[idx]["energy"], e, err_msg=str(jobs[idx]))
+        np.testing.assert_array_equal(res[idx]["aux"], a, err_msg=str(jobs[idx]))
+        assert_final_state(res[idx], st, jobs[idx])
+
+
 def test_pool_smem_planes_rejects_bad_values():
     with micsa.Pool(1 << 24, 4, 4) as p:
         for budget, bps in [(1 << 30, 1), (1 << 16, 0), (1 << 16, 9)]:
