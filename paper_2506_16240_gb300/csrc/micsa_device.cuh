@@ -38,6 +38,35 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
+// Philox4x32-10 with the ten round keys precomputed (same function as
+// philox4x32_10: round r uses key + r * Weyl increment).
+struct RoundKeys {
+    uint32_t k0[10], k1[10];
+};
+
+__device__ __forceinline__ RoundKeys round_keys(uint32_t key0, uint32_t key1) {
+    RoundKeys r;
+#pragma unroll
+    for (int i = 0; i < 10; ++i) {
+        r.k0[i] = key0 + (uint32_t)i * 0x9E3779B9u;
+        r.k1[i] = key1 + (uint32_t)i * 0xBB67AE85u;
+    }
+    return r;
+}
+
+// Philox4x32-10 with the round keys precomputed, each round's two products
+// taken as one 32 x 32 -> 64-bit multiply (high word and low word of the same
+// product).
+__device__ __forceinline__ uint4 philox_wide(uint4 c, const RoundKeys &rk) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c.x, p1 = (uint64_t)0xCD9E8D57u * c.z;
+        c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ rk.k0[r], (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ rk.k1[r],
+                       (uint32_t)p0);
+    }
+    return c;
+}
+
 __device__ __forceinline__ uint32_t lane_of(uint4 w, int lane) {
     return lane == 0 ? w.x : lane == 1 ? w.y : lane == 2 ? w.z : w.w;
 }

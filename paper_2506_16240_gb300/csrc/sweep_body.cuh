@@ -79,6 +79,7 @@ __device__ __forceinline__ void update_chunk(const Geometry &g, int8_t *spins, u
     uint32_t xp[NW], xm[NW];
     x_neighbours<NW, !FULL>(O, o, b0, g.Lh, edge, first, last, xp, xm);
     const uint32_t quad0 = (uint32_t)((((int64_t)p * g.L + z) * g.L + y) * g.W + c * NW);
+    const RoundKeys rk = round_keys(key0, key1);  // invariant over the thread's chunks
 
 #pragma unroll
     for (int j = 0; j < NW; ++j) {
@@ -87,9 +88,8 @@ __device__ __forceinline__ void update_chunk(const Geometry &g, int8_t *spins, u
         if (METRO) {
             // dH = 12 - 4u > 0 <=> u < 3; accept iff a fresh uniform is below
             // the Metropolis cut point of dH (index 2 - u).
-            const uint4 w = philox4x32_10(
-                make_uint4(quad0 + j, (uint32_t)t, (gid << 2) | kTagMetro, (uint32_t)((uint64_t)t >> 32)),
-                key0, key1);
+            const uint4 w = philox_wide(
+                make_uint4(quad0 + j, (uint32_t)t, (gid << 2) | kTagMetro, (uint32_t)((uint64_t)t >> 32)), rk);
             uint32_t am = 0;
 #pragma unroll
             for (int l = 0; l < 4; ++l) {
@@ -105,9 +105,8 @@ __device__ __forceinline__ void update_chunk(const Geometry &g, int8_t *spins, u
             S[j] ^= am & 0xFEFEFEFEu;
         } else {
             if (refresh) {
-                const uint4 w = philox4x32_10(
-                    make_uint4(quad0 + j, (uint32_t)t, (gid << 2) | kTagDaemon, (uint32_t)((uint64_t)t >> 32)),
-                    key0, key1);
+                const uint4 w = philox_wide(
+                    make_uint4(quad0 + j, (uint32_t)t, (gid << 2) | kTagDaemon, (uint32_t)((uint64_t)t >> 32)), rk);
                 D[j] = (daemon_from_uniform(w.x, th0, th1, th2) |
                         (daemon_from_uniform(w.y, th0, th1, th2) << 8) |
                         (daemon_from_uniform(w.z, th0, th1, th2) << 16) |
