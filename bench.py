@@ -856,13 +856,19 @@ def pool_breakdown(ticks=6, K=256):
     rng = np.random.default_rng(4)
     inst = [(int(L), int(r), int(s)) for L, r, s in
             zip(rng.choice([16, 24, 32, 48, 64], 256), rng.integers(5, 21, 256), rng.integers(1, 2 ** 62, 256))]
-    rows = [("all", lambda L: True, (0, 1)), ("all", lambda L: True, (100 << 10, 1)),
-            ("L >= 48", lambda L: L >= 48, (0, 1)), ("L >= 48", lambda L: L >= 48, (100 << 10, 1)),
-            ("L >= 48", lambda L: L >= 48, None), ("L <= 32", lambda L: L <= 32, (0, 1))]
+    rows = [("all", lambda L: True, (0, 1))]
+    for cl in (False, True):
+        for budget in (50 << 10, 100 << 10, 150 << 10):
+            rows.append(("L >= 48", lambda L: L >= 48, (budget, 1, cl)))
+        rows.append(("L >= 48", lambda L: L >= 48, (232432, 1, cl)))
+    rows += [("all", lambda L: True, (100 << 10, 1, False)), ("all", lambda L: True, (150 << 10, 1, True)),
+             ("all", lambda L: True, (50 << 10, 1, True)), ("L <= 32", lambda L: L <= 32, (0, 1))]
     for label, sel, smem in rows:
         with micsa.Pool(8 << 30, 512, K) as p:
             if smem is not None:
-                p.set_smem_planes(*smem)
+                p.set_smem_planes(*smem[:2])
+                if len(smem) > 2:
+                    p.set_smem_clusters(smem[2])
             for L, r, s in inst:
                 if sel(L):
                     p.submit(L, 2, s, 10 ** 6, r, 2.5, 0.5)

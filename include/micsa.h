@@ -412,6 +412,16 @@ int micsa_pool_set_planes(micsa_pool_t p, int on);
  * limit. Synchronizes. */
 int micsa_pool_set_smem_planes(micsa_pool_t p, size_t smem_bytes, int blocks_per_sm);
 
+/* For the jobs admitted from now on (on by default): a shared-memory unit of a
+ * job with 32 < L <= 128 is split over a thread-block cluster of ceil(L / 32)
+ * CTAs, CTA c holding z word c (32 z) of every column of the unit's replicas;
+ * the z neighbours across words are read from the peer CTAs' shared memory
+ * (distributed shared memory) and a cluster barrier separates the half-sweeps,
+ * so a unit's tick runs on several SMs and a replica's slice must fit the
+ * budget rather than the whole replica. Off: a unit in one CTA. Results are
+ * identical either way. */
+int micsa_pool_set_smem_clusters(micsa_pool_t p, int on);
+
 /* The current budget, the largest the device allows, and the blocks per SM of
  * the shared-memory bit-plane path. Any pointer may be NULL. */
 int micsa_pool_get_smem_planes(micsa_pool_t p, size_t *smem_bytes, size_t *max_smem_bytes, int *blocks_per_sm);

@@ -146,17 +146,23 @@ def apply_pool(pool, choice):
     pool.set_shape(choice["max_words"], choice["chains"])
     pool.set_launch_config(choice.get("blocks_per_sm", 0))  # 0: as many blocks as fit
     if "smem_planes" in choice:
-        budget, bps = choice["smem_planes"]
+        budget, bps = choice["smem_planes"][:2]
         pool.set_smem_planes(min(budget, pool.smem_planes()[1]), bps)
+        if len(choice["smem_planes"]) > 2:
+            pool.set_smem_clusters(bool(choice["smem_planes"][2]))
 
 
 def smem_plane_candidates(max_budget):
-    """(budget bytes, CTAs per SM) of the shared-memory bit-plane path: off; the
-    whole budget (a unit takes as many replicas of a job as fit); 100 KB (units of
-    one replica up to L = 64: more, shorter units, so the tick is not held up by
-    the longest one); 60 KB (one replica of L <= 48, the L = 56 and 64 jobs on the
-    global bit planes). One CTA of 512 threads per SM."""
-    return [(0, 1), (max_budget, 1), (min(max_budget, 100 << 10), 1), (min(max_budget, 60 << 10), 1)]
+    """(budget bytes, CTAs per SM, units over clusters) of the shared-memory bit-plane
+    path: off; the whole budget (a unit takes as many replicas of a job as fit), in
+    one CTA or split over a cluster of one CTA per z word; 100 KB (units of one
+    replica up to L = 64: more, shorter units, so the tick is not held up by the
+    longest one), in one CTA or over a cluster; 60 KB in one CTA (one replica of
+    L <= 48, the L = 56 and 64 jobs on the global bit planes). CTAs of 512 threads,
+    one per SM."""
+    half = min(max_budget, 100 << 10)
+    return [(0, 1, False), (max_budget, 1, False), (max_budget, 1, True), (half, 1, False), (half, 1, True),
+            (min(max_budget, 60 << 10), 1, False)]
 
 
 def time_pool_ticks(pool, ticks, clock):
@@ -208,18 +214,20 @@ def tune_pool_for_jobs(pool_factory, jobs, ticks=2, clock=None, smem=None):
     n_cand = len(pool_candidates()) + 5
     best = None
     settings = smem
-    for k in range(len(settings) if settings is not None else 4):
+    for k in range(len(settings) if settings is not None else len(smem_plane_candidates(1 << 20))):
         with pool_factory() as p:
             if settings is None:
                 settings = smem_plane_candidates(p.smem_planes()[1])
-            budget, bps = settings[k]
+            budget, bps = settings[k][:2]
             p.set_smem_planes(budget, bps)
+            if len(settings[k]) > 2:
+                p.set_smem_clusters(bool(settings[k][2]))
             K = p.tick_sweeps
             long = (1 + ticks) * K * (n_cand + 2)  # candidates x (warm-up + timed ticks), with a margin
             for L, R, seed, _, interval, T0, T1 in jobs:
                 if p.submit(L, R, seed, long, interval, T0, T1) is None:
                     break  # the scratch pool is full: tune on what fits
-            c = dict(tune_pool(p, ticks=ticks, clock=clock), smem_planes=[budget, bps])
+            c = dict(tune_pool(p, ticks=ticks, clock=clock), smem_planes=list(settings[k]))
         if best is None or c["s_per_tick"] < best["s_per_tick"]:
             best = c
     return best

@@ -82,6 +82,7 @@ struct JobDesc {
     int32_t use_planes;
     int32_t smem_planes;  // bit-plane job swept in shared memory by the tick's persistent kernel: the
                           // per-CTA shared-memory budget (bytes) it was admitted with; 0: not
+    int32_t smem_cluster;  // > 1: each of its shared-memory units is split over a cluster of this many CTAs
 };
 
 // One lattice (a replica of a sample or of a pool job) that a CTA keeps in

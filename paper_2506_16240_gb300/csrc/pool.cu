@@ -21,6 +21,8 @@
 #include <string>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "sweep_body.cuh"
 #include "msg_body.cuh"
 #include "../../include/micsa.h"
@@ -54,8 +56,11 @@ struct PVBlock {
 struct PlaneUnit {
     int32_t slot;
     int16_t r0, nrep;
-    int32_t bonds_smem;
+    int16_t bonds_smem;
+    int16_t C;  // 1: the unit in one CTA; C > 1: a cluster of C CTAs, CTA c holding z word c
 };
+
+constexpr int kMaxCluster = 4;  // clusters of 2..4 CTAs: L up to 128
 
 // CTA sizes of the shared-memory bit-plane kernel: 512 threads for one CTA per
 // SM, 256 threads for two or more (registers: about 120 per thread)
@@ -299,6 +304,11 @@ struct SplaneGeo {
     uint32_t WP;
     FastDiv dW4, dL;
     uint32_t bonds_off;  // word offset of the bond planes in shared memory
+    uint32_t bwp;        // words between consecutive bond planes (shared memory or global)
+    // a cluster's CTA: the z word it holds and the shared memory of the CTAs
+    // holding the next and the previous z word (generic addresses)
+    int zw0;
+    const uint32_t *up, *dn;
 };
 
 __device__ __forceinline__ void lds4(uint32_t idx, uint32_t (&v)[4]) {
@@ -319,12 +329,16 @@ __device__ __forceinline__ void sts4(uint32_t idx, const uint32_t (&v)[4]) {
 // with Eq. (flip-OK), bit-sliced; at a refresh sweep the daemons of the words
 // are drawn first from the same Philox blocks, Sec. 2.7), with 32-bit shared
 // memory indices. BSMEM: the bond planes are in shared memory, else at gb.
-template <bool BSMEM>
+// CL: the CTA holds one z word (G.zw0) of a unit split over a cluster; the
+// opposite-parity words at z word zw0 +- 1 are read from the CTAs holding them
+// (distributed shared memory), at the same index within their slice.
+template <bool BSMEM, bool CL = false>
 __device__ __forceinline__ void splane_group(const SplaneGeo &G, const uint32_t *gb, int p, uint32_t q, int nrep,
                                              int64_t t, bool refresh, const CutsGt &cut, const RoundKeys &rk,
                                              uint32_t gid0) {
     const uint32_t rowi = fdiv(q, G.dW4);
-    const uint32_t zw = fdiv(rowi, G.dL);
+    const uint32_t zw = CL ? 0u : fdiv(rowi, G.dL);  // z word within this CTA's planes
+    const uint32_t zwg = CL ? (uint32_t)G.zw0 : zw;   // the z word in the lattice
     const int L = G.L;
     const int y = (int)(rowi - zw * (uint32_t)L);
     const int i0 = 4 * (int)(q - rowi * (uint32_t)G.W4);
@@ -335,10 +349,10 @@ __device__ __forceinline__ void splane_group(const SplaneGeo &G, const uint32_t 
     const uint32_t P = (uint32_t)G.P, row = zw * (uint32_t)L;
     const uint32_t wc = (row + y) * P + i0;
     const uint32_t w_yp = (row + yp) * P + i0, w_ym = (row + ym) * P + i0;
-    const uint32_t w_zp = (zwp * L + y) * P + i0, w_zm = (zwm * L + y) * P + i0;
+    const uint32_t w_zp = CL ? wc : (zwp * L + y) * P + i0, w_zm = CL ? wc : (zwm * L + y) * P + i0;
     const uint32_t w_ip = (row + y) * P + ip, w_im = (row + y) * P + im;
     const uint32_t M = ((p + y) & 1) ? 0x55555555u : 0xAAAAAAAAu;  // bits whose site has x offset 1
-    const bool zlast = zw + 1 == (uint32_t)G.nzw, zfirst = zw == 0;
+    const bool zlast = zwg + 1 == (uint32_t)G.nzw, zfirst = zwg == 0;
     const int Lz = G.Lz;
     const uint32_t zmask = (zlast && Lz < 32) ? ((1u << Lz) - 1u) : 0xFFFFFFFFu;
     uint32_t wmask[4];  // words from Lr on are padding: no site
@@ -348,7 +362,7 @@ __device__ __forceinline__ void splane_group(const SplaneGeo &G, const uint32_t 
     uint32_t B[6][4];
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
-        const uint32_t bi = (uint32_t)(k * 2 + p) * G.WP + wc;
+        const uint32_t bi = (uint32_t)(k * 2 + p) * G.bwp + wc;
         if constexpr (BSMEM) {
             lds4(G.bonds_off + bi, B[k]);
         } else {
@@ -359,7 +373,7 @@ __device__ __forceinline__ void splane_group(const SplaneGeo &G, const uint32_t 
             B[k][3] = a.w;
         }
     }
-    const uint32_t quad0 = (((uint32_t)p * L + 32 * zw) * L + y) * (uint32_t)G.W4 + (uint32_t)(i0 >> 2);
+    const uint32_t quad0 = (((uint32_t)p * L + 32 * zwg) * L + y) * (uint32_t)G.W4 + (uint32_t)(i0 >> 2);
     for (int r = 0; r < nrep; ++r) {
         const uint32_t base = (uint32_t)r * 6 * G.WP;
         const uint32_t Ob = base + (uint32_t)o * G.WP, Sb = base + (uint32_t)p * G.WP;
@@ -368,8 +382,15 @@ __device__ __forceinline__ void splane_group(const SplaneGeo &G, const uint32_t 
         lds4(Ob + wc, Oc);
         lds4(Ob + w_yp, Oyp);
         lds4(Ob + w_ym, Oym);
-        lds4(Ob + w_zp, Ozp);
-        lds4(Ob + w_zm, Ozm);
+        if constexpr (CL) {
+            const uint4 a = *reinterpret_cast<const uint4 *>(G.up + Ob + w_zp);
+            const uint4 b = *reinterpret_cast<const uint4 *>(G.dn + Ob + w_zm);
+            Ozp[0] = a.x; Ozp[1] = a.y; Ozp[2] = a.z; Ozp[3] = a.w;
+            Ozm[0] = b.x; Ozm[1] = b.y; Ozm[2] = b.z; Ozm[3] = b.w;
+        } else {
+            lds4(Ob + w_zp, Ozp);
+            lds4(Ob + w_zm, Ozm);
+        }
         const uint32_t Oip = pool_spl[Ob + w_ip], Oim = pool_spl[Ob + w_im];
         lds4(Sb + wc, Sg);
         if (refresh) {
@@ -444,12 +465,15 @@ __device__ __forceinline__ void splane_group(const SplaneGeo &G, const uint32_t 
 // back. No state leaves the SM between the half-sweeps of a tick.
 template <int NT, int MINB>
 __global__ void __launch_bounds__(NT, MINB)
-    pool_smem_planes_kernel(PoolTables T, const PlaneUnit *units, const int32_t *n_units, int *counter, int K) {
+    pool_smem_planes_kernel(PoolTables T, const PlaneUnit *units, const int32_t *unit_start,
+                            const int32_t *n_units, int *counters, int K) {
     pool_wait();
     pool_release();
     uint32_t *spl = pool_spl;
     __shared__ int s_unit;
-    const int n = *n_units;
+    const int n = n_units[1];
+    units += unit_start[1];  // the units held in one CTA
+    int *counter = counters + 1;
     for (;;) {
         if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1);
         __syncthreads();
@@ -489,6 +513,9 @@ __global__ void __launch_bounds__(NT, MINB)
         G.dW4 = make_fastdiv_dev((uint32_t)G.W4);
         G.dL = make_fastdiv_dev((uint32_t)g.L);
         G.bonds_off = (uint32_t)(nrep * 6 * WP);
+        G.bwp = (uint32_t)WP;
+        G.zw0 = 0;
+        G.up = G.dn = nullptr;
         const RoundKeys rk = round_keys(J.key0, J.key1);
         const uint32_t groups = (uint32_t)(WP / 4);
         // a thread's word groups: ceil(groups / threads) each, spread over as many
@@ -522,6 +549,142 @@ __global__ void __launch_bounds__(NT, MINB)
             msg_convert_word(spl, spins, daemons, g, WP, 1, 6, 0, false, rep, par, rem - par * WP);
         }
         __syncthreads();  // the planes are read out before the next unit overwrites them
+    }
+}
+
+// Bytes <-> the slice of z word zw0 of one replica's planes in shared memory:
+// word w = y P + i of a slice plane holds, in bit b, the site of row (z, y),
+// byte i, z = 32 zw0 + b (b < nb); the words from Lh on are padding (zero).
+// Slice layout per replica: [spin p0, p1, m0 p0, p1, m1 p0, p1][S].
+__device__ __forceinline__ void slice_convert_word(uint32_t *spl, int8_t *spins, uint8_t *daemons, const Geometry &g,
+                                                   uint32_t S, int zw0, bool to_planes, int rep, int p, uint32_t w) {
+    const int i = (int)(w % (uint32_t)g.P), y = (int)(w / (uint32_t)g.P);
+    uint32_t *pl = spl + (uint32_t)rep * 6 * S;
+    if (i >= g.Lh) {
+        if (to_planes) pl[(uint32_t)p * S + w] = pl[(uint32_t)(2 + p) * S + w] = pl[(uint32_t)(4 + p) * S + w] = 0;
+        return;
+    }
+    const int64_t base = ((int64_t)rep * 2 + p) * g.half + ((int64_t)32 * zw0 * g.L + y) * g.P + i;
+    const int64_t zstep = (int64_t)g.L * g.P;
+    const int nb = g.L - 32 * zw0 < 32 ? g.L - 32 * zw0 : 32;
+    if (to_planes) {
+        uint32_t sv = 0, m0 = 0, m1 = 0;
+        for (int b = 0; b < nb; ++b) {
+            sv |= (((uint32_t)(uint8_t)spins[base + b * zstep] >> 7) & 1u) << b;
+            const uint32_t m = daemons[base + b * zstep];
+            m0 |= (m & 1u) << b;
+            m1 |= ((m >> 1) & 1u) << b;
+        }
+        pl[(uint32_t)p * S + w] = sv;
+        pl[(uint32_t)(2 + p) * S + w] = m0;
+        pl[(uint32_t)(4 + p) * S + w] = m1;
+    } else {
+        const uint32_t sv = pl[(uint32_t)p * S + w], m0 = pl[(uint32_t)(2 + p) * S + w], m1 = pl[(uint32_t)(4 + p) * S + w];
+        for (int b = 0; b < nb; ++b) {
+            spins[base + b * zstep] = ((sv >> b) & 1u) ? (int8_t)-1 : (int8_t)1;
+            daemons[base + b * zstep] = (uint8_t)(((m0 >> b) & 1u) | (((m1 >> b) & 1u) << 1));
+        }
+    }
+}
+
+// The shared-memory bit-plane tick with each unit split over a thread-block
+// cluster of C CTAs, CTA c holding z word c of every column of the unit's
+// replicas (and of the bond planes when they are held): the z neighbours across
+// word boundaries come from the peer CTAs' shared memory, and a cluster barrier
+// separates the half-sweeps. Rank 0 takes the units from the work counter and
+// the other CTAs read the index from its shared memory.
+template <int NT>
+__global__ void __launch_bounds__(NT, 1)
+    pool_cluster_planes_kernel(PoolTables T, const PlaneUnit *units, const int32_t *unit_start,
+                               const int32_t *n_units, int *counters, int K) {
+    namespace cg = cooperative_groups;
+    pool_wait();
+    pool_release();
+    cg::cluster_group cl = cg::this_cluster();
+    const int C = (int)cl.num_blocks(), c = (int)cl.block_rank();
+    uint32_t *spl = pool_spl;
+    __shared__ int s_unit;
+    const int n = n_units[C], u0 = unit_start[C];
+    int *counter = counters + C;
+    const uint32_t *up = cl.map_shared_rank(spl, (c + 1) % C);
+    const uint32_t *dn = cl.map_shared_rank(spl, (c + C - 1) % C);
+    const int *unit_of_rank0 = cl.map_shared_rank(&s_unit, 0);
+    for (;;) {
+        if (c == 0 && threadIdx.x == 0) s_unit = atomicAdd(counter, 1);
+        cl.sync();
+        const int u = *unit_of_rank0;
+        cl.sync();  // every CTA has read the index before rank 0 takes the next one
+        if (u >= n) break;
+        const PlaneUnit U = units[u0 + u];
+        const JobDesc &J = T.jobs[U.slot];
+        if (!J.live || J.t >= J.n_sweeps) continue;
+        const Geometry g = J.geo;
+        const int nzw = (g.L + 31) / 32;
+        const uint32_t S = (uint32_t)g.L * (uint32_t)g.P;  // words of a slice plane
+        const uint32_t WP = (uint32_t)nzw * S;             // words of a global plane
+        const int nrep = U.nrep;
+        int8_t *spins = J.spins + (int64_t)U.r0 * 2 * g.half;
+        uint8_t *daemons = J.daemons + (int64_t)U.r0 * 2 * g.half;
+        for (uint32_t idx = threadIdx.x; idx < (uint32_t)nrep * 2 * S; idx += blockDim.x) {
+            const int rep = (int)(idx / (2 * S));
+            const uint32_t rem = idx - (uint32_t)rep * 2 * S;
+            const int par = (int)(rem / S);
+            slice_convert_word(spl, spins, daemons, g, S, c, true, rep, par, rem - par * S);
+        }
+        uint32_t *sb = spl + (uint32_t)nrep * 6 * S;
+        if (U.bonds_smem)  // slice c of each of the 12 bond planes
+            for (uint32_t i = threadIdx.x; i < 12 * (S / 4); i += blockDim.x) {
+                const uint32_t k = i / (S / 4), j = i - k * (S / 4);
+                reinterpret_cast<uint4 *>(sb + k * S)[j] =
+                    reinterpret_cast<const uint4 *>(J.bplanes + (size_t)k * WP + (size_t)c * S)[j];
+            }
+        cl.sync();  // every slice is in place before a peer reads it
+        SplaneGeo G;
+        G.L = g.L;
+        G.P = g.P;
+        G.Lr = g.Lh;
+        G.nzw = nzw;
+        G.W4 = g.P / 4;
+        G.Lz = g.L - 32 * (nzw - 1);
+        G.WP = S;
+        G.dW4 = make_fastdiv_dev((uint32_t)G.W4);
+        G.dL = make_fastdiv_dev((uint32_t)g.L);
+        G.bonds_off = (uint32_t)nrep * 6 * S;
+        G.bwp = U.bonds_smem ? S : WP;
+        G.zw0 = c;
+        G.up = up;
+        G.dn = dn;
+        const uint32_t *gb = J.bplanes + (size_t)c * S;  // this slice of the global bond planes
+        const RoundKeys rk = round_keys(J.key0, J.key1);
+        const uint32_t groups = S / 4;
+        const uint32_t per = (groups + blockDim.x - 1) / blockDim.x;
+        const uint32_t span = (groups + per - 1) / per;
+        for (int k = 0; k < K; ++k) {
+            const int64_t t = J.t + k;
+            if (t >= J.n_sweeps) break;
+            const bool refresh = t % J.interval == 0;
+            CutsGt cut{0, 0, 0};
+            if (refresh) {
+                const uint64_t *th = J.thr + 3 * (t / J.interval);
+                cut = make_cuts_gt(th[0], th[1], th[2]);
+            }
+            for (int par = 0; par < 2; ++par) {
+                if (threadIdx.x < span)
+                    for (uint32_t q = threadIdx.x; q < groups; q += span) {
+                        if (U.bonds_smem)
+                            splane_group<true, true>(G, nullptr, par, q, nrep, t, refresh, cut, rk, (uint32_t)U.r0);
+                        else
+                            splane_group<false, true>(G, gb, par, q, nrep, t, refresh, cut, rk, (uint32_t)U.r0);
+                    }
+                cl.sync();  // the half-sweep's words are visible to the peers
+            }
+        }
+        for (uint32_t idx = threadIdx.x; idx < (uint32_t)nrep * 2 * S; idx += blockDim.x) {
+            const int rep = (int)(idx / (2 * S));
+            const uint32_t rem = idx - (uint32_t)rep * 2 * S;
+            const int par = (int)(rem / S);
+            slice_convert_word(spl, spins, daemons, g, S, c, false, rep, par, rem - par * S);
+        }
     }
 }
 
@@ -625,7 +788,7 @@ __global__ void __launch_bounds__(kVBlock) pool_best_copy_kernel(PoolTables T) {
 __global__ void pool_advance_kernel(JobDesc *jobs, int max_jobs, int K, int *counter) {
     pool_wait();
     pool_release();
-    if (blockIdx.x == 0 && threadIdx.x < 2) counter[threadIdx.x] = 0;  // the next tick's persistent kernels' work counters
+    if (blockIdx.x == 0 && threadIdx.x <= kMaxCluster) counter[threadIdx.x] = 0;  // the next tick's persistent kernels' work counters
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max_jobs; i += gridDim.x * blockDim.x) {
         JobDesc &J = jobs[i];
         if (!J.live) continue;
@@ -719,15 +882,17 @@ struct micsa_pool {
     size_t splanes_smem = 0;  // per-CTA shared-memory budget for the jobs admitted from now on; 0: off
     size_t splanes_max_smem = 0;  // what the device allows the kernel
     int splanes_grid = 0;
+    bool splanes_cluster = true;  // split the units of jobs with L > 32 over clusters (jobs admitted from now on)
     PlaneUnit *d_punits = nullptr, *h_punits = nullptr;
-    int32_t *d_npunits = nullptr, *h_npunits = nullptr;
+    // per cluster size C (index 1..kMaxCluster): first unit and unit count in the table
+    int32_t *d_npunits = nullptr, *h_npunits = nullptr, *d_pustart = nullptr, *h_pustart = nullptr;
     int max_punits = 0;
-    size_t splanes_launch_smem = 0;  // the largest unit of the current table
-    bool has_splane_jobs = false;
-    cudaStream_t splanes_stream = nullptr;
-    cudaEvent_t splanes_fork = nullptr, splanes_join = nullptr;
-    cudaGraphExec_t graphs[16] = {};  // by part mask: 1 resident, 2 byte-streamed, 4 bit-plane jobs,
-                                      // 8 bit-plane jobs in shared memory
+    size_t splanes_launch_smem[kMaxCluster + 1] = {};  // the largest unit of each cluster size
+    int cluster_grid[kMaxCluster + 1] = {};            // CTAs of the launch of each cluster size
+    cudaStream_t splanes_stream[kMaxCluster + 1] = {};
+    cudaEvent_t splanes_fork = nullptr, splanes_join[kMaxCluster + 1] = {};
+    cudaGraphExec_t graphs[128] = {};  // by part mask: 1 resident, 2 byte-streamed, 4 bit-plane jobs,
+                                       // 8 << (C - 1): bit-plane jobs in shared memory, units over C CTAs
     std::string err;
 };
 
@@ -877,7 +1042,8 @@ int upload_tables(micsa_pool_t p) {
         return p->slots[a].desc.L * p->slots[a].desc.n_replicas > p->slots[b].desc.L * p->slots[b].desc.n_replicas;
     });
     int npvb = 0, npu = 0;
-    size_t unit_smem = 0;
+    std::vector<PlaneUnit> units_c[kMaxCluster + 1];  // the shared-memory units by cluster size
+    size_t unit_smem[kMaxCluster + 1] = {};
     for (int i : order) {
         const JobDesc &J = p->h_jobs[i];
         if (J.resident) {
@@ -901,12 +1067,16 @@ int upload_tables(micsa_pool_t p) {
                     p->h_vblocks[nvb++] = VBlock{i, (int16_t)r, 0, (int32_t)c};
                 }
             if (pass == 1 && J.smem_planes) {
-                const SplaneSplit sp = splane_split(msg_plane_words(J.geo), J.R, J.smem_planes);
+                // one CTA per unit, or a cluster of C CTAs holding one z word each
+                const int C = J.smem_cluster > 1 ? J.smem_cluster : 1;
+                const int64_t words = C > 1 ? (int64_t)J.geo.L * J.geo.P : msg_plane_words(J.geo);
+                const SplaneSplit sp = splane_split(words, J.R, J.smem_planes);
                 for (int r0 = 0; r0 < J.R; r0 += sp.nrep) {
                     if (npu >= p->max_punits) return pfail(p, MICSA_E_BUSY, "plane unit table full");
-                    p->h_punits[npu++] = PlaneUnit{i, (int16_t)r0, (int16_t)std::min(sp.nrep, J.R - r0),
-                                                   sp.bonds_smem ? 1 : 0};
-                    unit_smem = std::max(unit_smem, sp.bytes);
+                    units_c[C].push_back(PlaneUnit{i, (int16_t)r0, (int16_t)std::min(sp.nrep, J.R - r0),
+                                                   (int16_t)(sp.bonds_smem ? 1 : 0), (int16_t)C});
+                    unit_smem[C] = std::max(unit_smem[C], sp.bytes);
+                    ++npu;
                 }
             } else if (pass == 1) {
                 const int64_t threads = msg_plane_words(J.geo) / 4;  // 4 plane words each
@@ -958,12 +1128,20 @@ int upload_tables(micsa_pool_t p) {
         prev = end;
     }
     *p->h_nunits = nunits;
-    *p->h_npunits = npu;
-    p->has_splane_jobs = npu > 0;
-    if (unit_smem != p->splanes_launch_smem) {  // the launch's shared memory changes: recapture
-        p->splanes_launch_smem = unit_smem;
-        drop_pool_graphs(p);
+    // the table by cluster size (each kernel reads its own range); a change of
+    // any launch's shared memory invalidates the captured ticks
+    int at = 0;
+    bool smem_changed = false;
+    for (int C = 0; C <= kMaxCluster; ++C) {
+        p->h_pustart[C] = at;
+        p->h_npunits[C] = (int32_t)units_c[C].size();
+        for (const PlaneUnit &U : units_c[C]) p->h_punits[at++] = U;
+        if (unit_smem[C] != p->splanes_launch_smem[C]) {
+            p->splanes_launch_smem[C] = unit_smem[C];
+            smem_changed = true;
+        }
     }
+    if (smem_changed) drop_pool_graphs(p);
     p->has_stream_jobs = nvb_stream > 0;
     p->has_resident_jobs = nunits > 0;
     p->has_plane_jobs = npvb > 0;
@@ -978,7 +1156,8 @@ int upload_tables(micsa_pool_t p) {
         PCK(p, cudaMemcpyAsync(p->d_nunits, p->h_nunits, sizeof(int32_t), cudaMemcpyHostToDevice, p->stream), "upload unit count");
     }
     PCK(p, cudaMemcpyAsync(p->d_punits, p->h_punits, sizeof(PlaneUnit) * (size_t)(npu ? npu : 1), cudaMemcpyHostToDevice, p->stream), "upload plane units");
-    PCK(p, cudaMemcpyAsync(p->d_npunits, p->h_npunits, sizeof(int32_t), cudaMemcpyHostToDevice, p->stream), "upload plane unit count");
+    PCK(p, cudaMemcpyAsync(p->d_npunits, p->h_npunits, sizeof(int32_t) * (kMaxCluster + 1), cudaMemcpyHostToDevice, p->stream), "upload plane unit counts");
+    PCK(p, cudaMemcpyAsync(p->d_pustart, p->h_pustart, sizeof(int32_t) * (kMaxCluster + 1), cudaMemcpyHostToDevice, p->stream), "upload plane unit starts");
     PCK(p, cudaEventRecord(p->tables_free, p->stream), "record table event");
     p->tables_dirty = false;
     return MICSA_OK;
@@ -1003,24 +1182,40 @@ int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
         PCK(p, cudaStreamWaitEvent(p->aux_stream, p->fork_ev, 0), "fork wait");
         rs = p->aux_stream;
     }
-    const bool splanes = (mask & 8) != 0;
-    if (splanes) {
-        // the bit-plane jobs held in shared memory: one persistent launch on its own branch
-        PCK(p, cudaEventRecord(p->splanes_fork, st), "smem planes fork event");
-        PCK(p, cudaStreamWaitEvent(p->splanes_stream, p->splanes_fork, 0), "smem planes fork wait");
+    // the bit-plane jobs held in shared memory: one persistent launch per cluster
+    // size present (bit 8 << (C - 1) of the mask), each on its own branch
+    const bool splanes = (mask & (((1 << kMaxCluster) - 1) << 3)) != 0;
+    if (splanes) PCK(p, cudaEventRecord(p->splanes_fork, st), "smem planes fork event");
+    for (int C = 1; C <= kMaxCluster; ++C) {
+        if (!(mask & (8 << (C - 1)))) continue;
+        cudaStream_t ss = p->splanes_stream[C];
+        PCK(p, cudaStreamWaitEvent(ss, p->splanes_fork, 0), "smem planes fork wait");
         int K = p->K;
-        int *ctr = p->d_counter + 1;
-        void *args[] = {&T, &p->d_punits, &p->d_npunits, &ctr, &K};
-        const bool small = p->splanes_grid > p->sm_count;  // two or more CTAs per SM
+        void *args[] = {&T, &p->d_punits, &p->d_pustart, &p->d_npunits, &p->d_counter, &K};
         cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(p->splanes_grid);
-        cfg.blockDim = dim3(small ? kSmemPlaneThreadsSmall : kSmemPlaneThreads);
-        cfg.dynamicSmemBytes = p->splanes_launch_smem;
-        cfg.stream = p->splanes_stream;
-        const void *fn = small ? (const void *)pool_smem_planes_kernel<kSmemPlaneThreadsSmall, 2>
-                               : (const void *)pool_smem_planes_kernel<kSmemPlaneThreads, 1>;
+        cudaLaunchAttribute attr[1];
+        cfg.dynamicSmemBytes = p->splanes_launch_smem[C];
+        cfg.stream = ss;
+        const void *fn;
+        if (C == 1) {
+            const bool small = p->splanes_grid > p->sm_count;  // two or more CTAs per SM
+            cfg.gridDim = dim3(p->splanes_grid);
+            cfg.blockDim = dim3(small ? kSmemPlaneThreadsSmall : kSmemPlaneThreads);
+            fn = small ? (const void *)pool_smem_planes_kernel<kSmemPlaneThreadsSmall, 2>
+                       : (const void *)pool_smem_planes_kernel<kSmemPlaneThreads, 1>;
+        } else {
+            cfg.gridDim = dim3(p->cluster_grid[C]);
+            cfg.blockDim = dim3(kSmemPlaneThreads);
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = C;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            fn = (const void *)pool_cluster_planes_kernel<kSmemPlaneThreads>;
+        }
         PCK(p, cudaLaunchKernelExC(&cfg, fn, args), "pool smem planes launch");
-        PCK(p, cudaEventRecord(p->splanes_join, p->splanes_stream), "smem planes join event");
+        PCK(p, cudaEventRecord(p->splanes_join[C], ss), "smem planes join event");
     }
     // the shared-memory multispin kernel after the longer bit-plane units: its CTAs take the
     // SMs that the bit-plane kernel leaves as its queue drains
@@ -1084,7 +1279,8 @@ int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
     if (planes)
         for (int part = 0; part < p->chains; ++part)
             PCK(p, cudaStreamWaitEvent(st, p->planes_join[part], 0), "planes join wait");
-    if (splanes) PCK(p, cudaStreamWaitEvent(st, p->splanes_join, 0), "smem planes join wait");
+    for (int C = 1; C <= kMaxCluster; ++C)
+        if (mask & (8 << (C - 1))) PCK(p, cudaStreamWaitEvent(st, p->splanes_join[C], 0), "smem planes join wait");
     if (streamed || planes || splanes) {
         int K = p->K;
         void *eargs[] = {&T};
@@ -1107,8 +1303,9 @@ int tick_launches(micsa_pool_t p, int mask) {
     const int resident = (mask & 1) && p->resident_smem ? 1 : 0;
     const int streamed = (mask & 2) ? 2 * p->chains * p->K : 0;
     const int planes = (mask & 4) ? p->chains * (2 * p->K + 2) : 0;
-    const int splanes = (mask & 8) ? 1 : 0;
-    return resident + streamed + planes + splanes + ((mask & 14) ? 3 : 0) + 1;
+    int splanes = 0;
+    for (int C = 1; C <= kMaxCluster; ++C) splanes += (mask & (8 << (C - 1))) ? 1 : 0;
+    return resident + streamed + planes + splanes + ((mask & ~1) ? 3 : 0) + 1;
 }
 
 int ensure_graph(micsa_pool_t p, int mask) {
@@ -1213,24 +1410,29 @@ int micsa_pool_create(size_t arena_bytes, int max_jobs, int tick_sweeps, micsa_p
         p->max_units = max_jobs * kPoolMaxR;
         if ((e = cudaMalloc(&p->d_units, sizeof(ResidentUnit) * (size_t)p->max_units)) != cudaSuccess ||
             (e = cudaMalloc(&p->d_nunits, sizeof(int32_t))) != cudaSuccess ||
-            (e = cudaMalloc(&p->d_counter, 2 * sizeof(int))) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_counter, (kMaxCluster + 1) * sizeof(int))) != cudaSuccess ||
             (e = cudaMallocHost(&p->h_units, sizeof(ResidentUnit) * (size_t)p->max_units)) != cudaSuccess ||
             (e = cudaMallocHost(&p->h_nunits, sizeof(int32_t))) != cudaSuccess) { bail(MICSA_E_OOM); break; }
         *p->h_nunits = 0;
         if ((e = cudaMemsetAsync(p->d_nunits, 0, sizeof(int32_t), p->stream)) != cudaSuccess ||
-            (e = cudaMemsetAsync(p->d_counter, 0, 2 * sizeof(int), p->stream)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+            (e = cudaMemsetAsync(p->d_counter, 0, (kMaxCluster + 1) * sizeof(int), p->stream)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         // bit-plane jobs in shared memory: one CTA of kSmemPlaneThreads per unit, the budget
         // the device allows a block (opt-in) less the kernel's static shared memory
         p->max_punits = max_jobs * kPoolMaxR;
         if ((e = cudaMalloc(&p->d_punits, sizeof(PlaneUnit) * (size_t)p->max_punits)) != cudaSuccess ||
-            (e = cudaMalloc(&p->d_npunits, sizeof(int32_t))) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_npunits, sizeof(int32_t) * (kMaxCluster + 1))) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_pustart, sizeof(int32_t) * (kMaxCluster + 1))) != cudaSuccess ||
             (e = cudaMallocHost(&p->h_punits, sizeof(PlaneUnit) * (size_t)p->max_punits)) != cudaSuccess ||
-            (e = cudaMallocHost(&p->h_npunits, sizeof(int32_t))) != cudaSuccess) { bail(MICSA_E_OOM); break; }
-        *p->h_npunits = 0;
-        if ((e = cudaMemsetAsync(p->d_npunits, 0, sizeof(int32_t), p->stream)) != cudaSuccess ||
-            (e = cudaStreamCreateWithFlags(&p->splanes_stream, cudaStreamNonBlocking)) != cudaSuccess ||
-            (e = cudaEventCreateWithFlags(&p->splanes_fork, cudaEventDisableTiming)) != cudaSuccess ||
-            (e = cudaEventCreateWithFlags(&p->splanes_join, cudaEventDisableTiming)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+            (e = cudaMallocHost(&p->h_npunits, sizeof(int32_t) * (kMaxCluster + 1))) != cudaSuccess ||
+            (e = cudaMallocHost(&p->h_pustart, sizeof(int32_t) * (kMaxCluster + 1))) != cudaSuccess) { bail(MICSA_E_OOM); break; }
+        for (int C = 0; C <= kMaxCluster; ++C) p->h_npunits[C] = p->h_pustart[C] = 0;
+        if ((e = cudaMemsetAsync(p->d_npunits, 0, sizeof(int32_t) * (kMaxCluster + 1), p->stream)) != cudaSuccess ||
+            (e = cudaMemsetAsync(p->d_pustart, 0, sizeof(int32_t) * (kMaxCluster + 1), p->stream)) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&p->splanes_fork, cudaEventDisableTiming)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+        for (int C = 1; C <= kMaxCluster && e == cudaSuccess; ++C)
+            if ((e = cudaStreamCreateWithFlags(&p->splanes_stream[C], cudaStreamNonBlocking)) == cudaSuccess)
+                e = cudaEventCreateWithFlags(&p->splanes_join[C], cudaEventDisableTiming);
+        if (e != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         {
             int optin = 0;
             cudaFuncAttributes fa{};
@@ -1247,6 +1449,33 @@ int micsa_pool_create(size_t arena_bytes, int max_jobs, int tick_sweeps, micsa_p
             }
             p->splanes_smem = p->splanes_max_smem;
             p->splanes_grid = p->sm_count;  // one CTA per SM at the full budget
+            if (p->splanes_max_smem &&
+                (e = cudaFuncSetAttribute(pool_cluster_planes_kernel<kSmemPlaneThreads>,
+                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->splanes_max_smem)) != cudaSuccess) {
+                bail(MICSA_E_CUDA);
+                break;
+            }
+            // clusters of C CTAs (one per SM at the full budget) that can be resident at once
+            for (int C = 2; C <= kMaxCluster; ++C) {
+                cudaLaunchConfig_t cfg = {};
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeClusterDimension;
+                attr[0].val.clusterDim.x = C;
+                attr[0].val.clusterDim.y = 1;
+                attr[0].val.clusterDim.z = 1;
+                cfg.gridDim = dim3((unsigned)(p->sm_count / C * C));
+                cfg.blockDim = dim3(kSmemPlaneThreads);
+                cfg.dynamicSmemBytes = p->splanes_max_smem;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                int clusters = 0;
+                if (cudaOccupancyMaxActiveClusters(&clusters, (const void *)pool_cluster_planes_kernel<kSmemPlaneThreads>,
+                                                   &cfg) != cudaSuccess || clusters < 1) {
+                    cudaGetLastError();  // not fatal: fall back to one cluster per C SMs
+                    clusters = p->sm_count / C;
+                }
+                p->cluster_grid[C] = std::max(1, clusters) * C;
+            }
         }
         int per_sm = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pool_half_sweep_kernel, kVBlock, 0);
@@ -1297,14 +1526,18 @@ void micsa_pool_destroy(micsa_pool_t p) {
     cudaFree(p->d_counter);
     cudaFree(p->d_punits);
     cudaFree(p->d_npunits);
+    cudaFree(p->d_pustart);
     cudaFreeHost(p->h_punits);
     cudaFreeHost(p->h_npunits);
-    if (p->splanes_stream) {
-        cudaStreamSynchronize(p->splanes_stream);
-        cudaStreamDestroy(p->splanes_stream);
+    cudaFreeHost(p->h_pustart);
+    for (int C = 1; C <= kMaxCluster; ++C) {
+        if (p->splanes_stream[C]) {
+            cudaStreamSynchronize(p->splanes_stream[C]);
+            cudaStreamDestroy(p->splanes_stream[C]);
+        }
+        if (p->splanes_join[C]) cudaEventDestroy(p->splanes_join[C]);
     }
     if (p->splanes_fork) cudaEventDestroy(p->splanes_fork);
-    if (p->splanes_join) cudaEventDestroy(p->splanes_join);
     cudaFreeHost(p->h_units);
     cudaFreeHost(p->h_nunits);
     cudaFreeHost(p->h_vblocks);
@@ -1437,8 +1670,18 @@ int micsa_pool_submit(micsa_pool_t p, const micsa_job_desc *job, int64_t *job_id
     D.divC_l = fdC.l;
     D.resident = (p->resident_smem && multispin_smem_bytes(s.g) && multispin_smem_bytes(s.g) <= p->resident_smem) ? 1 : 0;
     D.use_planes = (p->planes_on && plane_eligible(d) && !D.resident) ? 1 : 0;
-    D.smem_planes = (D.use_planes && splane_split(msg_plane_words(s.g), d.n_replicas, p->splanes_smem).nrep > 0)
-                        ? (int32_t)p->splanes_smem : 0;
+    // shared memory: split over a cluster of one CTA per z word when on and a
+    // replica's slice fits, else the whole unit in one CTA when a replica fits
+    const int nzw = (d.L + 31) / 32;
+    D.smem_cluster = 0;
+    D.smem_planes = 0;
+    if (D.use_planes && p->splanes_cluster && nzw >= 2 && nzw <= kMaxCluster &&
+        splane_split((int64_t)d.L * s.g.P, d.n_replicas, p->splanes_smem).nrep > 0) {
+        D.smem_cluster = nzw;
+        D.smem_planes = (int32_t)p->splanes_smem;
+    } else if (D.use_planes && splane_split(msg_plane_words(s.g), d.n_replicas, p->splanes_smem).nrep > 0) {
+        D.smem_planes = (int32_t)p->splanes_smem;
+    }
     D.planes = D.use_planes ? reinterpret_cast<uint32_t *>(base + J.off_planes) : nullptr;
     D.bplanes = D.use_planes ? reinterpret_cast<const uint32_t *>(base + J.off_bplanes) : nullptr;
     if (D.use_planes) {  // the bonds never change: their planes are made once
@@ -1455,8 +1698,8 @@ int micsa_pool_submit(micsa_pool_t p, const micsa_job_desc *job, int64_t *job_id
 int micsa_pool_tick(micsa_pool_t p) {
     if (!p) return MICSA_E_INVALID_ARG;
     if (int rc = upload_tables(p)) return rc;
-    const int mask = (p->has_resident_jobs ? 1 : 0) | (p->has_stream_jobs ? 2 : 0) | (p->has_plane_jobs ? 4 : 0) |
-                     (p->has_splane_jobs ? 8 : 0);
+    int mask = (p->has_resident_jobs ? 1 : 0) | (p->has_stream_jobs ? 2 : 0) | (p->has_plane_jobs ? 4 : 0);
+    for (int C = 1; C <= kMaxCluster; ++C) mask |= p->h_npunits[C] > 0 ? (8 << (C - 1)) : 0;
     if (int rc = ensure_graph(p, mask)) return rc;
     if (p->graphs[mask]) {
         PCK(p, cudaGraphLaunch(p->graphs[mask], p->stream), "pool graph launch");
@@ -1641,6 +1884,12 @@ int micsa_pool_set_smem_planes(micsa_pool_t p, size_t smem_bytes, int blocks_per
     drop_pool_graphs(p);
     p->splanes_smem = smem_bytes / 16 * 16;
     p->splanes_grid = blocks_per_sm * p->sm_count;
+    return MICSA_OK;
+}
+
+int micsa_pool_set_smem_clusters(micsa_pool_t p, int on) {
+    if (!p) return MICSA_E_INVALID_ARG;
+    p->splanes_cluster = on != 0;
     return MICSA_OK;
 }
 

@@ -240,14 +240,17 @@ class FakeShapedPool:
     def __init__(self, cost, tick_sweeps=8):
         self.cost, self.tick_sweeps = cost, tick_sweeps
         self.shape, self.blocks, self.now, self.submitted, self.ticks = (4, 2), 0, 0.0, [], 0
-        self.smem = (200_000, 1)
+        self.smem = (200_000, 1, True)
 
     def smem_planes(self):
         return self.smem[0], 200_000, self.smem[1]
 
     def set_smem_planes(self, budget, bps):
         assert 0 <= budget <= 200_000 and 1 <= bps <= 8
-        self.smem = (budget, bps)
+        self.smem = (budget, bps) + self.smem[2:]
+
+    def set_smem_clusters(self, on):
+        self.smem = self.smem[:2] + (bool(on),)
 
     def __enter__(self):
         return self
@@ -295,7 +298,8 @@ def test_pool_autotuner_picks_the_fastest_shared_memory_setting():
     """Each shared-memory bit-plane setting is set on a fresh scratch pool before
     the jobs are admitted; the fastest setting wins and is part of the choice."""
     fake = FakeShapedPool(lambda shape, blocks: 1.0)
-    fake.smem_cost = lambda sm: {(0, 1): 1.0, (200_000, 1): 0.9, (100 << 10, 1): 0.6, (60 << 10, 1): 0.7}[sm]
+    fake.smem_cost = lambda sm: {(0, 1, False): 1.0, (200_000, 1, False): 0.9, (200_000, 1, True): 0.8,
+                                 (100 << 10, 1, False): 0.6, (100 << 10, 1, True): 0.5, (60 << 10, 1, False): 0.7}[sm]
     seen = []
 
     def factory():
@@ -303,12 +307,12 @@ def test_pool_autotuner_picks_the_fastest_shared_memory_setting():
         return fake
     jobs = [(48, 2, 1, 100, 10, 2.5, 0.5)]
     choice = autotune.tune_pool_for_jobs(factory, jobs, ticks=1, clock=lambda: fake.now)
-    assert choice["smem_planes"] == [100 << 10, 1]
-    assert seen == [0, 1, 2, 3]
-    assert choice["s_per_tick"] == pytest.approx(0.6)
+    assert choice["smem_planes"] == [100 << 10, 1, True]
+    assert seen == [0, 1, 2, 3, 4, 5]
+    assert choice["s_per_tick"] == pytest.approx(0.5)
     applied = FakeShapedPool(lambda shape, blocks: 1.0)
     autotune.apply_pool(applied, choice)
-    assert applied.smem == (100 << 10, 1)
+    assert applied.smem == (100 << 10, 1, True)
 
 
 def test_pool_autotuner_keeps_the_default_grid_when_no_grid_is_faster():

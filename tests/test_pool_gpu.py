@@ -43,7 +43,9 @@ def run_pool(jobs, K=16, arena=1 << 28, max_jobs=64, order=None, shape=None, res
         if planes is not None:
             p.set_planes(planes)
         if smem is not None:
-            p.set_smem_planes(*smem)
+            p.set_smem_planes(*smem[:2])
+            if len(smem) > 2:
+                p.set_smem_clusters(smem[2])
         if shape:
             p.set_shape(shape[0], shape[1])
             p.set_launch_config(shape[2])
@@ -342,14 +344,17 @@ def _plane_oracle(idx):
     return _PLANE_REF[idx]
 
 
-@pytest.mark.parametrize("smem", [(0, 1), (60 << 10, 2), (120 << 10, 1), (120 << 10, 2)])
+@pytest.mark.parametrize("smem", [(0, 1), (60 << 10, 2), (120 << 10, 1), (120 << 10, 2), (60 << 10, 1, False),
+                                  (120 << 10, 1, False), (232432, 1, False)])
 def test_pool_smem_plane_budgets_match_oracle(smem):
-    """The shared-memory bit-plane kernel at several budgets: off; 60 KB (one
-    replica per unit, bonds from the arena, the larger jobs on the global bit
-    planes); 120 KB (one replica beside its bond planes for L = 40, two replicas
-    without them for L = 48, one for L = 56 and 64), one or two CTAs per SM; the
-    default budget is covered by every other pool test. Final state, energies
-    and daemon energies equal the oracle's."""
+    """The shared-memory bit-plane kernels at several budgets: off; 60 KB and
+    120 KB with the units split over clusters of one CTA per z word (the default)
+    and in one CTA each (one replica per unit, bonds from the arena, the larger
+    jobs on the global bit planes at 60 KB; one replica beside its bond planes for
+    L = 40, two replicas without them for L = 48 at 120 KB), one or two CTAs per
+    SM; the whole budget in one CTA; the default (whole budget, clusters) is
+    covered by every other pool test. Final state, energies and daemon energies
+    equal the oracle's."""
     res = run_pool(JOBS_PLANES, K=4, smem=smem)
     for idx, job in enumerate(JOBS_PLANES):
         st, (e, a, _) = _plane_oracle(idx)
@@ -358,7 +363,7 @@ def test_pool_smem_plane_budgets_match_oracle(smem):
         assert_final_state(res[idx], st, f"{job} {smem}")
 
 
-@pytest.mark.parametrize("smem", [None, (100 << 10, 1)])
+@pytest.mark.parametrize("smem", [None, (100 << 10, 1), (100 << 10, 1, False), (232432, 1, False)])
 def test_pool_smem_plane_units_split_replicas_match_oracle(smem):
     """Jobs with more replicas than one shared-memory unit holds are split into
     replica ranges (the default budget: L = 48 x 8 replicas in units of two, L = 40
