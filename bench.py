@@ -79,7 +79,8 @@ def parse(argv=None):
                     help="sweeps per step (profiling runs only; reported numbers use the default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="headline leg only")
-    ap.add_argument("--profile-case", choices=["stream", "chains", "single", "chains_l320", "chains_l400",
+    ap.add_argument("--profile-case", choices=["stream", "chains", "chains_bps0", "single", "chains_l320",
+                                               "chains_l400", "chains_l400_bps0",
                                                "multispin", "planes", "planes_metro", "onchip", "tma", "pool",
                                                "batched", "plane_jobs_smem", "plane_jobs_global",
                                                "plane_jobs_smem_norefresh"],
@@ -309,6 +310,20 @@ def leg_roofline(micsa, timer, stream, L, peaks, n_plain=2000, choice=None):
     if choice is not None and choice.get("engine") == "stream":
         from paper_2506_16240_gb300 import autotune
         autotune.apply(g, choice)
+        if L != WORKLOAD["L"]:
+            # another lattice: the grid choice of the tuned shape (grid-stride loop over
+            # the resident capacity, or one thread per chunk) that is faster at this L
+            best = None
+            for bps in (-1, 0):
+                lc = g.launch_config()
+                g.set_launch_config(lc["words_per_thread"], lc["block"], bps, bool(lc["pdl"]), lc["graph_sweeps"])
+                g.run(np.full(1, 0.7), 10)
+                g.run(np.full(100, 0.7), 2 ** 31 - 1)
+                ms = timer(lambda: g.run(np.full(100, 0.7), 2 ** 31 - 1))
+                if best is None or ms < best[0]:
+                    best = (ms, bps)
+            lc = g.launch_config()
+            g.set_launch_config(lc["words_per_thread"], lc["block"], best[1], bool(lc["pdl"]), lc["graph_sweeps"])
     g.run(np.full(1, 0.7), 10)  # t = 0 refresh; the timed sweeps below have none
     # warm-up as long as the timed run (and longer than two graph lengths), so that
     # the sweep table is sized and the sweep graph captured before the timed
@@ -324,7 +339,8 @@ def leg_roofline(micsa, timer, stream, L, peaks, n_plain=2000, choice=None):
     peak = hbm if hbm else 6800.0
     achieved = bytes_per_launch / (launch_us * 1e-6) / 1e9
     chains = (choice or {}).get("chains", 1)
-    key = f"L={L} R={R} chains={chains} nw={shape['words_per_thread']} block={shape['block']}"
+    key = (f"L={L} R={R} chains={chains} nw={shape['words_per_thread']} block={shape['block']} "
+           f"bps={shape['blocks_per_sm']}")
     rec = traffic_record("half_sweep", key)
     state_bytes = L ** 3 * (2 * R + 1)  # spins and daemons of each replica, bond bytes of the sample
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -738,6 +754,8 @@ def leg_serving(micsa, torch, stream, n_jobs, peaks, n_cap=600, slots=256, K=128
 #   chains        the same lattice with the two replicas as two chains, 140 sweeps
 #   single        the same with both replicas in each launch (one chain)
 #   chains_l320, chains_l400  as chains at L = 320 (164 MB of state) and L = 400 (320 MB)
+#   chains_bps0, chains_l400_bps0  as chains and chains_l400 with one thread per chunk (no
+#                 grid-stride loop)
 #   multispin     L=32, 64 x 2: 128 sweeps, blocks of 64
 #   planes        L=160, 1 x 128, bit planes: 12 sweeps
 #   planes_metro  the same lattice, 12 Metropolis sweeps
@@ -761,10 +779,10 @@ def case_stream():
     return g.measure()[0]
 
 
-def case_chains(L=160, chains=2):
+def case_chains(L=160, chains=2, bps=-1):
     g = _micsa().Micsa(L, 1, 2, 3)
     g.set_engine("stream")
-    g.set_launch_config(4, 128, -1, True, 64)
+    g.set_launch_config(4, 128, bps, True, 64)
     g.set_replica_chains(chains)
     g.run(np.full(140, 0.7), 10)  # 2 graph replays of 64 sweeps + 12 direct
     return g.measure()[0]
@@ -888,6 +906,7 @@ def pool_breakdown(ticks=6, K=256):
 PROFILE_CASES = {"stream": case_stream, "chains": case_chains, "multispin": case_multispin,
                  "single": lambda: case_chains(160, 1), "chains_l320": lambda: case_chains(320),
                  "chains_l400": lambda: case_chains(400), "batched": case_batched,
+                 "chains_bps0": lambda: case_chains(160, 2, 0), "chains_l400_bps0": lambda: case_chains(400, 2, 0),
                  "plane_jobs_smem": case_plane_jobs, "plane_jobs_global": lambda: case_plane_jobs(False),
                  "plane_jobs_smem_norefresh": lambda: case_plane_jobs(True, interval=1 << 20),
                  "planes": case_planes, "planes_metro": case_planes_metro, "onchip": case_onchip,
