@@ -422,6 +422,15 @@ int micsa_pool_set_smem_planes(micsa_pool_t p, size_t smem_bytes, int blocks_per
  * identical either way. */
 int micsa_pool_set_smem_clusters(micsa_pool_t p, int on);
 
+/* For the jobs admitted from now on (off by default): a job with L <= 32 is
+ * advanced as bit planes in shared memory too, in units of as many of its
+ * replicas as fit 48 KB beside its bond planes, by a persistent launch of CTAs of
+ * 128 threads (four per SM) per tick; off: the shared-memory multispin kernel
+ * (one replica per CTA, one thread per plane word), which measured twice as fast
+ * on such lattices (a unit's word groups of four are few: 32 at L = 16). Results
+ * are identical either way. */
+int micsa_pool_set_small_planes(micsa_pool_t p, int on);
+
 /* The current budget, the largest the device allows, and the blocks per SM of
  * the shared-memory bit-plane path. Any pointer may be NULL. */
 int micsa_pool_get_smem_planes(micsa_pool_t p, size_t *smem_bytes, size_t *max_smem_bytes, int *blocks_per_sm);

@@ -333,6 +333,7 @@ SIGNATURES.update({
     "micsa_pool_set_planes": (_c.c_int, [_P, _c.c_int]),
     "micsa_pool_set_smem_planes": (_c.c_int, [_P, _c.c_size_t, _c.c_int]),
     "micsa_pool_set_smem_clusters": (_c.c_int, [_P, _c.c_int]),
+    "micsa_pool_set_small_planes": (_c.c_int, [_P, _c.c_int]),
     "micsa_pool_get_smem_planes": (_c.c_int, [_P, ctypes.POINTER(ctypes.c_size_t), ctypes.POINTER(ctypes.c_size_t),
                                               ctypes.POINTER(_c.c_int)]),
     "micsa_pool_last_error": (_c.c_char_p, [_P]),
@@ -465,6 +466,12 @@ class Pool:
         """Split the shared-memory units of the jobs admitted from now on (32 < L <= 128)
         over thread-block clusters of one CTA per z word; results do not depend on it."""
         self._check(lib().micsa_pool_set_smem_clusters(self.h, int(bool(on))))
+
+    def set_small_planes(self, on=True):
+        """Jobs with L <= 32 admitted from now on as bit planes in shared memory (CTAs of
+        128 threads) instead of the multispin kernel (the default, faster on such
+        lattices); results do not depend on it."""
+        self._check(lib().micsa_pool_set_small_planes(self.h, int(bool(on))))
 
     def smem_planes(self):
         """(budget bytes, the device's largest budget, blocks per SM) of the

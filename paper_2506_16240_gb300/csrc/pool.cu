@@ -66,6 +66,10 @@ constexpr int kMaxCluster = 4;  // clusters of 2..4 CTAs: L up to 128
 // SM, 256 threads for two or more (registers: about 120 per thread)
 constexpr int kSmemPlaneThreads = 512;
 constexpr int kSmemPlaneThreadsSmall = 256;
+// lattices with L <= 32: units of a few replicas in CTAs of 128 threads, four per SM
+constexpr int kSmallPlaneThreads = 128;
+constexpr int kSmallPlaneBlocks = 4;
+constexpr size_t kSmallPlaneSmem = 48 << 10;
 
 struct PoolTables {
     JobDesc *jobs;          // [max_jobs]
@@ -463,7 +467,9 @@ __device__ __forceinline__ void splane_group(const SplaneGeo &G, const uint32_t 
 // odd one, each the body of the global bit-plane kernel (msg_update) over the
 // CTA's word groups, the refresh at the job's refresh sweeps -- and convert
 // back. No state leaves the SM between the half-sweeps of a tick.
-template <int NT, int MINB>
+// IDX: the unit table's part and work counter: 1 for the units of L > 32 held in
+// one CTA, 0 for the small lattices (L <= 32; counter kMaxCluster + 1).
+template <int NT, int MINB, int IDX = 1>
 __global__ void __launch_bounds__(NT, MINB)
     pool_smem_planes_kernel(PoolTables T, const PlaneUnit *units, const int32_t *unit_start,
                             const int32_t *n_units, int *counters, int K) {
@@ -471,9 +477,9 @@ __global__ void __launch_bounds__(NT, MINB)
     pool_release();
     uint32_t *spl = pool_spl;
     __shared__ int s_unit;
-    const int n = n_units[1];
-    units += unit_start[1];  // the units held in one CTA
-    int *counter = counters + 1;
+    const int n = n_units[IDX];
+    units += unit_start[IDX];  // the units held in one CTA
+    int *counter = counters + (IDX == 0 ? kMaxCluster + 1 : IDX);
     for (;;) {
         if (threadIdx.x == 0) s_unit = atomicAdd(counter, 1);
         __syncthreads();
@@ -788,7 +794,7 @@ __global__ void __launch_bounds__(kVBlock) pool_best_copy_kernel(PoolTables T) {
 __global__ void pool_advance_kernel(JobDesc *jobs, int max_jobs, int K, int *counter) {
     pool_wait();
     pool_release();
-    if (blockIdx.x == 0 && threadIdx.x <= kMaxCluster) counter[threadIdx.x] = 0;  // the next tick's persistent kernels' work counters
+    if (blockIdx.x == 0 && threadIdx.x <= kMaxCluster + 1) counter[threadIdx.x] = 0;  // the next tick's persistent kernels' work counters
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < max_jobs; i += gridDim.x * blockDim.x) {
         JobDesc &J = jobs[i];
         if (!J.live) continue;
@@ -883,16 +889,19 @@ struct micsa_pool {
     size_t splanes_max_smem = 0;  // what the device allows the kernel
     int splanes_grid = 0;
     bool splanes_cluster = true;  // split the units of jobs with L > 32 over clusters (jobs admitted from now on)
+    bool small_planes = false;    // jobs with L <= 32 as bit planes in shared memory (else the multispin kernel)
+    int small_grid = 0;
     PlaneUnit *d_punits = nullptr, *h_punits = nullptr;
     // per cluster size C (index 1..kMaxCluster): first unit and unit count in the table
     int32_t *d_npunits = nullptr, *h_npunits = nullptr, *d_pustart = nullptr, *h_pustart = nullptr;
     int max_punits = 0;
     size_t splanes_launch_smem[kMaxCluster + 1] = {};  // the largest unit of each cluster size
     int cluster_grid[kMaxCluster + 1] = {};            // CTAs of the launch of each cluster size
-    cudaStream_t splanes_stream[kMaxCluster + 1] = {};
-    cudaEvent_t splanes_fork = nullptr, splanes_join[kMaxCluster + 1] = {};
-    cudaGraphExec_t graphs[128] = {};  // by part mask: 1 resident, 2 byte-streamed, 4 bit-plane jobs,
-                                       // 8 << (C - 1): bit-plane jobs in shared memory, units over C CTAs
+    cudaStream_t splanes_stream[kMaxCluster + 2] = {};  // [kMaxCluster + 1]: the small lattices' launch
+    cudaEvent_t splanes_fork = nullptr, splanes_join[kMaxCluster + 2] = {};
+    cudaGraphExec_t graphs[256] = {};  // by part mask: 1 resident, 2 byte-streamed, 4 bit-plane jobs,
+                                       // 8 << (C - 1): bit-plane jobs in shared memory, units over C CTAs,
+                                       // 8 << kMaxCluster: the small lattices' units
     std::string err;
 };
 
@@ -1014,7 +1023,8 @@ JobSizes job_sizes(const micsa_job_desc &d) {
     s.thr = sizeof(uint64_t) * 3 * (size_t)s.n_refresh;
     const size_t WP = (size_t)msg_plane_words(s.g);
     s.planes = plane_eligible(d) ? sizeof(uint32_t) * 6 * WP * (size_t)d.n_replicas : 0;
-    s.bplanes = plane_eligible(d) ? sizeof(uint32_t) * 12 * WP : 0;
+    // bond planes also for the small lattices (L <= 32), which the shared-memory kernel can take
+    s.bplanes = (plane_eligible(d) || d.L <= 32) ? sizeof(uint32_t) * 12 * WP : 0;
     return s;
 }
 
@@ -1067,8 +1077,9 @@ int upload_tables(micsa_pool_t p) {
                     p->h_vblocks[nvb++] = VBlock{i, (int16_t)r, 0, (int32_t)c};
                 }
             if (pass == 1 && J.smem_planes) {
-                // one CTA per unit, or a cluster of C CTAs holding one z word each
-                const int C = J.smem_cluster > 1 ? J.smem_cluster : 1;
+                // one CTA per unit (C = 1; small lattices: C = 0, CTAs of 128 threads), or a
+                // cluster of C CTAs holding one z word each
+                const int C = J.geo.L <= 32 ? 0 : J.smem_cluster > 1 ? J.smem_cluster : 1;
                 const int64_t words = C > 1 ? (int64_t)J.geo.L * J.geo.P : msg_plane_words(J.geo);
                 const SplaneSplit sp = splane_split(words, J.R, J.smem_planes);
                 for (int r0 = 0; r0 < J.R; r0 += sp.nrep) {
@@ -1184,9 +1195,9 @@ int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
     }
     // the bit-plane jobs held in shared memory: one persistent launch per cluster
     // size present (bit 8 << (C - 1) of the mask), each on its own branch
-    const bool splanes = (mask & (((1 << kMaxCluster) - 1) << 3)) != 0;
+    const bool splanes = (mask & (((1 << (kMaxCluster + 1)) - 1) << 3)) != 0;
     if (splanes) PCK(p, cudaEventRecord(p->splanes_fork, st), "smem planes fork event");
-    for (int C = 1; C <= kMaxCluster; ++C) {
+    for (int C = 1; C <= kMaxCluster + 1; ++C) {
         if (!(mask & (8 << (C - 1)))) continue;
         cudaStream_t ss = p->splanes_stream[C];
         PCK(p, cudaStreamWaitEvent(ss, p->splanes_fork, 0), "smem planes fork wait");
@@ -1194,10 +1205,14 @@ int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
         void *args[] = {&T, &p->d_punits, &p->d_pustart, &p->d_npunits, &p->d_counter, &K};
         cudaLaunchConfig_t cfg = {};
         cudaLaunchAttribute attr[1];
-        cfg.dynamicSmemBytes = p->splanes_launch_smem[C];
+        cfg.dynamicSmemBytes = p->splanes_launch_smem[C == kMaxCluster + 1 ? 0 : C];
         cfg.stream = ss;
         const void *fn;
-        if (C == 1) {
+        if (C == kMaxCluster + 1) {  // the small lattices
+            cfg.gridDim = dim3(p->small_grid);
+            cfg.blockDim = dim3(kSmallPlaneThreads);
+            fn = (const void *)pool_smem_planes_kernel<kSmallPlaneThreads, kSmallPlaneBlocks, 0>;
+        } else if (C == 1) {
             const bool small = p->splanes_grid > p->sm_count;  // two or more CTAs per SM
             cfg.gridDim = dim3(p->splanes_grid);
             cfg.blockDim = dim3(small ? kSmemPlaneThreadsSmall : kSmemPlaneThreads);
@@ -1279,7 +1294,7 @@ int enqueue_tick(micsa_pool_t p, cudaStream_t st, int mask) {
     if (planes)
         for (int part = 0; part < p->chains; ++part)
             PCK(p, cudaStreamWaitEvent(st, p->planes_join[part], 0), "planes join wait");
-    for (int C = 1; C <= kMaxCluster; ++C)
+    for (int C = 1; C <= kMaxCluster + 1; ++C)
         if (mask & (8 << (C - 1))) PCK(p, cudaStreamWaitEvent(st, p->splanes_join[C], 0), "smem planes join wait");
     if (streamed || planes || splanes) {
         int K = p->K;
@@ -1304,7 +1319,7 @@ int tick_launches(micsa_pool_t p, int mask) {
     const int streamed = (mask & 2) ? 2 * p->chains * p->K : 0;
     const int planes = (mask & 4) ? p->chains * (2 * p->K + 2) : 0;
     int splanes = 0;
-    for (int C = 1; C <= kMaxCluster; ++C) splanes += (mask & (8 << (C - 1))) ? 1 : 0;
+    for (int C = 1; C <= kMaxCluster + 1; ++C) splanes += (mask & (8 << (C - 1))) ? 1 : 0;
     return resident + streamed + planes + splanes + ((mask & ~1) ? 3 : 0) + 1;
 }
 
@@ -1410,12 +1425,12 @@ int micsa_pool_create(size_t arena_bytes, int max_jobs, int tick_sweeps, micsa_p
         p->max_units = max_jobs * kPoolMaxR;
         if ((e = cudaMalloc(&p->d_units, sizeof(ResidentUnit) * (size_t)p->max_units)) != cudaSuccess ||
             (e = cudaMalloc(&p->d_nunits, sizeof(int32_t))) != cudaSuccess ||
-            (e = cudaMalloc(&p->d_counter, (kMaxCluster + 1) * sizeof(int))) != cudaSuccess ||
+            (e = cudaMalloc(&p->d_counter, (kMaxCluster + 2) * sizeof(int))) != cudaSuccess ||
             (e = cudaMallocHost(&p->h_units, sizeof(ResidentUnit) * (size_t)p->max_units)) != cudaSuccess ||
             (e = cudaMallocHost(&p->h_nunits, sizeof(int32_t))) != cudaSuccess) { bail(MICSA_E_OOM); break; }
         *p->h_nunits = 0;
         if ((e = cudaMemsetAsync(p->d_nunits, 0, sizeof(int32_t), p->stream)) != cudaSuccess ||
-            (e = cudaMemsetAsync(p->d_counter, 0, (kMaxCluster + 1) * sizeof(int), p->stream)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
+            (e = cudaMemsetAsync(p->d_counter, 0, (kMaxCluster + 2) * sizeof(int), p->stream)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
         // bit-plane jobs in shared memory: one CTA of kSmemPlaneThreads per unit, the budget
         // the device allows a block (opt-in) less the kernel's static shared memory
         p->max_punits = max_jobs * kPoolMaxR;
@@ -1429,7 +1444,7 @@ int micsa_pool_create(size_t arena_bytes, int max_jobs, int tick_sweeps, micsa_p
         if ((e = cudaMemsetAsync(p->d_npunits, 0, sizeof(int32_t) * (kMaxCluster + 1), p->stream)) != cudaSuccess ||
             (e = cudaMemsetAsync(p->d_pustart, 0, sizeof(int32_t) * (kMaxCluster + 1), p->stream)) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&p->splanes_fork, cudaEventDisableTiming)) != cudaSuccess) { bail(MICSA_E_CUDA); break; }
-        for (int C = 1; C <= kMaxCluster && e == cudaSuccess; ++C)
+        for (int C = 1; C <= kMaxCluster + 1 && e == cudaSuccess; ++C)
             if ((e = cudaStreamCreateWithFlags(&p->splanes_stream[C], cudaStreamNonBlocking)) == cudaSuccess)
                 e = cudaEventCreateWithFlags(&p->splanes_join[C], cudaEventDisableTiming);
         if (e != cudaSuccess) { bail(MICSA_E_CUDA); break; }
@@ -1450,11 +1465,14 @@ int micsa_pool_create(size_t arena_bytes, int max_jobs, int tick_sweeps, micsa_p
             p->splanes_smem = p->splanes_max_smem;
             p->splanes_grid = p->sm_count;  // one CTA per SM at the full budget
             if (p->splanes_max_smem &&
-                (e = cudaFuncSetAttribute(pool_cluster_planes_kernel<kSmemPlaneThreads>,
-                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->splanes_max_smem)) != cudaSuccess) {
+                ((e = cudaFuncSetAttribute(pool_cluster_planes_kernel<kSmemPlaneThreads>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p->splanes_max_smem)) != cudaSuccess ||
+                 (e = cudaFuncSetAttribute(pool_smem_planes_kernel<kSmallPlaneThreads, kSmallPlaneBlocks, 0>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmallPlaneSmem)) != cudaSuccess)) {
                 bail(MICSA_E_CUDA);
                 break;
             }
+            p->small_grid = kSmallPlaneBlocks * p->sm_count;
             // clusters of C CTAs (one per SM at the full budget) that can be resident at once
             for (int C = 2; C <= kMaxCluster; ++C) {
                 cudaLaunchConfig_t cfg = {};
@@ -1530,7 +1548,7 @@ void micsa_pool_destroy(micsa_pool_t p) {
     cudaFreeHost(p->h_punits);
     cudaFreeHost(p->h_npunits);
     cudaFreeHost(p->h_pustart);
-    for (int C = 1; C <= kMaxCluster; ++C) {
+    for (int C = 1; C <= kMaxCluster + 1; ++C) {
         if (p->splanes_stream[C]) {
             cudaStreamSynchronize(p->splanes_stream[C]);
             cudaStreamDestroy(p->splanes_stream[C]);
@@ -1668,14 +1686,20 @@ int micsa_pool_submit(micsa_pool_t p, const micsa_job_desc *job, int64_t *job_id
     const FastDiv fdC = make_fastdiv((uint32_t)(s.g.W / D.nw));
     D.divC_m = fdC.m;
     D.divC_l = fdC.l;
-    D.resident = (p->resident_smem && multispin_smem_bytes(s.g) && multispin_smem_bytes(s.g) <= p->resident_smem) ? 1 : 0;
-    D.use_planes = (p->planes_on && plane_eligible(d) && !D.resident) ? 1 : 0;
+    // L <= 32: bit planes in shared memory (units of a few replicas in CTAs of 128
+    // threads) when on, else the multispin kernel
+    const bool small_planes = p->small_planes && p->splanes_max_smem && d.L <= 32;
+    D.resident = (!small_planes && p->resident_smem && multispin_smem_bytes(s.g) &&
+                  multispin_smem_bytes(s.g) <= p->resident_smem) ? 1 : 0;
+    D.use_planes = ((p->planes_on && plane_eligible(d) && !D.resident) || small_planes) ? 1 : 0;
     // shared memory: split over a cluster of one CTA per z word when on and a
     // replica's slice fits, else the whole unit in one CTA when a replica fits
     const int nzw = (d.L + 31) / 32;
     D.smem_cluster = 0;
     D.smem_planes = 0;
-    if (D.use_planes && p->splanes_cluster && nzw >= 2 && nzw <= kMaxCluster &&
+    if (small_planes) {
+        D.smem_planes = (int32_t)kSmallPlaneSmem;
+    } else if (D.use_planes && p->splanes_cluster && nzw >= 2 && nzw <= kMaxCluster &&
         splane_split((int64_t)d.L * s.g.P, d.n_replicas, p->splanes_smem).nrep > 0) {
         D.smem_cluster = nzw;
         D.smem_planes = (int32_t)p->splanes_smem;
@@ -1700,6 +1724,7 @@ int micsa_pool_tick(micsa_pool_t p) {
     if (int rc = upload_tables(p)) return rc;
     int mask = (p->has_resident_jobs ? 1 : 0) | (p->has_stream_jobs ? 2 : 0) | (p->has_plane_jobs ? 4 : 0);
     for (int C = 1; C <= kMaxCluster; ++C) mask |= p->h_npunits[C] > 0 ? (8 << (C - 1)) : 0;
+    mask |= p->h_npunits[0] > 0 ? (8 << kMaxCluster) : 0;  // the small lattices
     if (int rc = ensure_graph(p, mask)) return rc;
     if (p->graphs[mask]) {
         PCK(p, cudaGraphLaunch(p->graphs[mask], p->stream), "pool graph launch");
@@ -1890,6 +1915,12 @@ int micsa_pool_set_smem_planes(micsa_pool_t p, size_t smem_bytes, int blocks_per
 int micsa_pool_set_smem_clusters(micsa_pool_t p, int on) {
     if (!p) return MICSA_E_INVALID_ARG;
     p->splanes_cluster = on != 0;
+    return MICSA_OK;
+}
+
+int micsa_pool_set_small_planes(micsa_pool_t p, int on) {
+    if (!p) return MICSA_E_INVALID_ARG;
+    p->small_planes = on != 0;
     return MICSA_OK;
 }
 

@@ -73,9 +73,11 @@ def test_pool_job_bytes_counts_plane_storage_for_plane_jobs(lib):
             half = L * L * P
             n_refresh = max(1, (n + r - 1) // r)
             expect = align(2 * half) + 2 * align(R * 2 * half) + align(R * max(L ** 3, 2 * half)) + align(24 * n_refresh)
-            if L % 2 == 0 and L > 32:  # rows of P plane words
-                WP = L * ((L + 31) // 32) * P
+            WP = L * ((L + 31) // 32) * P  # rows of P plane words
+            if L % 2 == 0 and L > 32:
                 expect += align(4 * 6 * WP * R) + align(4 * 12 * WP)
+            elif L <= 32:  # bond planes only (the shared-memory path of small lattices)
+                expect += align(4 * 12 * WP)
             assert micsa.Pool.job_bytes(L, R, n, r) == expect, (L, R, n, r)
 
 

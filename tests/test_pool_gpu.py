@@ -380,6 +380,34 @@ def test_pool_smem_plane_units_split_replicas_match_oracle(smem):
         assert_final_state(res[idx], st, jobs[idx])
 
 
+@pytest.mark.parametrize("small", [True, False])
+def test_pool_small_lattices_on_both_paths_match_oracle(small):
+    """Jobs with L <= 32 (odd L / 2, tiny lattices, up to eight replicas) as bit planes
+    in shared memory (CTAs of 128 threads, units of several replicas) or on the
+    multispin kernel: final state and energies equal the oracle's either way."""
+    jobs = [(2, 3, 71, 30, 2, 3.0, 0.5), (6, 4, 72, 33, 1, 3.0, 0.3), (10, 3, 73, 40, 7, 2.0, 1.0),
+            (16, 8, 74, 25, 5, 2.5, 0.5), (18, 1, 75, 64, 9, 2.5, 0.4), (24, 2, 76, 16, 16, 1.5, 1.5),
+            (30, 5, 77, 21, 4, 2.0, 0.7), (32, 2, 78, 50, 20, 2.5, 0.5)]
+    with micsa.Pool(1 << 28, 64, 8) as p:
+        p.set_small_planes(small)
+        ids = [p.submit(*j) for j in jobs]
+        res = {}
+        while len(res) < len(ids):
+            p.tick()
+            for k, jid in enumerate(ids):
+                if k not in res:
+                    r = p.poll(jid, final_state=True)
+                    if r is not None:
+                        res[k] = r
+    for k, (L, R, seed, n, interval, T0, T1) in enumerate(jobs):
+        st = O.create(L, 1, R, seed)
+        O.run(st, micsa.linear_schedule(T0, T1, n), interval)
+        e, a, _ = O.measure(st)
+        np.testing.assert_array_equal(res[k]["energy"], e, err_msg=str(jobs[k]))
+        np.testing.assert_array_equal(res[k]["aux"], a, err_msg=str(jobs[k]))
+        assert_final_state(res[k], st, jobs[k])
+
+
 def test_pool_smem_planes_rejects_bad_values():
     with micsa.Pool(1 << 24, 4, 4) as p:
         for budget, bps in [(1 << 30, 1), (1 << 16, 0), (1 << 16, 9)]:
