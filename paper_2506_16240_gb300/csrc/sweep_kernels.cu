@@ -58,17 +58,55 @@ __device__ __forceinline__ void half_sweep_body(const SweepArgs &a) {
             }
 }
 
-// FULL: rows without padding (P == L / 2), see update_chunk.
-template <int NW, bool METRO, bool FULL = false>
+// One chunk per thread: the grid covers every (chunk, sample, replica) exactly
+// once (x: the chunks of a sample, y: samples, z: groups of blockDim.y
+// replicas), so the body runs without the loops of half_sweep_body; refresh and
+// plain sweeps take separate copies of the update under a branch that is
+// uniform over the grid, so neither carries the other's code.
+template <int NW, bool METRO, bool FULL>
+__device__ __forceinline__ void half_sweep_flat_body(const SweepArgs &a) {
+    const int64_t kidx = a.k + (a.cursor ? *a.cursor : 0);
+    const SweepParam prm = a.params[kidx];
+    grid_dependency_wait();
+    grid_launch_dependents();
+    const Geometry g = a.geo;
+    const uint32_t per_sample = (uint32_t)g.L * g.L * (g.W / NW);
+    const uint32_t q = blockIdx.x * blockDim.x + threadIdx.x;
+    const int r = a.r0 + (int)(blockIdx.z * blockDim.y + threadIdx.y);
+    if (q >= per_sample || r >= a.r1) return;
+    const uint32_t row = fdiv(q, a.div_chunks);
+    const int c = (int)(q - row * a.div_chunks.d);
+    const int64_t gid = (int64_t)blockIdx.y * a.R + r;
+    const int64_t fam = gid * a.gamma + prm.alpha;
+    int8_t *spins = a.spins + gid * 2 * g.half;
+    uint8_t *daemons = a.daemons + fam * 2 * g.half;
+    const uint8_t *bonds = a.bonds + (int64_t)blockIdx.y * 2 * g.half;
+    if (METRO)
+        update_chunk<NW, true, false, FULL>(g, spins, daemons, bonds, a.parity, (int)row, c, (uint32_t)gid, a.key0,
+                                            a.key1, prm.t, false, prm.th0, prm.th1, prm.th2, a.div_L);
+    else if (prm.mode == kModeRefresh)
+        update_chunk<NW, false, false, FULL>(g, spins, daemons, bonds, a.parity, (int)row, c, (uint32_t)fam, a.key0,
+                                             a.key1, prm.t, true, prm.th0, prm.th1, prm.th2, a.div_L);
+    else
+        update_chunk<NW, false, false, FULL>(g, spins, daemons, bonds, a.parity, (int)row, c, (uint32_t)fam, a.key0,
+                                             a.key1, prm.t, false, prm.th0, prm.th1, prm.th2, a.div_L);
+}
+
+// FULL: rows without padding (P == L / 2), see update_chunk. FLAT: one chunk
+// per thread (half_sweep_flat_body), else the grid-stride loops of
+// half_sweep_body (any grid).
+template <int NW, bool METRO, bool FULL = false, bool FLAT = false>
 __global__ void __launch_bounds__(256) half_sweep_kernel(SweepArgs a) {
-    half_sweep_body<NW, METRO, FULL>(a);
+    if constexpr (FLAT) half_sweep_flat_body<NW, METRO, FULL>(a);
+    else half_sweep_body<NW, METRO, FULL>(a);
 }
 
 // The same kernel with registers capped at 64 per thread (8 blocks of 128
 // threads per SM): more warps in flight for the latency-bound L2-resident case.
-template <int NW, bool METRO, bool FULL = false>
+template <int NW, bool METRO, bool FULL = false, bool FLAT = false>
 __global__ void __launch_bounds__(128, 8) half_sweep_kernel_rc(SweepArgs a) {
-    half_sweep_body<NW, METRO, FULL>(a);
+    if constexpr (FLAT) half_sweep_flat_body<NW, METRO, FULL>(a);
+    else half_sweep_body<NW, METRO, FULL>(a);
 }
 
 // Two rows per thread (rows without padding, MicSA): thread q of a sample takes
@@ -187,11 +225,14 @@ static cudaError_t launch_variant(const SweepArgs &a0, const LaunchConfig &lc, c
     const dim3 blk = block_shape(a.r1 - a.r0, lc.regcap && lc.block > 128 ? 128 : lc.block);
     int64_t gx = (per_sample + blk.x - 1) / blk.x;
     int64_t gy = a.S < 65535 ? a.S : 65535;
+    // no grid cap and every sample on its own grid row: one chunk per thread
+    const bool flat = lc.max_blocks <= 0 && a.S <= 65535;
+    const int64_t gz = flat ? (a.r1 - a.r0 + blk.y - 1) / blk.y : 1;
     if (lc.max_blocks > 0 && gx * gy > lc.max_blocks) {  // grid-stride cap over chunks
         gx = lc.max_blocks / gy > 0 ? lc.max_blocks / gy : 1;
     }
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((unsigned)gx, (unsigned)gy);
+    cfg.gridDim = dim3((unsigned)gx, (unsigned)gy, (unsigned)gz);
     cfg.blockDim = blk;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -200,6 +241,13 @@ static cudaError_t launch_variant(const SweepArgs &a0, const LaunchConfig &lc, c
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     const bool full = a.geo.P == a.geo.Lh;
+    if (flat) {
+        if (lc.regcap)
+            return full ? cudaLaunchKernelEx(&cfg, half_sweep_kernel_rc<NW, METRO, true, true>, a)
+                        : cudaLaunchKernelEx(&cfg, half_sweep_kernel_rc<NW, METRO, false, true>, a);
+        return full ? cudaLaunchKernelEx(&cfg, half_sweep_kernel<NW, METRO, true, true>, a)
+                    : cudaLaunchKernelEx(&cfg, half_sweep_kernel<NW, METRO, false, true>, a);
+    }
     if (lc.regcap)
         return full ? cudaLaunchKernelEx(&cfg, half_sweep_kernel_rc<NW, METRO, true>, a)
                     : cudaLaunchKernelEx(&cfg, half_sweep_kernel_rc<NW, METRO, false>, a);
