@@ -206,9 +206,11 @@ __global__ void advance_cursor_kernel(int64_t *cursor, int64_t step) {
 }
 
 // Block = (chunks per block) x (replica rows, at most 8); `block` is the
-// requested total thread count, the chunk dimension a multiple of 32.
+// requested total thread count and an upper bound on it (the register-capped
+// kernels take at most 128), the chunk dimension a multiple of 32.
 dim3 block_shape(int R, int block) {
-    const int ry = R < 8 ? R : 8;
+    int ry = R < 8 ? R : 8;
+    if (ry > block / 32) ry = block / 32 > 0 ? block / 32 : 1;
     int cx = block / ry;
     cx = cx < 32 ? 32 : (cx / 32) * 32;
     while (cx > 32 && cx * ry > 256) cx -= 32;

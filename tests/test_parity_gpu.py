@@ -234,6 +234,36 @@ def test_replicas_in_one_thread_match_oracle(L, S, R, gamma, cfg):
         assert_same_state(g, st, f"L={L} S={S} R={R} gamma={gamma} {cfg}")
 
 
+@pytest.mark.parametrize("L,S,R,gamma", [(16, 3, 11, 1), (18, 2, 9, 1), (24, 2, 3, 3), (20, 1, 17, 2)])
+@pytest.mark.parametrize("cfg", [(4, 128, 0, 1, 64), (2, 256, 0, 0, 0), (1, 64, 0, 1, 8), (4 | 256, 128, 0, 1, 16)])
+def test_one_chunk_per_thread_matches_oracle(L, S, R, gamma, cfg):
+    """The uncapped grid (blocks_per_sm 0) runs the loop-free body: one chunk per
+    thread over a (chunks, samples, replica groups) grid, refresh and plain
+    sweeps as separate copies. Several samples, more replicas than one block's
+    replica rows (a second grid layer of replica groups, partly idle), padded
+    rows (L = 18, 20), gamma daemon families, Metropolis sweeps and the
+    register-capped kernel (at most 128 threads a block): same bits as the
+    oracle."""
+    n, interval = 48, 5
+    sched = np.linspace(2.4, 0.5, n)
+    with micsa.Micsa(L, S, R, 313 + L, gamma=gamma) as g:
+        g.set_engine("stream")
+        g.set_launch_config(*cfg)
+        assert g.launch_config()["blocks_per_sm"] == 0
+        st = O.create(L, S, R, 313 + L, gamma=gamma)
+        if gamma == 1:
+            g.run(sched[:20], interval)
+            O.run(st, sched[:20], interval)
+            g.run_metropolis(sched[20:30])
+            O.run_metropolis(st, sched[20:30])
+            g.run(sched[30:], interval)
+            O.run(st, sched[30:], interval)
+        else:
+            g.run(sched, interval)
+            O.run_ex(st, sched, interval)
+        assert_same_state(g, st, f"L={L} S={S} R={R} gamma={gamma} {cfg}")
+
+
 @pytest.mark.parametrize("L", [16, 18, 32, 160])
 def test_launch_configs_agree(L):
     """Every launch shape (vector width, block, grid-stride cap, PDL, graph
