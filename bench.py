@@ -702,7 +702,9 @@ def leg_serving(micsa, torch, stream, n_jobs, peaks, n_cap=600, slots=256, K=128
     from paper_2506_16240_gb300 import autotune, serve
     cap_reqs = serve.poisson_stream(n_cap, 1e6, seed=55)
     desc = [(r.L, r.n_replicas, r.seed, r.n_sweeps, r.refresh_interval, r.T_start, r.T_end) for r in cap_reqs[:slots]]
-    choice = autotune.tune_pool_for_jobs(lambda: micsa.Pool(16 << 30, slots, 32), desc)
+    # tuned at the serving pool's own tick length: the shared-memory path moves a job's
+    # state in and out once per tick, so shorter ticks would understate it
+    choice = autotune.tune_pool_for_jobs(lambda: micsa.Pool(16 << 30, slots, K), desc)
     with micsa.Pool(16 << 30, slots, K) as p:
         autotune.apply_pool(p, choice)
         budget = p.smem_planes()[0]

@@ -183,7 +183,7 @@ LaunchConfig effective_config(micsa_t h, bool metro) {
     LaunchConfig lc = h->lc;
     lc.nw = vector_words(h->geo, lc.nw);
     if (h->blocks_per_sm < 0) {
-        const dim3 b = block_shape(h->R, lc.regcap && lc.block > 128 ? 128 : lc.block);
+        const dim3 b = block_shape(h->R, lc.regcap && lc.block > 128 ? 128 : lc.block, lc.regcap ? 128 : 256);
         const bool full = !metro && h->geo.P == h->geo.Lh;
         const int per_sm = lc.pairs && full  ? max_resident_blocks_pairs(lc.nw, (int)(b.x * b.y))
                            : lc.reps && full ? max_resident_blocks_reps(lc.nw, lc.block)

@@ -217,7 +217,7 @@ int vector_words(const Geometry &g, int want);
 int max_resident_blocks(bool metro, int nw, int block, bool regcap);
 int max_resident_blocks_pairs(int nw, int block);
 int max_resident_blocks_reps(int nw, int block);
-dim3 block_shape(int R, int block);
+dim3 block_shape(int R, int block, int max_threads);
 
 // initialisation, layout conversion and measurement (init_measure.cu)
 cudaError_t launch_init_couplings(uint8_t *bonds, Geometry g, int S, uint32_t k0, uint32_t k1,

@@ -206,14 +206,15 @@ __global__ void advance_cursor_kernel(int64_t *cursor, int64_t step) {
 }
 
 // Block = (chunks per block) x (replica rows, at most 8); `block` is the
-// requested total thread count and an upper bound on it (the register-capped
-// kernels take at most 128), the chunk dimension a multiple of 32.
-dim3 block_shape(int R, int block) {
+// requested total thread count, the chunk dimension a multiple of 32, and the
+// block never exceeds max_threads (the kernel's launch bound: 128 for the
+// register-capped kernels, 256 for the others).
+dim3 block_shape(int R, int block, int max_threads) {
     int ry = R < 8 ? R : 8;
-    if (ry > block / 32) ry = block / 32 > 0 ? block / 32 : 1;
+    if (ry > max_threads / 32) ry = max_threads / 32;
     int cx = block / ry;
     cx = cx < 32 ? 32 : (cx / 32) * 32;
-    while (cx > 32 && cx * ry > 256) cx -= 32;
+    while (cx > 32 && cx * ry > max_threads) cx -= 32;
     return dim3((unsigned)cx, (unsigned)ry);
 }
 
@@ -224,7 +225,7 @@ static cudaError_t launch_variant(const SweepArgs &a0, const LaunchConfig &lc, c
     a.div_chunks = make_fastdiv((uint32_t)chunks);
     a.div_L = make_fastdiv((uint32_t)a.geo.L);
     const int64_t per_sample = (int64_t)a.geo.L * a.geo.L * chunks;
-    const dim3 blk = block_shape(a.r1 - a.r0, lc.regcap && lc.block > 128 ? 128 : lc.block);
+    const dim3 blk = block_shape(a.r1 - a.r0, lc.regcap && lc.block > 128 ? 128 : lc.block, lc.regcap ? 128 : 256);
     int64_t gx = (per_sample + blk.x - 1) / blk.x;
     int64_t gy = a.S < 65535 ? a.S : 65535;
     // no grid cap and every sample on its own grid row: one chunk per thread
@@ -270,7 +271,7 @@ static cudaError_t launch_pairs(const SweepArgs &a0, const LaunchConfig &lc, cud
     a.div_chunks = make_fastdiv((uint32_t)chunks);
     a.div_half_L = make_fastdiv((uint32_t)(a.geo.L / 2));
     const int64_t per_sample = (int64_t)a.geo.L * (a.geo.L / 2) * chunks;
-    const dim3 blk = block_shape(a.r1 - a.r0, lc.block);
+    const dim3 blk = block_shape(a.r1 - a.r0, lc.block, 256);
     int64_t gx = (per_sample + blk.x - 1) / blk.x;
     int64_t gy = a.S < 65535 ? a.S : 65535;
     if (lc.max_blocks > 0 && gx * gy > lc.max_blocks) gx = lc.max_blocks / gy > 0 ? lc.max_blocks / gy : 1;
