@@ -1097,6 +1097,14 @@ int upload_tables(micsa_pool_t p) {
                 }
             }
         }
+    // the shared-memory units longest first (site updates per sweep, L^3 x replicas), so
+    // that the persistent kernels' work counter hands them out in that order and the
+    // tick ends close to its longest unit
+    for (int C = 0; C <= kMaxCluster; ++C)
+        std::stable_sort(units_c[C].begin(), units_c[C].end(), [&](const PlaneUnit &a, const PlaneUnit &b) {
+            const int64_t La = p->h_jobs[a.slot].geo.L, Lb = p->h_jobs[b.slot].geo.L;
+            return La * La * La * a.nrep > Lb * Lb * Lb * b.nrep;
+        });
     int nvb_stream = 0;
     for (int i = 0; i < nvb; ++i)
         if (!p->h_jobs[p->h_vblocks[i].slot].use_planes) nvb_stream = i + 1;
