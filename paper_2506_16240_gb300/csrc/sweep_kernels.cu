@@ -66,7 +66,20 @@ __device__ __forceinline__ void half_sweep_body(const SweepArgs &a) {
 template <int NW, bool METRO, bool FULL>
 __device__ __forceinline__ void half_sweep_flat_body(const SweepArgs &a) {
     const int64_t kidx = a.k + (a.cursor ? *a.cursor : 0);
-    const SweepParam prm = a.params[kidx];
+    const SweepParam *pp = a.params + kidx;
+    // Only what selects the copy and the daemon family is read before the wait:
+    // every field read there is a load on every sweep's path. The sweep index
+    // and cut points of a refresh sweep are read in its own copy (a tenth of the
+    // sweeps or fewer); Metropolis needs them on every sweep.
+    const int mode = pp->mode, alpha = pp->alpha;
+    int64_t t = 0;
+    uint64_t th0 = 0, th1 = 0, th2 = 0;
+    if constexpr (METRO) {
+        t = pp->t;
+        th0 = pp->th0;
+        th1 = pp->th1;
+        th2 = pp->th2;
+    }
     grid_dependency_wait();
     grid_launch_dependents();
     const Geometry g = a.geo;
@@ -77,19 +90,19 @@ __device__ __forceinline__ void half_sweep_flat_body(const SweepArgs &a) {
     const uint32_t row = fdiv(q, a.div_chunks);
     const int c = (int)(q - row * a.div_chunks.d);
     const int64_t gid = (int64_t)blockIdx.y * a.R + r;
-    const int64_t fam = gid * a.gamma + prm.alpha;
+    const int64_t fam = gid * a.gamma + alpha;
     int8_t *spins = a.spins + gid * 2 * g.half;
     uint8_t *daemons = a.daemons + fam * 2 * g.half;
     const uint8_t *bonds = a.bonds + (int64_t)blockIdx.y * 2 * g.half;
     if (METRO)
         update_chunk<NW, true, false, FULL>(g, spins, daemons, bonds, a.parity, (int)row, c, (uint32_t)gid, a.key0,
-                                            a.key1, prm.t, false, prm.th0, prm.th1, prm.th2, a.div_L);
-    else if (prm.mode == kModeRefresh)
+                                            a.key1, t, false, th0, th1, th2, a.div_L);
+    else if (mode == kModeRefresh)
         update_chunk<NW, false, false, FULL>(g, spins, daemons, bonds, a.parity, (int)row, c, (uint32_t)fam, a.key0,
-                                             a.key1, prm.t, true, prm.th0, prm.th1, prm.th2, a.div_L);
-    else
+                                             a.key1, pp->t, true, pp->th0, pp->th1, pp->th2, a.div_L);
+    else  // a plain sweep uses neither the sweep index nor cut points
         update_chunk<NW, false, false, FULL>(g, spins, daemons, bonds, a.parity, (int)row, c, (uint32_t)fam, a.key0,
-                                             a.key1, prm.t, false, prm.th0, prm.th1, prm.th2, a.div_L);
+                                             a.key1, 0, false, 0, 0, 0, a.div_L);
 }
 
 // FULL: rows without padding (P == L / 2), see update_chunk. FLAT: one chunk
