@@ -81,7 +81,7 @@ def parse(argv=None):
     ap.add_argument("--no-extras", action="store_true", help="headline leg only")
     ap.add_argument("--profile-case", choices=["stream", "chains", "chains_bps0", "single", "chains_l320",
                                                "chains_l400", "chains_l400_bps0",
-                                               "multispin", "planes", "planes_metro", "onchip", "tma", "pool",
+                                               "multispin", "planes", "planes_r2", "planes_metro", "onchip", "tma", "pool",
                                                "batched", "plane_jobs_smem", "plane_jobs_global",
                                                "plane_jobs_smem_norefresh"],
                     help="run one small fixed workload for a profiler capture and exit")
@@ -760,7 +760,8 @@ def leg_serving(micsa, torch, stream, n_jobs, peaks, n_cap=600, slots=256, K=128
 #                 grid-stride loop)
 #   multispin     L=32, 64 x 2: 128 sweeps, blocks of 64
 #   planes        L=160, 1 x 128, bit planes: 12 sweeps
-#   planes_metro  the same lattice, 12 Metropolis sweeps
+#   planes_r2     L=160, 1 x 2 (the headline lattice), bit planes: 24 sweeps
+#   planes_metro  the L=160 x 128 lattice, 12 Metropolis sweeps
 #   onchip        L=160, 1 x 2, on-chip engine: 2 x 64 sweeps
 #   tma           L=160, 1 x 2, TMA engine: 12 sweeps
 #   pool          64 mixed jobs, 2 ticks of 64 sweeps
@@ -796,6 +797,14 @@ def case_planes():
     g.set_launch_config(4, 128, -1, True, 0)  # direct launches
     g.run(np.full(12, 0.7), 10)
     return g.measure()[0][:4]
+
+
+def case_planes_r2():
+    g = _micsa().Micsa(160, 1, 2, 3)
+    g.set_engine("multispin_global")
+    g.set_launch_config(4, 128, -1, True, 0)  # direct launches
+    g.run(np.full(24, 0.7), 10)
+    return g.measure()[0]
 
 
 def case_planes_metro():
@@ -911,7 +920,7 @@ PROFILE_CASES = {"stream": case_stream, "chains": case_chains, "multispin": case
                  "chains_bps0": lambda: case_chains(160, 2, 0), "chains_l400_bps0": lambda: case_chains(400, 2, 0),
                  "plane_jobs_smem": case_plane_jobs, "plane_jobs_global": lambda: case_plane_jobs(False),
                  "plane_jobs_smem_norefresh": lambda: case_plane_jobs(True, interval=1 << 20),
-                 "planes": case_planes, "planes_metro": case_planes_metro, "onchip": case_onchip,
+                 "planes": case_planes, "planes_r2": case_planes_r2, "planes_metro": case_planes_metro, "onchip": case_onchip,
                  "tma": case_tma, "pool": case_pool}
 
 
