@@ -160,8 +160,11 @@ int micsa_device_bytes(micsa_t h, size_t *bytes);
  * MICSA_LAUNCH_REPS for the streaming variant in which one thread updates its
  * words for every replica of its sample (rows without padding, MicSA; the bond
  * words and the neighbour offsets shared by the replicas), block 32..256 in
- * steps of 32, blocks_per_sm -1 (grid-stride loop over the resident capacity),
- * 0 (one thread per chunk) or a positive cap, pdl != 0 chains consecutive
+ * steps of 32 (the register-capped kernel takes at most 128 threads a block:
+ * fewer replica rows per block, more blocks), blocks_per_sm -1 (grid-stride
+ * loop over the resident capacity), 0 (one thread per chunk, a grid without
+ * loops: the streaming kernel's fastest form at L = 160) or a positive cap,
+ * pdl != 0 chains consecutive
  * half-sweeps with programmatic dependent launch, graph_sweeps > 0 replays a
  * captured CUDA graph of that many sweeps (0: direct launches). Synchronizes
  * the handle's stream. */
