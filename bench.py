@@ -299,11 +299,13 @@ class Timer:
         return e0.elapsed_time(e1)
 
 
-def leg_roofline(micsa, timer, stream, L, peaks, n_plain=2000, choice=None):
+def leg_roofline(micsa, timer, stream, L, peaks, n_plain=1984, choice=None):
     """Streaming half-sweep kernel in the launch shape `choice` (the tuned one;
     default shape if None): algorithmic bytes of one half-sweep of all
     replicas / mean time per half-sweep. With replica chains the half-sweep is
-    two concurrent launches (one replica each) and the time is their span."""
+    two concurrent launches (one replica each) and the time is their span. The
+    default n_plain is a multiple of the 64-sweep graph (every timed half-sweep
+    a graph node)."""
     R = 2
     g = micsa.Micsa(L, 1, R, 7, stream=stream)
     g.set_engine("stream")
