@@ -1041,7 +1041,7 @@ def main(argv=None):
 
     extras = {}
     if rank == 0 and not args.no_extras:
-        legs = [("dram_point", lambda: leg_roofline(micsa, timer, stream, 400, peaks, n_plain=300, choice=tuned)),
+        legs = [("dram_point", lambda: leg_roofline(micsa, timer, stream, 400, peaks, n_plain=320, choice=tuned)),
                 ("metropolis", lambda: leg_metropolis(micsa, timer, stream, choice=tuned)),
                 ("quench_l32", lambda: leg_quench_l32(micsa, timer, stream)),
                 ("batched", lambda: leg_batched(micsa, torch, stream, peaks)),
