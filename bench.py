@@ -299,13 +299,13 @@ class Timer:
         return e0.elapsed_time(e1)
 
 
-def leg_roofline(micsa, timer, stream, L, peaks, n_plain=1984, choice=None):
+def leg_roofline(micsa, timer, stream, L, peaks, n_plain=2048, choice=None):
     """Streaming half-sweep kernel in the launch shape `choice` (the tuned one;
     default shape if None): algorithmic bytes of one half-sweep of all
     replicas / mean time per half-sweep. With replica chains the half-sweep is
     two concurrent launches (one replica each) and the time is their span. The
-    default n_plain is a multiple of the 64-sweep graph (every timed half-sweep
-    a graph node)."""
+    default n_plain is a multiple of the 64- and 256-sweep graphs (every timed
+    half-sweep a graph node)."""
     R = 2
     g = micsa.Micsa(L, 1, R, 7, stream=stream)
     g.set_engine("stream")
@@ -1041,7 +1041,7 @@ def main(argv=None):
 
     extras = {}
     if rank == 0 and not args.no_extras:
-        legs = [("dram_point", lambda: leg_roofline(micsa, timer, stream, 400, peaks, n_plain=320, choice=tuned)),
+        legs = [("dram_point", lambda: leg_roofline(micsa, timer, stream, 400, peaks, n_plain=512, choice=tuned)),
                 ("metropolis", lambda: leg_metropolis(micsa, timer, stream, choice=tuned)),
                 ("quench_l32", lambda: leg_quench_l32(micsa, timer, stream)),
                 ("batched", lambda: leg_batched(micsa, torch, stream, peaks)),

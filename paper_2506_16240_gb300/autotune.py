@@ -53,8 +53,8 @@ def candidates(L, R=1):
     if R >= 2:  # replica groups as concurrent kernel chains in the graphs
         out += [{"engine": "stream", "words_per_thread": 4, "block": blk, "blocks_per_sm": bps, "chains": 2}
                 for blk, bps in itertools.product([64, 128, 256], [-1, 0, 3, 4])]
-        out += [{"engine": "stream", "words_per_thread": 4, "block": blk, "blocks_per_sm": -1, "chains": 2,
-                 "graph_sweeps": 256} for blk in (64, 128)]
+        out += [{"engine": "stream", "words_per_thread": 4, "block": blk, "blocks_per_sm": bps, "chains": 2,
+                 "graph_sweeps": 256} for blk, bps in itertools.product((64, 128), (-1, 0))]
         # two rows per thread (rows without padding)
         out += [{"engine": "stream", "words_per_thread": nw | 512, "block": blk, "blocks_per_sm": -1, "chains": 2}
                 for nw, blk in itertools.product([2, 4], [64, 128])]
