@@ -234,7 +234,8 @@ def test_replicas_in_one_thread_match_oracle(L, S, R, gamma, cfg):
         assert_same_state(g, st, f"L={L} S={S} R={R} gamma={gamma} {cfg}")
 
 
-@pytest.mark.parametrize("L,S,R,gamma", [(16, 3, 11, 1), (18, 2, 9, 1), (24, 2, 3, 3), (20, 1, 17, 2)])
+@pytest.mark.parametrize("L,S,R,gamma", [(16, 3, 11, 1), (18, 2, 9, 1), (24, 2, 3, 3), (20, 1, 17, 2), (2, 2, 3, 1),
+                                          (4, 1, 9, 2), (6, 3, 2, 1)])
 @pytest.mark.parametrize("cfg", [(4, 128, 0, 1, 64), (2, 256, 0, 0, 0), (1, 64, 0, 1, 8), (4 | 256, 128, 0, 1, 16)])
 def test_one_chunk_per_thread_matches_oracle(L, S, R, gamma, cfg):
     """The uncapped grid (blocks_per_sm 0) runs the loop-free body: one chunk per
