@@ -79,7 +79,7 @@ def parse(argv=None):
                     help="sweeps per step (profiling runs only; reported numbers use the default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="headline leg only")
-    ap.add_argument("--profile-case", choices=["stream", "chains", "chains_bps0", "single", "chains_l320",
+    ap.add_argument("--profile-case", choices=["stream", "chains", "chains_bps0", "chains_bps0_b160", "single", "chains_l320",
                                                "chains_l400", "chains_l400_bps0",
                                                "multispin", "planes", "planes_r2", "planes_metro", "onchip", "tma", "pool",
                                                "batched", "plane_jobs_smem", "plane_jobs_global",
@@ -762,7 +762,7 @@ def leg_serving(micsa, torch, stream, n_jobs, peaks, n_cap=600, slots=256, K=128
 #   single        the same with both replicas in each launch (one chain)
 #   chains_l320, chains_l400  as chains at L = 320 (164 MB of state) and L = 400 (320 MB)
 #   chains_bps0, chains_l400_bps0  as chains and chains_l400 with one thread per chunk (no
-#                 grid-stride loop)
+#                 grid-stride loop); chains_bps0_b160 the same in blocks of 160
 #   multispin     L=32, 64 x 2: 128 sweeps, blocks of 64
 #   planes        L=160, 1 x 128, bit planes: 12 sweeps
 #   planes_r2     L=160, 1 x 2 (the headline lattice), bit planes: 24 sweeps
@@ -787,10 +787,10 @@ def case_stream():
     return g.measure()[0]
 
 
-def case_chains(L=160, chains=2, bps=-1):
+def case_chains(L=160, chains=2, bps=-1, block=128):
     g = _micsa().Micsa(L, 1, 2, 3)
     g.set_engine("stream")
-    g.set_launch_config(4, 128, bps, True, 64)
+    g.set_launch_config(4, block, bps, True, 64)
     g.set_replica_chains(chains)
     g.run(np.full(140, 0.7), 10)  # 2 graph replays of 64 sweeps + 12 direct
     return g.measure()[0]
@@ -922,7 +922,7 @@ def pool_breakdown(ticks=6, K=256):
 PROFILE_CASES = {"stream": case_stream, "chains": case_chains, "multispin": case_multispin,
                  "single": lambda: case_chains(160, 1), "chains_l320": lambda: case_chains(320),
                  "chains_l400": lambda: case_chains(400), "batched": case_batched,
-                 "chains_bps0": lambda: case_chains(160, 2, 0), "chains_l400_bps0": lambda: case_chains(400, 2, 0),
+                 "chains_bps0_b160": lambda: case_chains(160, 2, 0, 160), "chains_bps0": lambda: case_chains(160, 2, 0), "chains_l400_bps0": lambda: case_chains(400, 2, 0),
                  "plane_jobs_smem": case_plane_jobs, "plane_jobs_global": lambda: case_plane_jobs(False),
                  "plane_jobs_smem_norefresh": lambda: case_plane_jobs(True, interval=1 << 20),
                  "planes": case_planes, "planes_r2": case_planes_r2, "planes_metro": case_planes_metro, "onchip": case_onchip,
