@@ -79,7 +79,8 @@ def parse(argv=None):
                     help="sweeps per step (profiling runs only; reported numbers use the default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="headline leg only")
-    ap.add_argument("--profile-case", choices=["stream", "chains", "chains_bps0", "chains_bps0_b160", "single", "chains_l320",
+    ap.add_argument("--profile-case", choices=["stream", "chains", "chains_bps0", "chains_bps0_b160", "chains_l400_b160",
+                                               "chains_l400_bps0_b160", "single", "chains_l320",
                                                "chains_l400", "chains_l400_bps0",
                                                "multispin", "planes", "planes_r2", "planes_metro", "onchip", "tma", "pool",
                                                "batched", "plane_jobs_smem", "plane_jobs_global",
@@ -313,19 +314,19 @@ def leg_roofline(micsa, timer, stream, L, peaks, n_plain=2048, choice=None):
         from paper_2506_16240_gb300 import autotune
         autotune.apply(g, choice)
         if L != WORKLOAD["L"]:
-            # another lattice: the grid choice of the tuned shape (grid-stride loop over
-            # the resident capacity, or one thread per chunk) that is faster at this L
+            # another lattice: the grid (grid-stride loop over the resident capacity, or
+            # one thread per chunk) and block (the tuned one or 128) that are faster at this L
             best = None
-            for bps in (-1, 0):
-                lc = g.launch_config()
-                g.set_launch_config(lc["words_per_thread"], lc["block"], bps, bool(lc["pdl"]), lc["graph_sweeps"])
-                g.run(np.full(1, 0.7), 10)
-                g.run(np.full(100, 0.7), 2 ** 31 - 1)
-                ms = timer(lambda: g.run(np.full(100, 0.7), 2 ** 31 - 1))
-                if best is None or ms < best[0]:
-                    best = (ms, bps)
-            lc = g.launch_config()
-            g.set_launch_config(lc["words_per_thread"], lc["block"], best[1], bool(lc["pdl"]), lc["graph_sweeps"])
+            lc0 = g.launch_config()
+            for blk in sorted({lc0["block"], 128}):
+                for bps in (-1, 0):
+                    g.set_launch_config(lc0["words_per_thread"], blk, bps, bool(lc0["pdl"]), lc0["graph_sweeps"])
+                    g.run(np.full(1, 0.7), 10)
+                    g.run(np.full(100, 0.7), 2 ** 31 - 1)
+                    ms = timer(lambda: g.run(np.full(100, 0.7), 2 ** 31 - 1))
+                    if best is None or ms < best[0]:
+                        best = (ms, blk, bps)
+            g.set_launch_config(lc0["words_per_thread"], best[1], best[2], bool(lc0["pdl"]), lc0["graph_sweeps"])
     g.run(np.full(1, 0.7), 10)  # t = 0 refresh; the timed sweeps below have none
     # warm-up as long as the timed run (and longer than two graph lengths), so that
     # the sweep table is sized and the sweep graph captured before the timed
@@ -762,7 +763,8 @@ def leg_serving(micsa, torch, stream, n_jobs, peaks, n_cap=600, slots=256, K=128
 #   single        the same with both replicas in each launch (one chain)
 #   chains_l320, chains_l400  as chains at L = 320 (164 MB of state) and L = 400 (320 MB)
 #   chains_bps0, chains_l400_bps0  as chains and chains_l400 with one thread per chunk (no
-#                 grid-stride loop); chains_bps0_b160 the same in blocks of 160
+#                 grid-stride loop); chains_bps0_b160, chains_l400_b160, chains_l400_bps0_b160
+#                 the same in blocks of 160
 #   multispin     L=32, 64 x 2: 128 sweeps, blocks of 64
 #   planes        L=160, 1 x 128, bit planes: 12 sweeps
 #   planes_r2     L=160, 1 x 2 (the headline lattice), bit planes: 24 sweeps
@@ -922,7 +924,7 @@ def pool_breakdown(ticks=6, K=256):
 PROFILE_CASES = {"stream": case_stream, "chains": case_chains, "multispin": case_multispin,
                  "single": lambda: case_chains(160, 1), "chains_l320": lambda: case_chains(320),
                  "chains_l400": lambda: case_chains(400), "batched": case_batched,
-                 "chains_bps0_b160": lambda: case_chains(160, 2, 0, 160), "chains_bps0": lambda: case_chains(160, 2, 0), "chains_l400_bps0": lambda: case_chains(400, 2, 0),
+                 "chains_bps0_b160": lambda: case_chains(160, 2, 0, 160), "chains_l400_b160": lambda: case_chains(400, 2, -1, 160), "chains_l400_bps0_b160": lambda: case_chains(400, 2, 0, 160), "chains_bps0": lambda: case_chains(160, 2, 0), "chains_l400_bps0": lambda: case_chains(400, 2, 0),
                  "plane_jobs_smem": case_plane_jobs, "plane_jobs_global": lambda: case_plane_jobs(False),
                  "plane_jobs_smem_norefresh": lambda: case_plane_jobs(True, interval=1 << 20),
                  "planes": case_planes, "planes_r2": case_planes_r2, "planes_metro": case_planes_metro, "onchip": case_onchip,
