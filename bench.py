@@ -559,13 +559,15 @@ def leg_metropolis(micsa, timer, stream, choice=None, n=10_000):
     T = w["T"]
     g = micsa.Micsa(w["L"], 1, w["replicas"], 3, stream=stream)
     shapes = []
-    for nw, blk, ch in [(4, 128, 2), (4, 128, 1), (2, 128, 2), (4, 256, 2), (2, 256, 1)]:
-        g.set_launch_config(nw, blk, -1, True, 64)
+    # (words per thread, block, replica chains, grid: -1 grid-stride, 0 one chunk per thread)
+    for nw, blk, ch, bps in [(4, 128, 2, -1), (4, 128, 1, -1), (2, 128, 2, -1), (4, 256, 2, -1), (2, 256, 1, -1),
+                             (4, 128, 2, 0), (4, 160, 2, 0), (2, 128, 2, 0)]:
+        g.set_launch_config(nw, blk, bps, True, 64)
         g.set_replica_chains(ch)
         g.run_metropolis(np.full(1000, T))
-        shapes.append((timer(lambda: g.run_metropolis(np.full(1000, T))), nw, blk, ch))
-    _, nw, blk, ch = min(shapes)
-    g.set_launch_config(nw, blk, -1, True, 64)
+        shapes.append((timer(lambda: g.run_metropolis(np.full(1000, T))), nw, blk, ch, bps))
+    _, nw, blk, ch, bps = min(shapes)
+    g.set_launch_config(nw, blk, bps, True, 64)
     g.set_replica_chains(ch)
     g.reinit(3)
     # warm-ups as long as the timed runs: sweep table sized, graphs captured (setup costs)
@@ -579,7 +581,7 @@ def leg_metropolis(micsa, timer, stream, choice=None, n=10_000):
     g.close()
     u = updates(w["L"], 1, w["replicas"], n)
     return {"value": u / (ms_metro * 1e6), "unit": METRIC, "sweeps": n,
-            "metropolis_launch": {"words_per_thread": nw, "block": blk, "replica_chains": ch},
+            "metropolis_launch": {"words_per_thread": nw, "block": blk, "replica_chains": ch, "blocks_per_sm": bps},
             "micsa_same_lattice": u / (ms_micsa * 1e6), "micsa_over_metropolis": ms_metro / ms_micsa}
 
 
