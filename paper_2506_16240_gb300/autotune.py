@@ -53,9 +53,9 @@ def candidates(L, R=1):
     if R >= 2:  # replica groups as concurrent kernel chains in the graphs
         out += [{"engine": "stream", "words_per_thread": 4, "block": blk, "blocks_per_sm": bps, "chains": 2}
                 for blk, bps in itertools.product([64, 128, 256], [-1, 0, 3, 4])]
-        # block sizes between: other wave and tail shapes of the one-chunk-per-thread grid
+        # the block sizes between: other wave and tail shapes of the one-chunk-per-thread grid
         out += [{"engine": "stream", "words_per_thread": 4, "block": blk, "blocks_per_sm": 0, "chains": 2}
-                for blk in (96, 160, 192)]
+                for blk in (96, 160, 192, 224)]
         out += [{"engine": "stream", "words_per_thread": 4, "block": blk, "blocks_per_sm": bps, "chains": 2,
                  "graph_sweeps": 256} for blk, bps in itertools.product((64, 128), (-1, 0))]
         # two rows per thread (rows without padding)
