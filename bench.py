@@ -79,7 +79,8 @@ def parse(argv=None):
                     help="sweeps per step (profiling runs only; reported numbers use the default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="headline leg only")
-    ap.add_argument("--profile-case", choices=["stream", "chains", "chains_bps0", "chains_bps0_b160", "chains_l400_b160",
+    ap.add_argument("--profile-case", choices=["stream", "chains", "chains_bps0", "chains_bps0_b96", "chains_bps0_b160",
+                                               "chains_bps0_b192", "chains_bps0_b224", "chains_l400_b160",
                                                "chains_l400_bps0_b160", "single", "chains_l320",
                                                "chains_l400", "chains_l400_bps0",
                                                "multispin", "planes", "planes_r2", "planes_metro", "onchip", "tma", "pool",
@@ -315,10 +316,10 @@ def leg_roofline(micsa, timer, stream, L, peaks, n_plain=2048, choice=None):
         autotune.apply(g, choice)
         if L != WORKLOAD["L"]:
             # another lattice: the grid (grid-stride loop over the resident capacity, or
-            # one thread per chunk) and block (the tuned one or 128) that are faster at this L
+            # one thread per chunk) and block (128 or 160) that are faster at this L
             best = None
             lc0 = g.launch_config()
-            for blk in sorted({lc0["block"], 128}):
+            for blk in (128, 160):  # the blocks whose traffic at this L is on record
                 for bps in (-1, 0):
                     g.set_launch_config(lc0["words_per_thread"], blk, bps, bool(lc0["pdl"]), lc0["graph_sweeps"])
                     g.run(np.full(1, 0.7), 10)
@@ -765,8 +766,8 @@ def leg_serving(micsa, torch, stream, n_jobs, peaks, n_cap=600, slots=256, K=128
 #   single        the same with both replicas in each launch (one chain)
 #   chains_l320, chains_l400  as chains at L = 320 (164 MB of state) and L = 400 (320 MB)
 #   chains_bps0, chains_l400_bps0  as chains and chains_l400 with one thread per chunk (no
-#                 grid-stride loop); chains_bps0_b160, chains_l400_b160, chains_l400_bps0_b160
-#                 the same in blocks of 160
+#                 grid-stride loop); chains_bps0_b96 / _b160 / _b192 / _b224 the same in
+#                 blocks of 96, 160, 192, 224; chains_l400_b160, chains_l400_bps0_b160 at L = 400
 #   multispin     L=32, 64 x 2: 128 sweeps, blocks of 64
 #   planes        L=160, 1 x 128, bit planes: 12 sweeps
 #   planes_r2     L=160, 1 x 2 (the headline lattice), bit planes: 24 sweeps
@@ -926,7 +927,7 @@ def pool_breakdown(ticks=6, K=256):
 PROFILE_CASES = {"stream": case_stream, "chains": case_chains, "multispin": case_multispin,
                  "single": lambda: case_chains(160, 1), "chains_l320": lambda: case_chains(320),
                  "chains_l400": lambda: case_chains(400), "batched": case_batched,
-                 "chains_bps0_b160": lambda: case_chains(160, 2, 0, 160), "chains_l400_b160": lambda: case_chains(400, 2, -1, 160), "chains_l400_bps0_b160": lambda: case_chains(400, 2, 0, 160), "chains_bps0": lambda: case_chains(160, 2, 0), "chains_l400_bps0": lambda: case_chains(400, 2, 0),
+                 "chains_bps0_b160": lambda: case_chains(160, 2, 0, 160), "chains_bps0_b96": lambda: case_chains(160, 2, 0, 96), "chains_bps0_b192": lambda: case_chains(160, 2, 0, 192), "chains_bps0_b224": lambda: case_chains(160, 2, 0, 224), "chains_l400_b160": lambda: case_chains(400, 2, -1, 160), "chains_l400_bps0_b160": lambda: case_chains(400, 2, 0, 160), "chains_bps0": lambda: case_chains(160, 2, 0), "chains_l400_bps0": lambda: case_chains(400, 2, 0),
                  "plane_jobs_smem": case_plane_jobs, "plane_jobs_global": lambda: case_plane_jobs(False),
                  "plane_jobs_smem_norefresh": lambda: case_plane_jobs(True, interval=1 << 20),
                  "planes": case_planes, "planes_r2": case_planes_r2, "planes_metro": case_planes_metro, "onchip": case_onchip,
