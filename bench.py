@@ -388,20 +388,24 @@ def plane_roofline(micsa, timer, stream, g, peaks, n_plain=1984):
 
 
 def tune_planes(g, timer, sweeps=300):
-    """Fastest (words per thread, replicas per thread) of the bit-plane engine."""
+    """Fastest (words per thread, replicas per thread, replica chains) of the
+    bit-plane engine."""
     best = None
     rpts = sorted({0} | {r for r in (1, 2, 4, 8, 16) if r <= g.R})
-    for nw in (1, 2, 4):
-        for rpt in rpts:
-            g.set_launch_config(nw, 128, -1, True, 64)
-            g.set_multispin_replicas(rpt)
-            g.run(np.full(20, 0.7), 10)
-            ms = timer(lambda: g.run(np.full(sweeps, 0.7), 10))
-            if best is None or ms < best[0]:
-                best = (ms, nw, rpt)
+    for ch in sorted({1, min(2, g.R)}):
+        for nw in (1, 2, 4):
+            for rpt in rpts:
+                g.set_replica_chains(ch)
+                g.set_launch_config(nw, 128, -1, True, 64)
+                g.set_multispin_replicas(rpt)
+                g.run(np.full(20, 0.7), 10)
+                ms = timer(lambda: g.run(np.full(sweeps, 0.7), 10))
+                if best is None or ms < best[0]:
+                    best = (ms, nw, rpt, ch)
+    g.set_replica_chains(best[3])
     g.set_launch_config(best[1], 128, -1, True, 64)
     g.set_multispin_replicas(best[2])
-    return {"words_per_thread": best[1], "replicas_per_thread": best[2]}
+    return {"words_per_thread": best[1], "replicas_per_thread": best[2], "chains": best[3]}
 
 
 def leg_multispin_l160(micsa, timer, stream, peaks, sweeps=20_000):
