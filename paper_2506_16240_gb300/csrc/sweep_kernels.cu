@@ -26,36 +26,60 @@ __device__ __forceinline__ void grid_launch_dependents() {
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// The grid-stride loops over samples, replicas and chunks for one kind of
+// sweep (REF: refresh drawn in the sweep; t and the cut points are used by the
+// refresh and Metropolis copies only).
+template <int NW, bool METRO, bool FULL, bool REF>
+__device__ __forceinline__ void half_sweep_loops(const SweepArgs &a, int alpha, int64_t t, uint64_t th0,
+                                                 uint64_t th1, uint64_t th2) {
+    const Geometry g = a.geo;
+    const uint32_t per_sample = (uint32_t)g.L * g.L * (g.W / NW);  // < 2^31 for L <= 1600
+    // grid: x over the chunks of one sample, y over samples; thread row y of
+    // the block takes replicas r0 + threadIdx.y, r0 + threadIdx.y + blockDim.y, ... < r1
+    for (int sample = blockIdx.y; sample < a.S; sample += gridDim.y)
+        for (int r = a.r0 + threadIdx.y; r < a.r1; r += blockDim.y) {
+            const int64_t gid = (int64_t)sample * a.R + r;
+            // daemon family alpha of this replica; its Philox id is gid * gamma + alpha
+            // (Metropolis draws use gid itself)
+            const int64_t fam = gid * a.gamma + alpha;
+            int8_t *spins = a.spins + gid * 2 * g.half;
+            uint8_t *daemons = a.daemons + fam * 2 * g.half;
+            const uint8_t *bonds = a.bonds + (int64_t)sample * 2 * g.half;
+            for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < per_sample; q += gridDim.x * blockDim.x) {
+                const uint32_t row = fdiv(q, a.div_chunks);
+                const int c = (int)(q - row * a.div_chunks.d);
+                update_chunk<NW, METRO, false, FULL>(g, spins, daemons, bonds, a.parity, (int)row, c,
+                                                     (uint32_t)(METRO ? gid : fam), a.key0, a.key1, t, REF, th0,
+                                                     th1, th2, a.div_L);
+            }
+        }
+}
+
 template <int NW, bool METRO, bool FULL>
 __device__ __forceinline__ void half_sweep_body(const SweepArgs &a) {
     // The sweep's parameters are read before waiting for the previous grid: no
     // kernel of a graph replay writes the table or the replay cursor (the
     // cursor is advanced by the replay's last node, and replays are ordered by
-    // the stream), so the two dependent loads overlap the wait.
+    // the stream), so the dependent loads overlap the wait. Only what selects
+    // the copy and the daemon family is read there (every field read there is a
+    // load on every sweep's path); a refresh sweep reads its index and cut
+    // points in its own copy, Metropolis needs them on every sweep.
     const int64_t kidx = a.k + (a.cursor ? *a.cursor : 0);
-    const SweepParam prm = a.params[kidx];
+    const SweepParam *pp = a.params + kidx;
+    const int mode = pp->mode, alpha = pp->alpha;
+    int64_t t = 0;
+    uint64_t th0 = 0, th1 = 0, th2 = 0;
+    if constexpr (METRO) {
+        t = pp->t;
+        th0 = pp->th0;
+        th1 = pp->th1;
+        th2 = pp->th2;
+    }
     grid_dependency_wait();  // the previous half-sweep's writes are visible after this
     grid_launch_dependents();
-    const Geometry g = a.geo;
-    const uint32_t per_sample = (uint32_t)g.L * g.L * (g.W / NW);  // < 2^31 for L <= 1600
-    const bool refresh = !METRO && prm.mode == kModeRefresh;
-
-    // grid: x over the chunks of one sample, y over samples; thread row y of
-    // the block takes replicas r0 + threadIdx.y, r0 + threadIdx.y + blockDim.y, ... < r1
-    for (int sample = blockIdx.y; sample < a.S; sample += gridDim.y)
-        for (int r = a.r0 + threadIdx.y; r < a.r1; r += blockDim.y)
-            for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < per_sample; q += gridDim.x * blockDim.x) {
-                const uint32_t row = fdiv(q, a.div_chunks);
-                const int c = (int)(q - row * a.div_chunks.d);
-                const int64_t gid = (int64_t)sample * a.R + r;
-                // daemon family alpha of this replica; its Philox id is gid * gamma + alpha
-                // (Metropolis draws use gid itself)
-                const int64_t fam = gid * a.gamma + prm.alpha;
-                update_chunk<NW, METRO, false, FULL>(g, a.spins + gid * 2 * g.half, a.daemons + fam * 2 * g.half,
-                                        a.bonds + (int64_t)sample * 2 * g.half, a.parity, (int)row, c,
-                                        (uint32_t)(METRO ? gid : fam), a.key0, a.key1, prm.t, refresh, prm.th0,
-                                        prm.th1, prm.th2, a.div_L);
-            }
+    if (METRO) half_sweep_loops<NW, true, FULL, false>(a, 0, t, th0, th1, th2);
+    else if (mode == kModeRefresh) half_sweep_loops<NW, false, FULL, true>(a, alpha, pp->t, pp->th0, pp->th1, pp->th2);
+    else half_sweep_loops<NW, false, FULL, false>(a, alpha, 0, 0, 0, 0);
 }
 
 // One chunk per thread: the grid covers every (chunk, sample, replica) exactly
