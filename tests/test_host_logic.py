@@ -320,3 +320,29 @@ def test_pool_autotuner_keeps_the_default_grid_when_no_grid_is_faster():
     choice = autotune.tune_pool(fake, ticks=1, clock=lambda: fake.now)
     assert (choice["max_words"], choice["chains"], choice["blocks_per_sm"]) == (1, 1, 0)
     assert fake.shape == (1, 1) and fake.blocks == 0
+
+
+def test_traffic_rows_are_well_formed():
+    """Every row of the steady-state traffic table that bench.py reads has a kernel
+    it knows, a digest of that kernel's sources' form, numeric byte counts and a
+    capture note naming a summary that exists in profiles/; the key of a row is
+    unique per kernel."""
+    import os
+    import re
+    import bench
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    seen = set()
+    n = 0
+    for ln in open(os.path.join(root, "profiles", "traffic.md")).read().splitlines():
+        cols = [c.strip() for c in ln.strip().strip("|").split("|")]
+        if len(cols) < 6 or cols[0] not in bench.KERNEL_SOURCES:
+            continue
+        n += 1
+        assert re.fullmatch(r"`[0-9a-f]{16}`", cols[2]), ln
+        float(cols[3]), float(cols[4])
+        summary = cols[5].split(" ")[0]
+        assert os.path.isfile(os.path.join(root, "profiles", summary)), summary
+        assert (cols[0], cols[1]) not in seen, ln
+        seen.add((cols[0], cols[1]))
+    assert n >= 2
+
